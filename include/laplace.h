@@ -1,0 +1,182 @@
+/*
+ * laplace.h -- C ABI of liblaplace.so, a GB300 (sm_103a) solver for the 2D Laplace
+ * equation discretised with the 5-point stencil, implementing the methods compared in
+ * "A Comparison of SOR, ADI and Multigrid Methods for Solving Partial Differential
+ * Equations" (arXiv 2208.02427): Jacobi, Gauss-Seidel and SOR (in red-black order),
+ * ADI line relaxation (zebra line order) and the multigrid V-cycle.
+ *
+ * Conventions shared by every entry point
+ *  - A field is m x n doubles, row-major with a row pitch: psi[j*pitch + i] is the
+ *    paper's psi_{i,j}; i = 0..m-1 runs along x, j = 0..n-1 along y (Problem
+ *    Definition, Eq. 4). pitch >= m, in elements. The outer ring (i = 0, i = m-1,
+ *    j = 0, j = n-1) holds the Dirichlet data and is never written.
+ *  - beta = dx/dy and d = 2(1 + beta^2) as in Eq. 5.
+ *  - Device pointers are owned by the caller; the library never frees them. They must
+ *    be 8-byte aligned device memory of the current device. Scratch memory belongs to
+ *    a lap_handle (see lap_create) and is bounded by its HBM budget.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream). Work is stream-ordered.
+ *    Entry points that return host values (lap_solve, lap_residual, lap_coarse_solve's
+ *    status) synchronise that stream before they return; the others only enqueue.
+ *  - Return value: LAP_OK (0) or a negative LAP_E* code; lap_strerror names it. No
+ *    exception or signal crosses the ABI. After LAP_ECUDA the device state is
+ *    whatever CUDA reported; the handle stays valid for lap_destroy.
+ *  - A lap_handle is not thread-safe: use one handle per host thread.
+ *
+ * Arithmetic: FP64 throughout. Jacobi, Gauss-Seidel, SOR, the multigrid smoother,
+ * residual, restriction and interpolation evaluate exactly the expressions written in
+ * each entry's comment, with every multiply-add fused where the comment says fma and
+ * nowhere else, so their results do not depend on the launch configuration. Line
+ * solves, the coarsest-grid solve and norms are reassociated for parallelism.
+ */
+#ifndef LAPLACE_H
+#define LAPLACE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LAP_ABI_VERSION 1
+
+enum {
+    LAP_OK = 0,
+    LAP_EINVAL = -1,       /* an argument is out of range (message via lap_last_error) */
+    LAP_ENOMEM = -2,       /* the handle's HBM budget or the device cannot hold the scratch */
+    LAP_ECUDA = -3,        /* a CUDA call failed */
+    LAP_EUNSUPPORTED = -4  /* valid but outside this build's limits (e.g. very long lines) */
+};
+
+typedef enum {
+    LAP_JACOBI = 0,  /* Eq. 5, out of place (a scratch copy of psi) */
+    LAP_GS_RB = 1,   /* Eq. 6, red (i+j even) then black points */
+    LAP_SOR_RB = 2,  /* Eq. 7, red then black points */
+    LAP_ADI = 3,     /* x-lines then y-lines per iteration (ADI subsection, Eqs. 8-10) */
+    LAP_MG = 4       /* V-cycle (Multigrid Method subsection, steps 1-11) */
+} lap_method;
+
+typedef enum {
+    LAP_NORM_L2_REL = 0,  /* stop when ||r(psi^k)||_2 <= tol * ||r(psi^0)||_2 */
+    LAP_NORM_L2_ABS = 1,  /* stop when ||r(psi^k)||_2 <= tol */
+    LAP_NORM_MAXDELTA = 2 /* stop when max|psi^k - psi^(k-1)| <= tol (Eq. 16) */
+} lap_norm;
+
+typedef enum {
+    LAP_FORM_A = 0, /* SLORA: solve the line system of Eq. 8, then relax (Eq. 9) */
+    LAP_FORM_B = 1  /* SLORB: relaxation inside the line system (Eq. 10) */
+} lap_line_form;
+
+typedef enum { LAP_CONVERGED = 0, LAP_MAXITER = 1, LAP_DIVERGED = 2 } lap_status;
+
+/* The grid of Eq. 4: m points along x, n along y, spacings dx and dy (> 0). */
+typedef struct {
+    int32_t m, n;     /* >= 3 each */
+    double dx, dy;
+    int64_t pitch;    /* row pitch of the field, in doubles, >= m */
+} lap_grid;
+
+typedef struct {
+    int32_t method;       /* lap_method */
+    double w;             /* relaxation factor: SOR (Eq. 7), ADI (Eqs. 9/10); in (0, 2) */
+    double tol;           /* stopping tolerance (>= 0; 0 = run max_iter iterations) */
+    int32_t norm;         /* lap_norm */
+    int64_t max_iter;     /* iteration cap (V-cycles for LAP_MG), >= 0 */
+    int32_t check_every;  /* test the stopping rule every this many iterations (>= 1);
+                             the last iteration is always tested */
+    int32_t nu1, nu2;     /* LAP_MG: pre/post smoothing sweeps (red-black) */
+    int32_t coarsest_min; /* LAP_MG: coarsen while both coarse sides stay >= this (>= 3) */
+    int32_t max_levels;   /* LAP_MG: 0 = as many as the sizes allow */
+    double smoother_w;    /* LAP_MG: smoother relaxation; 1 = Gauss-Seidel (Eq. 6) */
+    int32_t line_form;    /* LAP_ADI: lap_line_form */
+} lap_params;
+
+typedef struct {
+    int32_t status;  /* lap_status */
+    int64_t iters;   /* iterations (V-cycles) performed */
+    double r0;       /* ||r(psi^0)||_2 of the scaled residual dx^2 L(psi), Eqs. 11-12 */
+    double r_final;  /* ||r||_2 after the last iteration */
+    double last_check; /* the stopping-rule value at the last test (ratio for L2_REL) */
+} lap_result;
+
+typedef struct lap_handle_s* lap_handle;
+
+/* Defaults: SOR w = 1.0, tol 1e-10, L2_REL, max_iter 100000, check_every 1, MG V(2,2)
+ * down to coarsest side 5 with a Gauss-Seidel smoother, ADI form A. */
+void lap_default_params(lap_params* p);
+
+/* Create a handle on CUDA device `device` whose scratch memory may grow up to
+ * hbm_budget_bytes (0 = no limit beyond the device's). Returns LAP_EINVAL for a bad
+ * device, LAP_ECUDA if the device cannot be made current. */
+int lap_create(lap_handle* out, size_t hbm_budget_bytes, int device);
+
+/* Free every scratch buffer and table of the handle (synchronises its device). */
+void lap_destroy(lap_handle h);
+
+/* Scratch bytes lap_solve needs for this grid and method (admission against a budget). */
+int lap_workspace_bytes(const lap_grid* g, const lap_params* p, size_t* bytes);
+
+/* Iterate p->method on psi_dev until the stopping rule (p->norm, p->tol) holds or
+ * p->max_iter iterations are done; psi_dev holds the Dirichlet ring and the initial
+ * interior on entry and the last iterate on return. *out (host) receives the status,
+ * iteration count and norms. A non-finite norm stops the solve with LAP_DIVERGED.
+ * The stopping rule is tested after iterations check_every, 2 check_every, ... and
+ * after the last. Synchronises `stream` before returning. */
+int lap_solve(lap_handle h, const lap_grid* g, double* psi_dev, const lap_params* p,
+              lap_result* out, void* stream);
+
+/* ||r||_2 over interior nodes of the scaled residual of Eqs. 11-12,
+ * r = fma(-d, psi, fma(beta^2, N + S, E + W) [+ q]), written to *out (host).
+ * q_dev may be NULL (Laplace) or a field with the same pitch (coarse-level source). */
+int lap_residual(lap_handle h, const lap_grid* g, const double* psi_dev, const double* q_dev,
+                 double* out, void* stream);
+
+/* nsweeps red-black sweeps in place (Eq. 6 when w == 1, Eq. 7 otherwise) of
+ * (E+W) + beta^2 (N+S) - d psi + q = 0: red points then black points each sweep,
+ *   g = (fma(beta^2, N + S, E + W) [+ q]) * (1/d);  psi = w == 1 ? g : fma(w, g, (1-w) psi).
+ * q_dev may be NULL. This is the multigrid smoother (V-cycle steps 1, 4, 9, 11). */
+int lap_smooth(const lap_grid* g, double* psi_dev, const double* q_dev, double w, int nsweeps,
+               void* stream);
+
+/* One Jacobi sweep (Eq. 5) from in_dev to out_dev (distinct buffers, same pitch; the ring
+ * is copied): out = fma(beta^2, N + S, E + W) * (1/d). */
+int lap_jacobi_sweep(const lap_grid* g, const double* in_dev, double* out_dev, void* stream);
+
+/* V-cycle steps 2-3 (and 5-6): scaled residual of the fine level, restricted by full
+ * weighting to the coarse level and scaled to its equation:
+ *   qc(I,J) = 0.25 * ((4 r(2I,2J) + 2 ((r_W + r_E) + (r_S + r_N))) + ((r_SW + r_SE) + (r_NW + r_NE)))
+ * with r as in lap_residual. Also zeroes the coarse correction ec (initial guess of steps
+ * 4 and 7) when ec_dev is non-NULL. Needs (m-1), (n-1) even; the coarse grid is
+ * ((m-1)/2+1) x ((n-1)/2+1) with pitch pitch_c. r_dev is a fine-size scratch field. */
+int lap_restrict(const lap_grid* fine, const double* u_dev, const double* q_dev, double* r_dev,
+                 double* qc_dev, double* ec_dev, int64_t pitch_c, void* stream);
+
+/* V-cycle steps 8 and 10: u += bilinear interpolation of the coarse correction ec
+ * (copy at coincident nodes, 0.5 * (a + b) on edges, 0.25 * ((a + b) + (c + d)) at
+ * centres; ec's ring is read as given, zero in a V-cycle). */
+int lap_prolong_add(const lap_grid* fine, double* u_dev, const double* ec_dev, int64_t pitch_c,
+                    void* stream);
+
+/* V-cycle step 7 solved exactly: u's interior := solution of (E+W) + beta^2 (N+S) - d u + q = 0
+ * with u's ring as Dirichlet data. At most 1024 interior unknowns (LAP_EUNSUPPORTED beyond). */
+int lap_coarse_solve(lap_handle h, const lap_grid* g, double* u_dev, const double* q_dev,
+                     void* stream);
+
+/* One zebra half-sweep of line relaxation (Eqs. 8-10): direction 0 solves every x-line
+ * (row j; odd j first, then even j), direction 1 every y-line (column i; odd i first).
+ * A line system is solved exactly (partitioned Thomas with a cyclic-reduction solve of
+ * the interface unknowns); form A relaxes afterwards, form B inside the system. */
+int lap_line_sweep(lap_handle h, const lap_grid* g, double* psi_dev, double w, int form,
+                   int direction, void* stream);
+
+/* Human-readable name of a return code, and the message of the last error on this thread. */
+const char* lap_strerror(int code);
+const char* lap_last_error(void);
+
+/* Number of kernels this library has launched in this process (for launch accounting). */
+int64_t lap_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LAPLACE_H */

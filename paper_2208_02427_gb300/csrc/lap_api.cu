@@ -1,0 +1,882 @@
+// lap_api.cu -- the C ABI of liblaplace.so (declared in include/laplace.h): handles,
+// argument checks, host-side precomputation (line-solver tables, coarsest-grid inverse)
+// and the solver loops that drive the kernels on the caller's stream.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <stdexcept>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/laplace.h"
+#include "lap_internal.cuh"
+
+namespace lap {
+
+static std::atomic<int64_t> g_launches{0};
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+Coef make_coef(double dx, double dy)
+{
+    Coef c;
+    const double beta = dx / dy;
+    c.b2 = beta * beta;
+    c.d = 2.0 * (1.0 + c.b2);
+    c.inv_d = 1.0 / c.d;
+    c.unit_beta = c.b2 == 1.0;
+    int e = 0;
+    const double mant = std::frexp(c.inv_d, &e);
+    c.inv_d_shift = (mant == 0.5 && 1 - e >= 1 && 1 - e <= 60) ? 1 - e : 0;
+    return c;
+}
+
+}  // namespace lap
+
+using namespace lap;
+
+namespace {
+
+thread_local std::string t_last_error;
+
+struct Error {
+    int code;
+    std::string msg;
+};
+
+[[noreturn]] void fail(int code, const std::string& msg) { throw Error{code, msg}; }
+
+void ck(cudaError_t e, const char* what)
+{
+    if (e != cudaSuccess) fail(LAP_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+template <class F>
+int guarded(F&& body)
+{
+    try {
+        body();
+        return LAP_OK;
+    } catch (const Error& e) {
+        t_last_error = e.msg;
+        return e.code;
+    } catch (const std::bad_alloc&) {
+        t_last_error = "host allocation failed";
+        return LAP_ENOMEM;
+    } catch (...) {
+        t_last_error = "unexpected internal error";
+        return LAP_ECUDA;
+    }
+}
+
+int64_t round_up(int64_t v, int64_t a) { return (v + a - 1) / a * a; }
+
+// Host-side copy of a line-solver table set plus its device allocation.
+struct LineEntry {
+    LineTables t;
+    double* dev = nullptr;
+    size_t bytes = 0;
+};
+
+struct CoarseEntry {
+    double* dev = nullptr;
+    size_t bytes = 0;
+};
+
+}  // namespace
+
+struct lap_handle_s {
+    int device = 0;
+    size_t budget = 0;    // 0 = unlimited
+    size_t held = 0;      // bytes of device memory held (arena + tables)
+    double* arena = nullptr;
+    size_t arena_bytes = 0;
+    double* pinned = nullptr;  // 8 doubles of pinned host memory for results
+    std::map<std::tuple<int, double, double>, LineEntry> lines;
+    std::map<std::tuple<int, int, double>, CoarseEntry> coarse;
+};
+
+namespace {
+
+void set_device(lap_handle h) { ck(cudaSetDevice(h->device), "cudaSetDevice"); }
+
+void* dev_alloc(lap_handle h, size_t bytes)
+{
+    if (h->budget && h->held + bytes > h->budget)
+        fail(LAP_ENOMEM, "HBM budget of the handle exceeded (" + std::to_string(h->held + bytes) +
+                             " > " + std::to_string(h->budget) + " bytes)");
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        fail(LAP_ENOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
+    }
+    ck(e, "cudaMalloc");
+    h->held += bytes;
+    return p;
+}
+
+void dev_free(lap_handle h, void* p, size_t bytes)
+{
+    if (!p) return;
+    cudaFree(p);
+    h->held -= bytes;
+}
+
+// Scratch for one call: grows (never shrinks) the handle's arena. Nothing of the handle
+// is in flight between calls (lap_solve synchronises), so regrowing is safe.
+double* arena(lap_handle h, size_t bytes)
+{
+    bytes = (size_t)round_up((int64_t)std::max<size_t>(bytes, 256), 1 << 20);
+    if (bytes > h->arena_bytes) {
+        dev_free(h, h->arena, h->arena_bytes);
+        h->arena = nullptr;
+        h->arena_bytes = 0;
+        h->arena = (double*)dev_alloc(h, bytes);
+        h->arena_bytes = bytes;
+    }
+    return h->arena;
+}
+
+// Carves aligned sub-buffers out of a byte range.
+struct Carver {
+    char* base;
+    size_t off = 0;
+    explicit Carver(void* b) : base((char*)b) {}
+    template <class T>
+    T* take(size_t count)
+    {
+        off = (size_t)round_up((int64_t)off, 256);
+        T* p = (T*)(base + off);
+        off += count * sizeof(T);
+        return p;
+    }
+};
+// The same carving sequence without memory, to size the arena first.
+struct Sizer {
+    size_t off = 0;
+    template <class T>
+    T* take(size_t count)
+    {
+        off = (size_t)round_up((int64_t)off, 256) + count * sizeof(T);
+        return nullptr;
+    }
+};
+
+void check_grid(const lap_grid* g)
+{
+    if (!g) fail(LAP_EINVAL, "grid is NULL");
+    if (g->m < 3 || g->n < 3) fail(LAP_EINVAL, "grid needs m >= 3 and n >= 3");
+    if (!(g->dx > 0.0) || !(g->dy > 0.0) || !std::isfinite(g->dx) || !std::isfinite(g->dy))
+        fail(LAP_EINVAL, "dx and dy must be finite and > 0");
+    if (g->pitch < g->m) fail(LAP_EINVAL, "pitch must be >= m");
+    if ((int64_t)g->n * g->pitch > ((int64_t)1 << 40)) fail(LAP_EUNSUPPORTED, "field too large");
+}
+
+void check_device_ptr(lap_handle h, const void* p, const char* what, bool allow_null = false)
+{
+    if (!p) {
+        if (allow_null) return;
+        fail(LAP_EINVAL, std::string(what) + " is NULL");
+    }
+    if (((uintptr_t)p) % 8) fail(LAP_EINVAL, std::string(what) + " is not 8-byte aligned");
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        fail(LAP_EINVAL, std::string(what) + " is not a CUDA pointer");
+    }
+    if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged)
+        fail(LAP_EINVAL, std::string(what) + " is not device memory");
+    if (h && a.device != h->device)
+        fail(LAP_EINVAL, std::string(what) + " lives on another device than the handle");
+}
+
+void check_params(const lap_params* p)
+{
+    if (!p) fail(LAP_EINVAL, "params is NULL");
+    if (p->method < LAP_JACOBI || p->method > LAP_MG) fail(LAP_EINVAL, "unknown method");
+    if (p->norm < LAP_NORM_L2_REL || p->norm > LAP_NORM_MAXDELTA) fail(LAP_EINVAL, "unknown norm");
+    if (!(p->tol >= 0.0)) fail(LAP_EINVAL, "tol must be >= 0");
+    if (p->max_iter < 0) fail(LAP_EINVAL, "max_iter must be >= 0");
+    if (p->check_every < 1) fail(LAP_EINVAL, "check_every must be >= 1");
+    if ((p->method == LAP_SOR_RB || p->method == LAP_ADI) && !(p->w > 0.0 && p->w < 2.0))
+        fail(LAP_EINVAL, "w must lie in (0, 2)");
+    if (p->method == LAP_MG) {
+        if (p->nu1 < 0 || p->nu2 < 0 || p->nu1 + p->nu2 > 64)
+            fail(LAP_EINVAL, "nu1, nu2 must be >= 0 and nu1 + nu2 <= 64");
+        if (p->coarsest_min < 3) fail(LAP_EINVAL, "coarsest_min must be >= 3");
+        if (p->max_levels < 0) fail(LAP_EINVAL, "max_levels must be >= 0");
+        if (!(p->smoother_w > 0.0 && p->smoother_w < 2.0))
+            fail(LAP_EINVAL, "smoother_w must lie in (0, 2)");
+    }
+    if (p->method == LAP_ADI && p->line_form != LAP_FORM_A && p->line_form != LAP_FORM_B)
+        fail(LAP_EINVAL, "unknown line form");
+}
+
+// ---- line-solver tables --------------------------------------------------------------
+
+constexpr int LINE_MAX_CHUNKS = 128;
+constexpr int LINE_MAX_N = 16383;
+
+// Thomas solve of tridiag(-alpha, delta, -alpha) x = rhs (size len) on the host.
+std::vector<double> host_thomas(int len, double alpha, double delta, const std::vector<double>& rhs)
+{
+    std::vector<double> den(len), xp(len), x(len);
+    for (int o = 0; o < len; ++o) {
+        den[o] = o == 0 ? delta : delta - alpha * alpha / den[o - 1];
+        xp[o] = ((o == 0 ? 0.0 : alpha * xp[o - 1]) + rhs[o]) / den[o];
+    }
+    for (int o = len - 1; o >= 0; --o) x[o] = o == len - 1 ? xp[o] : xp[o] + alpha / den[o] * x[o + 1];
+    return x;
+}
+
+const LineTables& line_tables(lap_handle h, int N, double alpha, double delta)
+{
+    auto key = std::make_tuple(N, alpha, delta);
+    auto it = h->lines.find(key);
+    if (it != h->lines.end()) return it->second.t;
+    if (N > LINE_MAX_N) fail(LAP_EUNSUPPORTED, "line longer than 16383 unknowns");
+    LineTables t{};
+    t.N = N;
+    t.alpha = alpha;
+    t.delta = delta;
+    // P chunks of L unknowns, each but the last followed by one separator unknown; the
+    // last chunk holds the remaining 1..L unknowns (the line never ends on a separator)
+    t.L = std::max(1, (N - (LINE_MAX_CHUNKS - 1) + LINE_MAX_CHUNKS - 1) / LINE_MAX_CHUNKS);
+    for (;; ++t.L) {
+        t.P = (N + 1 + t.L) / (t.L + 1);  // ceil((N + 1) / (L + 1))
+        t.Ll = N - (t.P - 1) * (t.L + 1);
+        if (t.Ll >= 1) break;
+    }
+    if (t.Ll > t.L || t.P > LINE_MAX_CHUNKS) fail(LAP_ECUDA, "internal: bad line partition");
+    t.stride = (t.L + 1) | 1;
+    const int L = t.L, S = t.P - 1;
+    t.levels = 0;
+    for (int s = 1; s < S; s <<= 1) ++t.levels;
+
+    std::vector<double> inv_den(L), cpos(L);
+    double den = delta;
+    for (int o = 0; o < L; ++o) {
+        if (o) den = delta - alpha * alpha / den;
+        inv_den[o] = 1.0 / den;
+        cpos[o] = alpha / den;
+    }
+    auto influence = [&](int len, bool left) {
+        std::vector<double> rhs(len, 0.0);
+        rhs[left ? 0 : len - 1] = alpha;
+        std::vector<double> g = host_thomas(len, alpha, delta, rhs);
+        g.resize(L, 0.0);
+        return g;
+    };
+    std::vector<double> gL = influence(L, true), gR = influence(L, false);
+    std::vector<double> gLl = influence(t.Ll, true), gRl = influence(t.Ll, false);
+
+    // separator system a x_{p-1} + b x_p + c x_{p+1} = rho_p, p = 0..S-1 (see line_kernels.cu)
+    std::vector<double> a(S), b(S), c(S);
+    for (int p = 0; p < S; ++p) {
+        const bool right_last = p + 1 == t.P - 1;
+        a[p] = p >= 1 ? -alpha * gL[L - 1] : 0.0;
+        b[p] = delta - alpha * gR[L - 1] - alpha * (right_last ? gLl[0] : gL[0]);
+        c[p] = p + 1 <= S - 1 ? -alpha * gR[0] : 0.0;
+    }
+    std::vector<double> k1((size_t)t.levels * S), k2((size_t)t.levels * S), invb(S);
+    for (int lev = 0, s = 1; lev < t.levels; ++lev, s <<= 1) {
+        std::vector<double> na(S), nb(S), nc(S);
+        for (int p = 0; p < S; ++p) {
+            const double al = p - s >= 0 ? -a[p] / b[p - s] : 0.0;
+            const double ga = p + s < S ? -c[p] / b[p + s] : 0.0;
+            na[p] = p - s >= 0 ? al * a[p - s] : 0.0;
+            nc[p] = p + s < S ? ga * c[p + s] : 0.0;
+            nb[p] = b[p] + (p - s >= 0 ? al * c[p - s] : 0.0) + (p + s < S ? ga * a[p + s] : 0.0);
+            k1[(size_t)lev * S + p] = al;
+            k2[(size_t)lev * S + p] = ga;
+        }
+        a.swap(na);
+        b.swap(nb);
+        c.swap(nc);
+    }
+    for (int p = 0; p < S; ++p) invb[p] = 1.0 / b[p];
+
+    std::vector<double> blob;
+    auto put = [&](const std::vector<double>& v) {
+        size_t at = blob.size();
+        blob.insert(blob.end(), v.begin(), v.end());
+        return at;
+    };
+    size_t o_inv = put(inv_den), o_cp = put(cpos), o_gl = put(gL), o_gr = put(gR), o_gll = put(gLl),
+           o_grl = put(gRl), o_k1 = put(k1), o_k2 = put(k2), o_ib = put(invb);
+    LineEntry e;
+    e.bytes = std::max<size_t>(blob.size(), 1) * sizeof(double);
+    e.dev = (double*)dev_alloc(h, e.bytes);
+    ck(cudaMemcpy(e.dev, blob.data(), blob.size() * sizeof(double), cudaMemcpyHostToDevice),
+       "upload line tables");
+    t.inv_den = e.dev + o_inv;
+    t.cpos = e.dev + o_cp;
+    t.gL = e.dev + o_gl;
+    t.gR = e.dev + o_gr;
+    t.gLl = e.dev + o_gll;
+    t.gRl = e.dev + o_grl;
+    t.k1 = e.dev + o_k1;
+    t.k2 = e.dev + o_k2;
+    t.invb = e.dev + o_ib;
+    e.t = t;
+    return h->lines.emplace(key, e).first->second.t;
+}
+
+// One zebra half-sweep in `direction` (0: x-lines = rows, 1: y-lines = columns).
+void line_half_sweep(lap_handle h, const Field& f, const Coef& c, double w, int form,
+                     int direction, cudaStream_t s)
+{
+    const bool x = direction == 0;
+    const int N = x ? f.m - 2 : f.n - 2;
+    const int nlines = x ? f.n - 2 : f.m - 2;
+    const double off = x ? 1.0 : c.b2;
+    const double cross = x ? c.b2 : 1.0;
+    const double alpha = form == LAP_FORM_A ? off : w * off;
+    const LineTables& t = line_tables(h, N, alpha, c.d);
+    const int64_t sa = x ? 1 : f.pitch, sx = x ? f.pitch : 1;
+    for (int first = 1; first <= 2; ++first) {
+        const int count = first == 1 ? (nlines + 1) / 2 : nlines / 2;
+        ck(launch_line_colour(f.p, sa, sx, first, count, t, form, cross, w, s), "line kernel");
+    }
+}
+
+// ---- coarsest-grid inverse ------------------------------------------------------------
+
+constexpr int COARSE_MAX_UNKNOWNS = 1024;
+
+const double* coarse_inverse(lap_handle h, int m, int n, double b2, double d)
+{
+    auto key = std::make_tuple(m, n, b2);
+    auto it = h->coarse.find(key);
+    if (it != h->coarse.end()) return it->second.dev;
+    const int mi = m - 2, N = mi * (n - 2);
+    if (N > COARSE_MAX_UNKNOWNS) fail(LAP_EUNSUPPORTED, "coarsest grid has more than 1024 unknowns");
+    // A (unknowns k = (j-1) mi + (i-1)): d on the diagonal, -1 across x, -b2 across y
+    std::vector<double> A((size_t)N * N, 0.0), X((size_t)N * N, 0.0);
+    for (int k = 0; k < N; ++k) {
+        const int i = k % mi, j = k / mi;
+        A[(size_t)k * N + k] = d;
+        if (i > 0) A[(size_t)k * N + k - 1] = -1.0;
+        if (i < mi - 1) A[(size_t)k * N + k + 1] = -1.0;
+        if (j > 0) A[(size_t)k * N + k - mi] = -b2;
+        if (j < n - 3) A[(size_t)k * N + k + mi] = -b2;
+        X[(size_t)k * N + k] = 1.0;
+    }
+    // Gauss-Jordan with partial pivoting (A is symmetric positive definite, well conditioned
+    // at coarsest-grid sizes)
+    for (int col = 0; col < N; ++col) {
+        int piv = col;
+        for (int r = col + 1; r < N; ++r)
+            if (std::fabs(A[(size_t)r * N + col]) > std::fabs(A[(size_t)piv * N + col])) piv = r;
+        if (piv != col)
+            for (int t = 0; t < N; ++t) {
+                std::swap(A[(size_t)col * N + t], A[(size_t)piv * N + t]);
+                std::swap(X[(size_t)col * N + t], X[(size_t)piv * N + t]);
+            }
+        const double inv = 1.0 / A[(size_t)col * N + col];
+        for (int t = 0; t < N; ++t) {
+            A[(size_t)col * N + t] *= inv;
+            X[(size_t)col * N + t] *= inv;
+        }
+        for (int r = 0; r < N; ++r) {
+            if (r == col) continue;
+            const double f = A[(size_t)r * N + col];
+            if (f == 0.0) continue;
+            for (int t = 0; t < N; ++t) {
+                A[(size_t)r * N + t] -= f * A[(size_t)col * N + t];
+                X[(size_t)r * N + t] -= f * X[(size_t)col * N + t];
+            }
+        }
+    }
+    std::vector<double> xt((size_t)N * N);
+    for (int r = 0; r < N; ++r)
+        for (int t = 0; t < N; ++t) xt[(size_t)t * N + r] = X[(size_t)r * N + t];
+    CoarseEntry e;
+    e.bytes = xt.size() * sizeof(double);
+    e.dev = (double*)dev_alloc(h, e.bytes);
+    ck(cudaMemcpy(e.dev, xt.data(), e.bytes, cudaMemcpyHostToDevice), "upload coarse inverse");
+    return h->coarse.emplace(key, e).first->second.dev;
+}
+
+// ---- multigrid hierarchy -----------------------------------------------------------------
+
+struct Level {
+    Field u;            // level 0: the caller's field; deeper: the correction
+    double* q = nullptr;  // source term (levels >= 1)
+    double* r = nullptr;  // residual scratch (all but the coarsest), u's pitch
+};
+
+int mg_level_count(int m, int n, int coarsest_min, int max_levels)
+{
+    int levels = 1;
+    while ((max_levels <= 0 || levels < max_levels) && (m - 1) % 2 == 0 && (n - 1) % 2 == 0 &&
+           (m - 1) / 2 + 1 >= coarsest_min && (n - 1) / 2 + 1 >= coarsest_min) {
+        m = (m - 1) / 2 + 1;
+        n = (n - 1) / 2 + 1;
+        ++levels;
+    }
+    return levels;
+}
+
+// ---- the per-call workspace ----------------------------------------------------------------
+
+struct Work {
+    double* partials = nullptr;  // norm partial sums
+    double* nrm = nullptr;       // [sum, sqrt]
+    unsigned long long* maxd = nullptr;
+    double* aux = nullptr;       // Jacobi second buffer, or previous iterate for max|delta|
+    std::vector<Level> levels;
+};
+
+template <class C>
+void carve(C& cv, Work& w, const lap_grid* g, const lap_params* p)
+{
+    w.partials = cv.template take<double>(2048);
+    w.nrm = cv.template take<double>(2);
+    w.maxd = cv.template take<unsigned long long>(1);
+    const size_t field = (size_t)g->n * (size_t)g->pitch;
+    const bool need_aux =
+        p->method == LAP_JACOBI ||
+        (p->norm == LAP_NORM_MAXDELTA && (p->method == LAP_ADI || p->method == LAP_MG));
+    w.aux = need_aux ? cv.template take<double>(field) : nullptr;
+    w.levels.clear();
+    if (p->method == LAP_MG) {
+        const int L = mg_level_count(g->m, g->n, p->coarsest_min, p->max_levels);
+        int m = g->m, n = g->n;
+        for (int l = 0; l < L; ++l) {
+            Level lv;
+            const int64_t pitch = l == 0 ? g->pitch : round_up(m, 32);
+            lv.u = Field{nullptr, m, n, pitch};
+            if (l > 0) {
+                lv.u.p = cv.template take<double>((size_t)n * pitch);
+                lv.q = cv.template take<double>((size_t)n * pitch);
+            }
+            if (l < L - 1) lv.r = cv.template take<double>((size_t)n * pitch);
+            w.levels.push_back(lv);
+            m = (m - 1) / 2 + 1;
+            n = (n - 1) / 2 + 1;
+        }
+    }
+}
+
+size_t work_bytes(const lap_grid* g, const lap_params* p)
+{
+    Sizer sz;
+    Work w;
+    carve(sz, w, g, p);
+    return sz.off;
+}
+
+// ---- the solver loop ---------------------------------------------------------------------
+
+struct Solver {
+    lap_handle h;
+    cudaStream_t s;
+    Field f;
+    Coef c;
+    const lap_params* p;
+    Work w;
+
+    double residual(const Field& u, const double* q)
+    {
+        ck(launch_defect_sumsq(u, q, c, w.partials, s), "residual kernel");
+        ck(launch_sum_partials(w.partials, norm_blocks(u), w.nrm, s), "sum kernel");
+        ck(cudaMemcpyAsync(h->pinned, w.nrm + 1, sizeof(double), cudaMemcpyDeviceToHost, s),
+           "copy norm");
+        ck(cudaStreamSynchronize(s), "stream sync");
+        return h->pinned[0];
+    }
+
+    double read_maxd()
+    {
+        ck(cudaMemcpyAsync(h->pinned, w.maxd, sizeof(double), cudaMemcpyDeviceToHost, s),
+           "copy max delta");
+        ck(cudaStreamSynchronize(s), "stream sync");
+        uint64_t bits;
+        std::memcpy(&bits, h->pinned, 8);
+        double v;
+        std::memcpy(&v, &bits, 8);
+        return v;
+    }
+
+    void copy_field(double* dst, const double* src)
+    {
+        ck(cudaMemcpy2DAsync(dst, f.pitch * 8, src, f.pitch * 8, (size_t)f.m * 8, f.n,
+                             cudaMemcpyDeviceToDevice, s),
+           "copy field");
+    }
+
+    // ---- one iteration of each method ----
+    double* jac_cur = nullptr;  // Jacobi: buffer holding the current iterate
+    double* jac_other = nullptr;
+
+    void iterate(bool want_maxd)
+    {
+        unsigned long long* md = want_maxd ? w.maxd : nullptr;
+        const bool gs = p->method == LAP_GS_RB;
+        switch (p->method) {
+        case LAP_JACOBI: {
+            Field in{jac_cur, f.m, f.n, f.pitch};
+            ck(launch_jacobi(in, jac_other, c, md, s), "jacobi kernel");
+            std::swap(jac_cur, jac_other);
+            break;
+        }
+        case LAP_GS_RB:
+        case LAP_SOR_RB:
+            for (int colour = 0; colour < 2; ++colour)
+                ck(launch_rb_colour(f, nullptr, c, gs, gs ? 1.0 : p->w, colour, md, s), "rb kernel");
+            break;
+        case LAP_ADI:
+            line_half_sweep(h, f, c, p->w, p->line_form, 0, s);
+            line_half_sweep(h, f, c, p->w, p->line_form, 1, s);
+            break;
+        case LAP_MG:
+            vcycle(0);
+            break;
+        }
+    }
+
+    void smooth(const Level& lv, int sweeps)
+    {
+        const bool gs = p->smoother_w == 1.0;
+        for (int k = 0; k < sweeps; ++k)
+            for (int colour = 0; colour < 2; ++colour)
+                ck(launch_rb_colour(lv.u, lv.q, c, gs, p->smoother_w, colour, nullptr, s),
+                   "smoother kernel");
+    }
+
+    void vcycle(int l)
+    {
+        Level& lv = w.levels[l];
+        const int L = (int)w.levels.size();
+        if (l == L - 1) {
+            const double* ainv = coarse_inverse(h, lv.u.m, lv.u.n, c.b2, c.d);
+            ck(launch_coarse_solve(lv.u, lv.q, c, ainv, s), "coarse solve kernel");
+            return;
+        }
+        smooth(lv, p->nu1);
+        Level& cv = w.levels[l + 1];
+        ck(launch_defect(lv.u, lv.q, lv.r, c, s), "defect kernel");
+        ck(launch_restrict(Field{lv.r, lv.u.m, lv.u.n, lv.u.pitch}, cv.q, cv.u.p, cv.u.pitch, s),
+           "restrict kernel");
+        vcycle(l + 1);
+        ck(launch_prolong_add(lv.u, cv.u.p, cv.u.pitch, s), "prolong kernel");
+        smooth(lv, p->nu2);
+    }
+
+    void run(lap_result* out)
+    {
+        out->status = LAP_MAXITER;
+        out->iters = 0;
+        out->last_check = NAN;
+        if (p->method == LAP_JACOBI) {
+            copy_field(w.aux, f.p);  // ring + initial interior in both buffers
+            jac_cur = f.p;
+            jac_other = w.aux;
+        }
+        if (p->method == LAP_MG) {
+            w.levels[0].u.p = f.p;
+            for (size_t l = 1; l < w.levels.size(); ++l) {
+                const Field& u = w.levels[l].u;
+                ck(cudaMemsetAsync(u.p, 0, (size_t)u.n * u.pitch * 8, s), "zero coarse level");
+                ck(cudaMemsetAsync(w.levels[l].q, 0, (size_t)u.n * u.pitch * 8, s), "zero source");
+            }
+        }
+        const double r0 = residual(f, nullptr);
+        out->r0 = r0;
+        if (!std::isfinite(r0)) {
+            out->status = LAP_DIVERGED;
+        } else if ((p->norm == LAP_NORM_L2_REL && r0 == 0.0) ||
+                   (p->norm == LAP_NORM_L2_ABS && r0 <= p->tol)) {
+            out->status = LAP_CONVERGED;
+        }
+        int64_t k = 0;
+        while (out->status == LAP_MAXITER && k < p->max_iter) {
+            const int64_t steps = std::min<int64_t>(p->check_every - (k % p->check_every), p->max_iter - k);
+            const bool maxdelta = p->norm == LAP_NORM_MAXDELTA;
+            const bool fused_maxd = maxdelta && p->method != LAP_ADI && p->method != LAP_MG;
+            for (int64_t st = 0; st < steps; ++st) {
+                const bool last = st == steps - 1;
+                if (last && maxdelta) {
+                    ck(cudaMemsetAsync(w.maxd, 0, 8, s), "zero max delta");
+                    if (!fused_maxd) copy_field(w.aux, f.p);
+                }
+                iterate(last && fused_maxd);
+            }
+            k += steps;
+            double val;
+            bool conv;
+            if (maxdelta) {
+                if (!fused_maxd)
+                    ck(launch_maxdelta(f, w.aux, w.maxd, s), "max delta kernel");
+                val = read_maxd();
+                conv = val <= p->tol;
+            } else {
+                const Field cur{p->method == LAP_JACOBI ? jac_cur : f.p, f.m, f.n, f.pitch};
+                const double nr = residual(cur, nullptr);
+                val = p->norm == LAP_NORM_L2_REL ? nr / r0 : nr;
+                conv = p->norm == LAP_NORM_L2_REL ? nr <= p->tol * r0 : nr <= p->tol;
+            }
+            out->last_check = val;
+            if (!std::isfinite(val))
+                out->status = LAP_DIVERGED;
+            else if (conv)
+                out->status = LAP_CONVERGED;
+        }
+        out->iters = k;
+        if (p->method == LAP_JACOBI && jac_cur != f.p) copy_field(f.p, jac_cur);
+        out->r_final = residual(f, nullptr);
+    }
+};
+
+}  // namespace
+
+// ============================== C ABI =======================================================
+
+extern "C" {
+
+void lap_default_params(lap_params* p)
+{
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->method = LAP_SOR_RB;
+    p->w = 1.0;
+    p->tol = 1e-10;
+    p->norm = LAP_NORM_L2_REL;
+    p->max_iter = 100000;
+    p->check_every = 1;
+    p->nu1 = 2;
+    p->nu2 = 2;
+    p->coarsest_min = 5;
+    p->max_levels = 0;
+    p->smoother_w = 1.0;
+    p->line_form = LAP_FORM_A;
+}
+
+int lap_create(lap_handle* out, size_t hbm_budget_bytes, int device)
+{
+    return guarded([&] {
+        if (!out) fail(LAP_EINVAL, "out is NULL");
+        *out = nullptr;
+        int count = 0;
+        ck(cudaGetDeviceCount(&count), "cudaGetDeviceCount");
+        if (device < 0 || device >= count) fail(LAP_EINVAL, "no such CUDA device");
+        ck(cudaSetDevice(device), "cudaSetDevice");
+        lap_handle h = new lap_handle_s();
+        h->device = device;
+        h->budget = hbm_budget_bytes;
+        cudaError_t e = cudaMallocHost(&h->pinned, 8 * sizeof(double));
+        if (e != cudaSuccess) {
+            delete h;
+            ck(e, "cudaMallocHost");
+        }
+        *out = h;
+    });
+}
+
+void lap_destroy(lap_handle h)
+{
+    if (!h) return;
+    cudaSetDevice(h->device);
+    cudaDeviceSynchronize();
+    for (auto& kv : h->lines) dev_free(h, kv.second.dev, kv.second.bytes);
+    for (auto& kv : h->coarse) dev_free(h, kv.second.dev, kv.second.bytes);
+    dev_free(h, h->arena, h->arena_bytes);
+    if (h->pinned) cudaFreeHost(h->pinned);
+    delete h;
+}
+
+int lap_workspace_bytes(const lap_grid* g, const lap_params* p, size_t* bytes)
+{
+    return guarded([&] {
+        check_grid(g);
+        check_params(p);
+        if (!bytes) fail(LAP_EINVAL, "bytes is NULL");
+        *bytes = work_bytes(g, p);
+    });
+}
+
+int lap_solve(lap_handle h, const lap_grid* g, double* psi_dev, const lap_params* p,
+              lap_result* out, void* stream)
+{
+    return guarded([&] {
+        if (!h) fail(LAP_EINVAL, "handle is NULL");
+        if (!out) fail(LAP_EINVAL, "result is NULL");
+        check_grid(g);
+        check_params(p);
+        set_device(h);
+        check_device_ptr(h, psi_dev, "psi");
+        Solver sv{h, (cudaStream_t)stream, Field{psi_dev, g->m, g->n, g->pitch}, make_coef(g->dx, g->dy), p, {}};
+        if (p->method == LAP_MG) {
+            const int L = mg_level_count(g->m, g->n, p->coarsest_min, p->max_levels);
+            int m = g->m, n = g->n;
+            for (int l = 1; l < L; ++l) {
+                m = (m - 1) / 2 + 1;
+                n = (n - 1) / 2 + 1;
+            }
+            if ((int64_t)(m - 2) * (n - 2) > COARSE_MAX_UNKNOWNS)
+                fail(LAP_EUNSUPPORTED, "coarsest multigrid level has more than 1024 unknowns; "
+                                       "use sizes with (m-1), (n-1) divisible by more powers of two");
+        }
+        if (p->method == LAP_ADI && (g->m - 2 > LINE_MAX_N || g->n - 2 > LINE_MAX_N))
+            fail(LAP_EUNSUPPORTED, "ADI lines longer than 16383 unknowns");
+        const size_t need = work_bytes(g, p);
+        Carver cv(arena(h, need));
+        carve(cv, sv.w, g, p);
+        sv.run(out);
+    });
+}
+
+int lap_residual(lap_handle h, const lap_grid* g, const double* psi_dev, const double* q_dev,
+                 double* out, void* stream)
+{
+    return guarded([&] {
+        if (!h) fail(LAP_EINVAL, "handle is NULL");
+        if (!out) fail(LAP_EINVAL, "out is NULL");
+        check_grid(g);
+        set_device(h);
+        check_device_ptr(h, psi_dev, "psi");
+        check_device_ptr(h, q_dev, "q", true);
+        cudaStream_t s = (cudaStream_t)stream;
+        Carver cv(arena(h, 2048 * 8 + 1024));
+        double* partials = cv.take<double>(2048);
+        double* nrm = cv.take<double>(2);
+        const Field f{const_cast<double*>(psi_dev), g->m, g->n, g->pitch};
+        const Coef c = make_coef(g->dx, g->dy);
+        ck(launch_defect_sumsq(f, q_dev, c, partials, s), "residual kernel");
+        ck(launch_sum_partials(partials, norm_blocks(f), nrm, s), "sum kernel");
+        ck(cudaMemcpyAsync(h->pinned, nrm + 1, 8, cudaMemcpyDeviceToHost, s), "copy norm");
+        ck(cudaStreamSynchronize(s), "stream sync");
+        *out = h->pinned[0];
+    });
+}
+
+int lap_smooth(const lap_grid* g, double* psi_dev, const double* q_dev, double w, int nsweeps,
+               void* stream)
+{
+    return guarded([&] {
+        check_grid(g);
+        if (!(w > 0.0 && w < 2.0)) fail(LAP_EINVAL, "w must lie in (0, 2)");
+        if (nsweeps < 0) fail(LAP_EINVAL, "nsweeps must be >= 0");
+        check_device_ptr(nullptr, psi_dev, "psi");
+        check_device_ptr(nullptr, q_dev, "q", true);
+        const Field f{psi_dev, g->m, g->n, g->pitch};
+        const Coef c = make_coef(g->dx, g->dy);
+        for (int k = 0; k < nsweeps; ++k)
+            for (int colour = 0; colour < 2; ++colour)
+                ck(launch_rb_colour(f, q_dev, c, w == 1.0, w, colour, nullptr, (cudaStream_t)stream),
+                   "smoother kernel");
+    });
+}
+
+int lap_jacobi_sweep(const lap_grid* g, const double* in_dev, double* out_dev, void* stream)
+{
+    return guarded([&] {
+        check_grid(g);
+        check_device_ptr(nullptr, in_dev, "in");
+        check_device_ptr(nullptr, out_dev, "out");
+        if (in_dev == out_dev) fail(LAP_EINVAL, "Jacobi needs distinct in and out buffers");
+        cudaStream_t s = (cudaStream_t)stream;
+        ck(cudaMemcpy2DAsync(out_dev, g->pitch * 8, in_dev, g->pitch * 8, (size_t)g->m * 8, g->n,
+                             cudaMemcpyDeviceToDevice, s),
+           "copy ring");
+        const Field f{const_cast<double*>(in_dev), g->m, g->n, g->pitch};
+        ck(launch_jacobi(f, out_dev, make_coef(g->dx, g->dy), nullptr, s), "jacobi kernel");
+    });
+}
+
+int lap_restrict(const lap_grid* fine, const double* u_dev, const double* q_dev, double* r_dev,
+                 double* qc_dev, double* ec_dev, int64_t pitch_c, void* stream)
+{
+    return guarded([&] {
+        check_grid(fine);
+        if ((fine->m - 1) % 2 || (fine->n - 1) % 2 || fine->m < 5 || fine->n < 5)
+            fail(LAP_EINVAL, "restriction needs odd m, n >= 5");
+        if (pitch_c < (fine->m - 1) / 2 + 1) fail(LAP_EINVAL, "coarse pitch too small");
+        check_device_ptr(nullptr, u_dev, "u");
+        check_device_ptr(nullptr, q_dev, "q", true);
+        check_device_ptr(nullptr, r_dev, "r");
+        check_device_ptr(nullptr, qc_dev, "qc");
+        check_device_ptr(nullptr, ec_dev, "ec", true);
+        cudaStream_t s = (cudaStream_t)stream;
+        const Field f{const_cast<double*>(u_dev), fine->m, fine->n, fine->pitch};
+        const Coef c = make_coef(fine->dx, fine->dy);
+        ck(launch_defect(f, q_dev, r_dev, c, s), "defect kernel");
+        ck(launch_restrict(Field{r_dev, fine->m, fine->n, fine->pitch}, qc_dev, ec_dev, pitch_c, s),
+           "restrict kernel");
+    });
+}
+
+int lap_prolong_add(const lap_grid* fine, double* u_dev, const double* ec_dev, int64_t pitch_c,
+                    void* stream)
+{
+    return guarded([&] {
+        check_grid(fine);
+        if ((fine->m - 1) % 2 || (fine->n - 1) % 2 || fine->m < 5 || fine->n < 5)
+            fail(LAP_EINVAL, "interpolation needs odd m, n >= 5");
+        if (pitch_c < (fine->m - 1) / 2 + 1) fail(LAP_EINVAL, "coarse pitch too small");
+        check_device_ptr(nullptr, u_dev, "u");
+        check_device_ptr(nullptr, ec_dev, "ec");
+        ck(launch_prolong_add(Field{u_dev, fine->m, fine->n, fine->pitch}, ec_dev, pitch_c,
+                              (cudaStream_t)stream),
+           "prolong kernel");
+    });
+}
+
+int lap_coarse_solve(lap_handle h, const lap_grid* g, double* u_dev, const double* q_dev,
+                     void* stream)
+{
+    return guarded([&] {
+        if (!h) fail(LAP_EINVAL, "handle is NULL");
+        check_grid(g);
+        set_device(h);
+        check_device_ptr(h, u_dev, "u");
+        check_device_ptr(h, q_dev, "q", true);
+        const Coef c = make_coef(g->dx, g->dy);
+        const double* ainv = coarse_inverse(h, g->m, g->n, c.b2, c.d);
+        ck(launch_coarse_solve(Field{u_dev, g->m, g->n, g->pitch}, q_dev, c, ainv,
+                               (cudaStream_t)stream),
+           "coarse solve kernel");
+    });
+}
+
+int lap_line_sweep(lap_handle h, const lap_grid* g, double* psi_dev, double w, int form,
+                   int direction, void* stream)
+{
+    return guarded([&] {
+        if (!h) fail(LAP_EINVAL, "handle is NULL");
+        check_grid(g);
+        if (!(w > 0.0 && w < 2.0)) fail(LAP_EINVAL, "w must lie in (0, 2)");
+        if (form != LAP_FORM_A && form != LAP_FORM_B) fail(LAP_EINVAL, "unknown line form");
+        if (direction != 0 && direction != 1) fail(LAP_EINVAL, "direction must be 0 or 1");
+        set_device(h);
+        check_device_ptr(h, psi_dev, "psi");
+        line_half_sweep(h, Field{psi_dev, g->m, g->n, g->pitch}, make_coef(g->dx, g->dy), w, form,
+                        direction, (cudaStream_t)stream);
+    });
+}
+
+const char* lap_strerror(int code)
+{
+    switch (code) {
+    case LAP_OK: return "ok";
+    case LAP_EINVAL: return "invalid argument";
+    case LAP_ENOMEM: return "out of device memory or over the handle's HBM budget";
+    case LAP_ECUDA: return "CUDA error";
+    case LAP_EUNSUPPORTED: return "unsupported size";
+    default: return "unknown error";
+    }
+}
+
+const char* lap_last_error(void) { return t_last_error.c_str(); }
+
+int64_t lap_kernel_launches(void) { return g_launches.load(); }
+
+}  // extern "C"

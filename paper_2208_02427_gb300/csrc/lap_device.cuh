@@ -1,0 +1,65 @@
+// lap_device.cuh -- device helpers shared by the kernels of liblaplace.so.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+
+namespace lap {
+
+// x * 2^-k for k > 0, bit-identical to __dmul_rn(x, 2^-k). On GB300 the FP64 pipe
+// issues about 2 operations per clock per SM, the integer pipe 64 times more; when x is
+// normal and the result stays normal the product is just the exponent field lowered by
+// k, which the integer pipe does. Zero, subnormal, tiny, infinite and NaN inputs take
+// the FP64 multiply.
+__device__ __forceinline__ double scale_down_pow2(double x, int k, double two_pow_minus_k)
+{
+    int hi = __double2hiint(x);
+    int lo = __double2loint(x);
+    int e = (hi >> 20) & 0x7ff;
+    if (e > k && e < 0x7ff) return __hiloint2double(hi - (k << 20), lo);
+    return __dmul_rn(x, two_pow_minus_k);
+}
+
+// Multiply by 1/d: the integer-pipe path when 1/d is an exact power of two.
+template <bool POW2>
+__device__ __forceinline__ double times_inv_d(double s, double inv_d, int shift)
+{
+    if (POW2) return scale_down_pow2(s, shift, inv_d);
+    return __dmul_rn(s, inv_d);
+}
+
+// Neighbour sum of Eq. 5: fma(beta^2, N + S, E + W); with beta == 1 the fma is the add.
+template <bool UNIT_BETA>
+__device__ __forceinline__ double neighbour_sum(double w_, double e_, double s_, double n_,
+                                                double b2)
+{
+    double ew = __dadd_rn(w_, e_);
+    double ns = __dadd_rn(s_, n_);
+    return UNIT_BETA ? __dadd_rn(ns, ew) : __fma_rn(b2, ns, ew);
+}
+
+// Deterministic warp reductions (fixed xor tree).
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = __dadd_rn(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+__device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        unsigned long long u = __shfl_xor_sync(0xffffffffu, v, o);
+        v = u > v ? u : v;
+    }
+    return v;
+}
+
+// |x| as an orderable bit pattern (NaN above +inf above every finite value).
+__device__ __forceinline__ unsigned long long abs_bits(double x)
+{
+    return static_cast<unsigned long long>(__double_as_longlong(x)) & 0x7fffffffffffffffull;
+}
+
+}  // namespace lap

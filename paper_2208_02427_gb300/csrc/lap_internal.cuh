@@ -1,0 +1,97 @@
+// lap_internal.cuh -- declarations shared by the kernels and the C-ABI layer of
+// liblaplace.so. Not part of the public ABI (include/laplace.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+
+namespace lap {
+
+// Coefficients of the 5-point equation (E+W) + b2 (N+S) - d psi (+ q) = 0, Eq. 5.
+struct Coef {
+    double b2;      // beta^2, beta = dx/dy
+    double d;       // 2 (1 + beta^2)
+    double inv_d;   // the double nearest 1/d
+    bool unit_beta; // b2 == 1: fma(b2, x, y) == x + y, the multiply is skipped
+    int inv_d_shift;// > 0 when inv_d == 2^-inv_d_shift exactly (d a power of two)
+};
+Coef make_coef(double dx, double dy);
+
+// A pitched field of doubles on the device.
+struct Field {
+    double* p;
+    int m, n;
+    int64_t pitch;
+};
+
+// Every kernel launch of the library goes through this counter.
+void note_launch();
+
+// ---- point kernels (point_kernels.cu) -------------------------------------------
+// One colour of a red-black sweep, in place: Gauss-Seidel (Eq. 6) when gs is true,
+// SOR (Eq. 7) otherwise; q may be null. maxd (nullable) accumulates max|new - old| as
+// the bit pattern of a non-negative double.
+cudaError_t launch_rb_colour(const Field& f, const double* q, const Coef& c, bool gs, double w,
+                             int colour, unsigned long long* maxd, cudaStream_t s);
+// One Jacobi sweep (Eq. 5) from in to out (same pitch; ring not touched).
+cudaError_t launch_jacobi(const Field& in, double* out, const Coef& c, unsigned long long* maxd,
+                          cudaStream_t s);
+// r := scaled residual on interior nodes (Eqs. 11-12); r has f's pitch.
+cudaError_t launch_defect(const Field& f, const double* q, double* r, const Coef& c,
+                          cudaStream_t s);
+// sum of squares of the residual into per-block partials; partials[nblocks].
+int norm_blocks(const Field& f);
+cudaError_t launch_defect_sumsq(const Field& f, const double* q, const Coef& c, double* partials,
+                                cudaStream_t s);
+// out[0] = sum(partials[0..count)), fixed order; out[1] = sqrt(out[0]).
+cudaError_t launch_sum_partials(const double* partials, int count, double* out, cudaStream_t s);
+// maxd := max |a - b| over interior nodes (bit pattern), a and b share f's shape/pitch.
+cudaError_t launch_maxdelta(const Field& a, const double* b, unsigned long long* maxd,
+                            cudaStream_t s);
+
+// ---- multigrid transfer kernels (mg_kernels.cu) ----------------------------------
+// qc (coarse interior) := 0.25 ((4 r_c + 2 edges) + corners); ec (nullable) := 0 in the interior.
+cudaError_t launch_restrict(const Field& fine_r, double* qc, double* ec, int64_t pitch_c,
+                            cudaStream_t s);
+// u (fine interior) += bilinear interpolation of ec.
+cudaError_t launch_prolong_add(const Field& fine_u, const double* ec, int64_t pitch_c,
+                               cudaStream_t s);
+// u interior := Ainv_t^T b with b the coarse right-hand side assembled from q and u's ring.
+cudaError_t launch_coarse_solve(const Field& u, const double* q, const Coef& c,
+                                const double* ainv_t, cudaStream_t s);
+
+// ---- line relaxation (line_kernels.cu) --------------------------------------------
+// Constant-coefficient tridiagonal systems -alpha x_{k-1} + delta x_k - alpha x_{k+1} = r_k,
+// k = 1..N, solved by chunks (Thomas inside a chunk with zero ends), an exact solve of the
+// separator unknowns by cyclic reduction, and a fix-up with the chunk influence vectors.
+// Everything but the right-hand side is data-independent and precomputed on the host.
+struct LineTables {
+    int N;       // unknowns per line
+    int L;       // chunk length (full chunks)
+    int P;       // chunks; separators S = P - 1
+    int Ll;      // length of the last chunk (1..L)
+    int stride;  // shared-memory stride of a chunk (L + 1 rounded up to odd)
+    int levels;  // cyclic-reduction levels over the S separators
+    double alpha, delta;
+    // device arrays (one allocation): inv_den[L], cpos[L], gL[L], gR[L], gLl[L], gRl[L],
+    // k1[levels*S], k2[levels*S], invb[S]
+    const double* inv_den;
+    const double* cpos;
+    const double* gL;
+    const double* gR;
+    const double* gLl;
+    const double* gRl;
+    const double* k1;
+    const double* k2;
+    const double* invb;
+};
+size_t line_smem_bytes(const LineTables& t);
+int line_threads(const LineTables& t);
+// Relax every line of one zebra colour: lines first_line, first_line + 2, ... (count of
+// them). Line l's element k (0..N+1) is at psi + l * sx + k * sa; its neighbouring lines
+// at +-sx. form 0 = A (relax after), 1 = B (relaxation inside the system).
+cudaError_t launch_line_colour(double* psi, int64_t sa, int64_t sx, int first_line, int count,
+                               const LineTables& t, int form, double cross, double w,
+                               cudaStream_t s);
+
+}  // namespace lap

@@ -1,0 +1,249 @@
+// point_kernels.cu -- point relaxation sweeps, residual and norms for liblaplace.so.
+//
+// Jacobi (Eq. 5), red-black Gauss-Seidel (Eq. 6) and SOR (Eq. 7), and the scaled
+// residual r = dx^2 L(psi) (+ q) of Eqs. 11-12. Every value is computed with the same
+// sequence of correctly rounded operations as the written expression (explicit
+// __dadd_rn/__dmul_rn/__fma_rn; the file is built with --fmad=false), so results do not
+// depend on the launch shape.
+//
+// On GB300 the FP64 pipe (about 2 operations per clock per SM) and not HBM bounds these
+// sweeps; the kernels spend the minimum number of FP64 operations per point: 3 adds for
+// the neighbour sum (one more fma when beta != 1), the multiply by 1/d on the integer
+// pipe when 1/d is a power of two, and one multiply plus one fma for the SOR blend.
+#include "lap_device.cuh"
+#include "lap_internal.cuh"
+
+namespace lap {
+
+namespace {
+
+constexpr int RB_BX = 64, RB_BY = 4;   // red-black: 64 same-colour points x 4 rows
+constexpr int JA_BX = 128, JA_BY = 2;  // Jacobi: 128 points x 2 rows
+constexpr int NORM_THREADS = 256;
+constexpr int NORM_MAX_BLOCKS = 1216;  // 8 per SM on 152 SMs
+
+__device__ __forceinline__ void flush_maxd(unsigned long long v, unsigned long long* maxd)
+{
+    v = warp_max_u64(v);
+    if ((threadIdx.x & 31) == 0 && v) atomicMax(maxd, v);
+}
+
+// One colour of a red-black sweep. Thread (t, row j) updates the t-th point of colour
+// `colour` in row j: i = 1 + ((1 + j + colour) & 1) + 2t, so that (i + j) % 2 == colour.
+template <bool UNIT_BETA, bool POW2, bool HAS_Q, bool GS, bool MAXD>
+__global__ void __launch_bounds__(RB_BX* RB_BY)
+    rb_colour_kernel(double* __restrict__ psi, const double* __restrict__ q, int m, int n,
+                     int64_t pitch, int colour, double b2, double inv_d, int shift, double w,
+                     double one_minus_w, unsigned long long* __restrict__ maxd)
+{
+    const int j = 1 + blockIdx.y * RB_BY + threadIdx.y;
+    const int i = 1 + ((1 + j + colour) & 1) + 2 * (blockIdx.x * RB_BX + threadIdx.x);
+    unsigned long long dl = 0;
+    if (j <= n - 2 && i <= m - 2) {
+        const int64_t at = (int64_t)j * pitch + i;
+        double* c = psi + at;
+        double s = neighbour_sum<UNIT_BETA>(c[-1], c[1], c[-pitch], c[pitch], b2);
+        if (HAS_Q) s = __dadd_rn(s, q[at]);
+        const double g = times_inv_d<POW2>(s, inv_d, shift);
+        const double old = *c;
+        const double nv = GS ? g : __fma_rn(w, g, __dmul_rn(one_minus_w, old));
+        *c = nv;
+        if (MAXD) dl = abs_bits(__dsub_rn(nv, old));
+    }
+    if (MAXD) flush_maxd(dl, maxd);
+}
+
+template <bool UNIT_BETA, bool POW2, bool MAXD>
+__global__ void __launch_bounds__(JA_BX* JA_BY)
+    jacobi_kernel(const double* __restrict__ in, double* __restrict__ out, int m, int n,
+                  int64_t pitch, double b2, double inv_d, int shift,
+                  unsigned long long* __restrict__ maxd)
+{
+    const int j = 1 + blockIdx.y * JA_BY + threadIdx.y;
+    const int i = 1 + blockIdx.x * JA_BX + threadIdx.x;
+    unsigned long long dl = 0;
+    if (j <= n - 2 && i <= m - 2) {
+        const int64_t at = (int64_t)j * pitch + i;
+        const double* c = in + at;
+        const double s = neighbour_sum<UNIT_BETA>(c[-1], c[1], c[-pitch], c[pitch], b2);
+        const double nv = times_inv_d<POW2>(s, inv_d, shift);
+        out[at] = nv;
+        if (MAXD) dl = abs_bits(__dsub_rn(nv, *c));
+    }
+    if (MAXD) flush_maxd(dl, maxd);
+}
+
+template <bool UNIT_BETA, bool HAS_Q>
+__device__ __forceinline__ double defect_at(const double* __restrict__ u,
+                                            const double* __restrict__ q, int64_t at,
+                                            int64_t pitch, double b2, double d)
+{
+    const double* c = u + at;
+    double s = neighbour_sum<UNIT_BETA>(c[-1], c[1], c[-pitch], c[pitch], b2);
+    if (HAS_Q) s = __dadd_rn(s, q[at]);
+    return __fma_rn(-d, *c, s);
+}
+
+template <bool UNIT_BETA, bool HAS_Q>
+__global__ void __launch_bounds__(JA_BX* JA_BY)
+    defect_kernel(const double* __restrict__ u, const double* __restrict__ q,
+                  double* __restrict__ r, int m, int n, int64_t pitch, double b2, double d)
+{
+    const int j = 1 + blockIdx.y * JA_BY + threadIdx.y;
+    const int i = 1 + blockIdx.x * JA_BX + threadIdx.x;
+    if (j <= n - 2 && i <= m - 2) {
+        const int64_t at = (int64_t)j * pitch + i;
+        r[at] = defect_at<UNIT_BETA, HAS_Q>(u, q, at, pitch, b2, d);
+    }
+}
+
+// Sum of r^2 over the interior: block b takes rows 1 + b, 1 + b + gridDim.x, ...; the
+// per-block partial is reduced in a fixed order, so the result depends only on (m, n).
+template <bool UNIT_BETA, bool HAS_Q>
+__global__ void __launch_bounds__(NORM_THREADS)
+    defect_sumsq_kernel(const double* __restrict__ u, const double* __restrict__ q, int m, int n,
+                        int64_t pitch, double b2, double d, double* __restrict__ partials)
+{
+    double acc = 0.0;
+    for (int j = 1 + blockIdx.x; j <= n - 2; j += gridDim.x)
+        for (int i = 1 + threadIdx.x; i <= m - 2; i += NORM_THREADS) {
+            const double r = defect_at<UNIT_BETA, HAS_Q>(u, q, (int64_t)j * pitch + i, pitch, b2, d);
+            acc = __fma_rn(r, r, acc);
+        }
+    __shared__ double red[NORM_THREADS / 32];
+    acc = warp_sum(acc);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double v = threadIdx.x < NORM_THREADS / 32 ? red[threadIdx.x] : 0.0;
+        v = warp_sum(v);
+        if (threadIdx.x == 0) partials[blockIdx.x] = v;
+    }
+}
+
+__global__ void __launch_bounds__(NORM_THREADS)
+    sum_partials_kernel(const double* __restrict__ partials, int count, double* __restrict__ out)
+{
+    double acc = 0.0;
+    for (int k = threadIdx.x; k < count; k += NORM_THREADS) acc = __dadd_rn(acc, partials[k]);
+    __shared__ double red[NORM_THREADS / 32];
+    acc = warp_sum(acc);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double v = threadIdx.x < NORM_THREADS / 32 ? red[threadIdx.x] : 0.0;
+        v = warp_sum(v);
+        if (threadIdx.x == 0) {
+            out[0] = v;
+            out[1] = sqrt(v);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(JA_BX* JA_BY)
+    maxdelta_kernel(const double* __restrict__ a, const double* __restrict__ b, int m, int n,
+                    int64_t pitch, unsigned long long* __restrict__ maxd)
+{
+    const int j = 1 + blockIdx.y * JA_BY + threadIdx.y;
+    const int i = 1 + blockIdx.x * JA_BX + threadIdx.x;
+    unsigned long long dl = 0;
+    if (j <= n - 2 && i <= m - 2) {
+        const int64_t at = (int64_t)j * pitch + i;
+        dl = abs_bits(__dsub_rn(a[at], b[at]));
+    }
+    flush_maxd(dl, maxd);
+}
+
+dim3 rb_grid(int m, int n)
+{
+    const int per_row = (m - 2 + 1) / 2;  // points of one colour in a row, at most
+    return dim3((per_row + RB_BX - 1) / RB_BX, (n - 2 + RB_BY - 1) / RB_BY);
+}
+
+dim3 point_grid(int m, int n)
+{
+    return dim3((m - 2 + JA_BX - 1) / JA_BX, (n - 2 + JA_BY - 1) / JA_BY);
+}
+
+}  // namespace
+
+#define LAP_DISPATCH_BOOL(flag, NAME, ...) \
+    do {                                   \
+        if (flag) {                        \
+            constexpr bool NAME = true;    \
+            __VA_ARGS__;                   \
+        } else {                           \
+            constexpr bool NAME = false;   \
+            __VA_ARGS__;                   \
+        }                                  \
+    } while (0)
+
+cudaError_t launch_rb_colour(const Field& f, const double* q, const Coef& c, bool gs, double w,
+                             int colour, unsigned long long* maxd, cudaStream_t s)
+{
+    const dim3 grid = rb_grid(f.m, f.n), block(RB_BX, RB_BY);
+    const double omw = 1.0 - w;
+    LAP_DISPATCH_BOOL(c.unit_beta, UB, LAP_DISPATCH_BOOL(c.inv_d_shift > 0, P2,
+        LAP_DISPATCH_BOOL(q != nullptr, HQ, LAP_DISPATCH_BOOL(gs, GS, LAP_DISPATCH_BOOL(maxd != nullptr, MD,
+            rb_colour_kernel<UB, P2, HQ, GS, MD><<<grid, block, 0, s>>>(
+                f.p, q, f.m, f.n, f.pitch, colour, c.b2, c.inv_d, c.inv_d_shift, w, omw, maxd))))));
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_jacobi(const Field& in, double* out, const Coef& c, unsigned long long* maxd,
+                          cudaStream_t s)
+{
+    const dim3 grid = point_grid(in.m, in.n), block(JA_BX, JA_BY);
+    LAP_DISPATCH_BOOL(c.unit_beta, UB, LAP_DISPATCH_BOOL(c.inv_d_shift > 0, P2,
+        LAP_DISPATCH_BOOL(maxd != nullptr, MD,
+            jacobi_kernel<UB, P2, MD><<<grid, block, 0, s>>>(in.p, out, in.m, in.n, in.pitch, c.b2,
+                                                             c.inv_d, c.inv_d_shift, maxd))));
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_defect(const Field& f, const double* q, double* r, const Coef& c,
+                          cudaStream_t s)
+{
+    const dim3 grid = point_grid(f.m, f.n), block(JA_BX, JA_BY);
+    LAP_DISPATCH_BOOL(c.unit_beta, UB, LAP_DISPATCH_BOOL(q != nullptr, HQ,
+        defect_kernel<UB, HQ><<<grid, block, 0, s>>>(f.p, q, r, f.m, f.n, f.pitch, c.b2, c.d)));
+    note_launch();
+    return cudaGetLastError();
+}
+
+int norm_blocks(const Field& f)
+{
+    const int rows = f.n - 2;
+    return rows < NORM_MAX_BLOCKS ? rows : NORM_MAX_BLOCKS;
+}
+
+cudaError_t launch_defect_sumsq(const Field& f, const double* q, const Coef& c, double* partials,
+                                cudaStream_t s)
+{
+    const int blocks = norm_blocks(f);
+    LAP_DISPATCH_BOOL(c.unit_beta, UB, LAP_DISPATCH_BOOL(q != nullptr, HQ,
+        defect_sumsq_kernel<UB, HQ><<<blocks, NORM_THREADS, 0, s>>>(f.p, q, f.m, f.n, f.pitch, c.b2,
+                                                                    c.d, partials)));
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sum_partials(const double* partials, int count, double* out, cudaStream_t s)
+{
+    sum_partials_kernel<<<1, NORM_THREADS, 0, s>>>(partials, count, out);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_maxdelta(const Field& a, const double* b, unsigned long long* maxd,
+                            cudaStream_t s)
+{
+    maxdelta_kernel<<<point_grid(a.m, a.n), dim3(JA_BX, JA_BY), 0, s>>>(a.p, b, a.m, a.n, a.pitch,
+                                                                         maxd);
+    note_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace lap

@@ -1,0 +1,80 @@
+"""The C-ABI library builds, loads without a GPU and exports every entry point that
+include/laplace.h declares; host-only calls (defaults, error strings) work on the CPU."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "laplace.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(lap_[a-z_0-9]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2208_02427_gb300 import build
+    try:
+        path = build.build()
+    except RuntimeError as exc:
+        pytest.skip(f"no CUDA toolkit to build the library: {exc}")
+    return C.CDLL(path)
+
+
+def test_header_declares_the_entry_points():
+    names = declared_functions()
+    for must in ("lap_create", "lap_destroy", "lap_solve", "lap_residual", "lap_workspace_bytes",
+                 "lap_strerror", "lap_smooth", "lap_restrict", "lap_prolong_add",
+                 "lap_coarse_solve", "lap_line_sweep", "lap_jacobi_sweep"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_host_only_calls(lib):
+    from paper_2208_02427_gb300 import binding
+    p = binding.Params()
+    lib.lap_default_params(C.byref(p))
+    assert p.method == binding.METHODS["sor"] and p.tol == 1e-10 and p.nu1 == 2 and p.nu2 == 2
+    assert p.coarsest_min == 5 and p.smoother_w == 1.0 and p.check_every == 1
+    lib.lap_strerror.restype = C.c_char_p
+    assert lib.lap_strerror(0) == b"ok"
+    assert b"invalid" in lib.lap_strerror(-1)
+
+
+def test_struct_layouts_match_header(tmp_path):
+    """Every field offset and struct size of the ctypes mirrors equals the C compiler's."""
+    import shutil
+    import subprocess
+    from paper_2208_02427_gb300 import binding
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if not cc:
+        pytest.skip("no C compiler")
+    structs = {"lap_grid": binding.Grid, "lap_params": binding.Params, "lap_result": binding.Result}
+    lines = []
+    for cname, py in structs.items():
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in py._fields_:
+            lines.append(f'printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    prog = tmp_path / "layout.c"
+    prog.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "laplace.h"\nint main(void){'
+                    + "".join(lines) + "return 0;}\n")
+    exe = tmp_path / "layout"
+    subprocess.check_call([cc, "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)])
+    seen = {}
+    for row in subprocess.check_output([str(exe)], text=True).split("\n"):
+        if row:
+            cname, key, val = row.split()
+            seen[(cname, key)] = int(val)
+    for cname, py in structs.items():
+        assert seen[(cname, "size")] == C.sizeof(py)
+        for fname, _ in py._fields_:
+            assert seen[(cname, fname)] == getattr(py, fname).offset, (cname, fname)
