@@ -1,0 +1,376 @@
+"""Benchmark: Laplace solves/s to a 1e-10 relative residual on the 4097 x 4097 grid.
+
+Workload (seeded, synthetic): 4097 x 4097, dx = dy = 1/4096, every edge carries
+sum_{k=1..8} a_k sin(k pi s) with a_k ~ U[-1, 1], interior zero. One step solves it,
+from the same initial field, with
+  * red-black SOR at w_opt = 2 / (1 + sin(pi/4096)), residual tested every 100 sweeps, and
+  * the V(2,2) multigrid cycle down to 5 x 5, residual tested every cycle,
+each to ||r||_2 <= 1e-10 ||r_0||_2. value = solves per second over all ranks. The ADI half
+sweeps and the Jacobi sweep are timed per sweep in the same run ("kernels").
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs under torch.distributed.run, one process per GPU, each solving its own
+replica (no data-path collective); timings are the max over ranks. `--impl reference`
+times the CPU oracle on a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+M = N = 4097
+H = 1.0 / 4096
+TOL = 1e-10
+SOR_CHECK = 100
+METRIC = "Laplace solves/s to 1e-10 residual"
+WORKLOAD = "4097x4097 Laplace, sine-series Dirichlet edges, RB-SOR(w_opt) + V(2,2) multigrid"
+HBM_PEAK = None  # read from MEASURED_PEAKS.json when present
+# FP64 pipe: 2 operations (add, multiply or fused multiply-add) per clock per SM on GB300,
+# 152 SMs, 2070 MHz maximum SM clock -> 0.629 T FP64 operations/s (nominal 1.25 TFLOP/s
+# counts an fma as two flops)
+FP64_OPS_PEAK = 152 * 2 * 2.070e9
+# FP64 operations per point of one red-black SOR colour pass: 3 adds (neighbour sum),
+# 1 multiply by (1-w), 1 fma; the multiply by 1/d = 1/4 runs on the integer pipe
+SOR_OPS_PER_POINT = 5
+SOR_BYTES_PER_POINT = 16  # one fused two-colour sweep: read 8, write 8 bytes per point
+INTERIOR = (M - 2) * (N - 2)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--latency-solves", type=int, default=30, help="extra MG solves for p50/p99")
+    return ap.parse_args()
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def recorded_traffic(kernel: str):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel source is
+    unchanged since the capture (its sha256 is recorded beside the number)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    src = os.path.join(ROOT, "paper_2208_02427_gb300", "csrc", "point_kernels.cu")
+    try:
+        digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        for line in open(path):
+            parts = line.split()
+            if len(parts) >= 3 and parts[0] == kernel and parts[1] == digest:
+                return float(parts[2])
+    except OSError:
+        pass
+    return None
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, bus_id: str | None):
+        self.proc = None
+        self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                   "-lms", "200"]
+            if bus_id:
+                cmd += ["-i", bus_id]
+            self.proc = subprocess.Popen(cmd, stdout=self.file, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        self.proc.wait()
+        self.file.flush()
+        rows = []
+        for line in open(self.file.name):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) >= 9:
+                rows.append(p)
+        os.unlink(self.file.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        power = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows), "power_w_max": max(power) if power else None}
+
+
+def bus_id(dev):
+    import torch
+    p = torch.cuda.get_device_properties(dev)
+    try:
+        return f"{p.pci_domain_id:08X}:{p.pci_bus_id:02X}:{p.pci_device_id:02X}.0"
+    except AttributeError:
+        return None
+
+
+# ---- the oracle on the host (cpu_baseline and the reference arm) ----------------------
+
+def oracle_sample(psi, sor_sweeps: int, mg_cycles: int, sor_total: int, mg_total: int):
+    """Time the oracle on a bounded sample -- sor_sweeps calls of its red-black SOR sweep on
+    one buffer, and mg_cycles V(2,2) cycles through its driver (minus the two residual norms
+    the driver adds) -- and scale to whole solves with the iteration counts of this input."""
+    import ctypes as C
+
+    import numpy as np
+
+    import oracle as ora
+    from paper_2208_02427_gb300 import workloads as wl
+    w = wl.w_opt_sor(M, N)
+    buf = np.ascontiguousarray(psi, dtype=np.float64).copy()
+    ptr = buf.ctypes.data_as(C.POINTER(C.c_double))
+    lib = ora.lib()
+    t0 = time.perf_counter()
+    for _ in range(sor_sweeps):
+        lib.ora_sor_sweep(M, N, 1.0, w, ora.RB, ptr, None)
+    t_sor = (time.perf_counter() - t0) / sor_sweeps
+    t0 = time.perf_counter()
+    ora.defect_norm(psi)
+    t_norm = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    ora.solve(psi, method=ora.MG, ordering=ora.RB, dx=H, dy=H, tol=0.0, max_iter=mg_cycles)
+    t_mg = max(time.perf_counter() - t0 - 2 * t_norm, 0.0) / mg_cycles
+    solve_s = t_sor * sor_total + t_mg * mg_total
+    return {"value": 2.0 / solve_s, "unit": "solves/s", "cores": 1, "kind": "oracle",
+            "sample": f"{sor_sweeps} RB-SOR sweeps ({t_sor*1e3:.1f} ms each) + {mg_cycles} V(2,2) "
+                      f"cycles ({t_mg*1e3:.0f} ms each) of the single-threaded C oracle on the "
+                      f"4097^2 input, scaled to {sor_total} sweeps + {mg_total} cycles per solve",
+            "seconds_per_solve_pair": solve_s}
+
+
+# Iteration counts of this input to 1e-10 (RB-SOR tested every 100 sweeps; the oracle's
+# RB-SOR iterates are bitwise identical to the GPU's, so it needs the same count).
+SOR_SWEEPS_TO_TOL = 15600
+MG_CYCLES_TO_TOL = 7
+
+
+def reference_arm(args):
+    from paper_2208_02427_gb300 import replicas
+    from paper_2208_02427_gb300 import workloads as wl
+    rank, size, _ = replicas.world()
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    psi = wl.sine_edges(M, N, seed=wl.SEED_BASE + 1)
+    samples = []
+    for k in range(args.warmup + args.steps):
+        s = oracle_sample(psi, 4, 1, SOR_SWEEPS_TO_TOL, MG_CYCLES_TO_TOL)
+        if k >= args.warmup:
+            samples.append(s)
+    value = statistics.median(s["value"] for s in samples)
+    ms = 2.0 / value * 1e3
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "grid": "4097x4097", "tol": TOL},
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                             "sample": samples[0]["sample"] + " (each step one such sample)"},
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---- our arm ----------------------------------------------------------------------------
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return reference_arm(args)
+    import numpy as np
+    import torch
+    from paper_2208_02427_gb300 import binding as b
+    from paper_2208_02427_gb300 import replicas
+    from paper_2208_02427_gb300 import workloads as wl
+
+    rank, size, local = replicas.init()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(dev)
+    lap = b.Laplace(device=local)
+    psi_host = wl.sine_edges(M, N, seed=wl.SEED_BASE + 1)
+    init = b.to_field(psi_host, dev)
+    work = b.field(M, N, dev)
+    w_sor = wl.w_opt_sor(M, N)
+    sor_kw = dict(method="sor", w=w_sor, tol=TOL, check_every=SOR_CHECK, max_iter=200000)
+    mg_kw = dict(method="mg", tol=TOL, nu1=2, nu2=2, coarsest_min=5, max_iter=100)
+
+    def step(record=None):
+        out = {}
+        for name, kw in (("sor", sor_kw), ("mg", mg_kw)):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(stream):
+                work.copy_(init)
+                e0.record(stream)
+                info = lap.solve(work, H, H, stream=stream, **kw)
+                e1.record(stream)
+            stream.synchronize()
+            if info["status"] != "converged":
+                raise RuntimeError(f"{name} did not converge: {info}")
+            out[name] = dict(info, ms=e0.elapsed_time(e1))
+        return out
+
+    for _ in range(args.warmup):
+        step()
+    replicas.barrier()
+    torch.cuda.synchronize(dev)
+    clocks = Clocks(bus_id(dev))
+    launches0 = b.kernel_launches()
+    t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    per_step = [step() for _ in range(args.steps)]
+    t_end.record(stream)
+    stream.synchronize()
+    torch.cuda.synchronize(dev)
+    launches = b.kernel_launches() - launches0
+    clk = clocks.stop()
+    replicas.barrier()
+    local_ms = t_start.elapsed_time(t_end)
+    total_ms = replicas.reduce_scalar(local_ms, "max")
+    solves = replicas.reduce_scalar(2.0 * args.steps, "sum")
+    value = solves / (total_ms / 1e3)
+
+    # ---- dominant kernel: one red-black SOR colour pass, timed on the same stream -------
+    reps = 200
+    with torch.cuda.stream(stream):
+        work.copy_(init)
+        b.smooth(work, w=w_sor, nsweeps=5, dx=H, dy=H, stream=stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        b.smooth(work, w=w_sor, nsweeps=reps, dx=H, dy=H, stream=stream)
+        e1.record(stream)
+    stream.synchronize()
+    launch_s = e0.elapsed_time(e1) / 1e3 / (2 * reps)
+    pts_per_launch = INTERIOR / 2
+    ops = SOR_OPS_PER_POINT * pts_per_launch / launch_s
+    hbm_gbs = SOR_BYTES_PER_POINT / 2 * pts_per_launch / launch_s / 1e9
+    peaks = measured_peaks()
+    traffic = recorded_traffic("rb_colour_kernel")
+    roofline = {"bound": "alu", "kernel": "rb_colour_kernel (SOR, one colour)",
+                "achieved": ops / 1e12, "peak": FP64_OPS_PEAK / 1e12, "unit": "Top/s",
+                "frac": ops / FP64_OPS_PEAK, "traffic": traffic,
+                "peak_source": "derived: 152 SMs x 2 FP64 ops/clk x 2070 MHz",
+                "ms_per_launch": launch_s * 1e3,
+                "hbm_view": {"achieved_gbs": hbm_gbs, "peak_gbs": peaks.get("hbm_gbs"),
+                             "frac": hbm_gbs / peaks["hbm_gbs"] if peaks.get("hbm_gbs") else None,
+                             "bytes_per_point": SOR_BYTES_PER_POINT}}
+
+    # ---- other hot-path kernels, per sweep ------------------------------------------------
+    def kernel_ms(fn, reps):
+        with torch.cuda.stream(stream):
+            fn()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                fn()
+            e1.record(stream)
+        stream.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    other = b.field(M, N, dev)
+    other.copy_(init)
+    kernels = {}
+    ms = kernel_ms(lambda: b.smooth(work, w=1.0, nsweeps=1, dx=H, dy=H, stream=stream), 50)
+    kernels["gs_sweep"] = {"ms": ms, "fp64_ops_frac": 4 * INTERIOR / (ms / 1e3) / FP64_OPS_PEAK}
+    ms = kernel_ms(lambda: lap.line_sweep(work, 1.3, "A", 0, H, H, stream=stream), 10)
+    kernels["adi_x_half"] = {"ms": ms, "gbs_at_24B": 24 * INTERIOR / (ms / 1e3) / 1e9}
+    ms = kernel_ms(lambda: lap.line_sweep(work, 1.3, "A", 1, H, H, stream=stream), 10)
+    kernels["adi_y_half"] = {"ms": ms, "gbs_at_24B": 24 * INTERIOR / (ms / 1e3) / 1e9}
+    ms = kernel_ms(lambda: b.jacobi_sweep(init, other, H, H, stream=stream), 20)
+    kernels["jacobi_sweep_with_ring_copy"] = {"ms": ms}
+
+    # ---- latency distribution of multigrid solves ----------------------------------------
+    lat = []
+    for _ in range(args.latency_solves):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            work.copy_(init)
+            e0.record(stream)
+            lap.solve(work, H, H, stream=stream, **mg_kw)
+            e1.record(stream)
+        stream.synchronize()
+        lat.append(e0.elapsed_time(e1))
+    lat.sort()
+    latency = {"mg_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+                         "n": len(lat)},
+               "sor_ms": {"p50": statistics.median(s["sor"]["ms"] for s in per_step), "n": len(per_step)}}
+
+    # ---- end to end through the public API with host buffers -----------------------------
+    pinned = torch.from_numpy(psi_host.copy()).pin_memory()
+    out_host = torch.empty_like(pinned).pin_memory()
+    torch.cuda.synchronize(dev)
+    e2e_steps = max(1, args.steps)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        for kw in (sor_kw, mg_kw):
+            out_host.copy_(pinned)
+            lap.solve_host(out_host, H, H, work=work, stream=stream, **kw)
+    e2e_s = replicas.reduce_scalar(time.perf_counter() - t0, "max")
+    field_bytes = M * N * 8
+    e2e = {"value": replicas.reduce_scalar(2.0 * e2e_steps, "sum") / e2e_s, "unit": "solves/s",
+           "h2d_bytes_per_step": 2 * field_bytes, "d2h_bytes_per_step": 2 * field_bytes}
+
+    cpu = None
+    if rank == 0:
+        import oracle
+        oracle.build()
+        cpu = oracle_sample(psi_host, 30, 4, per_step[0]["sor"]["iters"], per_step[0]["mg"]["iters"])
+
+    lap.close()
+    replicas.finish()
+    if rank != 0:
+        return 0
+    line = {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": size, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "grid": "4097x4097", "dx": H, "tol": TOL,
+                   "norm": "L2 of the scaled residual, relative to the initial one",
+                   "sor_w": w_sor, "sor_check_every": SOR_CHECK, "mg": "V(2,2), RB Gauss-Seidel, "
+                   "full weighting, bilinear, 11 levels to 5x5, exact coarsest solve",
+                   "l2": "inputs larger than L2: field 134 MB + multigrid hierarchy",
+                   "parallelism": f"replicas x{size}"},
+        "methods": {k: {"iters": per_step[-1][k]["iters"],
+                        "ms_median": statistics.median(s[k]["ms"] for s in per_step),
+                        "r_final_over_r0": per_step[-1][k]["r_final"] / per_step[-1][k]["r0"]}
+                    for k in ("sor", "mg")},
+        "roofline": roofline, "kernels": kernels, "latency": latency,
+        "cpu_baseline": {k: v for k, v in cpu.items() if k != "seconds_per_solve_pair"},
+        "e2e": e2e, "gpu_launches": launches, "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

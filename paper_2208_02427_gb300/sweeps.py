@@ -1,0 +1,65 @@
+"""Run one hot-path kernel family repeatedly on a seeded grid and print its device time.
+
+    python -m paper_2208_02427_gb300.sweeps --method sor --m 4097 --n 4097 --iters 20
+
+Methods: jacobi, gs, sor (one red-black sweep = 2 launches), residual, adi-x, adi-y
+(zebra half sweeps), restrict, prolong, mg (one V(2,2) cycle). Used for profiling a
+single kernel under ncu: small launch counts, the same kernels the solver runs.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+
+import torch
+
+from . import binding as b
+from . import workloads as wl
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--method", default="sor")
+    ap.add_argument("--m", type=int, default=4097)
+    ap.add_argument("--n", type=int, default=4097)
+    ap.add_argument("--iters", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=2)
+    ap.add_argument("--w", type=float, default=None)
+    a = ap.parse_args()
+    m, n = a.m, a.n
+    h = 1.0 / (m - 1)
+    psi = wl.sine_edges(m, n)
+    lap = b.Laplace()
+    u = b.to_field(psi)
+    other = b.field(m, n)
+    mc, nc = (m - 1) // 2 + 1, (n - 1) // 2 + 1
+    qc, ec = b.field(mc, nc), b.field(mc, nc)
+    w = a.w if a.w is not None else wl.w_opt_sor(m, n)
+    ops = {
+        "jacobi": lambda: b.jacobi_sweep(u, other, h, h),
+        "gs": lambda: b.smooth(u, w=1.0, nsweeps=1, dx=h, dy=h),
+        "sor": lambda: b.smooth(u, w=w, nsweeps=1, dx=h, dy=h),
+        "residual": lambda: lap.residual(u, h, h),
+        "adi-x": lambda: lap.line_sweep(u, 1.3, "A", 0, h, h),
+        "adi-y": lambda: lap.line_sweep(u, 1.3, "A", 1, h, h),
+        "restrict": lambda: b.restrict(u, qc, other, ec=ec, dx=h, dy=h),
+        "prolong": lambda: b.prolong_add(u, ec, h, h),
+        "mg": lambda: lap.solve(u, h, h, method="mg", tol=0.0, max_iter=1),
+    }
+    fn = ops[a.method]
+    for _ in range(a.warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(a.iters):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    print(json.dumps({"method": a.method, "m": m, "n": n, "iters": a.iters,
+                      "ms_per_iter": e0.elapsed_time(e1) / a.iters}))
+    lap.close()
+
+
+if __name__ == "__main__":
+    main()
