@@ -169,6 +169,24 @@ int lap_coarse_solve(lap_handle h, const lap_grid* g, double* u_dev, const doubl
 int lap_line_sweep(lap_handle h, const lap_grid* g, double* psi_dev, double w, int form,
                    int direction, void* stream);
 
+/* Residual norm that allocates nothing. The paper has no counterpart: this entry point
+ * exists for callers that cannot make a device allocation -- their device memory is fully
+ * reserved by another allocator or budget, they cannot afford the synchronisation that
+ * cudaMalloc/cudaFree imply, or they hold no lap_handle.
+ * Computes the same ||r||_2 as lap_residual (same kernels, same summation order) and
+ * writes it to *out_dev, one double of device memory; nothing is returned to the host
+ * and the call only enqueues work on `stream` (read *out_dev after synchronising).
+ * psi_dev, q_dev (may be NULL) and out_dev must live on the current device.
+ * Scratch: a fixed device array of 1218 doubles (~9.5 KB) inside the library, present on
+ * every device that loads it until the process exits. The residual kernel uses at most
+ * 1216 partial sums for any grid; a call that would need more fails with
+ * LAP_EUNSUPPORTED. The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress), so make that first call before any stream capture. Every call
+ * on a device shares the array and overwrites it: calls whose work overlaps on the GPU
+ * (different streams or threads without ordering) race and must be serialised. */
+int lap_residual_noalloc(const lap_grid* g, const double* psi_dev, const double* q_dev,
+                         double* out_dev, void* stream);
+
 /* Human-readable name of a return code, and the message of the last error on this thread. */
 const char* lap_strerror(int code);
 const char* lap_last_error(void);

@@ -9,6 +9,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <stdexcept>
 #include <string>
 #include <tuple>
@@ -880,3 +881,89 @@ const char* lap_last_error(void) { return t_last_error.c_str(); }
 int64_t lap_kernel_launches(void) { return g_launches.load(); }
 
 }  // extern "C"
+
+// ============================== residual norm without allocation =========================
+//
+// lap_residual_noalloc computes the same norm as lap_residual for callers that cannot make
+// a device allocation (their device memory is fully reserved by another allocator or
+// budget, they cannot afford the device-wide synchronisation a cudaMalloc/cudaFree pair
+// implies, or they hold no lap_handle). Its scratch -- the per-block partial sums of the
+// residual kernel and the final pair [sum of squares, norm] -- lives in the file-scope
+// device array below instead of a handle's arena.
+
+namespace {
+
+// The residual kernel writes at most norm_blocks() <= 1216 partial sums (8 blocks per SM
+// on 152 SMs), whatever the grid size.
+constexpr int kNoAllocPartials = 1216;
+constexpr int kNoAllocDoubles = kNoAllocPartials + 2;  // partials, then [sum, sqrt(sum)]
+constexpr int kNoAllocMaxDevices = 64;
+
+// Device scratch shared by every call on a device, ~9.5 KB, held until the process exits.
+// In host code this name is only a stand-in; its device address comes from
+// cudaGetSymbolAddress.
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocDoubles];
+
+std::mutex g_noalloc_mutex;
+double* g_noalloc_addr[kNoAllocMaxDevices] = {};
+
+// Device address of the scratch array on `device` (the current device), looked up once
+// per device on the first call that runs there.
+double* noalloc_scratch(int device)
+{
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_addr[device]) {
+        void* p = nullptr;
+        ck(cudaGetSymbolAddress(&p, g_noalloc_scratch), "cudaGetSymbolAddress");
+        g_noalloc_addr[device] = static_cast<double*>(p);
+    }
+    return g_noalloc_addr[device];
+}
+
+void check_on_device(const void* p, int device, const char* what, bool allow_null)
+{
+    if (!p) {
+        if (allow_null) return;
+        fail(LAP_EINVAL, std::string(what) + " is NULL");
+    }
+    if (((uintptr_t)p) % 8) fail(LAP_EINVAL, std::string(what) + " is not 8-byte aligned");
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        fail(LAP_EINVAL, std::string(what) + " is not a CUDA pointer");
+    }
+    if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged)
+        fail(LAP_EINVAL, std::string(what) + " is not device memory");
+    if (a.device != device) fail(LAP_EINVAL, std::string(what) + " is not on the current device");
+}
+
+}  // namespace
+
+extern "C" int lap_residual_noalloc(const lap_grid* g, const double* psi_dev, const double* q_dev,
+                                    double* out_dev, void* stream)
+{
+    return guarded([&] {
+        check_grid(g);
+        int device = 0;
+        ck(cudaGetDevice(&device), "cudaGetDevice");
+        if (device < 0 || device >= kNoAllocMaxDevices)
+            fail(LAP_EUNSUPPORTED, "lap_residual_noalloc supports device ordinals below 64");
+        check_on_device(psi_dev, device, "psi", false);
+        check_on_device(q_dev, device, "q", true);
+        check_on_device(out_dev, device, "out", false);
+        const Field f{const_cast<double*>(psi_dev), g->m, g->n, g->pitch};
+        const int blocks = norm_blocks(f);
+        if (blocks > kNoAllocPartials)
+            fail(LAP_EUNSUPPORTED, "lap_residual_noalloc: the residual needs " +
+                                       std::to_string(blocks) + " partial sums, its scratch holds " +
+                                       std::to_string(kNoAllocPartials));
+        double* scratch = noalloc_scratch(device);
+        cudaStream_t s = (cudaStream_t)stream;
+        // every partial the sum reads is written first by this call: nothing to clear
+        ck(launch_defect_sumsq(f, q_dev, make_coef(g->dx, g->dy), scratch, s), "residual kernel");
+        ck(launch_sum_partials(scratch, blocks, scratch + kNoAllocPartials, s), "sum kernel");
+        ck(cudaMemcpyAsync(out_dev, scratch + kNoAllocPartials + 1, sizeof(double),
+                           cudaMemcpyDeviceToDevice, s),
+           "copy norm");
+    });
+}
