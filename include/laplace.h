@@ -187,6 +187,12 @@ int lap_line_sweep(lap_handle h, const lap_grid* g, double* psi_dev, double w, i
 int lap_residual_noalloc(const lap_grid* g, const double* psi_dev, const double* q_dev,
                          double* out_dev, void* stream);
 
+/* Enable (default) or disable CUDA-graph replay in lap_solve. With graphs, the
+ * iterations between two stopping tests are captured once per handle (keyed by the field,
+ * sizes and parameters) and replayed as one graph launch; the kernels and results are
+ * the same either way. */
+int lap_set_graphs(lap_handle h, int enabled);
+
 /* Human-readable name of a return code, and the message of the last error on this thread. */
 const char* lap_strerror(int code);
 const char* lap_last_error(void);

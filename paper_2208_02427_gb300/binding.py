@@ -87,6 +87,7 @@ def load():
             "lap_prolong_add": (C.c_int, [G, c_void_p, c_void_p, c_int64, c_void_p]),
             "lap_coarse_solve": (C.c_int, [c_void_p, G, c_void_p, c_void_p, c_void_p]),
             "lap_line_sweep": (C.c_int, [c_void_p, G, c_void_p, c_double, C.c_int, C.c_int, c_void_p]),
+            "lap_set_graphs": (C.c_int, [c_void_p, C.c_int]),
             "lap_strerror": (C.c_char_p, [C.c_int]),
             "lap_last_error": (C.c_char_p, []),
             "lap_kernel_launches": (c_int64, []),
@@ -179,6 +180,10 @@ class Laplace:
 
     def __exit__(self, *exc):
         self.close()
+
+    def set_graphs(self, enabled: bool):
+        """Replay each check period as a CUDA graph (default) or launch kernels one by one."""
+        _check(self._lib.lap_set_graphs(self._h, 1 if enabled else 0))
 
     def workspace_bytes(self, psi, dx=1.0, dy=1.0, **kw) -> int:
         out = C.c_size_t(0)

@@ -22,6 +22,8 @@ namespace lap {
 
 static std::atomic<int64_t> g_launches{0};
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+static int64_t launches_now() { return g_launches.load(); }
+static void add_launches(int64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 
 Coef make_coef(double dx, double dy)
 {
@@ -100,6 +102,11 @@ struct lap_handle_s {
     double* pinned = nullptr;  // 8 doubles of pinned host memory for results
     std::map<std::tuple<int, double, double>, LineEntry> lines;
     std::map<std::tuple<int, int, double>, CoarseEntry> coarse;
+    // CUDA graphs of whole check periods (the iterations between two stopping tests),
+    // keyed by every pointer and parameter baked into them; replayed on the caller's stream
+    bool use_graphs = true;
+    cudaStream_t capture = nullptr;
+    std::map<std::string, std::pair<cudaGraphExec_t, int64_t>> graphs;  // exec, kernels
 };
 
 namespace {
@@ -129,12 +136,19 @@ void dev_free(lap_handle h, void* p, size_t bytes)
     h->held -= bytes;
 }
 
+void drop_graphs(lap_handle h)
+{
+    for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second.first);
+    h->graphs.clear();
+}
+
 // Scratch for one call: grows (never shrinks) the handle's arena. Nothing of the handle
 // is in flight between calls (lap_solve synchronises), so regrowing is safe.
 double* arena(lap_handle h, size_t bytes)
 {
     bytes = (size_t)round_up((int64_t)std::max<size_t>(bytes, 256), 1 << 20);
     if (bytes > h->arena_bytes) {
+        drop_graphs(h);
         dev_free(h, h->arena, h->arena_bytes);
         h->arena = nullptr;
         h->arena_bytes = 0;
@@ -572,6 +586,100 @@ struct Solver {
         smooth(lv, p->nu2);
     }
 
+    // The iterations between two stopping tests, enqueued on stream s.
+    void period(int64_t steps, bool maxdelta, bool fused_maxd)
+    {
+        for (int64_t st = 0; st < steps; ++st) {
+            const bool last = st == steps - 1;
+            if (last && maxdelta) {
+                ck(cudaMemsetAsync(w.maxd, 0, 8, s), "zero max delta");
+                if (!fused_maxd) copy_field(w.aux, f.p);
+            }
+            iterate(last && fused_maxd);
+        }
+    }
+
+    // Host-side tables a period needs, built before capture (they upload synchronously).
+    void prepare()
+    {
+        if (p->method == LAP_ADI) {
+            for (int dir = 0; dir < 2; ++dir) {
+                const bool x = dir == 0;
+                const double off = x ? 1.0 : c.b2;
+                const int N = x ? f.m - 2 : f.n - 2;
+                const LineTables& t =
+                    line_tables(h, N, p->line_form == LAP_FORM_A ? off : p->w * off, c.d);
+                ck(prepare_line_kernels(line_smem_bytes(t)), "line kernel attributes");
+            }
+        }
+        if (p->method == LAP_MG) {
+            const Level& lv = w.levels.back();
+            coarse_inverse(h, lv.u.m, lv.u.n, c.b2, c.d);
+        }
+    }
+
+    std::string graph_key(int64_t steps, bool maxdelta, bool fused_maxd) const
+    {
+        std::string k;
+        auto put = [&](const void* v, size_t n) { k.append((const char*)v, n); };
+        const int64_t ints[] = {p->method, f.m, f.n, f.pitch, steps, maxdelta, fused_maxd,
+                                p->nu1, p->nu2, p->coarsest_min, p->max_levels, p->line_form,
+                                (int64_t)w.levels.size()};
+        const double dbl[] = {c.b2, c.d, c.inv_d, p->w, p->smoother_w};
+        const void* ptrs[] = {f.p, jac_cur, jac_other, w.aux, w.maxd, h->arena};
+        put(ints, sizeof ints);
+        put(dbl, sizeof dbl);
+        put(ptrs, sizeof ptrs);
+        return k;
+    }
+
+    // A period as one CUDA graph: captured once on the handle's own stream, replayed on s.
+    void run_period(int64_t steps, bool maxdelta, bool fused_maxd)
+    {
+        if (!h->use_graphs) {
+            period(steps, maxdelta, fused_maxd);
+            return;
+        }
+        const std::string key = graph_key(steps, maxdelta, fused_maxd);
+        auto it = h->graphs.find(key);
+        if (it == h->graphs.end()) {
+            prepare();
+            if (h->graphs.size() >= 64) drop_graphs(h);
+            if (!h->capture)
+                ck(cudaStreamCreateWithFlags(&h->capture, cudaStreamNonBlocking), "capture stream");
+            cudaStream_t caller = s;
+            double* cur0 = jac_cur;
+            double* other0 = jac_other;
+            const int64_t before = launches_now();
+            ck(cudaStreamBeginCapture(h->capture, cudaStreamCaptureModeThreadLocal), "begin capture");
+            s = h->capture;
+            cudaGraph_t g = nullptr;
+            try {
+                period(steps, maxdelta, fused_maxd);
+            } catch (...) {
+                s = caller;
+                cudaStreamEndCapture(h->capture, &g);
+                if (g) cudaGraphDestroy(g);
+                cudaGetLastError();
+                throw;
+            }
+            s = caller;
+            ck(cudaStreamEndCapture(h->capture, &g), "end capture");
+            const int64_t kernels = launches_now() - before;
+            add_launches(-kernels);  // captured, not launched
+            cudaGraphExec_t exec = nullptr;
+            const cudaError_t e = cudaGraphInstantiate(&exec, g, 0);
+            cudaGraphDestroy(g);
+            ck(e, "instantiate graph");
+            it = h->graphs.emplace(key, std::make_pair(exec, kernels)).first;
+            jac_cur = cur0;  // the host-side ping-pong state advances on replay below
+            jac_other = other0;
+        }
+        ck(cudaGraphLaunch(it->second.first, s), "launch graph");
+        add_launches(it->second.second);
+        if (p->method == LAP_JACOBI && (steps & 1)) std::swap(jac_cur, jac_other);
+    }
+
     void run(lap_result* out)
     {
         out->status = LAP_MAXITER;
@@ -603,14 +711,7 @@ struct Solver {
             const int64_t steps = std::min<int64_t>(p->check_every - (k % p->check_every), p->max_iter - k);
             const bool maxdelta = p->norm == LAP_NORM_MAXDELTA;
             const bool fused_maxd = maxdelta && p->method != LAP_ADI && p->method != LAP_MG;
-            for (int64_t st = 0; st < steps; ++st) {
-                const bool last = st == steps - 1;
-                if (last && maxdelta) {
-                    ck(cudaMemsetAsync(w.maxd, 0, 8, s), "zero max delta");
-                    if (!fused_maxd) copy_field(w.aux, f.p);
-                }
-                iterate(last && fused_maxd);
-            }
+            run_period(steps, maxdelta, fused_maxd);
             k += steps;
             double val;
             bool conv;
@@ -689,6 +790,8 @@ void lap_destroy(lap_handle h)
     cudaDeviceSynchronize();
     for (auto& kv : h->lines) dev_free(h, kv.second.dev, kv.second.bytes);
     for (auto& kv : h->coarse) dev_free(h, kv.second.dev, kv.second.bytes);
+    drop_graphs(h);
+    if (h->capture) cudaStreamDestroy(h->capture);
     dev_free(h, h->arena, h->arena_bytes);
     if (h->pinned) cudaFreeHost(h->pinned);
     delete h;
@@ -861,6 +964,14 @@ int lap_line_sweep(lap_handle h, const lap_grid* g, double* psi_dev, double w, i
         check_device_ptr(h, psi_dev, "psi");
         line_half_sweep(h, Field{psi_dev, g->m, g->n, g->pitch}, make_coef(g->dx, g->dy), w, form,
                         direction, (cudaStream_t)stream);
+    });
+}
+
+int lap_set_graphs(lap_handle h, int enabled)
+{
+    return guarded([&] {
+        if (!h) fail(LAP_EINVAL, "handle is NULL");
+        h->use_graphs = enabled != 0;
     });
 }
 

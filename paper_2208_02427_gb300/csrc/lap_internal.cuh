@@ -86,6 +86,7 @@ struct LineTables {
     const double* invb;
 };
 size_t line_smem_bytes(const LineTables& t);
+cudaError_t prepare_line_kernels(size_t smem);
 int line_threads(const LineTables& t);
 // Relax every line of one zebra colour: lines first_line, first_line + 2, ... (count of
 // them). Line l's element k (0..N+1) is at psi + l * sx + k * sa; its neighbouring lines

@@ -137,6 +137,25 @@ int line_threads(const LineTables& t)
     return th < 64 ? 64 : th;
 }
 
+// Raise the dynamic shared-memory limit of every line-kernel instantiation to `smem`
+// (done outside stream capture; launches below only repeat it when a larger line comes).
+static size_t g_line_smem_set = 48 * 1024;
+
+cudaError_t prepare_line_kernels(size_t smem)
+{
+    if (smem <= g_line_smem_set) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(line_colour_kernel<0, true>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(line_colour_kernel<0, false>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(line_colour_kernel<1, false>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) g_line_smem_set = smem;
+    return e;
+}
+
 cudaError_t launch_line_colour(double* psi, int64_t sa, int64_t sx, int first_line, int count,
                                const LineTables& t, int form, double cross, double w,
                                cudaStream_t s)
@@ -151,9 +170,7 @@ cudaError_t launch_line_colour(double* psi, int64_t sa, int64_t sx, int first_li
 #define LAP_LINE(F, U)                                                                          \
     do {                                                                                        \
         auto kern = line_colour_kernel<F, U>;                                                   \
-        if (smem > 48 * 1024)                                                                   \
-            err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,        \
-                                       (int)smem);                                              \
+        err = prepare_line_kernels(smem);                                                       \
         if (err == cudaSuccess)                                                                 \
             kern<<<count, threads, smem, s>>>(psi, sa, sx, first_line, t, cross, w, dmw, wcross); \
     } while (0)

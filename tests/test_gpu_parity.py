@@ -359,3 +359,32 @@ def test_host_buffer_solve_equals_device_solve(lap, b):
     t = b.to_field(psi)
     g2 = lap.solve(t, method="mg", tol=1e-10)
     assert g1["iters"] == g2["iters"] and np.array_equal(pinned.numpy(), host(t))
+
+
+@pytest.mark.parametrize("kw", [
+    dict(method="jacobi", max_iter=23, check_every=5),
+    dict(method="jacobi", max_iter=20, check_every=4, norm="maxdelta", tol=0.0),
+    dict(method="sor", w=1.7, max_iter=25, check_every=7),
+    dict(method="gs", max_iter=9, check_every=3, norm="maxdelta", tol=0.0),
+    dict(method="adi", w=1.2, line_form="B", max_iter=5, check_every=2),
+    dict(method="mg", max_iter=4, check_every=1),
+    dict(method="mg", max_iter=3, check_every=2, norm="maxdelta", tol=0.0),
+])
+def test_graph_replay_equals_direct_launches(b, kw):
+    kw = dict(kw)
+    kw.setdefault("tol", 0.0)
+    psi = rand_field(65, 33, 21)
+    outs = []
+    t = b.field(65, 33)  # one field: the third solve replays the graph the second captured
+    h = b.Laplace()
+    for graphs in (False, True, True):  # direct, graph capture, graph replay from cache
+        h.set_graphs(graphs)
+        t.copy_(torch.from_numpy(psi))
+        before = b.kernel_launches()
+        g = h.solve(t, 0.9, 1.0, **kw)
+        outs.append((host(t), (g["iters"], g["r_final"], g["last_check"]), h,
+                     b.kernel_launches() - before))
+    outs[0][2].close()
+    for o in outs[1:]:
+        assert np.array_equal(o[0], outs[0][0]) and o[1] == outs[0][1]
+        assert o[3] == outs[0][3]  # a replayed graph counts the kernels it runs
