@@ -53,7 +53,16 @@ typedef enum {
     LAP_GS_RB = 1,   /* Eq. 6, red (i+j even) then black points */
     LAP_SOR_RB = 2,  /* Eq. 7, red then black points */
     LAP_ADI = 3,     /* x-lines then y-lines per iteration (ADI subsection, Eqs. 8-10) */
-    LAP_MG = 4       /* V-cycle (Multigrid Method subsection, steps 1-11) */
+    LAP_MG = 4,      /* V-cycle (Multigrid Method subsection, steps 1-11) */
+    LAP_MG_MIXED = 5, /* the V-cycle's correction equation (Eqs. 13-15) solved by FP32
+                        V-cycles inside FP64 defect correction: per iteration,
+                        inner_cycles FP32 V(nu1,nu2) cycles on L e = -R, then psi += e
+                        and R = L(psi) in FP64 */
+    LAP_SLOR = 6,    /* line SOR by rows alone (SLOR subsection, Eqs. 8-10): one zebra
+                        x-line sweep per iteration, form line_form (A = SLORA, B = SLORB) */
+    LAP_GS_LEX = 7,  /* Eq. 6 in the paper's lexicographic order (i-1, j-1 already new), as
+                        diagonal wavefronts on one SM; m*n <= 28672 (else EUNSUPPORTED) */
+    LAP_SOR_LEX = 8  /* Eq. 7 in lexicographic order, same limits */
 } lap_method;
 
 typedef enum {
@@ -78,7 +87,7 @@ typedef struct {
 
 typedef struct {
     int32_t method;       /* lap_method */
-    double w;             /* relaxation factor: SOR (Eq. 7), ADI (Eqs. 9/10); in (0, 2) */
+    double w;             /* relaxation factor: SOR (Eq. 7), ADI/SLOR (Eqs. 9/10); in (0, 2) */
     double tol;           /* stopping tolerance (>= 0; 0 = run max_iter iterations) */
     int32_t norm;         /* lap_norm */
     int64_t max_iter;     /* iteration cap (V-cycles for LAP_MG), >= 0 */
@@ -88,7 +97,8 @@ typedef struct {
     int32_t coarsest_min; /* LAP_MG: coarsen while both coarse sides stay >= this (>= 3) */
     int32_t max_levels;   /* LAP_MG: 0 = as many as the sizes allow */
     double smoother_w;    /* LAP_MG: smoother relaxation; 1 = Gauss-Seidel (Eq. 6) */
-    int32_t line_form;    /* LAP_ADI: lap_line_form */
+    int32_t line_form;    /* LAP_ADI, LAP_SLOR: lap_line_form */
+    int32_t inner_cycles; /* LAP_MG_MIXED: FP32 V-cycles per FP64 correction (>= 1) */
 } lap_params;
 
 typedef struct {
@@ -102,7 +112,7 @@ typedef struct {
 typedef struct lap_handle_s* lap_handle;
 
 /* Defaults: SOR w = 1.0, tol 1e-10, L2_REL, max_iter 100000, check_every 1, MG V(2,2)
- * down to coarsest side 5 with a Gauss-Seidel smoother, ADI form A. */
+ * down to coarsest side 5 with a Gauss-Seidel smoother, ADI form A, 1 inner cycle. */
 void lap_default_params(lap_params* p);
 
 /* Create a handle on CUDA device `device` whose scratch memory may grow up to

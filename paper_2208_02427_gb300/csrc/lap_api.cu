@@ -215,14 +215,18 @@ void check_device_ptr(lap_handle h, const void* p, const char* what, bool allow_
 void check_params(const lap_params* p)
 {
     if (!p) fail(LAP_EINVAL, "params is NULL");
-    if (p->method < LAP_JACOBI || p->method > LAP_MG) fail(LAP_EINVAL, "unknown method");
+    if (p->method < LAP_JACOBI || p->method > LAP_SOR_LEX) fail(LAP_EINVAL, "unknown method");
     if (p->norm < LAP_NORM_L2_REL || p->norm > LAP_NORM_MAXDELTA) fail(LAP_EINVAL, "unknown norm");
     if (!(p->tol >= 0.0)) fail(LAP_EINVAL, "tol must be >= 0");
     if (p->max_iter < 0) fail(LAP_EINVAL, "max_iter must be >= 0");
     if (p->check_every < 1) fail(LAP_EINVAL, "check_every must be >= 1");
-    if ((p->method == LAP_SOR_RB || p->method == LAP_ADI) && !(p->w > 0.0 && p->w < 2.0))
+    if ((p->method == LAP_SOR_RB || p->method == LAP_ADI || p->method == LAP_SLOR ||
+         p->method == LAP_SOR_LEX) &&
+        !(p->w > 0.0 && p->w < 2.0))
         fail(LAP_EINVAL, "w must lie in (0, 2)");
-    if (p->method == LAP_MG) {
+    if (p->method == LAP_MG_MIXED && (p->inner_cycles < 1 || p->inner_cycles > 64))
+        fail(LAP_EINVAL, "inner_cycles must lie in 1..64");
+    if (p->method == LAP_MG || p->method == LAP_MG_MIXED) {
         if (p->nu1 < 0 || p->nu2 < 0 || p->nu1 + p->nu2 > 64)
             fail(LAP_EINVAL, "nu1, nu2 must be >= 0 and nu1 + nu2 <= 64");
         if (p->coarsest_min < 3) fail(LAP_EINVAL, "coarsest_min must be >= 3");
@@ -230,7 +234,8 @@ void check_params(const lap_params* p)
         if (!(p->smoother_w > 0.0 && p->smoother_w < 2.0))
             fail(LAP_EINVAL, "smoother_w must lie in (0, 2)");
     }
-    if (p->method == LAP_ADI && p->line_form != LAP_FORM_A && p->line_form != LAP_FORM_B)
+    if ((p->method == LAP_ADI || p->method == LAP_SLOR) && p->line_form != LAP_FORM_A &&
+        p->line_form != LAP_FORM_B)
         fail(LAP_EINVAL, "unknown line form");
 }
 
@@ -442,12 +447,19 @@ int mg_level_count(int m, int n, int coarsest_min, int max_levels)
 
 // ---- the per-call workspace ----------------------------------------------------------------
 
+struct Level32 {
+    Field32 u;           // inner correction (level 0: e of the fine grid)
+    float* q = nullptr;  // source (level 0: the FP64 residual rounded to FP32)
+    float* r = nullptr;  // residual scratch (all but the coarsest)
+};
+
 struct Work {
     double* partials = nullptr;  // norm partial sums
     double* nrm = nullptr;       // [sum, sqrt]
     unsigned long long* maxd = nullptr;
     double* aux = nullptr;       // Jacobi second buffer, or previous iterate for max|delta|
     std::vector<Level> levels;
+    std::vector<Level32> levels32;
 };
 
 template <class C>
@@ -459,7 +471,9 @@ void carve(C& cv, Work& w, const lap_grid* g, const lap_params* p)
     const size_t field = (size_t)g->n * (size_t)g->pitch;
     const bool need_aux =
         p->method == LAP_JACOBI ||
-        (p->norm == LAP_NORM_MAXDELTA && (p->method == LAP_ADI || p->method == LAP_MG));
+        (p->norm == LAP_NORM_MAXDELTA &&
+         (p->method == LAP_ADI || p->method == LAP_SLOR || p->method == LAP_MG ||
+          p->method == LAP_MG_MIXED));
     w.aux = need_aux ? cv.template take<double>(field) : nullptr;
     w.levels.clear();
     if (p->method == LAP_MG) {
@@ -475,6 +489,21 @@ void carve(C& cv, Work& w, const lap_grid* g, const lap_params* p)
             }
             if (l < L - 1) lv.r = cv.template take<double>((size_t)n * pitch);
             w.levels.push_back(lv);
+            m = (m - 1) / 2 + 1;
+            n = (n - 1) / 2 + 1;
+        }
+    }
+    w.levels32.clear();
+    if (p->method == LAP_MG_MIXED) {
+        const int L = mg_level_count(g->m, g->n, p->coarsest_min, p->max_levels);
+        int m = g->m, n = g->n;
+        for (int l = 0; l < L; ++l) {
+            Level32 lv;
+            const int64_t pitch = round_up(m, 32);
+            lv.u = Field32{cv.template take<float>((size_t)n * pitch), m, n, pitch};
+            lv.q = cv.template take<float>((size_t)n * pitch);
+            if (l < L - 1) lv.r = cv.template take<float>((size_t)n * pitch);
+            w.levels32.push_back(lv);
             m = (m - 1) / 2 + 1;
             n = (n - 1) / 2 + 1;
         }
@@ -503,6 +532,16 @@ struct Solver {
     {
         ck(launch_defect_sumsq(u, q, c, w.partials, s), "residual kernel");
         ck(launch_sum_partials(w.partials, norm_blocks(u), w.nrm, s), "sum kernel");
+        ck(cudaMemcpyAsync(h->pinned, w.nrm + 1, sizeof(double), cudaMemcpyDeviceToHost, s),
+           "copy norm");
+        ck(cudaStreamSynchronize(s), "stream sync");
+        return h->pinned[0];
+    }
+
+    // Norm from partial sums already written by the last FP64 residual pass.
+    double partial_norm(const Field& u)
+    {
+        ck(launch_sum_partials(w.partials, mixed_norm_blocks(u.n), w.nrm, s), "sum kernel");
         ck(cudaMemcpyAsync(h->pinned, w.nrm + 1, sizeof(double), cudaMemcpyDeviceToHost, s),
            "copy norm");
         ck(cudaStreamSynchronize(s), "stream sync");
@@ -552,10 +591,46 @@ struct Solver {
             line_half_sweep(h, f, c, p->w, p->line_form, 0, s);
             line_half_sweep(h, f, c, p->w, p->line_form, 1, s);
             break;
+        case LAP_SLOR:
+            line_half_sweep(h, f, c, p->w, p->line_form, 0, s);
+            break;
         case LAP_MG:
             vcycle(0);
             break;
+        case LAP_MG_MIXED: {
+            const Level32& l0 = w.levels32[0];
+            for (int k = 0; k < p->inner_cycles; ++k) vcycle32(0);
+            ck(launch_update64(f, l0.u.p, l0.u.pitch, s), "update kernel");
+            ck(launch_defect64_to32(f, c, l0.q, l0.u.p, l0.u.pitch, w.partials, s),
+               "mixed residual kernel");
+            break;
         }
+        }
+    }
+
+    // The FP32 image of vcycle() on the correction equation.
+    void vcycle32(int l)
+    {
+        Level32& lv = w.levels32[l];
+        const int L = (int)w.levels32.size();
+        if (l == L - 1) {
+            const double* ainv = coarse_inverse(h, lv.u.m, lv.u.n, c.b2, c.d);
+            ck(launch_coarse32(lv.u, lv.q, ainv, s), "coarse solve kernel");
+            return;
+        }
+        const bool gs = p->smoother_w == 1.0;
+        for (int k = 0; k < p->nu1; ++k)
+            for (int colour = 0; colour < 2; ++colour)
+                ck(launch_rb32(lv.u, lv.q, c, gs, p->smoother_w, colour, s), "smoother kernel");
+        Level32& cv = w.levels32[l + 1];
+        ck(launch_defect32(lv.u, lv.q, lv.r, c, s), "defect kernel");
+        ck(launch_restrict32(Field32{lv.r, lv.u.m, lv.u.n, lv.u.pitch}, cv.q, cv.u.p, cv.u.pitch, s),
+           "restrict kernel");
+        vcycle32(l + 1);
+        ck(launch_prolong32(lv.u, cv.u.p, cv.u.pitch, s), "prolong kernel");
+        for (int k = 0; k < p->nu2; ++k)
+            for (int colour = 0; colour < 2; ++colour)
+                ck(launch_rb32(lv.u, lv.q, c, gs, p->smoother_w, colour, s), "smoother kernel");
     }
 
     void smooth(const Level& lv, int sweeps)
@@ -589,6 +664,20 @@ struct Solver {
     // The iterations between two stopping tests, enqueued on stream s.
     void period(int64_t steps, bool maxdelta, bool fused_maxd)
     {
+        if (p->method == LAP_GS_LEX || p->method == LAP_SOR_LEX) {
+            // the whole period in one launch (the field stays in shared memory)
+            if (maxdelta) ck(cudaMemsetAsync(w.maxd, 0, 8, s), "zero max delta");
+            const bool gs = p->method == LAP_GS_LEX;
+            for (int64_t done = 0; done < steps;) {
+                const int chunk = (int)std::min<int64_t>(steps - done, 1 << 20);
+                const bool last = done + chunk == steps;
+                ck(launch_lex_sweeps(f, c, gs, gs ? 1.0 : p->w, chunk,
+                                     last && maxdelta ? w.maxd : nullptr, s),
+                   "lexicographic kernel");
+                done += chunk;
+            }
+            return;
+        }
         for (int64_t st = 0; st < steps; ++st) {
             const bool last = st == steps - 1;
             if (last && maxdelta) {
@@ -602,8 +691,8 @@ struct Solver {
     // Host-side tables a period needs, built before capture (they upload synchronously).
     void prepare()
     {
-        if (p->method == LAP_ADI) {
-            for (int dir = 0; dir < 2; ++dir) {
+        if (p->method == LAP_ADI || p->method == LAP_SLOR) {
+            for (int dir = 0; dir < (p->method == LAP_ADI ? 2 : 1); ++dir) {
                 const bool x = dir == 0;
                 const double off = x ? 1.0 : c.b2;
                 const int N = x ? f.m - 2 : f.n - 2;
@@ -616,6 +705,12 @@ struct Solver {
             const Level& lv = w.levels.back();
             coarse_inverse(h, lv.u.m, lv.u.n, c.b2, c.d);
         }
+        if (p->method == LAP_MG_MIXED) {
+            const Level32& lv = w.levels32.back();
+            coarse_inverse(h, lv.u.m, lv.u.n, c.b2, c.d);
+        }
+        if (p->method == LAP_GS_LEX || p->method == LAP_SOR_LEX)
+            ck(prepare_lex_kernels(lex_smem_bytes(f.m, f.n)), "lexicographic kernel attributes");
     }
 
     std::string graph_key(int64_t steps, bool maxdelta, bool fused_maxd) const
@@ -624,7 +719,8 @@ struct Solver {
         auto put = [&](const void* v, size_t n) { k.append((const char*)v, n); };
         const int64_t ints[] = {p->method, f.m, f.n, f.pitch, steps, maxdelta, fused_maxd,
                                 p->nu1, p->nu2, p->coarsest_min, p->max_levels, p->line_form,
-                                (int64_t)w.levels.size()};
+                                (int64_t)w.levels.size(), p->inner_cycles,
+                                (int64_t)w.levels32.size()};
         const double dbl[] = {c.b2, c.d, c.inv_d, p->w, p->smoother_w};
         const void* ptrs[] = {f.p, jac_cur, jac_other, w.aux, w.maxd, h->arena};
         put(ints, sizeof ints);
@@ -698,7 +794,16 @@ struct Solver {
                 ck(cudaMemsetAsync(w.levels[l].q, 0, (size_t)u.n * u.pitch * 8, s), "zero source");
             }
         }
-        const double r0 = residual(f, nullptr);
+        if (p->method == LAP_MG_MIXED) {
+            for (const Level32& lv : w.levels32) {
+                ck(cudaMemsetAsync(lv.u.p, 0, (size_t)lv.u.n * lv.u.pitch * 4, s), "zero level");
+                ck(cudaMemsetAsync(lv.q, 0, (size_t)lv.u.n * lv.u.pitch * 4, s), "zero source");
+            }
+            const Level32& l0 = w.levels32[0];
+            ck(launch_defect64_to32(f, c, l0.q, l0.u.p, l0.u.pitch, w.partials, s),
+               "mixed residual kernel");
+        }
+        const double r0 = p->method == LAP_MG_MIXED ? partial_norm(f) : residual(f, nullptr);
         out->r0 = r0;
         if (!std::isfinite(r0)) {
             out->status = LAP_DIVERGED;
@@ -710,7 +815,9 @@ struct Solver {
         while (out->status == LAP_MAXITER && k < p->max_iter) {
             const int64_t steps = std::min<int64_t>(p->check_every - (k % p->check_every), p->max_iter - k);
             const bool maxdelta = p->norm == LAP_NORM_MAXDELTA;
-            const bool fused_maxd = maxdelta && p->method != LAP_ADI && p->method != LAP_MG;
+            const bool fused_maxd = maxdelta && (p->method == LAP_JACOBI || p->method == LAP_GS_RB ||
+                                                 p->method == LAP_SOR_RB || p->method == LAP_GS_LEX ||
+                                                 p->method == LAP_SOR_LEX);
             run_period(steps, maxdelta, fused_maxd);
             k += steps;
             double val;
@@ -722,7 +829,8 @@ struct Solver {
                 conv = val <= p->tol;
             } else {
                 const Field cur{p->method == LAP_JACOBI ? jac_cur : f.p, f.m, f.n, f.pitch};
-                const double nr = residual(cur, nullptr);
+                // the mixed iteration ends with the FP64 residual's partial sums
+                const double nr = p->method == LAP_MG_MIXED ? partial_norm(f) : residual(cur, nullptr);
                 val = p->norm == LAP_NORM_L2_REL ? nr / r0 : nr;
                 conv = p->norm == LAP_NORM_L2_REL ? nr <= p->tol * r0 : nr <= p->tol;
             }
@@ -760,6 +868,7 @@ void lap_default_params(lap_params* p)
     p->max_levels = 0;
     p->smoother_w = 1.0;
     p->line_form = LAP_FORM_A;
+    p->inner_cycles = 1;
 }
 
 int lap_create(lap_handle* out, size_t hbm_budget_bytes, int device)
@@ -818,7 +927,7 @@ int lap_solve(lap_handle h, const lap_grid* g, double* psi_dev, const lap_params
         set_device(h);
         check_device_ptr(h, psi_dev, "psi");
         Solver sv{h, (cudaStream_t)stream, Field{psi_dev, g->m, g->n, g->pitch}, make_coef(g->dx, g->dy), p, {}};
-        if (p->method == LAP_MG) {
+        if (p->method == LAP_MG || p->method == LAP_MG_MIXED) {
             const int L = mg_level_count(g->m, g->n, p->coarsest_min, p->max_levels);
             int m = g->m, n = g->n;
             for (int l = 1; l < L; ++l) {
@@ -829,7 +938,12 @@ int lap_solve(lap_handle h, const lap_grid* g, double* psi_dev, const lap_params
                 fail(LAP_EUNSUPPORTED, "coarsest multigrid level has more than 1024 unknowns; "
                                        "use sizes with (m-1), (n-1) divisible by more powers of two");
         }
-        if (p->method == LAP_ADI && (g->m - 2 > LINE_MAX_N || g->n - 2 > LINE_MAX_N))
+        if ((p->method == LAP_GS_LEX || p->method == LAP_SOR_LEX) &&
+            (int64_t)g->m * g->n > lex_max_points())
+            fail(LAP_EUNSUPPORTED, "lexicographic methods hold the grid in one SM's shared memory: "
+                                   "at most 28672 points");
+        if ((p->method == LAP_ADI || p->method == LAP_SLOR) &&
+            (g->m - 2 > LINE_MAX_N || g->n - 2 > LINE_MAX_N))
             fail(LAP_EUNSUPPORTED, "ADI lines longer than 16383 unknowns");
         const size_t need = work_bytes(g, p);
         Carver cv(arena(h, need));

@@ -6,36 +6,54 @@
 
 namespace lap {
 
+// On GB300's FP64 pipe a fused multiply-add issues at ~0.60 T/s but an add or a multiply at
+// ~0.50 T/s (measured). x + y == fma(x, 1, y) and x * y == fma(x, y, -0) bit for bit, for every
+// input, so adds and multiplies are issued as fmas. The 1 and -0 arrive as kernel arguments:
+// as literals the compiler would turn the fma back into the add or multiply.
+struct FmaOps {
+    double one;    // 1.0
+    double nzero;  // -0.0
+};
+__device__ __forceinline__ double fadd(const FmaOps& o, double a, double b)
+{
+    return __fma_rn(a, o.one, b);
+}
+__device__ __forceinline__ double fmul(const FmaOps& o, double a, double b)
+{
+    return __fma_rn(a, b, o.nzero);
+}
+
 // x * 2^-k for k > 0, bit-identical to __dmul_rn(x, 2^-k). On GB300 the FP64 pipe
 // issues about 2 operations per clock per SM, the integer pipe 64 times more; when x is
 // normal and the result stays normal the product is just the exponent field lowered by
 // k, which the integer pipe does. Zero, subnormal, tiny, infinite and NaN inputs take
 // the FP64 multiply.
-__device__ __forceinline__ double scale_down_pow2(double x, int k, double two_pow_minus_k)
+__device__ __forceinline__ double scale_down_pow2(const FmaOps& o, double x, int k,
+                                                  double two_pow_minus_k)
 {
     int hi = __double2hiint(x);
     int lo = __double2loint(x);
     int e = (hi >> 20) & 0x7ff;
     if (e > k && e < 0x7ff) return __hiloint2double(hi - (k << 20), lo);
-    return __dmul_rn(x, two_pow_minus_k);
+    return fmul(o, x, two_pow_minus_k);
 }
 
 // Multiply by 1/d: the integer-pipe path when 1/d is an exact power of two.
 template <bool POW2>
-__device__ __forceinline__ double times_inv_d(double s, double inv_d, int shift)
+__device__ __forceinline__ double times_inv_d(const FmaOps& o, double s, double inv_d, int shift)
 {
-    if (POW2) return scale_down_pow2(s, shift, inv_d);
-    return __dmul_rn(s, inv_d);
+    if (POW2) return scale_down_pow2(o, s, shift, inv_d);
+    return fmul(o, s, inv_d);
 }
 
 // Neighbour sum of Eq. 5: fma(beta^2, N + S, E + W); with beta == 1 the fma is the add.
 template <bool UNIT_BETA>
-__device__ __forceinline__ double neighbour_sum(double w_, double e_, double s_, double n_,
-                                                double b2)
+__device__ __forceinline__ double neighbour_sum(const FmaOps& o, double w_, double e_, double s_,
+                                                double n_, double b2)
 {
-    double ew = __dadd_rn(w_, e_);
-    double ns = __dadd_rn(s_, n_);
-    return UNIT_BETA ? __dadd_rn(ns, ew) : __fma_rn(b2, ns, ew);
+    double ew = fadd(o, w_, e_);
+    double ns = fadd(o, s_, n_);
+    return UNIT_BETA ? fadd(o, ns, ew) : __fma_rn(b2, ns, ew);
 }
 
 // Deterministic warp reductions (fixed xor tree).

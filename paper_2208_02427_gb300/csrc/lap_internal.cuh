@@ -24,6 +24,13 @@ struct Field {
     int64_t pitch;
 };
 
+// A pitched field of floats (the inner FP32 multigrid cycle).
+struct Field32 {
+    float* p;
+    int m, n;
+    int64_t pitch;
+};
+
 // Every kernel launch of the library goes through this counter.
 void note_launch();
 
@@ -59,6 +66,33 @@ cudaError_t launch_prolong_add(const Field& fine_u, const double* ec, int64_t pi
 // u interior := Ainv_t^T b with b the coarse right-hand side assembled from q and u's ring.
 cudaError_t launch_coarse_solve(const Field& u, const double* q, const Coef& c,
                                 const double* ainv_t, cudaStream_t s);
+
+// ---- FP32 cycle inside FP64 defect correction (mixed_kernels.cu) -----------------
+int mixed_norm_blocks(int n);
+cudaError_t launch_rb32(const Field32& f, const float* q, const Coef& c, bool gs, double w,
+                        int colour, cudaStream_t s);
+cudaError_t launch_defect32(const Field32& f, const float* q, float* r, const Coef& c,
+                            cudaStream_t s);
+cudaError_t launch_restrict32(const Field32& fine_r, float* qc, float* ec, int64_t pitch_c,
+                              cudaStream_t s);
+cudaError_t launch_prolong32(const Field32& fine_u, const float* ec, int64_t pitch_c,
+                             cudaStream_t s);
+cudaError_t launch_coarse32(const Field32& u, const float* q, const double* ainv_t, cudaStream_t s);
+// r32 := (float) FP64 residual of psi, e32 := 0 (interiors), partials := per-block sums of r^2
+// (the same blocks and order as launch_defect_sumsq, so the sums are identical).
+cudaError_t launch_defect64_to32(const Field& psi, const Coef& c, float* r32, float* e32,
+                                 int64_t pitch32, double* partials, cudaStream_t s);
+// psi += (double) e32 on interior nodes.
+cudaError_t launch_update64(const Field& psi, const float* e32, int64_t pitch32, cudaStream_t s);
+
+// ---- lexicographic Gauss-Seidel / SOR on one SM (lex_kernels.cu) ---------------------
+// nsweeps sweeps of Eq. 6 (gs) or Eq. 7 in the paper's order as diagonal wavefronts, the
+// field resident in shared memory; maxd (nullable) gets max|new - old| of the last sweep.
+int64_t lex_max_points();
+size_t lex_smem_bytes(int m, int n);
+cudaError_t prepare_lex_kernels(size_t smem);
+cudaError_t launch_lex_sweeps(const Field& f, const Coef& c, bool gs, double w, int nsweeps,
+                              unsigned long long* maxd, cudaStream_t s);
 
 // ---- line relaxation (line_kernels.cu) --------------------------------------------
 // Constant-coefficient tridiagonal systems -alpha x_{k-1} + delta x_k - alpha x_{k+1} = r_k,

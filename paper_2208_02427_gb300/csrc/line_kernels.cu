@@ -26,7 +26,8 @@ namespace {
 template <int FORM, bool UNIT_CROSS>
 __global__ void __launch_bounds__(256)
     line_colour_kernel(double* __restrict__ psi, int64_t sa, int64_t sx, int first_line,
-                       const LineTables t, double cross, double w, double dmw, double wcross)
+                       const LineTables t, double cross, double w, double dmw, double wcross,
+                       const FmaOps o)
 {
     extern __shared__ double sm[];
     const int N = t.N, L = t.L, P = t.P, S = P - 1, Ls = t.stride;
@@ -37,13 +38,13 @@ __global__ void __launch_bounds__(256)
 
     // 1. right-hand side
     for (int k = 1 + threadIdx.x; k <= N; k += blockDim.x) {
-        const int64_t o = (int64_t)k * sa;
-        const double nb = __dadd_rn(base[o - sx], base[o + sx]);
+        const int64_t at = (int64_t)k * sa;
+        const double nb = fadd(o, base[at - sx], base[at + sx]);
         double r;
         if (FORM == 0)
-            r = UNIT_CROSS ? nb : __dmul_rn(cross, nb);
+            r = UNIT_CROSS ? nb : fmul(o, cross, nb);
         else
-            r = __fma_rn(dmw, base[o], __dmul_rn(wcross, nb));
+            r = __fma_rn(dmw, base[at], fmul(o, wcross, nb));
         if (k == 1) r = __fma_rn(alpha, base[0], r);
         if (k == N) r = __fma_rn(alpha, base[(int64_t)(N + 1) * sa], r);
         const int g = k - 1, p = g / (L + 1);
@@ -57,13 +58,13 @@ __global__ void __launch_bounds__(256)
         const int len = p == P - 1 ? t.Ll : L;
         double* y = lane + p * Ls;
         double prev = 0.0;
-        for (int o = 0; o < len; ++o) {
-            prev = __dmul_rn(__fma_rn(alpha, prev, y[o]), t.inv_den[o]);
-            y[o] = prev;
+        for (int q = 0; q < len; ++q) {
+            prev = fmul(o, __fma_rn(alpha, prev, y[q]), t.inv_den[q]);
+            y[q] = prev;
         }
-        for (int o = len - 2; o >= 0; --o) {
-            prev = __fma_rn(t.cpos[o], prev, y[o]);
-            y[o] = prev;
+        for (int q = len - 2; q >= 0; --q) {
+            prev = __fma_rn(t.cpos[q], prev, y[q]);
+            y[q] = prev;
         }
     }
     __syncthreads();
@@ -71,7 +72,7 @@ __global__ void __launch_bounds__(256)
     // 3. separators: rho_p = r_sep + alpha (y_last(chunk p) + y_first(chunk p+1))
     if (p < S) {
         const double* yl = lane + p * Ls;
-        rho[p] = __fma_rn(alpha, __dadd_rn(yl[L - 1], yl[Ls]), yl[L]);
+        rho[p] = __fma_rn(alpha, fadd(o, yl[L - 1], yl[Ls]), yl[L]);
     }
     __syncthreads();
     double* cur = rho;
@@ -88,7 +89,7 @@ __global__ void __launch_bounds__(256)
         cur = nxt;
         nxt = tmp;
     }
-    if (p < S) cur[p] = __dmul_rn(cur[p], t.invb[p]);
+    if (p < S) cur[p] = fmul(o, cur[p], t.invb[p]);
     __syncthreads();
 
     // 4. superpose the separator values onto each chunk
@@ -100,11 +101,11 @@ __global__ void __launch_bounds__(256)
         double* y = lane + p * Ls;
         if (p >= 1) {
             const double xl = cur[p - 1];
-            for (int o = 0; o < len; ++o) y[o] = __fma_rn(xl, gl[o], y[o]);
+            for (int q = 0; q < len; ++q) y[q] = __fma_rn(xl, gl[q], y[q]);
         }
         if (p < S) {
             const double xr = cur[p];
-            for (int o = 0; o < len; ++o) y[o] = __fma_rn(xr, gr[o], y[o]);
+            for (int q = 0; q < len; ++q) y[q] = __fma_rn(xr, gr[q], y[q]);
             y[L] = xr;
         }
     }
@@ -112,12 +113,12 @@ __global__ void __launch_bounds__(256)
 
     // 5. relax and write back
     for (int k = 1 + threadIdx.x; k <= N; k += blockDim.x) {
-        const int g = k - 1, q = g / (L + 1);
-        const double x = lane[q * Ls + (g - q * (L + 1))];
+        const int g = k - 1, c = g / (L + 1);
+        const double x = lane[c * Ls + (g - c * (L + 1))];
         double* dst = base + (int64_t)k * sa;
         if (FORM == 0) {
             const double old = *dst;
-            *dst = __fma_rn(w, __dsub_rn(x, old), old);
+            *dst = __fma_rn(w, fadd(o, x, -old), old);
         } else {
             *dst = x;
         }
@@ -172,7 +173,8 @@ cudaError_t launch_line_colour(double* psi, int64_t sa, int64_t sx, int first_li
         auto kern = line_colour_kernel<F, U>;                                                   \
         err = prepare_line_kernels(smem);                                                       \
         if (err == cudaSuccess)                                                                 \
-            kern<<<count, threads, smem, s>>>(psi, sa, sx, first_line, t, cross, w, dmw, wcross); \
+            kern<<<count, threads, smem, s>>>(psi, sa, sx, first_line, t, cross, w, dmw, wcross, \
+                                              FmaOps{1.0, -0.0});                                \
     } while (0)
     if (form == 0) {
         if (unit) LAP_LINE(0, true); else LAP_LINE(0, false);

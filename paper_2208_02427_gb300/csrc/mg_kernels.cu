@@ -19,20 +19,20 @@ constexpr int MG_BX = 64, MG_BY = 4;
 // reproduce the two rounded additions of the written expression.
 __global__ void __launch_bounds__(MG_BX* MG_BY)
     restrict_kernel(const double* __restrict__ r, int mf, int nf, int64_t pf,
-                    double* __restrict__ qc, double* __restrict__ ec, int64_t pc)
+                    double* __restrict__ qc, double* __restrict__ ec, int64_t pc, const FmaOps o)
 {
     const int mc = (mf - 1) / 2 + 1, nc = (nf - 1) / 2 + 1;
     const int I = 1 + blockIdx.x * MG_BX + threadIdx.x;
     const int J = 1 + blockIdx.y * MG_BY + threadIdx.y;
     if (I > mc - 2 || J > nc - 2) return;
     const double* c = r + (int64_t)(2 * J) * pf + 2 * I;
-    const double edges = __dadd_rn(__dadd_rn(c[-1], c[1]), __dadd_rn(c[-pf], c[pf]));
+    const double edges = fadd(o, fadd(o, c[-1], c[1]), fadd(o, c[-pf], c[pf]));
     const double corners =
-        __dadd_rn(__dadd_rn(c[-pf - 1], c[-pf + 1]), __dadd_rn(c[pf - 1], c[pf + 1]));
+        fadd(o, fadd(o, c[-pf - 1], c[-pf + 1]), fadd(o, c[pf - 1], c[pf + 1]));
     const double t = __fma_rn(2.0, c[0], edges);
     const double u = __fma_rn(2.0, t, corners);
     const int64_t at = (int64_t)J * pc + I;
-    qc[at] = scale_down_pow2(u, 2, 0.25);
+    qc[at] = scale_down_pow2(o, u, 2, 0.25);
     if (ec) ec[at] = 0.0;
 }
 
@@ -41,7 +41,7 @@ __global__ void __launch_bounds__(MG_BX* MG_BY)
 // (pairs along x first).
 __global__ void __launch_bounds__(MG_BX* MG_BY)
     prolong_add_kernel(double* __restrict__ u, int mf, int nf, int64_t pf,
-                       const double* __restrict__ ec, int64_t pc)
+                       const double* __restrict__ ec, int64_t pc, const FmaOps o)
 {
     const int I = blockIdx.x * MG_BX + threadIdx.x;  // coarse column 0 .. mc-2
     const int j = 1 + blockIdx.y * MG_BY + threadIdx.y;
@@ -52,14 +52,14 @@ __global__ void __launch_bounds__(MG_BX* MG_BY)
     const int i0 = 2 * I, i1 = 2 * I + 1;
     double* row = u + (int64_t)j * pf;
     if ((j & 1) == 0) {
-        if (i0 >= 1) row[i0] = __dadd_rn(row[i0], a[0]);
-        if (i1 <= mf - 2) row[i1] = __dadd_rn(row[i1], scale_down_pow2(__dadd_rn(a[0], a[1]), 1, 0.5));
+        if (i0 >= 1) row[i0] = fadd(o, row[i0], a[0]);
+        if (i1 <= mf - 2) row[i1] = fadd(o, row[i1], scale_down_pow2(o, fadd(o, a[0], a[1]), 1, 0.5));
     } else {
         if (i0 >= 1)
-            row[i0] = __dadd_rn(row[i0], scale_down_pow2(__dadd_rn(a[0], a[pc]), 1, 0.5));
+            row[i0] = fadd(o, row[i0], scale_down_pow2(o, fadd(o, a[0], a[pc]), 1, 0.5));
         if (i1 <= mf - 2) {
-            const double s = __dadd_rn(__dadd_rn(a[0], a[1]), __dadd_rn(a[pc], a[pc + 1]));
-            row[i1] = __dadd_rn(row[i1], scale_down_pow2(s, 2, 0.25));
+            const double s = fadd(o, fadd(o, a[0], a[1]), fadd(o, a[pc], a[pc + 1]));
+            row[i1] = fadd(o, row[i1], scale_down_pow2(o, s, 2, 0.25));
         }
     }
 }
@@ -99,7 +99,7 @@ cudaError_t launch_restrict(const Field& fine_r, double* qc, double* ec, int64_t
     const int mc = (fine_r.m - 1) / 2 + 1, nc = (fine_r.n - 1) / 2 + 1;
     const dim3 grid((mc - 2 + MG_BX - 1) / MG_BX, (nc - 2 + MG_BY - 1) / MG_BY);
     restrict_kernel<<<grid, dim3(MG_BX, MG_BY), 0, s>>>(fine_r.p, fine_r.m, fine_r.n, fine_r.pitch,
-                                                         qc, ec, pitch_c);
+                                                         qc, ec, pitch_c, FmaOps{1.0, -0.0});
     note_launch();
     return cudaGetLastError();
 }
@@ -110,7 +110,8 @@ cudaError_t launch_prolong_add(const Field& fine_u, const double* ec, int64_t pi
     const int mc = (fine_u.m - 1) / 2 + 1;
     const dim3 grid((mc - 1 + MG_BX - 1) / MG_BX, (fine_u.n - 2 + MG_BY - 1) / MG_BY);
     prolong_add_kernel<<<grid, dim3(MG_BX, MG_BY), 0, s>>>(fine_u.p, fine_u.m, fine_u.n,
-                                                            fine_u.pitch, ec, pitch_c);
+                                                            fine_u.pitch, ec, pitch_c,
+                                                            FmaOps{1.0, -0.0});
     note_launch();
     return cudaGetLastError();
 }

@@ -2,9 +2,9 @@
 //
 // Jacobi (Eq. 5), red-black Gauss-Seidel (Eq. 6) and SOR (Eq. 7), and the scaled
 // residual r = dx^2 L(psi) (+ q) of Eqs. 11-12. Every value is computed with the same
-// sequence of correctly rounded operations as the written expression (explicit
-// __dadd_rn/__dmul_rn/__fma_rn; the file is built with --fmad=false), so results do not
-// depend on the launch shape.
+// sequence of correctly rounded operations as the written expression (adds and
+// multiplies issued as exact fmas, see FmaOps; the file is built with --fmad=false), so
+// results do not depend on the launch shape.
 //
 // On GB300 the FP64 pipe (about 2 operations per clock per SM) and not HBM bounds these
 // sweeps; the kernels spend the minimum number of FP64 operations per point: 3 adds for
@@ -21,6 +21,7 @@ constexpr int RB_BX = 64, RB_BY = 4;   // red-black: 64 same-colour points x 4 r
 constexpr int JA_BX = 128, JA_BY = 2;  // Jacobi: 128 points x 2 rows
 constexpr int NORM_THREADS = 256;
 constexpr int NORM_MAX_BLOCKS = 1216;  // 8 per SM on 152 SMs
+const FmaOps kOps{1.0, -0.0};
 
 __device__ __forceinline__ void flush_maxd(unsigned long long v, unsigned long long* maxd)
 {
@@ -34,7 +35,7 @@ template <bool UNIT_BETA, bool POW2, bool HAS_Q, bool GS, bool MAXD>
 __global__ void __launch_bounds__(RB_BX* RB_BY)
     rb_colour_kernel(double* __restrict__ psi, const double* __restrict__ q, int m, int n,
                      int64_t pitch, int colour, double b2, double inv_d, int shift, double w,
-                     double one_minus_w, unsigned long long* __restrict__ maxd)
+                     double one_minus_w, unsigned long long* __restrict__ maxd, const FmaOps o)
 {
     const int j = 1 + blockIdx.y * RB_BY + threadIdx.y;
     const int i = 1 + ((1 + j + colour) & 1) + 2 * (blockIdx.x * RB_BX + threadIdx.x);
@@ -42,13 +43,13 @@ __global__ void __launch_bounds__(RB_BX* RB_BY)
     if (j <= n - 2 && i <= m - 2) {
         const int64_t at = (int64_t)j * pitch + i;
         double* c = psi + at;
-        double s = neighbour_sum<UNIT_BETA>(c[-1], c[1], c[-pitch], c[pitch], b2);
-        if (HAS_Q) s = __dadd_rn(s, q[at]);
-        const double g = times_inv_d<POW2>(s, inv_d, shift);
+        double s = neighbour_sum<UNIT_BETA>(o, c[-1], c[1], c[-pitch], c[pitch], b2);
+        if (HAS_Q) s = fadd(o, s, q[at]);
+        const double g = times_inv_d<POW2>(o, s, inv_d, shift);
         const double old = *c;
-        const double nv = GS ? g : __fma_rn(w, g, __dmul_rn(one_minus_w, old));
+        const double nv = GS ? g : __fma_rn(w, g, fmul(o, one_minus_w, old));
         *c = nv;
-        if (MAXD) dl = abs_bits(__dsub_rn(nv, old));
+        if (MAXD) dl = abs_bits(fadd(o, nv, -old));
     }
     if (MAXD) flush_maxd(dl, maxd);
 }
@@ -57,7 +58,7 @@ template <bool UNIT_BETA, bool POW2, bool MAXD>
 __global__ void __launch_bounds__(JA_BX* JA_BY)
     jacobi_kernel(const double* __restrict__ in, double* __restrict__ out, int m, int n,
                   int64_t pitch, double b2, double inv_d, int shift,
-                  unsigned long long* __restrict__ maxd)
+                  unsigned long long* __restrict__ maxd, const FmaOps o)
 {
     const int j = 1 + blockIdx.y * JA_BY + threadIdx.y;
     const int i = 1 + blockIdx.x * JA_BX + threadIdx.x;
@@ -65,35 +66,36 @@ __global__ void __launch_bounds__(JA_BX* JA_BY)
     if (j <= n - 2 && i <= m - 2) {
         const int64_t at = (int64_t)j * pitch + i;
         const double* c = in + at;
-        const double s = neighbour_sum<UNIT_BETA>(c[-1], c[1], c[-pitch], c[pitch], b2);
-        const double nv = times_inv_d<POW2>(s, inv_d, shift);
+        const double s = neighbour_sum<UNIT_BETA>(o, c[-1], c[1], c[-pitch], c[pitch], b2);
+        const double nv = times_inv_d<POW2>(o, s, inv_d, shift);
         out[at] = nv;
-        if (MAXD) dl = abs_bits(__dsub_rn(nv, *c));
+        if (MAXD) dl = abs_bits(fadd(o, nv, -*c));
     }
     if (MAXD) flush_maxd(dl, maxd);
 }
 
 template <bool UNIT_BETA, bool HAS_Q>
-__device__ __forceinline__ double defect_at(const double* __restrict__ u,
+__device__ __forceinline__ double defect_at(const FmaOps& o, const double* __restrict__ u,
                                             const double* __restrict__ q, int64_t at,
                                             int64_t pitch, double b2, double d)
 {
     const double* c = u + at;
-    double s = neighbour_sum<UNIT_BETA>(c[-1], c[1], c[-pitch], c[pitch], b2);
-    if (HAS_Q) s = __dadd_rn(s, q[at]);
+    double s = neighbour_sum<UNIT_BETA>(o, c[-1], c[1], c[-pitch], c[pitch], b2);
+    if (HAS_Q) s = fadd(o, s, q[at]);
     return __fma_rn(-d, *c, s);
 }
 
 template <bool UNIT_BETA, bool HAS_Q>
 __global__ void __launch_bounds__(JA_BX* JA_BY)
     defect_kernel(const double* __restrict__ u, const double* __restrict__ q,
-                  double* __restrict__ r, int m, int n, int64_t pitch, double b2, double d)
+                  double* __restrict__ r, int m, int n, int64_t pitch, double b2, double d,
+                  const FmaOps o)
 {
     const int j = 1 + blockIdx.y * JA_BY + threadIdx.y;
     const int i = 1 + blockIdx.x * JA_BX + threadIdx.x;
     if (j <= n - 2 && i <= m - 2) {
         const int64_t at = (int64_t)j * pitch + i;
-        r[at] = defect_at<UNIT_BETA, HAS_Q>(u, q, at, pitch, b2, d);
+        r[at] = defect_at<UNIT_BETA, HAS_Q>(o, u, q, at, pitch, b2, d);
     }
 }
 
@@ -102,12 +104,14 @@ __global__ void __launch_bounds__(JA_BX* JA_BY)
 template <bool UNIT_BETA, bool HAS_Q>
 __global__ void __launch_bounds__(NORM_THREADS)
     defect_sumsq_kernel(const double* __restrict__ u, const double* __restrict__ q, int m, int n,
-                        int64_t pitch, double b2, double d, double* __restrict__ partials)
+                        int64_t pitch, double b2, double d, double* __restrict__ partials,
+                        const FmaOps o)
 {
     double acc = 0.0;
     for (int j = 1 + blockIdx.x; j <= n - 2; j += gridDim.x)
         for (int i = 1 + threadIdx.x; i <= m - 2; i += NORM_THREADS) {
-            const double r = defect_at<UNIT_BETA, HAS_Q>(u, q, (int64_t)j * pitch + i, pitch, b2, d);
+            const double r =
+                defect_at<UNIT_BETA, HAS_Q>(o, u, q, (int64_t)j * pitch + i, pitch, b2, d);
             acc = __fma_rn(r, r, acc);
         }
     __shared__ double red[NORM_THREADS / 32];
@@ -142,14 +146,14 @@ __global__ void __launch_bounds__(NORM_THREADS)
 
 __global__ void __launch_bounds__(JA_BX* JA_BY)
     maxdelta_kernel(const double* __restrict__ a, const double* __restrict__ b, int m, int n,
-                    int64_t pitch, unsigned long long* __restrict__ maxd)
+                    int64_t pitch, unsigned long long* __restrict__ maxd, const FmaOps o)
 {
     const int j = 1 + blockIdx.y * JA_BY + threadIdx.y;
     const int i = 1 + blockIdx.x * JA_BX + threadIdx.x;
     unsigned long long dl = 0;
     if (j <= n - 2 && i <= m - 2) {
         const int64_t at = (int64_t)j * pitch + i;
-        dl = abs_bits(__dsub_rn(a[at], b[at]));
+        dl = abs_bits(fadd(o, a[at], -b[at]));
     }
     flush_maxd(dl, maxd);
 }
@@ -186,7 +190,8 @@ cudaError_t launch_rb_colour(const Field& f, const double* q, const Coef& c, boo
     LAP_DISPATCH_BOOL(c.unit_beta, UB, LAP_DISPATCH_BOOL(c.inv_d_shift > 0, P2,
         LAP_DISPATCH_BOOL(q != nullptr, HQ, LAP_DISPATCH_BOOL(gs, GS, LAP_DISPATCH_BOOL(maxd != nullptr, MD,
             rb_colour_kernel<UB, P2, HQ, GS, MD><<<grid, block, 0, s>>>(
-                f.p, q, f.m, f.n, f.pitch, colour, c.b2, c.inv_d, c.inv_d_shift, w, omw, maxd))))));
+                f.p, q, f.m, f.n, f.pitch, colour, c.b2, c.inv_d, c.inv_d_shift, w, omw, maxd,
+                kOps))))));
     note_launch();
     return cudaGetLastError();
 }
@@ -198,7 +203,7 @@ cudaError_t launch_jacobi(const Field& in, double* out, const Coef& c, unsigned 
     LAP_DISPATCH_BOOL(c.unit_beta, UB, LAP_DISPATCH_BOOL(c.inv_d_shift > 0, P2,
         LAP_DISPATCH_BOOL(maxd != nullptr, MD,
             jacobi_kernel<UB, P2, MD><<<grid, block, 0, s>>>(in.p, out, in.m, in.n, in.pitch, c.b2,
-                                                             c.inv_d, c.inv_d_shift, maxd))));
+                                                             c.inv_d, c.inv_d_shift, maxd, kOps))));
     note_launch();
     return cudaGetLastError();
 }
@@ -208,7 +213,7 @@ cudaError_t launch_defect(const Field& f, const double* q, double* r, const Coef
 {
     const dim3 grid = point_grid(f.m, f.n), block(JA_BX, JA_BY);
     LAP_DISPATCH_BOOL(c.unit_beta, UB, LAP_DISPATCH_BOOL(q != nullptr, HQ,
-        defect_kernel<UB, HQ><<<grid, block, 0, s>>>(f.p, q, r, f.m, f.n, f.pitch, c.b2, c.d)));
+        defect_kernel<UB, HQ><<<grid, block, 0, s>>>(f.p, q, r, f.m, f.n, f.pitch, c.b2, c.d, kOps)));
     note_launch();
     return cudaGetLastError();
 }
@@ -225,7 +230,7 @@ cudaError_t launch_defect_sumsq(const Field& f, const double* q, const Coef& c, 
     const int blocks = norm_blocks(f);
     LAP_DISPATCH_BOOL(c.unit_beta, UB, LAP_DISPATCH_BOOL(q != nullptr, HQ,
         defect_sumsq_kernel<UB, HQ><<<blocks, NORM_THREADS, 0, s>>>(f.p, q, f.m, f.n, f.pitch, c.b2,
-                                                                    c.d, partials)));
+                                                                    c.d, partials, kOps)));
     note_launch();
     return cudaGetLastError();
 }
@@ -241,7 +246,7 @@ cudaError_t launch_maxdelta(const Field& a, const double* b, unsigned long long*
                             cudaStream_t s)
 {
     maxdelta_kernel<<<point_grid(a.m, a.n), dim3(JA_BX, JA_BY), 0, s>>>(a.p, b, a.m, a.n, a.pitch,
-                                                                         maxd);
+                                                                         maxd, kOps);
     note_launch();
     return cudaGetLastError();
 }

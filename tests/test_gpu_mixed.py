@@ -1,0 +1,113 @@
+"""Mixed precision (FP32 V-cycles inside FP64 defect correction) against the FP64 oracle.
+
+The inner cycles are an approximation, so the bar is on what the refinement guarantees:
+the FP64 residual reaches the same stopping rule as the FP64 solvers, the initial residual
+norm is the FP64 one (bitwise: same kernel arithmetic, same reduction order), and the
+refined solution agrees with the oracle's FP64 multigrid solution and with the exact
+discrete solution (dense / DST) to the accuracy that the 1e-10 residual implies."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as ora
+from paper_2208_02427_gb300 import workloads as wl
+from tests import exact
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def b():
+    from paper_2208_02427_gb300 import binding
+    binding.load()
+    return binding
+
+
+@pytest.fixture(scope="module")
+def lap(b):
+    h = b.Laplace()
+    yield h
+    h.close()
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy().copy()
+
+
+CASES = [("chamber", 25, 17, 0.25, 0.25), ("sine", 65, 65, 1 / 64, 1 / 64),
+         ("sine", 129, 33, 1 / 128, 1 / 32), ("ring", 257, 129, 1.0, 1.25),
+         ("sine", 513, 513, 1 / 512, 1 / 512)]
+
+
+def field_of(kind, m, n):
+    if kind == "chamber":
+        return wl.chamber()
+    if kind == "sine":
+        return wl.sine_edges(m, n, seed=wl.SEED_BASE + 3)
+    return wl.random_ring(m, n, seed=31)
+
+
+@pytest.mark.parametrize("case", CASES, ids=[f"{c[0]}{c[1]}x{c[2]}" for c in CASES])
+@pytest.mark.parametrize("inner", [1, 2])
+def test_mixed_refinement_reaches_the_fp64_solution(lap, b, case, inner):
+    kind, m, n, dx, dy = case
+    psi = field_of(kind, m, n)
+    t = b.to_field(psi)
+    g = lap.solve(t, dx, dy, method="mg_mixed", tol=1e-10, inner_cycles=inner, max_iter=60)
+    assert g["status"] == "converged"
+    assert g["r_final"] <= 1e-10 * g["r0"] * 1.0000001
+    got = host(t)
+    # FP64 residual norm: bitwise the same as the FP64 kernels compute for the start field
+    assert g["r0"] == lap.residual(b.to_field(psi), dx, dy)
+    ref, o = ora.solve(psi, dx=dx, dy=dy, method=ora.MG, ordering=ora.RB, tol=1e-10)
+    ex = exact.dst_solve(psi, dx / dy)
+    scale = np.max(np.abs(ex))
+    err_mixed = np.max(np.abs(got - ex)) / scale
+    err_fp64 = np.max(np.abs(ref - ex)) / scale
+    # both stop at the same residual; their distance to the exact solution is of one size
+    assert err_mixed <= max(5 * err_fp64, 1e-12), (err_mixed, err_fp64)
+    assert np.max(np.abs(got - ref)) / scale <= max(5 * err_fp64, 1e-12)
+    # and the FP32 inner cycle does not slow the outer convergence much
+    assert g["iters"] <= o["iters"] + 4
+
+
+def test_mixed_full_size_matches_exact_solution(lap, b):
+    psi = wl.sine_edges(4097, 4097, seed=wl.SEED_BASE + 1)
+    t64, tm = b.to_field(psi), b.to_field(psi)
+    g64 = lap.solve(t64, 1 / 4096, 1 / 4096, method="mg", tol=1e-10)
+    gm = lap.solve(tm, 1 / 4096, 1 / 4096, method="mg_mixed", tol=1e-10)
+    assert gm["status"] == "converged" and gm["r0"] == g64["r0"]
+    ex = exact.dst_solve(psi)
+    scale = np.max(np.abs(ex))
+    e64 = np.max(np.abs(host(t64) - ex)) / scale
+    em = np.max(np.abs(host(tm) - ex)) / scale
+    assert em <= max(5 * e64, 1e-12), (em, e64)
+
+
+def test_mixed_handles_max_iter_and_divergence(lap, b):
+    psi = wl.sine_edges(65, 65, seed=3)
+    t = b.to_field(psi)
+    g = lap.solve(t, method="mg_mixed", tol=0.0, max_iter=3)
+    assert g["status"] == "max_iter" and g["iters"] == 3
+    bad = psi.copy()
+    bad[0, 7] = np.inf
+    g = lap.solve(b.to_field(bad), method="mg_mixed", tol=1e-10, max_iter=5)
+    assert g["status"] == "diverged"
+    with pytest.raises(b.LapError):
+        lap.solve(b.to_field(psi), method="mg_mixed", inner_cycles=0)
+
+
+def test_mixed_graphs_equal_direct_launches(b):
+    psi = wl.random_ring(129, 65, seed=5)
+    t = b.field(129, 65)
+    h = b.Laplace()
+    out = []
+    for graphs in (False, True, True):
+        h.set_graphs(graphs)
+        t.copy_(torch.from_numpy(psi))
+        g = h.solve(t, method="mg_mixed", tol=0.0, max_iter=4, check_every=2)
+        out.append((host(t), g["r_final"]))
+    h.close()
+    for o in out[1:]:
+        assert np.array_equal(o[0], out[0][0]) and o[1] == out[0][1]

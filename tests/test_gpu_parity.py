@@ -53,9 +53,13 @@ def ora_kw(method, w=1.0, line_form="A", nu1=2, nu2=2, coarsest_min=5, max_level
         return dict(method=ora.GS, ordering=ora.RB)
     if method == "sor":
         return dict(method=ora.SOR, ordering=ora.RB, w=w)
-    if method == "adi":
-        return dict(method=ora.ADI, w=w, form=ora.FORM_A if line_form == "A" else ora.FORM_B,
-                    line_order=ora.LINES_ZEBRA)
+    if method == "gs_lex":
+        return dict(method=ora.GS, ordering=ora.LEX)
+    if method == "sor_lex":
+        return dict(method=ora.SOR, ordering=ora.LEX, w=w)
+    if method in ("adi", "slor"):
+        return dict(method=ora.ADI if method == "adi" else ora.SLOR, w=w,
+                    form=ora.FORM_A if line_form == "A" else ora.FORM_B, line_order=ora.LINES_ZEBRA)
     return dict(method=ora.MG, ordering=ora.RB, w=smoother_w, nu1=nu1, nu2=nu2,
                 coarsest_min=coarsest_min, max_levels=max_levels, coarse=ora.COARSE_DIRECT)
 
@@ -388,3 +392,54 @@ def test_graph_replay_equals_direct_launches(b, kw):
     for o in outs[1:]:
         assert np.array_equal(o[0], outs[0][0]) and o[1] == outs[0][1]
         assert o[3] == outs[0][3]  # a replayed graph counts the kernels it runs
+
+
+@pytest.mark.parametrize("shape", [(3, 3), (25, 17), (67, 45), (130, 97)])
+@pytest.mark.parametrize("form,w", [("A", 1.0), ("A", 1.65), ("B", 1.25)])
+def test_slor_fixed_iterations(lap, b, shape, form, w):
+    m, n = shape
+    psi = rand_field(m, n, 22)
+    got, g, want, o = both(lap, b, psi, 1.0, 1.1, method="slor", w=w, line_form=form, tol=0.0,
+                           max_iter=6)
+    assert g["iters"] == 6
+    assert relerr(got, want) <= REL
+
+
+@pytest.mark.parametrize("form,w", [("A", 1.65), ("B", 1.25)])
+def test_slor_chamber_matches_oracle(lap, b, form, w):
+    got, g, want, o = both(lap, b, wl.chamber(), 0.25, 0.25, method="slor", line_form=form, w=w,
+                           norm="maxdelta", tol=1e-9)
+    assert g["status"] == o["status"] == "converged" and abs(g["iters"] - o["iters"]) <= 1
+    assert relerr(got, want) <= 1e-10
+
+
+@pytest.mark.parametrize("shape", [(3, 3), (25, 17), (67, 45), (130, 97), (33, 257)])
+@pytest.mark.parametrize("method,w", [("gs_lex", 1.0), ("sor_lex", 1.0), ("sor_lex", 1.8)])
+def test_lexicographic_fixed_iterations_bitwise(lap, b, shape, method, w):
+    m, n = shape
+    psi = rand_field(m, n, 23)
+    got, g, want, o = both(lap, b, psi, 1.0, 0.8, method=method, w=w, tol=0.0, max_iter=11,
+                           check_every=4)
+    assert g["iters"] == 11 and np.array_equal(got, want)
+
+
+def test_paper_chamber_counts_on_the_gpu(lap, b):
+    """The paper's own orderings on its chamber problem (stop at max|dpsi| <= 1e-9), run on
+    the GPU and bitwise equal to the oracle: Jacobi, lexicographic GS, and the SOR w sweep
+    whose optimum the paper prints (1.75)."""
+    kw = dict(norm="maxdelta", tol=1e-9)
+    for method in ("jacobi", "gs_lex"):
+        got, g, want, o = both(lap, b, wl.chamber(), 0.25, 0.25, method=method, **kw)
+        assert g["iters"] == o["iters"] and np.array_equal(got, want)
+    its = []
+    for w in np.round(np.arange(1.0, 1.951, 0.05), 2):
+        got, g, want, o = both(lap, b, wl.chamber(), 0.25, 0.25, method="sor_lex", w=float(w), **kw)
+        assert g["iters"] == o["iters"] and np.array_equal(got, want)
+        its.append(g["iters"])
+    assert np.round(np.arange(1.0, 1.951, 0.05), 2)[int(np.argmin(its))] == 1.75
+
+
+def test_lexicographic_refuses_grids_beyond_one_sm(lap, b):
+    with pytest.raises(b.LapError) as e:
+        lap.solve(b.field(257, 257), method="gs_lex", max_iter=1)
+    assert e.value.code == -4
