@@ -363,6 +363,53 @@ def main():
     mixed["grid_8193"] = mixed_vs_fp64(big_src, 1.0 / 8192, 3)
     del big_src
 
+    # ---- batched uneven grids: 4096 problems, sides 2^k+1 (k = 5..9), aspect <= 4 ---------
+    def batched_workload(count=4096, sample=128):
+        shapes = wl.batch_shapes(count, seed=wl.SEED_BASE + 2)
+        pristine = [b.to_field(wl.random_ring(m, n, seed=wl.SEED_BASE + 2 + 10 * k), dev)
+                    for k, (m, n) in enumerate(shapes)]
+        work = [f.clone() for f in pristine]
+        points = sum((m - 2) * (n - 2) for m, n in shapes)
+        out = {"problems": count, "interior_points": points,
+               "shapes": "m, n in {33, 65, 129, 257, 513}, aspect <= 4, ring U[0,1], interior 0"}
+        kw = dict(mg_kw)
+        for name, method in (("fp64", "mg"), ("mixed", "mg_mixed")):
+            times, res = [], None
+            for rep in range(3):  # first call warms up
+                for f, g in zip(work, pristine):
+                    f.copy_(g)
+                torch.cuda.synchronize(dev)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                res = lap.solve_batched(work, 1.0, 1.0, stream=stream, **dict(kw, method=method))
+                e1.record(stream)
+                stream.synchronize()
+                if rep:
+                    times.append(e0.elapsed_time(e1))
+            if not all(r["status"] == "converged" for r in res):
+                raise RuntimeError(f"batched {name}: not all problems converged")
+            ms = statistics.median(times)
+            out[name] = {"ms": ms, "solves_per_s": count / (ms / 1e3),
+                         "max_cycles": max(r["iters"] for r in res)}
+        # one problem at a time through lap_solve, on a sample
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for f, g in zip(work[:sample], pristine[:sample]):
+            f.copy_(g)
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        for f in work[:sample]:
+            lap.solve(f, 1.0, 1.0, stream=stream, **kw)
+        e1.record(stream)
+        stream.synchronize()
+        per = e0.elapsed_time(e1) / sample
+        out["fp64_one_at_a_time"] = {"ms_per_solve": per, "solves_per_s": 1e3 / per,
+                                     "sample": f"first {sample} problems"}
+        out["mixed_batched_over_fp64_one_at_a_time"] = out["mixed"]["solves_per_s"] / (1e3 / per)
+        out["mixed_batched_over_fp64_batched"] = out["mixed"]["solves_per_s"] / out["fp64"]["solves_per_s"]
+        return out
+
+    batched = batched_workload()
+
     # ---- end to end through the public API with host buffers -----------------------------
     pinned = torch.from_numpy(psi_host.copy()).pin_memory()
     out_host = torch.empty_like(pinned).pin_memory()
@@ -404,7 +451,8 @@ def main():
                     for k in ("sor", "mg")},
         "roofline": roofline, "kernels": kernels, "latency": latency,
         "cpu_baseline": {k: v for k, v in cpu.items() if k != "seconds_per_solve_pair"},
-        "mixed_precision": mixed, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
+        "mixed_precision": mixed, "batched": batched, "e2e": e2e, "gpu_launches": launches,
+        "clocks": clk,
     }
     print(json.dumps(line), flush=True)
     return 0

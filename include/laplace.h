@@ -135,6 +135,16 @@ int lap_workspace_bytes(const lap_grid* g, const lap_params* p, size_t* bytes);
 int lap_solve(lap_handle h, const lap_grid* g, double* psi_dev, const lap_params* p,
               lap_result* out, void* stream);
 
+/* Solve `count` independent problems (grids[k], psi_devs[k], each its own size and
+ * spacing) with the V-cycle: p->method LAP_MG or LAP_MG_MIXED, norm L2_REL or L2_ABS.
+ * Every phase of a cycle is one launch over all problems that take part in it; each
+ * problem gets exactly the arithmetic of its own lap_solve (per problem the iterates are
+ * the same), stops on its own (convergence is decided on the device) and reports in
+ * results[k] (host). p->check_every sets how often (in cycles) the host polls for the
+ * number of problems still running. Synchronises `stream` before returning. */
+int lap_solve_batched(lap_handle h, int count, const lap_grid* grids, double* const* psi_devs,
+                      const lap_params* p, lap_result* results, void* stream);
+
 /* ||r||_2 over interior nodes of the scaled residual of Eqs. 11-12,
  * r = fma(-d, psi, fma(beta^2, N + S, E + W) [+ q]), written to *out (host).
  * q_dev may be NULL (Laplace) or a field with the same pitch (coarse-level source). */

@@ -89,6 +89,7 @@ def load():
             "lap_coarse_solve": (C.c_int, [c_void_p, G, c_void_p, c_void_p, c_void_p]),
             "lap_line_sweep": (C.c_int, [c_void_p, G, c_void_p, c_double, C.c_int, C.c_int, c_void_p]),
             "lap_set_graphs": (C.c_int, [c_void_p, C.c_int]),
+            "lap_solve_batched": (C.c_int, [c_void_p, C.c_int, G, C.POINTER(c_void_p), P, R, c_void_p]),
             "lap_strerror": (C.c_char_p, [C.c_int]),
             "lap_last_error": (C.c_char_p, []),
             "lap_kernel_launches": (c_int64, []),
@@ -200,6 +201,21 @@ class Laplace:
                                    C.byref(params(**kw)), C.byref(res), _stream(stream, psi.device)))
         return {"status": STATUS.get(res.status, res.status), "iters": res.iters, "r0": res.r0,
                 "r_final": res.r_final, "last_check": res.last_check}
+
+    def solve_batched(self, fields, dx=1.0, dy=1.0, stream=None, **kw) -> list:
+        """Solve many fields (different sizes allowed) with the V-cycle in batched launches.
+        dx, dy: scalars or one value per field. Returns one result dict per field."""
+        n = len(fields)
+        dxs = dx if hasattr(dx, "__len__") else [dx] * n
+        dys = dy if hasattr(dy, "__len__") else [dy] * n
+        grids = (Grid * n)(*[_grid(f, a, c) for f, a, c in zip(fields, dxs, dys)])
+        ptrs = (c_void_p * n)(*[f.data_ptr() for f in fields])
+        res = (Result * n)()
+        dev = fields[0].device
+        _check(self._lib.lap_solve_batched(self._h, n, grids, ptrs, C.byref(params(**kw)), res,
+                                           _stream(stream, dev)))
+        return [{"status": STATUS.get(r.status, r.status), "iters": r.iters, "r0": r.r0,
+                 "r_final": r.r_final, "last_check": r.last_check} for r in res]
 
     def solve_host(self, psi_host: torch.Tensor, dx=1.0, dy=1.0, work=None, stream=None, **kw):
         """End-to-end solve of a host array: copy in, solve on the device, copy back

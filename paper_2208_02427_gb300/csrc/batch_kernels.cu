@@ -1,0 +1,384 @@
+// batch_kernels.cu -- the V-cycle over many independent grids of different sizes.
+//
+// Every phase of a cycle (a smoother colour pass, the residual, the restriction, the
+// interpolation, the coarsest solve, the residual norm) is one launch over a work list of
+// (level, block of rows) items gathered from all problems that take part in that phase.
+// Per problem the arithmetic is exactly the single-grid kernels' (same expressions, same
+// roundings), so a batched solve reproduces each problem's single-grid iterates. A
+// problem that has converged is skipped by every later launch (its `active` flag); the
+// norm kernels decide convergence on the device.
+//
+// The level data are generic in T: double for the FP64 V-cycle, float for the inner cycle
+// of the mixed-precision solver (FP32 inside FP64 defect correction).
+#include "lap_device.cuh"
+#include "lap_internal.cuh"
+
+namespace lap {
+
+namespace {
+
+constexpr int BT = 256;  // threads per work item
+
+// Arithmetic of one precision, matching the single-grid kernels of that precision.
+template <class T> struct Arith;
+template <> struct Arith<double> {
+    FmaOps o;
+    __device__ double add(double a, double b) const { return fadd(o, a, b); }
+    __device__ double mul(double a, double b) const { return fmul(o, a, b); }
+    __device__ double fma(double a, double b, double c) const { return __fma_rn(a, b, c); }
+    __device__ double nsum(double w, double e, double s, double n, double b2, bool unit) const
+    {
+        return unit ? neighbour_sum<true>(o, w, e, s, n, b2) : neighbour_sum<false>(o, w, e, s, n, b2);
+    }
+    __device__ double inv_d(double s, const BatchLevel<double>& L) const
+    {
+        return L.inv_d_shift > 0 ? times_inv_d<true>(o, s, L.inv_d, L.inv_d_shift)
+                                 : times_inv_d<false>(o, s, L.inv_d, 0);
+    }
+    __device__ double half(double x) const { return scale_down_pow2(o, x, 1, 0.5); }
+    __device__ double quarter(double x) const { return scale_down_pow2(o, x, 2, 0.25); }
+};
+template <> struct Arith<float> {
+    __device__ float add(float a, float b) const { return __fadd_rn(a, b); }
+    __device__ float mul(float a, float b) const { return __fmul_rn(a, b); }
+    __device__ float fma(float a, float b, float c) const { return __fmaf_rn(a, b, c); }
+    __device__ float nsum(float w, float e, float s, float n, float b2, bool unit) const
+    {
+        const float ew = __fadd_rn(w, e), ns = __fadd_rn(s, n);
+        return unit ? __fadd_rn(ns, ew) : __fmaf_rn(b2, ns, ew);
+    }
+    __device__ float inv_d(float s, const BatchLevel<float>& L) const
+    {
+        return __fmul_rn(s, (float)L.inv_d);
+    }
+    __device__ float half(float x) const { return __fmul_rn(0.5f, x); }
+    __device__ float quarter(float x) const { return __fmul_rn(0.25f, x); }
+};
+
+template <class T>
+__device__ __forceinline__ Arith<T> arith();
+template <>
+__device__ __forceinline__ Arith<double> arith<double>() { return Arith<double>{load_fma_ops()}; }
+template <>
+__device__ __forceinline__ Arith<float> arith<float>() { return Arith<float>{}; }
+
+// One smoother colour pass (Eq. 6 when gs, Eq. 7 otherwise) over the rows of each item.
+template <class T>
+__global__ void __launch_bounds__(BT)
+    b_rb_kernel(const BatchItem* __restrict__ items, const BatchLevel<T>* __restrict__ lv,
+                const int* __restrict__ active, int colour, int gs, T w, T omw)
+{
+    const BatchItem it = items[blockIdx.x];
+    const BatchLevel<T> L = lv[it.level];
+    if (!active[L.problem]) return;
+    const Arith<T> A = arith<T>();
+    const int half_w = (L.m - 2 + 1) / 2;
+    for (int k = threadIdx.x; k < it.rows * half_w; k += BT) {
+        const int j = it.row0 + k / half_w;
+        const int i = 1 + ((1 + j + colour) & 1) + 2 * (k % half_w);
+        if (i > L.m - 2) continue;
+        const int64_t at = (int64_t)j * L.pitch + i;
+        T* c = L.u + at;
+        T s = A.nsum(c[-1], c[1], c[-L.pitch], c[L.pitch], (T)L.b2, L.unit_beta);
+        if (L.q) s = A.add(s, L.q[at]);
+        const T g = A.inv_d(s, L);
+        *c = gs ? g : A.fma(w, g, A.mul(omw, *c));
+    }
+}
+
+template <class T>
+__global__ void __launch_bounds__(BT)
+    b_defect_kernel(const BatchItem* __restrict__ items, const BatchLevel<T>* __restrict__ lv,
+                    const int* __restrict__ active)
+{
+    const BatchItem it = items[blockIdx.x];
+    const BatchLevel<T> L = lv[it.level];
+    if (!active[L.problem]) return;
+    const Arith<T> A = arith<T>();
+    const int wdt = L.m - 2;
+    for (int k = threadIdx.x; k < it.rows * wdt; k += BT) {
+        const int j = it.row0 + k / wdt, i = 1 + k % wdt;
+        const int64_t at = (int64_t)j * L.pitch + i;
+        const T* c = L.u + at;
+        T s = A.nsum(c[-1], c[1], c[-L.pitch], c[L.pitch], (T)L.b2, L.unit_beta);
+        if (L.q) s = A.add(s, L.q[at]);
+        L.r[at] = A.fma(-(T)L.d, *c, s);
+    }
+}
+
+// Items of the coarse level: qc from the fine residual (the level before it in lv), and the
+// coarse correction zeroed.
+template <class T>
+__global__ void __launch_bounds__(BT)
+    b_restrict_kernel(const BatchItem* __restrict__ items, const BatchLevel<T>* __restrict__ lv,
+                      const int* __restrict__ active)
+{
+    const BatchItem it = items[blockIdx.x];
+    const BatchLevel<T> C = lv[it.level];
+    if (!active[C.problem]) return;
+    const BatchLevel<T> F = lv[it.level - 1];
+    const Arith<T> A = arith<T>();
+    const int wdt = C.m - 2;
+    const int64_t pf = F.pitch;
+    for (int k = threadIdx.x; k < it.rows * wdt; k += BT) {
+        const int J = it.row0 + k / wdt, I = 1 + k % wdt;
+        const T* c = F.r + (int64_t)(2 * J) * pf + 2 * I;
+        const T edges = A.add(A.add(c[-1], c[1]), A.add(c[-pf], c[pf]));
+        const T corners = A.add(A.add(c[-pf - 1], c[-pf + 1]), A.add(c[pf - 1], c[pf + 1]));
+        const T t = A.fma((T)2, c[0], edges);
+        const int64_t at = (int64_t)J * C.pitch + I;
+        C.q[at] = A.quarter(A.fma((T)2, t, corners));
+        C.u[at] = (T)0;
+    }
+}
+
+// Items of the fine level: u += bilinear interpolation of the next level's correction.
+template <class T>
+__global__ void __launch_bounds__(BT)
+    b_prolong_kernel(const BatchItem* __restrict__ items, const BatchLevel<T>* __restrict__ lv,
+                     const int* __restrict__ active)
+{
+    const BatchItem it = items[blockIdx.x];
+    const BatchLevel<T> F = lv[it.level];
+    if (!active[F.problem]) return;
+    const BatchLevel<T> C = lv[it.level + 1];
+    const Arith<T> A = arith<T>();
+    const int pairs = (F.m - 1) / 2;  // coarse columns 0 .. mc-2
+    const int64_t pc = C.pitch;
+    for (int k = threadIdx.x; k < it.rows * pairs; k += BT) {
+        const int j = it.row0 + k / pairs, I = k % pairs;
+        const T* a = C.u + (int64_t)(j >> 1) * pc + I;
+        const int i0 = 2 * I, i1 = 2 * I + 1;
+        T* row = F.u + (int64_t)j * F.pitch;
+        if ((j & 1) == 0) {
+            if (i0 >= 1) row[i0] = A.add(row[i0], a[0]);
+            if (i1 <= F.m - 2) row[i1] = A.add(row[i1], A.half(A.add(a[0], a[1])));
+        } else {
+            if (i0 >= 1) row[i0] = A.add(row[i0], A.half(A.add(a[0], a[pc])));
+            if (i1 <= F.m - 2) {
+                const T s = A.add(A.add(a[0], a[1]), A.add(a[pc], a[pc + 1]));
+                row[i1] = A.add(row[i1], A.quarter(s));
+            }
+        }
+    }
+}
+
+// One item per problem at its coarsest level: u = A^-1 b in FP64.
+template <class T>
+__global__ void __launch_bounds__(1024)
+    b_coarse_kernel(const BatchItem* __restrict__ items, const BatchLevel<T>* __restrict__ lv,
+                    const int* __restrict__ active)
+{
+    extern __shared__ double b[];
+    const BatchItem it = items[blockIdx.x];
+    const BatchLevel<T> L = lv[it.level];
+    if (!active[L.problem]) return;
+    const int mi = L.m - 2, N = mi * (L.n - 2);
+    for (int k = threadIdx.x; k < N; k += blockDim.x) {
+        const int i = 1 + k % mi, j = 1 + k / mi;
+        const int64_t at = (int64_t)j * L.pitch + i;
+        double v = L.q ? (double)L.q[at] : 0.0;
+        if (i == 1) v = __dadd_rn(v, (double)L.u[at - 1]);
+        if (i == L.m - 2) v = __dadd_rn(v, (double)L.u[at + 1]);
+        if (j == 1) v = __fma_rn(L.b2, (double)L.u[at - L.pitch], v);
+        if (j == L.n - 2) v = __fma_rn(L.b2, (double)L.u[at + L.pitch], v);
+        b[k] = v;
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < N; k += blockDim.x) {
+        double x = 0.0;
+        for (int l = 0; l < N; ++l) x = __fma_rn(L.ainv_t[(int64_t)l * N + k], b[l], x);
+        const int i = 1 + k % mi, j = 1 + k / mi;
+        L.u[(int64_t)j * L.pitch + i] = (T)x;
+    }
+}
+
+// FP64 residual of each item's rows: per-item sum of squares (fixed order) and, for the
+// mixed solver, the residual rounded to FP32 with the FP32 correction zeroed.
+__global__ void __launch_bounds__(BT)
+    b_sumsq_kernel(const BatchItem* __restrict__ items, const BatchLevel<double>* __restrict__ lv,
+                   const int* __restrict__ active, double* __restrict__ partials,
+                   const BatchLevel<float>* __restrict__ lv32)
+{
+    const BatchItem it = items[blockIdx.x];
+    const BatchLevel<double> L = lv[it.level];
+    if (!active[L.problem]) return;
+    const Arith<double> A = arith<double>();
+    const int wdt = L.m - 2;
+    double acc = 0.0;
+    float* r32 = nullptr;
+    float* e32 = nullptr;
+    int64_t p32 = 0;
+    if (lv32) {
+        r32 = lv32[it.level].q;
+        e32 = lv32[it.level].u;
+        p32 = lv32[it.level].pitch;
+    }
+    for (int k = threadIdx.x; k < it.rows * wdt; k += BT) {
+        const int j = it.row0 + k / wdt, i = 1 + k % wdt;
+        const double* c = L.u + (int64_t)j * L.pitch + i;
+        const double s = A.nsum(c[-1], c[1], c[-L.pitch], c[L.pitch], L.b2, L.unit_beta);
+        const double r = __fma_rn(-L.d, *c, s);
+        acc = __fma_rn(r, r, acc);
+        if (r32) {
+            const int64_t at = (int64_t)j * p32 + i;
+            r32[at] = __double2float_rn(r);
+            e32[at] = 0.0f;
+        }
+    }
+    __shared__ double red[BT / 32];
+    acc = warp_sum(acc);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double v = threadIdx.x < BT / 32 ? red[threadIdx.x] : 0.0;
+        v = warp_sum(v);
+        if (threadIdx.x == 0) partials[blockIdx.x] = v;
+    }
+}
+
+// psi += e32 (FP64 update of the mixed solver).
+__global__ void __launch_bounds__(BT)
+    b_update_kernel(const BatchItem* __restrict__ items, const BatchLevel<double>* __restrict__ lv,
+                    const int* __restrict__ active, const BatchLevel<float>* __restrict__ lv32)
+{
+    const BatchItem it = items[blockIdx.x];
+    const BatchLevel<double> L = lv[it.level];
+    if (!active[L.problem]) return;
+    const FmaOps o = load_fma_ops();
+    const BatchLevel<float> E = lv32[it.level];
+    const int wdt = L.m - 2;
+    for (int k = threadIdx.x; k < it.rows * wdt; k += BT) {
+        const int j = it.row0 + k / wdt, i = 1 + k % wdt;
+        double* c = L.u + (int64_t)j * L.pitch + i;
+        *c = fadd(o, *c, (double)E.u[(int64_t)j * E.pitch + i]);
+    }
+}
+
+// Per problem: the norm from its items' partials (fixed order), then the stopping test.
+// first_item[p] .. first_item[p+1] are problem p's items in the norm list. mode 0 records
+// r0; mode 1 tests ||r|| <= tol r0 (rel) or <= tol (abs) and retires converged problems.
+__global__ void b_converge_kernel(const double* __restrict__ partials,
+                                  const int* __restrict__ first_item, int count,
+                                  int* __restrict__ active, double* __restrict__ r0,
+                                  double* __restrict__ rnow, long long* __restrict__ iters,
+                                  int* __restrict__ status, int* __restrict__ remaining, int mode,
+                                  int rel, double tol)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= count || !active[p]) return;
+    double s = 0.0;
+    for (int k = first_item[p]; k < first_item[p + 1]; ++k) s = __dadd_rn(s, partials[k]);
+    const double nr = sqrt(s);
+    rnow[p] = nr;
+    if (mode == 0) {
+        r0[p] = nr;
+        iters[p] = 0;
+        if (!isfinite(nr)) {
+            status[p] = 2;
+        } else if ((rel && nr == 0.0) || (!rel && nr <= tol)) {
+            status[p] = 0;
+        } else {
+            return;
+        }
+    } else {
+        iters[p] += 1;  // cycles done while active (replayed graphs need no host counter)
+        if (!isfinite(nr)) status[p] = 2;
+        else if (rel ? nr <= tol * r0[p] : nr <= tol) status[p] = 0;
+        else return;
+    }
+    active[p] = 0;
+    atomicSub(remaining, 1);
+}
+
+}  // namespace
+
+template <class T>
+cudaError_t launch_b_rb(const BatchList& l, const BatchLevel<T>* lv, const int* active, int colour,
+                        bool gs, double w, cudaStream_t s)
+{
+    if (l.count == 0) return cudaSuccess;
+    b_rb_kernel<T><<<l.count, BT, 0, s>>>(l.items, lv, active, colour, gs ? 1 : 0, (T)w, (T)(1.0 - w));
+    note_launch();
+    return cudaGetLastError();
+}
+template <class T>
+cudaError_t launch_b_defect(const BatchList& l, const BatchLevel<T>* lv, const int* active,
+                            cudaStream_t s)
+{
+    if (l.count == 0) return cudaSuccess;
+    b_defect_kernel<T><<<l.count, BT, 0, s>>>(l.items, lv, active);
+    note_launch();
+    return cudaGetLastError();
+}
+template <class T>
+cudaError_t launch_b_restrict(const BatchList& l, const BatchLevel<T>* lv, const int* active,
+                              cudaStream_t s)
+{
+    if (l.count == 0) return cudaSuccess;
+    b_restrict_kernel<T><<<l.count, BT, 0, s>>>(l.items, lv, active);
+    note_launch();
+    return cudaGetLastError();
+}
+template <class T>
+cudaError_t launch_b_prolong(const BatchList& l, const BatchLevel<T>* lv, const int* active,
+                             cudaStream_t s)
+{
+    if (l.count == 0) return cudaSuccess;
+    b_prolong_kernel<T><<<l.count, BT, 0, s>>>(l.items, lv, active);
+    note_launch();
+    return cudaGetLastError();
+}
+template <class T>
+cudaError_t launch_b_coarse(const BatchList& l, const BatchLevel<T>* lv, const int* active,
+                            int max_unknowns, cudaStream_t s)
+{
+    if (l.count == 0) return cudaSuccess;
+    int threads = ((max_unknowns + 31) / 32) * 32;
+    threads = threads < 32 ? 32 : (threads > 1024 ? 1024 : threads);
+    b_coarse_kernel<T><<<l.count, threads, sizeof(double) * max_unknowns, s>>>(l.items, lv, active);
+    note_launch();
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_b_rb<double>(const BatchList&, const BatchLevel<double>*, const int*, int, bool, double, cudaStream_t);
+template cudaError_t launch_b_rb<float>(const BatchList&, const BatchLevel<float>*, const int*, int, bool, double, cudaStream_t);
+template cudaError_t launch_b_defect<double>(const BatchList&, const BatchLevel<double>*, const int*, cudaStream_t);
+template cudaError_t launch_b_defect<float>(const BatchList&, const BatchLevel<float>*, const int*, cudaStream_t);
+template cudaError_t launch_b_restrict<double>(const BatchList&, const BatchLevel<double>*, const int*, cudaStream_t);
+template cudaError_t launch_b_restrict<float>(const BatchList&, const BatchLevel<float>*, const int*, cudaStream_t);
+template cudaError_t launch_b_prolong<double>(const BatchList&, const BatchLevel<double>*, const int*, cudaStream_t);
+template cudaError_t launch_b_prolong<float>(const BatchList&, const BatchLevel<float>*, const int*, cudaStream_t);
+template cudaError_t launch_b_coarse<double>(const BatchList&, const BatchLevel<double>*, const int*, int, cudaStream_t);
+template cudaError_t launch_b_coarse<float>(const BatchList&, const BatchLevel<float>*, const int*, int, cudaStream_t);
+
+cudaError_t launch_b_sumsq(const BatchList& l, const BatchLevel<double>* lv, const int* active,
+                           double* partials, const BatchLevel<float>* lv32, cudaStream_t s)
+{
+    if (l.count == 0) return cudaSuccess;
+    b_sumsq_kernel<<<l.count, BT, 0, s>>>(l.items, lv, active, partials, lv32);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_b_update(const BatchList& l, const BatchLevel<double>* lv, const int* active,
+                            const BatchLevel<float>* lv32, cudaStream_t s)
+{
+    if (l.count == 0) return cudaSuccess;
+    b_update_kernel<<<l.count, BT, 0, s>>>(l.items, lv, active, lv32);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_b_converge(const double* partials, const int* first_item, int count, int* active,
+                              double* r0, double* rnow, long long* iters, int* status,
+                              int* remaining, int mode, bool rel, double tol, cudaStream_t s)
+{
+    b_converge_kernel<<<(count + 127) / 128, 128, 0, s>>>(partials, first_item, count, active, r0,
+                                                          rnow, iters, status, remaining, mode,
+                                                          rel ? 1 : 0, tol);
+    note_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace lap

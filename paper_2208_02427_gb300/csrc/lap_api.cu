@@ -454,6 +454,7 @@ struct Level32 {
 };
 
 struct Work {
+    double* wslot = nullptr;     // {w, 1 - w} of the point sweeps, read by the kernels
     double* partials = nullptr;  // norm partial sums
     double* nrm = nullptr;       // [sum, sqrt]
     unsigned long long* maxd = nullptr;
@@ -465,6 +466,7 @@ struct Work {
 template <class C>
 void carve(C& cv, Work& w, const lap_grid* g, const lap_params* p)
 {
+    w.wslot = cv.template take<double>(2);
     w.partials = cv.template take<double>(2048);
     w.nrm = cv.template take<double>(2);
     w.maxd = cv.template take<unsigned long long>(1);
@@ -585,7 +587,8 @@ struct Solver {
         case LAP_GS_RB:
         case LAP_SOR_RB:
             for (int colour = 0; colour < 2; ++colour)
-                ck(launch_rb_colour(f, nullptr, c, gs, gs ? 1.0 : p->w, colour, md, s), "rb kernel");
+                ck(launch_rb_colour(f, nullptr, c, gs, gs ? 1.0 : p->w, colour, md, s, w.wslot),
+                   "rb kernel");
             break;
         case LAP_ADI:
             line_half_sweep(h, f, c, p->w, p->line_form, 0, s);
@@ -638,7 +641,7 @@ struct Solver {
         const bool gs = p->smoother_w == 1.0;
         for (int k = 0; k < sweeps; ++k)
             for (int colour = 0; colour < 2; ++colour)
-                ck(launch_rb_colour(lv.u, lv.q, c, gs, p->smoother_w, colour, nullptr, s),
+                ck(launch_rb_colour(lv.u, lv.q, c, gs, p->smoother_w, colour, nullptr, s, w.wslot),
                    "smoother kernel");
     }
 
@@ -781,6 +784,11 @@ struct Solver {
         out->status = LAP_MAXITER;
         out->iters = 0;
         out->last_check = NAN;
+        {
+            const double wv = p->method == LAP_MG ? p->smoother_w : p->w;
+            const double pair[2] = {wv, 1.0 - wv};  // staged by the copy before it returns
+            ck(cudaMemcpyAsync(w.wslot, pair, sizeof pair, cudaMemcpyHostToDevice, s), "upload w");
+        }
         if (p->method == LAP_JACOBI) {
             copy_field(w.aux, f.p);  // ring + initial interior in both buffers
             jac_cur = f.p;
@@ -847,6 +855,283 @@ struct Solver {
 };
 
 }  // namespace
+
+// ---- many grids at once ---------------------------------------------------------------------
+
+namespace {
+
+constexpr int BATCH_ITEM_POINTS = 2048;  // interior points per work item (rows are not split)
+
+struct BatchPlan {
+    std::vector<BatchLevel<double>> lv64;
+    std::vector<BatchLevel<float>> lv32;
+    std::vector<int> nlev, base;       // levels and first level index per problem
+    std::vector<BatchItem> items;      // all work lists, back to back
+    std::vector<std::pair<int, int>> fine, all, coarse;  // per level: [first, count) into items
+    std::pair<int, int> norm;          // level-0 items of every problem, problem by problem
+    std::vector<int> first_item;       // per problem: its first item in the norm list (+ end)
+    int max_coarse_unknowns = 0;
+    int levels = 0;
+};
+
+void add_items(BatchPlan& P, int level_index, int m, int n)
+{
+    const int per = std::max(1, BATCH_ITEM_POINTS / std::max(1, m - 2));
+    for (int r = 1; r <= n - 2; r += per) P.items.push_back(BatchItem{level_index, r, std::min(per, n - 1 - r)});
+}
+
+}  // namespace
+
+extern "C" int lap_solve_batched(lap_handle h, int count, const lap_grid* grids,
+                                 double* const* psi_devs, const lap_params* p, lap_result* results,
+                                 void* stream)
+{
+    return guarded([&] {
+        if (!h) fail(LAP_EINVAL, "handle is NULL");
+        if (count < 1 || !grids || !psi_devs || !results) fail(LAP_EINVAL, "empty or NULL batch");
+        check_params(p);
+        if (p->method != LAP_MG && p->method != LAP_MG_MIXED)
+            fail(LAP_EINVAL, "batched solves take LAP_MG or LAP_MG_MIXED");
+        if (p->norm == LAP_NORM_MAXDELTA) fail(LAP_EINVAL, "batched solves stop on an L2 norm");
+        set_device(h);
+        const bool mixed = p->method == LAP_MG_MIXED;
+        cudaStream_t s = (cudaStream_t)stream;
+        BatchPlan P;
+        P.nlev.resize(count);
+        P.base.resize(count);
+        // ---- level descriptors (buffers are carved below) ----
+        for (int q = 0; q < count; ++q) {
+            const lap_grid* g = &grids[q];
+            check_grid(g);
+            check_device_ptr(h, psi_devs[q], "psi");
+            const int L = mg_level_count(g->m, g->n, p->coarsest_min, p->max_levels);
+            P.nlev[q] = L;
+            P.base[q] = (int)P.lv64.size();
+            P.levels = std::max(P.levels, L);
+            const Coef c = make_coef(g->dx, g->dy);
+            int m = g->m, n = g->n;
+            for (int l = 0; l < L; ++l) {
+                BatchLevel<double> d{};
+                d.m = m;
+                d.n = n;
+                d.pitch = l == 0 ? g->pitch : round_up(m, 32);
+                d.problem = q;
+                d.unit_beta = c.unit_beta;
+                d.inv_d_shift = c.inv_d_shift;
+                d.b2 = c.b2;
+                d.d = c.d;
+                d.inv_d = c.inv_d;
+                BatchLevel<float> f{};
+                f.m = m;
+                f.n = n;
+                f.pitch = round_up(m, 32);
+                f.problem = q;
+                f.unit_beta = c.unit_beta;
+                f.inv_d_shift = 0;
+                f.b2 = c.b2;
+                f.d = c.d;
+                f.inv_d = c.inv_d;
+                if (l == L - 1) {
+                    if ((int64_t)(m - 2) * (n - 2) > COARSE_MAX_UNKNOWNS)
+                        fail(LAP_EUNSUPPORTED, "coarsest level with more than 1024 unknowns");
+                    d.ainv_t = f.ainv_t = coarse_inverse(h, m, n, c.b2, c.d);
+                    P.max_coarse_unknowns = std::max(P.max_coarse_unknowns, (m - 2) * (n - 2));
+                }
+                P.lv64.push_back(d);
+                P.lv32.push_back(f);
+                m = (m - 1) / 2 + 1;
+                n = (n - 1) / 2 + 1;
+            }
+        }
+        // ---- work lists ----
+        P.fine.resize(P.levels);
+        P.all.resize(P.levels);
+        P.coarse.resize(P.levels);
+        for (int l = 0; l < P.levels; ++l) {
+            const int f0 = (int)P.items.size();
+            for (int q = 0; q < count; ++q)
+                if (P.nlev[q] - 1 > l) add_items(P, P.base[q] + l, P.lv64[P.base[q] + l].m, P.lv64[P.base[q] + l].n);
+            P.fine[l] = {f0, (int)P.items.size() - f0};
+            const int a0 = (int)P.items.size();
+            for (int q = 0; q < count; ++q)
+                if (P.nlev[q] > l) add_items(P, P.base[q] + l, P.lv64[P.base[q] + l].m, P.lv64[P.base[q] + l].n);
+            P.all[l] = {a0, (int)P.items.size() - a0};
+            const int c0 = (int)P.items.size();
+            for (int q = 0; q < count; ++q)
+                if (P.nlev[q] - 1 == l) {
+                    const BatchLevel<double>& d = P.lv64[P.base[q] + l];
+                    P.items.push_back(BatchItem{P.base[q] + l, 1, d.n - 2});
+                }
+            P.coarse[l] = {c0, (int)P.items.size() - c0};
+        }
+        const int n0 = (int)P.items.size();
+        for (int q = 0; q < count; ++q) {
+            P.first_item.push_back((int)P.items.size() - n0);
+            add_items(P, P.base[q], grids[q].m, grids[q].n);
+        }
+        P.first_item.push_back((int)P.items.size() - n0);
+        P.norm = {n0, (int)P.items.size() - n0};
+        // ---- memory: level buffers, descriptors, lists, state ----
+        auto carve_all = [&](auto& cv) {
+            for (int q = 0; q < count; ++q)
+                for (int l = 0; l < P.nlev[q]; ++l) {
+                    const int k = P.base[q] + l;
+                    BatchLevel<double>& d = P.lv64[k];
+                    BatchLevel<float>& f = P.lv32[k];
+                    const bool last = l == P.nlev[q] - 1;
+                    if (!mixed) {
+                        if (l == 0) {
+                            d.u = psi_devs[q];
+                            d.q = nullptr;
+                        } else {
+                            d.u = cv.template take<double>((size_t)d.n * d.pitch);
+                            d.q = cv.template take<double>((size_t)d.n * d.pitch);
+                        }
+                        d.r = last ? nullptr : cv.template take<double>((size_t)d.n * d.pitch);
+                    } else {
+                        if (l == 0) d.u = psi_devs[q];
+                        f.u = cv.template take<float>((size_t)f.n * f.pitch);
+                        f.q = cv.template take<float>((size_t)f.n * f.pitch);
+                        f.r = last ? nullptr : cv.template take<float>((size_t)f.n * f.pitch);
+                    }
+                }
+            auto* lv64 = cv.template take<BatchLevel<double>>(P.lv64.size());
+            auto* lv32 = cv.template take<BatchLevel<float>>(P.lv32.size());
+            auto* items = cv.template take<BatchItem>(P.items.size());
+            auto* first = cv.template take<int>(P.first_item.size());
+            auto* active = cv.template take<int>(count);
+            auto* status = cv.template take<int>(count);
+            auto* remaining = cv.template take<int>(1);
+            auto* iters = cv.template take<long long>(count);
+            auto* r0 = cv.template take<double>(count);
+            auto* rnow = cv.template take<double>(count);
+            auto* partials = cv.template take<double>(std::max(1, P.norm.second));
+            return std::make_tuple(lv64, lv32, items, first, active, status, remaining, iters, r0,
+                                   rnow, partials);
+        };
+        Sizer sz;
+        carve_all(sz);
+        Carver cv(arena(h, sz.off));
+        auto [lv64, lv32, items, first, active, status, remaining, iters, r0, rnow, partials] =
+            carve_all(cv);
+        // zero every level buffer (rings of corrections stay zero), then upload tables
+        const size_t level_bytes = (size_t)((char*)lv64 - (char*)h->arena);
+        if (level_bytes) ck(cudaMemsetAsync(h->arena, 0, level_bytes, s), "zero levels");
+        std::vector<int> ones(count, 1);
+        const int cnt = count;
+        ck(cudaMemcpyAsync(lv64, P.lv64.data(), P.lv64.size() * sizeof(P.lv64[0]), cudaMemcpyHostToDevice, s), "upload levels");
+        ck(cudaMemcpyAsync(lv32, P.lv32.data(), P.lv32.size() * sizeof(P.lv32[0]), cudaMemcpyHostToDevice, s), "upload levels");
+        ck(cudaMemcpyAsync(items, P.items.data(), P.items.size() * sizeof(BatchItem), cudaMemcpyHostToDevice, s), "upload items");
+        ck(cudaMemcpyAsync(first, P.first_item.data(), P.first_item.size() * sizeof(int), cudaMemcpyHostToDevice, s), "upload items");
+        ck(cudaMemcpyAsync(active, ones.data(), count * sizeof(int), cudaMemcpyHostToDevice, s), "upload flags");
+        ck(cudaMemcpyAsync(status, ones.data(), count * sizeof(int), cudaMemcpyHostToDevice, s), "upload flags");
+        ck(cudaMemcpyAsync(remaining, &cnt, sizeof(int), cudaMemcpyHostToDevice, s), "upload count");
+        ck(cudaMemsetAsync(iters, 0, count * sizeof(long long), s), "zero iterations");
+        ck(cudaStreamSynchronize(s), "stream sync");  // host vectors above go out of scope
+        auto list = [&](std::pair<int, int> r) { return BatchList{items + r.first, r.second}; };
+        const BatchList norm_list = list(P.norm);
+        const bool rel = p->norm == LAP_NORM_L2_REL;
+        // ---- one V-cycle over every active problem, in T precision ----
+        auto vcycle = [&](auto* lv, double smoother_w, cudaStream_t st) {
+            const bool gs = smoother_w == 1.0;
+            for (int l = 0; l < P.levels; ++l) {
+                ck(launch_b_coarse(list(P.coarse[l]), lv, active, P.max_coarse_unknowns, st), "batched coarse");
+                if (l == P.levels - 1) break;
+                for (int k = 0; k < p->nu1; ++k)
+                    for (int colour = 0; colour < 2; ++colour)
+                        ck(launch_b_rb(list(P.fine[l]), lv, active, colour, gs, smoother_w, st), "batched smoother");
+                ck(launch_b_defect(list(P.fine[l]), lv, active, st), "batched defect");
+                ck(launch_b_restrict(list(P.all[l + 1]), lv, active, st), "batched restrict");
+            }
+            for (int l = P.levels - 2; l >= 0; --l) {
+                ck(launch_b_prolong(list(P.fine[l]), lv, active, st), "batched prolong");
+                for (int k = 0; k < p->nu2; ++k)
+                    for (int colour = 0; colour < 2; ++colour)
+                        ck(launch_b_rb(list(P.fine[l]), lv, active, colour, gs, smoother_w, st), "batched smoother");
+            }
+        };
+        auto cycle = [&](cudaStream_t st) {
+            if (mixed) {
+                for (int k = 0; k < p->inner_cycles; ++k) vcycle(lv32, p->smoother_w, st);
+                ck(launch_b_update(norm_list, lv64, active, lv32, st), "batched update");
+                ck(launch_b_sumsq(norm_list, lv64, active, partials, lv32, st), "batched residual");
+            } else {
+                vcycle(lv64, p->smoother_w, st);
+                ck(launch_b_sumsq(norm_list, lv64, active, partials, nullptr, st), "batched residual");
+            }
+            ck(launch_b_converge(partials, first, count, active, r0, rnow, iters, status, remaining,
+                                 1, rel, p->tol, st), "batched convergence");
+        };
+        // initial residuals (and, for the mixed solver, the first FP32 right-hand sides)
+        ck(launch_b_sumsq(norm_list, lv64, active, partials, mixed ? lv32 : nullptr, s), "batched residual");
+        ck(launch_b_converge(partials, first, count, active, r0, rnow, iters, status, remaining, 0,
+                             rel, p->tol, s), "batched convergence");
+        // capture one cycle as a graph on the handle's stream, replay it on the caller's
+        cudaGraphExec_t exec = nullptr;
+        int64_t graph_kernels = 0;
+        if (h->use_graphs) {
+            if (!h->capture)
+                ck(cudaStreamCreateWithFlags(&h->capture, cudaStreamNonBlocking), "capture stream");
+            const int64_t before = launches_now();
+            ck(cudaStreamBeginCapture(h->capture, cudaStreamCaptureModeThreadLocal), "begin capture");
+            cudaGraph_t g = nullptr;
+            try {
+                cycle(h->capture);
+            } catch (...) {
+                cudaStreamEndCapture(h->capture, &g);
+                if (g) cudaGraphDestroy(g);
+                cudaGetLastError();
+                throw;
+            }
+            ck(cudaStreamEndCapture(h->capture, &g), "end capture");
+            graph_kernels = launches_now() - before;
+            add_launches(-graph_kernels);
+            const cudaError_t e = cudaGraphInstantiate(&exec, g, 0);
+            cudaGraphDestroy(g);
+            ck(e, "instantiate graph");
+        }
+        int64_t done = 0;
+        int left = count;
+        try {
+            while (done < p->max_iter) {
+                ck(cudaMemcpyAsync(h->pinned, remaining, sizeof(int), cudaMemcpyDeviceToHost, s), "copy count");
+                ck(cudaStreamSynchronize(s), "stream sync");
+                std::memcpy(&left, h->pinned, sizeof(int));
+                if (left == 0) break;
+                const int64_t steps = std::min<int64_t>(p->check_every, p->max_iter - done);
+                for (int64_t k = 0; k < steps; ++k) {
+                    if (exec) {
+                        ck(cudaGraphLaunch(exec, s), "launch graph");
+                        add_launches(graph_kernels);
+                    } else {
+                        cycle(s);
+                    }
+                }
+                done += steps;
+            }
+        } catch (...) {
+            if (exec) cudaGraphExecDestroy(exec);
+            throw;
+        }
+        if (exec) cudaGraphExecDestroy(exec);
+        // ---- results ----
+        std::vector<long long> it(count);
+        std::vector<int> st(count);
+        std::vector<double> a(count), z(count);
+        ck(cudaMemcpyAsync(it.data(), iters, count * sizeof(long long), cudaMemcpyDeviceToHost, s), "copy results");
+        ck(cudaMemcpyAsync(st.data(), status, count * sizeof(int), cudaMemcpyDeviceToHost, s), "copy results");
+        ck(cudaMemcpyAsync(a.data(), r0, count * sizeof(double), cudaMemcpyDeviceToHost, s), "copy results");
+        ck(cudaMemcpyAsync(z.data(), rnow, count * sizeof(double), cudaMemcpyDeviceToHost, s), "copy results");
+        ck(cudaStreamSynchronize(s), "stream sync");
+        for (int q = 0; q < count; ++q) {
+            results[q].status = st[q];
+            results[q].iters = it[q];
+            results[q].r0 = a[q];
+            results[q].r_final = z[q];
+            results[q].last_check = rel ? (a[q] > 0 ? z[q] / a[q] : 0.0) : z[q];
+        }
+    });
+}
 
 // ============================== C ABI =======================================================
 

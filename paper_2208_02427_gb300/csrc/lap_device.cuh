@@ -8,12 +8,23 @@ namespace lap {
 
 // On GB300's FP64 pipe a fused multiply-add issues at ~0.60 T/s but an add or a multiply at
 // ~0.50 T/s (measured). x + y == fma(x, 1, y) and x * y == fma(x, y, -0) bit for bit, for every
-// input, so adds and multiplies are issued as fmas. The 1 and -0 arrive as kernel arguments:
-// as literals the compiler would turn the fma back into the add or multiply.
+// input, so adds and multiplies are issued as fmas. The 1 and -0 are loaded from device memory
+// (load_fma_ops): as literals the compiler would turn the fma back into the add or multiply.
 struct FmaOps {
     double one;    // 1.0
     double nzero;  // -0.0
 };
+// 1 and -0 in device memory. Kernels load them on entry: loaded values live in registers,
+// whereas kernel arguments are read as constant-bank operands, and an FP64 fma with a
+// constant-bank operand issues no faster than the add it replaces (measured on GB300).
+// The array is not const, so the compiler cannot fold the loads away.
+static __device__ double g_fma_consts[2] = {1.0, -0.0};
+
+__device__ __forceinline__ FmaOps load_fma_ops()
+{
+    return FmaOps{g_fma_consts[0], g_fma_consts[1]};
+}
+
 __device__ __forceinline__ double fadd(const FmaOps& o, double a, double b)
 {
     return __fma_rn(a, o.one, b);

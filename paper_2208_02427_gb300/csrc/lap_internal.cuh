@@ -38,8 +38,10 @@ void note_launch();
 // One colour of a red-black sweep, in place: Gauss-Seidel (Eq. 6) when gs is true,
 // SOR (Eq. 7) otherwise; q may be null. maxd (nullable) accumulates max|new - old| as
 // the bit pattern of a non-negative double.
+// wslot (nullable): device copy of {w, 1 - w}, read instead of the w argument (faster).
 cudaError_t launch_rb_colour(const Field& f, const double* q, const Coef& c, bool gs, double w,
-                             int colour, unsigned long long* maxd, cudaStream_t s);
+                             int colour, unsigned long long* maxd, cudaStream_t s,
+                             const double* wslot = nullptr);
 // One Jacobi sweep (Eq. 5) from in to out (same pitch; ring not touched).
 cudaError_t launch_jacobi(const Field& in, double* out, const Coef& c, unsigned long long* maxd,
                           cudaStream_t s);
@@ -93,6 +95,57 @@ size_t lex_smem_bytes(int m, int n);
 cudaError_t prepare_lex_kernels(size_t smem);
 cudaError_t launch_lex_sweeps(const Field& f, const Coef& c, bool gs, double w, int nsweeps,
                               unsigned long long* maxd, cudaStream_t s);
+
+// ---- V-cycle over many grids (batch_kernels.cu) -------------------------------------
+// One level of one problem. Level 0 of the FP64 solve is the caller's field (q null).
+template <class T>
+struct BatchLevel {
+    T* u;  // field or correction
+    T* q;  // source term (null on the FP64 fine level); FP32 level 0: the FP64 residual
+    T* r;  // residual scratch (not on the coarsest level)
+    int m, n;
+    int64_t pitch;
+    int problem;
+    int unit_beta;
+    int inv_d_shift;
+    double b2, d, inv_d;
+    const double* ainv_t;  // coarsest level: transposed inverse of its 5-point matrix
+};
+struct BatchItem {
+    int level;  // index into the level array
+    int row0;   // first interior row
+    int rows;   // rows in this item
+};
+struct BatchList {
+    const BatchItem* items;
+    int count;
+};
+template <class T>
+cudaError_t launch_b_rb(const BatchList& l, const BatchLevel<T>* lv, const int* active, int colour,
+                        bool gs, double w, cudaStream_t s);
+template <class T>
+cudaError_t launch_b_defect(const BatchList& l, const BatchLevel<T>* lv, const int* active,
+                            cudaStream_t s);
+// items of the coarse level; the fine level is the preceding entry of lv
+template <class T>
+cudaError_t launch_b_restrict(const BatchList& l, const BatchLevel<T>* lv, const int* active,
+                              cudaStream_t s);
+// items of the fine level; the coarse level is the following entry of lv
+template <class T>
+cudaError_t launch_b_prolong(const BatchList& l, const BatchLevel<T>* lv, const int* active,
+                             cudaStream_t s);
+template <class T>
+cudaError_t launch_b_coarse(const BatchList& l, const BatchLevel<T>* lv, const int* active,
+                            int max_unknowns, cudaStream_t s);
+// per-item FP64 sum of squares of the residual; with lv32 also r32 := residual, e32 := 0
+cudaError_t launch_b_sumsq(const BatchList& l, const BatchLevel<double>* lv, const int* active,
+                           double* partials, const BatchLevel<float>* lv32, cudaStream_t s);
+cudaError_t launch_b_update(const BatchList& l, const BatchLevel<double>* lv, const int* active,
+                            const BatchLevel<float>* lv32, cudaStream_t s);
+// mode 0: record r0 (retire problems already converged); mode 1: count a cycle and test
+cudaError_t launch_b_converge(const double* partials, const int* first_item, int count, int* active,
+                              double* r0, double* rnow, long long* iters, int* status,
+                              int* remaining, int mode, bool rel, double tol, cudaStream_t s);
 
 // ---- line relaxation (line_kernels.cu) --------------------------------------------
 // Constant-coefficient tridiagonal systems -alpha x_{k-1} + delta x_k - alpha x_{k+1} = r_k,

@@ -19,8 +19,9 @@ template <bool UNIT_BETA, bool POW2, bool GS>
 __global__ void __launch_bounds__(LEX_THREADS)
     lex_sweeps_kernel(double* __restrict__ psi, int m, int n, int64_t pitch, int nsweeps,
                       double b2, double inv_d, int shift, double w, double one_minus_w,
-                      unsigned long long* __restrict__ maxd, const FmaOps o)
+                      unsigned long long* __restrict__ maxd)
 {
+    const FmaOps o = load_fma_ops();
     extern __shared__ double u[];  // dense m x n copy
     const int tid = threadIdx.x;
     for (int k = tid; k < m * n; k += blockDim.x) u[k] = psi[(int64_t)(k / m) * pitch + k % m];
@@ -97,7 +98,7 @@ cudaError_t launch_lex_sweeps(const Field& f, const Coef& c, bool gs, double w, 
         auto kern = lex_sweeps_kernel<UB, P2, G>;                                                 \
         if (err == cudaSuccess)                                                                   \
             kern<<<1, LEX_THREADS, smem, s>>>(f.p, f.m, f.n, f.pitch, nsweeps, c.b2, c.inv_d,       \
-                                              c.inv_d_shift, w, omw, maxd, FmaOps{1.0, -0.0});    \
+                                              c.inv_d_shift, w, omw, maxd);    \
     } while (0)
     const bool p2 = c.inv_d_shift > 0;
     if (c.unit_beta) {

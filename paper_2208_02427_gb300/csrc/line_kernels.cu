@@ -26,9 +26,9 @@ namespace {
 template <int FORM, bool UNIT_CROSS>
 __global__ void __launch_bounds__(256)
     line_colour_kernel(double* __restrict__ psi, int64_t sa, int64_t sx, int first_line,
-                       const LineTables t, double cross, double w, double dmw, double wcross,
-                       const FmaOps o)
+                       const LineTables t, double cross, double w, double dmw, double wcross)
 {
+    const FmaOps o = load_fma_ops();
     extern __shared__ double sm[];
     const int N = t.N, L = t.L, P = t.P, S = P - 1, Ls = t.stride;
     double* lane = sm;              // chunk p occupies lane[p*Ls .. p*Ls + L]; slot L = separator
@@ -173,8 +173,7 @@ cudaError_t launch_line_colour(double* psi, int64_t sa, int64_t sx, int first_li
         auto kern = line_colour_kernel<F, U>;                                                   \
         err = prepare_line_kernels(smem);                                                       \
         if (err == cudaSuccess)                                                                 \
-            kern<<<count, threads, smem, s>>>(psi, sa, sx, first_line, t, cross, w, dmw, wcross, \
-                                              FmaOps{1.0, -0.0});                                \
+            kern<<<count, threads, smem, s>>>(psi, sa, sx, first_line, t, cross, w, dmw, wcross); \
     } while (0)
     if (form == 0) {
         if (unit) LAP_LINE(0, true); else LAP_LINE(0, false);

@@ -19,8 +19,9 @@ constexpr int MG_BX = 64, MG_BY = 4;
 // reproduce the two rounded additions of the written expression.
 __global__ void __launch_bounds__(MG_BX* MG_BY)
     restrict_kernel(const double* __restrict__ r, int mf, int nf, int64_t pf,
-                    double* __restrict__ qc, double* __restrict__ ec, int64_t pc, const FmaOps o)
+                    double* __restrict__ qc, double* __restrict__ ec, int64_t pc)
 {
+    const FmaOps o = load_fma_ops();
     const int mc = (mf - 1) / 2 + 1, nc = (nf - 1) / 2 + 1;
     const int I = 1 + blockIdx.x * MG_BX + threadIdx.x;
     const int J = 1 + blockIdx.y * MG_BY + threadIdx.y;
@@ -41,8 +42,9 @@ __global__ void __launch_bounds__(MG_BX* MG_BY)
 // (pairs along x first).
 __global__ void __launch_bounds__(MG_BX* MG_BY)
     prolong_add_kernel(double* __restrict__ u, int mf, int nf, int64_t pf,
-                       const double* __restrict__ ec, int64_t pc, const FmaOps o)
+                       const double* __restrict__ ec, int64_t pc)
 {
+    const FmaOps o = load_fma_ops();
     const int I = blockIdx.x * MG_BX + threadIdx.x;  // coarse column 0 .. mc-2
     const int j = 1 + blockIdx.y * MG_BY + threadIdx.y;
     const int mc = (mf - 1) / 2 + 1;
@@ -99,7 +101,7 @@ cudaError_t launch_restrict(const Field& fine_r, double* qc, double* ec, int64_t
     const int mc = (fine_r.m - 1) / 2 + 1, nc = (fine_r.n - 1) / 2 + 1;
     const dim3 grid((mc - 2 + MG_BX - 1) / MG_BX, (nc - 2 + MG_BY - 1) / MG_BY);
     restrict_kernel<<<grid, dim3(MG_BX, MG_BY), 0, s>>>(fine_r.p, fine_r.m, fine_r.n, fine_r.pitch,
-                                                         qc, ec, pitch_c, FmaOps{1.0, -0.0});
+                                                         qc, ec, pitch_c);
     note_launch();
     return cudaGetLastError();
 }
@@ -110,8 +112,7 @@ cudaError_t launch_prolong_add(const Field& fine_u, const double* ec, int64_t pi
     const int mc = (fine_u.m - 1) / 2 + 1;
     const dim3 grid((mc - 1 + MG_BX - 1) / MG_BX, (fine_u.n - 2 + MG_BY - 1) / MG_BY);
     prolong_add_kernel<<<grid, dim3(MG_BX, MG_BY), 0, s>>>(fine_u.p, fine_u.m, fine_u.n,
-                                                            fine_u.pitch, ec, pitch_c,
-                                                            FmaOps{1.0, -0.0});
+                                                            fine_u.pitch, ec, pitch_c);
     note_launch();
     return cudaGetLastError();
 }

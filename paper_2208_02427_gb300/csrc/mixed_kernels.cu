@@ -131,8 +131,9 @@ template <bool UNIT>
 __global__ void __launch_bounds__(NORM_THREADS)
     defect64_to32_kernel(const double* __restrict__ psi, int m, int n, int64_t pitch, double b2,
                          double d, float* __restrict__ r32, float* __restrict__ e32,
-                         int64_t pitch32, double* __restrict__ partials, const FmaOps o)
+                         int64_t pitch32, double* __restrict__ partials)
 {
+    const FmaOps o = load_fma_ops();
     double acc = 0.0;
     for (int j = 1 + blockIdx.x; j <= n - 2; j += gridDim.x)
         for (int i = 1 + threadIdx.x; i <= m - 2; i += NORM_THREADS) {
@@ -157,8 +158,9 @@ __global__ void __launch_bounds__(NORM_THREADS)
 
 __global__ void __launch_bounds__(PX* PY)
     update64_kernel(double* __restrict__ psi, int m, int n, int64_t pitch,
-                    const float* __restrict__ e32, int64_t pitch32, const FmaOps o)
+                    const float* __restrict__ e32, int64_t pitch32)
 {
+    const FmaOps o = load_fma_ops();
     const int j = 1 + blockIdx.y * PY + threadIdx.y;
     const int i = 1 + blockIdx.x * PX + threadIdx.x;
     if (j > n - 2 || i > m - 2) return;
@@ -236,9 +238,9 @@ cudaError_t launch_defect64_to32(const Field& psi, const Coef& c, float* r32, fl
 {
     const int blocks = mixed_norm_blocks(psi.n);
     if (c.unit_beta)
-        defect64_to32_kernel<true><<<blocks, NORM_THREADS, 0, s>>>(psi.p, psi.m, psi.n, psi.pitch, c.b2, c.d, r32, e32, pitch32, partials, FmaOps{1.0, -0.0});
+        defect64_to32_kernel<true><<<blocks, NORM_THREADS, 0, s>>>(psi.p, psi.m, psi.n, psi.pitch, c.b2, c.d, r32, e32, pitch32, partials);
     else
-        defect64_to32_kernel<false><<<blocks, NORM_THREADS, 0, s>>>(psi.p, psi.m, psi.n, psi.pitch, c.b2, c.d, r32, e32, pitch32, partials, FmaOps{1.0, -0.0});
+        defect64_to32_kernel<false><<<blocks, NORM_THREADS, 0, s>>>(psi.p, psi.m, psi.n, psi.pitch, c.b2, c.d, r32, e32, pitch32, partials);
     note_launch();
     return cudaGetLastError();
 }
@@ -246,8 +248,7 @@ cudaError_t launch_defect64_to32(const Field& psi, const Coef& c, float* r32, fl
 cudaError_t launch_update64(const Field& psi, const float* e32, int64_t pitch32, cudaStream_t s)
 {
     const dim3 grid((psi.m - 2 + PX - 1) / PX, (psi.n - 2 + PY - 1) / PY), block(PX, PY);
-    update64_kernel<<<grid, block, 0, s>>>(psi.p, psi.m, psi.n, psi.pitch, e32, pitch32,
-                                           FmaOps{1.0, -0.0});
+    update64_kernel<<<grid, block, 0, s>>>(psi.p, psi.m, psi.n, psi.pitch, e32, pitch32);
     note_launch();
     return cudaGetLastError();
 }

@@ -21,7 +21,6 @@ constexpr int RB_BX = 64, RB_BY = 4;   // red-black: 64 same-colour points x 4 r
 constexpr int JA_BX = 128, JA_BY = 2;  // Jacobi: 128 points x 2 rows
 constexpr int NORM_THREADS = 256;
 constexpr int NORM_MAX_BLOCKS = 1216;  // 8 per SM on 152 SMs
-const FmaOps kOps{1.0, -0.0};
 
 __device__ __forceinline__ void flush_maxd(unsigned long long v, unsigned long long* maxd)
 {
@@ -35,8 +34,14 @@ template <bool UNIT_BETA, bool POW2, bool HAS_Q, bool GS, bool MAXD>
 __global__ void __launch_bounds__(RB_BX* RB_BY)
     rb_colour_kernel(double* __restrict__ psi, const double* __restrict__ q, int m, int n,
                      int64_t pitch, int colour, double b2, double inv_d, int shift, double w,
-                     double one_minus_w, unsigned long long* __restrict__ maxd, const FmaOps o)
+                     double one_minus_w, unsigned long long* __restrict__ maxd,
+                     const double* __restrict__ wslot)
 {
+    const FmaOps o = load_fma_ops();
+    if (!GS && wslot) {  // w and 1 - w from device memory: register operands for the blend
+        w = wslot[0];
+        one_minus_w = wslot[1];
+    }
     const int j = 1 + blockIdx.y * RB_BY + threadIdx.y;
     const int i = 1 + ((1 + j + colour) & 1) + 2 * (blockIdx.x * RB_BX + threadIdx.x);
     unsigned long long dl = 0;
@@ -58,8 +63,9 @@ template <bool UNIT_BETA, bool POW2, bool MAXD>
 __global__ void __launch_bounds__(JA_BX* JA_BY)
     jacobi_kernel(const double* __restrict__ in, double* __restrict__ out, int m, int n,
                   int64_t pitch, double b2, double inv_d, int shift,
-                  unsigned long long* __restrict__ maxd, const FmaOps o)
+                  unsigned long long* __restrict__ maxd)
 {
+    const FmaOps o = load_fma_ops();
     const int j = 1 + blockIdx.y * JA_BY + threadIdx.y;
     const int i = 1 + blockIdx.x * JA_BX + threadIdx.x;
     unsigned long long dl = 0;
@@ -88,9 +94,9 @@ __device__ __forceinline__ double defect_at(const FmaOps& o, const double* __res
 template <bool UNIT_BETA, bool HAS_Q>
 __global__ void __launch_bounds__(JA_BX* JA_BY)
     defect_kernel(const double* __restrict__ u, const double* __restrict__ q,
-                  double* __restrict__ r, int m, int n, int64_t pitch, double b2, double d,
-                  const FmaOps o)
+                  double* __restrict__ r, int m, int n, int64_t pitch, double b2, double d)
 {
+    const FmaOps o = load_fma_ops();
     const int j = 1 + blockIdx.y * JA_BY + threadIdx.y;
     const int i = 1 + blockIdx.x * JA_BX + threadIdx.x;
     if (j <= n - 2 && i <= m - 2) {
@@ -104,9 +110,9 @@ __global__ void __launch_bounds__(JA_BX* JA_BY)
 template <bool UNIT_BETA, bool HAS_Q>
 __global__ void __launch_bounds__(NORM_THREADS)
     defect_sumsq_kernel(const double* __restrict__ u, const double* __restrict__ q, int m, int n,
-                        int64_t pitch, double b2, double d, double* __restrict__ partials,
-                        const FmaOps o)
+                        int64_t pitch, double b2, double d, double* __restrict__ partials)
 {
+    const FmaOps o = load_fma_ops();
     double acc = 0.0;
     for (int j = 1 + blockIdx.x; j <= n - 2; j += gridDim.x)
         for (int i = 1 + threadIdx.x; i <= m - 2; i += NORM_THREADS) {
@@ -146,8 +152,9 @@ __global__ void __launch_bounds__(NORM_THREADS)
 
 __global__ void __launch_bounds__(JA_BX* JA_BY)
     maxdelta_kernel(const double* __restrict__ a, const double* __restrict__ b, int m, int n,
-                    int64_t pitch, unsigned long long* __restrict__ maxd, const FmaOps o)
+                    int64_t pitch, unsigned long long* __restrict__ maxd)
 {
+    const FmaOps o = load_fma_ops();
     const int j = 1 + blockIdx.y * JA_BY + threadIdx.y;
     const int i = 1 + blockIdx.x * JA_BX + threadIdx.x;
     unsigned long long dl = 0;
@@ -183,7 +190,8 @@ dim3 point_grid(int m, int n)
     } while (0)
 
 cudaError_t launch_rb_colour(const Field& f, const double* q, const Coef& c, bool gs, double w,
-                             int colour, unsigned long long* maxd, cudaStream_t s)
+                             int colour, unsigned long long* maxd, cudaStream_t s,
+                             const double* wslot)
 {
     const dim3 grid = rb_grid(f.m, f.n), block(RB_BX, RB_BY);
     const double omw = 1.0 - w;
@@ -191,7 +199,7 @@ cudaError_t launch_rb_colour(const Field& f, const double* q, const Coef& c, boo
         LAP_DISPATCH_BOOL(q != nullptr, HQ, LAP_DISPATCH_BOOL(gs, GS, LAP_DISPATCH_BOOL(maxd != nullptr, MD,
             rb_colour_kernel<UB, P2, HQ, GS, MD><<<grid, block, 0, s>>>(
                 f.p, q, f.m, f.n, f.pitch, colour, c.b2, c.inv_d, c.inv_d_shift, w, omw, maxd,
-                kOps))))));
+                wslot))))));
     note_launch();
     return cudaGetLastError();
 }
@@ -203,7 +211,7 @@ cudaError_t launch_jacobi(const Field& in, double* out, const Coef& c, unsigned 
     LAP_DISPATCH_BOOL(c.unit_beta, UB, LAP_DISPATCH_BOOL(c.inv_d_shift > 0, P2,
         LAP_DISPATCH_BOOL(maxd != nullptr, MD,
             jacobi_kernel<UB, P2, MD><<<grid, block, 0, s>>>(in.p, out, in.m, in.n, in.pitch, c.b2,
-                                                             c.inv_d, c.inv_d_shift, maxd, kOps))));
+                                                             c.inv_d, c.inv_d_shift, maxd))));
     note_launch();
     return cudaGetLastError();
 }
@@ -213,7 +221,7 @@ cudaError_t launch_defect(const Field& f, const double* q, double* r, const Coef
 {
     const dim3 grid = point_grid(f.m, f.n), block(JA_BX, JA_BY);
     LAP_DISPATCH_BOOL(c.unit_beta, UB, LAP_DISPATCH_BOOL(q != nullptr, HQ,
-        defect_kernel<UB, HQ><<<grid, block, 0, s>>>(f.p, q, r, f.m, f.n, f.pitch, c.b2, c.d, kOps)));
+        defect_kernel<UB, HQ><<<grid, block, 0, s>>>(f.p, q, r, f.m, f.n, f.pitch, c.b2, c.d)));
     note_launch();
     return cudaGetLastError();
 }
@@ -230,7 +238,7 @@ cudaError_t launch_defect_sumsq(const Field& f, const double* q, const Coef& c, 
     const int blocks = norm_blocks(f);
     LAP_DISPATCH_BOOL(c.unit_beta, UB, LAP_DISPATCH_BOOL(q != nullptr, HQ,
         defect_sumsq_kernel<UB, HQ><<<blocks, NORM_THREADS, 0, s>>>(f.p, q, f.m, f.n, f.pitch, c.b2,
-                                                                    c.d, partials, kOps)));
+                                                                    c.d, partials)));
     note_launch();
     return cudaGetLastError();
 }
@@ -246,7 +254,7 @@ cudaError_t launch_maxdelta(const Field& a, const double* b, unsigned long long*
                             cudaStream_t s)
 {
     maxdelta_kernel<<<point_grid(a.m, a.n), dim3(JA_BX, JA_BY), 0, s>>>(a.p, b, a.m, a.n, a.pitch,
-                                                                         maxd, kOps);
+                                                                         maxd);
     note_launch();
     return cudaGetLastError();
 }

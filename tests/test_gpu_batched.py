@@ -1,0 +1,80 @@
+"""Batched V-cycles over many grids of different sizes: each problem's result must be
+exactly (bitwise, same cycle count) what its own single-grid solve gives, for the FP64
+and the mixed-precision solver, and the FP64 results must match the oracle."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as ora
+from paper_2208_02427_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+SHAPES = [(33, 33), (65, 129), (129, 65), (257, 257), (33, 65), (24, 17), (3, 3), (9, 9),
+          (513, 129), (129, 33)]
+
+
+@pytest.fixture(scope="module")
+def b():
+    from paper_2208_02427_gb300 import binding
+    binding.load()
+    return binding
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy().copy()
+
+
+@pytest.mark.parametrize("method", ["mg", "mg_mixed"])
+def test_batched_equals_single_grid_solves(b, method):
+    lap = b.Laplace()
+    inputs = [wl.random_ring(m, n, seed=100 + k) for k, (m, n) in enumerate(SHAPES)]
+    dxs = [1.0 if k % 3 else 0.8 for k in range(len(SHAPES))]
+    fields = [b.to_field(x) for x in inputs]
+    res = lap.solve_batched(fields, dxs, 1.0, method=method, tol=1e-10, max_iter=40)
+    for k, (x, f, r) in enumerate(zip(inputs, fields, res)):
+        single = b.to_field(x)
+        g = lap.solve(single, dxs[k], 1.0, method=method, tol=1e-10, max_iter=40)
+        assert r["status"] == g["status"] == "converged", (k, r, g)
+        assert r["iters"] == g["iters"], (k, r, g)
+        assert np.array_equal(host(f), host(single)), k
+        assert abs(r["r0"] - g["r0"]) <= 1e-13 * g["r0"]
+    lap.close()
+
+
+def test_batched_fp64_matches_oracle(b):
+    lap = b.Laplace()
+    inputs = [wl.sine_edges(m, n, seed=7 + k) for k, (m, n) in enumerate([(65, 33), (33, 129), (129, 129)])]
+    fields = [b.to_field(x) for x in inputs]
+    res = lap.solve_batched(fields, 1.0, 1.0, method="mg", tol=0.0, max_iter=3)
+    for x, f, r in zip(inputs, fields, res):
+        want, o = ora.solve(x, method=ora.MG, ordering=ora.RB, tol=0.0, max_iter=3)
+        assert r["iters"] == 3 and r["status"] == "max_iter"
+        got = host(f)
+        assert np.max(np.abs(got - want)) / np.max(np.abs(want)) <= 1e-12
+    lap.close()
+
+
+def test_batched_workload_converges(b):
+    lap = b.Laplace()
+    shapes = wl.batch_shapes(256, seed=wl.SEED_BASE + 2)
+    fields = [b.to_field(wl.random_ring(m, n, seed=wl.SEED_BASE + 2 + 10 * k))
+              for k, (m, n) in enumerate(shapes)]
+    for method in ("mg", "mg_mixed"):
+        work = [f.clone() for f in fields]
+        res = lap.solve_batched(work, 1.0, 1.0, method=method, tol=1e-10, max_iter=60)
+        assert all(r["status"] == "converged" for r in res)
+        assert all(r["r_final"] <= 1e-10 * r["r0"] * (1 + 1e-12) for r in res)
+        assert max(r["iters"] for r in res) <= 15
+    lap.close()
+
+
+def test_batched_rejects_bad_requests(b):
+    lap = b.Laplace()
+    f = b.field(33, 33)
+    with pytest.raises(b.LapError):
+        lap.solve_batched([f], method="sor")
+    with pytest.raises(b.LapError):
+        lap.solve_batched([f], method="mg", norm="maxdelta")
+    lap.close()
