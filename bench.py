@@ -410,6 +410,67 @@ def main():
 
     batched = batched_workload()
 
+    # ---- serving: Poisson arrivals, continuous batching under a 40 GB budget ---------------
+    def serving_workload(seconds_per_load=3.0, burst=200):
+        import numpy as np
+        rng = np.random.default_rng(wl.SEED_BASE + 4)
+
+        def draw(count):
+            out = []
+            for _ in range(count):
+                m, n = (2 ** int(round(np.log2(v - 1))) + 1
+                        for v in np.exp(rng.uniform(np.log(33), np.log(2049), size=2)))
+                tol = float(np.exp(rng.uniform(np.log(1e-10), np.log(1e-6))))
+                method = "mg_mixed" if rng.uniform() < 0.5 else "sor"
+                out.append((m, n, tol, method, int(rng.integers(1 << 30))))
+            return out
+
+        def run(reqs, rate):
+            srv = b.Server(lap, hbm_budget=40 << 30, max_running=512, sor_sweeps=50)
+            fields = [b.to_field(wl.random_ring(m, n, seed), dev) for m, n, _, _, seed in reqs]
+            arrivals = np.cumsum(rng.exponential(1.0 / rate, size=len(reqs))) if rate else np.zeros(len(reqs))
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            ids, lat, nxt = {}, [], 0
+            while len(lat) < len(reqs):
+                now = time.perf_counter() - t0
+                while nxt < len(reqs) and arrivals[nxt] <= now:
+                    m, n, tol, method, _ = reqs[nxt]
+                    w = wl.w_opt_sor(m, n) if method == "sor" else 1.0
+                    ids[srv.submit(fields[nxt], 1.0, 1.0, method=method, w=w, tol=tol,
+                                   max_iter=10 ** 6)] = arrivals[nxt]
+                    nxt += 1
+                if not ids:
+                    time.sleep(max(0.0, min(arrivals[nxt] - now, 0.01)))
+                    continue
+                srv.step(stream)
+                done = time.perf_counter() - t0
+                for rid in list(ids):
+                    res = srv.poll(rid)
+                    if res is not None:
+                        if res["status"] != "converged":
+                            raise RuntimeError(f"served request did not converge: {res}")
+                        lat.append(done - ids.pop(rid))
+            total = time.perf_counter() - t0
+            srv.close()
+            lat.sort()
+            return {"requests": len(reqs), "seconds": total, "solves_per_s": len(reqs) / total,
+                    "p50_ms": 1e3 * lat[len(lat) // 2],
+                    "p99_ms": 1e3 * lat[min(len(lat) - 1, int(0.99 * len(lat)))]}
+
+        sat = run(draw(burst), 0.0)
+        out = {"workload": "m, n log-uniform in [33, 2049] snapped to 2^k+1; tol log-uniform in "
+                           "[1e-10, 1e-6]; 50% mixed-precision V(2,2) / 50% RB-SOR(w_opt, 50 sweeps "
+                           "per step); ring U[0,1]; 40 GB budget; host-side latency arrival -> result",
+               "saturation": sat, "loads": {}}
+        for load in (0.1, 0.3, 0.5, 0.7, 0.9, 1.2):
+            rate = load * sat["solves_per_s"]
+            count = max(20, int(rate * seconds_per_load))
+            out["loads"][f"{load:.1f}"] = run(draw(count), rate)
+        return out
+
+    serving = serving_workload()
+
     # ---- end to end through the public API with host buffers -----------------------------
     pinned = torch.from_numpy(psi_host.copy()).pin_memory()
     out_host = torch.empty_like(pinned).pin_memory()
@@ -451,7 +512,8 @@ def main():
                     for k in ("sor", "mg")},
         "roofline": roofline, "kernels": kernels, "latency": latency,
         "cpu_baseline": {k: v for k, v in cpu.items() if k != "seconds_per_solve_pair"},
-        "mixed_precision": mixed, "batched": batched, "e2e": e2e, "gpu_launches": launches,
+        "mixed_precision": mixed, "batched": batched, "serving": serving, "e2e": e2e,
+        "gpu_launches": launches,
         "clocks": clk,
     }
     print(json.dumps(line), flush=True)

@@ -145,6 +145,34 @@ int lap_solve(lap_handle h, const lap_grid* g, double* psi_dev, const lap_params
 int lap_solve_batched(lap_handle h, int count, const lap_grid* grids, double* const* psi_devs,
                       const lap_params* p, lap_result* results, void* stream);
 
+/* ---- serving: continuous batching over a stream of solve requests ----
+ * A server owns a device pool of hbm_budget_bytes for the grid hierarchies of the requests it
+ * runs (the fields themselves stay the caller's). lap_server_submit queues a request;
+ * every lap_server_step admits queued requests first-in first-out while a running slot is
+ * free (max_running) and the request's hierarchy fits the pool, then runs ONE iteration of
+ * every running request as batched launches shared by all of them -- a V-cycle (p->nu1,
+ * nu2, coarsest_min, max_levels, smoother_w, inner_cycles) for LAP_MG / LAP_MG_MIXED
+ * requests, sor_sweeps red-black sweeps with the request's own w for LAP_SOR_RB -- and
+ * tests each request's own stopping rule (L2 residual relative to its initial one <= its
+ * tol) on the device. Finished requests leave and free their memory; requests that arrive
+ * meanwhile join at the next step. Per request the arithmetic is that of lap_solve (SOR
+ * with check_every = sor_sweeps), so results do not depend on what else is running.
+ * lap_server_step synchronises `stream`; the caller must not touch a request's field
+ * until lap_server_poll has returned 1 for it. A server is not thread-safe. */
+typedef struct lap_server_s* lap_server;
+int lap_server_create(lap_server* out, lap_handle h, size_t hbm_budget_bytes, const lap_params* p,
+                      int max_running, int sor_sweeps);
+void lap_server_destroy(lap_server s);
+/* method: LAP_MG, LAP_MG_MIXED or LAP_SOR_RB; max_iter counts V-cycles, or sweeps for SOR.
+ * LAP_ENOMEM if the request's hierarchy exceeds the whole pool. *id identifies it. */
+int lap_server_submit(lap_server s, const lap_grid* g, double* psi_dev, int method, double w,
+                      double tol, int64_t max_iter, int64_t* id);
+/* *running / *queued (nullable): requests still running after the step / still queued. */
+int lap_server_step(lap_server s, void* stream, int* running, int* queued);
+/* 1 and *out filled if request id has finished (the request is then forgotten), 0 if not,
+ * LAP_EINVAL for an unknown id. */
+int lap_server_poll(lap_server s, int64_t id, lap_result* out);
+
 /* ||r||_2 over interior nodes of the scaled residual of Eqs. 11-12,
  * r = fma(-d, psi, fma(beta^2, N + S, E + W) [+ q]), written to *out (host).
  * q_dev may be NULL (Laplace) or a field with the same pitch (coarse-level source). */

@@ -90,6 +90,12 @@ def load():
             "lap_line_sweep": (C.c_int, [c_void_p, G, c_void_p, c_double, C.c_int, C.c_int, c_void_p]),
             "lap_set_graphs": (C.c_int, [c_void_p, C.c_int]),
             "lap_solve_batched": (C.c_int, [c_void_p, C.c_int, G, C.POINTER(c_void_p), P, R, c_void_p]),
+            "lap_server_create": (C.c_int, [C.POINTER(c_void_p), c_void_p, C.c_size_t, P, C.c_int, C.c_int]),
+            "lap_server_destroy": (None, [c_void_p]),
+            "lap_server_submit": (C.c_int, [c_void_p, G, c_void_p, C.c_int, c_double, c_double, c_int64,
+                                            C.POINTER(c_int64)]),
+            "lap_server_step": (C.c_int, [c_void_p, c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+            "lap_server_poll": (C.c_int, [c_void_p, c_int64, R]),
             "lap_strerror": (C.c_char_p, [C.c_int]),
             "lap_last_error": (C.c_char_p, []),
             "lap_kernel_launches": (c_int64, []),
@@ -281,3 +287,60 @@ def prolong_add(u, ec, dx=1.0, dy=1.0, stream=None):
         raise TypeError("ec must be a coarse field of shape ((n-1)/2+1, (m-1)/2+1)")
     _check(load().lap_prolong_add(C.byref(_grid(u, dx, dy)), _ptr(u), _ptr(ec), ec.stride(0),
                                   _stream(stream, u.device)))
+
+
+class Server:
+    """Continuous-batching solve server on one Laplace handle (see lap_server_* in laplace.h).
+
+    submit() queues a request on a caller-owned device field (kept referenced here until its
+    result is polled); step() admits what fits the HBM budget and runs one iteration of every
+    running request in shared launches; poll() returns the result dict once finished."""
+
+    def __init__(self, lap: Laplace, hbm_budget: int, max_running: int = 1024, sor_sweeps: int = 50,
+                 **mg_kw):
+        self._lap = lap
+        self._lib = lap._lib
+        h = c_void_p()
+        _check(self._lib.lap_server_create(C.byref(h), lap._h, int(hbm_budget),
+                                           C.byref(params(method="mg", **mg_kw)), int(max_running),
+                                           int(sor_sweeps)))
+        self._h = h
+        self._fields = {}
+
+    def submit(self, psi, dx=1.0, dy=1.0, method="mg_mixed", w=1.0, tol=1e-10,
+               max_iter=100000) -> int:
+        rid = c_int64(0)
+        _check(self._lib.lap_server_submit(self._h, C.byref(_grid(psi, dx, dy)), _ptr(psi),
+                                           METHODS[method], float(w), float(tol), int(max_iter),
+                                           C.byref(rid)))
+        self._fields[rid.value] = psi
+        return rid.value
+
+    def step(self, stream=None):
+        running, queued = C.c_int(0), C.c_int(0)
+        _check(self._lib.lap_server_step(self._h, _stream(stream, self._lap.device),
+                                         C.byref(running), C.byref(queued)))
+        return running.value, queued.value
+
+    def poll(self, rid: int):
+        res = Result()
+        rc = self._lib.lap_server_poll(self._h, int(rid), C.byref(res))
+        if rc < 0:
+            _check(rc)
+        if rc == 0:
+            return None
+        self._fields.pop(rid, None)
+        return {"status": STATUS.get(res.status, res.status), "iters": res.iters, "r0": res.r0,
+                "r_final": res.r_final, "last_check": res.last_check}
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.lap_server_destroy(self._h)
+            self._h = None
+            self._fields.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -66,12 +66,16 @@ __device__ __forceinline__ Arith<float> arith<float>() { return Arith<float>{}; 
 template <class T>
 __global__ void __launch_bounds__(BT)
     b_rb_kernel(const BatchItem* __restrict__ items, const BatchLevel<T>* __restrict__ lv,
-                const int* __restrict__ active, int colour, int gs, T w, T omw)
+                const int* __restrict__ active, int colour, int gs, T w, T omw, int per_level_w)
 {
     const BatchItem it = items[blockIdx.x];
     const BatchLevel<T> L = lv[it.level];
     if (!active[L.problem]) return;
     const Arith<T> A = arith<T>();
+    if (per_level_w) {
+        w = (T)L.w;
+        omw = (T)L.omw;
+    }
     const int half_w = (L.m - 2 + 1) / 2;
     for (int k = threadIdx.x; k < it.rows * half_w; k += BT) {
         const int j = it.row0 + k / half_w;
@@ -209,7 +213,7 @@ __global__ void __launch_bounds__(BT)
     float* r32 = nullptr;
     float* e32 = nullptr;
     int64_t p32 = 0;
-    if (lv32) {
+    if (lv32 && lv32[it.level].q) {  // problems solved by the FP32 inner cycle
         r32 = lv32[it.level].q;
         e32 = lv32[it.level].u;
         p32 = lv32[it.level].pitch;
@@ -263,10 +267,12 @@ __global__ void b_converge_kernel(const double* __restrict__ partials,
                                   int* __restrict__ active, double* __restrict__ r0,
                                   double* __restrict__ rnow, long long* __restrict__ iters,
                                   int* __restrict__ status, int* __restrict__ remaining, int mode,
-                                  int rel, double tol)
+                                  int rel, double tol, const double* __restrict__ tolv)
 {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= count || !active[p]) return;
+    if (first_item[p] == first_item[p + 1]) return;  // not in this list
+    if (tolv) tol = tolv[p];
     double s = 0.0;
     for (int k = first_item[p]; k < first_item[p + 1]; ++k) s = __dadd_rn(s, partials[k]);
     const double nr = sqrt(s);
@@ -295,10 +301,11 @@ __global__ void b_converge_kernel(const double* __restrict__ partials,
 
 template <class T>
 cudaError_t launch_b_rb(const BatchList& l, const BatchLevel<T>* lv, const int* active, int colour,
-                        bool gs, double w, cudaStream_t s)
+                        bool gs, double w, cudaStream_t s, bool per_level_w)
 {
     if (l.count == 0) return cudaSuccess;
-    b_rb_kernel<T><<<l.count, BT, 0, s>>>(l.items, lv, active, colour, gs ? 1 : 0, (T)w, (T)(1.0 - w));
+    b_rb_kernel<T><<<l.count, BT, 0, s>>>(l.items, lv, active, colour, gs ? 1 : 0, (T)w, (T)(1.0 - w),
+                                          per_level_w ? 1 : 0);
     note_launch();
     return cudaGetLastError();
 }
@@ -341,8 +348,8 @@ cudaError_t launch_b_coarse(const BatchList& l, const BatchLevel<T>* lv, const i
     return cudaGetLastError();
 }
 
-template cudaError_t launch_b_rb<double>(const BatchList&, const BatchLevel<double>*, const int*, int, bool, double, cudaStream_t);
-template cudaError_t launch_b_rb<float>(const BatchList&, const BatchLevel<float>*, const int*, int, bool, double, cudaStream_t);
+template cudaError_t launch_b_rb<double>(const BatchList&, const BatchLevel<double>*, const int*, int, bool, double, cudaStream_t, bool);
+template cudaError_t launch_b_rb<float>(const BatchList&, const BatchLevel<float>*, const int*, int, bool, double, cudaStream_t, bool);
 template cudaError_t launch_b_defect<double>(const BatchList&, const BatchLevel<double>*, const int*, cudaStream_t);
 template cudaError_t launch_b_defect<float>(const BatchList&, const BatchLevel<float>*, const int*, cudaStream_t);
 template cudaError_t launch_b_restrict<double>(const BatchList&, const BatchLevel<double>*, const int*, cudaStream_t);
@@ -372,11 +379,12 @@ cudaError_t launch_b_update(const BatchList& l, const BatchLevel<double>* lv, co
 
 cudaError_t launch_b_converge(const double* partials, const int* first_item, int count, int* active,
                               double* r0, double* rnow, long long* iters, int* status,
-                              int* remaining, int mode, bool rel, double tol, cudaStream_t s)
+                              int* remaining, int mode, bool rel, double tol, cudaStream_t s,
+                              const double* tolv)
 {
     b_converge_kernel<<<(count + 127) / 128, 128, 0, s>>>(partials, first_item, count, active, r0,
                                                           rnow, iters, status, remaining, mode,
-                                                          rel ? 1 : 0, tol);
+                                                          rel ? 1 : 0, tol, tolv);
     note_launch();
     return cudaGetLastError();
 }

@@ -109,6 +109,7 @@ struct BatchLevel {
     int unit_beta;
     int inv_d_shift;
     double b2, d, inv_d;
+    double w, omw;         // per-problem SOR factor and 1 - w (batched point sweeps)
     const double* ainv_t;  // coarsest level: transposed inverse of its 5-point matrix
 };
 struct BatchItem {
@@ -120,9 +121,10 @@ struct BatchList {
     const BatchItem* items;
     int count;
 };
+// per_level_w: Eq. 7 with each level's own w (BatchLevel::w) instead of the argument
 template <class T>
 cudaError_t launch_b_rb(const BatchList& l, const BatchLevel<T>* lv, const int* active, int colour,
-                        bool gs, double w, cudaStream_t s);
+                        bool gs, double w, cudaStream_t s, bool per_level_w = false);
 template <class T>
 cudaError_t launch_b_defect(const BatchList& l, const BatchLevel<T>* lv, const int* active,
                             cudaStream_t s);
@@ -142,10 +144,12 @@ cudaError_t launch_b_sumsq(const BatchList& l, const BatchLevel<double>* lv, con
                            double* partials, const BatchLevel<float>* lv32, cudaStream_t s);
 cudaError_t launch_b_update(const BatchList& l, const BatchLevel<double>* lv, const int* active,
                             const BatchLevel<float>* lv32, cudaStream_t s);
-// mode 0: record r0 (retire problems already converged); mode 1: count a cycle and test
+// mode 0: record r0 (retire problems already converged); mode 1: count a cycle and test.
+// Problems with no items in the list are left alone; tolv (nullable) gives one tol each.
 cudaError_t launch_b_converge(const double* partials, const int* first_item, int count, int* active,
                               double* r0, double* rnow, long long* iters, int* status,
-                              int* remaining, int mode, bool rel, double tol, cudaStream_t s);
+                              int* remaining, int mode, bool rel, double tol, cudaStream_t s,
+                              const double* tolv = nullptr);
 
 // ---- line relaxation (line_kernels.cu) --------------------------------------------
 // Constant-coefficient tridiagonal systems -alpha x_{k-1} + delta x_k - alpha x_{k+1} = r_k,
