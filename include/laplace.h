@@ -62,7 +62,11 @@ typedef enum {
                         x-line sweep per iteration, form line_form (A = SLORA, B = SLORB) */
     LAP_GS_LEX = 7,  /* Eq. 6 in the paper's lexicographic order (i-1, j-1 already new), as
                         diagonal wavefronts on one SM; m*n <= 28672 (else EUNSUPPORTED) */
-    LAP_SOR_LEX = 8  /* Eq. 7 in lexicographic order, same limits */
+    LAP_SOR_LEX = 8, /* Eq. 7 in lexicographic order, same limits */
+    LAP_MG_FP32 = 9  /* the V-cycle of LAP_MG entirely in FP32 (psi rounded to FP32 once,
+                        widened back at the end; stopping rule on the FP32 residual): the
+                        plain-FP32 comparison point of LAP_MG_MIXED, which stalls near FP32
+                        rounding (relative residual ~1e-6). Norm L2_REL or L2_ABS */
 } lap_method;
 
 typedef enum {
@@ -99,6 +103,16 @@ typedef struct {
     double smoother_w;    /* LAP_MG: smoother relaxation; 1 = Gauss-Seidel (Eq. 6) */
     int32_t line_form;    /* LAP_ADI, LAP_SLOR: lap_line_form */
     int32_t inner_cycles; /* LAP_MG_MIXED: FP32 V-cycles per FP64 correction (>= 1) */
+    int32_t tail_size;    /* LAP_MG, LAP_MG_MIXED, batched: the levels whose sides are all
+                             <= tail_size run as one single-CTA kernel per V-cycle (the
+                             small-level tail: a CTA barrier per phase instead of a launch;
+                             the same arithmetic, so the same iterates bit for bit).
+                             0 = chosen by timing the first cycles of a shape (cached in the
+                             handle), -1 = never; otherwise >= 3 */
+    int32_t unfused;      /* LAP_MG_MIXED: 0 = each FP32 level's descent (smoothing, residual,
+                             restriction) and ascent (interpolation, smoothing) run as one
+                             shared-memory tile kernel each; non-zero = one kernel per pass
+                             (the same values bit for bit; the reference for the tiles) */
 } lap_params;
 
 typedef struct {

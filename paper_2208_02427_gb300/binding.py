@@ -20,7 +20,7 @@ from . import build as _build
 
 c_int32, c_int64, c_double, c_void_p = C.c_int32, C.c_int64, C.c_double, C.c_void_p
 
-METHODS = {"jacobi": 0, "gs": 1, "sor": 2, "adi": 3, "mg": 4, "mg_mixed": 5, "slor": 6,
+METHODS = {"jacobi": 0, "gs": 1, "sor": 2, "adi": 3, "mg": 4, "mg_mixed": 5, "slor": 6, "mg_fp32": 9,
            "gs_lex": 7, "sor_lex": 8}
 NORMS = {"l2_rel": 0, "l2_abs": 1, "maxdelta": 2}
 FORMS = {"A": 0, "B": 1}
@@ -43,7 +43,8 @@ class Params(C.Structure):
     _fields_ = [("method", c_int32), ("w", c_double), ("tol", c_double), ("norm", c_int32),
                 ("max_iter", c_int64), ("check_every", c_int32), ("nu1", c_int32),
                 ("nu2", c_int32), ("coarsest_min", c_int32), ("max_levels", c_int32),
-                ("smoother_w", c_double), ("line_form", c_int32), ("inner_cycles", c_int32)]
+                ("smoother_w", c_double), ("line_form", c_int32), ("inner_cycles", c_int32),
+                ("tail_size", c_int32), ("unfused", c_int32)]
 
 
 class Result(C.Structure):
@@ -156,10 +157,11 @@ def _stream(stream, device):
 
 def params(method="sor", w=1.0, tol=1e-10, norm="l2_rel", max_iter=100000, check_every=1,
            nu1=2, nu2=2, coarsest_min=5, max_levels=0, smoother_w=1.0, line_form="A",
-           inner_cycles=1) -> Params:
+           inner_cycles=1, tail_size=0, unfused=False) -> Params:
     return Params(METHODS[method], float(w), float(tol), NORMS[norm], int(max_iter),
                   int(check_every), int(nu1), int(nu2), int(coarsest_min), int(max_levels),
-                  float(smoother_w), FORMS[line_form], int(inner_cycles))
+                  float(smoother_w), FORMS[line_form], int(inner_cycles), int(tail_size),
+                  1 if unfused else 0)
 
 
 class Laplace:

@@ -62,6 +62,91 @@ __device__ __forceinline__ Arith<double> arith<double>() { return Arith<double>{
 template <>
 __device__ __forceinline__ Arith<float> arith<float>() { return Arith<float>{}; }
 
+// The flattened index k = threadIdx.x, threadIdx.x + BT, ... of an item's rows x width points
+// as (row r, column c) pairs: one division per thread, then an add with carry per step.
+struct Walk {
+    int r, c, dr, dc, w;
+    __device__ __forceinline__ explicit Walk(int width) : w(width)
+    {
+        r = threadIdx.x / width;
+        c = threadIdx.x - r * width;
+        dr = BT / width;
+        dc = BT - dr * width;
+    }
+    __device__ __forceinline__ void next()
+    {
+        c += dc;
+        r += dr;
+        if (c >= w) {
+            c -= w;
+            ++r;
+        }
+    }
+};
+
+// ---- per-point arithmetic, shared by the item kernels and the small-level tail kernel ----
+
+// Eq. 6 (gs) or Eq. 7 at interior point (i, j) of level L, in place.
+template <class T>
+__device__ __forceinline__ void rb_point(const Arith<T>& A, const BatchLevel<T>& L, int i, int j,
+                                         bool gs, T w, T omw)
+{
+    const int64_t at = (int64_t)j * L.pitch + i;
+    T* c = L.u + at;
+    T s = A.nsum(c[-1], c[1], c[-L.pitch], c[L.pitch], (T)L.b2, L.unit_beta);
+    if (L.q) s = A.add(s, L.q[at]);
+    const T g = A.inv_d(s, L);
+    *c = gs ? g : A.fma(w, g, A.mul(omw, *c));
+}
+
+// r = (E+W) + b2 (N+S) (+ q) - d u at interior point (i, j).
+template <class T>
+__device__ __forceinline__ void defect_point(const Arith<T>& A, const BatchLevel<T>& L, int i, int j)
+{
+    const int64_t at = (int64_t)j * L.pitch + i;
+    const T* c = L.u + at;
+    T s = A.nsum(c[-1], c[1], c[-L.pitch], c[L.pitch], (T)L.b2, L.unit_beta);
+    if (L.q) s = A.add(s, L.q[at]);
+    L.r[at] = A.fma(-(T)L.d, *c, s);
+}
+
+// Coarse point (I, J): qc = 0.25 ((4 c + 2 edges) + corners) of the fine residual; the
+// coarse correction starts at zero.
+template <class T>
+__device__ __forceinline__ void restrict_point(const Arith<T>& A, const BatchLevel<T>& C,
+                                               const BatchLevel<T>& F, int I, int J)
+{
+    const int64_t pf = F.pitch;
+    const T* c = F.r + (int64_t)(2 * J) * pf + 2 * I;
+    const T edges = A.add(A.add(c[-1], c[1]), A.add(c[-pf], c[pf]));
+    const T corners = A.add(A.add(c[-pf - 1], c[-pf + 1]), A.add(c[pf - 1], c[pf + 1]));
+    const T t = A.fma((T)2, c[0], edges);
+    const int64_t at = (int64_t)J * C.pitch + I;
+    C.q[at] = A.quarter(A.fma((T)2, t, corners));
+    C.u[at] = (T)0;
+}
+
+// Fine row j, coarse column I: bilinear interpolation added to fine points 2I and 2I + 1.
+template <class T>
+__device__ __forceinline__ void prolong_pair(const Arith<T>& A, const BatchLevel<T>& F,
+                                             const BatchLevel<T>& C, int I, int j)
+{
+    const int64_t pc = C.pitch;
+    const T* a = C.u + (int64_t)(j >> 1) * pc + I;
+    const int i0 = 2 * I, i1 = 2 * I + 1;
+    T* row = F.u + (int64_t)j * F.pitch;
+    if ((j & 1) == 0) {
+        if (i0 >= 1) row[i0] = A.add(row[i0], a[0]);
+        if (i1 <= F.m - 2) row[i1] = A.add(row[i1], A.half(A.add(a[0], a[1])));
+    } else {
+        if (i0 >= 1) row[i0] = A.add(row[i0], A.half(A.add(a[0], a[pc])));
+        if (i1 <= F.m - 2) {
+            const T s = A.add(A.add(a[0], a[1]), A.add(a[pc], a[pc + 1]));
+            row[i1] = A.add(row[i1], A.quarter(s));
+        }
+    }
+}
+
 // One smoother colour pass (Eq. 6 when gs, Eq. 7 otherwise) over the rows of each item.
 template <class T>
 __global__ void __launch_bounds__(BT)
@@ -77,16 +162,10 @@ __global__ void __launch_bounds__(BT)
         omw = (T)L.omw;
     }
     const int half_w = (L.m - 2 + 1) / 2;
-    for (int k = threadIdx.x; k < it.rows * half_w; k += BT) {
-        const int j = it.row0 + k / half_w;
-        const int i = 1 + ((1 + j + colour) & 1) + 2 * (k % half_w);
-        if (i > L.m - 2) continue;
-        const int64_t at = (int64_t)j * L.pitch + i;
-        T* c = L.u + at;
-        T s = A.nsum(c[-1], c[1], c[-L.pitch], c[L.pitch], (T)L.b2, L.unit_beta);
-        if (L.q) s = A.add(s, L.q[at]);
-        const T g = A.inv_d(s, L);
-        *c = gs ? g : A.fma(w, g, A.mul(omw, *c));
+    for (Walk k(half_w); k.r < it.rows; k.next()) {
+        const int j = it.row0 + k.r;
+        const int i = 1 + ((1 + j + colour) & 1) + 2 * k.c;
+        if (i <= L.m - 2) rb_point(A, L, i, j, gs != 0, w, omw);
     }
 }
 
@@ -100,14 +179,7 @@ __global__ void __launch_bounds__(BT)
     if (!active[L.problem]) return;
     const Arith<T> A = arith<T>();
     const int wdt = L.m - 2;
-    for (int k = threadIdx.x; k < it.rows * wdt; k += BT) {
-        const int j = it.row0 + k / wdt, i = 1 + k % wdt;
-        const int64_t at = (int64_t)j * L.pitch + i;
-        const T* c = L.u + at;
-        T s = A.nsum(c[-1], c[1], c[-L.pitch], c[L.pitch], (T)L.b2, L.unit_beta);
-        if (L.q) s = A.add(s, L.q[at]);
-        L.r[at] = A.fma(-(T)L.d, *c, s);
-    }
+    for (Walk k(wdt); k.r < it.rows; k.next()) defect_point(A, L, 1 + k.c, it.row0 + k.r);
 }
 
 // Items of the coarse level: qc from the fine residual (the level before it in lv), and the
@@ -123,17 +195,7 @@ __global__ void __launch_bounds__(BT)
     const BatchLevel<T> F = lv[it.level - 1];
     const Arith<T> A = arith<T>();
     const int wdt = C.m - 2;
-    const int64_t pf = F.pitch;
-    for (int k = threadIdx.x; k < it.rows * wdt; k += BT) {
-        const int J = it.row0 + k / wdt, I = 1 + k % wdt;
-        const T* c = F.r + (int64_t)(2 * J) * pf + 2 * I;
-        const T edges = A.add(A.add(c[-1], c[1]), A.add(c[-pf], c[pf]));
-        const T corners = A.add(A.add(c[-pf - 1], c[-pf + 1]), A.add(c[pf - 1], c[pf + 1]));
-        const T t = A.fma((T)2, c[0], edges);
-        const int64_t at = (int64_t)J * C.pitch + I;
-        C.q[at] = A.quarter(A.fma((T)2, t, corners));
-        C.u[at] = (T)0;
-    }
+    for (Walk k(wdt); k.r < it.rows; k.next()) restrict_point(A, C, F, 1 + k.c, it.row0 + k.r);
 }
 
 // Items of the fine level: u += bilinear interpolation of the next level's correction.
@@ -148,35 +210,14 @@ __global__ void __launch_bounds__(BT)
     const BatchLevel<T> C = lv[it.level + 1];
     const Arith<T> A = arith<T>();
     const int pairs = (F.m - 1) / 2;  // coarse columns 0 .. mc-2
-    const int64_t pc = C.pitch;
-    for (int k = threadIdx.x; k < it.rows * pairs; k += BT) {
-        const int j = it.row0 + k / pairs, I = k % pairs;
-        const T* a = C.u + (int64_t)(j >> 1) * pc + I;
-        const int i0 = 2 * I, i1 = 2 * I + 1;
-        T* row = F.u + (int64_t)j * F.pitch;
-        if ((j & 1) == 0) {
-            if (i0 >= 1) row[i0] = A.add(row[i0], a[0]);
-            if (i1 <= F.m - 2) row[i1] = A.add(row[i1], A.half(A.add(a[0], a[1])));
-        } else {
-            if (i0 >= 1) row[i0] = A.add(row[i0], A.half(A.add(a[0], a[pc])));
-            if (i1 <= F.m - 2) {
-                const T s = A.add(A.add(a[0], a[1]), A.add(a[pc], a[pc + 1]));
-                row[i1] = A.add(row[i1], A.quarter(s));
-            }
-        }
-    }
+    for (Walk k(pairs); k.r < it.rows; k.next()) prolong_pair(A, F, C, k.c, it.row0 + k.r);
 }
 
-// One item per problem at its coarsest level: u = A^-1 b in FP64.
+// u = A^-1 b at the coarsest level L, b = q + ring terms assembled in FP64; all threads of the
+// CTA take part (b: shared memory of N doubles).
 template <class T>
-__global__ void __launch_bounds__(1024)
-    b_coarse_kernel(const BatchItem* __restrict__ items, const BatchLevel<T>* __restrict__ lv,
-                    const int* __restrict__ active)
+__device__ __forceinline__ void coarse_cta(const BatchLevel<T>& L, double* b)
 {
-    extern __shared__ double b[];
-    const BatchItem it = items[blockIdx.x];
-    const BatchLevel<T> L = lv[it.level];
-    if (!active[L.problem]) return;
     const int mi = L.m - 2, N = mi * (L.n - 2);
     for (int k = threadIdx.x; k < N; k += blockDim.x) {
         const int i = 1 + k % mi, j = 1 + k / mi;
@@ -194,6 +235,84 @@ __global__ void __launch_bounds__(1024)
         for (int l = 0; l < N; ++l) x = __fma_rn(L.ainv_t[(int64_t)l * N + k], b[l], x);
         const int i = 1 + k % mi, j = 1 + k / mi;
         L.u[(int64_t)j * L.pitch + i] = (T)x;
+    }
+}
+
+// One item per problem at its coarsest level: u = A^-1 b in FP64.
+template <class T>
+__global__ void __launch_bounds__(1024)
+    b_coarse_kernel(const BatchItem* __restrict__ items, const BatchLevel<T>* __restrict__ lv,
+                    const int* __restrict__ active)
+{
+    extern __shared__ double b[];
+    const BatchItem it = items[blockIdx.x];
+    const BatchLevel<T> L = lv[it.level];
+    if (!active[L.problem]) return;
+    coarse_cta(L, b);
+}
+
+// ---- the small-level tail: the rest of a V-cycle in one CTA ----
+// Below some size a level's launches cost more than its work. The tail kernel runs the
+// whole V-cycle from level `first` of one problem down to its coarsest level and back
+// (smoothing, residual, restriction, coarsest solve, interpolation, smoothing) in one
+// CTA, with a CTA barrier between phases instead of a launch. Rows are spread over the
+// warps and same-colour points over the lanes; the per-point arithmetic is that of the
+// item kernels, so the tail changes the launch structure and nothing else.
+constexpr int TAIL_THREADS = 512;
+
+template <class T>
+__device__ __forceinline__ void smooth_cta(const Arith<T>& A, const BatchLevel<T>& L, int sweeps,
+                                           bool gs, T w, T omw)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int half_w = (L.m - 2 + 1) / 2;
+    for (int k = 0; k < sweeps; ++k)
+        for (int colour = 0; colour < 2; ++colour) {
+            for (int j = 1 + wid; j <= L.n - 2; j += nw)
+                for (int t = lane; t < half_w; t += 32) {
+                    const int i = 1 + ((1 + j + colour) & 1) + 2 * t;
+                    if (i <= L.m - 2) rb_point(A, L, i, j, gs, w, omw);
+                }
+            __syncthreads();
+        }
+}
+
+template <class T>
+__global__ void __launch_bounds__(TAIL_THREADS)
+    b_tail_kernel(const TailJob* __restrict__ jobs, const BatchLevel<T>* __restrict__ lv,
+                  const int* __restrict__ active, int nu1, int nu2, int gs, T w, T omw,
+                  int per_level_w)
+{
+    extern __shared__ double b[];
+    const TailJob jb = jobs[blockIdx.x];
+    if (active && !active[lv[jb.first].problem]) return;
+    const Arith<T> A = arith<T>();
+    if (per_level_w) {
+        w = (T)lv[jb.first].w;
+        omw = (T)lv[jb.first].omw;
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int l = jb.first; l < jb.last; ++l) {
+        const BatchLevel<T> F = lv[l];
+        smooth_cta(A, F, nu1, gs != 0, w, omw);
+        for (int j = 1 + wid; j <= F.n - 2; j += nw)
+            for (int i = 1 + lane; i <= F.m - 2; i += 32) defect_point(A, F, i, j);
+        __syncthreads();
+        const BatchLevel<T> C = lv[l + 1];
+        for (int J = 1 + wid; J <= C.n - 2; J += nw)
+            for (int I = 1 + lane; I <= C.m - 2; I += 32) restrict_point(A, C, F, I, J);
+        __syncthreads();
+    }
+    coarse_cta(lv[jb.last], b);
+    __syncthreads();
+    for (int l = jb.last - 1; l >= jb.first; --l) {
+        const BatchLevel<T> F = lv[l];
+        const BatchLevel<T> C = lv[l + 1];
+        const int pairs = (F.m - 1) / 2;
+        for (int j = 1 + wid; j <= F.n - 2; j += nw)
+            for (int I = lane; I < pairs; I += 32) prolong_pair(A, F, C, I, j);
+        __syncthreads();
+        smooth_cta(A, F, nu2, gs != 0, w, omw);
     }
 }
 
@@ -218,8 +337,8 @@ __global__ void __launch_bounds__(BT)
         e32 = lv32[it.level].u;
         p32 = lv32[it.level].pitch;
     }
-    for (int k = threadIdx.x; k < it.rows * wdt; k += BT) {
-        const int j = it.row0 + k / wdt, i = 1 + k % wdt;
+    for (Walk k(wdt); k.r < it.rows; k.next()) {
+        const int j = it.row0 + k.r, i = 1 + k.c;
         const double* c = L.u + (int64_t)j * L.pitch + i;
         const double s = A.nsum(c[-1], c[1], c[-L.pitch], c[L.pitch], L.b2, L.unit_beta);
         const double r = __fma_rn(-L.d, *c, s);
@@ -252,8 +371,8 @@ __global__ void __launch_bounds__(BT)
     const FmaOps o = load_fma_ops();
     const BatchLevel<float> E = lv32[it.level];
     const int wdt = L.m - 2;
-    for (int k = threadIdx.x; k < it.rows * wdt; k += BT) {
-        const int j = it.row0 + k / wdt, i = 1 + k % wdt;
+    for (Walk k(wdt); k.r < it.rows; k.next()) {
+        const int j = it.row0 + k.r, i = 1 + k.c;
         double* c = L.u + (int64_t)j * L.pitch + i;
         *c = fadd(o, *c, (double)E.u[(int64_t)j * E.pitch + i]);
     }
@@ -358,6 +477,20 @@ template cudaError_t launch_b_prolong<double>(const BatchList&, const BatchLevel
 template cudaError_t launch_b_prolong<float>(const BatchList&, const BatchLevel<float>*, const int*, cudaStream_t);
 template cudaError_t launch_b_coarse<double>(const BatchList&, const BatchLevel<double>*, const int*, int, cudaStream_t);
 template cudaError_t launch_b_coarse<float>(const BatchList&, const BatchLevel<float>*, const int*, int, cudaStream_t);
+
+template <class T>
+cudaError_t launch_b_tail(const TailJob* jobs, int count, const BatchLevel<T>* lv, const int* active,
+                          int nu1, int nu2, bool gs, double w, int max_unknowns, cudaStream_t s,
+                          bool per_level_w)
+{
+    if (count == 0) return cudaSuccess;
+    b_tail_kernel<T><<<count, TAIL_THREADS, sizeof(double) * (max_unknowns > 0 ? max_unknowns : 1), s>>>(
+        jobs, lv, active, nu1, nu2, gs ? 1 : 0, (T)w, (T)(1.0 - w), per_level_w ? 1 : 0);
+    note_launch();
+    return cudaGetLastError();
+}
+template cudaError_t launch_b_tail<double>(const TailJob*, int, const BatchLevel<double>*, const int*, int, int, bool, double, int, cudaStream_t, bool);
+template cudaError_t launch_b_tail<float>(const TailJob*, int, const BatchLevel<float>*, const int*, int, int, bool, double, int, cudaStream_t, bool);
 
 cudaError_t launch_b_sumsq(const BatchList& l, const BatchLevel<double>* lv, const int* active,
                            double* partials, const BatchLevel<float>* lv32, cudaStream_t s)

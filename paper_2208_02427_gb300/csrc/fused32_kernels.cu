@@ -1,0 +1,463 @@
+// fused32_kernels.cu -- the FP32 V-cycle's work on a level in two passes over memory.
+//
+// The inner cycle of the mixed-precision solver (FP32 on the correction equation
+// (E+W) + b2 (N+S) - d e + q = 0) is memory-bound: each red-black colour pass, the
+// residual, the restriction and the interpolation would each stream the level once. Here
+// one tile kernel does a level's whole descent and one its whole ascent:
+//   down: nu1 pre-smoothing sweeps (2 nu1 colour passes), the residual, and the
+//         full-weighting restriction to the next level (whose correction it zeroes);
+//   up:   the bilinear interpolation of the coarse correction, then nu2 post-smoothing
+//         sweeps.
+// A CTA loads its tile plus a halo into shared memory (temporal blocking: the halo shrinks
+// by one point per colour pass), works there, and writes back only the points it owns.
+// Every value is the one the per-pass kernels compute (same expressions, same rounding),
+// so the result is the same bit for bit; halo points are computed redundantly by the
+// neighbouring tiles. Tiles read u from one buffer and write another (down: u -> r slot,
+// up: r slot -> u), so no tile reads a value another tile has already overwritten.
+//
+// Shared-memory layout: a region row keeps its even columns in one half and its odd
+// columns in the other, so the points of one colour in a row are contiguous and their
+// east/west neighbours are contiguous in the other half (no bank conflicts); the half
+// stride is 16 mod 32 words so that the two halves of a row fall into different banks.
+#include <algorithm>
+
+#include "lap_device.cuh"
+#include "lap_internal.cuh"
+
+namespace lap {
+
+namespace {
+
+constexpr int FT_THREADS = 512;
+constexpr int FT_NW = FT_THREADS / 32;  // 16 warps
+constexpr int FT_W = 128;               // region columns (even): 64 column pairs
+constexpr int FT_H = 64;                // region rows: 4 per warp
+constexpr int FT_HS = FT_W / 2 + 16;    // half-row stride, 16 mod 32
+constexpr int FT_RS = 2 * FT_HS;        // row stride
+constexpr int FT_ARR = FT_RS * FT_H;    // floats per shared array
+constexpr int FT_CS = FT_W / 2 + 4;     // row stride of the staged coarse points
+constexpr int FT_CARR = FT_CS * (FT_H / 2 + 2);
+
+// The region of a tile: global (gx0 + lx, gy0 + ly) for local 0 <= lx < w, 0 <= ly < h.
+// gx0 is even: local column lx = 2p + half sits at half `half`, index p, of its row, and
+// has the parity of its global column.
+struct Region {
+    int gx0, gy0, w, h;
+};
+
+struct Coef32 {
+    float2 b2, inv_d, d, w, omw;
+    bool unit, gs;
+};
+
+__device__ __forceinline__ float2 f2(float v) { return make_float2(v, v); }
+
+__device__ __forceinline__ Coef32 coef32(const BatchLevel<float>& L, bool gs, float w, float omw)
+{
+    return Coef32{f2((float)L.b2), f2((float)L.inv_d), f2((float)L.d), f2(w), f2(omw),
+                  L.unit_beta != 0, gs};
+}
+
+// (E+W) + b2 (N+S) for two points at once: per component the FP32 neighbour sum of the
+// per-pass kernels (packed FP32 operations round each component like the scalar ones).
+__device__ __forceinline__ float2 nsum2(float2 w_, float2 e_, float2 s_, float2 n_, const Coef32& k)
+{
+    const float2 ew = __fadd2_rn(w_, e_);
+    const float2 ns = __fadd2_rn(s_, n_);
+    return k.unit ? __fadd2_rn(ns, ew) : __ffma2_rn(k.b2, ns, ew);
+}
+
+// Asynchronous 4-byte copy global -> shared; completes at cp_async_wait_all.
+__device__ __forceinline__ void cp_async4(float* sdst, const float* gsrc)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(sdst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+__device__ __forceinline__ float2 lds2(const float* p) { return *reinterpret_cast<const float2*>(p); }
+
+// Stores the components of v whose flags are set (8-byte store when both are).
+__device__ __forceinline__ void sts2_masked(float* p, float2 v, bool lo, bool hi)
+{
+    if (lo && hi) *reinterpret_cast<float2*>(p) = v;
+    else if (lo) p[0] = v.x;
+    else if (hi) p[1] = v.y;
+}
+
+// The region's u and q (0 outside the array; u = 0 when zero_u): each lane moves column
+// pairs (gx, gx + 1), gx even, with 8-byte loads, all 16 of a thread in flight together,
+// and splits them into the two halves of the row. Level pitches are even.
+__device__ __forceinline__ void load_region(float* su, float* sq, const float* u, const float* q,
+                                            int64_t pitch, int m, int n, const Region& R,
+                                            bool zero_u)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    float2 vu[8], vq[8];
+#pragma unroll
+    for (int t = 0; t < 4; ++t)
+#pragma unroll
+        for (int s2 = 0; s2 < 2; ++s2) {
+            const int ly = wid + FT_NW * t, p = lane + 32 * s2;
+            const int gy = R.gy0 + ly, gx = R.gx0 + 2 * p;
+            float2 a = make_float2(0.f, 0.f), b = make_float2(0.f, 0.f);
+            if (ly < R.h && 2 * p < R.w && gy >= 0 && gy < n && gx >= 0 && gx < m) {
+                const int64_t at = (int64_t)gy * pitch + gx;
+                if (!zero_u) a = *reinterpret_cast<const float2*>(u + at);
+                b = *reinterpret_cast<const float2*>(q + at);
+                if (gx + 1 >= m) a.y = b.y = 0.f;  // past the last column (row padding)
+            }
+            vu[2 * t + s2] = a;
+            vq[2 * t + s2] = b;
+        }
+#pragma unroll
+    for (int t = 0; t < 4; ++t)
+#pragma unroll
+        for (int s2 = 0; s2 < 2; ++s2) {
+            const int ly = wid + FT_NW * t, p = lane + 32 * s2;
+            if (ly < R.h && 2 * p < R.w) {
+                const int o = ly * FT_RS + p;
+                su[o] = vu[2 * t + s2].x;
+                su[o + FT_HS] = vu[2 * t + s2].y;
+                sq[o] = vq[2 * t + s2].x;
+                sq[o + FT_HS] = vq[2 * t + s2].y;
+            }
+        }
+}
+
+// Indices c of the half row `half` whose columns lie in [lx_lo, lx_hi] (lx = 2c + half).
+__device__ __forceinline__ void half_range(int lx_lo, int lx_hi, int half, int* c_lo, int* c_hi)
+{
+    *c_lo = (lx_lo - half + 1) >> 1;
+    *c_hi = (lx_hi - half) >> 1;
+}
+
+// West and east neighbours of the pair at indices c0, c0 + 1 of half `half` of a row:
+// the other half holds them at c - 1 + half and c + half.
+__device__ __forceinline__ void west_east(const float* other, int c0, int half, float2* w_, float2* e_)
+{
+    if (half == 0) {
+        const float a = other[c0 - 1];
+        const float2 b = lds2(other + c0);
+        *w_ = make_float2(a, b.x);
+        *e_ = b;
+    } else {
+        const float2 a = lds2(other + c0);
+        const float b = other[c0 + 2];
+        *w_ = a;
+        *e_ = make_float2(a.y, b);
+    }
+}
+
+// One colour pass of Eq. 6 (gs) or Eq. 7 over the domain-interior points of the region
+// but its outer ring: points (gx + gy) % 2 == colour, i.e. half (colour + gy) & 1 of row
+// gy. Rows over warps, one pair of points per lane (a half row holds at most 64 points).
+__device__ __forceinline__ void colour_pass(float* su, const float* sq, const Region& R, int m, int n,
+                                            int colour, const Coef32& k)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int lx_lo = max(1, 1 - R.gx0), lx_hi = min(R.w - 2, m - 2 - R.gx0);
+    const int ly_lo = max(1, 1 - R.gy0), ly_hi = min(R.h - 2, n - 2 - R.gy0);
+    const int c0 = 2 * lane;
+    for (int ly = ly_lo + wid; ly <= ly_hi; ly += FT_NW) {
+        const int half = (colour + R.gy0 + ly) & 1;
+        int c_lo, c_hi;
+        half_range(lx_lo, lx_hi, half, &c_lo, &c_hi);
+        if (c0 + 1 < c_lo || c0 > c_hi) continue;
+        float* row = su + ly * FT_RS;
+        const int a = ly * FT_RS + half * FT_HS + c0;
+        float2 w_, e_;
+        west_east(row + (1 - half) * FT_HS, c0, half, &w_, &e_);
+        const float2 s = __fadd2_rn(nsum2(w_, e_, lds2(su + a - FT_RS), lds2(su + a + FT_RS), k),
+                                    lds2(sq + a));
+        const float2 g = __fmul2_rn(s, k.inv_d);
+        const float2 v = k.gs ? g : __ffma2_rn(k.w, g, __fmul2_rn(k.omw, lds2(su + a)));
+        sts2_masked(su + a, v, c0 >= c_lo, c0 + 1 <= c_hi);
+    }
+}
+
+__device__ __forceinline__ void smooth_region(float* su, const float* sq, const Region& R, int m,
+                                              int n, int sweeps, const Coef32& k)
+{
+    for (int s = 0; s < sweeps; ++s)
+        for (int colour = 0; colour < 2; ++colour) {
+            colour_pass(su, sq, R, m, n, colour, k);
+            __syncthreads();
+        }
+}
+
+// Owned points [x0, x1) x [y0, y1) from shared memory to dst, by column pairs (gx even).
+__device__ __forceinline__ void store_owned(float* dst, int64_t pitch, const float* su,
+                                            const Region& R, int x0, int x1, int y0, int y1)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int p_lo = (x0 - R.gx0) >> 1, p_hi = (x1 - 1 - R.gx0) >> 1;
+    for (int gy = y0 + wid; gy < y1; gy += FT_NW) {
+        const int ly = gy - R.gy0;
+        for (int p = p_lo + lane; p <= p_hi; p += 32) {
+            const int gx = R.gx0 + 2 * p;
+            const float2 v = make_float2(su[ly * FT_RS + p], su[ly * FT_RS + FT_HS + p]);
+            sts2_masked(dst + (int64_t)gy * pitch + gx, v, gx >= x0, gx + 1 < x1);
+        }
+    }
+}
+
+// Region of the tile of owned points [x0, x0 + tx) x [y0, y0 + ty) with a halo of `halo`
+// points on every side; gx0 rounded down to even, the width rounded up to even.
+__device__ __forceinline__ Region region_of(int x0, int y0, int tx, int ty, int halo)
+{
+    Region R;
+    R.gx0 = (x0 - halo) & ~1;
+    R.gy0 = y0 - halo;
+    const int last = x0 + tx - 1 + halo;
+    R.w = (last - R.gx0 + 2) & ~1;
+    R.h = ty + 2 * halo;
+    return R;
+}
+
+// Descent on one tile of level F: nu1 smoothing sweeps, the smoothed u of the owned points
+// to F.r (the second buffer of the level), the residual, and qc = 0.25 ((4 r + 2 edges) +
+// corners) with the correction zeroed at the coarse points whose centre the tile owns.
+__device__ __forceinline__ void down_tile(const BatchLevel<float>& F, const BatchLevel<float>& C,
+                                          int x0, int y0, int tx, int ty, int nu1, bool zero_u,
+                                          const Coef32& k, float* su, float* sq)
+{
+    const int m = F.m, n = F.n;
+    const Region R = region_of(x0, y0, tx, ty, 2 + 2 * nu1);
+    load_region(su, sq, F.u, F.q, F.pitch, m, n, R, zero_u);
+    __syncthreads();
+    smooth_region(su, sq, R, m, n, nu1, k);
+    const int x1 = min(x0 + tx, m - 1), y1 = min(y0 + ty, n - 1);
+    store_owned(F.r, F.pitch, su, R, x0, x1, y0, y1);
+    // residual r = (E+W) + b2 (N+S) + q - d u on the owned points and a ring of one, written
+    // over q (each point reads only its own q)
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int lx_lo = max(1, x0 - 1) - R.gx0, lx_hi = min(m - 2, x1) - R.gx0;
+    const int ly_lo = max(1, y0 - 1) - R.gy0, ly_hi = min(n - 2, y1) - R.gy0;
+    const int c0 = 2 * lane;
+    for (int t = wid; t <= 2 * (ly_hi - ly_lo) + 1; t += FT_NW) {
+        const int ly = ly_lo + (t >> 1), half = t & 1;
+        int c_lo, c_hi;
+        half_range(lx_lo, lx_hi, half, &c_lo, &c_hi);
+        if (c0 + 1 < c_lo || c0 > c_hi) continue;
+        const float* row = su + ly * FT_RS;
+        const int a = ly * FT_RS + half * FT_HS + c0;
+        float2 w_, e_;
+        west_east(row + (1 - half) * FT_HS, c0, half, &w_, &e_);
+        const float2 s = __fadd2_rn(nsum2(w_, e_, lds2(su + a - FT_RS), lds2(su + a + FT_RS), k),
+                                    lds2(sq + a));
+        const float2 r = __ffma2_rn(make_float2(-k.d.x, -k.d.y), lds2(su + a), s);
+        sts2_masked(sq + a, r, c0 >= c_lo, c0 + 1 <= c_hi);
+    }
+    __syncthreads();
+    // restriction to the coarse points (I, J) with (2I, 2J) owned: the centre is at half 0,
+    // index c = I - gx0 / 2; west/east at half 1, c - 1 and c; rows 2J - 1, 2J, 2J + 1
+    const int mc = (m - 1) / 2 + 1, nc = (n - 1) / 2 + 1;
+    const int I0 = max(1, (x0 + 1) >> 1), I1 = min(mc - 2, (x1 - 1) >> 1);
+    const int J0 = max(1, (y0 + 1) >> 1), J1 = min(nc - 2, (y1 - 1) >> 1);
+    const float* r = sq;
+    for (int J = J0 + wid; J <= J1; J += FT_NW) {
+        const int ly = 2 * J - R.gy0;
+        const float* r0 = r + ly * FT_RS;
+        for (int I = I0 + lane; I <= I1; I += 32) {
+            const int c = I - (R.gx0 >> 1);
+            const float* mid = r0 + c;
+            const float* odd = r0 + FT_HS + c;
+            const float edges = __fadd_rn(__fadd_rn(odd[-1], odd[0]), __fadd_rn(mid[-FT_RS], mid[FT_RS]));
+            const float corners = __fadd_rn(__fadd_rn(odd[-FT_RS - 1], odd[-FT_RS]),
+                                            __fadd_rn(odd[FT_RS - 1], odd[FT_RS]));
+            const float tt = __fmaf_rn(2.0f, mid[0], edges);
+            const int64_t at = (int64_t)J * C.pitch + I;
+            C.q[at] = __fmul_rn(0.25f, __fmaf_rn(2.0f, tt, corners));
+            C.u[at] = 0.0f;
+        }
+    }
+}
+
+// Ascent on one tile of level F: u (from F.r) plus the bilinear interpolation of C.u, nu2
+// smoothing sweeps, the owned points to F.u. The coarse points under the region are staged
+// in shared memory (sc): a column pair p of the region lies over coarse column gx0 / 2 + p.
+__device__ __forceinline__ void up_tile(const BatchLevel<float>& F, const BatchLevel<float>& C,
+                                        int x0, int y0, int tx, int ty, int nu2, const Coef32& k,
+                                        float* su, float* sq, float* sc)
+{
+    const int m = F.m, n = F.n;
+    const Region R = region_of(x0, y0, tx, ty, 2 * nu2);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int cI0 = R.gx0 >> 1, cJ0 = R.gy0 >> 1;  // floor halves (gy0 may be negative)
+    const int cw = (R.w >> 1) + 1, ch = ((R.gy0 + R.h - 1) >> 1) - cJ0 + 2;
+    const int mc = (m - 1) / 2 + 1, nc = (n - 1) / 2 + 1;
+    for (int cy = wid; cy < ch; cy += FT_NW) {
+        const int J = cJ0 + cy;
+        const bool rowin = J >= 0 && J < nc;
+        for (int cx = lane; cx < cw; cx += 32) {
+            const int I = cI0 + cx;
+            float* d = sc + cy * FT_CS + cx;
+            if (rowin && I >= 0 && I < mc) cp_async4(d, C.u + (int64_t)J * C.pitch + I);
+            else *d = 0.f;
+        }
+    }
+    load_region(su, sq, F.r, F.q, F.pitch, m, n, R, false);
+    cp_async_wait_all();
+    __syncthreads();
+    // u += P e: even rows take coarse row J = gy / 2, odd rows the mean of rows J and J + 1;
+    // even columns (half 0) coarse column p, odd columns (half 1) the mean of p and p + 1
+    const int lx_lo = max(0, 1 - R.gx0), lx_hi = min(R.w - 1, m - 2 - R.gx0);
+    const int ly_lo = max(0, 1 - R.gy0), ly_hi = min(R.h - 1, n - 2 - R.gy0);
+    for (int ly = ly_lo + wid; ly <= ly_hi; ly += FT_NW) {
+        const int gy = R.gy0 + ly;
+        const float* a = sc + ((gy >> 1) - cJ0) * FT_CS;
+        float* row = su + ly * FT_RS;
+        for (int p = lane; 2 * p <= lx_hi; p += 32) {
+            const bool ok0 = 2 * p >= lx_lo, ok1 = 2 * p + 1 >= lx_lo && 2 * p + 1 <= lx_hi;
+            float e0, e1;
+            if ((gy & 1) == 0) {
+                e0 = a[p];
+                e1 = __fmul_rn(0.5f, __fadd_rn(a[p], a[p + 1]));
+            } else {
+                e0 = __fmul_rn(0.5f, __fadd_rn(a[p], a[p + FT_CS]));
+                e1 = __fmul_rn(0.25f, __fadd_rn(__fadd_rn(a[p], a[p + 1]),
+                                                __fadd_rn(a[p + FT_CS], a[p + FT_CS + 1])));
+            }
+            if (ok0) row[p] = __fadd_rn(row[p], e0);
+            if (ok1) row[FT_HS + p] = __fadd_rn(row[FT_HS + p], e1);
+        }
+    }
+    __syncthreads();
+    smooth_region(su, sq, R, m, n, nu2, k);
+    store_owned(F.u, F.pitch, su, R, x0, min(x0 + tx, m - 1), y0, min(y0 + ty, n - 1));
+}
+
+// ---- one grid: tile (blockIdx.x, blockIdx.y) of owned points 1 + (bx tx, by ty) ----
+__global__ void __launch_bounds__(FT_THREADS, 2)
+    down32_kernel(BatchLevel<float> F, BatchLevel<float> C, int tx, int ty, int nu1, int zero_u,
+                  int gs, float w, float omw)
+{
+    extern __shared__ float4 smem4[];
+    float* smem = reinterpret_cast<float*>(smem4);
+    down_tile(F, C, 1 + blockIdx.x * tx, 1 + blockIdx.y * ty, tx, ty, nu1, zero_u != 0,
+              coef32(F, gs != 0, w, omw), smem, smem + FT_ARR);
+}
+
+__global__ void __launch_bounds__(FT_THREADS, 2)
+    up32_kernel(BatchLevel<float> F, BatchLevel<float> C, int tx, int ty, int nu2, int gs, float w,
+                float omw)
+{
+    extern __shared__ float4 smem4[];
+    float* smem = reinterpret_cast<float*>(smem4);
+    up_tile(F, C, 1 + blockIdx.x * tx, 1 + blockIdx.y * ty, tx, ty, nu2, coef32(F, gs != 0, w, omw),
+            smem, smem + FT_ARR, smem + 2 * FT_ARR);
+}
+
+// ---- many grids: one tile item per CTA ----
+__global__ void __launch_bounds__(FT_THREADS, 2)
+    b_down32_kernel(const TileItem* __restrict__ items, const BatchLevel<float>* __restrict__ lv,
+                    const int* __restrict__ active, int nu1, int zero_u, int gs, float w, float omw)
+{
+    extern __shared__ float4 smem4[];
+    float* smem = reinterpret_cast<float*>(smem4);
+    const TileItem it = items[blockIdx.x];
+    const BatchLevel<float> F = lv[it.level];
+    if (active && !active[F.problem]) return;
+    down_tile(F, lv[it.level + 1], it.x0, it.y0, it.tx, it.ty, nu1, zero_u != 0,
+              coef32(F, gs != 0, w, omw), smem, smem + FT_ARR);
+}
+
+__global__ void __launch_bounds__(FT_THREADS, 2)
+    b_up32_kernel(const TileItem* __restrict__ items, const BatchLevel<float>* __restrict__ lv,
+                  const int* __restrict__ active, int nu2, int gs, float w, float omw)
+{
+    extern __shared__ float4 smem4[];
+    float* smem = reinterpret_cast<float*>(smem4);
+    const TileItem it = items[blockIdx.x];
+    const BatchLevel<float> F = lv[it.level];
+    if (active && !active[F.problem]) return;
+    up_tile(F, lv[it.level + 1], it.x0, it.y0, it.tx, it.ty, nu2, coef32(F, gs != 0, w, omw), smem,
+            smem + FT_ARR, smem + 2 * FT_ARR);
+}
+
+constexpr size_t FT_SMEM = (2 * FT_ARR + FT_CARR) * sizeof(float);
+
+}  // namespace
+
+// Halo of a descent (nu1 sweeps, then a residual ring feeding the restriction) and of an
+// ascent (nu2 sweeps).
+static int halo_down(int nu1) { return 2 + 2 * nu1; }
+static int halo_up(int nu2) { return 2 * nu2; }
+
+bool fused32_supported(int nu1, int nu2)
+{
+    const int h = std::max(halo_down(nu1), halo_up(nu2));
+    return FT_W - 2 * h - 2 >= 16 && FT_H - 2 * h >= 8;
+}
+
+// Balanced tiles no larger than the region allows: the interior (m-2) x (n-2) split into
+// ntx x nty tiles of tx x ty owned points.
+void fused32_tile(int m, int n, int nu1, int nu2, int* tx, int* ty, int* ntx, int* nty)
+{
+    const int h = std::max(halo_down(nu1), halo_up(nu2));
+    const int mx = FT_W - 2 * h - 2, my = FT_H - 2 * h;
+    const int W = std::max(1, m - 2), H = std::max(1, n - 2);
+    *ntx = (W + mx - 1) / mx;
+    *nty = (H + my - 1) / my;
+    *tx = (W + *ntx - 1) / *ntx;
+    *ty = (H + *nty - 1) / *nty;
+}
+
+static bool g_fused32_ready = false;
+
+cudaError_t prepare_fused32()
+{
+    if (g_fused32_ready) return cudaSuccess;
+    const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    cudaError_t e = cudaFuncSetAttribute(down32_kernel, a, (int)FT_SMEM);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(up32_kernel, a, (int)FT_SMEM);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(b_down32_kernel, a, (int)FT_SMEM);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(b_up32_kernel, a, (int)FT_SMEM);
+    if (e == cudaSuccess) g_fused32_ready = true;
+    return e;
+}
+
+cudaError_t launch_down32(const BatchLevel<float>& F, const BatchLevel<float>& C, int nu1, int nu2,
+                          bool zero_u, bool gs, double w, cudaStream_t s)
+{
+    int tx, ty, ntx, nty;
+    fused32_tile(F.m, F.n, nu1, nu2, &tx, &ty, &ntx, &nty);
+    down32_kernel<<<dim3(ntx, nty), FT_THREADS, FT_SMEM, s>>>(F, C, tx, ty, nu1, zero_u ? 1 : 0,
+                                                              gs ? 1 : 0, (float)w, (float)(1.0 - w));
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_up32(const BatchLevel<float>& F, const BatchLevel<float>& C, int nu1, int nu2,
+                        bool gs, double w, cudaStream_t s)
+{
+    int tx, ty, ntx, nty;
+    fused32_tile(F.m, F.n, nu1, nu2, &tx, &ty, &ntx, &nty);
+    up32_kernel<<<dim3(ntx, nty), FT_THREADS, FT_SMEM, s>>>(F, C, tx, ty, nu2, gs ? 1 : 0, (float)w,
+                                                            (float)(1.0 - w));
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_b_down32(const TileItem* items, int count, const BatchLevel<float>* lv,
+                            const int* active, int nu1, bool zero_u, bool gs, double w, cudaStream_t s)
+{
+    if (count == 0) return cudaSuccess;
+    b_down32_kernel<<<count, FT_THREADS, FT_SMEM, s>>>(items, lv, active, nu1, zero_u ? 1 : 0,
+                                                       gs ? 1 : 0, (float)w, (float)(1.0 - w));
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_b_up32(const TileItem* items, int count, const BatchLevel<float>* lv,
+                          const int* active, int nu2, bool gs, double w, cudaStream_t s)
+{
+    if (count == 0) return cudaSuccess;
+    b_up32_kernel<<<count, FT_THREADS, FT_SMEM, s>>>(items, lv, active, nu2, gs ? 1 : 0, (float)w,
+                                                     (float)(1.0 - w));
+    note_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace lap

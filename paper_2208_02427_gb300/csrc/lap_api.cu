@@ -40,6 +40,43 @@ Coef make_coef(double dx, double dy)
     return c;
 }
 
+// Chooses the small-level tail size of one shape by timing. The tail changes how a V-cycle
+// is launched and nothing else (every candidate gives the same iterates bit for bit), so
+// the candidates are tried on the first cycles of real solves: each cycle (or check
+// period) runs with the next untried candidate, its device time per cycle is recorded,
+// and once every candidate has been timed the fastest is kept for the handle's lifetime.
+struct TailTuner {
+    std::vector<int> cand;  // tail sizes; -1 = no tail
+    std::vector<double> ms; // best time per cycle seen, +inf = not tried yet
+    int best = 0;
+    bool done = false;
+    void init(std::vector<int> c)
+    {
+        cand = std::move(c);
+        ms.assign(cand.size(), HUGE_VAL);
+        best = 0;
+        done = cand.size() <= 1;
+    }
+    int next() const
+    {
+        if (done) return best;
+        for (size_t i = 0; i < cand.size(); ++i)
+            if (ms[i] == HUGE_VAL) return (int)i;
+        return best;
+    }
+    void record(int i, double v)
+    {
+        if (done || i < 0 || i >= (int)cand.size() || !(v > 0.0)) return;
+        ms[i] = std::min(ms[i], v);
+        bool all = true;
+        for (size_t k = 0; k < cand.size(); ++k) {
+            if (ms[k] == HUGE_VAL) all = false;
+            else if (ms[k] < ms[best] || ms[best] == HUGE_VAL) best = (int)k;
+        }
+        done = all;
+    }
+};
+
 }  // namespace lap
 
 using namespace lap;
@@ -108,6 +145,9 @@ struct lap_handle_s {
     bool use_graphs = true;
     cudaStream_t capture = nullptr;
     std::map<std::string, std::pair<cudaGraphExec_t, int64_t>> graphs;  // exec, kernels
+    // Small-level tail sizes chosen by timing, per shape (see TailTuner)
+    std::map<std::string, lap::TailTuner> tail_tuners;
+    cudaEvent_t ev[2] = {nullptr, nullptr};
 };
 
 namespace {
@@ -216,7 +256,7 @@ void check_device_ptr(lap_handle h, const void* p, const char* what, bool allow_
 void check_params(const lap_params* p)
 {
     if (!p) fail(LAP_EINVAL, "params is NULL");
-    if (p->method < LAP_JACOBI || p->method > LAP_SOR_LEX) fail(LAP_EINVAL, "unknown method");
+    if (p->method < LAP_JACOBI || p->method > LAP_MG_FP32) fail(LAP_EINVAL, "unknown method");
     if (p->norm < LAP_NORM_L2_REL || p->norm > LAP_NORM_MAXDELTA) fail(LAP_EINVAL, "unknown norm");
     if (!(p->tol >= 0.0)) fail(LAP_EINVAL, "tol must be >= 0");
     if (p->max_iter < 0) fail(LAP_EINVAL, "max_iter must be >= 0");
@@ -227,13 +267,17 @@ void check_params(const lap_params* p)
         fail(LAP_EINVAL, "w must lie in (0, 2)");
     if (p->method == LAP_MG_MIXED && (p->inner_cycles < 1 || p->inner_cycles > 64))
         fail(LAP_EINVAL, "inner_cycles must lie in 1..64");
-    if (p->method == LAP_MG || p->method == LAP_MG_MIXED) {
+    if (p->method == LAP_MG_FP32 && p->norm == LAP_NORM_MAXDELTA)
+        fail(LAP_EINVAL, "LAP_MG_FP32 stops on an L2 norm");
+    if (p->method == LAP_MG || p->method == LAP_MG_MIXED || p->method == LAP_MG_FP32) {
         if (p->nu1 < 0 || p->nu2 < 0 || p->nu1 + p->nu2 > 64)
             fail(LAP_EINVAL, "nu1, nu2 must be >= 0 and nu1 + nu2 <= 64");
         if (p->coarsest_min < 3) fail(LAP_EINVAL, "coarsest_min must be >= 3");
         if (p->max_levels < 0) fail(LAP_EINVAL, "max_levels must be >= 0");
         if (!(p->smoother_w > 0.0 && p->smoother_w < 2.0))
             fail(LAP_EINVAL, "smoother_w must lie in (0, 2)");
+        if (p->tail_size < -1 || p->tail_size == 1 || p->tail_size == 2)
+            fail(LAP_EINVAL, "tail_size must be -1, 0 or >= 3");
     }
     if ((p->method == LAP_ADI || p->method == LAP_SLOR) && p->line_form != LAP_FORM_A &&
         p->line_form != LAP_FORM_B)
@@ -462,6 +506,10 @@ struct Work {
     double* aux = nullptr;       // Jacobi second buffer, or previous iterate for max|delta|
     std::vector<Level> levels;
     std::vector<Level32> levels32;
+    // the small-level tail: level descriptors and one job per possible first level
+    BatchLevel<double>* tl64 = nullptr;
+    BatchLevel<float>* tl32 = nullptr;
+    TailJob* tjob = nullptr;
 };
 
 template <class C>
@@ -495,9 +543,11 @@ void carve(C& cv, Work& w, const lap_grid* g, const lap_params* p)
             m = (m - 1) / 2 + 1;
             n = (n - 1) / 2 + 1;
         }
+        w.tl64 = cv.template take<BatchLevel<double>>(L);
+        w.tjob = cv.template take<TailJob>(L);
     }
     w.levels32.clear();
-    if (p->method == LAP_MG_MIXED) {
+    if (p->method == LAP_MG_MIXED || p->method == LAP_MG_FP32) {
         const int L = mg_level_count(g->m, g->n, p->coarsest_min, p->max_levels);
         int m = g->m, n = g->n;
         for (int l = 0; l < L; ++l) {
@@ -510,6 +560,8 @@ void carve(C& cv, Work& w, const lap_grid* g, const lap_params* p)
             m = (m - 1) / 2 + 1;
             n = (n - 1) / 2 + 1;
         }
+        w.tl32 = cv.template take<BatchLevel<float>>(L);
+        w.tjob = cv.template take<TailJob>(L);
     }
 }
 
@@ -519,6 +571,35 @@ size_t work_bytes(const lap_grid* g, const lap_params* p)
     Work w;
     carve(sz, w, g, p);
     return sz.off;
+}
+
+// Tail sizes worth timing for a batch of V-cycles (one CTA per problem runs the levels at or
+// below the size) and for one grid (one CTA in all).
+std::vector<int> tail_candidates(bool batched, bool fp32, int tail_size)
+{
+    if (tail_size != 0) return {tail_size};
+    if (batched) return {-1, 33, 65, 129, 257};
+    return fp32 ? std::vector<int>{-1, 33, 65, 129, 257} : std::vector<int>{-1, 17, 33, 65};
+}
+
+std::string tuner_key(char kind, const lap_params* p, const std::vector<int>& shape)
+{
+    uint64_t hsh = 1469598103934665603ull;  // FNV-1a over the shapes
+    for (int v : shape) {
+        hsh ^= (uint32_t)v;
+        hsh *= 1099511628211ull;
+    }
+    char buf[192];
+    std::snprintf(buf, sizeof buf, "%c %d %d %d %d %d %.17g %d %d %d %zu %llx", kind, p->method,
+                  p->nu1, p->nu2, p->coarsest_min, p->max_levels, p->smoother_w, p->inner_cycles,
+                  p->tail_size, p->unfused, shape.size(), (unsigned long long)hsh);
+    return buf;
+}
+
+cudaEvent_t tuner_event(lap_handle h, int k)
+{
+    if (!h->ev[k]) ck(cudaEventCreate(&h->ev[k]), "create event");
+    return h->ev[k];
 }
 
 // ---- the solver loop ---------------------------------------------------------------------
@@ -601,9 +682,12 @@ struct Solver {
         case LAP_MG:
             vcycle(0);
             break;
+        case LAP_MG_FP32:
+            vcycle32(0);
+            break;
         case LAP_MG_MIXED: {
             const Level32& l0 = w.levels32[0];
-            for (int k = 0; k < p->inner_cycles; ++k) vcycle32(0);
+            for (int k = 0; k < p->inner_cycles; ++k) vcycle32(0, k == 0);
             ck(launch_update64(f, l0.u.p, l0.u.pitch, s), "update kernel");
             ck(launch_defect64_to32(f, c, l0.q, l0.u.p, l0.u.pitch, w.partials, s),
                "mixed residual kernel");
@@ -612,11 +696,127 @@ struct Solver {
         }
     }
 
-    // The FP32 image of vcycle() on the correction equation.
-    void vcycle32(int l)
+    // First level of the small-level tail in vcycle()/vcycle32() (-1: none), see set_tail.
+    int tail_first = -1;
+
+    // Run the levels whose sides are both <= S (S > 0) as the tail; -1 = no tail.
+    void set_tail(int S)
+    {
+        tail_first = -1;
+        if (S <= 0) return;
+        const int L = p->method == LAP_MG ? (int)w.levels.size() : (int)w.levels32.size();
+        int m = f.m, n = f.n;
+        for (int l = 0; l < L; ++l) {
+            if (m <= S && n <= S) {
+                tail_first = l;
+                return;
+            }
+            m = (m - 1) / 2 + 1;
+            n = (n - 1) / 2 + 1;
+        }
+    }
+
+    int coarsest_unknowns() const
+    {
+        const int L = p->method == LAP_MG ? (int)w.levels.size() : (int)w.levels32.size();
+        int m = f.m, n = f.n;
+        for (int l = 1; l < L; ++l) {
+            m = (m - 1) / 2 + 1;
+            n = (n - 1) / 2 + 1;
+        }
+        return (m - 2) * (n - 2);
+    }
+
+    // Level descriptors and tail jobs of this call (level 0 is the caller's field, or the
+    // FP32 correction), uploaded before any period runs.
+    void upload_tail()
+    {
+        const bool mixed = p->method == LAP_MG_MIXED || p->method == LAP_MG_FP32;
+        const int L = mixed ? (int)w.levels32.size() : (int)w.levels.size();
+        std::vector<BatchLevel<double>> d(L);
+        std::vector<BatchLevel<float>> g(L);
+        std::vector<TailJob> jobs(L);
+        int m = f.m, n = f.n;
+        for (int l = 0; l < L; ++l) {
+            BatchLevel<double> a{};
+            a.m = m;
+            a.n = n;
+            a.problem = 0;
+            a.unit_beta = c.unit_beta;
+            a.b2 = c.b2;
+            a.d = c.d;
+            a.inv_d = c.inv_d;
+            a.w = p->smoother_w;
+            a.omw = 1.0 - p->smoother_w;
+            a.ainv_t = l == L - 1 ? coarse_inverse(h, m, n, c.b2, c.d) : nullptr;
+            if (mixed) {
+                BatchLevel<float> b{};
+                b.u = w.levels32[l].u.p;
+                b.q = w.levels32[l].q;
+                b.r = w.levels32[l].r;
+                b.m = m;
+                b.n = n;
+                b.pitch = w.levels32[l].u.pitch;
+                b.unit_beta = a.unit_beta;
+                b.inv_d_shift = 0;
+                b.b2 = a.b2;
+                b.d = a.d;
+                b.inv_d = a.inv_d;
+                b.w = a.w;
+                b.omw = a.omw;
+                b.ainv_t = a.ainv_t;
+                g[l] = b;
+            } else {
+                a.u = w.levels[l].u.p;
+                a.q = w.levels[l].q;
+                a.r = w.levels[l].r;
+                a.pitch = w.levels[l].u.pitch;
+                a.inv_d_shift = c.inv_d_shift;
+                d[l] = a;
+            }
+            jobs[l] = TailJob{l, L - 1};
+            m = (m - 1) / 2 + 1;
+            n = (n - 1) / 2 + 1;
+        }
+        // pageable sources: the copies are staged before the calls return
+        if (mixed) hl32 = g;
+        if (mixed)
+            ck(cudaMemcpyAsync(w.tl32, g.data(), L * sizeof(g[0]), cudaMemcpyHostToDevice, s), "upload levels");
+        else
+            ck(cudaMemcpyAsync(w.tl64, d.data(), L * sizeof(d[0]), cudaMemcpyHostToDevice, s), "upload levels");
+        ck(cudaMemcpyAsync(w.tjob, jobs.data(), L * sizeof(TailJob), cudaMemcpyHostToDevice, s), "upload jobs");
+    }
+
+    std::vector<BatchLevel<float>> hl32;  // FP32 level descriptors (host copy)
+    bool fused32 = false;                 // descents/ascents as tile kernels
+
+    // The FP32 image of vcycle() on the correction equation. first: the first inner cycle
+    // of an outer iteration (the level-0 correction starts at zero).
+    void vcycle32(int l, bool first = false)
     {
         Level32& lv = w.levels32[l];
         const int L = (int)w.levels32.size();
+        if (l == tail_first) {
+            ck(launch_b_tail(w.tjob + l, 1, w.tl32, nullptr, p->nu1, p->nu2, p->smoother_w == 1.0,
+                             p->smoother_w, coarsest_unknowns(), s),
+               "tail kernel");
+            return;
+        }
+        if (l == L - 1 && p->method == LAP_MG_FP32) {
+            // level 0 carries the Dirichlet ring: the tail's coarsest solve adds ring terms
+            ck(launch_b_tail(w.tjob + l, 1, w.tl32, nullptr, p->nu1, p->nu2, p->smoother_w == 1.0,
+                             p->smoother_w, coarsest_unknowns(), s),
+               "coarse solve kernel");
+            return;
+        }
+        if (fused32 && l < L - 1) {
+            const bool gs = p->smoother_w == 1.0;
+            ck(launch_down32(hl32[l], hl32[l + 1], p->nu1, p->nu2, l > 0 || first, gs, p->smoother_w, s),
+               "descent kernel");
+            vcycle32(l + 1);
+            ck(launch_up32(hl32[l], hl32[l + 1], p->nu1, p->nu2, gs, p->smoother_w, s), "ascent kernel");
+            return;
+        }
         if (l == L - 1) {
             const double* ainv = coarse_inverse(h, lv.u.m, lv.u.n, c.b2, c.d);
             ck(launch_coarse32(lv.u, lv.q, ainv, s), "coarse solve kernel");
@@ -650,6 +850,12 @@ struct Solver {
     {
         Level& lv = w.levels[l];
         const int L = (int)w.levels.size();
+        if (l == tail_first) {
+            ck(launch_b_tail(w.tjob + l, 1, w.tl64, nullptr, p->nu1, p->nu2, p->smoother_w == 1.0,
+                             p->smoother_w, coarsest_unknowns(), s),
+               "tail kernel");
+            return;
+        }
         if (l == L - 1) {
             const double* ainv = coarse_inverse(h, lv.u.m, lv.u.n, c.b2, c.d);
             ck(launch_coarse_solve(lv.u, lv.q, c, ainv, s), "coarse solve kernel");
@@ -709,7 +915,7 @@ struct Solver {
             const Level& lv = w.levels.back();
             coarse_inverse(h, lv.u.m, lv.u.n, c.b2, c.d);
         }
-        if (p->method == LAP_MG_MIXED) {
+        if (p->method == LAP_MG_MIXED || p->method == LAP_MG_FP32) {
             const Level32& lv = w.levels32.back();
             coarse_inverse(h, lv.u.m, lv.u.n, c.b2, c.d);
         }
@@ -724,7 +930,7 @@ struct Solver {
         const int64_t ints[] = {p->method, f.m, f.n, f.pitch, steps, maxdelta, fused_maxd,
                                 p->nu1, p->nu2, p->coarsest_min, p->max_levels, p->line_form,
                                 (int64_t)w.levels.size(), p->inner_cycles,
-                                (int64_t)w.levels32.size()};
+                                (int64_t)w.levels32.size(), tail_first, fused32};
         const double dbl[] = {c.b2, c.d, c.inv_d, p->w, p->smoother_w};
         const void* ptrs[] = {f.p, jac_cur, jac_other, w.aux, w.maxd, h->arena};
         put(ints, sizeof ints);
@@ -734,12 +940,14 @@ struct Solver {
     }
 
     // A period as one CUDA graph: captured once on the handle's own stream, replayed on s.
-    void run_period(int64_t steps, bool maxdelta, bool fused_maxd)
+    // Returns true when this call captured the graph (its first use).
+    bool run_period(int64_t steps, bool maxdelta, bool fused_maxd)
     {
         if (!h->use_graphs) {
             period(steps, maxdelta, fused_maxd);
-            return;
+            return false;
         }
+        bool captured = false;
         const std::string key = graph_key(steps, maxdelta, fused_maxd);
         auto it = h->graphs.find(key);
         if (it == h->graphs.end()) {
@@ -774,10 +982,12 @@ struct Solver {
             it = h->graphs.emplace(key, std::make_pair(exec, kernels)).first;
             jac_cur = cur0;  // the host-side ping-pong state advances on replay below
             jac_other = other0;
+            captured = true;
         }
         ck(cudaGraphLaunch(it->second.first, s), "launch graph");
         add_launches(it->second.second);
         if (p->method == LAP_JACOBI && (steps & 1)) std::swap(jac_cur, jac_other);
+        return captured;
     }
 
     void run(lap_result* out)
@@ -803,16 +1013,35 @@ struct Solver {
                 ck(cudaMemsetAsync(w.levels[l].q, 0, (size_t)u.n * u.pitch * 8, s), "zero source");
             }
         }
-        if (p->method == LAP_MG_MIXED) {
+        if (p->method == LAP_MG_MIXED || p->method == LAP_MG_FP32) {
             for (const Level32& lv : w.levels32) {
                 ck(cudaMemsetAsync(lv.u.p, 0, (size_t)lv.u.n * lv.u.pitch * 4, s), "zero level");
                 ck(cudaMemsetAsync(lv.q, 0, (size_t)lv.u.n * lv.u.pitch * 4, s), "zero source");
+                if (lv.r) ck(cudaMemsetAsync(lv.r, 0, (size_t)lv.u.n * lv.u.pitch * 4, s), "zero level");
             }
+            fused32 = !p->unfused && fused32_supported(p->nu1, p->nu2);
+            if (fused32) ck(prepare_fused32(), "tile kernel attributes");
             const Level32& l0 = w.levels32[0];
-            ck(launch_defect64_to32(f, c, l0.q, l0.u.p, l0.u.pitch, w.partials, s),
-               "mixed residual kernel");
+            if (p->method == LAP_MG_MIXED) {
+                ck(launch_defect64_to32(f, c, l0.q, l0.u.p, l0.u.pitch, w.partials, s),
+                   "mixed residual kernel");
+            } else {
+                // FP32 alone: psi (ring included) rounded into level 0's two buffers, q = 0
+                ck(launch_to32(f, l0.u.p, l0.r, l0.u.pitch, s), "conversion kernel");
+                ck(launch_defect32_sumsq(l0.u, l0.q, c, w.partials, s), "residual kernel");
+            }
         }
-        const double r0 = p->method == LAP_MG_MIXED ? partial_norm(f) : residual(f, nullptr);
+        TailTuner* tuner = nullptr;
+        const bool fp32_norm = p->method == LAP_MG_MIXED || p->method == LAP_MG_FP32;
+        if (p->method == LAP_MG || fp32_norm) {
+            upload_tail();
+            const char kind = p->method == LAP_MG ? 'S' : (p->method == LAP_MG_MIXED ? 'M' : 'F');
+            tuner = &h->tail_tuners[tuner_key(kind, p, {f.m, f.n})];
+            if (tuner->cand.empty()) tuner->init(tail_candidates(false, kind != 'S', p->tail_size));
+        }
+        // the mixed iteration ends with the FP64 residual's partial sums; FP32 alone with
+        // its FP32 residual's
+        const double r0 = fp32_norm ? partial_norm(f) : residual(f, nullptr);
         out->r0 = r0;
         if (!std::isfinite(r0)) {
             out->status = LAP_DIVERGED;
@@ -827,7 +1056,25 @@ struct Solver {
             const bool fused_maxd = maxdelta && (p->method == LAP_JACOBI || p->method == LAP_GS_RB ||
                                                  p->method == LAP_SOR_RB || p->method == LAP_GS_LEX ||
                                                  p->method == LAP_SOR_LEX);
-            run_period(steps, maxdelta, fused_maxd);
+            if (tuner) {
+                // the tail size of this period: the next untried candidate while tuning; a
+                // period that captures its graph is not timed
+                const int cidx = tuner->next();
+                set_tail(tuner->cand[cidx]);
+                if (tuner->done) {
+                    run_period(steps, maxdelta, fused_maxd);
+                } else {
+                    ck(cudaEventRecord(tuner_event(h, 0), s), "record event");
+                    const bool captured = run_period(steps, maxdelta, fused_maxd);
+                    ck(cudaEventRecord(tuner_event(h, 1), s), "record event");
+                    ck(cudaEventSynchronize(tuner_event(h, 1)), "event sync");
+                    float ms = 0.f;
+                    ck(cudaEventElapsedTime(&ms, tuner_event(h, 0), tuner_event(h, 1)), "event time");
+                    if (!captured) tuner->record(cidx, ms / (double)steps);
+                }
+            } else {
+                run_period(steps, maxdelta, fused_maxd);
+            }
             k += steps;
             double val;
             bool conv;
@@ -838,8 +1085,10 @@ struct Solver {
                 conv = val <= p->tol;
             } else {
                 const Field cur{p->method == LAP_JACOBI ? jac_cur : f.p, f.m, f.n, f.pitch};
-                // the mixed iteration ends with the FP64 residual's partial sums
-                const double nr = p->method == LAP_MG_MIXED ? partial_norm(f) : residual(cur, nullptr);
+                if (p->method == LAP_MG_FP32)
+                    ck(launch_defect32_sumsq(w.levels32[0].u, w.levels32[0].q, c, w.partials, s),
+                       "residual kernel");
+                const double nr = fp32_norm ? partial_norm(f) : residual(cur, nullptr);
                 val = p->norm == LAP_NORM_L2_REL ? nr / r0 : nr;
                 conv = p->norm == LAP_NORM_L2_REL ? nr <= p->tol * r0 : nr <= p->tol;
             }
@@ -851,6 +1100,8 @@ struct Solver {
         }
         out->iters = k;
         if (p->method == LAP_JACOBI && jac_cur != f.p) copy_field(f.p, jac_cur);
+        if (p->method == LAP_MG_FP32)
+            ck(launch_to64(f, w.levels32[0].u.p, w.levels32[0].u.pitch, s), "conversion kernel");
         out->r_final = residual(f, nullptr);
     }
 };
@@ -869,22 +1120,108 @@ void add_items(std::vector<BatchItem>& items, int level_index, int m, int n)
     for (int r = 1; r <= n - 2; r += per) items.push_back(BatchItem{level_index, r, std::min(per, n - 1 - r)});
 }
 
-// Per-level work lists of one V-cycle over a set of problems: [first, count) into the items.
+// Per-level work lists of one V-cycle over a set of problems: [first, count) into the items
+// (fine, all, coarse) or into the tail jobs (tail).
 struct LevelLists {
-    std::vector<std::pair<int, int>> fine, all, coarse;
+    std::vector<std::pair<int, int>> fine, all, coarse, tail;
+    std::vector<std::pair<int, int>> tiles;  // FP32 tile items of the fine lists (fused cycle)
+    bool fused = false;
     int levels = 0;
     int max_coarse = 0;
 };
 
-// One V-cycle over every active problem of L: descend (coarsest solves when the descent
-// reaches a problem's coarsest level), then ascend; each problem sees its own V-cycle.
+// First level of a problem that the small-level tail runs (both sides <= tail_size), or
+// nlev when it has none.
+int tail_start(const BatchLevel<double>* lv, int nlev, int tail_size)
+{
+    if (tail_size <= 0) return nlev;
+    for (int l = 0; l < nlev; ++l)
+        if (lv[l].m <= tail_size && lv[l].n <= tail_size) return l;
+    return nlev;
+}
+
+// Lists of one V-cycle over problems `who`: problem q owns levels base[q] .. base[q] +
+// nlev[q] - 1 of lv. Levels above a problem's tail go through item lists, the tail is one job.
+// With tiles, the fine levels also get the tile items of the fused FP32 descent/ascent.
+void build_lists(LevelLists& L, std::vector<BatchItem>& items, std::vector<TailJob>& jobs,
+                 const std::vector<int>& who, const std::vector<int>& base,
+                 const std::vector<int>& nlev, const std::vector<BatchLevel<double>>& lv,
+                 int tail_size, std::vector<TileItem>* tiles = nullptr, int nu1 = 0, int nu2 = 0)
+{
+    L.fused = tiles != nullptr;
+    L.tiles.assign(0, {0, 0});
+    L.levels = 0;
+    for (int q : who) L.levels = std::max(L.levels, nlev[q]);
+    L.fine.assign(L.levels, {0, 0});
+    L.all.assign(L.levels, {0, 0});
+    L.coarse.assign(L.levels, {0, 0});
+    L.tail.assign(L.levels, {0, 0});
+    L.tiles.assign(L.levels, {0, 0});
+    std::vector<int> t(who.size());
+    for (size_t k = 0; k < who.size(); ++k) t[k] = tail_start(&lv[base[who[k]]], nlev[who[k]], tail_size);
+    for (int l = 0; l < L.levels; ++l) {
+        const int f0 = (int)items.size();
+        for (size_t k = 0; k < who.size(); ++k) {
+            const int q = who[k];
+            if (nlev[q] - 1 > l && l < t[k]) add_items(items, base[q] + l, lv[base[q] + l].m, lv[base[q] + l].n);
+        }
+        L.fine[l] = {f0, (int)items.size() - f0};
+        if (tiles) {
+            const int t0 = (int)tiles->size();
+            for (size_t k = 0; k < who.size(); ++k) {
+                const int q = who[k];
+                if (!(nlev[q] - 1 > l && l < t[k])) continue;
+                const BatchLevel<double>& d = lv[base[q] + l];
+                int tx, ty, ntx, nty;
+                fused32_tile(d.m, d.n, nu1, nu2, &tx, &ty, &ntx, &nty);
+                for (int by = 0; by < nty; ++by)
+                    for (int bx = 0; bx < ntx; ++bx)
+                        tiles->push_back(TileItem{base[q] + l, 1 + bx * tx, 1 + by * ty, tx, ty});
+            }
+            L.tiles[l] = {t0, (int)tiles->size() - t0};
+        }
+        const int a0 = (int)items.size();
+        for (size_t k = 0; k < who.size(); ++k) {
+            const int q = who[k];
+            if (nlev[q] > l && l <= t[k]) add_items(items, base[q] + l, lv[base[q] + l].m, lv[base[q] + l].n);
+        }
+        L.all[l] = {a0, (int)items.size() - a0};
+        const int c0 = (int)items.size();
+        for (size_t k = 0; k < who.size(); ++k) {
+            const int q = who[k];
+            if (nlev[q] - 1 == l && t[k] == nlev[q]) {
+                const BatchLevel<double>& d = lv[base[q] + l];
+                items.push_back(BatchItem{base[q] + l, 1, d.n - 2});
+                L.max_coarse = std::max(L.max_coarse, (d.m - 2) * (d.n - 2));
+            }
+        }
+        L.coarse[l] = {c0, (int)items.size() - c0};
+        const int j0 = (int)jobs.size();
+        for (size_t k = 0; k < who.size(); ++k) {
+            const int q = who[k];
+            if (t[k] == l && l < nlev[q]) {
+                jobs.push_back(TailJob{base[q] + l, base[q] + nlev[q] - 1});
+                const BatchLevel<double>& d = lv[base[q] + nlev[q] - 1];
+                L.max_coarse = std::max(L.max_coarse, (d.m - 2) * (d.n - 2));
+            }
+        }
+        L.tail[l] = {j0, (int)jobs.size() - j0};
+    }
+}
+
+// One V-cycle over every active problem of L: descend (coarsest solves and tails start when
+// the descent reaches a problem's coarsest or tail level), then ascend; each problem sees
+// its own V-cycle.
 template <class ListFn, class T>
 void enqueue_vcycle(ListFn list, const LevelLists& L, const BatchLevel<T>* lv, const int* active,
-                    const lap_params& p, double smoother_w, cudaStream_t st)
+                    const TailJob* jobs, const lap_params& p, double smoother_w, cudaStream_t st)
 {
     const bool gs = smoother_w == 1.0;
     for (int l = 0; l < L.levels; ++l) {
         ck(launch_b_coarse(list(L.coarse[l]), lv, active, L.max_coarse, st), "batched coarse");
+        ck(launch_b_tail(jobs + L.tail[l].first, L.tail[l].second, lv, active, p.nu1, p.nu2, gs,
+                         smoother_w, L.max_coarse, st),
+           "batched tail");
         if (l == L.levels - 1) break;
         for (int k = 0; k < p.nu1; ++k)
             for (int colour = 0; colour < 2; ++colour)
@@ -900,18 +1237,43 @@ void enqueue_vcycle(ListFn list, const LevelLists& L, const BatchLevel<T>* lv, c
     }
 }
 
+// The FP32 V-cycle with each fine level's descent and ascent as one tile launch over all
+// problems (first: the level-0 corrections start at zero).
+template <class ListFn>
+void enqueue_vcycle32_fused(ListFn list, const LevelLists& L, const BatchLevel<float>* lv,
+                            const int* active, const TailJob* jobs, const TileItem* tiles,
+                            const lap_params& p, double smoother_w, bool first, cudaStream_t st)
+{
+    const bool gs = smoother_w == 1.0;
+    for (int l = 0; l < L.levels; ++l) {
+        ck(launch_b_coarse(list(L.coarse[l]), lv, active, L.max_coarse, st), "batched coarse");
+        ck(launch_b_tail(jobs + L.tail[l].first, L.tail[l].second, lv, active, p.nu1, p.nu2, gs,
+                         smoother_w, L.max_coarse, st),
+           "batched tail");
+        if (l == L.levels - 1) break;
+        ck(launch_b_down32(tiles + L.tiles[l].first, L.tiles[l].second, lv, active, p.nu1,
+                           l > 0 || first, gs, smoother_w, st),
+           "batched descent");
+    }
+    for (int l = L.levels - 2; l >= 0; --l)
+        ck(launch_b_up32(tiles + L.tiles[l].first, L.tiles[l].second, lv, active, p.nu2, gs,
+                         smoother_w, st),
+           "batched ascent");
+}
+
 struct BatchPlan {
     std::vector<BatchLevel<double>> lv64;
     std::vector<BatchLevel<float>> lv32;
     std::vector<int> nlev, base;       // levels and first level index per problem
     std::vector<BatchItem> items;      // all work lists, back to back
-    std::vector<std::pair<int, int>> fine, all, coarse;  // per level: [first, count) into items
+    std::vector<TailJob> jobs;         // tail jobs of every candidate, back to back
+    std::vector<TileItem> tiles;       // FP32 tile items of every candidate (fused cycle)
+    std::vector<LevelLists> cands;     // the V-cycle's lists for each tail-size candidate
     std::pair<int, int> norm;          // level-0 items of every problem, problem by problem
     std::vector<int> first_item;       // per problem: its first item in the norm list (+ end)
     int max_coarse_unknowns = 0;
     int levels = 0;
 };
-
 
 
 }  // namespace
@@ -977,26 +1339,23 @@ extern "C" int lap_solve_batched(lap_handle h, int count, const lap_grid* grids,
                 n = (n - 1) / 2 + 1;
             }
         }
-        // ---- work lists ----
-        P.fine.resize(P.levels);
-        P.all.resize(P.levels);
-        P.coarse.resize(P.levels);
-        for (int l = 0; l < P.levels; ++l) {
-            const int f0 = (int)P.items.size();
-            for (int q = 0; q < count; ++q)
-                if (P.nlev[q] - 1 > l) add_items(P.items, P.base[q] + l, P.lv64[P.base[q] + l].m, P.lv64[P.base[q] + l].n);
-            P.fine[l] = {f0, (int)P.items.size() - f0};
-            const int a0 = (int)P.items.size();
-            for (int q = 0; q < count; ++q)
-                if (P.nlev[q] > l) add_items(P.items, P.base[q] + l, P.lv64[P.base[q] + l].m, P.lv64[P.base[q] + l].n);
-            P.all[l] = {a0, (int)P.items.size() - a0};
-            const int c0 = (int)P.items.size();
-            for (int q = 0; q < count; ++q)
-                if (P.nlev[q] - 1 == l) {
-                    const BatchLevel<double>& d = P.lv64[P.base[q] + l];
-                    P.items.push_back(BatchItem{P.base[q] + l, 1, d.n - 2});
-                }
-            P.coarse[l] = {c0, (int)P.items.size() - c0};
+        // ---- work lists: one set per tail-size candidate ----
+        std::vector<int> all_problems(count), shape;
+        for (int q = 0; q < count; ++q) {
+            all_problems[q] = q;
+            shape.push_back(grids[q].m);
+            shape.push_back(grids[q].n);
+        }
+        TailTuner& tuner = h->tail_tuners[tuner_key('B', p, shape)];
+        if (tuner.cand.empty()) tuner.init(tail_candidates(true, mixed, p->tail_size));
+        const bool fused = mixed && !p->unfused && fused32_supported(p->nu1, p->nu2);
+        if (fused) ck(prepare_fused32(), "tile kernel attributes");
+        for (int cand : tuner.cand) {
+            LevelLists L;
+            build_lists(L, P.items, P.jobs, all_problems, P.base, P.nlev, P.lv64, cand,
+                        fused ? &P.tiles : nullptr, p->nu1, p->nu2);
+            P.max_coarse_unknowns = std::max(P.max_coarse_unknowns, L.max_coarse);
+            P.cands.push_back(L);
         }
         const int n0 = (int)P.items.size();
         for (int q = 0; q < count; ++q) {
@@ -1032,6 +1391,8 @@ extern "C" int lap_solve_batched(lap_handle h, int count, const lap_grid* grids,
             auto* lv64 = cv.template take<BatchLevel<double>>(P.lv64.size());
             auto* lv32 = cv.template take<BatchLevel<float>>(P.lv32.size());
             auto* items = cv.template take<BatchItem>(P.items.size());
+            auto* jobs = cv.template take<TailJob>(std::max<size_t>(1, P.jobs.size()));
+            auto* tiles = cv.template take<TileItem>(std::max<size_t>(1, P.tiles.size()));
             auto* first = cv.template take<int>(P.first_item.size());
             auto* active = cv.template take<int>(count);
             auto* status = cv.template take<int>(count);
@@ -1040,14 +1401,14 @@ extern "C" int lap_solve_batched(lap_handle h, int count, const lap_grid* grids,
             auto* r0 = cv.template take<double>(count);
             auto* rnow = cv.template take<double>(count);
             auto* partials = cv.template take<double>(std::max(1, P.norm.second));
-            return std::make_tuple(lv64, lv32, items, first, active, status, remaining, iters, r0,
-                                   rnow, partials);
+            return std::make_tuple(lv64, lv32, items, jobs, tiles, first, active, status, remaining,
+                                   iters, r0, rnow, partials);
         };
         Sizer sz;
         carve_all(sz);
         Carver cv(arena(h, sz.off));
-        auto [lv64, lv32, items, first, active, status, remaining, iters, r0, rnow, partials] =
-            carve_all(cv);
+        auto [lv64, lv32, items, jobs, tiles, first, active, status, remaining, iters, r0, rnow,
+              partials] = carve_all(cv);
         // zero every level buffer (rings of corrections stay zero), then upload tables
         const size_t level_bytes = (size_t)((char*)lv64 - (char*)h->arena);
         if (level_bytes) ck(cudaMemsetAsync(h->arena, 0, level_bytes, s), "zero levels");
@@ -1056,6 +1417,10 @@ extern "C" int lap_solve_batched(lap_handle h, int count, const lap_grid* grids,
         ck(cudaMemcpyAsync(lv64, P.lv64.data(), P.lv64.size() * sizeof(P.lv64[0]), cudaMemcpyHostToDevice, s), "upload levels");
         ck(cudaMemcpyAsync(lv32, P.lv32.data(), P.lv32.size() * sizeof(P.lv32[0]), cudaMemcpyHostToDevice, s), "upload levels");
         ck(cudaMemcpyAsync(items, P.items.data(), P.items.size() * sizeof(BatchItem), cudaMemcpyHostToDevice, s), "upload items");
+        if (!P.jobs.empty())
+            ck(cudaMemcpyAsync(jobs, P.jobs.data(), P.jobs.size() * sizeof(TailJob), cudaMemcpyHostToDevice, s), "upload jobs");
+        if (!P.tiles.empty())
+            ck(cudaMemcpyAsync(tiles, P.tiles.data(), P.tiles.size() * sizeof(TileItem), cudaMemcpyHostToDevice, s), "upload tiles");
         ck(cudaMemcpyAsync(first, P.first_item.data(), P.first_item.size() * sizeof(int), cudaMemcpyHostToDevice, s), "upload items");
         ck(cudaMemcpyAsync(active, ones.data(), count * sizeof(int), cudaMemcpyHostToDevice, s), "upload flags");
         ck(cudaMemcpyAsync(status, ones.data(), count * sizeof(int), cudaMemcpyHostToDevice, s), "upload flags");
@@ -1065,32 +1430,21 @@ extern "C" int lap_solve_batched(lap_handle h, int count, const lap_grid* grids,
         auto list = [&](std::pair<int, int> r) { return BatchList{items + r.first, r.second}; };
         const BatchList norm_list = list(P.norm);
         const bool rel = p->norm == LAP_NORM_L2_REL;
-        // ---- one V-cycle over every active problem, in T precision ----
-        auto vcycle = [&](auto* lv, double smoother_w, cudaStream_t st) {
-            const bool gs = smoother_w == 1.0;
-            for (int l = 0; l < P.levels; ++l) {
-                ck(launch_b_coarse(list(P.coarse[l]), lv, active, P.max_coarse_unknowns, st), "batched coarse");
-                if (l == P.levels - 1) break;
-                for (int k = 0; k < p->nu1; ++k)
-                    for (int colour = 0; colour < 2; ++colour)
-                        ck(launch_b_rb(list(P.fine[l]), lv, active, colour, gs, smoother_w, st), "batched smoother");
-                ck(launch_b_defect(list(P.fine[l]), lv, active, st), "batched defect");
-                ck(launch_b_restrict(list(P.all[l + 1]), lv, active, st), "batched restrict");
-            }
-            for (int l = P.levels - 2; l >= 0; --l) {
-                ck(launch_b_prolong(list(P.fine[l]), lv, active, st), "batched prolong");
-                for (int k = 0; k < p->nu2; ++k)
-                    for (int colour = 0; colour < 2; ++colour)
-                        ck(launch_b_rb(list(P.fine[l]), lv, active, colour, gs, smoother_w, st), "batched smoother");
-            }
-        };
-        auto cycle = [&](cudaStream_t st) {
+        // ---- one cycle (V-cycle(s) and stopping test) with tail-size candidate c ----
+        auto cycle = [&](int c, cudaStream_t st) {
+            const LevelLists& L = P.cands[c];
             if (mixed) {
-                for (int k = 0; k < p->inner_cycles; ++k) vcycle(lv32, p->smoother_w, st);
+                for (int k = 0; k < p->inner_cycles; ++k) {
+                    if (L.fused)
+                        enqueue_vcycle32_fused(list, L, lv32, active, jobs, tiles, *p, p->smoother_w,
+                                               k == 0, st);
+                    else
+                        enqueue_vcycle(list, L, lv32, active, jobs, *p, p->smoother_w, st);
+                }
                 ck(launch_b_update(norm_list, lv64, active, lv32, st), "batched update");
                 ck(launch_b_sumsq(norm_list, lv64, active, partials, lv32, st), "batched residual");
             } else {
-                vcycle(lv64, p->smoother_w, st);
+                enqueue_vcycle(list, L, lv64, active, jobs, *p, p->smoother_w, st);
                 ck(launch_b_sumsq(norm_list, lv64, active, partials, nullptr, st), "batched residual");
             }
             ck(launch_b_converge(partials, first, count, active, r0, rnow, iters, status, remaining,
@@ -1100,30 +1454,42 @@ extern "C" int lap_solve_batched(lap_handle h, int count, const lap_grid* grids,
         ck(launch_b_sumsq(norm_list, lv64, active, partials, mixed ? lv32 : nullptr, s), "batched residual");
         ck(launch_b_converge(partials, first, count, active, r0, rnow, iters, status, remaining, 0,
                              rel, p->tol, s), "batched convergence");
-        // capture one cycle as a graph on the handle's stream, replay it on the caller's
-        cudaGraphExec_t exec = nullptr;
-        int64_t graph_kernels = 0;
-        if (h->use_graphs) {
-            if (!h->capture)
-                ck(cudaStreamCreateWithFlags(&h->capture, cudaStreamNonBlocking), "capture stream");
-            const int64_t before = launches_now();
-            ck(cudaStreamBeginCapture(h->capture, cudaStreamCaptureModeThreadLocal), "begin capture");
-            cudaGraph_t g = nullptr;
-            try {
-                cycle(h->capture);
-            } catch (...) {
-                cudaStreamEndCapture(h->capture, &g);
-                if (g) cudaGraphDestroy(g);
-                cudaGetLastError();
-                throw;
+        // one cycle per candidate as a graph, captured on the handle's stream when first
+        // used and replayed on the caller's
+        std::vector<std::pair<cudaGraphExec_t, int64_t>> exec(P.cands.size(), {nullptr, 0});
+        auto release = [&] {
+            for (auto& e : exec)
+                if (e.first) cudaGraphExecDestroy(e.first);
+        };
+        auto launch_cycle = [&](int c) {
+            if (!h->use_graphs) {
+                cycle(c, s);
+                return;
             }
-            ck(cudaStreamEndCapture(h->capture, &g), "end capture");
-            graph_kernels = launches_now() - before;
-            add_launches(-graph_kernels);
-            const cudaError_t e = cudaGraphInstantiate(&exec, g, 0);
-            cudaGraphDestroy(g);
-            ck(e, "instantiate graph");
-        }
+            if (!exec[c].first) {
+                if (!h->capture)
+                    ck(cudaStreamCreateWithFlags(&h->capture, cudaStreamNonBlocking), "capture stream");
+                const int64_t before = launches_now();
+                ck(cudaStreamBeginCapture(h->capture, cudaStreamCaptureModeThreadLocal), "begin capture");
+                cudaGraph_t g = nullptr;
+                try {
+                    cycle(c, h->capture);
+                } catch (...) {
+                    cudaStreamEndCapture(h->capture, &g);
+                    if (g) cudaGraphDestroy(g);
+                    cudaGetLastError();
+                    throw;
+                }
+                ck(cudaStreamEndCapture(h->capture, &g), "end capture");
+                exec[c].second = launches_now() - before;
+                add_launches(-exec[c].second);
+                const cudaError_t e = cudaGraphInstantiate(&exec[c].first, g, 0);
+                cudaGraphDestroy(g);
+                ck(e, "instantiate graph");
+            }
+            ck(cudaGraphLaunch(exec[c].first, s), "launch graph");
+            add_launches(exec[c].second);
+        };
         int64_t done = 0;
         int left = count;
         try {
@@ -1134,20 +1500,32 @@ extern "C" int lap_solve_batched(lap_handle h, int count, const lap_grid* grids,
                 if (left == 0) break;
                 const int64_t steps = std::min<int64_t>(p->check_every, p->max_iter - done);
                 for (int64_t k = 0; k < steps; ++k) {
-                    if (exec) {
-                        ck(cudaGraphLaunch(exec, s), "launch graph");
-                        add_launches(graph_kernels);
-                    } else {
-                        cycle(s);
+                    const int c = tuner.next();
+                    if (tuner.done) {
+                        launch_cycle(c);
+                        continue;
                     }
+                    // not tuned yet: time this cycle (the graph of c is captured before e0)
+                    if (h->use_graphs && !exec[c].first) {
+                        launch_cycle(c);  // first use captures and runs it once
+                        ck(cudaStreamSynchronize(s), "stream sync");
+                        continue;
+                    }
+                    ck(cudaEventRecord(tuner_event(h, 0), s), "record event");
+                    launch_cycle(c);
+                    ck(cudaEventRecord(tuner_event(h, 1), s), "record event");
+                    ck(cudaEventSynchronize(tuner_event(h, 1)), "event sync");
+                    float ms = 0.f;
+                    ck(cudaEventElapsedTime(&ms, tuner_event(h, 0), tuner_event(h, 1)), "event time");
+                    tuner.record(c, ms);
                 }
                 done += steps;
             }
         } catch (...) {
-            if (exec) cudaGraphExecDestroy(exec);
+            release();
             throw;
         }
-        if (exec) cudaGraphExecDestroy(exec);
+        release();
         // ---- results ----
         std::vector<long long> it(count);
         std::vector<int> st(count);
@@ -1286,10 +1664,17 @@ void srv_levels(lap_server S, SrvRequest& r, C& cv)
     }
 }
 
+// Small-level tail sizes of the server's V-cycles (one CTA per request runs its levels at
+// or below the size).
+constexpr int SERVER_TAIL_FP64 = 33;
+constexpr int SERVER_TAIL_FP32 = 129;
+
 struct SrvPlan {
     std::vector<BatchLevel<double>> lv64;
     std::vector<BatchLevel<float>> lv32;
     std::vector<BatchItem> items;
+    std::vector<TailJob> jobs;
+    std::vector<TileItem> tiles;
     LevelLists mg64, mg32;
     std::pair<int, int> sor, update, init, norm;
     std::vector<int> first_init, first_norm;
@@ -1430,31 +1815,19 @@ extern "C" int lap_server_step(lap_server S, void* stream, int* running, int* qu
                 P.lv32.push_back(f);
             }
         }
+        std::vector<int> nlev(R);
+        for (int q = 0; q < R; ++q) nlev[q] = run[q]->nlev;
         auto mg_lists = [&](int method, LevelLists& L) {
             std::vector<int> who;
             for (int q = 0; q < R; ++q)
                 if (run[q]->method == method) who.push_back(q);
-            for (int q : who) L.levels = std::max(L.levels, run[q]->nlev);
-            L.fine.resize(L.levels);
-            L.all.resize(L.levels);
-            L.coarse.resize(L.levels);
-            for (int l = 0; l < L.levels; ++l) {
-                const int f0 = (int)P.items.size();
-                for (int q : who)
-                    if (run[q]->nlev - 1 > l) add_items(P.items, base[q] + l, run[q]->lv64[l].m, run[q]->lv64[l].n);
-                L.fine[l] = {f0, (int)P.items.size() - f0};
-                const int a0 = (int)P.items.size();
-                for (int q : who)
-                    if (run[q]->nlev > l) add_items(P.items, base[q] + l, run[q]->lv64[l].m, run[q]->lv64[l].n);
-                L.all[l] = {a0, (int)P.items.size() - a0};
-                const int c0 = (int)P.items.size();
-                for (int q : who)
-                    if (run[q]->nlev - 1 == l) {
-                        P.items.push_back(BatchItem{base[q] + l, 1, run[q]->lv64[l].n - 2});
-                        L.max_coarse = std::max(L.max_coarse, (run[q]->lv64[l].m - 2) * (run[q]->lv64[l].n - 2));
-                    }
-                L.coarse[l] = {c0, (int)P.items.size() - c0};
-            }
+            // no timing across steps (the running set changes): fixed tail sizes
+            const int ts = S->mg.tail_size != 0 ? S->mg.tail_size
+                                                : (method == LAP_MG_MIXED ? SERVER_TAIL_FP32 : SERVER_TAIL_FP64);
+            const bool fused = method == LAP_MG_MIXED && !S->mg.unfused &&
+                               fused32_supported(S->mg.nu1, S->mg.nu2);
+            build_lists(L, P.items, P.jobs, who, base, nlev, P.lv64, ts, fused ? &P.tiles : nullptr,
+                        S->mg.nu1, S->mg.nu2);
         };
         mg_lists(LAP_MG, P.mg64);
         mg_lists(LAP_MG_MIXED, P.mg32);
@@ -1484,6 +1857,8 @@ extern "C" int lap_server_step(lap_server S, void* stream, int* running, int* qu
             auto* lv64 = cv.template take<BatchLevel<double>>(P.lv64.size());
             auto* lv32 = cv.template take<BatchLevel<float>>(P.lv32.size());
             auto* items = cv.template take<BatchItem>(std::max<size_t>(1, P.items.size()));
+            auto* jobs = cv.template take<TailJob>(std::max<size_t>(1, P.jobs.size()));
+            auto* tiles = cv.template take<TileItem>(std::max<size_t>(1, P.tiles.size()));
             auto* fi = cv.template take<int>(P.first_init.size());
             auto* fn = cv.template take<int>(P.first_norm.size());
             auto* active = cv.template take<int>(R);
@@ -1495,8 +1870,8 @@ extern "C" int lap_server_step(lap_server S, void* stream, int* running, int* qu
             auto* dtol = cv.template take<double>(R);
             auto* pinit = cv.template take<double>(std::max(1, P.init.second));
             auto* pnorm = cv.template take<double>(std::max(1, P.norm.second));
-            return std::make_tuple(lv64, lv32, items, fi, fn, active, status, remaining, iters, dr0,
-                                   rnow, dtol, pinit, pnorm);
+            return std::make_tuple(lv64, lv32, items, jobs, tiles, fi, fn, active, status, remaining,
+                                   iters, dr0, rnow, dtol, pinit, pnorm);
         };
         Sizer sz;
         carve_stage(sz);
@@ -1509,14 +1884,17 @@ extern "C" int lap_server_step(lap_server S, void* stream, int* running, int* qu
             S->stage_bytes = nb;
         }
         Carver cv(S->stage);
-        auto [lv64, lv32, items, fi, fn, active, status, remaining, iters, dr0, rnow, dtol, pinit, pnorm] =
-            carve_stage(cv);
+        auto [lv64, lv32, items, jobs, tiles, fi, fn, active, status, remaining, iters, dr0, rnow, dtol,
+              pinit, pnorm] = carve_stage(cv);
         auto up = [&](void* dst, const void* src, size_t bytes) {
             if (bytes) ck(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st), "upload plan");
         };
         up(lv64, P.lv64.data(), P.lv64.size() * sizeof(P.lv64[0]));
         up(lv32, P.lv32.data(), P.lv32.size() * sizeof(P.lv32[0]));
         up(items, P.items.data(), P.items.size() * sizeof(BatchItem));
+        up(jobs, P.jobs.data(), P.jobs.size() * sizeof(TailJob));
+        up(tiles, P.tiles.data(), P.tiles.size() * sizeof(TileItem));
+        if (P.mg32.fused) ck(prepare_fused32(), "tile kernel attributes");
         up(fi, P.first_init.data(), P.first_init.size() * sizeof(int));
         up(fn, P.first_norm.data(), P.first_norm.size() * sizeof(int));
         up(active, act.data(), R * sizeof(int));
@@ -1530,9 +1908,14 @@ extern "C" int lap_server_step(lap_server S, void* stream, int* running, int* qu
         ck(launch_b_sumsq(list(P.init), lv64, active, pinit, lv32, st), "server residual");
         ck(launch_b_converge(pinit, fi, R, active, dr0, rnow, iters, status, remaining, 0, true, 0.0,
                              st, dtol), "server convergence");
-        enqueue_vcycle(list, P.mg64, lv64, active, S->mg, S->mg.smoother_w, st);
-        for (int k = 0; k < S->mg.inner_cycles && P.mg32.levels; ++k)
-            enqueue_vcycle(list, P.mg32, lv32, active, S->mg, S->mg.smoother_w, st);
+        enqueue_vcycle(list, P.mg64, lv64, active, jobs, S->mg, S->mg.smoother_w, st);
+        for (int k = 0; k < S->mg.inner_cycles && P.mg32.levels; ++k) {
+            if (P.mg32.fused)
+                enqueue_vcycle32_fused(list, P.mg32, lv32, active, jobs, tiles, S->mg, S->mg.smoother_w,
+                                       k == 0, st);
+            else
+                enqueue_vcycle(list, P.mg32, lv32, active, jobs, S->mg, S->mg.smoother_w, st);
+        }
         ck(launch_b_update(list(P.update), lv64, active, lv32, st), "server update");
         for (int k = 0; k < S->sor_sweeps && P.sor.second; ++k)
             for (int colour = 0; colour < 2; ++colour)
@@ -1628,6 +2011,8 @@ void lap_destroy(lap_handle h)
     for (auto& kv : h->coarse) dev_free(h, kv.second.dev, kv.second.bytes);
     drop_graphs(h);
     if (h->capture) cudaStreamDestroy(h->capture);
+    for (cudaEvent_t e : h->ev)
+        if (e) cudaEventDestroy(e);
     dev_free(h, h->arena, h->arena_bytes);
     if (h->pinned) cudaFreeHost(h->pinned);
     delete h;
@@ -1654,7 +2039,7 @@ int lap_solve(lap_handle h, const lap_grid* g, double* psi_dev, const lap_params
         set_device(h);
         check_device_ptr(h, psi_dev, "psi");
         Solver sv{h, (cudaStream_t)stream, Field{psi_dev, g->m, g->n, g->pitch}, make_coef(g->dx, g->dy), p, {}};
-        if (p->method == LAP_MG || p->method == LAP_MG_MIXED) {
+        if (p->method == LAP_MG || p->method == LAP_MG_MIXED || p->method == LAP_MG_FP32) {
             const int L = mg_level_count(g->m, g->n, p->coarsest_min, p->max_levels);
             int m = g->m, n = g->n;
             for (int l = 1; l < L; ++l) {

@@ -84,6 +84,12 @@ cudaError_t launch_coarse32(const Field32& u, const float* q, const double* ainv
 // (the same blocks and order as launch_defect_sumsq, so the sums are identical).
 cudaError_t launch_defect64_to32(const Field& psi, const Coef& c, float* r32, float* e32,
                                  int64_t pitch32, double* partials, cudaStream_t s);
+// FP32 alone: a (and b, nullable) := psi rounded to FP32 on every node; psi interior :=
+// (double) u; per-block FP64 sums of the squared FP32 residual (mixed_norm_blocks blocks).
+cudaError_t launch_to32(const Field& psi, float* a, float* b, int64_t pitch32, cudaStream_t s);
+cudaError_t launch_to64(const Field& psi, const float* u, int64_t pitch32, cudaStream_t s);
+cudaError_t launch_defect32_sumsq(const Field32& f, const float* q, const Coef& c, double* partials,
+                                  cudaStream_t s);
 // psi += (double) e32 on interior nodes.
 cudaError_t launch_update64(const Field& psi, const float* e32, int64_t pitch32, cudaStream_t s);
 
@@ -121,6 +127,10 @@ struct BatchList {
     const BatchItem* items;
     int count;
 };
+// The small-level tail of one problem's V-cycle: levels first .. last (its coarsest) of lv.
+struct TailJob {
+    int first, last;
+};
 // per_level_w: Eq. 7 with each level's own w (BatchLevel::w) instead of the argument
 template <class T>
 cudaError_t launch_b_rb(const BatchList& l, const BatchLevel<T>* lv, const int* active, int colour,
@@ -139,6 +149,13 @@ cudaError_t launch_b_prolong(const BatchList& l, const BatchLevel<T>* lv, const 
 template <class T>
 cudaError_t launch_b_coarse(const BatchList& l, const BatchLevel<T>* lv, const int* active,
                             int max_unknowns, cudaStream_t s);
+// One CTA per job runs the V-cycle from level `first` down to the coarsest and back (nu1/nu2
+// smoothing sweeps, gs or SOR with w, or each level's own w); active may be null (all run).
+// max_unknowns: the largest coarsest level among the jobs.
+template <class T>
+cudaError_t launch_b_tail(const TailJob* jobs, int count, const BatchLevel<T>* lv, const int* active,
+                          int nu1, int nu2, bool gs, double w, int max_unknowns, cudaStream_t s,
+                          bool per_level_w = false);
 // per-item FP64 sum of squares of the residual; with lv32 also r32 := residual, e32 := 0
 cudaError_t launch_b_sumsq(const BatchList& l, const BatchLevel<double>* lv, const int* active,
                            double* partials, const BatchLevel<float>* lv32, cudaStream_t s);
@@ -150,6 +167,27 @@ cudaError_t launch_b_converge(const double* partials, const int* first_item, int
                               double* r0, double* rnow, long long* iters, int* status,
                               int* remaining, int mode, bool rel, double tol, cudaStream_t s,
                               const double* tolv = nullptr);
+
+// ---- the FP32 cycle's levels in two tile passes (fused32_kernels.cu) --------------
+// One tile of owned points [x0, x0 + tx) x [y0, y0 + ty) of level `level` of lv.
+struct TileItem {
+    int level, x0, y0, tx, ty;
+};
+// Whether nu1, nu2 sweeps fit the tile halos; tiles of a level: ntx x nty of tx x ty.
+bool fused32_supported(int nu1, int nu2);
+void fused32_tile(int m, int n, int nu1, int nu2, int* tx, int* ty, int* ntx, int* nty);
+cudaError_t prepare_fused32();  // shared-memory limit of the tile kernels (outside capture)
+// Descent of level F: nu1 sweeps on u (F.u, or zeros), smoothed u -> F.r, C.q := restricted
+// residual, C.u := 0. Ascent: F.u := smoothed (F.r + P C.u) after nu2 sweeps.
+cudaError_t launch_down32(const BatchLevel<float>& F, const BatchLevel<float>& C, int nu1, int nu2,
+                          bool zero_u, bool gs, double w, cudaStream_t s);
+cudaError_t launch_up32(const BatchLevel<float>& F, const BatchLevel<float>& C, int nu1, int nu2,
+                        bool gs, double w, cudaStream_t s);
+// The same over tile items of many problems (the coarse level of item level l is l + 1).
+cudaError_t launch_b_down32(const TileItem* items, int count, const BatchLevel<float>* lv,
+                            const int* active, int nu1, bool zero_u, bool gs, double w, cudaStream_t s);
+cudaError_t launch_b_up32(const TileItem* items, int count, const BatchLevel<float>* lv,
+                          const int* active, int nu2, bool gs, double w, cudaStream_t s);
 
 // ---- line relaxation (line_kernels.cu) --------------------------------------------
 // Constant-coefficient tridiagonal systems -alpha x_{k-1} + delta x_k - alpha x_{k+1} = r_k,

@@ -168,9 +168,89 @@ __global__ void __launch_bounds__(PX* PY)
     *c = fadd(o, *c, (double)e32[(int64_t)j * pitch32 + i]);
 }
 
+// ---- FP32 alone (the comparison point of the mixed solver) ----
+
+// u32 := psi rounded to FP32 on every node (ring included), into two buffers.
+__global__ void __launch_bounds__(PX* PY)
+    to32_kernel(const double* __restrict__ psi, int m, int n, int64_t pitch, float* __restrict__ a,
+                float* __restrict__ b, int64_t pitch32)
+{
+    const int j = blockIdx.y * PY + threadIdx.y;
+    const int i = blockIdx.x * PX + threadIdx.x;
+    if (j > n - 1 || i > m - 1) return;
+    const float v = __double2float_rn(psi[(int64_t)j * pitch + i]);
+    a[(int64_t)j * pitch32 + i] = v;
+    if (b) b[(int64_t)j * pitch32 + i] = v;
+}
+
+// psi := (double) u32 on interior nodes.
+__global__ void __launch_bounds__(PX* PY)
+    to64_kernel(double* __restrict__ psi, int m, int n, int64_t pitch, const float* __restrict__ u,
+                int64_t pitch32)
+{
+    const int j = 1 + blockIdx.y * PY + threadIdx.y;
+    const int i = 1 + blockIdx.x * PX + threadIdx.x;
+    if (j > n - 2 || i > m - 2) return;
+    psi[(int64_t)j * pitch + i] = (double)u[(int64_t)j * pitch32 + i];
+}
+
+// Per-block sums (FP64) of the squared FP32 residual r = (E+W) + b2 (N+S) + q - d u.
+template <bool UNIT>
+__global__ void __launch_bounds__(NORM_THREADS)
+    defect32_sumsq_kernel(const float* __restrict__ u, const float* __restrict__ q, int m, int n,
+                          int64_t pitch, float b2, float d, double* __restrict__ partials)
+{
+    double acc = 0.0;
+    for (int j = 1 + blockIdx.x; j <= n - 2; j += gridDim.x)
+        for (int i = 1 + threadIdx.x; i <= m - 2; i += NORM_THREADS) {
+            const int64_t at = (int64_t)j * pitch + i;
+            const float* c = u + at;
+            const float s = __fadd_rn(nsum32(c[-1], c[1], c[-pitch], c[pitch], b2, UNIT), q[at]);
+            const double r = (double)__fmaf_rn(-d, *c, s);
+            acc = __fma_rn(r, r, acc);
+        }
+    __shared__ double red[NORM_THREADS / 32];
+    acc = warp_sum(acc);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double v = threadIdx.x < NORM_THREADS / 32 ? red[threadIdx.x] : 0.0;
+        v = warp_sum(v);
+        if (threadIdx.x == 0) partials[blockIdx.x] = v;
+    }
+}
+
 }  // namespace
 
-int mixed_norm_blocks(int n) { return n - 2 < NORM_MAX_BLOCKS ? n - 2 : NORM_MAX_BLOCKS; }
+cudaError_t launch_to32(const Field& psi, float* a, float* b, int64_t pitch32, cudaStream_t s)
+{
+    const dim3 grid((psi.m + PX - 1) / PX, (psi.n + PY - 1) / PY), block(PX, PY);
+    to32_kernel<<<grid, block, 0, s>>>(psi.p, psi.m, psi.n, psi.pitch, a, b, pitch32);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_to64(const Field& psi, const float* u, int64_t pitch32, cudaStream_t s)
+{
+    const dim3 grid((psi.m - 2 + PX - 1) / PX, (psi.n - 2 + PY - 1) / PY), block(PX, PY);
+    to64_kernel<<<grid, block, 0, s>>>(psi.p, psi.m, psi.n, psi.pitch, u, pitch32);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_defect32_sumsq(const Field32& f, const float* q, const Coef& c, double* partials,
+                                  cudaStream_t s)
+{
+    const int blocks = mixed_norm_blocks(f.n);
+    if (c.unit_beta)
+        defect32_sumsq_kernel<true><<<blocks, NORM_THREADS, 0, s>>>(f.p, q, f.m, f.n, f.pitch, (float)c.b2, (float)c.d, partials);
+    else
+        defect32_sumsq_kernel<false><<<blocks, NORM_THREADS, 0, s>>>(f.p, q, f.m, f.n, f.pitch, (float)c.b2, (float)c.d, partials);
+    note_launch();
+    return cudaGetLastError();
+}
+
+int mixed_norm_blocks(int n) { return n - 2 < NORM_MAX_BLOCKS ? (n - 2 > 0 ? n - 2 : 1) : NORM_MAX_BLOCKS; }
 
 cudaError_t launch_rb32(const Field32& f, const float* q, const Coef& c, bool gs, double w,
                         int colour, cudaStream_t s)

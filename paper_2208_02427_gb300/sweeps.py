@@ -3,8 +3,10 @@
     python -m paper_2208_02427_gb300.sweeps --method sor --m 4097 --n 4097 --iters 20
 
 Methods: jacobi, gs, sor (one red-black sweep = 2 launches), residual, adi-x, adi-y
-(zebra half sweeps), restrict, prolong, mg (one V(2,2) cycle). Used for profiling a
-single kernel under ncu: small launch counts, the same kernels the solver runs.
+(zebra half sweeps), restrict, prolong, mg (one V(2,2) cycle), mg_mixed (one FP32
+V(2,2) cycle inside one FP64 defect-correction step), batched / batched_mixed (one cycle
+of --count uneven grids, 33..513 per side, through lap_solve_batched). Used for profiling
+a single kernel under ncu: small launch counts, the same kernels the solver runs.
 """
 from __future__ import annotations
 
@@ -25,6 +27,11 @@ def main():
     ap.add_argument("--iters", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=2)
     ap.add_argument("--w", type=float, default=None)
+    ap.add_argument("--count", type=int, default=4096, help="problems for batched methods")
+    ap.add_argument("--tail", type=int, default=0,
+                    help="V-cycle small-level tail size (0 = timed choice, -1 = none)")
+    ap.add_argument("--unfused", action="store_true",
+                    help="FP32 cycle: one kernel per pass instead of the tile kernels")
     a = ap.parse_args()
     m, n = a.m, a.n
     h = 1.0 / (m - 1)
@@ -44,8 +51,18 @@ def main():
         "adi-y": lambda: lap.line_sweep(u, 1.3, "A", 1, h, h),
         "restrict": lambda: b.restrict(u, qc, other, ec=ec, dx=h, dy=h),
         "prolong": lambda: b.prolong_add(u, ec, h, h),
-        "mg": lambda: lap.solve(u, h, h, method="mg", tol=0.0, max_iter=1),
+        "mg": lambda: lap.solve(u, h, h, method="mg", tol=0.0, max_iter=1, tail_size=a.tail),
+        "mg_mixed": lambda: lap.solve(u, h, h, method="mg_mixed", tol=0.0, max_iter=1,
+                                      tail_size=a.tail, unfused=a.unfused),
     }
+    if a.method.startswith("batched"):
+        shapes = wl.batch_shapes(a.count, seed=wl.SEED_BASE + 2)
+        fields = [b.to_field(wl.random_ring(bm, bn, seed=wl.SEED_BASE + 2 + 10 * k))
+                  for k, (bm, bn) in enumerate(shapes)]
+        meth = "mg_mixed" if a.method == "batched_mixed" else "mg"
+        ops[a.method] = lambda: lap.solve_batched(fields, 1.0, 1.0, method=meth, tol=0.0,
+                                                  max_iter=1, tail_size=a.tail,
+                                                  unfused=a.unfused)
     fn = ops[a.method]
     for _ in range(a.warmup):
         fn()

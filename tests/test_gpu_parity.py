@@ -377,6 +377,8 @@ def test_host_buffer_solve_equals_device_solve(lap, b):
 def test_graph_replay_equals_direct_launches(b, kw):
     kw = dict(kw)
     kw.setdefault("tol", 0.0)
+    if kw["method"] == "mg":
+        kw["tail_size"] = -1  # a fixed launch structure (the timed choice varies per period)
     psi = rand_field(65, 33, 21)
     outs = []
     t = b.field(65, 33)  # one field: the third solve replays the graph the second captured
