@@ -132,47 +132,66 @@ __device__ __forceinline__ void half_range(int lx_lo, int lx_hi, int half, int* 
     *c_hi = (lx_hi - half) >> 1;
 }
 
-// West and east neighbours of the pair at indices c0, c0 + 1 of half `half` of a row:
-// the other half holds them at c - 1 + half and c + half.
-__device__ __forceinline__ void west_east(const float* other, int c0, int half, float2* w_, float2* e_)
+__device__ __forceinline__ float4 lds4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+
+// Stores the components of v at p[0..3] whose index lies in [lo, hi] (16-byte store when all do).
+__device__ __forceinline__ void sts4_masked(float* p, float4 v, int c0, int lo, int hi)
 {
-    if (half == 0) {
-        const float a = other[c0 - 1];
-        const float2 b = lds2(other + c0);
-        *w_ = make_float2(a, b.x);
-        *e_ = b;
-    } else {
-        const float2 a = lds2(other + c0);
-        const float b = other[c0 + 2];
-        *w_ = a;
-        *e_ = make_float2(a.y, b);
+    if (c0 >= lo && c0 + 3 <= hi) {
+        *reinterpret_cast<float4*>(p) = v;
+        return;
     }
+    if (c0 >= lo && c0 <= hi) p[0] = v.x;
+    if (c0 + 1 >= lo && c0 + 1 <= hi) p[1] = v.y;
+    if (c0 + 2 >= lo && c0 + 2 <= hi) p[2] = v.z;
+    if (c0 + 3 >= lo && c0 + 3 <= hi) p[3] = v.w;
+}
+
+// s = (E+W) + b2 (N+S) + q for the four points c0 .. c0 + 3 of half `half` of region row ly,
+// as two float2 (points c0, c0 + 1 and c0 + 2, c0 + 3). Their west/east neighbours are in the
+// other half of the row at c - 1 + half and c + half.
+__device__ __forceinline__ void stencil4(const float* su, const float* sq, int ly, int half, int c0,
+                                         const Coef32& k, float2& sA, float2& sB)
+{
+    const float* oth = su + ly * FT_RS + (1 - half) * FT_HS;
+    const int a = ly * FT_RS + half * FT_HS + c0;
+    const float4 o = lds4(oth + c0);
+    const float ol = oth[c0 - 1], orr = oth[c0 + 4];
+    const bool h = half != 0;
+    const float2 wA = make_float2(h ? o.x : ol, h ? o.y : o.x);
+    const float2 wB = make_float2(h ? o.z : o.y, h ? o.w : o.z);
+    const float2 eA = make_float2(h ? o.y : o.x, h ? o.z : o.y);
+    const float2 eB = make_float2(h ? o.w : o.z, h ? orr : o.w);
+    const float4 S = lds4(su + a - FT_RS), N = lds4(su + a + FT_RS), Q = lds4(sq + a);
+    sA = __fadd2_rn(nsum2(wA, eA, make_float2(S.x, S.y), make_float2(N.x, N.y), k), make_float2(Q.x, Q.y));
+    sB = __fadd2_rn(nsum2(wB, eB, make_float2(S.z, S.w), make_float2(N.z, N.w), k), make_float2(Q.z, Q.w));
 }
 
 // One colour pass of Eq. 6 (gs) or Eq. 7 over the domain-interior points of the region
 // but its outer ring: points (gx + gy) % 2 == colour, i.e. half (colour + gy) & 1 of row
-// gy. Rows over warps, one pair of points per lane (a half row holds at most 64 points).
+// gy. Each half warp takes a row, each lane four consecutive points of its half row.
 __device__ __forceinline__ void colour_pass(float* su, const float* sq, const Region& R, int m, int n,
                                             int colour, const Coef32& k)
 {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int lx_lo = max(1, 1 - R.gx0), lx_hi = min(R.w - 2, m - 2 - R.gx0);
     const int ly_lo = max(1, 1 - R.gy0), ly_hi = min(R.h - 2, n - 2 - R.gy0);
-    const int c0 = 2 * lane;
-    for (int ly = ly_lo + wid; ly <= ly_hi; ly += FT_NW) {
+    const int c0 = 4 * (lane & 15);
+    for (int ly = ly_lo + 2 * wid + (lane >> 4); ly <= ly_hi; ly += 2 * FT_NW) {
         const int half = (colour + R.gy0 + ly) & 1;
         int c_lo, c_hi;
         half_range(lx_lo, lx_hi, half, &c_lo, &c_hi);
-        if (c0 + 1 < c_lo || c0 > c_hi) continue;
-        float* row = su + ly * FT_RS;
-        const int a = ly * FT_RS + half * FT_HS + c0;
-        float2 w_, e_;
-        west_east(row + (1 - half) * FT_HS, c0, half, &w_, &e_);
-        const float2 s = __fadd2_rn(nsum2(w_, e_, lds2(su + a - FT_RS), lds2(su + a + FT_RS), k),
-                                    lds2(sq + a));
-        const float2 g = __fmul2_rn(s, k.inv_d);
-        const float2 v = k.gs ? g : __ffma2_rn(k.w, g, __fmul2_rn(k.omw, lds2(su + a)));
-        sts2_masked(su + a, v, c0 >= c_lo, c0 + 1 <= c_hi);
+        if (c0 + 3 < c_lo || c0 > c_hi) continue;
+        float2 sA, sB;
+        stencil4(su, sq, ly, half, c0, k, sA, sB);
+        float* at = su + ly * FT_RS + half * FT_HS + c0;
+        float2 gA = __fmul2_rn(sA, k.inv_d), gB = __fmul2_rn(sB, k.inv_d);
+        if (!k.gs) {
+            const float4 old = lds4(at);
+            gA = __ffma2_rn(k.w, gA, __fmul2_rn(k.omw, make_float2(old.x, old.y)));
+            gB = __ffma2_rn(k.w, gB, __fmul2_rn(k.omw, make_float2(old.z, old.w)));
+        }
+        sts4_masked(at, make_float4(gA.x, gA.y, gB.x, gB.y), c0, c_lo, c_hi);
     }
 }
 
@@ -234,20 +253,20 @@ __device__ __forceinline__ void down_tile(const BatchLevel<float>& F, const Batc
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int lx_lo = max(1, x0 - 1) - R.gx0, lx_hi = min(m - 2, x1) - R.gx0;
     const int ly_lo = max(1, y0 - 1) - R.gy0, ly_hi = min(n - 2, y1) - R.gy0;
-    const int c0 = 2 * lane;
-    for (int t = wid; t <= 2 * (ly_hi - ly_lo) + 1; t += FT_NW) {
+    const int c0 = 4 * (lane & 15);
+    const float2 nd = make_float2(-k.d.x, -k.d.y);
+    for (int t = 2 * wid + (lane >> 4); t <= 2 * (ly_hi - ly_lo) + 1; t += 2 * FT_NW) {
         const int ly = ly_lo + (t >> 1), half = t & 1;
         int c_lo, c_hi;
         half_range(lx_lo, lx_hi, half, &c_lo, &c_hi);
-        if (c0 + 1 < c_lo || c0 > c_hi) continue;
-        const float* row = su + ly * FT_RS;
+        if (c0 + 3 < c_lo || c0 > c_hi) continue;
+        float2 sA, sB;
+        stencil4(su, sq, ly, half, c0, k, sA, sB);
         const int a = ly * FT_RS + half * FT_HS + c0;
-        float2 w_, e_;
-        west_east(row + (1 - half) * FT_HS, c0, half, &w_, &e_);
-        const float2 s = __fadd2_rn(nsum2(w_, e_, lds2(su + a - FT_RS), lds2(su + a + FT_RS), k),
-                                    lds2(sq + a));
-        const float2 r = __ffma2_rn(make_float2(-k.d.x, -k.d.y), lds2(su + a), s);
-        sts2_masked(sq + a, r, c0 >= c_lo, c0 + 1 <= c_hi);
+        const float4 u4 = lds4(su + a);
+        const float2 rA = __ffma2_rn(nd, make_float2(u4.x, u4.y), sA);
+        const float2 rB = __ffma2_rn(nd, make_float2(u4.z, u4.w), sB);
+        sts4_masked(sq + a, make_float4(rA.x, rA.y, rB.x, rB.y), c0, c_lo, c_hi);
     }
     __syncthreads();
     // restriction to the coarse points (I, J) with (2I, 2J) owned: the centre is at half 0,
@@ -277,9 +296,12 @@ __device__ __forceinline__ void down_tile(const BatchLevel<float>& F, const Batc
 // Ascent on one tile of level F: u (from F.r) plus the bilinear interpolation of C.u, nu2
 // smoothing sweeps, the owned points to F.u. The coarse points under the region are staged
 // in shared memory (sc): a column pair p of the region lies over coarse column gx0 / 2 + p.
+// With psi (the FP64 field of the mixed solver's level 0), the last ascent adds its result
+// to psi in FP64 (psi += e, the update of the defect correction) instead of storing e.
 __device__ __forceinline__ void up_tile(const BatchLevel<float>& F, const BatchLevel<float>& C,
                                         int x0, int y0, int tx, int ty, int nu2, const Coef32& k,
-                                        float* su, float* sq, float* sc)
+                                        float* su, float* sq, float* sc, double* psi,
+                                        int64_t psi_pitch)
 {
     const int m = F.m, n = F.n;
     const Region R = region_of(x0, y0, tx, ty, 2 * nu2);
@@ -325,7 +347,49 @@ __device__ __forceinline__ void up_tile(const BatchLevel<float>& F, const BatchL
     }
     __syncthreads();
     smooth_region(su, sq, R, m, n, nu2, k);
-    store_owned(F.u, F.pitch, su, R, x0, min(x0 + tx, m - 1), y0, min(y0 + ty, n - 1));
+    const int x1 = min(x0 + tx, m - 1), y1 = min(y0 + ty, n - 1);
+    if (!psi) {
+        store_owned(F.u, F.pitch, su, R, x0, x1, y0, y1);
+        return;
+    }
+    // column pairs (gx even: 16-byte aligned double2 when the pitch is even), two per lane,
+    // so that each thread has four FP64 loads in flight per row
+    const FmaOps o = load_fma_ops();
+    const int p_lo = (x0 - R.gx0) >> 1, p_hi = (x1 - 1 - R.gx0) >> 1;
+    const bool even_pitch = (psi_pitch & 1) == 0;
+    for (int gy = y0 + wid; gy < y1; gy += FT_NW) {
+        const float* row = su + (gy - R.gy0) * FT_RS;
+        double* prow = psi + (int64_t)gy * psi_pitch;
+        double2 v[2];
+        bool lo[2], hi[2];
+#pragma unroll
+        for (int s2 = 0; s2 < 2; ++s2) {
+            const int p = p_lo + lane + 32 * s2;
+            const int gx = R.gx0 + 2 * p;
+            lo[s2] = p <= p_hi && gx >= x0;
+            hi[s2] = p <= p_hi && gx + 1 < x1;
+            if (lo[s2] && hi[s2] && even_pitch) {
+                v[s2] = *reinterpret_cast<const double2*>(prow + gx);
+            } else {
+                v[s2].x = lo[s2] ? prow[gx] : 0.0;
+                v[s2].y = hi[s2] ? prow[gx + 1] : 0.0;
+            }
+        }
+#pragma unroll
+        for (int s2 = 0; s2 < 2; ++s2) {
+            const int p = p_lo + lane + 32 * s2;
+            const int gx = R.gx0 + 2 * p;
+            if (!lo[s2] && !hi[s2]) continue;
+            const double a = fadd(o, v[s2].x, (double)row[p]);
+            const double b = fadd(o, v[s2].y, (double)row[FT_HS + p]);
+            if (lo[s2] && hi[s2] && even_pitch) {
+                *reinterpret_cast<double2*>(prow + gx) = make_double2(a, b);
+            } else {
+                if (lo[s2]) prow[gx] = a;
+                if (hi[s2]) prow[gx + 1] = b;
+            }
+        }
+    }
 }
 
 // ---- one grid: tile (blockIdx.x, blockIdx.y) of owned points 1 + (bx tx, by ty) ----
@@ -341,12 +405,12 @@ __global__ void __launch_bounds__(FT_THREADS, 2)
 
 __global__ void __launch_bounds__(FT_THREADS, 2)
     up32_kernel(BatchLevel<float> F, BatchLevel<float> C, int tx, int ty, int nu2, int gs, float w,
-                float omw)
+                float omw, double* psi, int64_t psi_pitch)
 {
     extern __shared__ float4 smem4[];
     float* smem = reinterpret_cast<float*>(smem4);
     up_tile(F, C, 1 + blockIdx.x * tx, 1 + blockIdx.y * ty, tx, ty, nu2, coef32(F, gs != 0, w, omw),
-            smem, smem + FT_ARR, smem + 2 * FT_ARR);
+            smem, smem + FT_ARR, smem + 2 * FT_ARR, psi, psi_pitch);
 }
 
 // ---- many grids: one tile item per CTA ----
@@ -365,15 +429,18 @@ __global__ void __launch_bounds__(FT_THREADS, 2)
 
 __global__ void __launch_bounds__(FT_THREADS, 2)
     b_up32_kernel(const TileItem* __restrict__ items, const BatchLevel<float>* __restrict__ lv,
-                  const int* __restrict__ active, int nu2, int gs, float w, float omw)
+                  const int* __restrict__ active, int nu2, int gs, float w, float omw,
+                  const BatchLevel<double>* __restrict__ lv64)
 {
     extern __shared__ float4 smem4[];
     float* smem = reinterpret_cast<float*>(smem4);
     const TileItem it = items[blockIdx.x];
     const BatchLevel<float> F = lv[it.level];
     if (active && !active[F.problem]) return;
+    double* psi = lv64 ? lv64[it.level].u : nullptr;
+    const int64_t pp = lv64 ? lv64[it.level].pitch : 0;
     up_tile(F, lv[it.level + 1], it.x0, it.y0, it.tx, it.ty, nu2, coef32(F, gs != 0, w, omw), smem,
-            smem + FT_ARR, smem + 2 * FT_ARR);
+            smem + FT_ARR, smem + 2 * FT_ARR, psi, pp);
 }
 
 constexpr size_t FT_SMEM = (2 * FT_ARR + FT_CARR) * sizeof(float);
@@ -430,12 +497,12 @@ cudaError_t launch_down32(const BatchLevel<float>& F, const BatchLevel<float>& C
 }
 
 cudaError_t launch_up32(const BatchLevel<float>& F, const BatchLevel<float>& C, int nu1, int nu2,
-                        bool gs, double w, cudaStream_t s)
+                        bool gs, double w, cudaStream_t s, double* psi, int64_t psi_pitch)
 {
     int tx, ty, ntx, nty;
     fused32_tile(F.m, F.n, nu1, nu2, &tx, &ty, &ntx, &nty);
     up32_kernel<<<dim3(ntx, nty), FT_THREADS, FT_SMEM, s>>>(F, C, tx, ty, nu2, gs ? 1 : 0, (float)w,
-                                                            (float)(1.0 - w));
+                                                            (float)(1.0 - w), psi, psi_pitch);
     note_launch();
     return cudaGetLastError();
 }
@@ -451,11 +518,12 @@ cudaError_t launch_b_down32(const TileItem* items, int count, const BatchLevel<f
 }
 
 cudaError_t launch_b_up32(const TileItem* items, int count, const BatchLevel<float>* lv,
-                          const int* active, int nu2, bool gs, double w, cudaStream_t s)
+                          const int* active, int nu2, bool gs, double w, cudaStream_t s,
+                          const BatchLevel<double>* lv64)
 {
     if (count == 0) return cudaSuccess;
     b_up32_kernel<<<count, FT_THREADS, FT_SMEM, s>>>(items, lv, active, nu2, gs ? 1 : 0, (float)w,
-                                                     (float)(1.0 - w));
+                                                     (float)(1.0 - w), lv64);
     note_launch();
     return cudaGetLastError();
 }

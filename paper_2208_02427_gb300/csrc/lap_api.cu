@@ -687,8 +687,10 @@ struct Solver {
             break;
         case LAP_MG_MIXED: {
             const Level32& l0 = w.levels32[0];
-            for (int k = 0; k < p->inner_cycles; ++k) vcycle32(0, k == 0);
-            ck(launch_update64(f, l0.u.p, l0.u.pitch, s), "update kernel");
+            // with the tile kernels the last level-0 ascent also does psi += e
+            const bool fold = fused32 && tail_first != 0 && w.levels32.size() > 1;
+            for (int k = 0; k < p->inner_cycles; ++k) vcycle32(0, k == 0, fold && k == p->inner_cycles - 1);
+            if (!fold) ck(launch_update64(f, l0.u.p, l0.u.pitch, s), "update kernel");
             ck(launch_defect64_to32(f, c, l0.q, l0.u.p, l0.u.pitch, w.partials, s),
                "mixed residual kernel");
             break;
@@ -792,7 +794,7 @@ struct Solver {
 
     // The FP32 image of vcycle() on the correction equation. first: the first inner cycle
     // of an outer iteration (the level-0 correction starts at zero).
-    void vcycle32(int l, bool first = false)
+    void vcycle32(int l, bool first = false, bool fold = false)
     {
         Level32& lv = w.levels32[l];
         const int L = (int)w.levels32.size();
@@ -814,7 +816,9 @@ struct Solver {
             ck(launch_down32(hl32[l], hl32[l + 1], p->nu1, p->nu2, l > 0 || first, gs, p->smoother_w, s),
                "descent kernel");
             vcycle32(l + 1);
-            ck(launch_up32(hl32[l], hl32[l + 1], p->nu1, p->nu2, gs, p->smoother_w, s), "ascent kernel");
+            ck(launch_up32(hl32[l], hl32[l + 1], p->nu1, p->nu2, gs, p->smoother_w, s,
+                           fold && l == 0 ? f.p : nullptr, f.pitch),
+               "ascent kernel");
             return;
         }
         if (l == L - 1) {
@@ -1125,6 +1129,7 @@ void add_items(std::vector<BatchItem>& items, int level_index, int m, int n)
 struct LevelLists {
     std::vector<std::pair<int, int>> fine, all, coarse, tail;
     std::vector<std::pair<int, int>> tiles;  // FP32 tile items of the fine lists (fused cycle)
+    std::pair<int, int> upd0{0, 0};  // fused: level-0 items of the problems without level-0 tiles
     bool fused = false;
     int levels = 0;
     int max_coarse = 0;
@@ -1207,6 +1212,14 @@ void build_lists(LevelLists& L, std::vector<BatchItem>& items, std::vector<TailJ
         }
         L.tail[l] = {j0, (int)jobs.size() - j0};
     }
+    if (tiles) {
+        const int u0 = (int)items.size();
+        for (size_t k = 0; k < who.size(); ++k) {
+            const int q = who[k];
+            if (t[k] == 0 || nlev[q] == 1) add_items(items, base[q], lv[base[q]].m, lv[base[q]].n);
+        }
+        L.upd0 = {u0, (int)items.size() - u0};
+    }
 }
 
 // One V-cycle over every active problem of L: descend (coarsest solves and tails start when
@@ -1239,10 +1252,12 @@ void enqueue_vcycle(ListFn list, const LevelLists& L, const BatchLevel<T>* lv, c
 
 // The FP32 V-cycle with each fine level's descent and ascent as one tile launch over all
 // problems (first: the level-0 corrections start at zero).
+// fold64 (nullable): the level-0 ascent adds its result to these FP64 fields (psi += e).
 template <class ListFn>
 void enqueue_vcycle32_fused(ListFn list, const LevelLists& L, const BatchLevel<float>* lv,
                             const int* active, const TailJob* jobs, const TileItem* tiles,
-                            const lap_params& p, double smoother_w, bool first, cudaStream_t st)
+                            const lap_params& p, double smoother_w, bool first, cudaStream_t st,
+                            const BatchLevel<double>* fold64 = nullptr)
 {
     const bool gs = smoother_w == 1.0;
     for (int l = 0; l < L.levels; ++l) {
@@ -1257,7 +1272,7 @@ void enqueue_vcycle32_fused(ListFn list, const LevelLists& L, const BatchLevel<f
     }
     for (int l = L.levels - 2; l >= 0; --l)
         ck(launch_b_up32(tiles + L.tiles[l].first, L.tiles[l].second, lv, active, p.nu2, gs,
-                         smoother_w, st),
+                         smoother_w, st, l == 0 ? fold64 : nullptr),
            "batched ascent");
 }
 
@@ -1437,11 +1452,13 @@ extern "C" int lap_solve_batched(lap_handle h, int count, const lap_grid* grids,
                 for (int k = 0; k < p->inner_cycles; ++k) {
                     if (L.fused)
                         enqueue_vcycle32_fused(list, L, lv32, active, jobs, tiles, *p, p->smoother_w,
-                                               k == 0, st);
+                                               k == 0, st, k == p->inner_cycles - 1 ? lv64 : nullptr);
                     else
                         enqueue_vcycle(list, L, lv32, active, jobs, *p, p->smoother_w, st);
                 }
-                ck(launch_b_update(norm_list, lv64, active, lv32, st), "batched update");
+                // fused: the level-0 ascents did psi += e except where a tail holds level 0
+                ck(launch_b_update(L.fused ? list(L.upd0) : norm_list, lv64, active, lv32, st),
+                   "batched update");
                 ck(launch_b_sumsq(norm_list, lv64, active, partials, lv32, st), "batched residual");
             } else {
                 enqueue_vcycle(list, L, lv64, active, jobs, *p, p->smoother_w, st);
@@ -1912,11 +1929,13 @@ extern "C" int lap_server_step(lap_server S, void* stream, int* running, int* qu
         for (int k = 0; k < S->mg.inner_cycles && P.mg32.levels; ++k) {
             if (P.mg32.fused)
                 enqueue_vcycle32_fused(list, P.mg32, lv32, active, jobs, tiles, S->mg, S->mg.smoother_w,
-                                       k == 0, st);
+                                       k == 0, st, k == S->mg.inner_cycles - 1 ? lv64 : nullptr);
             else
                 enqueue_vcycle(list, P.mg32, lv32, active, jobs, S->mg, S->mg.smoother_w, st);
         }
-        ck(launch_b_update(list(P.update), lv64, active, lv32, st), "server update");
+        // fused: the level-0 ascents did psi += e except where a tail holds level 0
+        ck(launch_b_update(list(P.mg32.fused ? P.mg32.upd0 : P.update), lv64, active, lv32, st),
+           "server update");
         for (int k = 0; k < S->sor_sweeps && P.sor.second; ++k)
             for (int colour = 0; colour < 2; ++colour)
                 ck(launch_b_rb(list(P.sor), lv64, active, colour, false, 1.0, st, true), "server sweep");

@@ -181,13 +181,18 @@ cudaError_t prepare_fused32();  // shared-memory limit of the tile kernels (outs
 // residual, C.u := 0. Ascent: F.u := smoothed (F.r + P C.u) after nu2 sweeps.
 cudaError_t launch_down32(const BatchLevel<float>& F, const BatchLevel<float>& C, int nu1, int nu2,
                           bool zero_u, bool gs, double w, cudaStream_t s);
+// psi (nullable): add the ascent's result to this FP64 field instead of storing it (the
+// mixed solver's update, folded into its last level-0 ascent).
 cudaError_t launch_up32(const BatchLevel<float>& F, const BatchLevel<float>& C, int nu1, int nu2,
-                        bool gs, double w, cudaStream_t s);
+                        bool gs, double w, cudaStream_t s, double* psi = nullptr,
+                        int64_t psi_pitch = 0);
 // The same over tile items of many problems (the coarse level of item level l is l + 1).
 cudaError_t launch_b_down32(const TileItem* items, int count, const BatchLevel<float>* lv,
                             const int* active, int nu1, bool zero_u, bool gs, double w, cudaStream_t s);
+// lv64 (nullable): items' FP64 fields (same level indices) take psi += result instead.
 cudaError_t launch_b_up32(const TileItem* items, int count, const BatchLevel<float>* lv,
-                          const int* active, int nu2, bool gs, double w, cudaStream_t s);
+                          const int* active, int nu2, bool gs, double w, cudaStream_t s,
+                          const BatchLevel<double>* lv64 = nullptr);
 
 // ---- line relaxation (line_kernels.cu) --------------------------------------------
 // Constant-coefficient tridiagonal systems -alpha x_{k-1} + delta x_k - alpha x_{k+1} = r_k,
