@@ -29,7 +29,6 @@ namespace lap {
 namespace {
 
 constexpr int FT_THREADS = 512;
-constexpr int FT_NW = FT_THREADS / 32;  // 16 warps
 constexpr int FT_W = 128;               // region columns (even): 64 column pairs
 constexpr int FT_H = 64;                // region rows: 4 per warp
 constexpr int FT_HS = FT_W / 2 + 16;    // half-row stride, 16 mod 32
@@ -88,17 +87,19 @@ __device__ __forceinline__ void sts2_masked(float* p, float2 v, bool lo, bool hi
 // The region's u and q (0 outside the array; u = 0 when zero_u): each lane moves column
 // pairs (gx, gx + 1), gx even, with 8-byte loads, all 16 of a thread in flight together,
 // and splits them into the two halves of the row. Level pitches are even.
+template <int NT>
 __device__ __forceinline__ void load_region(float* su, float* sq, const float* u, const float* q,
                                             int64_t pitch, int m, int n, const Region& R,
                                             bool zero_u)
 {
+    constexpr int NW = NT / 32, RPW = FT_H / NW;  // region rows per warp
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    float2 vu[8], vq[8];
+    float2 vu[2 * RPW], vq[2 * RPW];
 #pragma unroll
-    for (int t = 0; t < 4; ++t)
+    for (int t = 0; t < RPW; ++t)
 #pragma unroll
         for (int s2 = 0; s2 < 2; ++s2) {
-            const int ly = wid + FT_NW * t, p = lane + 32 * s2;
+            const int ly = wid + NW * t, p = lane + 32 * s2;
             const int gy = R.gy0 + ly, gx = R.gx0 + 2 * p;
             float2 a = make_float2(0.f, 0.f), b = make_float2(0.f, 0.f);
             if (ly < R.h && 2 * p < R.w && gy >= 0 && gy < n && gx >= 0 && gx < m) {
@@ -111,10 +112,10 @@ __device__ __forceinline__ void load_region(float* su, float* sq, const float* u
             vq[2 * t + s2] = b;
         }
 #pragma unroll
-    for (int t = 0; t < 4; ++t)
+    for (int t = 0; t < RPW; ++t)
 #pragma unroll
         for (int s2 = 0; s2 < 2; ++s2) {
-            const int ly = wid + FT_NW * t, p = lane + 32 * s2;
+            const int ly = wid + NW * t, p = lane + 32 * s2;
             if (ly < R.h && 2 * p < R.w) {
                 const int o = ly * FT_RS + p;
                 su[o] = vu[2 * t + s2].x;
@@ -147,71 +148,103 @@ __device__ __forceinline__ void sts4_masked(float* p, float4 v, int c0, int lo, 
     if (c0 + 3 >= lo && c0 + 3 <= hi) p[3] = v.w;
 }
 
-// s = (E+W) + b2 (N+S) + q for the four points c0 .. c0 + 3 of half `half` of region row ly,
+// s = (E+W) + b2 (N+S) + q for the four points c0 .. c0 + 3 of half HALF of region row ly,
 // as two float2 (points c0, c0 + 1 and c0 + 2, c0 + 3). Their west/east neighbours are in the
-// other half of the row at c - 1 + half and c + half.
-__device__ __forceinline__ void stencil4(const float* su, const float* sq, int ly, int half, int c0,
+// other half of the row at c - 1 + HALF and c + HALF.
+template <int HALF>
+__device__ __forceinline__ void stencil4(const float* su, const float* sq, int ly, int c0,
                                          const Coef32& k, float2& sA, float2& sB)
 {
-    const float* oth = su + ly * FT_RS + (1 - half) * FT_HS;
-    const int a = ly * FT_RS + half * FT_HS + c0;
+    const float* oth = su + ly * FT_RS + (1 - HALF) * FT_HS;
+    const int a = ly * FT_RS + HALF * FT_HS + c0;
     const float4 o = lds4(oth + c0);
-    const float ol = oth[c0 - 1], orr = oth[c0 + 4];
-    const bool h = half != 0;
-    const float2 wA = make_float2(h ? o.x : ol, h ? o.y : o.x);
-    const float2 wB = make_float2(h ? o.z : o.y, h ? o.w : o.z);
-    const float2 eA = make_float2(h ? o.y : o.x, h ? o.z : o.y);
-    const float2 eB = make_float2(h ? o.w : o.z, h ? orr : o.w);
+    float2 wA, wB, eA, eB;
+    if (HALF == 0) {
+        const float ol = oth[c0 - 1];
+        wA = make_float2(ol, o.x);
+        wB = make_float2(o.y, o.z);
+        eA = make_float2(o.x, o.y);
+        eB = make_float2(o.z, o.w);
+    } else {
+        const float orr = oth[c0 + 4];
+        wA = make_float2(o.x, o.y);
+        wB = make_float2(o.z, o.w);
+        eA = make_float2(o.y, o.z);
+        eB = make_float2(o.w, orr);
+    }
     const float4 S = lds4(su + a - FT_RS), N = lds4(su + a + FT_RS), Q = lds4(sq + a);
     sA = __fadd2_rn(nsum2(wA, eA, make_float2(S.x, S.y), make_float2(N.x, N.y), k), make_float2(Q.x, Q.y));
     sB = __fadd2_rn(nsum2(wB, eB, make_float2(S.z, S.w), make_float2(N.z, N.w), k), make_float2(Q.z, Q.w));
 }
 
+// Eq. 6 (gs) or Eq. 7 on the four points c0 .. c0 + 3 of half HALF of row ly, those in
+// [c_lo, c_hi] stored.
+template <int HALF>
+__device__ __forceinline__ void relax4(float* su, const float* sq, int ly, int c0, int c_lo, int c_hi,
+                                       const Coef32& k)
+{
+    float2 sA, sB;
+    stencil4<HALF>(su, sq, ly, c0, k, sA, sB);
+    float* at = su + ly * FT_RS + HALF * FT_HS + c0;
+    float2 gA = __fmul2_rn(sA, k.inv_d), gB = __fmul2_rn(sB, k.inv_d);
+    if (!k.gs) {
+        const float4 old = lds4(at);
+        gA = __ffma2_rn(k.w, gA, __fmul2_rn(k.omw, make_float2(old.x, old.y)));
+        gB = __ffma2_rn(k.w, gB, __fmul2_rn(k.omw, make_float2(old.z, old.w)));
+    }
+    sts4_masked(at, make_float4(gA.x, gA.y, gB.x, gB.y), c0, c_lo, c_hi);
+}
+
 // One colour pass of Eq. 6 (gs) or Eq. 7 over the domain-interior points of the region
 // but its outer ring: points (gx + gy) % 2 == colour, i.e. half (colour + gy) & 1 of row
-// gy. Each half warp takes a row, each lane four consecutive points of its half row.
+// gy. A warp takes two rows of the same parity (ly, ly + 2: the same half), a half warp one
+// row, a lane four consecutive points of its half row.
+template <int NT>
 __device__ __forceinline__ void colour_pass(float* su, const float* sq, const Region& R, int m, int n,
                                             int colour, const Coef32& k)
 {
+    constexpr int NW = NT / 32;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int lx_lo = max(1, 1 - R.gx0), lx_hi = min(R.w - 2, m - 2 - R.gx0);
     const int ly_lo = max(1, 1 - R.gy0), ly_hi = min(R.h - 2, n - 2 - R.gy0);
-    const int c0 = 4 * (lane & 15);
-    for (int ly = ly_lo + 2 * wid + (lane >> 4); ly <= ly_hi; ly += 2 * FT_NW) {
-        const int half = (colour + R.gy0 + ly) & 1;
-        int c_lo, c_hi;
-        half_range(lx_lo, lx_hi, half, &c_lo, &c_hi);
-        if (c0 + 3 < c_lo || c0 > c_hi) continue;
-        float2 sA, sB;
-        stencil4(su, sq, ly, half, c0, k, sA, sB);
-        float* at = su + ly * FT_RS + half * FT_HS + c0;
-        float2 gA = __fmul2_rn(sA, k.inv_d), gB = __fmul2_rn(sB, k.inv_d);
-        if (!k.gs) {
-            const float4 old = lds4(at);
-            gA = __ffma2_rn(k.w, gA, __fmul2_rn(k.omw, make_float2(old.x, old.y)));
-            gB = __ffma2_rn(k.w, gB, __fmul2_rn(k.omw, make_float2(old.z, old.w)));
+    int cl0, ch0, cl1, ch1;
+    half_range(lx_lo, lx_hi, 0, &cl0, &ch0);
+    half_range(lx_lo, lx_hi, 1, &cl1, &ch1);
+    const int c0 = 4 * (lane & 15), sub = 2 * (lane >> 4);
+    for (int g = wid;; g += NW) {
+        const int r = ly_lo + 4 * (g >> 1) + (g & 1);
+        if (r > ly_hi) break;
+        const int ly = r + sub;
+        const int half = (colour + R.gy0 + r) & 1;  // the same for r and r + 2
+        if (ly > ly_hi) continue;
+        if (half == 0) {
+            if (c0 + 3 >= cl0 && c0 <= ch0) relax4<0>(su, sq, ly, c0, cl0, ch0, k);
+        } else {
+            if (c0 + 3 >= cl1 && c0 <= ch1) relax4<1>(su, sq, ly, c0, cl1, ch1, k);
         }
-        sts4_masked(at, make_float4(gA.x, gA.y, gB.x, gB.y), c0, c_lo, c_hi);
     }
 }
 
+template <int NT>
 __device__ __forceinline__ void smooth_region(float* su, const float* sq, const Region& R, int m,
                                               int n, int sweeps, const Coef32& k)
 {
     for (int s = 0; s < sweeps; ++s)
         for (int colour = 0; colour < 2; ++colour) {
-            colour_pass(su, sq, R, m, n, colour, k);
+            colour_pass<NT>(su, sq, R, m, n, colour, k);
             __syncthreads();
         }
 }
 
 // Owned points [x0, x1) x [y0, y1) from shared memory to dst, by column pairs (gx even).
+template <int NT>
 __device__ __forceinline__ void store_owned(float* dst, int64_t pitch, const float* su,
                                             const Region& R, int x0, int x1, int y0, int y1)
 {
+    constexpr int NW = NT / 32;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int p_lo = (x0 - R.gx0) >> 1, p_hi = (x1 - 1 - R.gx0) >> 1;
-    for (int gy = y0 + wid; gy < y1; gy += FT_NW) {
+    for (int gy = y0 + wid; gy < y1; gy += NW) {
         const int ly = gy - R.gy0;
         for (int p = p_lo + lane; p <= p_hi; p += 32) {
             const int gx = R.gx0 + 2 * p;
@@ -237,36 +270,43 @@ __device__ __forceinline__ Region region_of(int x0, int y0, int tx, int ty, int 
 // Descent on one tile of level F: nu1 smoothing sweeps, the smoothed u of the owned points
 // to F.r (the second buffer of the level), the residual, and qc = 0.25 ((4 r + 2 edges) +
 // corners) with the correction zeroed at the coarse points whose centre the tile owns.
+template <int NT>
 __device__ __forceinline__ void down_tile(const BatchLevel<float>& F, const BatchLevel<float>& C,
                                           int x0, int y0, int tx, int ty, int nu1, bool zero_u,
                                           const Coef32& k, float* su, float* sq)
 {
+    constexpr int NW = NT / 32;
     const int m = F.m, n = F.n;
     const Region R = region_of(x0, y0, tx, ty, 2 + 2 * nu1);
-    load_region(su, sq, F.u, F.q, F.pitch, m, n, R, zero_u);
+    load_region<NT>(su, sq, F.u, F.q, F.pitch, m, n, R, zero_u);
     __syncthreads();
-    smooth_region(su, sq, R, m, n, nu1, k);
+    smooth_region<NT>(su, sq, R, m, n, nu1, k);
     const int x1 = min(x0 + tx, m - 1), y1 = min(y0 + ty, n - 1);
-    store_owned(F.r, F.pitch, su, R, x0, x1, y0, y1);
+    store_owned<NT>(F.r, F.pitch, su, R, x0, x1, y0, y1);
     // residual r = (E+W) + b2 (N+S) + q - d u on the owned points and a ring of one, written
     // over q (each point reads only its own q)
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int lx_lo = max(1, x0 - 1) - R.gx0, lx_hi = min(m - 2, x1) - R.gx0;
     const int ly_lo = max(1, y0 - 1) - R.gy0, ly_hi = min(n - 2, y1) - R.gy0;
-    const int c0 = 4 * (lane & 15);
+    // a warp takes rows ly, ly + 1 of one half (half warps), a lane four points
+    int cl0, ch0, cl1, ch1;
+    half_range(lx_lo, lx_hi, 0, &cl0, &ch0);
+    half_range(lx_lo, lx_hi, 1, &cl1, &ch1);
+    const int c0 = 4 * (lane & 15), sub = lane >> 4;
     const float2 nd = make_float2(-k.d.x, -k.d.y);
-    for (int t = 2 * wid + (lane >> 4); t <= 2 * (ly_hi - ly_lo) + 1; t += 2 * FT_NW) {
-        const int ly = ly_lo + (t >> 1), half = t & 1;
-        int c_lo, c_hi;
-        half_range(lx_lo, lx_hi, half, &c_lo, &c_hi);
-        if (c0 + 3 < c_lo || c0 > c_hi) continue;
+    for (int g = wid;; g += NW) {
+        const int half = g & 1, ly = ly_lo + 2 * (g >> 1) + sub;
+        if (ly_lo + 2 * (g >> 1) > ly_hi) break;
+        const int clo = half ? cl1 : cl0, chi = half ? ch1 : ch0;
+        if (ly > ly_hi || c0 + 3 < clo || c0 > chi) continue;
         float2 sA, sB;
-        stencil4(su, sq, ly, half, c0, k, sA, sB);
+        if (half == 0) stencil4<0>(su, sq, ly, c0, k, sA, sB);
+        else stencil4<1>(su, sq, ly, c0, k, sA, sB);
         const int a = ly * FT_RS + half * FT_HS + c0;
         const float4 u4 = lds4(su + a);
         const float2 rA = __ffma2_rn(nd, make_float2(u4.x, u4.y), sA);
         const float2 rB = __ffma2_rn(nd, make_float2(u4.z, u4.w), sB);
-        sts4_masked(sq + a, make_float4(rA.x, rA.y, rB.x, rB.y), c0, c_lo, c_hi);
+        sts4_masked(sq + a, make_float4(rA.x, rA.y, rB.x, rB.y), c0, clo, chi);
     }
     __syncthreads();
     // restriction to the coarse points (I, J) with (2I, 2J) owned: the centre is at half 0,
@@ -275,7 +315,7 @@ __device__ __forceinline__ void down_tile(const BatchLevel<float>& F, const Batc
     const int I0 = max(1, (x0 + 1) >> 1), I1 = min(mc - 2, (x1 - 1) >> 1);
     const int J0 = max(1, (y0 + 1) >> 1), J1 = min(nc - 2, (y1 - 1) >> 1);
     const float* r = sq;
-    for (int J = J0 + wid; J <= J1; J += FT_NW) {
+    for (int J = J0 + wid; J <= J1; J += NW) {
         const int ly = 2 * J - R.gy0;
         const float* r0 = r + ly * FT_RS;
         for (int I = I0 + lane; I <= I1; I += 32) {
@@ -298,18 +338,20 @@ __device__ __forceinline__ void down_tile(const BatchLevel<float>& F, const Batc
 // in shared memory (sc): a column pair p of the region lies over coarse column gx0 / 2 + p.
 // With psi (the FP64 field of the mixed solver's level 0), the last ascent adds its result
 // to psi in FP64 (psi += e, the update of the defect correction) instead of storing e.
+template <int NT>
 __device__ __forceinline__ void up_tile(const BatchLevel<float>& F, const BatchLevel<float>& C,
                                         int x0, int y0, int tx, int ty, int nu2, const Coef32& k,
                                         float* su, float* sq, float* sc, double* psi,
                                         int64_t psi_pitch)
 {
+    constexpr int NW = NT / 32;
     const int m = F.m, n = F.n;
     const Region R = region_of(x0, y0, tx, ty, 2 * nu2);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int cI0 = R.gx0 >> 1, cJ0 = R.gy0 >> 1;  // floor halves (gy0 may be negative)
     const int cw = (R.w >> 1) + 1, ch = ((R.gy0 + R.h - 1) >> 1) - cJ0 + 2;
     const int mc = (m - 1) / 2 + 1, nc = (n - 1) / 2 + 1;
-    for (int cy = wid; cy < ch; cy += FT_NW) {
+    for (int cy = wid; cy < ch; cy += NW) {
         const int J = cJ0 + cy;
         const bool rowin = J >= 0 && J < nc;
         for (int cx = lane; cx < cw; cx += 32) {
@@ -319,14 +361,14 @@ __device__ __forceinline__ void up_tile(const BatchLevel<float>& F, const BatchL
             else *d = 0.f;
         }
     }
-    load_region(su, sq, F.r, F.q, F.pitch, m, n, R, false);
+    load_region<NT>(su, sq, F.r, F.q, F.pitch, m, n, R, false);
     cp_async_wait_all();
     __syncthreads();
     // u += P e: even rows take coarse row J = gy / 2, odd rows the mean of rows J and J + 1;
     // even columns (half 0) coarse column p, odd columns (half 1) the mean of p and p + 1
     const int lx_lo = max(0, 1 - R.gx0), lx_hi = min(R.w - 1, m - 2 - R.gx0);
     const int ly_lo = max(0, 1 - R.gy0), ly_hi = min(R.h - 1, n - 2 - R.gy0);
-    for (int ly = ly_lo + wid; ly <= ly_hi; ly += FT_NW) {
+    for (int ly = ly_lo + wid; ly <= ly_hi; ly += NW) {
         const int gy = R.gy0 + ly;
         const float* a = sc + ((gy >> 1) - cJ0) * FT_CS;
         float* row = su + ly * FT_RS;
@@ -346,10 +388,10 @@ __device__ __forceinline__ void up_tile(const BatchLevel<float>& F, const BatchL
         }
     }
     __syncthreads();
-    smooth_region(su, sq, R, m, n, nu2, k);
+    smooth_region<NT>(su, sq, R, m, n, nu2, k);
     const int x1 = min(x0 + tx, m - 1), y1 = min(y0 + ty, n - 1);
     if (!psi) {
-        store_owned(F.u, F.pitch, su, R, x0, x1, y0, y1);
+        store_owned<NT>(F.u, F.pitch, su, R, x0, x1, y0, y1);
         return;
     }
     // column pairs (gx even: 16-byte aligned double2 when the pitch is even), two per lane,
@@ -357,7 +399,7 @@ __device__ __forceinline__ void up_tile(const BatchLevel<float>& F, const BatchL
     const FmaOps o = load_fma_ops();
     const int p_lo = (x0 - R.gx0) >> 1, p_hi = (x1 - 1 - R.gx0) >> 1;
     const bool even_pitch = (psi_pitch & 1) == 0;
-    for (int gy = y0 + wid; gy < y1; gy += FT_NW) {
+    for (int gy = y0 + wid; gy < y1; gy += NW) {
         const float* row = su + (gy - R.gy0) * FT_RS;
         double* prow = psi + (int64_t)gy * psi_pitch;
         double2 v[2];
@@ -393,24 +435,28 @@ __device__ __forceinline__ void up_tile(const BatchLevel<float>& F, const BatchL
 }
 
 // ---- one grid: tile (blockIdx.x, blockIdx.y) of owned points 1 + (bx tx, by ty) ----
-__global__ void __launch_bounds__(FT_THREADS, 2)
+// NT threads: 512 (two CTAs per SM) for levels with many tiles, 1024 (one CTA per SM, half
+// the rows per warp: a shorter critical path) for levels with fewer tiles than SMs.
+template <int NT>
+__global__ void __launch_bounds__(NT, 1024 / NT)
     down32_kernel(BatchLevel<float> F, BatchLevel<float> C, int tx, int ty, int nu1, int zero_u,
                   int gs, float w, float omw)
 {
     extern __shared__ float4 smem4[];
     float* smem = reinterpret_cast<float*>(smem4);
-    down_tile(F, C, 1 + blockIdx.x * tx, 1 + blockIdx.y * ty, tx, ty, nu1, zero_u != 0,
-              coef32(F, gs != 0, w, omw), smem, smem + FT_ARR);
+    down_tile<NT>(F, C, 1 + blockIdx.x * tx, 1 + blockIdx.y * ty, tx, ty, nu1, zero_u != 0,
+                  coef32(F, gs != 0, w, omw), smem, smem + FT_ARR);
 }
 
-__global__ void __launch_bounds__(FT_THREADS, 2)
+template <int NT>
+__global__ void __launch_bounds__(NT, 1024 / NT)
     up32_kernel(BatchLevel<float> F, BatchLevel<float> C, int tx, int ty, int nu2, int gs, float w,
                 float omw, double* psi, int64_t psi_pitch)
 {
     extern __shared__ float4 smem4[];
     float* smem = reinterpret_cast<float*>(smem4);
-    up_tile(F, C, 1 + blockIdx.x * tx, 1 + blockIdx.y * ty, tx, ty, nu2, coef32(F, gs != 0, w, omw),
-            smem, smem + FT_ARR, smem + 2 * FT_ARR, psi, psi_pitch);
+    up_tile<NT>(F, C, 1 + blockIdx.x * tx, 1 + blockIdx.y * ty, tx, ty, nu2,
+                coef32(F, gs != 0, w, omw), smem, smem + FT_ARR, smem + 2 * FT_ARR, psi, psi_pitch);
 }
 
 // ---- many grids: one tile item per CTA ----
@@ -423,8 +469,8 @@ __global__ void __launch_bounds__(FT_THREADS, 2)
     const TileItem it = items[blockIdx.x];
     const BatchLevel<float> F = lv[it.level];
     if (active && !active[F.problem]) return;
-    down_tile(F, lv[it.level + 1], it.x0, it.y0, it.tx, it.ty, nu1, zero_u != 0,
-              coef32(F, gs != 0, w, omw), smem, smem + FT_ARR);
+    down_tile<FT_THREADS>(F, lv[it.level + 1], it.x0, it.y0, it.tx, it.ty, nu1, zero_u != 0,
+                          coef32(F, gs != 0, w, omw), smem, smem + FT_ARR);
 }
 
 __global__ void __launch_bounds__(FT_THREADS, 2)
@@ -439,11 +485,12 @@ __global__ void __launch_bounds__(FT_THREADS, 2)
     if (active && !active[F.problem]) return;
     double* psi = lv64 ? lv64[it.level].u : nullptr;
     const int64_t pp = lv64 ? lv64[it.level].pitch : 0;
-    up_tile(F, lv[it.level + 1], it.x0, it.y0, it.tx, it.ty, nu2, coef32(F, gs != 0, w, omw), smem,
-            smem + FT_ARR, smem + 2 * FT_ARR, psi, pp);
+    up_tile<FT_THREADS>(F, lv[it.level + 1], it.x0, it.y0, it.tx, it.ty, nu2,
+                        coef32(F, gs != 0, w, omw), smem, smem + FT_ARR, smem + 2 * FT_ARR, psi, pp);
 }
 
 constexpr size_t FT_SMEM = (2 * FT_ARR + FT_CARR) * sizeof(float);
+constexpr int FT_FEW_TILES = 152;  // below one tile per SM: 1024-thread tiles
 
 }  // namespace
 
@@ -477,8 +524,10 @@ cudaError_t prepare_fused32()
 {
     if (g_fused32_ready) return cudaSuccess;
     const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
-    cudaError_t e = cudaFuncSetAttribute(down32_kernel, a, (int)FT_SMEM);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(up32_kernel, a, (int)FT_SMEM);
+    cudaError_t e = cudaFuncSetAttribute(down32_kernel<512>, a, (int)FT_SMEM);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(up32_kernel<512>, a, (int)FT_SMEM);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(down32_kernel<1024>, a, (int)FT_SMEM);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(up32_kernel<1024>, a, (int)FT_SMEM);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(b_down32_kernel, a, (int)FT_SMEM);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(b_up32_kernel, a, (int)FT_SMEM);
     if (e == cudaSuccess) g_fused32_ready = true;
@@ -490,8 +539,13 @@ cudaError_t launch_down32(const BatchLevel<float>& F, const BatchLevel<float>& C
 {
     int tx, ty, ntx, nty;
     fused32_tile(F.m, F.n, nu1, nu2, &tx, &ty, &ntx, &nty);
-    down32_kernel<<<dim3(ntx, nty), FT_THREADS, FT_SMEM, s>>>(F, C, tx, ty, nu1, zero_u ? 1 : 0,
-                                                              gs ? 1 : 0, (float)w, (float)(1.0 - w));
+    const float wf = (float)w, omw = (float)(1.0 - w);
+    if (ntx * nty < FT_FEW_TILES)
+        down32_kernel<1024><<<dim3(ntx, nty), 1024, FT_SMEM, s>>>(F, C, tx, ty, nu1, zero_u ? 1 : 0,
+                                                                  gs ? 1 : 0, wf, omw);
+    else
+        down32_kernel<512><<<dim3(ntx, nty), 512, FT_SMEM, s>>>(F, C, tx, ty, nu1, zero_u ? 1 : 0,
+                                                                gs ? 1 : 0, wf, omw);
     note_launch();
     return cudaGetLastError();
 }
@@ -501,8 +555,13 @@ cudaError_t launch_up32(const BatchLevel<float>& F, const BatchLevel<float>& C, 
 {
     int tx, ty, ntx, nty;
     fused32_tile(F.m, F.n, nu1, nu2, &tx, &ty, &ntx, &nty);
-    up32_kernel<<<dim3(ntx, nty), FT_THREADS, FT_SMEM, s>>>(F, C, tx, ty, nu2, gs ? 1 : 0, (float)w,
-                                                            (float)(1.0 - w), psi, psi_pitch);
+    const float wf = (float)w, omw = (float)(1.0 - w);
+    if (ntx * nty < FT_FEW_TILES)
+        up32_kernel<1024><<<dim3(ntx, nty), 1024, FT_SMEM, s>>>(F, C, tx, ty, nu2, gs ? 1 : 0, wf, omw,
+                                                                psi, psi_pitch);
+    else
+        up32_kernel<512><<<dim3(ntx, nty), 512, FT_SMEM, s>>>(F, C, tx, ty, nu2, gs ? 1 : 0, wf, omw,
+                                                              psi, psi_pitch);
     note_launch();
     return cudaGetLastError();
 }
