@@ -148,6 +148,9 @@ struct lap_handle_s {
     // Small-level tail sizes chosen by timing, per shape (see TailTuner)
     std::map<std::string, lap::TailTuner> tail_tuners;
     cudaEvent_t ev[2] = {nullptr, nullptr};
+    // transposed copy of a field for the y-lines of line relaxation (grown on demand)
+    double* tscratch = nullptr;
+    size_t tscratch_bytes = 0;
 };
 
 namespace {
@@ -395,6 +398,27 @@ const LineTables& line_tables(lap_handle h, int N, double alpha, double delta)
 }
 
 // One zebra half-sweep in `direction` (0: x-lines = rows, 1: y-lines = columns).
+// Row pitch of the transposed copy of an m x n field (its m rows hold the n-long columns).
+int64_t transposed_pitch(const Field& f) { return round_up(f.n, 32); }
+
+// The transposed-copy buffer for fields of this shape (allocated outside graph capture).
+double* transposed_scratch(lap_handle h, const Field& f)
+{
+    const size_t bytes = (size_t)f.m * (size_t)transposed_pitch(f) * sizeof(double);
+    if (bytes > h->tscratch_bytes) {
+        dev_free(h, h->tscratch, h->tscratch_bytes);
+        h->tscratch = nullptr;
+        h->tscratch_bytes = 0;
+        h->tscratch = (double*)dev_alloc(h, bytes);
+        h->tscratch_bytes = bytes;
+    }
+    return h->tscratch;
+}
+
+// One zebra half sweep: x-lines (direction 0) in place; y-lines (direction 1) on a
+// transposed copy, so that the line kernel reads every line contiguously (the columns of
+// a row-major field are strided by the pitch), then copied back. The line arithmetic is
+// the same either way.
 void line_half_sweep(lap_handle h, const Field& f, const Coef& c, double w, int form,
                      int direction, cudaStream_t s)
 {
@@ -405,11 +429,18 @@ void line_half_sweep(lap_handle h, const Field& f, const Coef& c, double w, int 
     const double cross = x ? c.b2 : 1.0;
     const double alpha = form == LAP_FORM_A ? off : w * off;
     const LineTables& t = line_tables(h, N, alpha, c.d);
-    const int64_t sa = x ? 1 : f.pitch, sx = x ? f.pitch : 1;
+    double* p = f.p;
+    int64_t sx = f.pitch;
+    if (!x) {
+        p = transposed_scratch(h, f);
+        sx = transposed_pitch(f);
+        ck(launch_transpose(f.p, f.pitch, p, sx, f.n, f.m, s), "transpose kernel");
+    }
     for (int first = 1; first <= 2; ++first) {
         const int count = first == 1 ? (nlines + 1) / 2 : nlines / 2;
-        ck(launch_line_colour(f.p, sa, sx, first, count, t, form, cross, w, s), "line kernel");
+        ck(launch_line_colour(p, 1, sx, first, count, t, form, cross, w, s), "line kernel");
     }
+    if (!x) ck(launch_transpose(p, sx, f.p, f.pitch, f.m, f.n, s), "transpose kernel");
 }
 
 // ---- coarsest-grid inverse ------------------------------------------------------------
@@ -914,6 +945,7 @@ struct Solver {
                     line_tables(h, N, p->line_form == LAP_FORM_A ? off : p->w * off, c.d);
                 ck(prepare_line_kernels(line_smem_bytes(t)), "line kernel attributes");
             }
+            if (p->method == LAP_ADI) transposed_scratch(h, f);
         }
         if (p->method == LAP_MG) {
             const Level& lv = w.levels.back();
@@ -936,7 +968,7 @@ struct Solver {
                                 (int64_t)w.levels.size(), p->inner_cycles,
                                 (int64_t)w.levels32.size(), tail_first, fused32};
         const double dbl[] = {c.b2, c.d, c.inv_d, p->w, p->smoother_w};
-        const void* ptrs[] = {f.p, jac_cur, jac_other, w.aux, w.maxd, h->arena};
+        const void* ptrs[] = {f.p, jac_cur, jac_other, w.aux, w.maxd, h->arena, h->tscratch};
         put(ints, sizeof ints);
         put(dbl, sizeof dbl);
         put(ptrs, sizeof ptrs);
@@ -1004,6 +1036,7 @@ struct Solver {
             const double pair[2] = {wv, 1.0 - wv};  // staged by the copy before it returns
             ck(cudaMemcpyAsync(w.wslot, pair, sizeof pair, cudaMemcpyHostToDevice, s), "upload w");
         }
+        if (p->method == LAP_ADI) transposed_scratch(h, f);  // before any graph capture
         if (p->method == LAP_JACOBI) {
             copy_field(w.aux, f.p);  // ring + initial interior in both buffers
             jac_cur = f.p;
@@ -2032,6 +2065,7 @@ void lap_destroy(lap_handle h)
     if (h->capture) cudaStreamDestroy(h->capture);
     for (cudaEvent_t e : h->ev)
         if (e) cudaEventDestroy(e);
+    dev_free(h, h->tscratch, h->tscratch_bytes);
     dev_free(h, h->arena, h->arena_bytes);
     if (h->pinned) cudaFreeHost(h->pinned);
     delete h;

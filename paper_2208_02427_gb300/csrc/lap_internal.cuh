@@ -228,5 +228,8 @@ int line_threads(const LineTables& t);
 cudaError_t launch_line_colour(double* psi, int64_t sa, int64_t sx, int first_line, int count,
                                const LineTables& t, int form, double cross, double w,
                                cudaStream_t s);
+// dst[c * dp + r] = src[r * sp + c] for r < rows, c < cols (coalesced tiled transpose).
+cudaError_t launch_transpose(const double* src, int64_t sp, double* dst, int64_t dp, int rows,
+                             int cols, cudaStream_t s);
 
 }  // namespace lap

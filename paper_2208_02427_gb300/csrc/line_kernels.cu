@@ -157,6 +157,39 @@ cudaError_t prepare_line_kernels(size_t smem)
     return e;
 }
 
+namespace {
+
+// dst[c][r] = src[r][c] for r < rows, c < cols: 32x32 tiles through shared memory (one
+// column of padding), reads and writes coalesced along rows.
+constexpr int TT = 32, TR = 8;
+__global__ void __launch_bounds__(TT* TR)
+    transpose_kernel(const double* __restrict__ src, int64_t sp, double* __restrict__ dst,
+                     int64_t dp, int rows, int cols)
+{
+    __shared__ double tile[TT][TT + 1];
+    const int c0 = blockIdx.x * TT, r0 = blockIdx.y * TT;
+    for (int k = threadIdx.y; k < TT; k += TR) {
+        const int r = r0 + k, c = c0 + threadIdx.x;
+        if (r < rows && c < cols) tile[k][threadIdx.x] = src[(int64_t)r * sp + c];
+    }
+    __syncthreads();
+    for (int k = threadIdx.y; k < TT; k += TR) {
+        const int c = c0 + k, r = r0 + threadIdx.x;
+        if (r < rows && c < cols) dst[(int64_t)c * dp + r] = tile[threadIdx.x][k];
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_transpose(const double* src, int64_t sp, double* dst, int64_t dp, int rows,
+                             int cols, cudaStream_t s)
+{
+    const dim3 grid((cols + TT - 1) / TT, (rows + TT - 1) / TT), block(TT, TR);
+    transpose_kernel<<<grid, block, 0, s>>>(src, sp, dst, dp, rows, cols);
+    note_launch();
+    return cudaGetLastError();
+}
+
 cudaError_t launch_line_colour(double* psi, int64_t sa, int64_t sx, int first_line, int count,
                                const LineTables& t, int form, double cross, double w,
                                cudaStream_t s)
