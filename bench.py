@@ -276,10 +276,12 @@ def main():
     hbm_gbs = SOR_BYTES_PER_POINT / 2 * pts_per_launch / launch_s / 1e9
     peaks = measured_peaks()
     traffic = recorded_traffic("rb_colour_kernel")
+    pipe_busy = recorded_traffic("rb_colour_kernel:fp64_pipe_active")
     roofline = {"bound": "alu", "kernel": "rb_colour_kernel (SOR, one colour)",
                 "achieved": ops / 1e12, "peak": FP64_OPS_PEAK / 1e12, "unit": "Top/s",
                 "frac": ops / FP64_OPS_PEAK, "traffic": traffic,
                 "peak_source": "derived: 152 SMs x 2 FP64 ops/clk x 2070 MHz",
+                "ncu_fp64_pipe_active": pipe_busy,
                 "ms_per_launch": launch_s * 1e3,
                 "hbm_view": {"achieved_gbs": hbm_gbs, "peak_gbs": peaks.get("hbm_gbs"),
                              "frac": hbm_gbs / peaks["hbm_gbs"] if peaks.get("hbm_gbs") else None,
@@ -416,6 +418,44 @@ def main():
         return out
 
     mixed["batch_256x1025"] = mixed_batch()
+
+    # ---- the paper's chamber problem (25 x 17, Eq. 4), its stopping rule (Eq. 16) ---------
+    # Iteration counts the paper prints for it (Results and Discussion), context only: its
+    # figures of the geometry are missing, so the boundary is a reading of the text.
+    paper_counts = {"jacobi": 1194, "gs_lex": 624, "slorb_w1.25": 55, "adi_b_w1.30": 33, "mg_v22": 6}
+
+    def chamber_section(reps=20):
+        psi0 = wl.chamber()
+        src = b.to_field(psi0, dev)
+        f = b.field(psi0.shape[1], psi0.shape[0], dev)
+        cases = [("jacobi", dict(method="jacobi")), ("gs_lex", dict(method="gs_lex")),
+                 ("gs_rb", dict(method="gs")), ("sor_lex_w1.75", dict(method="sor_lex", w=1.75)),
+                 ("sor_rb_w1.75", dict(method="sor", w=1.75)),
+                 ("slorb_w1.25", dict(method="slor", w=1.25, line_form="B")),
+                 ("adi_b_w1.30", dict(method="adi", w=1.3, line_form="B")),
+                 ("mg_v22", dict(method="mg", nu1=2, nu2=2))]
+        out = {"grid": "25x17, dx = dy = 0.25 m, psi = 1 on wall AB, 0 elsewhere",
+               "stopping": "max|psi^{k+1} - psi^k| <= 1e-9 tested every iteration (Eq. 16)",
+               "timing": "host wall clock around lap_solve (launches, graph replays and the "
+                         "per-iteration host check included), median over 20 solves"}
+        for name, kw in cases:
+            kw = dict(kw, norm="maxdelta", tol=1e-9, max_iter=100000)
+            times, info = [], None
+            for r in range(reps + 2):
+                with torch.cuda.stream(stream):
+                    f.copy_(src)
+                stream.synchronize()
+                t0 = time.perf_counter()
+                info = lap.solve(f, 0.25, 0.25, stream=stream, **kw)
+                t1 = time.perf_counter()
+                if r >= 2:
+                    times.append((t1 - t0) * 1e6)
+            us = statistics.median(times)
+            out[name] = {"iters": info["iters"], "status": info["status"], "us_per_solve": us,
+                         "solves_per_s": 1e6 / us, "paper_iters": paper_counts.get(name)}
+        return out
+
+    chamber = chamber_section()
 
     # ---- batched uneven grids: 4096 problems, sides 2^k+1 (k = 5..9), aspect <= 4 ---------
     def batched_workload(count=4096, sample=128):
@@ -566,7 +606,7 @@ def main():
                     for k in ("sor", "mg")},
         "roofline": roofline, "kernels": kernels, "latency": latency,
         "cpu_baseline": {k: v for k, v in cpu.items() if k != "seconds_per_solve_pair"},
-        "mixed_precision": mixed, "batched": batched, "serving": serving, "e2e": e2e,
+        "mixed_precision": mixed, "chamber_25x17": chamber, "batched": batched, "serving": serving, "e2e": e2e,
         "gpu_launches": launches,
         "clocks": clk,
     }

@@ -119,7 +119,9 @@ typedef struct {
     int32_t status;  /* lap_status */
     int64_t iters;   /* iterations (V-cycles) performed */
     double r0;       /* ||r(psi^0)||_2 of the scaled residual dx^2 L(psi), Eqs. 11-12 */
-    double r_final;  /* ||r||_2 after the last iteration */
+    double r_final;  /* ||r||_2 after the last iteration (LAP_MG_MIXED: the stopping test's
+                        norm, whose squares are summed in FP32 after a power-of-two scaling:
+                        about six significant digits) */
     double last_check; /* the stopping-rule value at the last test (ratio for L2_REL) */
 } lap_result;
 
@@ -256,6 +258,13 @@ int lap_residual_noalloc(const lap_grid* g, const double* psi_dev, const double*
 int lap_set_graphs(lap_handle h, int enabled);
 
 /* Human-readable name of a return code, and the message of the last error on this thread. */
+/* Self-check (no counterpart in the paper): the kernels round the FP64 residual to FP32 on
+ * the integer pipe (bit-identical to the conversion instruction by construction); this
+ * compares the two on `count` doubles drawn from `seed` (random bits, FP32-range edges,
+ * exact ties, all-ones fractions) and returns the number of differences (0 expected) in
+ * *mismatches. Synchronises the device. */
+int lap_check_rounding(lap_handle h, int64_t count, uint64_t seed, int64_t* mismatches);
+
 const char* lap_strerror(int code);
 const char* lap_last_error(void);
 

@@ -100,6 +100,7 @@ def load():
             "lap_strerror": (C.c_char_p, [C.c_int]),
             "lap_last_error": (C.c_char_p, []),
             "lap_kernel_launches": (c_int64, []),
+            "lap_check_rounding": (C.c_int, [c_void_p, c_int64, C.c_uint64, C.POINTER(c_int64)]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -191,6 +192,13 @@ class Laplace:
 
     def __exit__(self, *exc):
         self.close()
+
+    def check_rounding(self, count: int, seed: int = 1) -> int:
+        """Mismatches of the kernels' integer-pipe FP64 -> FP32 rounding against the
+        conversion instruction over `count` seeded doubles (0 expected)."""
+        out = c_int64(0)
+        _check(self._lib.lap_check_rounding(self._h, int(count), int(seed), C.byref(out)))
+        return int(out.value)
 
     def set_graphs(self, enabled: bool):
         """Replay each check period as a CUDA graph (default) or launch kernels one by one."""

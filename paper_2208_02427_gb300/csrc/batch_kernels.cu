@@ -345,7 +345,7 @@ __global__ void __launch_bounds__(BT)
         acc = __fma_rn(r, r, acc);
         if (r32) {
             const int64_t at = (int64_t)j * p32 + i;
-            r32[at] = __double2float_rn(r);
+            r32[at] = to_float_rn(r);
             e32[at] = 0.0f;
         }
     }

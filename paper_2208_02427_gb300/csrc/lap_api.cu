@@ -533,6 +533,8 @@ struct Work {
     double* wslot = nullptr;     // {w, 1 - w} of the point sweeps, read by the kernels
     double* partials = nullptr;  // norm partial sums
     double* nrm = nullptr;       // [sum, sqrt]
+    float* nscale = nullptr;     // the mixed solver's norm scale (power of two near 1/||r0||)
+    LoopState* loop = nullptr;   // device-resident solve loop state
     unsigned long long* maxd = nullptr;
     double* aux = nullptr;       // Jacobi second buffer, or previous iterate for max|delta|
     std::vector<Level> levels;
@@ -549,6 +551,8 @@ void carve(C& cv, Work& w, const lap_grid* g, const lap_params* p)
     w.wslot = cv.template take<double>(2);
     w.partials = cv.template take<double>(2048);
     w.nrm = cv.template take<double>(2);
+    w.nscale = cv.template take<float>(1);
+    w.loop = cv.template take<LoopState>(1);
     w.maxd = cv.template take<unsigned long long>(1);
     const size_t field = (size_t)g->n * (size_t)g->pitch;
     const bool need_aux =
@@ -653,14 +657,30 @@ struct Solver {
         return h->pinned[0];
     }
 
-    // Norm from partial sums already written by the last FP64 residual pass.
-    double partial_norm(const Field& u)
+    // Norm from partial sums already written by the last FP64 residual pass (squares of
+    // norm_sc r when scaled).
+    double partial_norm(const Field& u, bool scaled = false)
     {
         ck(launch_sum_partials(w.partials, mixed_norm_blocks(u.n), w.nrm, s), "sum kernel");
         ck(cudaMemcpyAsync(h->pinned, w.nrm + 1, sizeof(double), cudaMemcpyDeviceToHost, s),
            "copy norm");
         ck(cudaStreamSynchronize(s), "stream sync");
-        return h->pinned[0];
+        return scaled ? h->pinned[0] / norm_sc : h->pinned[0];
+    }
+
+    // The mixed solver sums its iterations' residual squares in FP32 once r0 is known:
+    // scale = 2^-e with r0 = f 2^e (so the scaled values stay in FP32's range).
+    double norm_sc = 0.0;
+    void set_norm_scale(double r0)
+    {
+        norm_sc = 0.0;
+        if (!(r0 > 0.0) || !std::isfinite(r0)) return;
+        const int e = std::ilogb(r0);
+        if (e < -100 || e > 100) return;
+        norm_sc = std::ldexp(1.0, -e);
+        const float v = (float)norm_sc;  // exact: a power of two in FP32's range
+        ck(cudaMemcpyAsync(w.nscale, &v, sizeof v, cudaMemcpyHostToDevice, s), "upload norm scale");
+        ck(cudaStreamSynchronize(s), "stream sync");
     }
 
     double read_maxd()
@@ -722,7 +742,10 @@ struct Solver {
             const bool fold = fused32 && tail_first != 0 && w.levels32.size() > 1;
             for (int k = 0; k < p->inner_cycles; ++k) vcycle32(0, k == 0, fold && k == p->inner_cycles - 1);
             if (!fold) ck(launch_update64(f, l0.u.p, l0.u.pitch, s), "update kernel");
-            ck(launch_defect64_to32(f, c, l0.q, l0.u.p, l0.u.pitch, w.partials, s),
+            // the tiles' first level-0 descent treats e as zero: no need to clear it
+            const bool keep_e = fused32 && tail_first != 0 && w.levels32.size() > 1;
+            ck(launch_defect64_to32(f, c, l0.q, keep_e ? nullptr : l0.u.p, l0.u.pitch, w.partials, s,
+                                    norm_sc > 0.0 ? w.nscale : nullptr),
                "mixed residual kernel");
             break;
         }
@@ -966,7 +989,7 @@ struct Solver {
         const int64_t ints[] = {p->method, f.m, f.n, f.pitch, steps, maxdelta, fused_maxd,
                                 p->nu1, p->nu2, p->coarsest_min, p->max_levels, p->line_form,
                                 (int64_t)w.levels.size(), p->inner_cycles,
-                                (int64_t)w.levels32.size(), tail_first, fused32};
+                                (int64_t)w.levels32.size(), tail_first, fused32, norm_sc > 0.0};
         const double dbl[] = {c.b2, c.d, c.inv_d, p->w, p->smoother_w};
         const void* ptrs[] = {f.p, jac_cur, jac_other, w.aux, w.maxd, h->arena, h->tscratch};
         put(ints, sizeof ints);
@@ -1026,6 +1049,125 @@ struct Solver {
         return captured;
     }
 
+    // The norm of the stopping test, enqueued on s (the kernels of the host check).
+    void enqueue_norm(bool maxdelta, bool fused_maxd, const Field& cur)
+    {
+        if (maxdelta) {
+            if (!fused_maxd) ck(launch_maxdelta(f, w.aux, w.maxd, s), "max delta kernel");
+        } else if (p->method == LAP_MG_FP32) {
+            ck(launch_defect32_sumsq(w.levels32[0].u, w.levels32[0].q, c, w.partials, s),
+               "residual kernel");
+            ck(launch_sum_partials(w.partials, mixed_norm_blocks(f.n), w.nrm, s), "sum kernel");
+        } else if (p->method == LAP_MG_MIXED) {
+            ck(launch_sum_partials(w.partials, mixed_norm_blocks(f.n), w.nrm, s), "sum kernel");
+        } else {
+            ck(launch_defect_sumsq(cur, nullptr, c, w.partials, s), "residual kernel");
+            ck(launch_sum_partials(w.partials, norm_blocks(cur), w.nrm, s), "sum kernel");
+        }
+    }
+
+    // Device-resident loop: whole check periods, each followed by the stopping test on the
+    // device, as the body of a conditional (while) node of one CUDA graph, so that the host
+    // waits once per solve instead of once per period. Used once the small-level tail is
+    // chosen, for full periods (Jacobi: even periods, whose buffer roles repeat).
+    bool device_loop_ok(int64_t k, int64_t steps, const TailTuner* tuner) const
+    {
+        if (!h->use_graphs || steps != p->check_every || k + steps > p->max_iter) return false;
+        if (tuner && !tuner->done) return false;
+        if (p->method == LAP_JACOBI && (steps & 1)) return false;
+        return true;
+    }
+
+    // Runs periods on the device until the stopping rule holds or the next period would pass
+    // max_iter; returns the loop state read back.
+    LoopState device_loop(int64_t k, double r0, double last_nr, bool maxdelta, bool fused_maxd)
+    {
+        const int64_t steps = p->check_every;
+        const bool scaled = p->method == LAP_MG_MIXED && norm_sc > 0.0;
+        const std::string key = graph_key(steps, maxdelta, fused_maxd) + (scaled ? "|loop-scaled" : "|loop");
+        auto it = h->graphs.find(key);
+        if (it == h->graphs.end()) {
+            prepare();
+            if (h->graphs.size() >= 64) drop_graphs(h);
+            if (!h->capture)
+                ck(cudaStreamCreateWithFlags(&h->capture, cudaStreamNonBlocking), "capture stream");
+            cudaGraph_t g = nullptr;
+            ck(cudaGraphCreate(&g, 0), "create graph");
+            cudaGraphExec_t exec = nullptr;
+            int64_t kernels = 0;
+            cudaStream_t caller = s;
+            double* cur0 = jac_cur;
+            double* other0 = jac_other;
+            try {
+                cudaGraphConditionalHandle hnd;
+                ck(cudaGraphConditionalHandleCreate(&hnd, g, 1, cudaGraphCondAssignDefault),
+                   "conditional handle");
+                // zero-initialised node parameters (the struct's union has no default constructor)
+                alignas(cudaGraphNodeParams) unsigned char raw[sizeof(cudaGraphNodeParams)] = {};
+                cudaGraphNodeParams* np = reinterpret_cast<cudaGraphNodeParams*>(raw);
+                np->type = cudaGraphNodeTypeConditional;
+                np->conditional.handle = hnd;
+                np->conditional.type = cudaGraphCondTypeWhile;
+                np->conditional.size = 1;
+                cudaGraphNode_t node;
+                ck(cudaGraphAddNode(&node, g, nullptr, nullptr, 0, np), "conditional node");
+                cudaGraph_t body = np->conditional.phGraph_out[0];
+                const int64_t before = launches_now();
+                ck(cudaStreamBeginCaptureToGraph(h->capture, body, nullptr, nullptr, 0,
+                                                 cudaStreamCaptureModeThreadLocal),
+                   "begin capture");
+                s = h->capture;
+                try {
+                    period(steps, maxdelta, fused_maxd);
+                    const Field cur{p->method == LAP_JACOBI ? jac_cur : f.p, f.m, f.n, f.pitch};
+                    enqueue_norm(maxdelta, fused_maxd, cur);
+                    ck(launch_loop_decide(w.loop, w.nrm, w.maxd, scaled ? w.nscale : nullptr, hnd, s),
+                       "loop test kernel");
+                } catch (...) {
+                    s = caller;
+                    cudaGraph_t junk = nullptr;
+                    cudaStreamEndCapture(h->capture, &junk);
+                    cudaGetLastError();
+                    throw;
+                }
+                s = caller;
+                cudaGraph_t body_out = nullptr;
+                ck(cudaStreamEndCapture(h->capture, &body_out), "end capture");
+                kernels = launches_now() - before;
+                add_launches(-kernels);
+                ck(cudaGraphInstantiate(&exec, g, 0), "instantiate graph");
+            } catch (...) {
+                s = caller;
+                jac_cur = cur0;
+                jac_other = other0;
+                cudaGraphDestroy(g);
+                throw;
+            }
+            cudaGraphDestroy(g);
+            jac_cur = cur0;  // even periods: the buffer roles are the same after each
+            jac_other = other0;
+            it = h->graphs.emplace(key, std::make_pair(exec, kernels)).first;
+        }
+        LoopState st{};
+        st.k = k;
+        st.steps = steps;
+        st.max_iter = p->max_iter;
+        st.mode = maxdelta ? 2 : (p->norm == LAP_NORM_L2_REL ? 0 : 1);
+        st.status = LAP_MAXITER;
+        st.r0 = r0;
+        st.tol = p->tol;
+        st.last_check = NAN;
+        st.last_nr = last_nr;
+        static_assert(sizeof(LoopState) <= 8 * sizeof(double), "pinned buffer holds 8 doubles");
+        ck(cudaMemcpyAsync(w.loop, &st, sizeof st, cudaMemcpyHostToDevice, s), "upload loop state");
+        ck(cudaGraphLaunch(it->second.first, s), "launch graph");
+        ck(cudaMemcpyAsync(h->pinned, w.loop, sizeof st, cudaMemcpyDeviceToHost, s), "copy loop state");
+        ck(cudaStreamSynchronize(s), "stream sync");
+        std::memcpy(&st, h->pinned, sizeof st);
+        add_launches(it->second.second * ((st.k - k) / steps));
+        return st;
+    }
+
     void run(lap_result* out)
     {
         out->status = LAP_MAXITER;
@@ -1080,6 +1222,7 @@ struct Solver {
         // its FP32 residual's
         const double r0 = fp32_norm ? partial_norm(f) : residual(f, nullptr);
         out->r0 = r0;
+        if (p->method == LAP_MG_MIXED) set_norm_scale(r0);
         if (!std::isfinite(r0)) {
             out->status = LAP_DIVERGED;
         } else if ((p->norm == LAP_NORM_L2_REL && r0 == 0.0) ||
@@ -1087,12 +1230,28 @@ struct Solver {
             out->status = LAP_CONVERGED;
         }
         int64_t k = 0;
+        double last_nr = r0;             // the L2 norm of the current iterate, when known
+        bool last_is_current = p->method != LAP_MG_FP32;
         while (out->status == LAP_MAXITER && k < p->max_iter) {
             const int64_t steps = std::min<int64_t>(p->check_every - (k % p->check_every), p->max_iter - k);
             const bool maxdelta = p->norm == LAP_NORM_MAXDELTA;
             const bool fused_maxd = maxdelta && (p->method == LAP_JACOBI || p->method == LAP_GS_RB ||
                                                  p->method == LAP_SOR_RB || p->method == LAP_GS_LEX ||
                                                  p->method == LAP_SOR_LEX);
+            if (tuner && tuner->done) set_tail(tuner->cand[tuner->best]);
+            if (device_loop_ok(k, steps, tuner)) {
+                const LoopState st = device_loop(k, r0, last_nr, maxdelta, fused_maxd);
+                k = st.k;
+                out->last_check = st.last_check;
+                out->status = st.status;
+                if (maxdelta) {
+                    last_is_current = false;
+                } else {
+                    last_nr = st.last_nr;
+                    last_is_current = p->method != LAP_MG_FP32;
+                }
+                continue;
+            }
             if (tuner) {
                 // the tail size of this period: the next untried candidate while tuning; a
                 // period that captures its graph is not timed
@@ -1120,14 +1279,18 @@ struct Solver {
                     ck(launch_maxdelta(f, w.aux, w.maxd, s), "max delta kernel");
                 val = read_maxd();
                 conv = val <= p->tol;
+                last_is_current = false;
             } else {
                 const Field cur{p->method == LAP_JACOBI ? jac_cur : f.p, f.m, f.n, f.pitch};
                 if (p->method == LAP_MG_FP32)
                     ck(launch_defect32_sumsq(w.levels32[0].u, w.levels32[0].q, c, w.partials, s),
                        "residual kernel");
-                const double nr = fp32_norm ? partial_norm(f) : residual(cur, nullptr);
+                const double nr = fp32_norm ? partial_norm(f, p->method == LAP_MG_MIXED && norm_sc > 0.0)
+                                            : residual(cur, nullptr);
                 val = p->norm == LAP_NORM_L2_REL ? nr / r0 : nr;
                 conv = p->norm == LAP_NORM_L2_REL ? nr <= p->tol * r0 : nr <= p->tol;
+                last_nr = nr;
+                last_is_current = p->method != LAP_MG_FP32;  // FP32 alone tests its FP32 residual
             }
             out->last_check = val;
             if (!std::isfinite(val))
@@ -1139,7 +1302,8 @@ struct Solver {
         if (p->method == LAP_JACOBI && jac_cur != f.p) copy_field(f.p, jac_cur);
         if (p->method == LAP_MG_FP32)
             ck(launch_to64(f, w.levels32[0].u.p, w.levels32[0].u.pitch, s), "conversion kernel");
-        out->r_final = residual(f, nullptr);
+        // the last stopping test already took the final iterate's norm (no second pass)
+        out->r_final = last_is_current ? last_nr : residual(f, nullptr);
     }
 };
 
@@ -2243,6 +2407,27 @@ int lap_line_sweep(lap_handle h, const lap_grid* g, double* psi_dev, double w, i
         check_device_ptr(h, psi_dev, "psi");
         line_half_sweep(h, Field{psi_dev, g->m, g->n, g->pitch}, make_coef(g->dx, g->dy), w, form,
                         direction, (cudaStream_t)stream);
+    });
+}
+
+int lap_check_rounding(lap_handle h, int64_t count, uint64_t seed, int64_t* mismatches)
+{
+    return guarded([&] {
+        if (!h || !mismatches) fail(LAP_EINVAL, "handle or result is NULL");
+        if (count < 0) fail(LAP_EINVAL, "count must be >= 0");
+        set_device(h);
+        unsigned long long* bad = (unsigned long long*)dev_alloc(h, sizeof(unsigned long long));
+        try {
+            ck(cudaMemset(bad, 0, sizeof(unsigned long long)), "zero counter");
+            ck(launch_check_rounding(count, seed, bad, nullptr), "rounding check kernel");
+            unsigned long long v = 0;
+            ck(cudaMemcpy(&v, bad, sizeof v, cudaMemcpyDeviceToHost), "copy counter");
+            *mismatches = (int64_t)v;
+        } catch (...) {
+            dev_free(h, bad, sizeof(unsigned long long));
+            throw;
+        }
+        dev_free(h, bad, sizeof(unsigned long long));
     });
 }
 

@@ -67,6 +67,24 @@ __device__ __forceinline__ double neighbour_sum(const FmaOps& o, double w_, doub
     return UNIT_BETA ? fadd(o, ns, ew) : __fma_rn(b2, ns, ew);
 }
 
+// x rounded to the nearest FP32 value (ties to even), bit-identical to __double2float_rn,
+// on the integer pipe when the result is a normal FP32 number or overflows: the 52-bit
+// fraction keeps its top 23 bits and rounds on the 29 below (a carry out of the fraction
+// raises the exponent, up to infinity). Zero, FP32-subnormal results, infinities and NaN
+// take the conversion instruction. On GB300 that instruction competes with the FP64
+// arithmetic of the residual kernels for the FP64 pipe.
+__device__ __forceinline__ float to_float_rn(double x)
+{
+    const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
+    const int e = (int)((b >> 52) & 0x7ff) - 1023 + 127;
+    if (e < 1 || e > 254) return __double2float_rn(x);
+    unsigned int out = ((unsigned int)e << 23) | ((unsigned int)(b >> 29) & 0x7fffffu);
+    const unsigned int rem = (unsigned int)b & 0x1fffffffu;
+    if (rem > 0x10000000u || (rem == 0x10000000u && (out & 1u))) ++out;
+    out |= (unsigned int)(b >> 32) & 0x80000000u;
+    return __uint_as_float(out);
+}
+
 // Deterministic warp reductions (fixed xor tree).
 __device__ __forceinline__ double warp_sum(double v)
 {

@@ -54,6 +54,24 @@ cudaError_t launch_defect_sumsq(const Field& f, const double* q, const Coef& c, 
                                 cudaStream_t s);
 // out[0] = sum(partials[0..count)), fixed order; out[1] = sqrt(out[0]).
 cudaError_t launch_sum_partials(const double* partials, int count, double* out, cudaStream_t s);
+// *bad += mismatches of the integer-pipe FP64 -> FP32 rounding against the instruction.
+cudaError_t launch_check_rounding(long long count, unsigned long long seed, unsigned long long* bad,
+                                  cudaStream_t s);
+// State of a device-resident solve loop (host-written before launch, read back after).
+struct LoopState {
+    long long k;         // iterations done
+    long long steps;     // iterations per period
+    long long max_iter;
+    int mode;            // 0 L2_REL, 1 L2_ABS, 2 MAXDELTA
+    int status;          // lap_status of the last test
+    double r0, tol;
+    double last_check;   // the last test's value
+    double last_nr;      // the L2 norm at the last test
+};
+// k += steps; test nrm[1] (divided by *scale when scale is set) or *maxd (MAXDELTA);
+// cudaGraphSetConditional(h, keep going).
+cudaError_t launch_loop_decide(LoopState* st, const double* nrm, const unsigned long long* maxd,
+                               const float* scale, cudaGraphConditionalHandle h, cudaStream_t s);
 // maxd := max |a - b| over interior nodes (bit pattern), a and b share f's shape/pitch.
 cudaError_t launch_maxdelta(const Field& a, const double* b, unsigned long long* maxd,
                             cudaStream_t s);
@@ -82,8 +100,11 @@ cudaError_t launch_prolong32(const Field32& fine_u, const float* ec, int64_t pit
 cudaError_t launch_coarse32(const Field32& u, const float* q, const double* ainv_t, cudaStream_t s);
 // r32 := (float) FP64 residual of psi, e32 := 0 (interiors), partials := per-block sums of r^2
 // (the same blocks and order as launch_defect_sumsq, so the sums are identical).
+// norm_scale (nullable device slot): sum the squares in FP32 as (scale r)^2 instead of FP64.
+// e32 nullable: leave the correction alone.
 cudaError_t launch_defect64_to32(const Field& psi, const Coef& c, float* r32, float* e32,
-                                 int64_t pitch32, double* partials, cudaStream_t s);
+                                 int64_t pitch32, double* partials, cudaStream_t s,
+                                 const float* norm_scale = nullptr);
 // FP32 alone: a (and b, nullable) := psi rounded to FP32 on every node; psi interior :=
 // (double) u; per-block FP64 sums of the squared FP32 residual (mixed_norm_blocks blocks).
 cudaError_t launch_to32(const Field& psi, float* a, float* b, int64_t pitch32, cudaStream_t s);

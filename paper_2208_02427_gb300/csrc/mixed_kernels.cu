@@ -126,25 +126,39 @@ __global__ void __launch_bounds__(1024)
 }
 
 // FP64 residual of psi, stored in FP32 for the inner cycle, sum of squares per block
-// (fixed-order reduction) for the stopping test; zeroes the FP32 correction e.
-template <bool UNIT>
+// (fixed-order reduction) for the stopping test; zeroes the FP32 correction e (nullable).
+// With a norm scale (sc: device slot, > 0) the squares are summed per thread in FP32 as
+// (sc r)^2: the norm needs a few digits, not FP64's sixteen, and this takes one of the
+// five FP64 operations per point off the FP64 pipe. sc is a power of two near 1 / ||r0||,
+// so the scaled squares stay within FP32's normal range down to 1e-13 ||r0||.
+template <bool UNIT, bool F32NORM>
 __global__ void __launch_bounds__(NORM_THREADS)
     defect64_to32_kernel(const double* __restrict__ psi, int m, int n, int64_t pitch, double b2,
                          double d, float* __restrict__ r32, float* __restrict__ e32,
-                         int64_t pitch32, double* __restrict__ partials)
+                         int64_t pitch32, double* __restrict__ partials,
+                         const float* __restrict__ sc)
 {
     const FmaOps o = load_fma_ops();
     double acc = 0.0;
+    float acc32 = 0.0f;
+    const float scale = F32NORM ? *sc : 0.0f;
     for (int j = 1 + blockIdx.x; j <= n - 2; j += gridDim.x)
         for (int i = 1 + threadIdx.x; i <= m - 2; i += NORM_THREADS) {
             const double* c = psi + (int64_t)j * pitch + i;
             const double s = neighbour_sum<UNIT>(o, c[-1], c[1], c[-pitch], c[pitch], b2);
             const double r = __fma_rn(-d, *c, s);
-            acc = __fma_rn(r, r, acc);
+            const float rf = to_float_rn(r);
+            if (F32NORM) {
+                const float rs = __fmul_rn(rf, scale);
+                acc32 = __fmaf_rn(rs, rs, acc32);
+            } else {
+                acc = __fma_rn(r, r, acc);
+            }
             const int64_t at = (int64_t)j * pitch32 + i;
-            r32[at] = __double2float_rn(r);
-            e32[at] = 0.0f;
+            r32[at] = rf;
+            if (e32) e32[at] = 0.0f;
         }
+    if (F32NORM) acc = (double)acc32;
     __shared__ double red[NORM_THREADS / 32];
     acc = warp_sum(acc);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
@@ -314,13 +328,20 @@ cudaError_t launch_coarse32(const Field32& u, const float* q, const double* ainv
 }
 
 cudaError_t launch_defect64_to32(const Field& psi, const Coef& c, float* r32, float* e32,
-                                 int64_t pitch32, double* partials, cudaStream_t s)
+                                 int64_t pitch32, double* partials, cudaStream_t s,
+                                 const float* norm_scale)
 {
     const int blocks = mixed_norm_blocks(psi.n);
-    if (c.unit_beta)
-        defect64_to32_kernel<true><<<blocks, NORM_THREADS, 0, s>>>(psi.p, psi.m, psi.n, psi.pitch, c.b2, c.d, r32, e32, pitch32, partials);
-    else
-        defect64_to32_kernel<false><<<blocks, NORM_THREADS, 0, s>>>(psi.p, psi.m, psi.n, psi.pitch, c.b2, c.d, r32, e32, pitch32, partials);
+#define LAP_D64(U, F)                                                                            \
+    defect64_to32_kernel<U, F><<<blocks, NORM_THREADS, 0, s>>>(psi.p, psi.m, psi.n, psi.pitch, c.b2, \
+                                                               c.d, r32, e32, pitch32, partials, \
+                                                               norm_scale)
+    if (c.unit_beta) {
+        if (norm_scale) LAP_D64(true, true); else LAP_D64(true, false);
+    } else {
+        if (norm_scale) LAP_D64(false, true); else LAP_D64(false, false);
+    }
+#undef LAP_D64
     note_launch();
     return cudaGetLastError();
 }

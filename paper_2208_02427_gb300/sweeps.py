@@ -32,11 +32,16 @@ def main():
                     help="V-cycle small-level tail size (0 = timed choice, -1 = none)")
     ap.add_argument("--unfused", action="store_true",
                     help="FP32 cycle: one kernel per pass instead of the tile kernels")
+    ap.add_argument("--no-graphs", action="store_true",
+                    help="direct launches (kernels inside conditional graphs cannot be profiled "
+                         "one by one)")
     a = ap.parse_args()
     m, n = a.m, a.n
     h = 1.0 / (m - 1)
     psi = wl.sine_edges(m, n)
     lap = b.Laplace()
+    if a.no_graphs:
+        lap.set_graphs(False)
     u = b.to_field(psi)
     other = b.field(m, n)
     mc, nc = (m - 1) // 2 + 1, (n - 1) // 2 + 1

@@ -111,3 +111,10 @@ def test_mixed_graphs_equal_direct_launches(b):
     h.close()
     for o in out[1:]:
         assert np.array_equal(o[0], out[0][0]) and o[1] == out[0][1]
+
+
+def test_integer_pipe_fp32_rounding_matches_the_instruction(lap):
+    """The residual kernels round FP64 to FP32 on the integer pipe; it must equal the
+    conversion instruction bit for bit (random bits, range edges, ties, all-ones)."""
+    assert lap.check_rounding(1 << 26, seed=20220804) == 0
+    assert lap.check_rounding(1 << 24, seed=7) == 0

@@ -393,7 +393,9 @@ def test_graph_replay_equals_direct_launches(b, kw):
     outs[0][2].close()
     for o in outs[1:]:
         assert np.array_equal(o[0], outs[0][0]) and o[1] == outs[0][1]
-        assert o[3] == outs[0][3]  # a replayed graph counts the kernels it runs
+    # a replayed graph counts the kernels it runs; with graphs the stopping test of whole
+    # check periods runs on the device (one more kernel per period)
+    assert outs[1][3] == outs[2][3] >= outs[0][3]
 
 
 @pytest.mark.parametrize("shape", [(3, 3), (25, 17), (67, 45), (130, 97)])
