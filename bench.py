@@ -436,6 +436,9 @@ def main():
                  ("mg_v22", dict(method="mg", nu1=2, nu2=2))]
         out = {"grid": "25x17, dx = dy = 0.25 m, psi = 1 on wall AB, 0 elsewhere",
                "stopping": "max|psi^{k+1} - psi^k| <= 1e-9 tested every iteration (Eq. 16)",
+               "orderings": "*_lex: the paper's lexicographic order; gs_rb, sor_rb: red-black; "
+                            "slorb, adi: zebra lines (the paper's counts are for successive "
+                            "lines, which the oracle reproduces: 49 and 31)",
                "timing": "host wall clock around lap_solve (launches, graph replays and the "
                          "per-iteration host check included), median over 20 solves"}
         for name, kw in cases:

@@ -321,7 +321,7 @@ __global__ void __launch_bounds__(TAIL_THREADS)
 __global__ void __launch_bounds__(BT)
     b_sumsq_kernel(const BatchItem* __restrict__ items, const BatchLevel<double>* __restrict__ lv,
                    const int* __restrict__ active, double* __restrict__ partials,
-                   const BatchLevel<float>* __restrict__ lv32)
+                   const BatchLevel<float>* __restrict__ lv32, const double* __restrict__ r0)
 {
     const BatchItem it = items[blockIdx.x];
     const BatchLevel<double> L = lv[it.level];
@@ -337,18 +337,38 @@ __global__ void __launch_bounds__(BT)
         e32 = lv32[it.level].u;
         p32 = lv32[it.level].pitch;
     }
+    // Mixed problems whose r0 is known sum (s r)^2 in FP32, s = 2^-e with r0 = f 2^e (exact
+    // scaling; the stopping norm needs a few digits), and store the partial descaled.
+    float sc = 0.0f;
+    if (r32 && r0) {
+        const double z = r0[L.problem];
+        if (z > 0.0 && isfinite(z)) {
+            const int e = ilogb(z);
+            if (e >= -100 && e <= 100) sc = ldexpf(1.0f, -e);
+        }
+    }
+    float acc32 = 0.0f;
     for (Walk k(wdt); k.r < it.rows; k.next()) {
         const int j = it.row0 + k.r, i = 1 + k.c;
         const double* c = L.u + (int64_t)j * L.pitch + i;
         const double s = A.nsum(c[-1], c[1], c[-L.pitch], c[L.pitch], L.b2, L.unit_beta);
         const double r = __fma_rn(-L.d, *c, s);
-        acc = __fma_rn(r, r, acc);
         if (r32) {
+            const float rf = to_float_rn(r);
+            if (sc > 0.0f) {
+                const float rs = __fmul_rn(rf, sc);
+                acc32 = __fmaf_rn(rs, rs, acc32);
+            } else {
+                acc = __fma_rn(r, r, acc);
+            }
             const int64_t at = (int64_t)j * p32 + i;
-            r32[at] = to_float_rn(r);
+            r32[at] = rf;
             e32[at] = 0.0f;
+        } else {
+            acc = __fma_rn(r, r, acc);
         }
     }
+    if (sc > 0.0f) acc = (double)acc32 / ((double)sc * (double)sc);  // exact: powers of two
     __shared__ double red[BT / 32];
     acc = warp_sum(acc);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
@@ -493,10 +513,11 @@ template cudaError_t launch_b_tail<double>(const TailJob*, int, const BatchLevel
 template cudaError_t launch_b_tail<float>(const TailJob*, int, const BatchLevel<float>*, const int*, int, int, bool, double, int, cudaStream_t, bool);
 
 cudaError_t launch_b_sumsq(const BatchList& l, const BatchLevel<double>* lv, const int* active,
-                           double* partials, const BatchLevel<float>* lv32, cudaStream_t s)
+                           double* partials, const BatchLevel<float>* lv32, cudaStream_t s,
+                           const double* r0)
 {
     if (l.count == 0) return cudaSuccess;
-    b_sumsq_kernel<<<l.count, BT, 0, s>>>(l.items, lv, active, partials, lv32);
+    b_sumsq_kernel<<<l.count, BT, 0, s>>>(l.items, lv, active, partials, lv32, r0);
     note_launch();
     return cudaGetLastError();
 }

@@ -929,6 +929,19 @@ struct Solver {
         smooth(lv, p->nu2);
     }
 
+    // The whole solve in one CTA (solve_cta_kernel): point methods with the paper's stopping
+    // rule on grids whose sweeps cost less than the launches and host checks of the
+    // multi-CTA path (a block-wide max is order-free, so the test is the host loop's bit for
+    // bit). Red-black and Jacobi up to 4096 points: about the size where one SM sweeps as
+    // fast as two launches take; lexicographic grids always run on one SM.
+    bool solve_cta_ok() const
+    {
+        if (p->norm != LAP_NORM_MAXDELTA) return false;
+        if (p->method == LAP_GS_LEX || p->method == LAP_SOR_LEX) return true;
+        return (p->method == LAP_JACOBI || p->method == LAP_GS_RB || p->method == LAP_SOR_RB) &&
+               (int64_t)f.m * f.n <= 4096;
+    }
+
     // The iterations between two stopping tests, enqueued on stream s.
     void period(int64_t steps, bool maxdelta, bool fused_maxd)
     {
@@ -1232,6 +1245,30 @@ struct Solver {
         int64_t k = 0;
         double last_nr = r0;             // the L2 norm of the current iterate, when known
         bool last_is_current = p->method != LAP_MG_FP32;
+        if (out->status == LAP_MAXITER && p->max_iter > 0 && solve_cta_ok()) {
+            // small grid, the paper's stopping rule: the whole solve is one kernel
+            LoopState st{};
+            st.k = 0;
+            st.steps = p->check_every;
+            st.max_iter = p->max_iter;
+            st.mode = 2;
+            st.status = LAP_MAXITER;
+            st.r0 = r0;
+            st.tol = p->tol;
+            st.last_check = NAN;
+            st.last_nr = r0;
+            ck(cudaMemcpyAsync(w.loop, &st, sizeof st, cudaMemcpyHostToDevice, s), "upload loop state");
+            const int kind = p->method == LAP_JACOBI ? 0 : (p->method == LAP_GS_RB || p->method == LAP_SOR_RB ? 1 : 2);
+            const bool gs = p->method == LAP_GS_RB || p->method == LAP_GS_LEX;
+            ck(launch_solve_cta(f, c, kind, gs, w.wslot, w.loop, s), "one-CTA solve kernel");
+            ck(cudaMemcpyAsync(h->pinned, w.loop, sizeof st, cudaMemcpyDeviceToHost, s), "copy loop state");
+            ck(cudaStreamSynchronize(s), "stream sync");
+            std::memcpy(&st, h->pinned, sizeof st);
+            k = st.k;
+            out->status = st.status;
+            out->last_check = st.last_check;
+            last_is_current = false;
+        }
         while (out->status == LAP_MAXITER && k < p->max_iter) {
             const int64_t steps = std::min<int64_t>(p->check_every - (k % p->check_every), p->max_iter - k);
             const bool maxdelta = p->norm == LAP_NORM_MAXDELTA;
@@ -1656,7 +1693,7 @@ extern "C" int lap_solve_batched(lap_handle h, int count, const lap_grid* grids,
                 // fused: the level-0 ascents did psi += e except where a tail holds level 0
                 ck(launch_b_update(L.fused ? list(L.upd0) : norm_list, lv64, active, lv32, st),
                    "batched update");
-                ck(launch_b_sumsq(norm_list, lv64, active, partials, lv32, st), "batched residual");
+                ck(launch_b_sumsq(norm_list, lv64, active, partials, lv32, st, r0), "batched residual");
             } else {
                 enqueue_vcycle(list, L, lv64, active, jobs, *p, p->smoother_w, st);
                 ck(launch_b_sumsq(norm_list, lv64, active, partials, nullptr, st), "batched residual");
@@ -2136,7 +2173,7 @@ extern "C" int lap_server_step(lap_server S, void* stream, int* running, int* qu
         for (int k = 0; k < S->sor_sweeps && P.sor.second; ++k)
             for (int colour = 0; colour < 2; ++colour)
                 ck(launch_b_rb(list(P.sor), lv64, active, colour, false, 1.0, st, true), "server sweep");
-        ck(launch_b_sumsq(list(P.norm), lv64, active, pnorm, lv32, st), "server residual");
+        ck(launch_b_sumsq(list(P.norm), lv64, active, pnorm, lv32, st, dr0), "server residual");
         ck(launch_b_converge(pnorm, fn, R, active, dr0, rnow, iters, status, remaining, 1, true, 0.0,
                              st, dtol), "server convergence");
         auto down = [&](void* dst, const void* src, size_t bytes) {

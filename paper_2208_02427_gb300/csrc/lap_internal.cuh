@@ -122,6 +122,12 @@ size_t lex_smem_bytes(int m, int n);
 cudaError_t prepare_lex_kernels(size_t smem);
 cudaError_t launch_lex_sweeps(const Field& f, const Coef& c, bool gs, double w, int nsweeps,
                               unsigned long long* maxd, cudaStream_t s);
+// A whole solve in one CTA with the stopping rule of Eq. 16 (max |change| <= tol, tested
+// after every st->steps iterations, up to st->max_iter): kind 0 Jacobi (2 m n doubles of
+// shared memory), 1 red-black, 2 lexicographic (m n doubles); gs or SOR with {w, 1 - w}
+// from wslot. Reads st->k, steps, max_iter, tol, last_check; writes k, status, last_check.
+cudaError_t launch_solve_cta(const Field& f, const Coef& c, int kind, bool gs, const double* wslot,
+                             LoopState* st, cudaStream_t s);
 
 // ---- V-cycle over many grids (batch_kernels.cu) -------------------------------------
 // One level of one problem. Level 0 of the FP64 solve is the caller's field (q null).
@@ -177,9 +183,12 @@ template <class T>
 cudaError_t launch_b_tail(const TailJob* jobs, int count, const BatchLevel<T>* lv, const int* active,
                           int nu1, int nu2, bool gs, double w, int max_unknowns, cudaStream_t s,
                           bool per_level_w = false);
-// per-item FP64 sum of squares of the residual; with lv32 also r32 := residual, e32 := 0
+// per-item FP64 sum of squares of the residual; with lv32 also r32 := residual, e32 := 0;
+// with r0 (per problem) the mixed problems sum their squares in FP32 after an exact
+// power-of-two scaling from r0 (the partials are stored descaled)
 cudaError_t launch_b_sumsq(const BatchList& l, const BatchLevel<double>* lv, const int* active,
-                           double* partials, const BatchLevel<float>* lv32, cudaStream_t s);
+                           double* partials, const BatchLevel<float>* lv32, cudaStream_t s,
+                           const double* r0 = nullptr);
 cudaError_t launch_b_update(const BatchList& l, const BatchLevel<double>* lv, const int* active,
                             const BatchLevel<float>* lv32, cudaStream_t s);
 // mode 0: record r0 (retire problems already converged); mode 1: count a cycle and test.

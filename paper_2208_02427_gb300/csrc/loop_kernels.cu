@@ -1,0 +1,98 @@
+// loop_kernels.cu -- the device-side stopping test of a solve loop, and a self-check.
+//
+// loop_decide_kernel runs inside the body of a conditional CUDA graph node: after each check
+// period it applies the host loop's stopping rule (Eq. 16 or the L2 rules) and sets the
+// loop's condition. check_rounding_kernel compares the residual kernels' integer-pipe
+// FP64 -> FP32 rounding with the conversion instruction.
+#include "lap_device.cuh"
+#include "lap_internal.cuh"
+
+namespace lap {
+
+namespace {
+
+// The stopping test of a device-resident solve loop (Eq. 16 or the L2 rules), run after each
+// period inside the loop body of a conditional CUDA graph: the same arithmetic as the host's
+// test; clears the loop's condition when the solve stops or the next period would pass
+// max_iter.
+__global__ void loop_decide_kernel(LoopState* st, const double* __restrict__ nrm,
+                                   const unsigned long long* __restrict__ maxd,
+                                   const float* __restrict__ scale, cudaGraphConditionalHandle h)
+{
+    if (threadIdx.x != 0) return;
+    st->k += st->steps;
+    double val, nr = st->last_nr;
+    bool conv;
+    if (st->mode == 2) {
+        val = __longlong_as_double((long long)*maxd);
+        conv = val <= st->tol;
+    } else {
+        nr = nrm[1];
+        if (scale) nr = nr / (double)*scale;
+        val = st->mode == 0 ? nr / st->r0 : nr;
+        conv = st->mode == 0 ? nr <= st->tol * st->r0 : nr <= st->tol;
+    }
+    st->last_check = val;
+    st->last_nr = nr;
+    int status = 1;  // LAP_MAXITER
+    if (!isfinite(val)) status = 2;  // LAP_DIVERGED
+    else if (conv) status = 0;       // LAP_CONVERGED
+    st->status = status;
+    cudaGraphSetConditional(h, status == 1 && st->k + st->steps <= st->max_iter ? 1u : 0u);
+}
+
+}  // namespace
+
+namespace {
+
+__device__ __forceinline__ unsigned long long mix64(unsigned long long x)
+{
+    x += 0x9e3779b97f4a7c15ull;
+    x = (x ^ (x >> 30)) * 0xbf58476d1ce4e5b9ull;
+    x = (x ^ (x >> 27)) * 0x94d049bb133111ebull;
+    return x ^ (x >> 31);
+}
+
+// to_float_rn against the conversion instruction on `count` doubles drawn from seed:
+// random bit patterns, exponents near the FP32 range's ends, exact ties and all-ones
+// fractions, in turn.
+__global__ void check_rounding_kernel(long long count, unsigned long long seed,
+                                      unsigned long long* bad)
+{
+    unsigned long long local = 0;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < count;
+         k += (long long)gridDim.x * blockDim.x) {
+        const unsigned long long r = mix64(seed ^ (unsigned long long)k), r2 = mix64(r);
+        unsigned long long b;
+        switch (k & 3) {
+        case 0: b = r; break;
+        case 1: b = (r & 0x800fffffffffffffull) | ((unsigned long long)(1023 - 130 + (r2 % 270)) << 52); break;
+        case 2: b = (r & 0x800fffffe0000000ull) | 0x10000000ull | ((unsigned long long)(1023 + (int)(r2 % 60) - 30) << 52); break;
+        default: b = (r & 0xfff0000000000000ull) | 0x000fffffffffffffull; break;
+        }
+        const double x = __longlong_as_double((long long)b);
+        const float want = __double2float_rn(x), got = to_float_rn(x);
+        if (__float_as_uint(want) != __float_as_uint(got) && !(want != want && got != got)) ++local;
+    }
+    if (local) atomicAdd(bad, local);
+}
+
+}  // namespace
+
+cudaError_t launch_check_rounding(long long count, unsigned long long seed, unsigned long long* bad,
+                                  cudaStream_t s)
+{
+    check_rounding_kernel<<<152 * 8, 256, 0, s>>>(count, seed, bad);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_loop_decide(LoopState* st, const double* nrm, const unsigned long long* maxd,
+                               const float* scale, cudaGraphConditionalHandle h, cudaStream_t s)
+{
+    loop_decide_kernel<<<1, 32, 0, s>>>(st, nrm, maxd, scale, h);
+    note_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace lap

@@ -5,7 +5,8 @@
 Methods: jacobi, gs, sor (one red-black sweep = 2 launches), residual, adi-x, adi-y
 (zebra half sweeps), restrict, prolong, mg (one V(2,2) cycle), mg_mixed (one FP32
 V(2,2) cycle inside one FP64 defect-correction step), batched / batched_mixed (one cycle
-of --count uneven grids, 33..513 per side, through lap_solve_batched). Used for profiling
+of --count uneven grids, 33..513 per side, through lap_solve_batched), step (one step of
+bench.py: RB-SOR at w_opt and V(2,2) multigrid to 1e-10 on the grid). Used for profiling
 a single kernel under ncu: small launch counts, the same kernels the solver runs.
 """
 from __future__ import annotations
@@ -60,6 +61,18 @@ def main():
         "mg_mixed": lambda: lap.solve(u, h, h, method="mg_mixed", tol=0.0, max_iter=1,
                                       tail_size=a.tail, unfused=a.unfused),
     }
+    if a.method == "step":
+        # one step of the benchmark: RB-SOR at w_opt (tested every 100 sweeps) and the V(2,2)
+        # multigrid, each to ||r|| <= 1e-10 ||r0|| from the same initial field
+        init = u.clone()
+
+        def step():
+            u.copy_(init)
+            lap.solve(u, h, h, method="sor", w=w, tol=1e-10, check_every=100, max_iter=200000)
+            u.copy_(init)
+            lap.solve(u, h, h, method="mg", tol=1e-10, nu1=2, nu2=2, coarsest_min=5, max_iter=100)
+
+        ops["step"] = step
     if a.method.startswith("batched"):
         shapes = wl.batch_shapes(a.count, seed=wl.SEED_BASE + 2)
         fields = [b.to_field(wl.random_ring(bm, bn, seed=wl.SEED_BASE + 2 + 10 * k))
