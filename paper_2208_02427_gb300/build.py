@@ -18,10 +18,10 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "liblaplace.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["lap_api.cu", "point_kernels.cu", "line_kernels.cu", "mg_kernels.cu",
+SOURCES = ["lap_api.cu", "lap_batched.cu", "lap_server.cu", "point_kernels.cu", "line_kernels.cu", "mg_kernels.cu",
            "mixed_kernels.cu", "lex_kernels.cu", "batch_kernels.cu", "fused32_kernels.cu",
            "loop_kernels.cu"]
-HEADERS = ["lap_internal.cuh", "lap_device.cuh"]
+HEADERS = ["lap_internal.cuh", "lap_device.cuh", "lap_host.cuh"]
 
 
 def nvcc() -> str:

@@ -1,30 +1,16 @@
 // lap_api.cu -- the C ABI of liblaplace.so (declared in include/laplace.h): handles,
 // argument checks, host-side precomputation (line-solver tables, coarsest-grid inverse)
 // and the solver loops that drive the kernels on the caller's stream.
-#include <cuda_runtime.h>
-
-#include <algorithm>
-#include <atomic>
-#include <cmath>
-#include <cstdio>
-#include <cstring>
-#include <deque>
-#include <map>
-#include <mutex>
-#include <stdexcept>
-#include <string>
-#include <tuple>
-#include <vector>
-
-#include "../../include/laplace.h"
-#include "lap_internal.cuh"
+#include "lap_host.cuh"
 
 namespace lap {
 
 static std::atomic<int64_t> g_launches{0};
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
-static int64_t launches_now() { return g_launches.load(); }
-static void add_launches(int64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+int64_t launches_now() { return g_launches.load(); }
+void add_launches(int64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+thread_local std::string t_last_error;
 
 Coef make_coef(double dx, double dy)
 {
@@ -39,121 +25,6 @@ Coef make_coef(double dx, double dy)
     c.inv_d_shift = (mant == 0.5 && 1 - e >= 1 && 1 - e <= 60) ? 1 - e : 0;
     return c;
 }
-
-// Chooses the small-level tail size of one shape by timing. The tail changes how a V-cycle
-// is launched and nothing else (every candidate gives the same iterates bit for bit), so
-// the candidates are tried on the first cycles of real solves: each cycle (or check
-// period) runs with the next untried candidate, its device time per cycle is recorded,
-// and once every candidate has been timed the fastest is kept for the handle's lifetime.
-struct TailTuner {
-    std::vector<int> cand;  // tail sizes; -1 = no tail
-    std::vector<double> ms; // best time per cycle seen, +inf = not tried yet
-    int best = 0;
-    bool done = false;
-    void init(std::vector<int> c)
-    {
-        cand = std::move(c);
-        ms.assign(cand.size(), HUGE_VAL);
-        best = 0;
-        done = cand.size() <= 1;
-    }
-    int next() const
-    {
-        if (done) return best;
-        for (size_t i = 0; i < cand.size(); ++i)
-            if (ms[i] == HUGE_VAL) return (int)i;
-        return best;
-    }
-    void record(int i, double v)
-    {
-        if (done || i < 0 || i >= (int)cand.size() || !(v > 0.0)) return;
-        ms[i] = std::min(ms[i], v);
-        bool all = true;
-        for (size_t k = 0; k < cand.size(); ++k) {
-            if (ms[k] == HUGE_VAL) all = false;
-            else if (ms[k] < ms[best] || ms[best] == HUGE_VAL) best = (int)k;
-        }
-        done = all;
-    }
-};
-
-}  // namespace lap
-
-using namespace lap;
-
-namespace {
-
-thread_local std::string t_last_error;
-
-struct Error {
-    int code;
-    std::string msg;
-};
-
-[[noreturn]] void fail(int code, const std::string& msg) { throw Error{code, msg}; }
-
-void ck(cudaError_t e, const char* what)
-{
-    if (e != cudaSuccess) fail(LAP_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
-}
-
-template <class F>
-int guarded(F&& body)
-{
-    try {
-        body();
-        return LAP_OK;
-    } catch (const Error& e) {
-        t_last_error = e.msg;
-        return e.code;
-    } catch (const std::bad_alloc&) {
-        t_last_error = "host allocation failed";
-        return LAP_ENOMEM;
-    } catch (...) {
-        t_last_error = "unexpected internal error";
-        return LAP_ECUDA;
-    }
-}
-
-int64_t round_up(int64_t v, int64_t a) { return (v + a - 1) / a * a; }
-
-// Host-side copy of a line-solver table set plus its device allocation.
-struct LineEntry {
-    LineTables t;
-    double* dev = nullptr;
-    size_t bytes = 0;
-};
-
-struct CoarseEntry {
-    double* dev = nullptr;
-    size_t bytes = 0;
-};
-
-}  // namespace
-
-struct lap_handle_s {
-    int device = 0;
-    size_t budget = 0;    // 0 = unlimited
-    size_t held = 0;      // bytes of device memory held (arena + tables)
-    double* arena = nullptr;
-    size_t arena_bytes = 0;
-    double* pinned = nullptr;  // 8 doubles of pinned host memory for results
-    std::map<std::tuple<int, double, double>, LineEntry> lines;
-    std::map<std::tuple<int, int, double>, CoarseEntry> coarse;
-    // CUDA graphs of whole check periods (the iterations between two stopping tests),
-    // keyed by every pointer and parameter baked into them; replayed on the caller's stream
-    bool use_graphs = true;
-    cudaStream_t capture = nullptr;
-    std::map<std::string, std::pair<cudaGraphExec_t, int64_t>> graphs;  // exec, kernels
-    // Small-level tail sizes chosen by timing, per shape (see TailTuner)
-    std::map<std::string, lap::TailTuner> tail_tuners;
-    cudaEvent_t ev[2] = {nullptr, nullptr};
-    // transposed copy of a field for the y-lines of line relaxation (grown on demand)
-    double* tscratch = nullptr;
-    size_t tscratch_bytes = 0;
-};
-
-namespace {
 
 void set_device(lap_handle h) { ck(cudaSetDevice(h->device), "cudaSetDevice"); }
 
@@ -202,31 +73,6 @@ double* arena(lap_handle h, size_t bytes)
     return h->arena;
 }
 
-// Carves aligned sub-buffers out of a byte range.
-struct Carver {
-    char* base;
-    size_t off = 0;
-    explicit Carver(void* b) : base((char*)b) {}
-    template <class T>
-    T* take(size_t count)
-    {
-        off = (size_t)round_up((int64_t)off, 256);
-        T* p = (T*)(base + off);
-        off += count * sizeof(T);
-        return p;
-    }
-};
-// The same carving sequence without memory, to size the arena first.
-struct Sizer {
-    size_t off = 0;
-    template <class T>
-    T* take(size_t count)
-    {
-        off = (size_t)round_up((int64_t)off, 256) + count * sizeof(T);
-        return nullptr;
-    }
-};
-
 void check_grid(const lap_grid* g)
 {
     if (!g) fail(LAP_EINVAL, "grid is NULL");
@@ -237,7 +83,7 @@ void check_grid(const lap_grid* g)
     if ((int64_t)g->n * g->pitch > ((int64_t)1 << 40)) fail(LAP_EUNSUPPORTED, "field too large");
 }
 
-void check_device_ptr(lap_handle h, const void* p, const char* what, bool allow_null = false)
+void check_device_ptr(lap_handle h, const void* p, const char* what, bool allow_null)
 {
     if (!p) {
         if (allow_null) return;
@@ -445,7 +291,6 @@ void line_half_sweep(lap_handle h, const Field& f, const Coef& c, double w, int 
 
 // ---- coarsest-grid inverse ------------------------------------------------------------
 
-constexpr int COARSE_MAX_UNKNOWNS = 1024;
 
 const double* coarse_inverse(lap_handle h, int m, int n, double b2, double d)
 {
@@ -501,14 +346,6 @@ const double* coarse_inverse(lap_handle h, int m, int n, double b2, double d)
     return h->coarse.emplace(key, e).first->second.dev;
 }
 
-// ---- multigrid hierarchy -----------------------------------------------------------------
-
-struct Level {
-    Field u;            // level 0: the caller's field; deeper: the correction
-    double* q = nullptr;  // source term (levels >= 1)
-    double* r = nullptr;  // residual scratch (all but the coarsest), u's pitch
-};
-
 int mg_level_count(int m, int n, int coarsest_min, int max_levels)
 {
     int levels = 1;
@@ -520,6 +357,49 @@ int mg_level_count(int m, int n, int coarsest_min, int max_levels)
     }
     return levels;
 }
+
+// Tail sizes worth timing for a batch of V-cycles (one CTA per problem runs the levels at or
+// below the size) and for one grid (one CTA in all).
+std::vector<int> tail_candidates(bool batched, bool fp32, int tail_size)
+{
+    if (tail_size != 0) return {tail_size};
+    if (batched) return {-1, 33, 65, 129, 257};
+    return fp32 ? std::vector<int>{-1, 33, 65, 129, 257} : std::vector<int>{-1, 17, 33, 65};
+}
+
+std::string tuner_key(char kind, const lap_params* p, const std::vector<int>& shape)
+{
+    uint64_t hsh = 1469598103934665603ull;  // FNV-1a over the shapes
+    for (int v : shape) {
+        hsh ^= (uint32_t)v;
+        hsh *= 1099511628211ull;
+    }
+    char buf[192];
+    std::snprintf(buf, sizeof buf, "%c %d %d %d %d %d %.17g %d %d %d %zu %llx", kind, p->method,
+                  p->nu1, p->nu2, p->coarsest_min, p->max_levels, p->smoother_w, p->inner_cycles,
+                  p->tail_size, p->unfused, shape.size(), (unsigned long long)hsh);
+    return buf;
+}
+
+cudaEvent_t tuner_event(lap_handle h, int k)
+{
+    if (!h->ev[k]) ck(cudaEventCreate(&h->ev[k]), "create event");
+    return h->ev[k];
+}
+
+}  // namespace lap
+
+using namespace lap;
+
+namespace {
+
+// ---- multigrid hierarchy -----------------------------------------------------------------
+
+struct Level {
+    Field u;            // level 0: the caller's field; deeper: the correction
+    double* q = nullptr;  // source term (levels >= 1)
+    double* r = nullptr;  // residual scratch (all but the coarsest), u's pitch
+};
 
 // ---- the per-call workspace ----------------------------------------------------------------
 
@@ -606,35 +486,6 @@ size_t work_bytes(const lap_grid* g, const lap_params* p)
     Work w;
     carve(sz, w, g, p);
     return sz.off;
-}
-
-// Tail sizes worth timing for a batch of V-cycles (one CTA per problem runs the levels at or
-// below the size) and for one grid (one CTA in all).
-std::vector<int> tail_candidates(bool batched, bool fp32, int tail_size)
-{
-    if (tail_size != 0) return {tail_size};
-    if (batched) return {-1, 33, 65, 129, 257};
-    return fp32 ? std::vector<int>{-1, 33, 65, 129, 257} : std::vector<int>{-1, 17, 33, 65};
-}
-
-std::string tuner_key(char kind, const lap_params* p, const std::vector<int>& shape)
-{
-    uint64_t hsh = 1469598103934665603ull;  // FNV-1a over the shapes
-    for (int v : shape) {
-        hsh ^= (uint32_t)v;
-        hsh *= 1099511628211ull;
-    }
-    char buf[192];
-    std::snprintf(buf, sizeof buf, "%c %d %d %d %d %d %.17g %d %d %d %zu %llx", kind, p->method,
-                  p->nu1, p->nu2, p->coarsest_min, p->max_levels, p->smoother_w, p->inner_cycles,
-                  p->tail_size, p->unfused, shape.size(), (unsigned long long)hsh);
-    return buf;
-}
-
-cudaEvent_t tuner_event(lap_handle h, int k)
-{
-    if (!h->ev[k]) ck(cudaEventCreate(&h->ev[k]), "create event");
-    return h->ev[k];
 }
 
 // ---- the solver loop ---------------------------------------------------------------------
@@ -1345,871 +1196,6 @@ struct Solver {
 };
 
 }  // namespace
-
-// ---- many grids at once ---------------------------------------------------------------------
-
-namespace {
-
-constexpr int BATCH_ITEM_POINTS = 2048;  // interior points per work item (rows are not split)
-
-void add_items(std::vector<BatchItem>& items, int level_index, int m, int n)
-{
-    const int per = std::max(1, BATCH_ITEM_POINTS / std::max(1, m - 2));
-    for (int r = 1; r <= n - 2; r += per) items.push_back(BatchItem{level_index, r, std::min(per, n - 1 - r)});
-}
-
-// Per-level work lists of one V-cycle over a set of problems: [first, count) into the items
-// (fine, all, coarse) or into the tail jobs (tail).
-struct LevelLists {
-    std::vector<std::pair<int, int>> fine, all, coarse, tail;
-    std::vector<std::pair<int, int>> tiles;  // FP32 tile items of the fine lists (fused cycle)
-    std::pair<int, int> upd0{0, 0};  // fused: level-0 items of the problems without level-0 tiles
-    bool fused = false;
-    int levels = 0;
-    int max_coarse = 0;
-};
-
-// First level of a problem that the small-level tail runs (both sides <= tail_size), or
-// nlev when it has none.
-int tail_start(const BatchLevel<double>* lv, int nlev, int tail_size)
-{
-    if (tail_size <= 0) return nlev;
-    for (int l = 0; l < nlev; ++l)
-        if (lv[l].m <= tail_size && lv[l].n <= tail_size) return l;
-    return nlev;
-}
-
-// Lists of one V-cycle over problems `who`: problem q owns levels base[q] .. base[q] +
-// nlev[q] - 1 of lv. Levels above a problem's tail go through item lists, the tail is one job.
-// With tiles, the fine levels also get the tile items of the fused FP32 descent/ascent.
-void build_lists(LevelLists& L, std::vector<BatchItem>& items, std::vector<TailJob>& jobs,
-                 const std::vector<int>& who, const std::vector<int>& base,
-                 const std::vector<int>& nlev, const std::vector<BatchLevel<double>>& lv,
-                 int tail_size, std::vector<TileItem>* tiles = nullptr, int nu1 = 0, int nu2 = 0)
-{
-    L.fused = tiles != nullptr;
-    L.tiles.assign(0, {0, 0});
-    L.levels = 0;
-    for (int q : who) L.levels = std::max(L.levels, nlev[q]);
-    L.fine.assign(L.levels, {0, 0});
-    L.all.assign(L.levels, {0, 0});
-    L.coarse.assign(L.levels, {0, 0});
-    L.tail.assign(L.levels, {0, 0});
-    L.tiles.assign(L.levels, {0, 0});
-    std::vector<int> t(who.size());
-    for (size_t k = 0; k < who.size(); ++k) t[k] = tail_start(&lv[base[who[k]]], nlev[who[k]], tail_size);
-    for (int l = 0; l < L.levels; ++l) {
-        const int f0 = (int)items.size();
-        for (size_t k = 0; k < who.size(); ++k) {
-            const int q = who[k];
-            if (nlev[q] - 1 > l && l < t[k]) add_items(items, base[q] + l, lv[base[q] + l].m, lv[base[q] + l].n);
-        }
-        L.fine[l] = {f0, (int)items.size() - f0};
-        if (tiles) {
-            const int t0 = (int)tiles->size();
-            for (size_t k = 0; k < who.size(); ++k) {
-                const int q = who[k];
-                if (!(nlev[q] - 1 > l && l < t[k])) continue;
-                const BatchLevel<double>& d = lv[base[q] + l];
-                int tx, ty, ntx, nty;
-                fused32_tile(d.m, d.n, nu1, nu2, &tx, &ty, &ntx, &nty);
-                for (int by = 0; by < nty; ++by)
-                    for (int bx = 0; bx < ntx; ++bx)
-                        tiles->push_back(TileItem{base[q] + l, 1 + bx * tx, 1 + by * ty, tx, ty});
-            }
-            L.tiles[l] = {t0, (int)tiles->size() - t0};
-        }
-        const int a0 = (int)items.size();
-        for (size_t k = 0; k < who.size(); ++k) {
-            const int q = who[k];
-            if (nlev[q] > l && l <= t[k]) add_items(items, base[q] + l, lv[base[q] + l].m, lv[base[q] + l].n);
-        }
-        L.all[l] = {a0, (int)items.size() - a0};
-        const int c0 = (int)items.size();
-        for (size_t k = 0; k < who.size(); ++k) {
-            const int q = who[k];
-            if (nlev[q] - 1 == l && t[k] == nlev[q]) {
-                const BatchLevel<double>& d = lv[base[q] + l];
-                items.push_back(BatchItem{base[q] + l, 1, d.n - 2});
-                L.max_coarse = std::max(L.max_coarse, (d.m - 2) * (d.n - 2));
-            }
-        }
-        L.coarse[l] = {c0, (int)items.size() - c0};
-        const int j0 = (int)jobs.size();
-        for (size_t k = 0; k < who.size(); ++k) {
-            const int q = who[k];
-            if (t[k] == l && l < nlev[q]) {
-                jobs.push_back(TailJob{base[q] + l, base[q] + nlev[q] - 1});
-                const BatchLevel<double>& d = lv[base[q] + nlev[q] - 1];
-                L.max_coarse = std::max(L.max_coarse, (d.m - 2) * (d.n - 2));
-            }
-        }
-        L.tail[l] = {j0, (int)jobs.size() - j0};
-    }
-    if (tiles) {
-        const int u0 = (int)items.size();
-        for (size_t k = 0; k < who.size(); ++k) {
-            const int q = who[k];
-            if (t[k] == 0 || nlev[q] == 1) add_items(items, base[q], lv[base[q]].m, lv[base[q]].n);
-        }
-        L.upd0 = {u0, (int)items.size() - u0};
-    }
-}
-
-// One V-cycle over every active problem of L: descend (coarsest solves and tails start when
-// the descent reaches a problem's coarsest or tail level), then ascend; each problem sees
-// its own V-cycle.
-template <class ListFn, class T>
-void enqueue_vcycle(ListFn list, const LevelLists& L, const BatchLevel<T>* lv, const int* active,
-                    const TailJob* jobs, const lap_params& p, double smoother_w, cudaStream_t st)
-{
-    const bool gs = smoother_w == 1.0;
-    for (int l = 0; l < L.levels; ++l) {
-        ck(launch_b_coarse(list(L.coarse[l]), lv, active, L.max_coarse, st), "batched coarse");
-        ck(launch_b_tail(jobs + L.tail[l].first, L.tail[l].second, lv, active, p.nu1, p.nu2, gs,
-                         smoother_w, L.max_coarse, st),
-           "batched tail");
-        if (l == L.levels - 1) break;
-        for (int k = 0; k < p.nu1; ++k)
-            for (int colour = 0; colour < 2; ++colour)
-                ck(launch_b_rb(list(L.fine[l]), lv, active, colour, gs, smoother_w, st), "batched smoother");
-        ck(launch_b_defect(list(L.fine[l]), lv, active, st), "batched defect");
-        ck(launch_b_restrict(list(L.all[l + 1]), lv, active, st), "batched restrict");
-    }
-    for (int l = L.levels - 2; l >= 0; --l) {
-        ck(launch_b_prolong(list(L.fine[l]), lv, active, st), "batched prolong");
-        for (int k = 0; k < p.nu2; ++k)
-            for (int colour = 0; colour < 2; ++colour)
-                ck(launch_b_rb(list(L.fine[l]), lv, active, colour, gs, smoother_w, st), "batched smoother");
-    }
-}
-
-// The FP32 V-cycle with each fine level's descent and ascent as one tile launch over all
-// problems (first: the level-0 corrections start at zero).
-// fold64 (nullable): the level-0 ascent adds its result to these FP64 fields (psi += e).
-template <class ListFn>
-void enqueue_vcycle32_fused(ListFn list, const LevelLists& L, const BatchLevel<float>* lv,
-                            const int* active, const TailJob* jobs, const TileItem* tiles,
-                            const lap_params& p, double smoother_w, bool first, cudaStream_t st,
-                            const BatchLevel<double>* fold64 = nullptr)
-{
-    const bool gs = smoother_w == 1.0;
-    for (int l = 0; l < L.levels; ++l) {
-        ck(launch_b_coarse(list(L.coarse[l]), lv, active, L.max_coarse, st), "batched coarse");
-        ck(launch_b_tail(jobs + L.tail[l].first, L.tail[l].second, lv, active, p.nu1, p.nu2, gs,
-                         smoother_w, L.max_coarse, st),
-           "batched tail");
-        if (l == L.levels - 1) break;
-        ck(launch_b_down32(tiles + L.tiles[l].first, L.tiles[l].second, lv, active, p.nu1,
-                           l > 0 || first, gs, smoother_w, st),
-           "batched descent");
-    }
-    for (int l = L.levels - 2; l >= 0; --l)
-        ck(launch_b_up32(tiles + L.tiles[l].first, L.tiles[l].second, lv, active, p.nu2, gs,
-                         smoother_w, st, l == 0 ? fold64 : nullptr),
-           "batched ascent");
-}
-
-struct BatchPlan {
-    std::vector<BatchLevel<double>> lv64;
-    std::vector<BatchLevel<float>> lv32;
-    std::vector<int> nlev, base;       // levels and first level index per problem
-    std::vector<BatchItem> items;      // all work lists, back to back
-    std::vector<TailJob> jobs;         // tail jobs of every candidate, back to back
-    std::vector<TileItem> tiles;       // FP32 tile items of every candidate (fused cycle)
-    std::vector<LevelLists> cands;     // the V-cycle's lists for each tail-size candidate
-    std::pair<int, int> norm;          // level-0 items of every problem, problem by problem
-    std::vector<int> first_item;       // per problem: its first item in the norm list (+ end)
-    int max_coarse_unknowns = 0;
-    int levels = 0;
-};
-
-
-}  // namespace
-
-extern "C" int lap_solve_batched(lap_handle h, int count, const lap_grid* grids,
-                                 double* const* psi_devs, const lap_params* p, lap_result* results,
-                                 void* stream)
-{
-    return guarded([&] {
-        if (!h) fail(LAP_EINVAL, "handle is NULL");
-        if (count < 1 || !grids || !psi_devs || !results) fail(LAP_EINVAL, "empty or NULL batch");
-        check_params(p);
-        if (p->method != LAP_MG && p->method != LAP_MG_MIXED)
-            fail(LAP_EINVAL, "batched solves take LAP_MG or LAP_MG_MIXED");
-        if (p->norm == LAP_NORM_MAXDELTA) fail(LAP_EINVAL, "batched solves stop on an L2 norm");
-        set_device(h);
-        const bool mixed = p->method == LAP_MG_MIXED;
-        cudaStream_t s = (cudaStream_t)stream;
-        BatchPlan P;
-        P.nlev.resize(count);
-        P.base.resize(count);
-        // ---- level descriptors (buffers are carved below) ----
-        for (int q = 0; q < count; ++q) {
-            const lap_grid* g = &grids[q];
-            check_grid(g);
-            check_device_ptr(h, psi_devs[q], "psi");
-            const int L = mg_level_count(g->m, g->n, p->coarsest_min, p->max_levels);
-            P.nlev[q] = L;
-            P.base[q] = (int)P.lv64.size();
-            P.levels = std::max(P.levels, L);
-            const Coef c = make_coef(g->dx, g->dy);
-            int m = g->m, n = g->n;
-            for (int l = 0; l < L; ++l) {
-                BatchLevel<double> d{};
-                d.m = m;
-                d.n = n;
-                d.pitch = l == 0 ? g->pitch : round_up(m, 32);
-                d.problem = q;
-                d.unit_beta = c.unit_beta;
-                d.inv_d_shift = c.inv_d_shift;
-                d.b2 = c.b2;
-                d.d = c.d;
-                d.inv_d = c.inv_d;
-                BatchLevel<float> f{};
-                f.m = m;
-                f.n = n;
-                f.pitch = round_up(m, 32);
-                f.problem = q;
-                f.unit_beta = c.unit_beta;
-                f.inv_d_shift = 0;
-                f.b2 = c.b2;
-                f.d = c.d;
-                f.inv_d = c.inv_d;
-                if (l == L - 1) {
-                    if ((int64_t)(m - 2) * (n - 2) > COARSE_MAX_UNKNOWNS)
-                        fail(LAP_EUNSUPPORTED, "coarsest level with more than 1024 unknowns");
-                    d.ainv_t = f.ainv_t = coarse_inverse(h, m, n, c.b2, c.d);
-                    P.max_coarse_unknowns = std::max(P.max_coarse_unknowns, (m - 2) * (n - 2));
-                }
-                P.lv64.push_back(d);
-                P.lv32.push_back(f);
-                m = (m - 1) / 2 + 1;
-                n = (n - 1) / 2 + 1;
-            }
-        }
-        // ---- work lists: one set per tail-size candidate ----
-        std::vector<int> all_problems(count), shape;
-        for (int q = 0; q < count; ++q) {
-            all_problems[q] = q;
-            shape.push_back(grids[q].m);
-            shape.push_back(grids[q].n);
-        }
-        TailTuner& tuner = h->tail_tuners[tuner_key('B', p, shape)];
-        if (tuner.cand.empty()) tuner.init(tail_candidates(true, mixed, p->tail_size));
-        const bool fused = mixed && !p->unfused && fused32_supported(p->nu1, p->nu2);
-        if (fused) ck(prepare_fused32(), "tile kernel attributes");
-        for (int cand : tuner.cand) {
-            LevelLists L;
-            build_lists(L, P.items, P.jobs, all_problems, P.base, P.nlev, P.lv64, cand,
-                        fused ? &P.tiles : nullptr, p->nu1, p->nu2);
-            P.max_coarse_unknowns = std::max(P.max_coarse_unknowns, L.max_coarse);
-            P.cands.push_back(L);
-        }
-        const int n0 = (int)P.items.size();
-        for (int q = 0; q < count; ++q) {
-            P.first_item.push_back((int)P.items.size() - n0);
-            add_items(P.items, P.base[q], grids[q].m, grids[q].n);
-        }
-        P.first_item.push_back((int)P.items.size() - n0);
-        P.norm = {n0, (int)P.items.size() - n0};
-        // ---- memory: level buffers, descriptors, lists, state ----
-        auto carve_all = [&](auto& cv) {
-            for (int q = 0; q < count; ++q)
-                for (int l = 0; l < P.nlev[q]; ++l) {
-                    const int k = P.base[q] + l;
-                    BatchLevel<double>& d = P.lv64[k];
-                    BatchLevel<float>& f = P.lv32[k];
-                    const bool last = l == P.nlev[q] - 1;
-                    if (!mixed) {
-                        if (l == 0) {
-                            d.u = psi_devs[q];
-                            d.q = nullptr;
-                        } else {
-                            d.u = cv.template take<double>((size_t)d.n * d.pitch);
-                            d.q = cv.template take<double>((size_t)d.n * d.pitch);
-                        }
-                        d.r = last ? nullptr : cv.template take<double>((size_t)d.n * d.pitch);
-                    } else {
-                        if (l == 0) d.u = psi_devs[q];
-                        f.u = cv.template take<float>((size_t)f.n * f.pitch);
-                        f.q = cv.template take<float>((size_t)f.n * f.pitch);
-                        f.r = last ? nullptr : cv.template take<float>((size_t)f.n * f.pitch);
-                    }
-                }
-            auto* lv64 = cv.template take<BatchLevel<double>>(P.lv64.size());
-            auto* lv32 = cv.template take<BatchLevel<float>>(P.lv32.size());
-            auto* items = cv.template take<BatchItem>(P.items.size());
-            auto* jobs = cv.template take<TailJob>(std::max<size_t>(1, P.jobs.size()));
-            auto* tiles = cv.template take<TileItem>(std::max<size_t>(1, P.tiles.size()));
-            auto* first = cv.template take<int>(P.first_item.size());
-            auto* active = cv.template take<int>(count);
-            auto* status = cv.template take<int>(count);
-            auto* remaining = cv.template take<int>(1);
-            auto* iters = cv.template take<long long>(count);
-            auto* r0 = cv.template take<double>(count);
-            auto* rnow = cv.template take<double>(count);
-            auto* partials = cv.template take<double>(std::max(1, P.norm.second));
-            return std::make_tuple(lv64, lv32, items, jobs, tiles, first, active, status, remaining,
-                                   iters, r0, rnow, partials);
-        };
-        Sizer sz;
-        carve_all(sz);
-        Carver cv(arena(h, sz.off));
-        auto [lv64, lv32, items, jobs, tiles, first, active, status, remaining, iters, r0, rnow,
-              partials] = carve_all(cv);
-        // zero every level buffer (rings of corrections stay zero), then upload tables
-        const size_t level_bytes = (size_t)((char*)lv64 - (char*)h->arena);
-        if (level_bytes) ck(cudaMemsetAsync(h->arena, 0, level_bytes, s), "zero levels");
-        std::vector<int> ones(count, 1);
-        const int cnt = count;
-        ck(cudaMemcpyAsync(lv64, P.lv64.data(), P.lv64.size() * sizeof(P.lv64[0]), cudaMemcpyHostToDevice, s), "upload levels");
-        ck(cudaMemcpyAsync(lv32, P.lv32.data(), P.lv32.size() * sizeof(P.lv32[0]), cudaMemcpyHostToDevice, s), "upload levels");
-        ck(cudaMemcpyAsync(items, P.items.data(), P.items.size() * sizeof(BatchItem), cudaMemcpyHostToDevice, s), "upload items");
-        if (!P.jobs.empty())
-            ck(cudaMemcpyAsync(jobs, P.jobs.data(), P.jobs.size() * sizeof(TailJob), cudaMemcpyHostToDevice, s), "upload jobs");
-        if (!P.tiles.empty())
-            ck(cudaMemcpyAsync(tiles, P.tiles.data(), P.tiles.size() * sizeof(TileItem), cudaMemcpyHostToDevice, s), "upload tiles");
-        ck(cudaMemcpyAsync(first, P.first_item.data(), P.first_item.size() * sizeof(int), cudaMemcpyHostToDevice, s), "upload items");
-        ck(cudaMemcpyAsync(active, ones.data(), count * sizeof(int), cudaMemcpyHostToDevice, s), "upload flags");
-        ck(cudaMemcpyAsync(status, ones.data(), count * sizeof(int), cudaMemcpyHostToDevice, s), "upload flags");
-        ck(cudaMemcpyAsync(remaining, &cnt, sizeof(int), cudaMemcpyHostToDevice, s), "upload count");
-        ck(cudaMemsetAsync(iters, 0, count * sizeof(long long), s), "zero iterations");
-        ck(cudaStreamSynchronize(s), "stream sync");  // host vectors above go out of scope
-        auto list = [&](std::pair<int, int> r) { return BatchList{items + r.first, r.second}; };
-        const BatchList norm_list = list(P.norm);
-        const bool rel = p->norm == LAP_NORM_L2_REL;
-        // ---- one cycle (V-cycle(s) and stopping test) with tail-size candidate c ----
-        auto cycle = [&](int c, cudaStream_t st) {
-            const LevelLists& L = P.cands[c];
-            if (mixed) {
-                for (int k = 0; k < p->inner_cycles; ++k) {
-                    if (L.fused)
-                        enqueue_vcycle32_fused(list, L, lv32, active, jobs, tiles, *p, p->smoother_w,
-                                               k == 0, st, k == p->inner_cycles - 1 ? lv64 : nullptr);
-                    else
-                        enqueue_vcycle(list, L, lv32, active, jobs, *p, p->smoother_w, st);
-                }
-                // fused: the level-0 ascents did psi += e except where a tail holds level 0
-                ck(launch_b_update(L.fused ? list(L.upd0) : norm_list, lv64, active, lv32, st),
-                   "batched update");
-                ck(launch_b_sumsq(norm_list, lv64, active, partials, lv32, st, r0), "batched residual");
-            } else {
-                enqueue_vcycle(list, L, lv64, active, jobs, *p, p->smoother_w, st);
-                ck(launch_b_sumsq(norm_list, lv64, active, partials, nullptr, st), "batched residual");
-            }
-            ck(launch_b_converge(partials, first, count, active, r0, rnow, iters, status, remaining,
-                                 1, rel, p->tol, st), "batched convergence");
-        };
-        // initial residuals (and, for the mixed solver, the first FP32 right-hand sides)
-        ck(launch_b_sumsq(norm_list, lv64, active, partials, mixed ? lv32 : nullptr, s), "batched residual");
-        ck(launch_b_converge(partials, first, count, active, r0, rnow, iters, status, remaining, 0,
-                             rel, p->tol, s), "batched convergence");
-        // one cycle per candidate as a graph, captured on the handle's stream when first
-        // used and replayed on the caller's
-        std::vector<std::pair<cudaGraphExec_t, int64_t>> exec(P.cands.size(), {nullptr, 0});
-        auto release = [&] {
-            for (auto& e : exec)
-                if (e.first) cudaGraphExecDestroy(e.first);
-        };
-        auto launch_cycle = [&](int c) {
-            if (!h->use_graphs) {
-                cycle(c, s);
-                return;
-            }
-            if (!exec[c].first) {
-                if (!h->capture)
-                    ck(cudaStreamCreateWithFlags(&h->capture, cudaStreamNonBlocking), "capture stream");
-                const int64_t before = launches_now();
-                ck(cudaStreamBeginCapture(h->capture, cudaStreamCaptureModeThreadLocal), "begin capture");
-                cudaGraph_t g = nullptr;
-                try {
-                    cycle(c, h->capture);
-                } catch (...) {
-                    cudaStreamEndCapture(h->capture, &g);
-                    if (g) cudaGraphDestroy(g);
-                    cudaGetLastError();
-                    throw;
-                }
-                ck(cudaStreamEndCapture(h->capture, &g), "end capture");
-                exec[c].second = launches_now() - before;
-                add_launches(-exec[c].second);
-                const cudaError_t e = cudaGraphInstantiate(&exec[c].first, g, 0);
-                cudaGraphDestroy(g);
-                ck(e, "instantiate graph");
-            }
-            ck(cudaGraphLaunch(exec[c].first, s), "launch graph");
-            add_launches(exec[c].second);
-        };
-        int64_t done = 0;
-        int left = count;
-        try {
-            while (done < p->max_iter) {
-                ck(cudaMemcpyAsync(h->pinned, remaining, sizeof(int), cudaMemcpyDeviceToHost, s), "copy count");
-                ck(cudaStreamSynchronize(s), "stream sync");
-                std::memcpy(&left, h->pinned, sizeof(int));
-                if (left == 0) break;
-                const int64_t steps = std::min<int64_t>(p->check_every, p->max_iter - done);
-                for (int64_t k = 0; k < steps; ++k) {
-                    const int c = tuner.next();
-                    if (tuner.done) {
-                        launch_cycle(c);
-                        continue;
-                    }
-                    // not tuned yet: time this cycle (the graph of c is captured before e0)
-                    if (h->use_graphs && !exec[c].first) {
-                        launch_cycle(c);  // first use captures and runs it once
-                        ck(cudaStreamSynchronize(s), "stream sync");
-                        continue;
-                    }
-                    ck(cudaEventRecord(tuner_event(h, 0), s), "record event");
-                    launch_cycle(c);
-                    ck(cudaEventRecord(tuner_event(h, 1), s), "record event");
-                    ck(cudaEventSynchronize(tuner_event(h, 1)), "event sync");
-                    float ms = 0.f;
-                    ck(cudaEventElapsedTime(&ms, tuner_event(h, 0), tuner_event(h, 1)), "event time");
-                    tuner.record(c, ms);
-                }
-                done += steps;
-            }
-        } catch (...) {
-            release();
-            throw;
-        }
-        release();
-        // ---- results ----
-        std::vector<long long> it(count);
-        std::vector<int> st(count);
-        std::vector<double> a(count), z(count);
-        ck(cudaMemcpyAsync(it.data(), iters, count * sizeof(long long), cudaMemcpyDeviceToHost, s), "copy results");
-        ck(cudaMemcpyAsync(st.data(), status, count * sizeof(int), cudaMemcpyDeviceToHost, s), "copy results");
-        ck(cudaMemcpyAsync(a.data(), r0, count * sizeof(double), cudaMemcpyDeviceToHost, s), "copy results");
-        ck(cudaMemcpyAsync(z.data(), rnow, count * sizeof(double), cudaMemcpyDeviceToHost, s), "copy results");
-        ck(cudaStreamSynchronize(s), "stream sync");
-        for (int q = 0; q < count; ++q) {
-            results[q].status = st[q];
-            results[q].iters = it[q];
-            results[q].r0 = a[q];
-            results[q].r_final = z[q];
-            results[q].last_check = rel ? (a[q] > 0 ? z[q] / a[q] : 0.0) : z[q];
-        }
-    });
-}
-
-// ---- serving: continuous batching over a stream of requests ----------------------------------
-
-namespace {
-
-struct SrvRequest {
-    int64_t id = 0;
-    lap_grid g{};
-    double* psi = nullptr;
-    int method = LAP_MG_MIXED;  // LAP_MG, LAP_MG_MIXED or LAP_SOR_RB
-    double w = 1.0, tol = 1e-10;
-    int64_t max_iter = 0;       // V-cycles, or sweeps for SOR
-    int state = 0;              // 0 queued, 1 running, 2 finished
-    bool fresh = true;          // admitted, initial residual not yet taken
-    size_t off = 0, bytes = 0;  // block of the pool holding its hierarchy
-    int nlev = 1;
-    std::vector<BatchLevel<double>> lv64;
-    std::vector<BatchLevel<float>> lv32;
-    double r0 = 0.0, rnow = 0.0;
-    long long steps = 0;        // iterations run (V-cycles, or sweep batches for SOR)
-    lap_result res{};
-};
-
-}  // namespace
-
-struct lap_server_s {
-    lap_handle h = nullptr;
-    size_t budget = 0;
-    char* pool = nullptr;
-    std::map<size_t, size_t> free_blocks;  // offset -> bytes
-    std::deque<int64_t> queue;
-    std::map<int64_t, SrvRequest> reqs;
-    int64_t next_id = 1;
-    int max_running = 1024;
-    int sor_sweeps = 50;
-    lap_params mg{};  // nu1, nu2, coarsest_min, max_levels, smoother_w, inner_cycles
-    char* stage = nullptr;
-    size_t stage_bytes = 0;
-};
-
-namespace {
-
-bool pool_alloc(lap_server S, size_t bytes, size_t* off)
-{
-    for (auto it = S->free_blocks.begin(); it != S->free_blocks.end(); ++it)
-        if (it->second >= bytes) {
-            *off = it->first;
-            const size_t rest = it->second - bytes;
-            const size_t at = it->first + bytes;
-            S->free_blocks.erase(it);
-            if (rest) S->free_blocks[at] = rest;
-            return true;
-        }
-    return false;
-}
-
-void pool_free(lap_server S, size_t off, size_t bytes)
-{
-    auto it = S->free_blocks.emplace(off, bytes).first;
-    auto next = std::next(it);
-    if (next != S->free_blocks.end() && it->first + it->second == next->first) {
-        it->second += next->second;
-        S->free_blocks.erase(next);
-    }
-    if (it != S->free_blocks.begin()) {
-        auto prev = std::prev(it);
-        if (prev->first + prev->second == it->first) {
-            prev->second += it->second;
-            S->free_blocks.erase(it);
-        }
-    }
-}
-
-// Level descriptors of a request's hierarchy, carved from `cv` (a Sizer or a Carver).
-template <class C>
-void srv_levels(lap_server S, SrvRequest& r, C& cv)
-{
-    const Coef c = make_coef(r.g.dx, r.g.dy);
-    const bool mg = r.method != LAP_SOR_RB;
-    r.nlev = mg ? mg_level_count(r.g.m, r.g.n, S->mg.coarsest_min, S->mg.max_levels) : 1;
-    r.lv64.assign(r.nlev, BatchLevel<double>{});
-    r.lv32.assign(r.nlev, BatchLevel<float>{});
-    int m = r.g.m, n = r.g.n;
-    for (int l = 0; l < r.nlev; ++l) {
-        BatchLevel<double>& d = r.lv64[l];
-        BatchLevel<float>& f = r.lv32[l];
-        d.m = f.m = m;
-        d.n = f.n = n;
-        d.pitch = l == 0 ? r.g.pitch : round_up(m, 32);
-        f.pitch = round_up(m, 32);
-        d.unit_beta = f.unit_beta = c.unit_beta;
-        d.inv_d_shift = c.inv_d_shift;
-        d.b2 = f.b2 = c.b2;
-        d.d = f.d = c.d;
-        d.inv_d = f.inv_d = c.inv_d;
-        d.w = r.w;
-        d.omw = 1.0 - r.w;
-        const bool last = l == r.nlev - 1;
-        if (mg && last) {
-            if ((int64_t)(m - 2) * (n - 2) > COARSE_MAX_UNKNOWNS)
-                fail(LAP_EUNSUPPORTED, "coarsest level with more than 1024 unknowns");
-            d.ainv_t = f.ainv_t = nullptr;  // set at admission (needs the device)
-        }
-        if (l == 0) d.u = r.psi;
-        if (r.method == LAP_MG) {
-            if (l > 0) {
-                d.u = cv.template take<double>((size_t)n * d.pitch);
-                d.q = cv.template take<double>((size_t)n * d.pitch);
-            }
-            if (!last) d.r = cv.template take<double>((size_t)n * d.pitch);
-        } else if (r.method == LAP_MG_MIXED) {
-            f.u = cv.template take<float>((size_t)n * f.pitch);
-            f.q = cv.template take<float>((size_t)n * f.pitch);
-            if (!last) f.r = cv.template take<float>((size_t)n * f.pitch);
-        }
-        m = (m - 1) / 2 + 1;
-        n = (n - 1) / 2 + 1;
-    }
-}
-
-// Small-level tail sizes of the server's V-cycles (one CTA per request runs its levels at
-// or below the size).
-constexpr int SERVER_TAIL_FP64 = 33;
-constexpr int SERVER_TAIL_FP32 = 129;
-
-struct SrvPlan {
-    std::vector<BatchLevel<double>> lv64;
-    std::vector<BatchLevel<float>> lv32;
-    std::vector<BatchItem> items;
-    std::vector<TailJob> jobs;
-    std::vector<TileItem> tiles;
-    LevelLists mg64, mg32;
-    std::pair<int, int> sor, update, init, norm;
-    std::vector<int> first_init, first_norm;
-};
-
-}  // namespace
-
-extern "C" int lap_server_create(lap_server* out, lap_handle h, size_t hbm_budget_bytes,
-                                 const lap_params* mg, int max_running, int sor_sweeps)
-{
-    return guarded([&] {
-        if (!out || !h) fail(LAP_EINVAL, "NULL server or handle");
-        *out = nullptr;
-        if (max_running < 1 || sor_sweeps < 1) fail(LAP_EINVAL, "max_running and sor_sweeps must be >= 1");
-        lap_params d;
-        lap_default_params(&d);
-        if (mg) d = *mg;
-        d.method = LAP_MG;
-        check_params(&d);
-        set_device(h);
-        lap_server S = new lap_server_s();
-        S->h = h;
-        S->budget = hbm_budget_bytes;
-        S->mg = d;
-        S->max_running = max_running;
-        S->sor_sweeps = sor_sweeps;
-        if (hbm_budget_bytes) {
-            try {
-                S->pool = (char*)dev_alloc(h, hbm_budget_bytes);
-            } catch (...) {
-                delete S;
-                throw;
-            }
-            S->free_blocks[0] = hbm_budget_bytes;
-        }
-        *out = S;
-    });
-}
-
-extern "C" void lap_server_destroy(lap_server S)
-{
-    if (!S) return;
-    cudaSetDevice(S->h->device);
-    cudaDeviceSynchronize();
-    dev_free(S->h, S->pool, S->budget);
-    dev_free(S->h, S->stage, S->stage_bytes);
-    delete S;
-}
-
-extern "C" int lap_server_submit(lap_server S, const lap_grid* g, double* psi_dev, int method,
-                                 double w, double tol, int64_t max_iter, int64_t* id)
-{
-    return guarded([&] {
-        if (!S || !id) fail(LAP_EINVAL, "NULL server or id");
-        check_grid(g);
-        set_device(S->h);
-        check_device_ptr(S->h, psi_dev, "psi");
-        if (method != LAP_MG && method != LAP_MG_MIXED && method != LAP_SOR_RB)
-            fail(LAP_EINVAL, "served methods: LAP_MG, LAP_MG_MIXED, LAP_SOR_RB");
-        if (method == LAP_SOR_RB && !(w > 0.0 && w < 2.0)) fail(LAP_EINVAL, "w must lie in (0, 2)");
-        if (!(tol >= 0.0) || max_iter < 0) fail(LAP_EINVAL, "tol >= 0 and max_iter >= 0");
-        SrvRequest r;
-        r.id = S->next_id++;
-        r.g = *g;
-        r.psi = psi_dev;
-        r.method = method;
-        r.w = method == LAP_SOR_RB ? w : 1.0;
-        r.tol = tol;
-        r.max_iter = max_iter;
-        Sizer sz;
-        srv_levels(S, r, sz);
-        r.bytes = (size_t)round_up((int64_t)sz.off, 256);  // every block starts 256-byte aligned
-        if (r.bytes > S->budget && r.bytes) fail(LAP_ENOMEM, "request needs more than the whole budget");
-        *id = r.id;
-        S->queue.push_back(r.id);
-        S->reqs.emplace(r.id, std::move(r));
-    });
-}
-
-extern "C" int lap_server_poll(lap_server S, int64_t id, lap_result* out)
-{
-    if (!S || !out) return LAP_EINVAL;
-    auto it = S->reqs.find(id);
-    if (it == S->reqs.end()) return LAP_EINVAL;
-    if (it->second.state != 2) return 0;
-    *out = it->second.res;
-    S->reqs.erase(it);
-    return 1;
-}
-
-extern "C" int lap_server_step(lap_server S, void* stream, int* running, int* queued)
-{
-    return guarded([&] {
-        if (!S) fail(LAP_EINVAL, "server is NULL");
-        set_device(S->h);
-        cudaStream_t st = (cudaStream_t)stream;
-        int nrun = 0;
-        for (auto& kv : S->reqs) nrun += kv.second.state == 1;
-        // ---- admission: FIFO, while a slot is free and the hierarchy fits the pool ----
-        while (!S->queue.empty() && nrun < S->max_running) {
-            SrvRequest& r = S->reqs.at(S->queue.front());
-            size_t off = 0;
-            if (r.bytes && !pool_alloc(S, r.bytes, &off)) break;
-            r.off = off;
-            Carver cv(S->pool + off);
-            srv_levels(S, r, cv);
-            if (r.method != LAP_SOR_RB) {
-                BatchLevel<double>& d = r.lv64[r.nlev - 1];
-                const double* ainv = coarse_inverse(S->h, d.m, d.n, d.b2, d.d);
-                d.ainv_t = ainv;
-                r.lv32[r.nlev - 1].ainv_t = ainv;
-            }
-            if (r.bytes) ck(cudaMemsetAsync(S->pool + off, 0, r.bytes, st), "zero hierarchy");
-            r.state = 1;
-            r.fresh = true;
-            S->queue.pop_front();
-            ++nrun;
-        }
-        std::vector<SrvRequest*> run;
-        for (auto& kv : S->reqs)
-            if (kv.second.state == 1) run.push_back(&kv.second);
-        if (queued) *queued = (int)S->queue.size();
-        if (run.empty()) {
-            if (running) *running = 0;
-            return;
-        }
-        // ---- the plan of this step ----
-        const int R = (int)run.size();
-        SrvPlan P;
-        std::vector<int> base(R);
-        for (int q = 0; q < R; ++q) {
-            base[q] = (int)P.lv64.size();
-            for (int l = 0; l < run[q]->nlev; ++l) {
-                BatchLevel<double> d = run[q]->lv64[l];
-                BatchLevel<float> f = run[q]->lv32[l];
-                d.problem = f.problem = q;
-                P.lv64.push_back(d);
-                P.lv32.push_back(f);
-            }
-        }
-        std::vector<int> nlev(R);
-        for (int q = 0; q < R; ++q) nlev[q] = run[q]->nlev;
-        auto mg_lists = [&](int method, LevelLists& L) {
-            std::vector<int> who;
-            for (int q = 0; q < R; ++q)
-                if (run[q]->method == method) who.push_back(q);
-            // no timing across steps (the running set changes): fixed tail sizes
-            const int ts = S->mg.tail_size != 0 ? S->mg.tail_size
-                                                : (method == LAP_MG_MIXED ? SERVER_TAIL_FP32 : SERVER_TAIL_FP64);
-            const bool fused = method == LAP_MG_MIXED && !S->mg.unfused &&
-                               fused32_supported(S->mg.nu1, S->mg.nu2);
-            build_lists(L, P.items, P.jobs, who, base, nlev, P.lv64, ts, fused ? &P.tiles : nullptr,
-                        S->mg.nu1, S->mg.nu2);
-        };
-        mg_lists(LAP_MG, P.mg64);
-        mg_lists(LAP_MG_MIXED, P.mg32);
-        auto level0 = [&](auto pred, std::vector<int>* first) {
-            const int i0 = (int)P.items.size();
-            for (int q = 0; q < R; ++q) {
-                if (first) first->push_back((int)P.items.size() - i0);
-                if (pred(*run[q])) add_items(P.items, base[q], run[q]->g.m, run[q]->g.n);
-            }
-            if (first) first->push_back((int)P.items.size() - i0);
-            return std::make_pair(i0, (int)P.items.size() - i0);
-        };
-        P.sor = level0([](const SrvRequest& r) { return r.method == LAP_SOR_RB; }, nullptr);
-        P.update = level0([](const SrvRequest& r) { return r.method == LAP_MG_MIXED; }, nullptr);
-        P.init = level0([](const SrvRequest& r) { return r.fresh; }, &P.first_init);
-        P.norm = level0([](const SrvRequest&) { return true; }, &P.first_norm);
-        // ---- stage: descriptors, items, per-request state ----
-        std::vector<int> act(R, 1), stat(R, 1);
-        std::vector<long long> it(R);
-        std::vector<double> r0(R), tolv(R);
-        for (int q = 0; q < R; ++q) {
-            it[q] = run[q]->steps;
-            r0[q] = run[q]->r0;
-            tolv[q] = run[q]->tol;
-        }
-        auto carve_stage = [&](auto& cv) {
-            auto* lv64 = cv.template take<BatchLevel<double>>(P.lv64.size());
-            auto* lv32 = cv.template take<BatchLevel<float>>(P.lv32.size());
-            auto* items = cv.template take<BatchItem>(std::max<size_t>(1, P.items.size()));
-            auto* jobs = cv.template take<TailJob>(std::max<size_t>(1, P.jobs.size()));
-            auto* tiles = cv.template take<TileItem>(std::max<size_t>(1, P.tiles.size()));
-            auto* fi = cv.template take<int>(P.first_init.size());
-            auto* fn = cv.template take<int>(P.first_norm.size());
-            auto* active = cv.template take<int>(R);
-            auto* status = cv.template take<int>(R);
-            auto* remaining = cv.template take<int>(1);
-            auto* iters = cv.template take<long long>(R);
-            auto* dr0 = cv.template take<double>(R);
-            auto* rnow = cv.template take<double>(R);
-            auto* dtol = cv.template take<double>(R);
-            auto* pinit = cv.template take<double>(std::max(1, P.init.second));
-            auto* pnorm = cv.template take<double>(std::max(1, P.norm.second));
-            return std::make_tuple(lv64, lv32, items, jobs, tiles, fi, fn, active, status, remaining,
-                                   iters, dr0, rnow, dtol, pinit, pnorm);
-        };
-        Sizer sz;
-        carve_stage(sz);
-        if (sz.off > S->stage_bytes) {
-            dev_free(S->h, S->stage, S->stage_bytes);
-            S->stage = nullptr;
-            S->stage_bytes = 0;
-            const size_t nb = (size_t)round_up((int64_t)sz.off * 2, 1 << 20);
-            S->stage = (char*)dev_alloc(S->h, nb);
-            S->stage_bytes = nb;
-        }
-        Carver cv(S->stage);
-        auto [lv64, lv32, items, jobs, tiles, fi, fn, active, status, remaining, iters, dr0, rnow, dtol,
-              pinit, pnorm] = carve_stage(cv);
-        auto up = [&](void* dst, const void* src, size_t bytes) {
-            if (bytes) ck(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st), "upload plan");
-        };
-        up(lv64, P.lv64.data(), P.lv64.size() * sizeof(P.lv64[0]));
-        up(lv32, P.lv32.data(), P.lv32.size() * sizeof(P.lv32[0]));
-        up(items, P.items.data(), P.items.size() * sizeof(BatchItem));
-        up(jobs, P.jobs.data(), P.jobs.size() * sizeof(TailJob));
-        up(tiles, P.tiles.data(), P.tiles.size() * sizeof(TileItem));
-        if (P.mg32.fused) ck(prepare_fused32(), "tile kernel attributes");
-        up(fi, P.first_init.data(), P.first_init.size() * sizeof(int));
-        up(fn, P.first_norm.data(), P.first_norm.size() * sizeof(int));
-        up(active, act.data(), R * sizeof(int));
-        up(status, stat.data(), R * sizeof(int));
-        up(remaining, &R, sizeof(int));
-        up(iters, it.data(), R * sizeof(long long));
-        up(dr0, r0.data(), R * sizeof(double));
-        up(dtol, tolv.data(), R * sizeof(double));
-        auto list = [&](std::pair<int, int> r) { return BatchList{items + r.first, r.second}; };
-        // ---- one iteration of every running request ----
-        ck(launch_b_sumsq(list(P.init), lv64, active, pinit, lv32, st), "server residual");
-        ck(launch_b_converge(pinit, fi, R, active, dr0, rnow, iters, status, remaining, 0, true, 0.0,
-                             st, dtol), "server convergence");
-        enqueue_vcycle(list, P.mg64, lv64, active, jobs, S->mg, S->mg.smoother_w, st);
-        for (int k = 0; k < S->mg.inner_cycles && P.mg32.levels; ++k) {
-            if (P.mg32.fused)
-                enqueue_vcycle32_fused(list, P.mg32, lv32, active, jobs, tiles, S->mg, S->mg.smoother_w,
-                                       k == 0, st, k == S->mg.inner_cycles - 1 ? lv64 : nullptr);
-            else
-                enqueue_vcycle(list, P.mg32, lv32, active, jobs, S->mg, S->mg.smoother_w, st);
-        }
-        // fused: the level-0 ascents did psi += e except where a tail holds level 0
-        ck(launch_b_update(list(P.mg32.fused ? P.mg32.upd0 : P.update), lv64, active, lv32, st),
-           "server update");
-        for (int k = 0; k < S->sor_sweeps && P.sor.second; ++k)
-            for (int colour = 0; colour < 2; ++colour)
-                ck(launch_b_rb(list(P.sor), lv64, active, colour, false, 1.0, st, true), "server sweep");
-        ck(launch_b_sumsq(list(P.norm), lv64, active, pnorm, lv32, st, dr0), "server residual");
-        ck(launch_b_converge(pnorm, fn, R, active, dr0, rnow, iters, status, remaining, 1, true, 0.0,
-                             st, dtol), "server convergence");
-        auto down = [&](void* dst, const void* src, size_t bytes) {
-            ck(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, st), "download state");
-        };
-        std::vector<double> rn(R);
-        down(stat.data(), status, R * sizeof(int));
-        down(it.data(), iters, R * sizeof(long long));
-        down(r0.data(), dr0, R * sizeof(double));
-        down(rn.data(), rnow, R * sizeof(double));
-        ck(cudaStreamSynchronize(st), "stream sync");
-        // ---- retire finished requests ----
-        int still = 0;
-        for (int q = 0; q < R; ++q) {
-            SrvRequest& r = *run[q];
-            r.fresh = false;
-            r.steps = it[q];
-            r.r0 = r0[q];
-            r.rnow = rn[q];
-            const int64_t done = r.method == LAP_SOR_RB ? r.steps * S->sor_sweeps : r.steps;
-            const bool capped = stat[q] == 1 && done >= r.max_iter;
-            if (stat[q] == 1 && !capped) {
-                ++still;
-                continue;
-            }
-            r.res.status = stat[q] == 1 ? LAP_MAXITER : stat[q];
-            r.res.iters = done;
-            r.res.r0 = r.r0;
-            r.res.r_final = r.rnow;
-            r.res.last_check = r.r0 > 0 ? r.rnow / r.r0 : 0.0;
-            r.state = 2;
-            if (r.bytes) pool_free(S, r.off, r.bytes);
-        }
-        if (running) *running = still;
-    });
-}
 
 // ============================== C ABI =======================================================
 

@@ -1,0 +1,390 @@
+// lap_batched.cu -- lap_solve_batched: the V-cycle over many independent grids of different
+// sizes, every phase one launch over all problems (work lists built here, kernels in
+// batch_kernels.cu and fused32_kernels.cu).
+#include "lap_host.cuh"
+
+namespace lap {
+
+void add_items(std::vector<BatchItem>& items, int level_index, int m, int n)
+{
+    const int per = std::max(1, BATCH_ITEM_POINTS / std::max(1, m - 2));
+    for (int r = 1; r <= n - 2; r += per) items.push_back(BatchItem{level_index, r, std::min(per, n - 1 - r)});
+}
+
+// First level of a problem that the small-level tail runs (both sides <= tail_size), or
+// nlev when it has none.
+int tail_start(const BatchLevel<double>* lv, int nlev, int tail_size)
+{
+    if (tail_size <= 0) return nlev;
+    for (int l = 0; l < nlev; ++l)
+        if (lv[l].m <= tail_size && lv[l].n <= tail_size) return l;
+    return nlev;
+}
+
+// Lists of one V-cycle over problems `who`: problem q owns levels base[q] .. base[q] +
+// nlev[q] - 1 of lv. Levels above a problem's tail go through item lists, the tail is one job.
+// With tiles, the fine levels also get the tile items of the fused FP32 descent/ascent.
+void build_lists(LevelLists& L, std::vector<BatchItem>& items, std::vector<TailJob>& jobs,
+                 const std::vector<int>& who, const std::vector<int>& base,
+                 const std::vector<int>& nlev, const std::vector<BatchLevel<double>>& lv,
+                 int tail_size, std::vector<TileItem>* tiles, int nu1, int nu2)
+{
+    L.fused = tiles != nullptr;
+    L.tiles.assign(0, {0, 0});
+    L.levels = 0;
+    for (int q : who) L.levels = std::max(L.levels, nlev[q]);
+    L.fine.assign(L.levels, {0, 0});
+    L.all.assign(L.levels, {0, 0});
+    L.coarse.assign(L.levels, {0, 0});
+    L.tail.assign(L.levels, {0, 0});
+    L.tiles.assign(L.levels, {0, 0});
+    std::vector<int> t(who.size());
+    for (size_t k = 0; k < who.size(); ++k) t[k] = tail_start(&lv[base[who[k]]], nlev[who[k]], tail_size);
+    for (int l = 0; l < L.levels; ++l) {
+        const int f0 = (int)items.size();
+        for (size_t k = 0; k < who.size(); ++k) {
+            const int q = who[k];
+            if (nlev[q] - 1 > l && l < t[k]) add_items(items, base[q] + l, lv[base[q] + l].m, lv[base[q] + l].n);
+        }
+        L.fine[l] = {f0, (int)items.size() - f0};
+        if (tiles) {
+            const int t0 = (int)tiles->size();
+            for (size_t k = 0; k < who.size(); ++k) {
+                const int q = who[k];
+                if (!(nlev[q] - 1 > l && l < t[k])) continue;
+                const BatchLevel<double>& d = lv[base[q] + l];
+                int tx, ty, ntx, nty;
+                fused32_tile(d.m, d.n, nu1, nu2, &tx, &ty, &ntx, &nty);
+                for (int by = 0; by < nty; ++by)
+                    for (int bx = 0; bx < ntx; ++bx)
+                        tiles->push_back(TileItem{base[q] + l, 1 + bx * tx, 1 + by * ty, tx, ty});
+            }
+            L.tiles[l] = {t0, (int)tiles->size() - t0};
+        }
+        const int a0 = (int)items.size();
+        for (size_t k = 0; k < who.size(); ++k) {
+            const int q = who[k];
+            if (nlev[q] > l && l <= t[k]) add_items(items, base[q] + l, lv[base[q] + l].m, lv[base[q] + l].n);
+        }
+        L.all[l] = {a0, (int)items.size() - a0};
+        const int c0 = (int)items.size();
+        for (size_t k = 0; k < who.size(); ++k) {
+            const int q = who[k];
+            if (nlev[q] - 1 == l && t[k] == nlev[q]) {
+                const BatchLevel<double>& d = lv[base[q] + l];
+                items.push_back(BatchItem{base[q] + l, 1, d.n - 2});
+                L.max_coarse = std::max(L.max_coarse, (d.m - 2) * (d.n - 2));
+            }
+        }
+        L.coarse[l] = {c0, (int)items.size() - c0};
+        const int j0 = (int)jobs.size();
+        for (size_t k = 0; k < who.size(); ++k) {
+            const int q = who[k];
+            if (t[k] == l && l < nlev[q]) {
+                jobs.push_back(TailJob{base[q] + l, base[q] + nlev[q] - 1});
+                const BatchLevel<double>& d = lv[base[q] + nlev[q] - 1];
+                L.max_coarse = std::max(L.max_coarse, (d.m - 2) * (d.n - 2));
+            }
+        }
+        L.tail[l] = {j0, (int)jobs.size() - j0};
+    }
+    if (tiles) {
+        const int u0 = (int)items.size();
+        for (size_t k = 0; k < who.size(); ++k) {
+            const int q = who[k];
+            if (t[k] == 0 || nlev[q] == 1) add_items(items, base[q], lv[base[q]].m, lv[base[q]].n);
+        }
+        L.upd0 = {u0, (int)items.size() - u0};
+    }
+}
+
+}  // namespace lap
+
+using namespace lap;
+
+namespace {
+
+struct BatchPlan {
+    std::vector<BatchLevel<double>> lv64;
+    std::vector<BatchLevel<float>> lv32;
+    std::vector<int> nlev, base;       // levels and first level index per problem
+    std::vector<BatchItem> items;      // all work lists, back to back
+    std::vector<TailJob> jobs;         // tail jobs of every candidate, back to back
+    std::vector<TileItem> tiles;       // FP32 tile items of every candidate (fused cycle)
+    std::vector<LevelLists> cands;     // the V-cycle's lists for each tail-size candidate
+    std::pair<int, int> norm;          // level-0 items of every problem, problem by problem
+    std::vector<int> first_item;       // per problem: its first item in the norm list (+ end)
+    int max_coarse_unknowns = 0;
+    int levels = 0;
+};
+
+}  // namespace
+
+extern "C" int lap_solve_batched(lap_handle h, int count, const lap_grid* grids,
+                                 double* const* psi_devs, const lap_params* p, lap_result* results,
+                                 void* stream)
+{
+    return guarded([&] {
+        if (!h) fail(LAP_EINVAL, "handle is NULL");
+        if (count < 1 || !grids || !psi_devs || !results) fail(LAP_EINVAL, "empty or NULL batch");
+        check_params(p);
+        if (p->method != LAP_MG && p->method != LAP_MG_MIXED)
+            fail(LAP_EINVAL, "batched solves take LAP_MG or LAP_MG_MIXED");
+        if (p->norm == LAP_NORM_MAXDELTA) fail(LAP_EINVAL, "batched solves stop on an L2 norm");
+        set_device(h);
+        const bool mixed = p->method == LAP_MG_MIXED;
+        cudaStream_t s = (cudaStream_t)stream;
+        BatchPlan P;
+        P.nlev.resize(count);
+        P.base.resize(count);
+        // ---- level descriptors (buffers are carved below) ----
+        for (int q = 0; q < count; ++q) {
+            const lap_grid* g = &grids[q];
+            check_grid(g);
+            check_device_ptr(h, psi_devs[q], "psi");
+            const int L = mg_level_count(g->m, g->n, p->coarsest_min, p->max_levels);
+            P.nlev[q] = L;
+            P.base[q] = (int)P.lv64.size();
+            P.levels = std::max(P.levels, L);
+            const Coef c = make_coef(g->dx, g->dy);
+            int m = g->m, n = g->n;
+            for (int l = 0; l < L; ++l) {
+                BatchLevel<double> d{};
+                d.m = m;
+                d.n = n;
+                d.pitch = l == 0 ? g->pitch : round_up(m, 32);
+                d.problem = q;
+                d.unit_beta = c.unit_beta;
+                d.inv_d_shift = c.inv_d_shift;
+                d.b2 = c.b2;
+                d.d = c.d;
+                d.inv_d = c.inv_d;
+                BatchLevel<float> f{};
+                f.m = m;
+                f.n = n;
+                f.pitch = round_up(m, 32);
+                f.problem = q;
+                f.unit_beta = c.unit_beta;
+                f.inv_d_shift = 0;
+                f.b2 = c.b2;
+                f.d = c.d;
+                f.inv_d = c.inv_d;
+                if (l == L - 1) {
+                    if ((int64_t)(m - 2) * (n - 2) > COARSE_MAX_UNKNOWNS)
+                        fail(LAP_EUNSUPPORTED, "coarsest level with more than 1024 unknowns");
+                    d.ainv_t = f.ainv_t = coarse_inverse(h, m, n, c.b2, c.d);
+                    P.max_coarse_unknowns = std::max(P.max_coarse_unknowns, (m - 2) * (n - 2));
+                }
+                P.lv64.push_back(d);
+                P.lv32.push_back(f);
+                m = (m - 1) / 2 + 1;
+                n = (n - 1) / 2 + 1;
+            }
+        }
+        // ---- work lists: one set per tail-size candidate ----
+        std::vector<int> all_problems(count), shape;
+        for (int q = 0; q < count; ++q) {
+            all_problems[q] = q;
+            shape.push_back(grids[q].m);
+            shape.push_back(grids[q].n);
+        }
+        TailTuner& tuner = h->tail_tuners[tuner_key('B', p, shape)];
+        if (tuner.cand.empty()) tuner.init(tail_candidates(true, mixed, p->tail_size));
+        const bool fused = mixed && !p->unfused && fused32_supported(p->nu1, p->nu2);
+        if (fused) ck(prepare_fused32(), "tile kernel attributes");
+        for (int cand : tuner.cand) {
+            LevelLists L;
+            build_lists(L, P.items, P.jobs, all_problems, P.base, P.nlev, P.lv64, cand,
+                        fused ? &P.tiles : nullptr, p->nu1, p->nu2);
+            P.max_coarse_unknowns = std::max(P.max_coarse_unknowns, L.max_coarse);
+            P.cands.push_back(L);
+        }
+        const int n0 = (int)P.items.size();
+        for (int q = 0; q < count; ++q) {
+            P.first_item.push_back((int)P.items.size() - n0);
+            add_items(P.items, P.base[q], grids[q].m, grids[q].n);
+        }
+        P.first_item.push_back((int)P.items.size() - n0);
+        P.norm = {n0, (int)P.items.size() - n0};
+        // ---- memory: level buffers, descriptors, lists, state ----
+        auto carve_all = [&](auto& cv) {
+            for (int q = 0; q < count; ++q)
+                for (int l = 0; l < P.nlev[q]; ++l) {
+                    const int k = P.base[q] + l;
+                    BatchLevel<double>& d = P.lv64[k];
+                    BatchLevel<float>& f = P.lv32[k];
+                    const bool last = l == P.nlev[q] - 1;
+                    if (!mixed) {
+                        if (l == 0) {
+                            d.u = psi_devs[q];
+                            d.q = nullptr;
+                        } else {
+                            d.u = cv.template take<double>((size_t)d.n * d.pitch);
+                            d.q = cv.template take<double>((size_t)d.n * d.pitch);
+                        }
+                        d.r = last ? nullptr : cv.template take<double>((size_t)d.n * d.pitch);
+                    } else {
+                        if (l == 0) d.u = psi_devs[q];
+                        f.u = cv.template take<float>((size_t)f.n * f.pitch);
+                        f.q = cv.template take<float>((size_t)f.n * f.pitch);
+                        f.r = last ? nullptr : cv.template take<float>((size_t)f.n * f.pitch);
+                    }
+                }
+            auto* lv64 = cv.template take<BatchLevel<double>>(P.lv64.size());
+            auto* lv32 = cv.template take<BatchLevel<float>>(P.lv32.size());
+            auto* items = cv.template take<BatchItem>(P.items.size());
+            auto* jobs = cv.template take<TailJob>(std::max<size_t>(1, P.jobs.size()));
+            auto* tiles = cv.template take<TileItem>(std::max<size_t>(1, P.tiles.size()));
+            auto* first = cv.template take<int>(P.first_item.size());
+            auto* active = cv.template take<int>(count);
+            auto* status = cv.template take<int>(count);
+            auto* remaining = cv.template take<int>(1);
+            auto* iters = cv.template take<long long>(count);
+            auto* r0 = cv.template take<double>(count);
+            auto* rnow = cv.template take<double>(count);
+            auto* partials = cv.template take<double>(std::max(1, P.norm.second));
+            return std::make_tuple(lv64, lv32, items, jobs, tiles, first, active, status, remaining,
+                                   iters, r0, rnow, partials);
+        };
+        Sizer sz;
+        carve_all(sz);
+        Carver cv(arena(h, sz.off));
+        auto [lv64, lv32, items, jobs, tiles, first, active, status, remaining, iters, r0, rnow,
+              partials] = carve_all(cv);
+        // zero every level buffer (rings of corrections stay zero), then upload tables
+        const size_t level_bytes = (size_t)((char*)lv64 - (char*)h->arena);
+        if (level_bytes) ck(cudaMemsetAsync(h->arena, 0, level_bytes, s), "zero levels");
+        std::vector<int> ones(count, 1);
+        const int cnt = count;
+        ck(cudaMemcpyAsync(lv64, P.lv64.data(), P.lv64.size() * sizeof(P.lv64[0]), cudaMemcpyHostToDevice, s), "upload levels");
+        ck(cudaMemcpyAsync(lv32, P.lv32.data(), P.lv32.size() * sizeof(P.lv32[0]), cudaMemcpyHostToDevice, s), "upload levels");
+        ck(cudaMemcpyAsync(items, P.items.data(), P.items.size() * sizeof(BatchItem), cudaMemcpyHostToDevice, s), "upload items");
+        if (!P.jobs.empty())
+            ck(cudaMemcpyAsync(jobs, P.jobs.data(), P.jobs.size() * sizeof(TailJob), cudaMemcpyHostToDevice, s), "upload jobs");
+        if (!P.tiles.empty())
+            ck(cudaMemcpyAsync(tiles, P.tiles.data(), P.tiles.size() * sizeof(TileItem), cudaMemcpyHostToDevice, s), "upload tiles");
+        ck(cudaMemcpyAsync(first, P.first_item.data(), P.first_item.size() * sizeof(int), cudaMemcpyHostToDevice, s), "upload items");
+        ck(cudaMemcpyAsync(active, ones.data(), count * sizeof(int), cudaMemcpyHostToDevice, s), "upload flags");
+        ck(cudaMemcpyAsync(status, ones.data(), count * sizeof(int), cudaMemcpyHostToDevice, s), "upload flags");
+        ck(cudaMemcpyAsync(remaining, &cnt, sizeof(int), cudaMemcpyHostToDevice, s), "upload count");
+        ck(cudaMemsetAsync(iters, 0, count * sizeof(long long), s), "zero iterations");
+        ck(cudaStreamSynchronize(s), "stream sync");  // host vectors above go out of scope
+        auto list = [&](std::pair<int, int> r) { return BatchList{items + r.first, r.second}; };
+        const BatchList norm_list = list(P.norm);
+        const bool rel = p->norm == LAP_NORM_L2_REL;
+        // ---- one cycle (V-cycle(s) and stopping test) with tail-size candidate c ----
+        auto cycle = [&](int c, cudaStream_t st) {
+            const LevelLists& L = P.cands[c];
+            if (mixed) {
+                for (int k = 0; k < p->inner_cycles; ++k) {
+                    if (L.fused)
+                        enqueue_vcycle32_fused(list, L, lv32, active, jobs, tiles, *p, p->smoother_w,
+                                               k == 0, st, k == p->inner_cycles - 1 ? lv64 : nullptr);
+                    else
+                        enqueue_vcycle(list, L, lv32, active, jobs, *p, p->smoother_w, st);
+                }
+                // fused: the level-0 ascents did psi += e except where a tail holds level 0
+                ck(launch_b_update(L.fused ? list(L.upd0) : norm_list, lv64, active, lv32, st),
+                   "batched update");
+                ck(launch_b_sumsq(norm_list, lv64, active, partials, lv32, st, r0), "batched residual");
+            } else {
+                enqueue_vcycle(list, L, lv64, active, jobs, *p, p->smoother_w, st);
+                ck(launch_b_sumsq(norm_list, lv64, active, partials, nullptr, st), "batched residual");
+            }
+            ck(launch_b_converge(partials, first, count, active, r0, rnow, iters, status, remaining,
+                                 1, rel, p->tol, st), "batched convergence");
+        };
+        // initial residuals (and, for the mixed solver, the first FP32 right-hand sides)
+        ck(launch_b_sumsq(norm_list, lv64, active, partials, mixed ? lv32 : nullptr, s), "batched residual");
+        ck(launch_b_converge(partials, first, count, active, r0, rnow, iters, status, remaining, 0,
+                             rel, p->tol, s), "batched convergence");
+        // one cycle per candidate as a graph, captured on the handle's stream when first
+        // used and replayed on the caller's
+        std::vector<std::pair<cudaGraphExec_t, int64_t>> exec(P.cands.size(), {nullptr, 0});
+        auto release = [&] {
+            for (auto& e : exec)
+                if (e.first) cudaGraphExecDestroy(e.first);
+        };
+        auto launch_cycle = [&](int c) {
+            if (!h->use_graphs) {
+                cycle(c, s);
+                return;
+            }
+            if (!exec[c].first) {
+                if (!h->capture)
+                    ck(cudaStreamCreateWithFlags(&h->capture, cudaStreamNonBlocking), "capture stream");
+                const int64_t before = launches_now();
+                ck(cudaStreamBeginCapture(h->capture, cudaStreamCaptureModeThreadLocal), "begin capture");
+                cudaGraph_t g = nullptr;
+                try {
+                    cycle(c, h->capture);
+                } catch (...) {
+                    cudaStreamEndCapture(h->capture, &g);
+                    if (g) cudaGraphDestroy(g);
+                    cudaGetLastError();
+                    throw;
+                }
+                ck(cudaStreamEndCapture(h->capture, &g), "end capture");
+                exec[c].second = launches_now() - before;
+                add_launches(-exec[c].second);
+                const cudaError_t e = cudaGraphInstantiate(&exec[c].first, g, 0);
+                cudaGraphDestroy(g);
+                ck(e, "instantiate graph");
+            }
+            ck(cudaGraphLaunch(exec[c].first, s), "launch graph");
+            add_launches(exec[c].second);
+        };
+        int64_t done = 0;
+        int left = count;
+        try {
+            while (done < p->max_iter) {
+                ck(cudaMemcpyAsync(h->pinned, remaining, sizeof(int), cudaMemcpyDeviceToHost, s), "copy count");
+                ck(cudaStreamSynchronize(s), "stream sync");
+                std::memcpy(&left, h->pinned, sizeof(int));
+                if (left == 0) break;
+                const int64_t steps = std::min<int64_t>(p->check_every, p->max_iter - done);
+                for (int64_t k = 0; k < steps; ++k) {
+                    const int c = tuner.next();
+                    if (tuner.done) {
+                        launch_cycle(c);
+                        continue;
+                    }
+                    // not tuned yet: time this cycle (the graph of c is captured before e0)
+                    if (h->use_graphs && !exec[c].first) {
+                        launch_cycle(c);  // first use captures and runs it once
+                        ck(cudaStreamSynchronize(s), "stream sync");
+                        continue;
+                    }
+                    ck(cudaEventRecord(tuner_event(h, 0), s), "record event");
+                    launch_cycle(c);
+                    ck(cudaEventRecord(tuner_event(h, 1), s), "record event");
+                    ck(cudaEventSynchronize(tuner_event(h, 1)), "event sync");
+                    float ms = 0.f;
+                    ck(cudaEventElapsedTime(&ms, tuner_event(h, 0), tuner_event(h, 1)), "event time");
+                    tuner.record(c, ms);
+                }
+                done += steps;
+            }
+        } catch (...) {
+            release();
+            throw;
+        }
+        release();
+        // ---- results ----
+        std::vector<long long> it(count);
+        std::vector<int> st(count);
+        std::vector<double> a(count), z(count);
+        ck(cudaMemcpyAsync(it.data(), iters, count * sizeof(long long), cudaMemcpyDeviceToHost, s), "copy results");
+        ck(cudaMemcpyAsync(st.data(), status, count * sizeof(int), cudaMemcpyDeviceToHost, s), "copy results");
+        ck(cudaMemcpyAsync(a.data(), r0, count * sizeof(double), cudaMemcpyDeviceToHost, s), "copy results");
+        ck(cudaMemcpyAsync(z.data(), rnow, count * sizeof(double), cudaMemcpyDeviceToHost, s), "copy results");
+        ck(cudaStreamSynchronize(s), "stream sync");
+        for (int q = 0; q < count; ++q) {
+            results[q].status = st[q];
+            results[q].iters = it[q];
+            results[q].r0 = a[q];
+            results[q].r_final = z[q];
+            results[q].last_check = rel ? (a[q] > 0 ? z[q] / a[q] : 0.0) : z[q];
+        }
+    });
+}
