@@ -447,3 +447,28 @@ def test_lexicographic_refuses_grids_beyond_one_sm(lap, b):
     with pytest.raises(b.LapError) as e:
         lap.solve(b.field(257, 257), method="gs_lex", max_iter=1)
     assert e.value.code == -4
+
+
+# ---- the whole solve in one CTA (small grids, the stopping rule of Eq. 16) -------------
+
+@pytest.mark.parametrize("method,w", [("jacobi", 1.0), ("gs", 1.0), ("sor", 1.6), ("gs_lex", 1.0),
+                                      ("sor_lex", 1.6)])
+@pytest.mark.parametrize("every,max_iter,tol", [(1, 400, 1e-7), (3, 10, 0.0), (4, 23, 0.0),
+                                                (7, 1000, 1e-8), (5, 5, 0.0)])
+@pytest.mark.parametrize("shape,beta", [((25, 17), 1.0), ((33, 65), 0.8), ((3, 3), 1.0)])
+def test_one_cta_solve_matches_oracle(lap, b, method, w, every, max_iter, tol, shape, beta):
+    """Point methods on grids of at most 4096 points with max|psi^{k+1} - psi^k| <= tol run
+    the whole solve (periods and tests) in one kernel: the same iterates, stopping
+    iteration and test value as the oracle, for any period length and iteration cap."""
+    m, n = shape
+    psi = rand_field(m, n, 23 + m)
+    t = b.to_field(psi)
+    g = lap.solve(t, beta, 1.0, method=method, w=w, norm="maxdelta", tol=tol, check_every=every,
+                  max_iter=max_iter)
+    want, o = ora.solve(psi, dx=beta, dy=1.0, tol=tol, norm=ora.NORM_MAXDELTA, max_iter=max_iter,
+                        check_every=every, history=True, **ora_kw(method, w=w))
+    assert g["status"] == o["status"]
+    assert g["iters"] == o["iters"]
+    assert np.array_equal(host(t), want)
+    if g["iters"]:
+        assert g["last_check"] == o["hist"][-1]
