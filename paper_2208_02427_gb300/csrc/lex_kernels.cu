@@ -15,55 +15,9 @@ namespace {
 
 constexpr int LEX_THREADS = 512;
 
-template <bool UNIT_BETA, bool POW2, bool GS>
-__global__ void __launch_bounds__(LEX_THREADS)
-    lex_sweeps_kernel(double* __restrict__ psi, int m, int n, int64_t pitch, int nsweeps,
-                      double b2, double inv_d, int shift, double w, double one_minus_w,
-                      unsigned long long* __restrict__ maxd)
-{
-    const FmaOps o = load_fma_ops();
-    extern __shared__ double u[];  // dense m x n copy
-    const int tid = threadIdx.x;
-    for (int k = tid; k < m * n; k += blockDim.x) u[k] = psi[(int64_t)(k / m) * pitch + k % m];
-    __syncthreads();
-    unsigned long long dl = 0;
-    const int last_diag = (m - 2) + (n - 2);
-    for (int sweep = 0; sweep < nsweeps; ++sweep) {
-        const bool track = maxd && sweep == nsweeps - 1;
-        for (int k = 2; k <= last_diag; ++k) {
-            const int i_lo = k - (n - 2) > 1 ? k - (n - 2) : 1;
-            const int i_hi = k - 1 < m - 2 ? k - 1 : m - 2;
-            for (int i = i_lo + tid; i <= i_hi; i += blockDim.x) {
-                const int j = k - i;
-                double* c = u + j * m + i;
-                const double s = neighbour_sum<UNIT_BETA>(o, c[-1], c[1], c[-m], c[m], b2);
-                const double g = times_inv_d<POW2>(o, s, inv_d, shift);
-                const double old = *c;
-                const double nv = GS ? g : __fma_rn(w, g, fmul(o, one_minus_w, old));
-                *c = nv;
-                if (track) {
-                    const unsigned long long b = abs_bits(fadd(o, nv, -old));
-                    dl = b > dl ? b : dl;
-                }
-            }
-            __syncthreads();
-        }
-    }
-    const int mi = m - 2;  // write back the interior only: the ring is never written
-    for (int k = tid; k < mi * (n - 2); k += blockDim.x) {
-        const int i = 1 + k % mi, j = 1 + k / mi;
-        psi[(int64_t)j * pitch + i] = u[j * m + i];
-    }
-    if (maxd) {
-        dl = warp_max_u64(dl);
-        if ((tid & 31) == 0 && dl) atomicMax(maxd, dl);
-    }
-}
-
-// ---- a whole solve in one CTA (small grids, the paper's stopping rule, Eq. 16) ----
 // The point methods' sweeps on a shared-memory copy, each returning the thread's largest
 // |new - old| (as ordered bits) when `track`: the same per-point expressions as the
-// multi-CTA kernels and the wavefront kernel above.
+// multi-CTA kernels (Eqs. 5-7), in lexicographic wavefronts, red-black colours or Jacobi.
 template <bool UNIT_BETA, bool POW2, bool GS>
 __device__ __forceinline__ unsigned long long sweep_lex(const FmaOps& o, double* u, int m, int n,
                                                         double b2, double inv_d, int shift, double w,
@@ -141,6 +95,35 @@ __device__ __forceinline__ unsigned long long sweep_jacobi(const FmaOps& o, cons
     return dl;
 }
 
+// nsweeps lexicographic sweeps (one check period) in one CTA; maxd gets the last sweep's
+// max |new - old|.
+template <bool UNIT_BETA, bool POW2, bool GS>
+__global__ void __launch_bounds__(LEX_THREADS)
+    lex_sweeps_kernel(double* __restrict__ psi, int m, int n, int64_t pitch, int nsweeps,
+                      double b2, double inv_d, int shift, double w, double one_minus_w,
+                      unsigned long long* __restrict__ maxd)
+{
+    const FmaOps o = load_fma_ops();
+    extern __shared__ double u[];  // dense m x n copy
+    const int tid = threadIdx.x;
+    for (int k = tid; k < m * n; k += blockDim.x) u[k] = psi[(int64_t)(k / m) * pitch + k % m];
+    __syncthreads();
+    unsigned long long dl = 0;
+    for (int sweep = 0; sweep < nsweeps; ++sweep)
+        dl = sweep_lex<UNIT_BETA, POW2, GS>(o, u, m, n, b2, inv_d, shift, w, one_minus_w,
+                                            maxd && sweep == nsweeps - 1);
+    const int mi = m - 2;  // write back the interior only: the ring is never written
+    for (int k = tid; k < mi * (n - 2); k += blockDim.x) {
+        const int i = 1 + k % mi, j = 1 + k / mi;
+        psi[(int64_t)j * pitch + i] = u[j * m + i];
+    }
+    if (maxd) {
+        dl = warp_max_u64(dl);
+        if ((tid & 31) == 0 && dl) atomicMax(maxd, dl);
+    }
+}
+
+// ---- a whole solve in one CTA (small grids, the paper's stopping rule, Eq. 16) ----
 // KIND 0 Jacobi, 1 red-black, 2 lexicographic. Runs check periods (check_every iterations, the
 // last shortened to max_iter) until max |psi^{k+1} - psi^k| over the period's last iteration
 // is <= tol (or not finite): the host loop's rule, on a block-wide max of the same bits.
