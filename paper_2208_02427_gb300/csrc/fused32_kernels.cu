@@ -518,11 +518,13 @@ void fused32_tile(int m, int n, int nu1, int nu2, int* tx, int* ty, int* ntx, in
     *ty = (H + *nty - 1) / *nty;
 }
 
-static bool g_fused32_ready = false;
+// Nonzero once the tile kernels' shared-memory limit is raised on that device.
+static std::atomic<size_t> g_fused32_ready[ATTR_DEVICES];
 
 cudaError_t prepare_fused32()
 {
-    if (g_fused32_ready) return cudaSuccess;
+    const int dev = attr_slot();
+    if (dev >= 0 && g_fused32_ready[dev].load() != 0) return cudaSuccess;
     const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
     cudaError_t e = cudaFuncSetAttribute(down32_kernel<512>, a, (int)FT_SMEM);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(up32_kernel<512>, a, (int)FT_SMEM);
@@ -530,7 +532,7 @@ cudaError_t prepare_fused32()
     if (e == cudaSuccess) e = cudaFuncSetAttribute(up32_kernel<1024>, a, (int)FT_SMEM);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(b_down32_kernel, a, (int)FT_SMEM);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(b_up32_kernel, a, (int)FT_SMEM);
-    if (e == cudaSuccess) g_fused32_ready = true;
+    if (e == cudaSuccess) attr_record(g_fused32_ready, dev, 1);
     return e;
 }
 

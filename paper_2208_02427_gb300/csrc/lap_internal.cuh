@@ -3,9 +3,28 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <atomic>
 #include <cstdint>
 
 namespace lap {
+
+// cudaFuncSetAttribute acts on the current device only, so what a prepare_* function has
+// already raised is recorded per device ordinal. Ordinals past the table are never recorded
+// (their attributes are set again on every call, which is harmless).
+constexpr int ATTR_DEVICES = 64;
+inline int attr_slot()
+{
+    int d = -1;
+    if (cudaGetDevice(&d) != cudaSuccess || d < 0 || d >= ATTR_DEVICES) return -1;
+    return d;
+}
+// Raise the recorded value of slot d to at least v.
+inline void attr_record(std::atomic<size_t>* table, int d, size_t v)
+{
+    if (d < 0) return;
+    size_t cur = table[d].load();
+    while (cur < v && !table[d].compare_exchange_weak(cur, v)) {}
+}
 
 // Coefficients of the 5-point equation (E+W) + b2 (N+S) - d psi (+ q) = 0, Eq. 5.
 struct Coef {

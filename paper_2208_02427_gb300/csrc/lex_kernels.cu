@@ -201,13 +201,15 @@ __global__ void __launch_bounds__(LEX_THREADS)
 size_t lex_smem_bytes(int m, int n) { return sizeof(double) * (size_t)m * (size_t)n; }
 int64_t lex_max_points() { return 224 * 1024 / sizeof(double); }
 
-// Raise the dynamic shared-memory limit of every instantiation once (outside any stream
-// capture); later launches with at most that much shared memory skip it.
-static size_t g_lex_smem_set = 48 * 1024;
+// Raise the dynamic shared-memory limit of every instantiation once per device (outside any
+// stream capture); later launches with at most that much shared memory skip it.
+static std::atomic<size_t> g_lex_smem_set[ATTR_DEVICES];
 
 cudaError_t prepare_lex_kernels(size_t smem)
 {
-    if (smem <= g_lex_smem_set) return cudaSuccess;
+    const int dev = attr_slot();
+    if (smem <= 48 * 1024 || (dev >= 0 && smem <= g_lex_smem_set[dev].load()))
+        return cudaSuccess;
     const int v = (int)smem;
     const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
     cudaError_t e = cudaSuccess;
@@ -230,7 +232,7 @@ cudaError_t prepare_lex_kernels(size_t smem)
     LAP_SOLVE_ATTR(2, true)
     LAP_SOLVE_ATTR(2, false)
 #undef LAP_SOLVE_ATTR
-    if (e == cudaSuccess) g_lex_smem_set = smem;
+    if (e == cudaSuccess) attr_record(g_lex_smem_set, dev, smem);
     return e;
 }
 

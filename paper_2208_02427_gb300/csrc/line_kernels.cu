@@ -139,12 +139,15 @@ int line_threads(const LineTables& t)
 }
 
 // Raise the dynamic shared-memory limit of every line-kernel instantiation to `smem`
-// (done outside stream capture; launches below only repeat it when a larger line comes).
-static size_t g_line_smem_set = 48 * 1024;
+// on the current device (done outside stream capture; launches below only repeat it when a
+// larger line comes).
+static std::atomic<size_t> g_line_smem_set[ATTR_DEVICES];
 
 cudaError_t prepare_line_kernels(size_t smem)
 {
-    if (smem <= g_line_smem_set) return cudaSuccess;
+    const int dev = attr_slot();
+    if (smem <= 48 * 1024 || (dev >= 0 && smem <= g_line_smem_set[dev].load()))
+        return cudaSuccess;
     cudaError_t e = cudaFuncSetAttribute(line_colour_kernel<0, true>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess)
@@ -153,7 +156,7 @@ cudaError_t prepare_line_kernels(size_t smem)
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(line_colour_kernel<1, false>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess) g_line_smem_set = smem;
+    if (e == cudaSuccess) attr_record(g_line_smem_set, dev, smem);
     return e;
 }
 
