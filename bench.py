@@ -66,12 +66,16 @@ def measured_peaks():
 
 def recorded_traffic(kernel: str):
     """DRAM bytes per launch from the committed ncu summary, if the kernel source is
-    unchanged since the capture (its sha256 is recorded beside the number)."""
+    unchanged since the capture (the sha256 of its source file and of the device helpers
+    it includes is recorded beside the number)."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "traffic.txt")
-    src = os.path.join(ROOT, "paper_2208_02427_gb300", "csrc", "point_kernels.cu")
+    csrc = os.path.join(ROOT, "paper_2208_02427_gb300", "csrc")
     try:
-        digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        h = hashlib.sha256()
+        for name in ("point_kernels.cu", "lap_device.cuh"):
+            h.update(open(os.path.join(csrc, name), "rb").read())
+        digest = h.hexdigest()[:16]
         for line in open(path):
             parts = line.split()
             if len(parts) >= 3 and parts[0] == kernel and parts[1] == digest:

@@ -194,8 +194,8 @@ class Laplace:
         self.close()
 
     def check_rounding(self, count: int, seed: int = 1) -> int:
-        """Mismatches of the kernels' integer-pipe FP64 -> FP32 rounding against the
-        conversion instruction over `count` seeded doubles (0 expected)."""
+        """Mismatches of the kernels' integer-pipe FP64 -> FP32 rounding and multiply by
+        2^-s against the instructions they replace, over `count` seeded doubles (0 expected)."""
         out = c_int64(0)
         _check(self._lib.lap_check_rounding(self._h, int(count), int(seed), C.byref(out)))
         return int(out.value)

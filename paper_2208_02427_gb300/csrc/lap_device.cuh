@@ -34,11 +34,21 @@ __device__ __forceinline__ double fmul(const FmaOps& o, double a, double b)
     return __fma_rn(a, b, o.nzero);
 }
 
+// The rare inputs of the integer-pipe paths below take these out-of-line functions. Written
+// inline, the compiler evaluates the fallback for every input and selects the result, which
+// spends the very FP64 operation the integer path saves (measured on GB300: the SOR colour
+// pass at 4097^2 ran 94 us with the fallback inline, 76 us with it out of line).
+static __device__ __noinline__ double fmul_rare(double x, double y, double nzero)
+{
+    return __fma_rn(x, y, nzero);
+}
+static __device__ __noinline__ float to_float_rare(double x) { return __double2float_rn(x); }
+
 // x * 2^-k for k > 0, bit-identical to __dmul_rn(x, 2^-k). On GB300 the FP64 pipe
 // issues about 2 operations per clock per SM, the integer pipe 64 times more; when x is
 // normal and the result stays normal the product is just the exponent field lowered by
-// k, which the integer pipe does. Zero, subnormal, tiny, infinite and NaN inputs take
-// the FP64 multiply.
+// k, and when x is +-0 it is x itself, both done on the integer pipe. Subnormal, tiny,
+// infinite and NaN inputs take the FP64 multiply.
 __device__ __forceinline__ double scale_down_pow2(const FmaOps& o, double x, int k,
                                                   double two_pow_minus_k)
 {
@@ -46,7 +56,8 @@ __device__ __forceinline__ double scale_down_pow2(const FmaOps& o, double x, int
     int lo = __double2loint(x);
     int e = (hi >> 20) & 0x7ff;
     if (e > k && e < 0x7ff) return __hiloint2double(hi - (k << 20), lo);
-    return fmul(o, x, two_pow_minus_k);
+    if (((hi & 0x7fffffff) | lo) == 0) return x;
+    return fmul_rare(x, two_pow_minus_k, o.nzero);
 }
 
 // Multiply by 1/d: the integer-pipe path when 1/d is an exact power of two.
@@ -70,14 +81,17 @@ __device__ __forceinline__ double neighbour_sum(const FmaOps& o, double w_, doub
 // x rounded to the nearest FP32 value (ties to even), bit-identical to __double2float_rn,
 // on the integer pipe when the result is a normal FP32 number or overflows: the 52-bit
 // fraction keeps its top 23 bits and rounds on the 29 below (a carry out of the fraction
-// raises the exponent, up to infinity). Zero, FP32-subnormal results, infinities and NaN
-// take the conversion instruction. On GB300 that instruction competes with the FP64
+// raises the exponent, up to infinity); +-0 maps to +-0. FP32-subnormal results, infinities
+// and NaN take the conversion instruction. On GB300 that instruction competes with the FP64
 // arithmetic of the residual kernels for the FP64 pipe.
 __device__ __forceinline__ float to_float_rn(double x)
 {
     const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
     const int e = (int)((b >> 52) & 0x7ff) - 1023 + 127;
-    if (e < 1 || e > 254) return __double2float_rn(x);
+    if (e < 1 || e > 254) {
+        if ((b << 1) == 0) return __uint_as_float((unsigned int)(b >> 32));
+        return to_float_rare(x);
+    }
     unsigned int out = ((unsigned int)e << 23) | ((unsigned int)(b >> 29) & 0x7fffffu);
     const unsigned int rem = (unsigned int)b & 0x1fffffffu;
     if (rem > 0x10000000u || (rem == 0x10000000u && (out & 1u))) ++out;

@@ -53,26 +53,36 @@ __device__ __forceinline__ unsigned long long mix64(unsigned long long x)
     return x ^ (x >> 31);
 }
 
-// to_float_rn against the conversion instruction on `count` doubles drawn from seed:
-// random bit patterns, exponents near the FP32 range's ends, exact ties and all-ones
-// fractions, in turn.
+// to_float_rn against the conversion instruction, and scale_down_pow2 against the FP64
+// multiply by 2^-s (s = 1..4), on `count` doubles drawn from seed: random bit patterns,
+// exponents near the FP32 range's ends, exact ties, all-ones fractions, +-0 and FP64
+// subnormals, and exponents within a few of zero, in turn.
 __global__ void check_rounding_kernel(long long count, unsigned long long seed,
                                       unsigned long long* bad)
 {
+    const FmaOps o = load_fma_ops();
     unsigned long long local = 0;
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < count;
          k += (long long)gridDim.x * blockDim.x) {
         const unsigned long long r = mix64(seed ^ (unsigned long long)k), r2 = mix64(r);
+        const unsigned long long sign_frac = r & 0x800fffffffffffffull;
         unsigned long long b;
-        switch (k & 3) {
+        switch (k % 6) {
         case 0: b = r; break;
-        case 1: b = (r & 0x800fffffffffffffull) | ((unsigned long long)(1023 - 130 + (r2 % 270)) << 52); break;
+        case 1: b = sign_frac | ((unsigned long long)(1023 - 130 + (r2 % 270)) << 52); break;
         case 2: b = (r & 0x800fffffe0000000ull) | 0x10000000ull | ((unsigned long long)(1023 + (int)(r2 % 60) - 30) << 52); break;
-        default: b = (r & 0xfff0000000000000ull) | 0x000fffffffffffffull; break;
+        case 3: b = (r & 0xfff0000000000000ull) | 0x000fffffffffffffull; break;
+        case 4: b = (r2 & 3) ? (r & 0x8000000000000000ull) : sign_frac; break;  // +-0, subnormal
+        default: b = sign_frac | ((r2 % 8) << 52); break;
         }
         const double x = __longlong_as_double((long long)b);
         const float want = __double2float_rn(x), got = to_float_rn(x);
         if (__float_as_uint(want) != __float_as_uint(got) && !(want != want && got != got)) ++local;
+        const int s = 1 + (int)((r2 >> 8) & 3);
+        const double p = __hiloint2double((1023 - s) << 20, 0);  // 2^-s
+        const double wd = __dmul_rn(x, p), gd = scale_down_pow2(o, x, s, p);
+        if (__double_as_longlong(wd) != __double_as_longlong(gd) && !(wd != wd && gd != gd))
+            ++local;
     }
     if (local) atomicAdd(bad, local);
 }

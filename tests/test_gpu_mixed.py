@@ -114,7 +114,8 @@ def test_mixed_graphs_equal_direct_launches(b):
 
 
 def test_integer_pipe_fp32_rounding_matches_the_instruction(lap):
-    """The residual kernels round FP64 to FP32 on the integer pipe; it must equal the
-    conversion instruction bit for bit (random bits, range edges, ties, all-ones)."""
+    """The residual kernels round FP64 to FP32, and the sweeps multiply by 1/d = 2^-s, on
+    the integer pipe; both must equal the instruction they replace bit for bit (random bits,
+    range edges, ties, all-ones fractions, +-0, subnormals, tiny exponents)."""
     assert lap.check_rounding(1 << 26, seed=20220804) == 0
     assert lap.check_rounding(1 << 24, seed=7) == 0
