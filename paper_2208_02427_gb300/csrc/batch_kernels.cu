@@ -37,6 +37,7 @@ template <> struct Arith<double> {
     }
     __device__ double half(double x) const { return scale_down_pow2(o, x, 1, 0.5); }
     __device__ double quarter(double x) const { return scale_down_pow2(o, x, 2, 0.25); }
+    __device__ double two() const { return in_reg(o, 2.0); }
 };
 template <> struct Arith<float> {
     __device__ float add(float a, float b) const { return __fadd_rn(a, b); }
@@ -53,6 +54,7 @@ template <> struct Arith<float> {
     }
     __device__ float half(float x) const { return __fmul_rn(0.5f, x); }
     __device__ float quarter(float x) const { return __fmul_rn(0.25f, x); }
+    __device__ float two() const { return 2.0f; }
 };
 
 template <class T>
@@ -120,9 +122,10 @@ __device__ __forceinline__ void restrict_point(const Arith<T>& A, const BatchLev
     const T* c = F.r + (int64_t)(2 * J) * pf + 2 * I;
     const T edges = A.add(A.add(c[-1], c[1]), A.add(c[-pf], c[pf]));
     const T corners = A.add(A.add(c[-pf - 1], c[-pf + 1]), A.add(c[pf - 1], c[pf + 1]));
-    const T t = A.fma((T)2, c[0], edges);
+    const T two = A.two();
+    const T t = A.fma(two, c[0], edges);
     const int64_t at = (int64_t)J * C.pitch + I;
-    C.q[at] = A.quarter(A.fma((T)2, t, corners));
+    C.q[at] = A.quarter(A.fma(two, t, corners));
     C.u[at] = (T)0;
 }
 
@@ -394,7 +397,7 @@ __global__ void __launch_bounds__(BT)
     for (Walk k(wdt); k.r < it.rows; k.next()) {
         const int j = it.row0 + k.r, i = 1 + k.c;
         double* c = L.u + (int64_t)j * L.pitch + i;
-        *c = fadd(o, *c, (double)E.u[(int64_t)j * E.pitch + i]);
+        *c = fadd(o, *c, to_double_exact(E.u[(int64_t)j * E.pitch + i]));
     }
 }
 

@@ -74,8 +74,6 @@ __device__ __forceinline__ void cp_async4(float* sdst, const float* gsrc)
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
-__device__ __forceinline__ float2 lds2(const float* p) { return *reinterpret_cast<const float2*>(p); }
-
 // Stores the components of v whose flags are set (8-byte store when both are).
 __device__ __forceinline__ void sts2_masked(float* p, float2 v, bool lo, bool hi)
 {
@@ -422,8 +420,8 @@ __device__ __forceinline__ void up_tile(const BatchLevel<float>& F, const BatchL
             const int p = p_lo + lane + 32 * s2;
             const int gx = R.gx0 + 2 * p;
             if (!lo[s2] && !hi[s2]) continue;
-            const double a = fadd(o, v[s2].x, (double)row[p]);
-            const double b = fadd(o, v[s2].y, (double)row[FT_HS + p]);
+            const double a = fadd(o, v[s2].x, to_double_exact(row[p]));
+            const double b = fadd(o, v[s2].y, to_double_exact(row[FT_HS + p]));
             if (lo[s2] && hi[s2] && even_pitch) {
                 *reinterpret_cast<double2*>(prow + gx) = make_double2(a, b);
             } else {

@@ -512,7 +512,7 @@ struct Solver {
     // norm_sc r when scaled).
     double partial_norm(const Field& u, bool scaled = false)
     {
-        ck(launch_sum_partials(w.partials, mixed_norm_blocks(u.n), w.nrm, s), "sum kernel");
+        ck(launch_sum_partials(w.partials, mixed_norm_blocks(u.m, u.n), w.nrm, s), "sum kernel");
         ck(cudaMemcpyAsync(h->pinned, w.nrm + 1, sizeof(double), cudaMemcpyDeviceToHost, s),
            "copy norm");
         ck(cudaStreamSynchronize(s), "stream sync");
@@ -921,9 +921,9 @@ struct Solver {
         } else if (p->method == LAP_MG_FP32) {
             ck(launch_defect32_sumsq(w.levels32[0].u, w.levels32[0].q, c, w.partials, s),
                "residual kernel");
-            ck(launch_sum_partials(w.partials, mixed_norm_blocks(f.n), w.nrm, s), "sum kernel");
+            ck(launch_sum_partials(w.partials, mixed_norm_blocks(f.m, f.n), w.nrm, s), "sum kernel");
         } else if (p->method == LAP_MG_MIXED) {
-            ck(launch_sum_partials(w.partials, mixed_norm_blocks(f.n), w.nrm, s), "sum kernel");
+            ck(launch_sum_partials(w.partials, mixed_norm_blocks(f.m, f.n), w.nrm, s), "sum kernel");
         } else {
             ck(launch_defect_sumsq(cur, nullptr, c, w.partials, s), "residual kernel");
             ck(launch_sum_partials(w.partials, norm_blocks(cur), w.nrm, s), "sum kernel");

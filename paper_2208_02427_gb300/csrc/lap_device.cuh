@@ -25,6 +25,16 @@ __device__ __forceinline__ FmaOps load_fma_ops()
     return FmaOps{g_fma_consts[0], g_fma_consts[1]};
 }
 
+// c copied into a register on the integer pipe. Kernel arguments are constant-bank operands,
+// and an FP64 fma with a constant-bank operand issues at the rate of an add; an XOR with an
+// integer zero that the compiler cannot see (from the loaded -0) gives a register operand
+// without spending an FP64 operation. Coefficients used on every point go through this.
+__device__ __forceinline__ double in_reg(const FmaOps& o, double c)
+{
+    const long long zero = __double_as_longlong(o.nzero) << 1;
+    return __longlong_as_double(__double_as_longlong(c) ^ zero);
+}
+
 __device__ __forceinline__ double fadd(const FmaOps& o, double a, double b)
 {
     return __fma_rn(a, o.one, b);
@@ -43,6 +53,23 @@ static __device__ __noinline__ double fmul_rare(double x, double y, double nzero
     return __fma_rn(x, y, nzero);
 }
 static __device__ __noinline__ float to_float_rare(double x) { return __double2float_rn(x); }
+static __device__ __noinline__ double to_double_rare(float x) { return (double)x; }
+
+// (double)f, exact, on the integer pipe when f is a normal FP32 number or +-0: the 8-bit
+// exponent is rebiased (127 -> 1023) and the 23-bit fraction becomes the top of the 52-bit
+// one. FP32 subnormals, infinities and NaN take the conversion instruction, which on GB300
+// issues on the FP64 pipe.
+__device__ __forceinline__ double to_double_exact(float f)
+{
+    const unsigned int u = __float_as_uint(f);
+    const unsigned int e = (u >> 23) & 0xffu;
+    if (e - 1u < 254u)
+        return __hiloint2double(
+            (int)((u & 0x80000000u) | ((e + (1023u - 127u)) << 20) | ((u >> 3) & 0xfffffu)),
+            (int)(u << 29));
+    if ((u << 1) == 0) return __hiloint2double((int)(u & 0x80000000u), 0);
+    return to_double_rare(f);
+}
 
 // x * 2^-k for k > 0, bit-identical to __dmul_rn(x, 2^-k). On GB300 the FP64 pipe
 // issues about 2 operations per clock per SM, the integer pipe 64 times more; when x is
@@ -98,6 +125,41 @@ __device__ __forceinline__ float to_float_rn(double x)
     out |= (unsigned int)(b >> 32) & 0x80000000u;
     return __uint_as_float(out);
 }
+
+// A grid-stride walk over the interior points of an m x n field in row-major order: thread
+// g = blockIdx.x * NT + threadIdx.x visits flattened points g, g + S, g + 2S, ... with
+// S = gridDim.x * NT, so every thread has the same number of points to one, and at any time
+// the blocks work on one contiguous window of S points (neighbour rows shared in L2). Handing
+// out whole rows instead leaves the blocks that got one row more as the tail. (i, j) are the
+// current point's coordinates (1-based interior); stepping needs no division.
+template <int NT>
+struct StrideWalk {
+    int i, j, mi, di, dj;
+    int64_t left;  // points still to visit, the current one included
+    __device__ __forceinline__ StrideWalk(int m, int n) : i(1), j(1), mi(m - 2), di(0), dj(0), left(0)
+    {
+        if (m < 3 || n < 3) return;
+        const int64_t total = (int64_t)(m - 2) * (int64_t)(n - 2);
+        const int64_t k = (int64_t)blockIdx.x * NT + threadIdx.x;
+        if (k >= total) return;
+        const int64_t step = (int64_t)gridDim.x * NT;
+        left = (total - 1 - k) / step + 1;
+        j = 1 + (int)(k / mi);
+        i = 1 + (int)(k % mi);
+        dj = (int)(step / mi);
+        di = (int)(step % mi);
+    }
+    __device__ __forceinline__ void next()
+    {
+        i += di;
+        j += dj;
+        if (i > mi) {
+            i -= mi;
+            ++j;
+        }
+        --left;
+    }
+};
 
 // Deterministic warp reductions (fixed xor tree).
 __device__ __forceinline__ double warp_sum(double v)

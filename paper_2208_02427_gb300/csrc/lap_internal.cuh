@@ -68,6 +68,14 @@ cudaError_t launch_jacobi(const Field& in, double* out, const Coef& c, unsigned 
 cudaError_t launch_defect(const Field& f, const double* q, double* r, const Coef& c,
                           cudaStream_t s);
 // sum of squares of the residual into per-block partials; partials[nblocks].
+// Blocks of the norm kernels (256 threads, a grid-stride walk over the interior): one per 256
+// interior points, at least 1 and at most 912 (6 per SM on 152 SMs, all resident at once).
+inline int norm_blocks_for(int m, int n)
+{
+    if (m < 3 || n < 3) return 1;
+    const int64_t b = ((int64_t)(m - 2) * (int64_t)(n - 2) + 255) / 256;
+    return b < 912 ? (int)b : 912;
+}
 int norm_blocks(const Field& f);
 cudaError_t launch_defect_sumsq(const Field& f, const double* q, const Coef& c, double* partials,
                                 cudaStream_t s);
@@ -107,7 +115,7 @@ cudaError_t launch_coarse_solve(const Field& u, const double* q, const Coef& c,
                                 const double* ainv_t, cudaStream_t s);
 
 // ---- FP32 cycle inside FP64 defect correction (mixed_kernels.cu) -----------------
-int mixed_norm_blocks(int n);
+int mixed_norm_blocks(int m, int n);
 cudaError_t launch_rb32(const Field32& f, const float* q, const Coef& c, bool gs, double w,
                         int colour, cudaStream_t s);
 cudaError_t launch_defect32(const Field32& f, const float* q, float* r, const Coef& c,

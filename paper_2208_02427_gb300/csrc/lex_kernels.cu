@@ -104,6 +104,10 @@ __global__ void __launch_bounds__(LEX_THREADS)
                       unsigned long long* __restrict__ maxd)
 {
     const FmaOps o = load_fma_ops();
+    b2 = in_reg(o, b2);
+    inv_d = in_reg(o, inv_d);
+    w = in_reg(o, w);
+    one_minus_w = in_reg(o, one_minus_w);
     extern __shared__ double u[];  // dense m x n copy
     const int tid = threadIdx.x;
     for (int k = tid; k < m * n; k += blockDim.x) u[k] = psi[(int64_t)(k / m) * pitch + k % m];
@@ -134,6 +138,8 @@ __global__ void __launch_bounds__(LEX_THREADS)
 {
     const FmaOps o = load_fma_ops();
     const double w = GS ? 1.0 : wslot[0], one_minus_w = GS ? 0.0 : wslot[1];
+    b2 = in_reg(o, b2);
+    inv_d = in_reg(o, inv_d);
     extern __shared__ double u[];
     double* a = u;
     double* b = KIND == 0 ? u + m * n : u;

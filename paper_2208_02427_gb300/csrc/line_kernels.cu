@@ -34,7 +34,11 @@ __global__ void __launch_bounds__(256)
     double* lane = sm;              // chunk p occupies lane[p*Ls .. p*Ls + L]; slot L = separator
     double* rho = sm + (size_t)P * Ls;  // 2*S: cyclic-reduction double buffer
     double* base = psi + (int64_t)(first_line + 2 * (int)blockIdx.x) * sx;
-    const double alpha = t.alpha;
+    const double alpha = in_reg(o, t.alpha);
+    cross = in_reg(o, cross);
+    w = in_reg(o, w);
+    dmw = in_reg(o, dmw);
+    wcross = in_reg(o, wcross);
 
     // 1. right-hand side
     for (int k = 1 + threadIdx.x; k <= N; k += blockDim.x) {

@@ -56,7 +56,9 @@ __device__ __forceinline__ unsigned long long mix64(unsigned long long x)
 // to_float_rn against the conversion instruction, and scale_down_pow2 against the FP64
 // multiply by 2^-s (s = 1..4), on `count` doubles drawn from seed: random bit patterns,
 // exponents near the FP32 range's ends, exact ties, all-ones fractions, +-0 and FP64
-// subnormals, and exponents within a few of zero, in turn.
+// subnormals, and exponents within a few of zero, in turn; and to_double_exact against the
+// conversion on random FP32 bit patterns, every eighth one with a zero exponent (+-0 or
+// an FP32 subnormal).
 __global__ void check_rounding_kernel(long long count, unsigned long long seed,
                                       unsigned long long* bad)
 {
@@ -78,6 +80,10 @@ __global__ void check_rounding_kernel(long long count, unsigned long long seed,
         const double x = __longlong_as_double((long long)b);
         const float want = __double2float_rn(x), got = to_float_rn(x);
         if (__float_as_uint(want) != __float_as_uint(got) && !(want != want && got != got)) ++local;
+        const float f = __uint_as_float((unsigned int)(k & 7 ? r2 >> 32 : (r2 >> 32) & 0x807fffffu));
+        const double fw = (double)f, fg = to_double_exact(f);
+        if (__double_as_longlong(fw) != __double_as_longlong(fg) && !(fw != fw && fg != fg))
+            ++local;
         const int s = 1 + (int)((r2 >> 8) & 3);
         const double p = __hiloint2double((1023 - s) << 20, 0);  // 2^-s
         const double wd = __dmul_rn(x, p), gd = scale_down_pow2(o, x, s, p);

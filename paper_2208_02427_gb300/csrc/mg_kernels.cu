@@ -30,8 +30,9 @@ __global__ void __launch_bounds__(MG_BX* MG_BY)
     const double edges = fadd(o, fadd(o, c[-1], c[1]), fadd(o, c[-pf], c[pf]));
     const double corners =
         fadd(o, fadd(o, c[-pf - 1], c[-pf + 1]), fadd(o, c[pf - 1], c[pf + 1]));
-    const double t = __fma_rn(2.0, c[0], edges);
-    const double u = __fma_rn(2.0, t, corners);
+    const double two = in_reg(o, 2.0);
+    const double t = __fma_rn(two, c[0], edges);
+    const double u = __fma_rn(two, t, corners);
     const int64_t at = (int64_t)J * pc + I;
     qc[at] = scale_down_pow2(o, u, 2, 0.25);
     if (ec) ec[at] = 0.0;

@@ -20,7 +20,9 @@ namespace {
 constexpr int BX = 64, BY = 4;      // red-black and transfer kernels
 constexpr int PX = 128, PY = 2;     // point kernels over all interior nodes
 constexpr int NORM_THREADS = 256;
-constexpr int NORM_MAX_BLOCKS = 1216;
+// 6 blocks of 256 threads per SM (at most 42 registers a thread): the norm kernels' grid of
+// at most 912 blocks (152 SMs) is resident at once.
+constexpr int NORM_BLOCKS_PER_SM = 6;
 
 __device__ __forceinline__ float nsum32(float w_, float e_, float s_, float n_, float b2,
                                         bool unit)
@@ -132,32 +134,33 @@ __global__ void __launch_bounds__(1024)
 // five FP64 operations per point off the FP64 pipe. sc is a power of two near 1 / ||r0||,
 // so the scaled squares stay within FP32's normal range down to 1e-13 ||r0||.
 template <bool UNIT, bool F32NORM>
-__global__ void __launch_bounds__(NORM_THREADS)
+__global__ void __launch_bounds__(NORM_THREADS, NORM_BLOCKS_PER_SM)
     defect64_to32_kernel(const double* __restrict__ psi, int m, int n, int64_t pitch, double b2,
                          double d, float* __restrict__ r32, float* __restrict__ e32,
                          int64_t pitch32, double* __restrict__ partials,
                          const float* __restrict__ sc)
 {
     const FmaOps o = load_fma_ops();
+    if (!UNIT) b2 = in_reg(o, b2);
+    d = in_reg(o, d);
     double acc = 0.0;
     float acc32 = 0.0f;
     const float scale = F32NORM ? *sc : 0.0f;
-    for (int j = 1 + blockIdx.x; j <= n - 2; j += gridDim.x)
-        for (int i = 1 + threadIdx.x; i <= m - 2; i += NORM_THREADS) {
-            const double* c = psi + (int64_t)j * pitch + i;
-            const double s = neighbour_sum<UNIT>(o, c[-1], c[1], c[-pitch], c[pitch], b2);
-            const double r = __fma_rn(-d, *c, s);
-            const float rf = to_float_rn(r);
-            if (F32NORM) {
-                const float rs = __fmul_rn(rf, scale);
-                acc32 = __fmaf_rn(rs, rs, acc32);
-            } else {
-                acc = __fma_rn(r, r, acc);
-            }
-            const int64_t at = (int64_t)j * pitch32 + i;
-            r32[at] = rf;
-            if (e32) e32[at] = 0.0f;
+    for (StrideWalk<NORM_THREADS> p(m, n); p.left > 0; p.next()) {
+        const double* c = psi + (int64_t)p.j * pitch + p.i;
+        const double s = neighbour_sum<UNIT>(o, c[-1], c[1], c[-pitch], c[pitch], b2);
+        const double r = __fma_rn(-d, *c, s);
+        const float rf = to_float_rn(r);
+        if (F32NORM) {
+            const float rs = __fmul_rn(rf, scale);
+            acc32 = __fmaf_rn(rs, rs, acc32);
+        } else {
+            acc = __fma_rn(r, r, acc);
         }
+        const int64_t at = (int64_t)p.j * pitch32 + p.i;
+        r32[at] = rf;
+        if (e32) e32[at] = 0.0f;
+    }
     if (F32NORM) acc = (double)acc32;
     __shared__ double red[NORM_THREADS / 32];
     acc = warp_sum(acc);
@@ -179,7 +182,7 @@ __global__ void __launch_bounds__(PX* PY)
     const int i = 1 + blockIdx.x * PX + threadIdx.x;
     if (j > n - 2 || i > m - 2) return;
     double* c = psi + (int64_t)j * pitch + i;
-    *c = fadd(o, *c, (double)e32[(int64_t)j * pitch32 + i]);
+    *c = fadd(o, *c, to_double_exact(e32[(int64_t)j * pitch32 + i]));
 }
 
 // ---- FP32 alone (the comparison point of the mixed solver) ----
@@ -210,19 +213,18 @@ __global__ void __launch_bounds__(PX* PY)
 
 // Per-block sums (FP64) of the squared FP32 residual r = (E+W) + b2 (N+S) + q - d u.
 template <bool UNIT>
-__global__ void __launch_bounds__(NORM_THREADS)
+__global__ void __launch_bounds__(NORM_THREADS, NORM_BLOCKS_PER_SM)
     defect32_sumsq_kernel(const float* __restrict__ u, const float* __restrict__ q, int m, int n,
                           int64_t pitch, float b2, float d, double* __restrict__ partials)
 {
     double acc = 0.0;
-    for (int j = 1 + blockIdx.x; j <= n - 2; j += gridDim.x)
-        for (int i = 1 + threadIdx.x; i <= m - 2; i += NORM_THREADS) {
-            const int64_t at = (int64_t)j * pitch + i;
-            const float* c = u + at;
-            const float s = __fadd_rn(nsum32(c[-1], c[1], c[-pitch], c[pitch], b2, UNIT), q[at]);
-            const double r = (double)__fmaf_rn(-d, *c, s);
-            acc = __fma_rn(r, r, acc);
-        }
+    for (StrideWalk<NORM_THREADS> p(m, n); p.left > 0; p.next()) {
+        const int64_t at = (int64_t)p.j * pitch + p.i;
+        const float* c = u + at;
+        const float s = __fadd_rn(nsum32(c[-1], c[1], c[-pitch], c[pitch], b2, UNIT), q[at]);
+        const double r = (double)__fmaf_rn(-d, *c, s);
+        acc = __fma_rn(r, r, acc);
+    }
     __shared__ double red[NORM_THREADS / 32];
     acc = warp_sum(acc);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
@@ -255,7 +257,7 @@ cudaError_t launch_to64(const Field& psi, const float* u, int64_t pitch32, cudaS
 cudaError_t launch_defect32_sumsq(const Field32& f, const float* q, const Coef& c, double* partials,
                                   cudaStream_t s)
 {
-    const int blocks = mixed_norm_blocks(f.n);
+    const int blocks = mixed_norm_blocks(f.m, f.n);
     if (c.unit_beta)
         defect32_sumsq_kernel<true><<<blocks, NORM_THREADS, 0, s>>>(f.p, q, f.m, f.n, f.pitch, (float)c.b2, (float)c.d, partials);
     else
@@ -264,7 +266,7 @@ cudaError_t launch_defect32_sumsq(const Field32& f, const float* q, const Coef& 
     return cudaGetLastError();
 }
 
-int mixed_norm_blocks(int n) { return n - 2 < NORM_MAX_BLOCKS ? (n - 2 > 0 ? n - 2 : 1) : NORM_MAX_BLOCKS; }
+int mixed_norm_blocks(int m, int n) { return norm_blocks_for(m, n); }
 
 cudaError_t launch_rb32(const Field32& f, const float* q, const Coef& c, bool gs, double w,
                         int colour, cudaStream_t s)
@@ -331,7 +333,7 @@ cudaError_t launch_defect64_to32(const Field& psi, const Coef& c, float* r32, fl
                                  int64_t pitch32, double* partials, cudaStream_t s,
                                  const float* norm_scale)
 {
-    const int blocks = mixed_norm_blocks(psi.n);
+    const int blocks = mixed_norm_blocks(psi.m, psi.n);
 #define LAP_D64(U, F)                                                                            \
     defect64_to32_kernel<U, F><<<blocks, NORM_THREADS, 0, s>>>(psi.p, psi.m, psi.n, psi.pitch, c.b2, \
                                                                c.d, r32, e32, pitch32, partials, \

@@ -20,7 +20,9 @@ namespace {
 constexpr int RB_BX = 64, RB_BY = 4;   // red-black: 64 same-colour points x 4 rows
 constexpr int JA_BX = 128, JA_BY = 2;  // Jacobi: 128 points x 2 rows
 constexpr int NORM_THREADS = 256;
-constexpr int NORM_MAX_BLOCKS = 1216;  // 8 per SM on 152 SMs
+// 6 blocks of 256 threads per SM (at most 42 registers a thread): the norm kernels' grid of
+// at most 912 blocks (152 SMs) is resident at once.
+constexpr int NORM_BLOCKS_PER_SM = 6;
 
 __device__ __forceinline__ void flush_maxd(unsigned long long v, unsigned long long* maxd)
 {
@@ -41,7 +43,12 @@ __global__ void __launch_bounds__(RB_BX* RB_BY)
     if (!GS && wslot) {  // w and 1 - w from device memory: register operands for the blend
         w = wslot[0];
         one_minus_w = wslot[1];
+    } else if (!GS) {
+        w = in_reg(o, w);
+        one_minus_w = in_reg(o, one_minus_w);
     }
+    if (!UNIT_BETA) b2 = in_reg(o, b2);
+    if (!POW2) inv_d = in_reg(o, inv_d);
     const int j = 1 + blockIdx.y * RB_BY + threadIdx.y;
     const int i = 1 + ((1 + j + colour) & 1) + 2 * (blockIdx.x * RB_BX + threadIdx.x);
     unsigned long long dl = 0;
@@ -66,6 +73,8 @@ __global__ void __launch_bounds__(JA_BX* JA_BY)
                   unsigned long long* __restrict__ maxd)
 {
     const FmaOps o = load_fma_ops();
+    if (!UNIT_BETA) b2 = in_reg(o, b2);
+    if (!POW2) inv_d = in_reg(o, inv_d);
     const int j = 1 + blockIdx.y * JA_BY + threadIdx.y;
     const int i = 1 + blockIdx.x * JA_BX + threadIdx.x;
     unsigned long long dl = 0;
@@ -97,6 +106,8 @@ __global__ void __launch_bounds__(JA_BX* JA_BY)
                   double* __restrict__ r, int m, int n, int64_t pitch, double b2, double d)
 {
     const FmaOps o = load_fma_ops();
+    if (!UNIT_BETA) b2 = in_reg(o, b2);
+    d = in_reg(o, d);
     const int j = 1 + blockIdx.y * JA_BY + threadIdx.y;
     const int i = 1 + blockIdx.x * JA_BX + threadIdx.x;
     if (j <= n - 2 && i <= m - 2) {
@@ -108,18 +119,19 @@ __global__ void __launch_bounds__(JA_BX* JA_BY)
 // Sum of r^2 over the interior: block b takes rows 1 + b, 1 + b + gridDim.x, ...; the
 // per-block partial is reduced in a fixed order, so the result depends only on (m, n).
 template <bool UNIT_BETA, bool HAS_Q>
-__global__ void __launch_bounds__(NORM_THREADS)
+__global__ void __launch_bounds__(NORM_THREADS, NORM_BLOCKS_PER_SM)
     defect_sumsq_kernel(const double* __restrict__ u, const double* __restrict__ q, int m, int n,
                         int64_t pitch, double b2, double d, double* __restrict__ partials)
 {
     const FmaOps o = load_fma_ops();
+    if (!UNIT_BETA) b2 = in_reg(o, b2);
+    d = in_reg(o, d);
     double acc = 0.0;
-    for (int j = 1 + blockIdx.x; j <= n - 2; j += gridDim.x)
-        for (int i = 1 + threadIdx.x; i <= m - 2; i += NORM_THREADS) {
-            const double r =
-                defect_at<UNIT_BETA, HAS_Q>(o, u, q, (int64_t)j * pitch + i, pitch, b2, d);
-            acc = __fma_rn(r, r, acc);
-        }
+    for (StrideWalk<NORM_THREADS> p(m, n); p.left > 0; p.next()) {
+        const double r =
+            defect_at<UNIT_BETA, HAS_Q>(o, u, q, (int64_t)p.j * pitch + p.i, pitch, b2, d);
+        acc = __fma_rn(r, r, acc);
+    }
     __shared__ double red[NORM_THREADS / 32];
     acc = warp_sum(acc);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
@@ -226,11 +238,7 @@ cudaError_t launch_defect(const Field& f, const double* q, double* r, const Coef
     return cudaGetLastError();
 }
 
-int norm_blocks(const Field& f)
-{
-    const int rows = f.n - 2;
-    return rows < NORM_MAX_BLOCKS ? rows : NORM_MAX_BLOCKS;
-}
+int norm_blocks(const Field& f) { return norm_blocks_for(f.m, f.n); }
 
 cudaError_t launch_defect_sumsq(const Field& f, const double* q, const Coef& c, double* partials,
                                 cudaStream_t s)
