@@ -341,7 +341,9 @@ __global__ void __launch_bounds__(BT)
         p32 = lv32[it.level].pitch;
     }
     // Mixed problems whose r0 is known sum (s r)^2 in FP32, s = 2^-e with r0 = f 2^e (exact
-    // scaling; the stopping norm needs a few digits), and store the partial descaled.
+    // scaling; the stopping norm needs a few digits), and store the partial descaled. The
+    // descaling by 2^2e is exact, so it is done once on the block's sum (the same value as
+    // descaling every thread's sum first).
     float sc = 0.0f;
     if (r32 && r0) {
         const double z = r0[L.problem];
@@ -371,7 +373,7 @@ __global__ void __launch_bounds__(BT)
             acc = __fma_rn(r, r, acc);
         }
     }
-    if (sc > 0.0f) acc = (double)acc32 / ((double)sc * (double)sc);  // exact: powers of two
+    if (sc > 0.0f) acc = (double)acc32;
     __shared__ double red[BT / 32];
     acc = warp_sum(acc);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
@@ -379,7 +381,8 @@ __global__ void __launch_bounds__(BT)
     if (threadIdx.x < 32) {
         double v = threadIdx.x < BT / 32 ? red[threadIdx.x] : 0.0;
         v = warp_sum(v);
-        if (threadIdx.x == 0) partials[blockIdx.x] = v;
+        if (threadIdx.x == 0)
+            partials[blockIdx.x] = sc > 0.0f ? v / ((double)sc * (double)sc) : v;  // exact
     }
 }
 

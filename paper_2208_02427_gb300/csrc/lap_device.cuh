@@ -161,6 +161,17 @@ struct StrideWalk {
     }
 };
 
+// The five FP64 values of a 5-point stencil at c (pitch p): loaded together for two points
+// before either is used, so that each thread of a grid-stride loop has two points' loads in
+// flight.
+struct Stencil5 {
+    double c, w, e, s, n;
+};
+__device__ __forceinline__ Stencil5 load5(const double* __restrict__ c, int64_t p)
+{
+    return Stencil5{c[0], c[-1], c[1], c[-p], c[p]};
+}
+
 // Deterministic warp reductions (fixed xor tree).
 __device__ __forceinline__ double warp_sum(double v)
 {

@@ -146,10 +146,9 @@ __global__ void __launch_bounds__(NORM_THREADS, NORM_BLOCKS_PER_SM)
     double acc = 0.0;
     float acc32 = 0.0f;
     const float scale = F32NORM ? *sc : 0.0f;
-    for (StrideWalk<NORM_THREADS> p(m, n); p.left > 0; p.next()) {
-        const double* c = psi + (int64_t)p.j * pitch + p.i;
-        const double s = neighbour_sum<UNIT>(o, c[-1], c[1], c[-pitch], c[pitch], b2);
-        const double r = __fma_rn(-d, *c, s);
+    // one point: r from its stencil values, rounded to FP32, summed, stored (e zeroed)
+    auto point = [&](const Stencil5& x, int i, int j) {
+        const double r = __fma_rn(-d, x.c, neighbour_sum<UNIT>(o, x.w, x.e, x.s, x.n, b2));
         const float rf = to_float_rn(r);
         if (F32NORM) {
             const float rs = __fmul_rn(rf, scale);
@@ -157,10 +156,23 @@ __global__ void __launch_bounds__(NORM_THREADS, NORM_BLOCKS_PER_SM)
         } else {
             acc = __fma_rn(r, r, acc);
         }
-        const int64_t at = (int64_t)p.j * pitch32 + p.i;
+        const int64_t at = (int64_t)j * pitch32 + i;
         r32[at] = rf;
         if (e32) e32[at] = 0.0f;
+    };
+    // a grid-stride walk, two points per step (both points' loads first), in walk order
+    StrideWalk<NORM_THREADS> p(m, n);
+    while (p.left >= 2) {
+        const int i0 = p.i, j0 = p.j;
+        p.next();
+        const int i1 = p.i, j1 = p.j;
+        p.next();
+        const Stencil5 x0 = load5(psi + (int64_t)j0 * pitch + i0, pitch);
+        const Stencil5 x1 = load5(psi + (int64_t)j1 * pitch + i1, pitch);
+        point(x0, i0, j0);
+        point(x1, i1, j1);
     }
+    if (p.left > 0) point(load5(psi + (int64_t)p.j * pitch + p.i, pitch), p.i, p.j);
     if (F32NORM) acc = (double)acc32;
     __shared__ double red[NORM_THREADS / 32];
     acc = warp_sum(acc);

@@ -89,6 +89,16 @@ __global__ void __launch_bounds__(JA_BX* JA_BY)
     if (MAXD) flush_maxd(dl, maxd);
 }
 
+// The scaled defect of Eq. 11 from loaded stencil values (q: the source term when HAS_Q).
+template <bool UNIT_BETA, bool HAS_Q>
+__device__ __forceinline__ double defect5(const FmaOps& o, const Stencil5& x, double q,
+                                          double b2, double d)
+{
+    double s = neighbour_sum<UNIT_BETA>(o, x.w, x.e, x.s, x.n, b2);
+    if (HAS_Q) s = fadd(o, s, q);
+    return __fma_rn(-d, x.c, s);
+}
+
 template <bool UNIT_BETA, bool HAS_Q>
 __device__ __forceinline__ double defect_at(const FmaOps& o, const double* __restrict__ u,
                                             const double* __restrict__ q, int64_t at,
@@ -116,8 +126,8 @@ __global__ void __launch_bounds__(JA_BX* JA_BY)
     }
 }
 
-// Sum of r^2 over the interior: block b takes rows 1 + b, 1 + b + gridDim.x, ...; the
-// per-block partial is reduced in a fixed order, so the result depends only on (m, n).
+// Sum of r^2 over the interior (a grid-stride walk, two points per step, summed in walk order);
+// the per-block partial is reduced in a fixed order, so the result depends only on (m, n).
 template <bool UNIT_BETA, bool HAS_Q>
 __global__ void __launch_bounds__(NORM_THREADS, NORM_BLOCKS_PER_SM)
     defect_sumsq_kernel(const double* __restrict__ u, const double* __restrict__ q, int m, int n,
@@ -127,7 +137,20 @@ __global__ void __launch_bounds__(NORM_THREADS, NORM_BLOCKS_PER_SM)
     if (!UNIT_BETA) b2 = in_reg(o, b2);
     d = in_reg(o, d);
     double acc = 0.0;
-    for (StrideWalk<NORM_THREADS> p(m, n); p.left > 0; p.next()) {
+    StrideWalk<NORM_THREADS> p(m, n);
+    while (p.left >= 2) {
+        const int64_t a0 = (int64_t)p.j * pitch + p.i;
+        p.next();
+        const int64_t a1 = (int64_t)p.j * pitch + p.i;
+        p.next();
+        const Stencil5 x0 = load5(u + a0, pitch), x1 = load5(u + a1, pitch);
+        const double q0 = HAS_Q ? q[a0] : 0.0, q1 = HAS_Q ? q[a1] : 0.0;
+        const double r0 = defect5<UNIT_BETA, HAS_Q>(o, x0, q0, b2, d);
+        const double r1 = defect5<UNIT_BETA, HAS_Q>(o, x1, q1, b2, d);
+        acc = __fma_rn(r0, r0, acc);
+        acc = __fma_rn(r1, r1, acc);
+    }
+    if (p.left > 0) {
         const double r =
             defect_at<UNIT_BETA, HAS_Q>(o, u, q, (int64_t)p.j * pitch + p.i, pitch, b2, d);
         acc = __fma_rn(r, r, acc);
