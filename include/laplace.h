@@ -257,13 +257,14 @@ int lap_residual_noalloc(const lap_grid* g, const double* psi_dev, const double*
  * the same either way. */
 int lap_set_graphs(lap_handle h, int enabled);
 
-/* Self-check (no counterpart in the paper): the kernels replace two FP64-pipe operations by
- * integer-pipe bit manipulation that is bit-identical by construction -- rounding the FP64
- * residual to FP32, and multiplying by 1/d when 1/d is 2^-k. This compares each with the
- * instruction it replaces on `count` doubles drawn from `seed` (random bits, FP32-range
- * edges, exact ties, all-ones fractions, zeros and subnormals, exponents at most a few
- * above zero; k = 1..4) and returns the number of differences (0 expected; two NaNs count as
- * equal) in *mismatches. Synchronises the device. */
+/* Self-check (no counterpart in the paper): the kernels replace three FP64-pipe operations
+ * by integer-pipe bit manipulation that is bit-identical by construction -- rounding the
+ * FP64 residual to FP32, widening the FP32 correction to FP64, and multiplying by 1/d when
+ * 1/d is 2^-k. This compares each with the instruction it replaces on `count` values drawn
+ * from `seed` (random bits, FP32-range edges, exact ties, all-ones fractions, zeros and
+ * subnormals, exponents at most a few above zero; k = 1..4) and returns the number of
+ * differences (0 expected; two NaNs count as equal) in *mismatches. Synchronises the
+ * device. */
 int lap_check_rounding(lap_handle h, int64_t count, uint64_t seed, int64_t* mismatches);
 
 /* Human-readable name of a return code, and the message of the last error on this thread. */
