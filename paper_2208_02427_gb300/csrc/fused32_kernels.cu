@@ -346,6 +346,18 @@ __device__ __forceinline__ void up_tile(const BatchLevel<float>& F, const BatchL
     const int m = F.m, n = F.n;
     const Region R = region_of(x0, y0, tx, ty, 2 * nu2);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (psi) {
+        // the owned points' FP64 lines into L2 now, so that the update after the smoothing
+        // does not wait on HBM (a row of at most 128 doubles spans at most 9 lines of 128 B)
+        const int px1 = min(x0 + tx, m - 1), py1 = min(y0 + ty, n - 1);
+        for (int gy = y0 + wid; gy < py1; gy += NW) {
+            const double* row = psi + (int64_t)gy * psi_pitch;
+            const uintptr_t first = reinterpret_cast<uintptr_t>(row + x0) & ~(uintptr_t)127;
+            const uintptr_t line = first + 128 * (uintptr_t)lane;
+            if (line <= reinterpret_cast<uintptr_t>(row + px1 - 1))
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(line));
+        }
+    }
     const int cI0 = R.gx0 >> 1, cJ0 = R.gy0 >> 1;  // floor halves (gy0 may be negative)
     const int cw = (R.w >> 1) + 1, ch = ((R.gy0 + R.h - 1) >> 1) - cJ0 + 2;
     const int mc = (m - 1) / 2 + 1, nc = (n - 1) / 2 + 1;
