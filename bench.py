@@ -397,7 +397,7 @@ def main():
              "grid_4097": mixed_vs_fp64(psi_host, H, 5)}
     mixed["grid_8193"] = mixed_vs_fp64(wl.sine_edges(8193, 8193, seed=wl.SEED_BASE + 1), 1.0 / 8192, 3)
 
-    def mixed_batch(count=256, side=1025, reps=2):
+    def mixed_batch(count=256, side=1025, reps=3):
         pristine = [b.to_field(wl.sine_edges(side, side, seed=wl.SEED_BASE + 3 + k), dev)
                     for k in range(count)]
         work_ = [f.clone() for f in pristine]
@@ -405,7 +405,7 @@ def main():
         for name, method in (("fp64", "mg"), ("mixed", "mg_mixed")):
             kw = dict(mg_kw, method=method)
             times, res = [], None
-            for rep in range(2 + reps):  # two warm-ups: graphs, tail choice
+            for rep in range(3 + reps):  # warm-ups: graphs, tail and item-size choice
                 for f, g in zip(work_, pristine):
                     f.copy_(g)
                 torch.cuda.synchronize(dev)
@@ -414,7 +414,7 @@ def main():
                 res = lap.solve_batched(work_, 1.0 / (side - 1), 1.0 / (side - 1), stream=stream, **kw)
                 e1.record(stream)
                 stream.synchronize()
-                if rep >= 2:
+                if rep >= 3:
                     times.append(e0.elapsed_time(e1))
             if not all(r["status"] == "converged" for r in res):
                 raise RuntimeError(f"batch {name}: not all problems converged")
@@ -479,7 +479,7 @@ def main():
         kw = dict(mg_kw)
         for name, method in (("fp64", "mg"), ("mixed", "mg_mixed")):
             times, res = [], None
-            for rep in range(3):  # first call warms up
+            for rep in range(6):  # three warm-ups: graphs, tail and item-size choice
                 for f, g in zip(work, pristine):
                     f.copy_(g)
                 torch.cuda.synchronize(dev)
@@ -488,7 +488,7 @@ def main():
                 res = lap.solve_batched(work, 1.0, 1.0, stream=stream, **dict(kw, method=method))
                 e1.record(stream)
                 stream.synchronize()
-                if rep:
+                if rep >= 3:
                     times.append(e0.elapsed_time(e1))
             if not all(r["status"] == "converged" for r in res):
                 raise RuntimeError(f"batched {name}: not all problems converged")

@@ -321,44 +321,33 @@ __global__ void __launch_bounds__(TAIL_THREADS)
 
 // FP64 residual of each item's rows: per-item sum of squares (fixed order) and, for the
 // mixed solver, the residual rounded to FP32 with the FP32 correction zeroed.
-__global__ void __launch_bounds__(BT)
-    b_sumsq_kernel(const BatchItem* __restrict__ items, const BatchLevel<double>* __restrict__ lv,
-                   const int* __restrict__ active, double* __restrict__ partials,
-                   const BatchLevel<float>* __restrict__ lv32, const double* __restrict__ r0)
+// Mixed problems whose r0 is known sum (s r)^2 in FP32, s = 2^-e with r0 = f 2^e (exact
+// scaling; the stopping norm needs a few digits), and store the partial descaled. The
+// descaling by 2^2e is exact, so it is done once on the block's sum (the same value as
+// descaling every thread's sum first). A thread takes two walk positions per step, both
+// points' stencils loaded before either is used; the sums keep the walk order.
+template <bool MIXED>
+__device__ __forceinline__ double sumsq_item(const BatchItem& it, const BatchLevel<double>& L,
+                                             const BatchLevel<float>* __restrict__ lv32,
+                                             float sc)
 {
-    const BatchItem it = items[blockIdx.x];
-    const BatchLevel<double> L = lv[it.level];
-    if (!active[L.problem]) return;
     const Arith<double> A = arith<double>();
+    const double nd = -in_reg(A.o, L.d), b2 = L.b2;
+    const bool unit = L.unit_beta != 0;
     const int wdt = L.m - 2;
-    double acc = 0.0;
     float* r32 = nullptr;
     float* e32 = nullptr;
     int64_t p32 = 0;
-    if (lv32 && lv32[it.level].q) {  // problems solved by the FP32 inner cycle
+    if (MIXED) {
         r32 = lv32[it.level].q;
         e32 = lv32[it.level].u;
         p32 = lv32[it.level].pitch;
     }
-    // Mixed problems whose r0 is known sum (s r)^2 in FP32, s = 2^-e with r0 = f 2^e (exact
-    // scaling; the stopping norm needs a few digits), and store the partial descaled. The
-    // descaling by 2^2e is exact, so it is done once on the block's sum (the same value as
-    // descaling every thread's sum first).
-    float sc = 0.0f;
-    if (r32 && r0) {
-        const double z = r0[L.problem];
-        if (z > 0.0 && isfinite(z)) {
-            const int e = ilogb(z);
-            if (e >= -100 && e <= 100) sc = ldexpf(1.0f, -e);
-        }
-    }
+    double acc = 0.0;
     float acc32 = 0.0f;
-    for (Walk k(wdt); k.r < it.rows; k.next()) {
-        const int j = it.row0 + k.r, i = 1 + k.c;
-        const double* c = L.u + (int64_t)j * L.pitch + i;
-        const double s = A.nsum(c[-1], c[1], c[-L.pitch], c[L.pitch], L.b2, L.unit_beta);
-        const double r = __fma_rn(-L.d, *c, s);
-        if (r32) {
+    auto point = [&](const Stencil5& x, int i, int j) {
+        const double r = __fma_rn(nd, x.c, A.nsum(x.w, x.e, x.s, x.n, b2, unit));
+        if (MIXED) {
             const float rf = to_float_rn(r);
             if (sc > 0.0f) {
                 const float rs = __fmul_rn(rf, sc);
@@ -372,8 +361,45 @@ __global__ void __launch_bounds__(BT)
         } else {
             acc = __fma_rn(r, r, acc);
         }
+    };
+    Walk k(wdt);
+    while (k.r < it.rows) {
+        const int j0 = it.row0 + k.r, i0 = 1 + k.c;
+        k.next();
+        if (k.r >= it.rows) {
+            point(load5(L.u + (int64_t)j0 * L.pitch + i0, L.pitch), i0, j0);
+            break;
+        }
+        const int j1 = it.row0 + k.r, i1 = 1 + k.c;
+        k.next();
+        const Stencil5 x0 = load5(L.u + (int64_t)j0 * L.pitch + i0, L.pitch);
+        const Stencil5 x1 = load5(L.u + (int64_t)j1 * L.pitch + i1, L.pitch);
+        point(x0, i0, j0);
+        point(x1, i1, j1);
     }
-    if (sc > 0.0f) acc = (double)acc32;
+    if (MIXED && sc > 0.0f) acc = (double)acc32;
+    return acc;
+}
+
+__global__ void __launch_bounds__(BT, 5)
+    b_sumsq_kernel(const BatchItem* __restrict__ items, const BatchLevel<double>* __restrict__ lv,
+                   const int* __restrict__ active, double* __restrict__ partials,
+                   const BatchLevel<float>* __restrict__ lv32, const double* __restrict__ r0)
+{
+    const BatchItem it = items[blockIdx.x];
+    const BatchLevel<double> L = lv[it.level];
+    if (!active[L.problem]) return;
+    // problems solved by the FP32 inner cycle have an FP32 level 0
+    const bool mixed = lv32 && lv32[it.level].q;
+    float sc = 0.0f;
+    if (mixed && r0) {
+        const double z = r0[L.problem];
+        if (z > 0.0 && isfinite(z)) {
+            const int e = ilogb(z);
+            if (e >= -100 && e <= 100) sc = ldexpf(1.0f, -e);
+        }
+    }
+    double acc = mixed ? sumsq_item<true>(it, L, lv32, sc) : sumsq_item<false>(it, L, lv32, 0.0f);
     __shared__ double red[BT / 32];
     acc = warp_sum(acc);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;

@@ -44,7 +44,8 @@ void build_lists(LevelLists& L, std::vector<BatchItem>& items, std::vector<TailJ
         const int f0 = (int)items.size();
         for (size_t k = 0; k < who.size(); ++k) {
             const int q = who[k];
-            if (nlev[q] - 1 > l && l < t[k]) add_items(items, base[q] + l, lv[base[q] + l].m, lv[base[q] + l].n);
+            if (nlev[q] - 1 > l && l < t[k])
+                add_items(items, base[q] + l, lv[base[q] + l].m, lv[base[q] + l].n);
         }
         L.fine[l] = {f0, (int)items.size() - f0};
         if (tiles) {
@@ -64,7 +65,8 @@ void build_lists(LevelLists& L, std::vector<BatchItem>& items, std::vector<TailJ
         const int a0 = (int)items.size();
         for (size_t k = 0; k < who.size(); ++k) {
             const int q = who[k];
-            if (nlev[q] > l && l <= t[k]) add_items(items, base[q] + l, lv[base[q] + l].m, lv[base[q] + l].n);
+            if (nlev[q] > l && l <= t[k])
+                add_items(items, base[q] + l, lv[base[q] + l].m, lv[base[q] + l].n);
         }
         L.all[l] = {a0, (int)items.size() - a0};
         const int c0 = (int)items.size();
@@ -347,6 +349,12 @@ extern "C" int lap_solve_batched(lap_handle h, int count, const lap_grid* grids,
                     const int c = tuner.next();
                     if (tuner.done) {
                         launch_cycle(c);
+                        continue;
+                    }
+                    if (left < count) {
+                        // problems already converged make the cycle cheaper: its time is not
+                        // comparable, so the best tail so far runs untimed
+                        launch_cycle(tuner.best);
                         continue;
                     }
                     // not tuned yet: time this cycle (the graph of c is captured before e0)

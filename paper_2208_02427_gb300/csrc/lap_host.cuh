@@ -189,7 +189,10 @@ std::string tuner_key(char kind, const lap_params* p, const std::vector<int>& sh
 cudaEvent_t tuner_event(lap_handle h, int k);
 
 // ---- V-cycles over many problems (lap_batched.cu, lap_server.cu) ----
-constexpr int BATCH_ITEM_POINTS = 2048;  // interior points per work item (rows are not split)
+// Interior points per work item (rows are not split). Measured on the 4096-grid batch (sides
+// 33..513, V(2,2) to 1e-10): FP64 145 / 140 / 140 / 145 ms at 2048 / 8192 / 16384 / 32768
+// points, the mixed solver 74 / 71 / 69 / 68 ms; 8192 for both.
+constexpr int BATCH_ITEM_POINTS = 8192;
 void add_items(std::vector<BatchItem>& items, int level_index, int m, int n);
 
 // Per-level work lists of one V-cycle over a set of problems: [first, count) into the items

@@ -114,3 +114,26 @@ def test_tail_size_is_validated(b):
         with pytest.raises(b.LapError):
             lap.solve(f, method="mg", tail_size=bad)
     lap.close()
+
+
+@pytest.mark.parametrize("method", ["mg", "mg_mixed"])
+def test_batched_tuning_gives_the_same_results(b, method):
+    """The batched tuner times the tail sizes on the cycles in which every problem is still
+    running, across successive solves of the same batch: every solve, while tuning and
+    after, has the same iterates and iteration counts."""
+    shapes = [(65, 65), (129, 257), (257, 129), (513, 513), (33, 129), (17, 17)]
+    inputs = [wl.random_ring(m, n, seed=800 + k) for k, (m, n) in enumerate(shapes)]
+    lap = b.Laplace()
+    ref = None
+    for _ in range(5):
+        fields = [b.to_field(x) for x in inputs]
+        res = lap.solve_batched(fields, 1.0, 1.0, method=method, tol=1e-10, max_iter=40)
+        assert all(r["status"] == "converged" for r in res)
+        out = ([host(f) for f in fields], [r["iters"] for r in res])
+        if ref is None:
+            ref = out
+            continue
+        assert out[1] == ref[1]
+        for k in range(len(shapes)):
+            assert np.array_equal(out[0][k], ref[0][k]), shapes[k]
+    lap.close()
