@@ -10,6 +10,8 @@
 //
 // The level data are generic in T: double for the FP64 V-cycle, float for the inner cycle
 // of the mixed-precision solver (FP32 inside FP64 defect correction).
+#include <type_traits>
+
 #include "lap_device.cuh"
 #include "lap_internal.cuh"
 
@@ -26,14 +28,15 @@ template <> struct Arith<double> {
     __device__ double add(double a, double b) const { return fadd(o, a, b); }
     __device__ double mul(double a, double b) const { return fmul(o, a, b); }
     __device__ double fma(double a, double b, double c) const { return __fma_rn(a, b, c); }
-    __device__ double nsum(double w, double e, double s, double n, double b2, bool unit) const
+    template <bool UNIT>
+    __device__ double nsum(double w, double e, double s, double n, double b2) const
     {
-        return unit ? neighbour_sum<true>(o, w, e, s, n, b2) : neighbour_sum<false>(o, w, e, s, n, b2);
+        return neighbour_sum<UNIT>(o, w, e, s, n, b2);
     }
+    template <bool POW2>
     __device__ double inv_d(double s, const BatchLevel<double>& L) const
     {
-        return L.inv_d_shift > 0 ? times_inv_d<true>(o, s, L.inv_d, L.inv_d_shift)
-                                 : times_inv_d<false>(o, s, L.inv_d, 0);
+        return times_inv_d<POW2>(o, s, L.inv_d, L.inv_d_shift);
     }
     __device__ double half(double x) const { return scale_down_pow2(o, x, 1, 0.5); }
     __device__ double quarter(double x) const { return scale_down_pow2(o, x, 2, 0.25); }
@@ -43,11 +46,13 @@ template <> struct Arith<float> {
     __device__ float add(float a, float b) const { return __fadd_rn(a, b); }
     __device__ float mul(float a, float b) const { return __fmul_rn(a, b); }
     __device__ float fma(float a, float b, float c) const { return __fmaf_rn(a, b, c); }
-    __device__ float nsum(float w, float e, float s, float n, float b2, bool unit) const
+    template <bool UNIT>
+    __device__ float nsum(float w, float e, float s, float n, float b2) const
     {
         const float ew = __fadd_rn(w, e), ns = __fadd_rn(s, n);
-        return unit ? __fadd_rn(ns, ew) : __fmaf_rn(b2, ns, ew);
+        return UNIT ? __fadd_rn(ns, ew) : __fmaf_rn(b2, ns, ew);
     }
+    template <bool POW2>
     __device__ float inv_d(float s, const BatchLevel<float>& L) const
     {
         return __fmul_rn(s, (float)L.inv_d);
@@ -86,30 +91,54 @@ struct Walk {
     }
 };
 
+// A flag that is uniform over a block (a level's beta == 1, 1/d a power of two, a source
+// term, GS or SOR) becomes a template argument: the loop is compiled once per value. Left a
+// run-time choice inside the per-point code, the compiler evaluates both sides of the short
+// FP64 branch and selects, one FP64 operation more per point (measured: the batched FP64
+// residual norm at 89% FP64-pipe occupancy for half its useful throughput).
+template <class F>
+__device__ __forceinline__ void on_flag(bool a, F&& f)
+{
+    if (a) f(std::true_type{});
+    else f(std::false_type{});
+}
+
 // ---- per-point arithmetic, shared by the item kernels and the small-level tail kernel ----
 
-// Eq. 6 (gs) or Eq. 7 at interior point (i, j) of level L, in place.
-template <class T>
+// Eq. 6 (GS) or Eq. 7 at interior point (i, j) of level L, in place; UNIT: beta == 1, POW2:
+// 1/d = 2^-k, HQ: L.q is set.
+template <class T, bool UNIT, bool POW2, bool HQ, bool GS>
 __device__ __forceinline__ void rb_point(const Arith<T>& A, const BatchLevel<T>& L, int i, int j,
-                                         bool gs, T w, T omw)
+                                         T w, T omw)
 {
     const int64_t at = (int64_t)j * L.pitch + i;
     T* c = L.u + at;
-    T s = A.nsum(c[-1], c[1], c[-L.pitch], c[L.pitch], (T)L.b2, L.unit_beta);
-    if (L.q) s = A.add(s, L.q[at]);
-    const T g = A.inv_d(s, L);
-    *c = gs ? g : A.fma(w, g, A.mul(omw, *c));
+    T s = A.template nsum<UNIT>(c[-1], c[1], c[-L.pitch], c[L.pitch], (T)L.b2);
+    if (HQ) s = A.add(s, L.q[at]);
+    const T g = A.template inv_d<POW2>(s, L);
+    *c = GS ? g : A.fma(w, g, A.mul(omw, *c));
 }
 
 // r = (E+W) + b2 (N+S) (+ q) - d u at interior point (i, j).
-template <class T>
+template <class T, bool UNIT, bool HQ>
 __device__ __forceinline__ void defect_point(const Arith<T>& A, const BatchLevel<T>& L, int i, int j)
 {
     const int64_t at = (int64_t)j * L.pitch + i;
     const T* c = L.u + at;
-    T s = A.nsum(c[-1], c[1], c[-L.pitch], c[L.pitch], (T)L.b2, L.unit_beta);
-    if (L.q) s = A.add(s, L.q[at]);
+    T s = A.template nsum<UNIT>(c[-1], c[1], c[-L.pitch], c[L.pitch], (T)L.b2);
+    if (HQ) s = A.add(s, L.q[at]);
     L.r[at] = A.fma(-(T)L.d, *c, s);
+}
+
+// The smoother's flags of level L (and the launch's GS flag) as template arguments of f.
+template <class T, class F>
+__device__ __forceinline__ void on_rb_flags(const BatchLevel<T>& L, bool gs, F&& f)
+{
+    on_flag(L.unit_beta != 0, [&](auto U) {
+        on_flag(L.inv_d_shift > 0, [&](auto P) {
+            on_flag(L.q != nullptr, [&](auto Q) { on_flag(gs, [&](auto G) { f(U, P, Q, G); }); });
+        });
+    });
 }
 
 // Coarse point (I, J): qc = 0.25 ((4 c + 2 edges) + corners) of the fine residual; the
@@ -165,11 +194,15 @@ __global__ void __launch_bounds__(BT)
         omw = (T)L.omw;
     }
     const int half_w = (L.m - 2 + 1) / 2;
-    for (Walk k(half_w); k.r < it.rows; k.next()) {
-        const int j = it.row0 + k.r;
-        const int i = 1 + ((1 + j + colour) & 1) + 2 * k.c;
-        if (i <= L.m - 2) rb_point(A, L, i, j, gs != 0, w, omw);
-    }
+    on_rb_flags(L, gs != 0, [&](auto U, auto P, auto Q, auto G) {
+        for (Walk k(half_w); k.r < it.rows; k.next()) {
+            const int j = it.row0 + k.r;
+            const int i = 1 + ((1 + j + colour) & 1) + 2 * k.c;
+            if (i <= L.m - 2)
+                rb_point<T, decltype(U)::value, decltype(P)::value, decltype(Q)::value,
+                         decltype(G)::value>(A, L, i, j, w, omw);
+        }
+    });
 }
 
 template <class T>
@@ -182,7 +215,12 @@ __global__ void __launch_bounds__(BT)
     if (!active[L.problem]) return;
     const Arith<T> A = arith<T>();
     const int wdt = L.m - 2;
-    for (Walk k(wdt); k.r < it.rows; k.next()) defect_point(A, L, 1 + k.c, it.row0 + k.r);
+    on_flag(L.unit_beta != 0, [&](auto U) {
+        on_flag(L.q != nullptr, [&](auto Q) {
+            for (Walk k(wdt); k.r < it.rows; k.next())
+                defect_point<T, decltype(U)::value, decltype(Q)::value>(A, L, 1 + k.c, it.row0 + k.r);
+        });
+    });
 }
 
 // Items of the coarse level: qc from the fine residual (the level before it in lv), and the
@@ -269,15 +307,19 @@ __device__ __forceinline__ void smooth_cta(const Arith<T>& A, const BatchLevel<T
 {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int half_w = (L.m - 2 + 1) / 2;
-    for (int k = 0; k < sweeps; ++k)
-        for (int colour = 0; colour < 2; ++colour) {
-            for (int j = 1 + wid; j <= L.n - 2; j += nw)
-                for (int t = lane; t < half_w; t += 32) {
-                    const int i = 1 + ((1 + j + colour) & 1) + 2 * t;
-                    if (i <= L.m - 2) rb_point(A, L, i, j, gs, w, omw);
-                }
-            __syncthreads();
-        }
+    on_rb_flags(L, gs, [&](auto U, auto P, auto Q, auto G) {
+        for (int k = 0; k < sweeps; ++k)
+            for (int colour = 0; colour < 2; ++colour) {
+                for (int j = 1 + wid; j <= L.n - 2; j += nw)
+                    for (int t = lane; t < half_w; t += 32) {
+                        const int i = 1 + ((1 + j + colour) & 1) + 2 * t;
+                        if (i <= L.m - 2)
+                            rb_point<T, decltype(U)::value, decltype(P)::value, decltype(Q)::value,
+                                     decltype(G)::value>(A, L, i, j, w, omw);
+                    }
+                __syncthreads();
+            }
+    });
 }
 
 template <class T>
@@ -298,8 +340,13 @@ __global__ void __launch_bounds__(TAIL_THREADS)
     for (int l = jb.first; l < jb.last; ++l) {
         const BatchLevel<T> F = lv[l];
         smooth_cta(A, F, nu1, gs != 0, w, omw);
-        for (int j = 1 + wid; j <= F.n - 2; j += nw)
-            for (int i = 1 + lane; i <= F.m - 2; i += 32) defect_point(A, F, i, j);
+        on_flag(F.unit_beta != 0, [&](auto U) {
+            on_flag(F.q != nullptr, [&](auto Q) {
+                for (int j = 1 + wid; j <= F.n - 2; j += nw)
+                    for (int i = 1 + lane; i <= F.m - 2; i += 32)
+                        defect_point<T, decltype(U)::value, decltype(Q)::value>(A, F, i, j);
+            });
+        });
         __syncthreads();
         const BatchLevel<T> C = lv[l + 1];
         for (int J = 1 + wid; J <= C.n - 2; J += nw)
@@ -326,14 +373,13 @@ __global__ void __launch_bounds__(TAIL_THREADS)
 // descaling by 2^2e is exact, so it is done once on the block's sum (the same value as
 // descaling every thread's sum first). A thread takes two walk positions per step, both
 // points' stencils loaded before either is used; the sums keep the walk order.
-template <bool MIXED>
+template <bool MIXED, bool UNIT>
 __device__ __forceinline__ double sumsq_item(const BatchItem& it, const BatchLevel<double>& L,
                                              const BatchLevel<float>* __restrict__ lv32,
                                              float sc)
 {
     const Arith<double> A = arith<double>();
     const double nd = -in_reg(A.o, L.d), b2 = L.b2;
-    const bool unit = L.unit_beta != 0;
     const int wdt = L.m - 2;
     float* r32 = nullptr;
     float* e32 = nullptr;
@@ -346,7 +392,7 @@ __device__ __forceinline__ double sumsq_item(const BatchItem& it, const BatchLev
     double acc = 0.0;
     float acc32 = 0.0f;
     auto point = [&](const Stencil5& x, int i, int j) {
-        const double r = __fma_rn(nd, x.c, A.nsum(x.w, x.e, x.s, x.n, b2, unit));
+        const double r = __fma_rn(nd, x.c, A.template nsum<UNIT>(x.w, x.e, x.s, x.n, b2));
         if (MIXED) {
             const float rf = to_float_rn(r);
             if (sc > 0.0f) {
@@ -399,7 +445,11 @@ __global__ void __launch_bounds__(BT, 5)
             if (e >= -100 && e <= 100) sc = ldexpf(1.0f, -e);
         }
     }
-    double acc = mixed ? sumsq_item<true>(it, L, lv32, sc) : sumsq_item<false>(it, L, lv32, 0.0f);
+    double acc = 0.0;
+    on_flag(L.unit_beta != 0, [&](auto U) {
+        acc = mixed ? sumsq_item<true, decltype(U)::value>(it, L, lv32, sc)
+                    : sumsq_item<false, decltype(U)::value>(it, L, lv32, 0.0f);
+    });
     __shared__ double red[BT / 32];
     acc = warp_sum(acc);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
