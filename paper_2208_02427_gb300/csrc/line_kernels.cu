@@ -40,7 +40,9 @@ __global__ void __launch_bounds__(256)
     dmw = in_reg(o, dmw);
     wcross = in_reg(o, wcross);
 
-    // 1. right-hand side
+    // 1. right-hand side; the Dirichlet ends' terms are added after the loop by the threads
+    //    that wrote those entries (the same fma, applied last, as written per point: a test
+    //    per point would let the compiler issue both fmas for every point)
     for (int k = 1 + threadIdx.x; k <= N; k += blockDim.x) {
         const int64_t at = (int64_t)k * sa;
         const double nb = fadd(o, base[at - sx], base[at + sx]);
@@ -49,10 +51,14 @@ __global__ void __launch_bounds__(256)
             r = UNIT_CROSS ? nb : fmul(o, cross, nb);
         else
             r = __fma_rn(dmw, base[at], fmul(o, wcross, nb));
-        if (k == 1) r = __fma_rn(alpha, base[0], r);
-        if (k == N) r = __fma_rn(alpha, base[(int64_t)(N + 1) * sa], r);
         const int g = k - 1, p = g / (L + 1);
         lane[p * Ls + (g - p * (L + 1))] = r;
+    }
+    if (threadIdx.x == 0) lane[0] = __fma_rn(alpha, base[0], lane[0]);  // k = 1: chunk 0, slot 0
+    if (threadIdx.x == (N - 1) % blockDim.x) {  // k = N, written by this thread
+        const int g = N - 1, p = g / (L + 1);
+        double* e = lane + p * Ls + (g - p * (L + 1));
+        *e = __fma_rn(alpha, base[(int64_t)(N + 1) * sa], *e);
     }
     __syncthreads();
 
