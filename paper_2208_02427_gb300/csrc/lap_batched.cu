@@ -251,8 +251,17 @@ extern "C" int lap_solve_batched(lap_handle h, int count, const lap_grid* grids,
         Sizer sz;
         carve_all(sz);
         Carver cv(arena(h, sz.off));
-        auto [lv64, lv32, items, jobs, tiles, first, active, status, remaining, iters, r0, rnow,
-              partials] = carve_all(cv);
+        // plain variables (lambdas below capture them; capturing structured bindings is C++20)
+        BatchLevel<double>* lv64;
+        BatchLevel<float>* lv32;
+        BatchItem* items;
+        TailJob* jobs;
+        TileItem* tiles;
+        int *first, *active, *status, *remaining;
+        long long* iters;
+        double *r0, *rnow, *partials;
+        std::tie(lv64, lv32, items, jobs, tiles, first, active, status, remaining, iters, r0, rnow,
+                 partials) = carve_all(cv);
         // zero every level buffer (rings of corrections stay zero), then upload tables
         const size_t level_bytes = (size_t)((char*)lv64 - (char*)h->arena);
         if (level_bytes) ck(cudaMemsetAsync(h->arena, 0, level_bytes, s), "zero levels");

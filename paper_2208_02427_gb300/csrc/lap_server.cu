@@ -343,8 +343,17 @@ extern "C" int lap_server_step(lap_server S, void* stream, int* running, int* qu
             S->stage_bytes = nb;
         }
         Carver cv(S->stage);
-        auto [lv64, lv32, items, jobs, tiles, fi, fn, active, status, remaining, iters, dr0, rnow, dtol,
-              pinit, pnorm] = carve_stage(cv);
+        // plain variables (lambdas below capture them; capturing structured bindings is C++20)
+        BatchLevel<double>* lv64;
+        BatchLevel<float>* lv32;
+        BatchItem* items;
+        TailJob* jobs;
+        TileItem* tiles;
+        int *fi, *fn, *active, *status, *remaining;
+        long long* iters;
+        double *dr0, *rnow, *dtol, *pinit, *pnorm;
+        std::tie(lv64, lv32, items, jobs, tiles, fi, fn, active, status, remaining, iters, dr0, rnow,
+                 dtol, pinit, pnorm) = carve_stage(cv);
         auto up = [&](void* dst, const void* src, size_t bytes) {
             if (bytes) ck(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st), "upload plan");
         };
