@@ -530,8 +530,8 @@ struct Solver {
         if (e < -100 || e > 100) return;
         norm_sc = std::ldexp(1.0, -e);
         const float v = (float)norm_sc;  // exact: a power of two in FP32's range
+        // pageable source: staged by the copy before it returns
         ck(cudaMemcpyAsync(w.nscale, &v, sizeof v, cudaMemcpyHostToDevice, s), "upload norm scale");
-        ck(cudaStreamSynchronize(s), "stream sync");
     }
 
     double read_maxd()
@@ -1057,11 +1057,14 @@ struct Solver {
             }
         }
         if (p->method == LAP_MG_MIXED || p->method == LAP_MG_FP32) {
-            for (const Level32& lv : w.levels32) {
-                ck(cudaMemsetAsync(lv.u.p, 0, (size_t)lv.u.n * lv.u.pitch * 4, s), "zero level");
-                ck(cudaMemsetAsync(lv.q, 0, (size_t)lv.u.n * lv.u.pitch * 4, s), "zero source");
-                if (lv.r) ck(cudaMemsetAsync(lv.r, 0, (size_t)lv.u.n * lv.u.pitch * 4, s), "zero level");
-            }
+            // FP32 alone needs its level-0 source zero; the mixed solver writes every interior
+            // before reading it and needs only the rings zero (after upload_tail, below)
+            if (p->method == LAP_MG_FP32)
+                for (const Level32& lv : w.levels32) {
+                    ck(cudaMemsetAsync(lv.u.p, 0, (size_t)lv.u.n * lv.u.pitch * 4, s), "zero level");
+                    ck(cudaMemsetAsync(lv.q, 0, (size_t)lv.u.n * lv.u.pitch * 4, s), "zero source");
+                    if (lv.r) ck(cudaMemsetAsync(lv.r, 0, (size_t)lv.u.n * lv.u.pitch * 4, s), "zero level");
+                }
             fused32 = !p->unfused && fused32_supported(p->nu1, p->nu2);
             if (fused32) ck(prepare_fused32(), "tile kernel attributes");
             const Level32& l0 = w.levels32[0];
@@ -1078,6 +1081,9 @@ struct Solver {
         const bool fp32_norm = p->method == LAP_MG_MIXED || p->method == LAP_MG_FP32;
         if (p->method == LAP_MG || fp32_norm) {
             upload_tail();
+            if (p->method == LAP_MG_MIXED)
+                ck(launch_zero_rings32(w.tl32, (int)w.levels32.size(), std::max(f.m, f.n), s),
+                   "ring kernel");
             const char kind = p->method == LAP_MG ? 'S' : (p->method == LAP_MG_MIXED ? 'M' : 'F');
             tuner = &h->tail_tuners[tuner_key(kind, p, {f.m, f.n})];
             if (tuner->cand.empty()) tuner->init(tail_candidates(false, kind != 'S', p->tail_size));

@@ -185,6 +185,9 @@ struct BatchList {
 struct TailJob {
     int first, last;
 };
+// The Dirichlet ring of the u, q and r buffers of FP32 levels lv[0 .. count) (device
+// descriptors) set to zero; max_side >= every level's m and n.
+cudaError_t launch_zero_rings32(const BatchLevel<float>* lv, int count, int max_side, cudaStream_t s);
 // per_level_w: Eq. 7 with each level's own w (BatchLevel::w) instead of the argument
 template <class T>
 cudaError_t launch_b_rb(const BatchList& l, const BatchLevel<T>* lv, const int* active, int colour,

@@ -248,7 +248,34 @@ __global__ void __launch_bounds__(NORM_THREADS, NORM_BLOCKS_PER_SM)
     }
 }
 
+// The ring of every FP32 level buffer (u, q, r) of levels 0 .. count - 1 set to zero: thread k
+// of block row l takes point k of level l's ring (row 0, row n - 1, column 0, column m - 1).
+__global__ void zero_rings32_kernel(const BatchLevel<float>* __restrict__ lv)
+{
+    const BatchLevel<float> V = lv[blockIdx.y];
+    const int m = V.m, n = V.n;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < 2 * m + 2 * n; k += gridDim.x * blockDim.x) {
+        int64_t at;
+        if (k < m) at = k;
+        else if (k < 2 * m) at = (int64_t)(n - 1) * V.pitch + (k - m);
+        else if (k < 2 * m + n) at = (int64_t)(k - 2 * m) * V.pitch;
+        else at = (int64_t)(k - 2 * m - n) * V.pitch + (m - 1);
+        V.u[at] = 0.0f;
+        if (V.q) V.q[at] = 0.0f;
+        if (V.r) V.r[at] = 0.0f;
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_zero_rings32(const BatchLevel<float>* lv, int count, int max_side, cudaStream_t s)
+{
+    if (count <= 0) return cudaSuccess;
+    const int per = 4 * max_side;
+    zero_rings32_kernel<<<dim3((per + 255) / 256, count), 256, 0, s>>>(lv);
+    note_launch();
+    return cudaGetLastError();
+}
 
 cudaError_t launch_to32(const Field& psi, float* a, float* b, int64_t pitch32, cudaStream_t s)
 {

@@ -119,3 +119,31 @@ def test_integer_pipe_fp32_rounding_matches_the_instruction(lap):
     range edges, ties, all-ones fractions, +-0, subnormals, tiny exponents)."""
     assert lap.check_rounding(1 << 26, seed=20220804) == 0
     assert lap.check_rounding(1 << 24, seed=7) == 0
+
+
+def test_reused_workspace_gives_fresh_results(b):
+    """The mixed solver zeroes only the rings of its FP32 levels and writes every interior
+    before reading it: after solves that leave other shapes' values and NaN in the handle's
+    workspace, results equal those of a fresh handle bit for bit (tiles, per-pass kernels,
+    with and without the small-level tail)."""
+    used = b.Laplace()
+    bad = wl.sine_edges(513, 1025, seed=70)
+    bad[200, 300] = np.nan
+    r = used.solve(b.to_field(bad), 1.0, 1.0, method="mg_mixed", tol=1e-10, max_iter=3)
+    assert r["status"] == "diverged"
+    used.solve(b.to_field(wl.random_ring(1025, 513, seed=71)), 1.0, 1.0, method="mg_mixed",
+               tol=0.0, max_iter=2)
+    for shape, kw in (((513, 257), {}), ((257, 513), dict(unfused=True)),
+                      ((385, 129), dict(tail_size=-1)), ((129, 129), dict(tail_size=65))):
+        x = wl.random_ring(*shape, seed=72 + shape[0])
+        outs = []
+        fresh = b.Laplace()
+        for lap in (used, fresh):
+            f = b.to_field(x)
+            res = lap.solve(f, 1.0, 1.0, method="mg_mixed", tol=1e-10, max_iter=30, **kw)
+            outs.append((host(f), res["iters"], res["status"]))
+        fresh.close()
+        assert outs[0][2] == outs[1][2] == "converged", shape
+        assert outs[0][1] == outs[1][1], shape
+        assert np.array_equal(outs[0][0], outs[1][0]), shape
+    used.close()
