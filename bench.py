@@ -42,8 +42,11 @@ FP64_OPS_PEAK = 152 * 2 * 2.070e9
 # FP64 operations per point of one red-black SOR colour pass: 3 adds (neighbour sum),
 # 1 multiply by (1-w), 1 fma; the multiply by 1/d = 1/4 runs on the integer pipe
 SOR_OPS_PER_POINT = 5
-SOR_BYTES_PER_POINT = 16  # one fused two-colour sweep: read 8, write 8 bytes per point
+SOR_BYTES_PER_POINT = 16  # algorithmic bytes of a sweep: read 8, write 8 bytes per point
+# FP64 operations per unknown of a zebra line half sweep, form A, beta = 1 (the kernel's count)
+LINE_OPS_PER_POINT = 8
 INTERIOR = (M - 2) * (N - 2)
+ORACLE_BATCH_SAMPLE = (0, 85, 170, 255)  # problems of the 256-grid batch checked against the oracle
 
 
 def parse():
@@ -139,10 +142,12 @@ def bus_id(dev):
 
 # ---- the oracle on the host (cpu_baseline and the reference arm) ----------------------
 
-def oracle_sample(psi, sor_sweeps: int, mg_cycles: int, sor_total: int, mg_total: int):
-    """Time the oracle on a bounded sample -- sor_sweeps calls of its red-black SOR sweep on
-    one buffer, and mg_cycles V(2,2) cycles through its driver (minus the two residual norms
-    the driver adds) -- and scale to whole solves with the iteration counts of this input."""
+def oracle_sample(psi, sor_sweeps: int, sor_total: int, threads: int = 0):
+    """Time the oracle on a bounded sample of one step's work: sor_sweeps calls of its
+    red-black SOR sweep on one buffer (scaled to sor_total, the sweeps this input needs), and
+    its whole V(2,2) multigrid solve to 1e-10 (run in full). With threads > 1 the SOR sweeps
+    run in the threaded timing wrapper (bitwise the oracle's sweeps; rows split across host
+    threads). Returns the baseline and the oracle's multigrid solution."""
     import ctypes as C
 
     import numpy as np
@@ -151,30 +156,32 @@ def oracle_sample(psi, sor_sweeps: int, mg_cycles: int, sor_total: int, mg_total
     from paper_2208_02427_gb300 import workloads as wl
     w = wl.w_opt_sor(M, N)
     buf = np.ascontiguousarray(psi, dtype=np.float64).copy()
-    ptr = buf.ctypes.data_as(C.POINTER(C.c_double))
-    lib = ora.lib()
     t0 = time.perf_counter()
-    for _ in range(sor_sweeps):
-        lib.ora_sor_sweep(M, N, 1.0, w, ora.RB, ptr, None)
+    if threads > 1:
+        buf = ora.mt_sor_rb_sweeps(buf, w, sor_sweeps, 1.0, threads)
+    else:
+        ptr = buf.ctypes.data_as(C.POINTER(C.c_double))
+        lib = ora.lib()
+        for _ in range(sor_sweeps):
+            lib.ora_sor_sweep(M, N, 1.0, w, ora.RB, ptr, None)
     t_sor = (time.perf_counter() - t0) / sor_sweeps
     t0 = time.perf_counter()
-    ora.defect_norm(psi)
-    t_norm = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    ora.solve(psi, method=ora.MG, ordering=ora.RB, dx=H, dy=H, tol=0.0, max_iter=mg_cycles)
-    t_mg = max(time.perf_counter() - t0 - 2 * t_norm, 0.0) / mg_cycles
-    solve_s = t_sor * sor_total + t_mg * mg_total
-    return {"value": 2.0 / solve_s, "unit": "solves/s", "cores": 1, "kind": "oracle",
-            "sample": f"{sor_sweeps} RB-SOR sweeps ({t_sor*1e3:.1f} ms each) + {mg_cycles} V(2,2) "
-                      f"cycles ({t_mg*1e3:.0f} ms each) of the single-threaded C oracle on the "
-                      f"4097^2 input, scaled to {sor_total} sweeps + {mg_total} cycles per solve",
-            "seconds_per_solve_pair": solve_s}
+    sol, info = ora.solve(psi, method=ora.MG, ordering=ora.RB, dx=H, dy=H, tol=TOL, max_iter=100)
+    t_mg = time.perf_counter() - t0
+    solve_s = t_sor * sor_total + t_mg
+    cores = max(1, threads)
+    return {"value": 2.0 / solve_s, "unit": "solves/s", "cores": cores, "kind": "oracle",
+            "sample": f"{sor_sweeps} RB-SOR sweeps ({t_sor*1e3:.1f} ms each, "
+                      f"{'threaded over ' + str(threads) + ' host threads' if threads > 1 else 'single-threaded'}) "
+                      f"scaled to {sor_total} sweeps, + the whole V(2,2) multigrid solve to 1e-10 "
+                      f"({info['iters']} cycles, {t_mg:.2f} s, single-threaded) of the C oracle "
+                      f"on the 4097^2 input",
+            "seconds_per_solve_pair": solve_s, "mg_cycles": info["iters"]}, sol
 
 
-# Iteration counts of this input to 1e-10 (RB-SOR tested every 100 sweeps; the oracle's
-# RB-SOR iterates are bitwise identical to the GPU's, so it needs the same count).
+# Sweeps of this input to 1e-10 (RB-SOR tested every 100 sweeps; the oracle's RB-SOR iterates
+# are bitwise identical to the GPU's, so it needs the same count).
 SOR_SWEEPS_TO_TOL = 15600
-MG_CYCLES_TO_TOL = 7
 
 
 def reference_arm(args):
@@ -188,7 +195,7 @@ def reference_arm(args):
     psi = wl.sine_edges(M, N, seed=wl.SEED_BASE + 1)
     samples = []
     for k in range(args.warmup + args.steps):
-        s = oracle_sample(psi, 4, 1, SOR_SWEEPS_TO_TOL, MG_CYCLES_TO_TOL)
+        s, _ = oracle_sample(psi, 4, SOR_SWEEPS_TO_TOL)
         if k >= args.warmup:
             samples.append(s)
     value = statistics.median(s["value"] for s in samples)
@@ -198,7 +205,8 @@ def reference_arm(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": WORKLOAD, "grid": "4097x4097", "tol": TOL},
             "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle",
-                             "sample": samples[0]["sample"] + " (each step one such sample)"},
+                             "sample": samples[0]["sample"] + " (each step one such sample; "
+                                       "the SOR part is extrapolated from the sampled sweeps)"},
             "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -264,32 +272,57 @@ def main():
     solves = replicas.reduce_scalar(2.0 * args.steps, "sum")
     value = solves / (total_ms / 1e3)
 
-    # ---- dominant kernel: one red-black SOR colour pass, timed on the same stream -------
-    reps = 200
-    with torch.cuda.stream(stream):
-        work.copy_(init)
-        b.smooth(work, w=w_sor, nsweeps=5, dx=H, dy=H, stream=stream)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        b.smooth(work, w=w_sor, nsweeps=reps, dx=H, dy=H, stream=stream)
-        e1.record(stream)
-    stream.synchronize()
-    launch_s = e0.elapsed_time(e1) / 1e3 / (2 * reps)
+    # ---- dominant kernel: one red-black SOR colour pass, inside the solve's graphs -------
+    # The solve replays check periods (100 sweeps + the residual norm + the device-side test)
+    # as one CUDA graph. Timing one-period solves of 200 and 2200 sweeps the same way and
+    # differencing leaves 2000 in-graph sweeps (4000 colour passes): the per-launch time of
+    # the kernel as it runs inside the timed step.
+    fma_rate = lap.fp64_rate()  # measured FP64 fma issue rate of this device (probe kernel)
+
+    def sor_period_ms(sweeps, reps=3):
+        kw = dict(sor_kw, tol=0.0, max_iter=sweeps, check_every=sweeps)
+        times = []
+        for r in range(2 + reps):  # two warm-ups: the period graph is captured on first use
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(stream):
+                work.copy_(init)
+                e0.record(stream)
+                lap.solve(work, H, H, stream=stream, **kw)
+                e1.record(stream)
+            stream.synchronize()
+            if r >= 2:
+                times.append(e0.elapsed_time(e1))
+        return statistics.median(times)
+
+    t_short, t_long = sor_period_ms(200), sor_period_ms(2200)
+    launch_s = (t_long - t_short) / 1e3 / (2 * 2000)
     pts_per_launch = INTERIOR / 2
     ops = SOR_OPS_PER_POINT * pts_per_launch / launch_s
-    hbm_gbs = SOR_BYTES_PER_POINT / 2 * pts_per_launch / launch_s / 1e9
+    # the algorithmic bytes of a red-black sweep are 16 per point (read and write each point
+    # once); a colour pass updates half the points: 16 B x pts_per_launch per launch
+    hbm_gbs = SOR_BYTES_PER_POINT * pts_per_launch / launch_s / 1e9
     peaks = measured_peaks()
     traffic = recorded_traffic("rb_colour_kernel")
     pipe_busy = recorded_traffic("rb_colour_kernel:fp64_pipe_active")
+    sor_step_ms = statistics.median(s["sor"]["ms"] for s in per_step)
+    sor_sweeps = per_step[-1]["sor"]["iters"]
     roofline = {"bound": "alu", "kernel": "rb_colour_kernel (SOR, one colour)",
-                "achieved": ops / 1e12, "peak": FP64_OPS_PEAK / 1e12, "unit": "Top/s",
-                "frac": ops / FP64_OPS_PEAK, "traffic": traffic,
-                "peak_source": "derived: 152 SMs x 2 FP64 ops/clk x 2070 MHz",
+                "achieved": ops / 1e12, "peak": fma_rate / 1e12, "unit": "Top/s",
+                "frac": ops / fma_rate, "traffic": traffic,
+                "peak_source": "measured live: lap_fp64_rate, FP64 fma chains on register "
+                               "operands over 4 blocks x 256 threads per SM",
+                "peak_derived": FP64_OPS_PEAK / 1e12,
+                "frac_of_derived": ops / FP64_OPS_PEAK,
+                "ops_per_point": SOR_OPS_PER_POINT, "points_per_launch": pts_per_launch,
                 "ncu_fp64_pipe_active": pipe_busy,
                 "ms_per_launch": launch_s * 1e3,
+                "ms_per_launch_how": "in-graph: (one-period solve of 2200 sweeps - one of 200) / "
+                                     "4000 colour passes, CUDA events on the solve stream",
+                "step_check": {"sor_solve_ms": sor_step_ms, "passes": 2 * sor_sweeps,
+                               "passes_x_ms_per_launch": 2 * sor_sweeps * launch_s * 1e3},
                 "hbm_view": {"achieved_gbs": hbm_gbs, "peak_gbs": peaks.get("hbm_gbs"),
                              "frac": hbm_gbs / peaks["hbm_gbs"] if peaks.get("hbm_gbs") else None,
-                             "bytes_per_point": SOR_BYTES_PER_POINT}}
+                             "bytes_per_point_per_sweep": SOR_BYTES_PER_POINT}}
 
     # ---- other hot-path kernels, per sweep ------------------------------------------------
     def kernel_ms(fn, reps):
@@ -303,18 +336,29 @@ def main():
         stream.synchronize()
         return e0.elapsed_time(e1) / reps
 
+    def alu_entry(ms, ops_pp, bytes_pp):
+        s_ = ms / 1e3
+        return {"ms": ms, "fp64_ops_per_point": ops_pp,
+                "achieved_top_s": ops_pp * INTERIOR / s_ / 1e12,
+                "frac_of_measured_fp64": ops_pp * INTERIOR / s_ / fma_rate,
+                "alg_bytes_per_point": bytes_pp, "gbs": bytes_pp * INTERIOR / s_ / 1e9,
+                "hbm_frac": (bytes_pp * INTERIOR / s_ / 1e9 / peaks["hbm_gbs"]
+                             if peaks.get("hbm_gbs") else None)}
+
     other = b.field(M, N, dev)
     other.copy_(init)
     kernels = {}
     ms = kernel_ms(lambda: b.smooth(work, w=1.0, nsweeps=1, dx=H, dy=H, stream=stream), 50)
     # GS at beta = 1 without a source term: the three adds of the neighbour sum (the multiply
     # by 1/4 runs on the integer pipe)
-    kernels["gs_sweep"] = {"ms": ms, "fp64_ops_per_point": 3,
-                           "fp64_ops_frac": 3 * INTERIOR / (ms / 1e3) / FP64_OPS_PEAK}
+    kernels["gs_sweep"] = alu_entry(ms, 3, 16)
+    # line relaxation, form A at beta = 1: per unknown 1 add (right-hand side), 3 (Thomas),
+    # 2 (separator superposition), 2 (relaxation) FP64 operations; 24 bytes per point
+    # (two neighbour lines read, the line read and written, per zebra colour)
     ms = kernel_ms(lambda: lap.line_sweep(work, 1.3, "A", 0, H, H, stream=stream), 10)
-    kernels["adi_x_half"] = {"ms": ms, "gbs_at_24B": 24 * INTERIOR / (ms / 1e3) / 1e9}
+    kernels["adi_x_half"] = alu_entry(ms, LINE_OPS_PER_POINT, 24)
     ms = kernel_ms(lambda: lap.line_sweep(work, 1.3, "A", 1, H, H, stream=stream), 10)
-    kernels["adi_y_half"] = {"ms": ms, "gbs_at_24B": 24 * INTERIOR / (ms / 1e3) / 1e9}
+    kernels["adi_y_half"] = alu_entry(ms, LINE_OPS_PER_POINT, 24)
     ms = kernel_ms(lambda: b.jacobi_sweep(init, other, H, H, stream=stream), 20)
     kernels["jacobi_sweep_with_ring_copy"] = {"ms": ms}
 
@@ -333,6 +377,32 @@ def main():
     latency = {"mg_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
                          "n": len(lat)},
                "sor_ms": {"p50": statistics.median(s["sor"]["ms"] for s in per_step), "n": len(per_step)}}
+
+    # ---- line relaxation to 1e-10: zebra SLOR by x-lines (form A) at its optimum ------------
+    # Zebra ADI (x-lines then y-lines) is not accelerated by w on fine grids (its iteration
+    # count grows like h^-2, about 1e6 iterations here); zebra SLOR is consistently ordered,
+    # so at Young's optimum it converges like h^-1 and reaches 1e-10 in bounded time.
+    w_slor = wl.w_opt_slor(M, N)
+    slor_kw = dict(method="slor", w=w_slor, line_form="A", tol=TOL, check_every=SOR_CHECK,
+                   max_iter=400000)
+    with torch.cuda.stream(stream):
+        work.copy_(init)
+        lap.solve(work, H, H, stream=stream, **dict(slor_kw, tol=0.0, max_iter=2 * SOR_CHECK))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        work.copy_(init)
+        e0.record(stream)
+        slor_info = lap.solve(work, H, H, stream=stream, **slor_kw)
+        e1.record(stream)
+    stream.synchronize()
+    slor_ms = e0.elapsed_time(e1)
+    line_solve = {"method": "zebra line SOR by x-lines, form A (Eqs. 8-9), residual tested every "
+                            f"{SOR_CHECK} sweeps", "w": w_slor, "iters": slor_info["iters"],
+                  "status": slor_info["status"], "ms": slor_ms, "solves_per_s": 1e3 / slor_ms,
+                  "r_final_over_r0": slor_info["r_final"] / slor_info["r0"],
+                  "ms_per_sweep": slor_ms / max(1, slor_info["iters"]),
+                  "adi": "zebra ADI is not run to 1e-10: not accelerated by w on this grid (h^-2 "
+                         "growth of its iteration count, about 1e6 iterations); its half sweeps "
+                         "are timed under kernels"}
 
     # ---- mixed precision: FP32 V-cycles inside FP64 defect correction ---------------------
     def timed_solve(field, src, kw, h):
@@ -362,7 +432,7 @@ def main():
         out[1:-1, 1:-1] = scipy.fft.idstn(uh, type=1, norm="ortho", workers=-1)
         return out
 
-    def mixed_vs_fp64(psi_np, h, reps):
+    def mixed_vs_fp64(psi_np, h, reps, keep):
         src = b.to_field(psi_np, dev)
         mixed_kw = dict(mg_kw, method="mg_mixed", inner_cycles=1)
         fp32_kw = dict(mg_kw, method="mg_fp32", tol=1e-5)
@@ -384,6 +454,7 @@ def main():
         for name, f in fields.items():
             got = f.cpu().numpy()
             out[name]["max_err_vs_exact_over_max"] = float(np.abs(got - want).max()) / scale
+            keep[name] = got  # compared with the oracle's solution in the CPU-baseline leg
         del want
         diff = (fields["mixed"] - fields["fp64"]).abs().max().item()
         out["speedup"] = out["fp64"]["ms_median"] / out["mixed"]["ms_median"]
@@ -394,8 +465,13 @@ def main():
                        "FP64 defect correction; FP64 residual, update and coarsest solve",
              "error": "max |psi - psi_exact| / max |psi_exact|, psi_exact the exact discrete "
                       "solution (DST-I, host FP64)",
-             "grid_4097": mixed_vs_fp64(psi_host, H, 5)}
-    mixed["grid_8193"] = mixed_vs_fp64(wl.sine_edges(8193, 8193, seed=wl.SEED_BASE + 1), 1.0 / 8192, 3)
+             "error_vs_oracle": "max |psi - psi_oracle| / max |psi_oracle|, psi_oracle the oracle's "
+                                "FP64 V(2,2) solution to the same 1e-10 (computed in the CPU-"
+                                "baseline leg)"}
+    kept = {"grid_4097": {}, "grid_8193": {}, "batch_256x1025": {}}
+    mixed["grid_4097"] = mixed_vs_fp64(psi_host, H, 5, kept["grid_4097"])
+    psi_8193 = wl.sine_edges(8193, 8193, seed=wl.SEED_BASE + 1)
+    mixed["grid_8193"] = mixed_vs_fp64(psi_8193, 1.0 / 8192, 3, kept["grid_8193"])
 
     def mixed_batch(count=256, side=1025, reps=3):
         pristine = [b.to_field(wl.sine_edges(side, side, seed=wl.SEED_BASE + 3 + k), dev)
@@ -421,10 +497,12 @@ def main():
             ms = statistics.median(times)
             out[name] = {"ms": ms, "solves_per_s": count / (ms / 1e3),
                          "max_cycles": max(r["iters"] for r in res)}
+            kept["batch_256x1025"][name] = [work_[k].cpu().numpy() for k in ORACLE_BATCH_SAMPLE]
         out["speedup"] = out["fp64"]["ms"] / out["mixed"]["ms"]
         return out
 
     mixed["batch_256x1025"] = mixed_batch()
+    batch_inputs = [wl.sine_edges(1025, 1025, seed=wl.SEED_BASE + 3 + k) for k in ORACLE_BATCH_SAMPLE]
 
     # ---- the paper's chamber problem (25 x 17, Eq. 4), its stopping rule (Eq. 16) ---------
     # Iteration counts the paper prints for it (Results and Discussion), context only: its
@@ -592,9 +670,40 @@ def main():
 
     cpu = None
     if rank == 0:
-        import oracle
-        oracle.build()
-        cpu = oracle_sample(psi_host, 30, 4, per_step[0]["sor"]["iters"], per_step[0]["mg"]["iters"])
+        # The CPU-baseline leg: the oracle timed on the host cores on a bounded sample (SOR
+        # sweeps scaled, the multigrid solve whole), single-threaded and with the SOR sweeps
+        # threaded over every host core; its multigrid solutions (4097^2, 8193^2, four
+        # problems of the 1025^2 batch) are the reference of the mixed-precision errors.
+        import oracle as ora
+        ora.build()
+        sor_iters = per_step[0]["sor"]["iters"]
+        cpu, sol = oracle_sample(psi_host, 30, sor_iters)
+        cores = os.cpu_count() or 1
+        cpu_mt, _ = oracle_sample(psi_host, 30, sor_iters, threads=cores)
+        cpu["all_cores"] = {k: v for k, v in cpu_mt.items() if k != "seconds_per_solve_pair"}
+
+        def rel(a, ref):
+            return float(np.abs(a - ref).max() / np.abs(ref).max())
+
+        mixed["grid_4097"]["oracle"] = {name: rel(got, sol) for name, got in kept["grid_4097"].items()}
+        t0 = time.perf_counter()
+        sol8, info8 = ora.solve(psi_8193, method=ora.MG, ordering=ora.RB, dx=1.0 / 8192, dy=1.0 / 8192,
+                                tol=TOL, max_iter=100)
+        mixed["grid_8193"]["oracle"] = {name: rel(got, sol8) for name, got in kept["grid_8193"].items()}
+        mixed["grid_8193"]["oracle"]["oracle_cycles"] = info8["iters"]
+        mixed["grid_8193"]["oracle"]["oracle_seconds"] = time.perf_counter() - t0
+        del sol8
+        bo = {"fp64": [], "mixed": []}
+        for k, x in enumerate(batch_inputs):
+            ref, _ = ora.solve(x, method=ora.MG, ordering=ora.RB, dx=1.0 / 1024, dy=1.0 / 1024,
+                               tol=TOL, max_iter=100)
+            for name in bo:
+                bo[name].append(rel(kept["batch_256x1025"][name][k], ref))
+        mixed["batch_256x1025"]["oracle"] = {name: max(v) for name, v in bo.items()}
+        mixed["batch_256x1025"]["oracle"]["sample"] = f"problems {list(ORACLE_BATCH_SAMPLE)}"
+        for key in ("grid_4097", "grid_8193", "batch_256x1025"):
+            o = mixed[key]["oracle"]
+            o["mixed_within_1e-10"] = o["mixed"] <= 1e-10
 
     lap.close()
     replicas.finish()
@@ -614,7 +723,7 @@ def main():
                         "ms_median": statistics.median(s[k]["ms"] for s in per_step),
                         "r_final_over_r0": per_step[-1][k]["r_final"] / per_step[-1][k]["r0"]}
                     for k in ("sor", "mg")},
-        "roofline": roofline, "kernels": kernels, "latency": latency,
+        "roofline": roofline, "kernels": kernels, "latency": latency, "line_relaxation": line_solve,
         "cpu_baseline": {k: v for k, v in cpu.items() if k != "seconds_per_solve_pair"},
         "mixed_precision": mixed, "chamber_25x17": chamber, "batched": batched, "serving": serving, "e2e": e2e,
         "gpu_launches": launches,

@@ -242,14 +242,23 @@ int lap_line_sweep(lap_handle h, const lap_grid* g, double* psi_dev, double w, i
  * and the call only enqueues work on `stream` (read *out_dev after synchronising).
  * psi_dev, q_dev (may be NULL) and out_dev must live on the current device.
  * Scratch: a fixed device array of 1218 doubles (~9.5 KB) inside the library, present on
- * every device that loads it until the process exits. The residual kernel uses at most
- * 1216 partial sums for any grid; a call that would need more fails with
- * LAP_EUNSUPPORTED. The first call on each device looks up the array's device address
+ * every device that loads it until the process exits: 1216 partial sums and the final
+ * pair. The residual kernel writes 6 partial sums per multiprocessor at most, whatever
+ * the grid (912 on a 152-SM GB300); on a device that would need more than 1216 the call
+ * fails with LAP_EUNSUPPORTED. The first call on each device looks up the array's device address
  * (cudaGetSymbolAddress), so make that first call before any stream capture. Every call
  * on a device shares the array and overwrites it: calls whose work overlaps on the GPU
  * (different streams or threads without ordering) race and must be serialised. */
 int lap_residual_noalloc(const lap_grid* g, const double* psi_dev, const double* q_dev,
                          double* out_dev, void* stream);
+
+/* Measurement aid (no counterpart in the paper): the FP64 fused multiply-add issue rate of
+ * the handle's device, *fma_per_s (host) = fmas per second, measured by a kernel whose
+ * threads run independent fma chains on register operands, timed with CUDA events on the
+ * legacy default stream (one warm-up launch, one timed launch, ~20 ms). Every FP64 kernel
+ * of this library issues its adds and multiplies as fmas, so this is the peak their
+ * operation counts are compared against. Synchronises the device's default stream. */
+int lap_fp64_rate(lap_handle h, double* fma_per_s);
 
 /* Enable (default) or disable CUDA-graph replay in lap_solve. With graphs, the
  * iterations between two stopping tests are captured once per handle (keyed by the field,

@@ -18,6 +18,8 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
+_SRC_MT = os.path.join(_HERE, "timing_mt.c")
+_LIB_MT = os.path.join(_HERE, "liboracle_mt.so")
 
 LEX, RB = 0, 1
 LINES_SUCCESSIVE, LINES_ZEBRA = 0, 1
@@ -36,6 +38,11 @@ def build(force: bool = False) -> str:
         subprocess.check_call(
             ["gcc", "-O2", "-std=c11", "-Wall", "-ffp-contract=off", "-fno-fast-math",
              "-fPIC", "-shared", "-o", _LIB, _SRC, "-lm"]
+        )
+    if force or not os.path.exists(_LIB_MT) or os.path.getmtime(_LIB_MT) < os.path.getmtime(_SRC_MT):
+        subprocess.check_call(
+            ["gcc", "-O2", "-std=gnu11", "-Wall", "-ffp-contract=off", "-fno-fast-math",
+             "-fPIC", "-shared", "-pthread", "-o", _LIB_MT, _SRC_MT, "-lm"]
         )
     return _LIB
 
@@ -79,6 +86,30 @@ def lib():
             fn.restype = res
             fn.argtypes = args
     return _lib
+
+
+_lib_mt = None
+
+
+def lib_mt():
+    """The threaded red-black SOR timing wrapper (timing_mt.c), for the all-cores baseline."""
+    global _lib_mt
+    if _lib_mt is None:
+        build()
+        _lib_mt = C.CDLL(_LIB_MT)
+        _lib_mt.ora_mt_sor_rb_sweeps.restype = C.c_int
+        _lib_mt.ora_mt_sor_rb_sweeps.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, C.c_int,
+                                                 C.POINTER(C.c_double), C.c_int]
+    return _lib_mt
+
+
+def mt_sor_rb_sweeps(psi, w, nsweeps, beta=1.0, threads=1):
+    """nsweeps red-black SOR sweeps on `threads` host threads (returns a copy)."""
+    psi = _field(psi).copy()
+    n, m = psi.shape
+    if lib_mt().ora_mt_sor_rb_sweeps(m, n, beta, w, nsweeps, _ptr(psi), threads) != 0:
+        raise RuntimeError("could not start the timing threads")
+    return psi
 
 
 def _ptr(a):

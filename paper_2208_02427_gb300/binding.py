@@ -101,6 +101,7 @@ def load():
             "lap_last_error": (C.c_char_p, []),
             "lap_kernel_launches": (c_int64, []),
             "lap_check_rounding": (C.c_int, [c_void_p, c_int64, C.c_uint64, C.POINTER(c_int64)]),
+            "lap_fp64_rate": (C.c_int, [c_void_p, C.POINTER(c_double)]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -199,6 +200,12 @@ class Laplace:
         out = c_int64(0)
         _check(self._lib.lap_check_rounding(self._h, int(count), int(seed), C.byref(out)))
         return int(out.value)
+
+    def fp64_rate(self) -> float:
+        """FP64 fused multiply-adds per second on this handle's device (a probe kernel)."""
+        out = c_double(0)
+        _check(self._lib.lap_fp64_rate(self._h, C.byref(out)))
+        return out.value
 
     def set_graphs(self, enabled: bool):
         """Replay each check period as a CUDA graph (default) or launch kernels one by one."""

@@ -12,6 +12,25 @@ void add_launches(int64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed
 
 thread_local std::string t_last_error;
 
+static std::atomic<int> g_device_sms[ATTR_DEVICES];
+
+int device_sms()
+{
+    const int d = attr_slot();
+    if (d >= 0) {
+        const int known = g_device_sms[d].load();
+        if (known > 0) return known;
+    }
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, d < 0 ? 0 : d) != cudaSuccess ||
+        sms <= 0) {
+        cudaGetLastError();
+        return 152;  // the attribute query failed: GB300's count
+    }
+    if (d >= 0) g_device_sms[d].store(sms);
+    return sms;
+}
+
 Coef make_coef(double dx, double dy)
 {
     Coef c;
@@ -429,7 +448,7 @@ template <class C>
 void carve(C& cv, Work& w, const lap_grid* g, const lap_params* p)
 {
     w.wslot = cv.template take<double>(2);
-    w.partials = cv.template take<double>(2048);
+    w.partials = cv.template take<double>(NORM_PARTIALS_MAX);
     w.nrm = cv.template take<double>(2);
     w.nscale = cv.template take<float>(1);
     w.loop = cv.template take<LoopState>(1);
@@ -1321,8 +1340,8 @@ int lap_residual(lap_handle h, const lap_grid* g, const double* psi_dev, const d
         check_device_ptr(h, psi_dev, "psi");
         check_device_ptr(h, q_dev, "q", true);
         cudaStream_t s = (cudaStream_t)stream;
-        Carver cv(arena(h, 2048 * 8 + 1024));
-        double* partials = cv.take<double>(2048);
+        Carver cv(arena(h, NORM_PARTIALS_MAX * 8 + 1024));
+        double* partials = cv.take<double>(NORM_PARTIALS_MAX);
         double* nrm = cv.take<double>(2);
         const Field f{const_cast<double*>(psi_dev), g->m, g->n, g->pitch};
         const Coef c = make_coef(g->dx, g->dy);
@@ -1460,6 +1479,39 @@ int lap_check_rounding(lap_handle h, int64_t count, uint64_t seed, int64_t* mism
     });
 }
 
+int lap_fp64_rate(lap_handle h, double* fma_per_s)
+{
+    return guarded([&] {
+        if (!h || !fma_per_s) fail(LAP_EINVAL, "handle or result is NULL");
+        set_device(h);
+        const int blocks = 4 * device_sms();
+        double* sink = (double*)dev_alloc(h, sizeof(double) * blocks);
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        try {
+            ck(cudaEventCreate(&e0), "create event");
+            ck(cudaEventCreate(&e1), "create event");
+            const long long iters = 1 << 13;
+            if (launch_fp64_rate(blocks, iters, sink, nullptr) < 0) ck(cudaGetLastError(), "rate kernel");
+            ck(cudaEventRecord(e0, nullptr), "record event");
+            const int64_t fmas = launch_fp64_rate(blocks, iters, sink, nullptr);
+            if (fmas < 0) ck(cudaGetLastError(), "rate kernel");
+            ck(cudaEventRecord(e1, nullptr), "record event");
+            ck(cudaEventSynchronize(e1), "event sync");
+            float ms = 0.f;
+            ck(cudaEventElapsedTime(&ms, e0, e1), "event time");
+            *fma_per_s = (double)fmas / (ms * 1e-3);
+        } catch (...) {
+            if (e0) cudaEventDestroy(e0);
+            if (e1) cudaEventDestroy(e1);
+            dev_free(h, sink, sizeof(double) * blocks);
+            throw;
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        dev_free(h, sink, sizeof(double) * blocks);
+    });
+}
+
 int lap_set_graphs(lap_handle h, int enabled)
 {
     return guarded([&] {
@@ -1497,8 +1549,9 @@ int64_t lap_kernel_launches(void) { return g_launches.load(); }
 
 namespace {
 
-// The residual kernel writes at most norm_blocks() <= 1216 partial sums (8 blocks per SM
-// on 152 SMs), whatever the grid size.
+// The residual kernel writes at most norm_blocks() partial sums, 6 per multiprocessor of
+// the device whatever the grid size: 912 on a 152-SM GB300. The array holds 1216 (devices
+// of up to 202 multiprocessors); a call that would need more is refused.
 constexpr int kNoAllocPartials = 1216;
 constexpr int kNoAllocDoubles = kNoAllocPartials + 2;  // partials, then [sum, sqrt(sum)]
 constexpr int kNoAllocMaxDevices = 64;

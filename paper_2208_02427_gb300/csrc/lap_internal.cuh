@@ -67,20 +67,31 @@ cudaError_t launch_jacobi(const Field& in, double* out, const Coef& c, unsigned 
 // r := scaled residual on interior nodes (Eqs. 11-12); r has f's pitch.
 cudaError_t launch_defect(const Field& f, const double* q, double* r, const Coef& c,
                           cudaStream_t s);
+// Multiprocessors of the current device (looked up once per device ordinal).
+int device_sms();
+// The most partial sums a norm kernel writes: its solve-scratch buffers hold this many.
+constexpr int NORM_PARTIALS_MAX = 2046;
 // sum of squares of the residual into per-block partials; partials[nblocks].
 // Blocks of the norm kernels (256 threads, a grid-stride walk over the interior): one per 256
-// interior points, at least 1 and at most 912 (6 per SM on 152 SMs, all resident at once).
+// interior points, at least 1 and at most 6 per multiprocessor of the current device, all
+// resident at once (912 on a 152-SM GB300); never more than NORM_PARTIALS_MAX.
 inline int norm_blocks_for(int m, int n)
 {
     if (m < 3 || n < 3) return 1;
     const int64_t b = ((int64_t)(m - 2) * (int64_t)(n - 2) + 255) / 256;
-    return b < 912 ? (int)b : 912;
+    int cap = 6 * device_sms();
+    if (cap > NORM_PARTIALS_MAX) cap = NORM_PARTIALS_MAX;
+    return b < cap ? (int)b : cap;
 }
 int norm_blocks(const Field& f);
 cudaError_t launch_defect_sumsq(const Field& f, const double* q, const Coef& c, double* partials,
                                 cudaStream_t s);
 // out[0] = sum(partials[0..count)), fixed order; out[1] = sqrt(out[0]).
 cudaError_t launch_sum_partials(const double* partials, int count, double* out, cudaStream_t s);
+// FP64 fma issue-rate probe: blocks x 256 threads, `iters` steps of 8 independent fma chains
+// each; returns the fmas issued (-1 on a launch error). sink: blocks doubles (never written
+// in practice).
+int64_t launch_fp64_rate(int blocks, long long iters, double* sink, cudaStream_t s);
 // *bad += mismatches of the integer-pipe FP64 -> FP32 rounding against the instruction.
 cudaError_t launch_check_rounding(long long count, unsigned long long seed, unsigned long long* bad,
                                   cudaStream_t s);

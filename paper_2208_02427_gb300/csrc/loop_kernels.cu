@@ -3,7 +3,8 @@
 // loop_decide_kernel runs inside the body of a conditional CUDA graph node: after each check
 // period it applies the host loop's stopping rule (Eq. 16 or the L2 rules) and sets the
 // loop's condition. check_rounding_kernel compares the residual kernels' integer-pipe
-// FP64 -> FP32 rounding with the conversion instruction.
+// FP64 -> FP32 rounding with the conversion instruction. fp64_rate_kernel measures the FP64
+// fused multiply-add issue rate, the peak that the FP64-bound kernels are measured against.
 #include "lap_device.cuh"
 #include "lap_internal.cuh"
 
@@ -93,7 +94,41 @@ __global__ void check_rounding_kernel(long long count, unsigned long long seed,
     if (local) atomicAdd(bad, local);
 }
 
+// FP64 issue-rate probe: every thread runs CHAINS independent recurrences x = fma(x, a, b)
+// for `iters` steps, with a and b in registers (in_reg; constant-bank operands issue slower,
+// see lap_device.cuh), so the FP64 pipe never waits on a dependency once a few warps per SM
+// are resident. fmas issued = threads * CHAINS * iters. The result is stored only when it
+// equals an impossible value, which keeps the chains live.
+constexpr int RATE_CHAINS = 8;
+__global__ void __launch_bounds__(256)
+    fp64_rate_kernel(long long iters, double a, double b, double* __restrict__ sink)
+{
+    const FmaOps o = load_fma_ops();
+    a = in_reg(o, a);
+    b = in_reg(o, b);
+    double x[RATE_CHAINS];
+#pragma unroll
+    for (int k = 0; k < RATE_CHAINS; ++k) x[k] = (double)(threadIdx.x + 32 * k) * 1e-3;
+    for (long long t = 0; t < iters; ++t) {
+#pragma unroll
+        for (int k = 0; k < RATE_CHAINS; ++k) x[k] = __fma_rn(x[k], a, b);
+    }
+    double acc = x[0];
+#pragma unroll
+    for (int k = 1; k < RATE_CHAINS; ++k) acc = fmax(acc, x[k]);
+    if (acc == -1.0) sink[blockIdx.x] = acc;
+}
+
 }  // namespace
+
+int64_t launch_fp64_rate(int blocks, long long iters, double* sink, cudaStream_t s)
+{
+    // a < 1, b > 0: every chain tends to b / (1 - a) = 1, no overflow or subnormals
+    fp64_rate_kernel<<<blocks, 256, 0, s>>>(iters, 0.999999, 1e-6, sink);
+    note_launch();
+    if (cudaGetLastError() != cudaSuccess) return -1;
+    return (int64_t)blocks * 256 * RATE_CHAINS * iters;
+}
 
 cudaError_t launch_check_rounding(long long count, unsigned long long seed, unsigned long long* bad,
                                   cudaStream_t s)

@@ -21,7 +21,7 @@ constexpr int BX = 64, BY = 4;      // red-black and transfer kernels
 constexpr int PX = 128, PY = 2;     // point kernels over all interior nodes
 constexpr int NORM_THREADS = 256;
 // 6 blocks of 256 threads per SM (at most 42 registers a thread): the norm kernels' grid of
-// at most 912 blocks (152 SMs) is resident at once.
+// at most 6 blocks per SM (norm_blocks_for; 912 on 152 SMs) is resident at once.
 constexpr int NORM_BLOCKS_PER_SM = 6;
 
 __device__ __forceinline__ float nsum32(float w_, float e_, float s_, float n_, float b2,

@@ -117,3 +117,13 @@ def w_opt_sor(m: int, n: int, beta: float = 1.0) -> float:
     b2 = beta * beta
     rho = (np.cos(np.pi / (m - 1)) + b2 * np.cos(np.pi / (n - 1))) / (1.0 + b2)
     return float(2.0 / (1.0 + np.sqrt(1.0 - rho * rho)))
+
+
+def w_opt_slor(m: int, n: int, beta: float = 1.0) -> float:
+    """Optimal factor of zebra line SOR by x-lines, 2 / (1 + sqrt(1 - rho^2)), from the
+    spectral radius of line Jacobi by x-lines, rho = beta^2 cos(pi/(n-1)) /
+    (1 + beta^2 - cos(pi/(m-1))) (its slowest mode sin(pi x) sin(pi y)); zebra ordering
+    is consistently ordered, so Young's formula applies."""
+    b2 = beta * beta
+    rho = b2 * np.cos(np.pi / (n - 1)) / (1.0 + b2 - np.cos(np.pi / (m - 1)))
+    return float(2.0 / (1.0 + np.sqrt(1.0 - rho * rho)))

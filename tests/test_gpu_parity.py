@@ -267,6 +267,25 @@ def test_full_size_adi_iteration(lap, b, big):
     assert relerr(got, want) <= REL
 
 
+@pytest.mark.parametrize("form", ["A", "B"])
+def test_full_size_slor_iterations(lap, b, big, form):
+    """Zebra line SOR on the full 4097^2 field at the line-SOR optimum (the bench's solve),
+    two iterations against the oracle."""
+    w = wl.w_opt_slor(4097, 4097)
+    got, g, want, o = both(lap, b, big, 1 / 4096, 1 / 4096, method="slor", w=w, line_form=form,
+                           tol=0.0, max_iter=2)
+    assert g["iters"] == o["iters"] == 2
+    assert relerr(got, want) <= REL
+
+
+def test_fp64_rate_probe(lap):
+    """lap_fp64_rate: the FP64 fma issue rate the bench's ALU roofline divides by. GB300 is
+    specified at 1.25 TFLOP/s FP64 (0.625 T fma/s); a measurement far outside means the probe
+    does not measure what it claims."""
+    r = lap.fp64_rate()
+    assert 2e11 < r < 2e12, r
+
+
 def test_full_size_multigrid_cycle(lap, b, big):
     got, g, want, o = both(lap, b, big, 1 / 4096, 1 / 4096, method="mg", tol=0.0, max_iter=1)
     assert relerr(got, want) <= REL

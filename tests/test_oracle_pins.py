@@ -381,3 +381,35 @@ def test_line_sweep_defect_comes_from_later_lines(order, direction):
             later = [l - 1, l + 1] if l % 2 == 1 else []
         want = sum(cross * delta[k, 1:-1] for k in later)
         assert np.max(np.abs(r[l, 1:-1] - want)) <= 1e-13, (l, order, direction)
+
+
+def test_slor_optimum_minimises_the_oracle_radius():
+    """w_opt_slor (the bench's zebra line-SOR factor) from the x-line Jacobi radius: at it the
+    oracle's zebra SLOR (form A) iteration matrix has radius w_opt - 1 (Young's optimum for a
+    consistently ordered splitting), and nearby factors converge more slowly."""
+    m, n, beta = 9, 8, 1.3
+    w = wl.w_opt_slor(m, n, beta)
+
+    def radius(wv):
+        T = exact.iteration_matrix(lambda e: ora.line_sweep(e, wv, 0, beta, ora.FORM_A, ora.LINES_ZEBRA),
+                                   m, n)
+        return exact.spectral_radius(T)
+
+    # the optimum is a double eigenvalue (a Jordan block): computed to about sqrt(eps)
+    assert abs(radius(w) - (w - 1.0)) <= 1e-6
+    assert radius(w - 0.05) > radius(w) + 1e-3
+    assert radius(w + 0.05) > radius(w) + 1e-3
+
+
+@pytest.mark.parametrize("shape,beta,threads", [((33, 17), 1.0, 1), ((65, 40), 1.3, 3),
+                                                ((257, 129), 1.0, 8), ((9, 5), 0.7, 16)])
+def test_threaded_timing_sweeps_equal_the_oracle(shape, beta, threads):
+    """The all-cores CPU baseline's threaded red-black SOR sweeps are the oracle's sweeps bit
+    for bit (same update expression; rows split across threads, a barrier per colour)."""
+    m, n = shape
+    psi = wl.random_interior(wl.random_ring(m, n, seed=m + n), seed=m * n)
+    want = psi.copy()
+    for _ in range(5):
+        want = ora.sor_sweep(want, 1.7, beta, ora.RB)
+    got = ora.mt_sor_rb_sweeps(psi, 1.7, 5, beta, threads)
+    assert np.array_equal(got, want)
