@@ -43,8 +43,10 @@ FP64_OPS_PEAK = 152 * 2 * 2.070e9
 # 1 multiply by (1-w), 1 fma; the multiply by 1/d = 1/4 runs on the integer pipe
 SOR_OPS_PER_POINT = 5
 SOR_BYTES_PER_POINT = 16  # algorithmic bytes of a sweep: read 8, write 8 bytes per point
-# FP64 operations per unknown of a zebra line half sweep, form A, beta = 1 (the kernel's count)
-LINE_OPS_PER_POINT = 8
+# FP64 operations per unknown of a zebra line half sweep, form A, beta = 1 (the kernels' count):
+# 1 add (right-hand side), 1 fma forward, 1 fma back, 2 for the relaxed output, plus 2 fmas in the
+# first K0 = 34 positions of each 127-unknown chunk (the boundary layer): 5 + 68/127
+LINE_OPS_PER_POINT = 5.54
 INTERIOR = (M - 2) * (N - 2)
 ORACLE_BATCH_SAMPLE = (0, 85, 170, 255)  # problems of the 256-grid batch checked against the oracle
 
@@ -352,9 +354,9 @@ def main():
     # GS at beta = 1 without a source term: the three adds of the neighbour sum (the multiply
     # by 1/4 runs on the integer pipe)
     kernels["gs_sweep"] = alu_entry(ms, 3, 16)
-    # line relaxation, form A at beta = 1: per unknown 1 add (right-hand side), 3 (Thomas),
-    # 2 (separator superposition), 2 (relaxation) FP64 operations; 24 bytes per point
-    # (two neighbour lines read, the line read and written, per zebra colour)
+    # line relaxation, form A at beta = 1: LINE_OPS_PER_POINT FP64 operations per unknown;
+    # 24 algorithmic bytes per point (per zebra colour the other colour's lines read, the
+    # line read and written)
     ms = kernel_ms(lambda: lap.line_sweep(work, 1.3, "A", 0, H, H, stream=stream), 10)
     kernels["adi_x_half"] = alu_entry(ms, LINE_OPS_PER_POINT, 24)
     ms = kernel_ms(lambda: lap.line_sweep(work, 1.3, "A", 1, H, H, stream=stream), 10)

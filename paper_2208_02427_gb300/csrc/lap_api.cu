@@ -154,8 +154,8 @@ void check_params(const lap_params* p)
 
 // ---- line-solver tables --------------------------------------------------------------
 
-constexpr int LINE_MAX_CHUNKS = 128;
 constexpr int LINE_MAX_N = 16383;
+constexpr int LINE_MIN_CHUNK = 16;
 
 // Thomas solve of tridiag(-alpha, delta, -alpha) x = rhs (size len) on the host.
 std::vector<double> host_thomas(int len, double alpha, double delta, const std::vector<double>& rhs)
@@ -169,9 +169,9 @@ std::vector<double> host_thomas(int len, double alpha, double delta, const std::
     return x;
 }
 
-const LineTables& line_tables(lap_handle h, int N, double alpha, double delta)
+const LineTables& line_tables(lap_handle h, int N, double alpha, double delta, double wc)
 {
-    auto key = std::make_tuple(N, alpha, delta);
+    auto key = std::make_tuple(N, alpha, delta, wc);
     auto it = h->lines.find(key);
     if (it != h->lines.end()) return it->second.t;
     if (N > LINE_MAX_N) fail(LAP_EUNSUPPORTED, "line longer than 16383 unknowns");
@@ -179,13 +179,19 @@ const LineTables& line_tables(lap_handle h, int N, double alpha, double delta)
     t.N = N;
     t.alpha = alpha;
     t.delta = delta;
-    // P chunks of L unknowns, each but the last followed by one separator unknown; the
+    t.wc = wc;
+    // P <= 32 chunks of L unknowns, each but the last followed by one separator unknown; the
     // last chunk holds the remaining 1..L unknowns (the line never ends on a separator)
-    t.L = std::max(1, (N - (LINE_MAX_CHUNKS - 1) + LINE_MAX_CHUNKS - 1) / LINE_MAX_CHUNKS);
-    for (;; ++t.L) {
-        t.P = (N + 1 + t.L) / (t.L + 1);  // ceil((N + 1) / (L + 1))
-        t.Ll = N - (t.P - 1) * (t.L + 1);
-        if (t.Ll >= 1) break;
+    if (N <= LINE_MIN_CHUNK) {
+        t.L = t.Ll = N;
+        t.P = 1;
+    } else {
+        t.L = std::max(LINE_MIN_CHUNK, (N - (LINE_MAX_CHUNKS - 1) + LINE_MAX_CHUNKS - 1) / LINE_MAX_CHUNKS);
+        for (;; ++t.L) {
+            t.P = (N + 1 + t.L) / (t.L + 1);  // ceil((N + 1) / (L + 1))
+            t.Ll = N - (t.P - 1) * (t.L + 1);
+            if (t.Ll >= 1) break;
+        }
     }
     if (t.Ll > t.L || t.P > LINE_MAX_CHUNKS) fail(LAP_ECUDA, "internal: bad line partition");
     t.stride = (t.L + 1) | 1;
@@ -193,13 +199,17 @@ const LineTables& line_tables(lap_handle h, int N, double alpha, double delta)
     t.levels = 0;
     for (int s = 1; s < S; s <<= 1) ++t.levels;
 
-    std::vector<double> inv_den(L), cpos(L);
+    std::vector<double> e(L), inv_den(L), sc(L + 1), F(L, 0.0);
     double den = delta;
-    for (int o = 0; o < L; ++o) {
-        if (o) den = delta - alpha * alpha / den;
-        inv_den[o] = 1.0 / den;
-        cpos[o] = alpha / den;
+    for (int q = 0; q < L; ++q) {
+        if (q) den = delta - alpha * alpha / den;
+        inv_den[q] = 1.0 / den;
+        e[q] = alpha / den;
+        sc[q] = wc / den;
     }
+    sc[L] = wc;
+    F[0] = alpha;
+    for (int q = 1; q < L; ++q) F[q] = F[q - 1] * e[q - 1];
     auto influence = [&](int len, bool left) {
         std::vector<double> rhs(len, 0.0);
         rhs[left ? 0 : len - 1] = alpha;
@@ -209,8 +219,24 @@ const LineTables& line_tables(lap_handle h, int N, double alpha, double delta)
     };
     std::vector<double> gL = influence(L, true), gR = influence(L, false);
     std::vector<double> gLl = influence(t.Ll, true), gRl = influence(t.Ll, false);
+    std::vector<double> gln(L), glnl(L);
+    for (int q = 0; q < L; ++q) {
+        gln[q] = gL[q] / alpha;  // (T^-1)_{q0} = (T^-1)_{0q}: T is symmetric
+        glnl[q] = gLl[q] / alpha;
+    }
+    // the boundary layer: from K0 on, F and the first inverse rows are below 2^-64 of their
+    // first entries and their terms are left out
+    auto big = [](double v, double ref) { return std::fabs(v) > std::ldexp(std::fabs(ref), -64); };
+    t.K0 = 1;
+    for (int q = L - 1; q >= 1; --q)
+        if (big(F[q], F[0]) || big(gln[q], gln[0]) || (q < t.Ll && big(glnl[q], glnl[0]))) {
+            t.K0 = q + 1;
+            break;
+        }
 
-    // separator system a x_{p-1} + b x_p + c x_{p+1} = rho_p, p = 0..S-1 (see line_kernels.cu)
+    // separator system a x_{p-1} + b x_p + c x_{p+1} = rho_p, p = 0..S-1: the chunk left of
+    // separator p ends in y_last + x_{p-1} gL[L-1] + x_p gR[L-1], the chunk right of it starts in
+    // y_first + x_p gL'[0] + x_{p+1} gR'[0] (the last chunk's vectors for p = S - 1)
     std::vector<double> a(S), b(S), c(S);
     for (int p = 0; p < S; ++p) {
         const bool right_last = p + 1 == t.P - 1;
@@ -218,7 +244,8 @@ const LineTables& line_tables(lap_handle h, int N, double alpha, double delta)
         b[p] = delta - alpha * gR[L - 1] - alpha * (right_last ? gLl[0] : gL[0]);
         c[p] = p + 1 <= S - 1 ? -alpha * gR[0] : 0.0;
     }
-    std::vector<double> k1((size_t)t.levels * S), k2((size_t)t.levels * S), invb(S);
+    // parallel cyclic reduction, one lane per separator: tables indexed [level * 32 + lane]
+    std::vector<double> k1((size_t)std::max(1, t.levels) * 32, 0.0), k2(k1.size(), 0.0), invb(32, 0.0);
     for (int lev = 0, s = 1; lev < t.levels; ++lev, s <<= 1) {
         std::vector<double> na(S), nb(S), nc(S);
         for (int p = 0; p < S; ++p) {
@@ -227,8 +254,8 @@ const LineTables& line_tables(lap_handle h, int N, double alpha, double delta)
             na[p] = p - s >= 0 ? al * a[p - s] : 0.0;
             nc[p] = p + s < S ? ga * c[p + s] : 0.0;
             nb[p] = b[p] + (p - s >= 0 ? al * c[p - s] : 0.0) + (p + s < S ? ga * a[p + s] : 0.0);
-            k1[(size_t)lev * S + p] = al;
-            k2[(size_t)lev * S + p] = ga;
+            k1[(size_t)lev * 32 + p] = al;
+            k2[(size_t)lev * 32 + p] = ga;
         }
         a.swap(na);
         b.swap(nb);
@@ -242,70 +269,85 @@ const LineTables& line_tables(lap_handle h, int N, double alpha, double delta)
         blob.insert(blob.end(), v.begin(), v.end());
         return at;
     };
-    size_t o_inv = put(inv_den), o_cp = put(cpos), o_gl = put(gL), o_gr = put(gR), o_gll = put(gLl),
-           o_grl = put(gRl), o_k1 = put(k1), o_k2 = put(k2), o_ib = put(invb);
-    LineEntry e;
-    e.bytes = std::max<size_t>(blob.size(), 1) * sizeof(double);
-    e.dev = (double*)dev_alloc(h, e.bytes);
-    ck(cudaMemcpy(e.dev, blob.data(), blob.size() * sizeof(double), cudaMemcpyHostToDevice),
-       "upload line tables");
-    t.inv_den = e.dev + o_inv;
-    t.cpos = e.dev + o_cp;
-    t.gL = e.dev + o_gl;
-    t.gR = e.dev + o_gr;
-    t.gLl = e.dev + o_gll;
-    t.gRl = e.dev + o_grl;
-    t.k1 = e.dev + o_k1;
-    t.k2 = e.dev + o_k2;
-    t.invb = e.dev + o_ib;
-    e.t = t;
-    return h->lines.emplace(key, e).first->second.t;
+    const size_t o_e = put(e), o_id = put(inv_den), o_sc = put(sc), o_F = put(F), o_gl = put(gln),
+                 o_gll = put(glnl), o_k1 = put(k1), o_k2 = put(k2), o_ib = put(invb);
+    LineEntry en;
+    en.bytes = blob.size() * sizeof(double);
+    en.dev = (double*)dev_alloc(h, en.bytes);
+    ck(cudaMemcpy(en.dev, blob.data(), en.bytes, cudaMemcpyHostToDevice), "upload line tables");
+    t.e = en.dev + o_e;
+    t.inv_den = en.dev + o_id;
+    t.sc = en.dev + o_sc;
+    t.F = en.dev + o_F;
+    t.gln = en.dev + o_gl;
+    t.glnl = en.dev + o_gll;
+    t.k1 = en.dev + o_k1;
+    t.k2 = en.dev + o_k2;
+    t.invb = en.dev + o_ib;
+    en.t = t;
+    return h->lines.emplace(key, en).first->second.t;
 }
 
-// One zebra half-sweep in `direction` (0: x-lines = rows, 1: y-lines = columns).
-// Row pitch of the transposed copy of an m x n field (its m rows hold the n-long columns).
-int64_t transposed_pitch(const Field& f) { return round_up(f.n, 32); }
+// Row pitch (in lines) of the y-line scratch: the lines of the larger zebra colour, rounded up.
+int64_t line_y_pitch(const Field& f) { return round_up((int64_t)(f.m - 2 + 1) / 2, 32); }
 
-// The transposed-copy buffer for fields of this shape (allocated outside graph capture).
-double* transposed_scratch(lap_handle h, const Field& f)
+// The y-line scratch for tables t (grown on demand, outside graph capture: growing drops the
+// handle's graphs, which hold the old buffer).
+double* line_scratch(lap_handle h, const LineTables& t, int64_t gp)
 {
-    const size_t bytes = (size_t)f.m * (size_t)transposed_pitch(f) * sizeof(double);
-    if (bytes > h->tscratch_bytes) {
-        dev_free(h, h->tscratch, h->tscratch_bytes);
-        h->tscratch = nullptr;
-        h->tscratch_bytes = 0;
-        h->tscratch = (double*)dev_alloc(h, bytes);
-        h->tscratch_bytes = bytes;
+    const size_t bytes = line_y_scratch_doubles(t, gp) * sizeof(double);
+    if (bytes > h->lscratch_bytes) {
+        drop_graphs(h);
+        dev_free(h, h->lscratch, h->lscratch_bytes);
+        h->lscratch = nullptr;
+        h->lscratch_bytes = 0;
+        h->lscratch = (double*)dev_alloc(h, bytes);
+        h->lscratch_bytes = bytes;
     }
-    return h->tscratch;
+    return h->lscratch;
 }
 
-// One zebra half sweep: x-lines (direction 0) in place; y-lines (direction 1) on a
-// transposed copy, so that the line kernel reads every line contiguously (the columns of
-// a row-major field are strided by the pitch), then copied back. The line arithmetic is
-// the same either way.
-void line_half_sweep(lap_handle h, const Field& f, const Coef& c, double w, int form,
-                     int direction, cudaStream_t s)
+// Tables, per-call coefficients and (y-lines) scratch of one zebra half sweep; allocates only
+// on the first use of a shape, so calling it before a graph capture prepares the capture.
+const LineTables& line_setup(lap_handle h, const Field& f, const Coef& c, double w, int form,
+                             int direction, LineCoefs* k, double** scratch)
 {
     const bool x = direction == 0;
     const int N = x ? f.m - 2 : f.n - 2;
-    const int nlines = x ? f.n - 2 : f.m - 2;
-    const double off = x ? 1.0 : c.b2;
-    const double cross = x ? c.b2 : 1.0;
+    const double off = x ? 1.0 : c.b2;    // coefficient along the line
+    const double cross = x ? c.b2 : 1.0;  // coefficient of the neighbouring lines
     const double alpha = form == LAP_FORM_A ? off : w * off;
-    const LineTables& t = line_tables(h, N, alpha, c.d);
-    double* p = f.p;
-    int64_t sx = f.pitch;
-    if (!x) {
-        p = transposed_scratch(h, f);
-        sx = transposed_pitch(f);
-        ck(launch_transpose(f.p, f.pitch, p, sx, f.n, f.m, s), "transpose kernel");
+    k->wc = w * cross;
+    k->bnd = off / cross;
+    k->c1 = form == LAP_FORM_B ? c.d * (1.0 - w) / k->wc : 0.0;
+    k->omw = 1.0 - w;
+    const LineTables& t = line_tables(h, N, alpha, c.d, k->wc);
+    if (x) {
+        ck(prepare_line_kernels(line_smem_bytes(t)), "line kernel attributes");
+        *scratch = nullptr;
+    } else {
+        *scratch = line_scratch(h, t, line_y_pitch(f));
     }
+    return t;
+}
+
+// One zebra half sweep (odd lines, then even lines) in `direction` (0: x-lines = rows,
+// 1: y-lines = columns), form A or B.
+void line_half_sweep(lap_handle h, const Field& f, const Coef& c, double w, int form,
+                     int direction, cudaStream_t s)
+{
+    LineCoefs k;
+    double* scratch = nullptr;
+    const LineTables& t = line_setup(h, f, c, w, form, direction, &k, &scratch);
+    const int nlines = direction == 0 ? f.n - 2 : f.m - 2;
     for (int first = 1; first <= 2; ++first) {
         const int count = first == 1 ? (nlines + 1) / 2 : nlines / 2;
-        ck(launch_line_colour(p, 1, sx, first, count, t, form, cross, w, s), "line kernel");
+        if (direction == 0)
+            ck(launch_line_x(f.p, f.pitch, first, count, t, form, k, s), "x-line kernel");
+        else
+            ck(launch_line_y(f.p, f.pitch, first, count, t, form, k, scratch, line_y_pitch(f), s),
+               "y-line kernels");
     }
-    if (!x) ck(launch_transpose(p, sx, f.p, f.pitch, f.m, f.n, s), "transpose kernel");
 }
 
 // ---- coarsest-grid inverse ------------------------------------------------------------
@@ -844,14 +886,10 @@ struct Solver {
     {
         if (p->method == LAP_ADI || p->method == LAP_SLOR) {
             for (int dir = 0; dir < (p->method == LAP_ADI ? 2 : 1); ++dir) {
-                const bool x = dir == 0;
-                const double off = x ? 1.0 : c.b2;
-                const int N = x ? f.m - 2 : f.n - 2;
-                const LineTables& t =
-                    line_tables(h, N, p->line_form == LAP_FORM_A ? off : p->w * off, c.d);
-                ck(prepare_line_kernels(line_smem_bytes(t)), "line kernel attributes");
+                LineCoefs k;
+                double* scratch = nullptr;
+                line_setup(h, f, c, p->w, p->line_form, dir, &k, &scratch);
             }
-            if (p->method == LAP_ADI) transposed_scratch(h, f);
         }
         if (p->method == LAP_MG) {
             const Level& lv = w.levels.back();
@@ -874,7 +912,7 @@ struct Solver {
                                 (int64_t)w.levels.size(), p->inner_cycles,
                                 (int64_t)w.levels32.size(), tail_first, fused32, norm_sc > 0.0};
         const double dbl[] = {c.b2, c.d, c.inv_d, p->w, p->smoother_w};
-        const void* ptrs[] = {f.p, jac_cur, jac_other, w.aux, w.maxd, h->arena, h->tscratch};
+        const void* ptrs[] = {f.p, jac_cur, jac_other, w.aux, w.maxd, h->arena, h->lscratch};
         put(ints, sizeof ints);
         put(dbl, sizeof dbl);
         put(ptrs, sizeof ptrs);
@@ -1061,7 +1099,7 @@ struct Solver {
             const double pair[2] = {wv, 1.0 - wv};  // staged by the copy before it returns
             ck(cudaMemcpyAsync(w.wslot, pair, sizeof pair, cudaMemcpyHostToDevice, s), "upload w");
         }
-        if (p->method == LAP_ADI) transposed_scratch(h, f);  // before any graph capture
+        if (p->method == LAP_ADI || p->method == LAP_SLOR) prepare();  // tables, scratch: before any capture
         if (p->method == LAP_JACOBI) {
             copy_field(w.aux, f.p);  // ring + initial interior in both buffers
             jac_cur = f.p;
@@ -1277,7 +1315,7 @@ void lap_destroy(lap_handle h)
     if (h->capture) cudaStreamDestroy(h->capture);
     for (cudaEvent_t e : h->ev)
         if (e) cudaEventDestroy(e);
-    dev_free(h, h->tscratch, h->tscratch_bytes);
+    dev_free(h, h->lscratch, h->lscratch_bytes);
     dev_free(h, h->arena, h->arena_bytes);
     if (h->pinned) cudaFreeHost(h->pinned);
     delete h;

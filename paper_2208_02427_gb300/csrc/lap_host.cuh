@@ -118,7 +118,7 @@ struct lap_handle_s {
     double* arena = nullptr;
     size_t arena_bytes = 0;
     double* pinned = nullptr;  // 8 doubles of pinned host memory for results
-    std::map<std::tuple<int, double, double>, lap::LineEntry> lines;
+    std::map<std::tuple<int, double, double, double>, lap::LineEntry> lines;
     std::map<std::tuple<int, int, double>, lap::CoarseEntry> coarse;
     // CUDA graphs of whole check periods (the iterations between two stopping tests),
     // keyed by every pointer and parameter baked into them; replayed on the caller's stream
@@ -128,9 +128,10 @@ struct lap_handle_s {
     // Small-level tail sizes chosen by timing, per shape (see TailTuner)
     std::map<std::string, lap::TailTuner> tail_tuners;
     cudaEvent_t ev[2] = {nullptr, nullptr};
-    // transposed copy of a field for the y-lines of line relaxation (grown on demand)
-    double* tscratch = nullptr;
-    size_t tscratch_bytes = 0;
+    // y-line scratch of line relaxation: forward-elimination values and chunk ends (grown on
+    // demand)
+    double* lscratch = nullptr;
+    size_t lscratch_bytes = 0;
 };
 
 namespace lap {
@@ -171,10 +172,11 @@ void check_grid(const lap_grid* g);
 void check_device_ptr(lap_handle h, const void* p, const char* what, bool allow_null = false);
 void check_params(const lap_params* p);
 
-// line relaxation: cached tables of a line length and coefficients; one zebra half sweep
-const LineTables& line_tables(lap_handle h, int N, double alpha, double delta);
-int64_t transposed_pitch(const Field& f);
-double* transposed_scratch(lap_handle h, const Field& f);
+// line relaxation: cached tables of a line length and coefficients; the tables, coefficients
+// and scratch of a half sweep (allocating only on a shape's first use); one zebra half sweep
+const LineTables& line_tables(lap_handle h, int N, double alpha, double delta, double wc);
+const LineTables& line_setup(lap_handle h, const Field& f, const Coef& c, double w, int form,
+                             int direction, LineCoefs* k, double** scratch);
 void line_half_sweep(lap_handle h, const Field& f, const Coef& c, double w, int form,
                      int direction, cudaStream_t s);
 

@@ -266,41 +266,48 @@ cudaError_t launch_b_up32(const TileItem* items, int count, const BatchLevel<flo
                           const BatchLevel<double>* lv64 = nullptr);
 
 // ---- line relaxation (line_kernels.cu) --------------------------------------------
-// Constant-coefficient tridiagonal systems -alpha x_{k-1} + delta x_k - alpha x_{k+1} = r_k,
-// k = 1..N, solved by chunks (Thomas inside a chunk with zero ends), an exact solve of the
-// separator unknowns by cyclic reduction, and a fix-up with the chunk influence vectors.
-// Everything but the right-hand side is data-independent and precomputed on the host.
+// Constant-coefficient tridiagonal systems -alpha x_{k-1} + delta x_k - alpha x_{k+1} = b_k,
+// k = 1..N, cut into P <= 32 chunks of L unknowns (the last one Ll), each but the last followed
+// by one separator unknown; solved by unnormalised forward elimination per chunk, an exact
+// cyclic-reduction solve of the separators, and a scaled back substitution (line_kernels.cu).
+// Everything but the right-hand side depends only on (N, alpha, delta, w cross) and is
+// precomputed on the host.
+constexpr int LINE_MAX_CHUNKS = 32;
 struct LineTables {
     int N;       // unknowns per line
     int L;       // chunk length (full chunks)
-    int P;       // chunks; separators S = P - 1
+    int P;       // chunks (<= 32); separators S = P - 1
     int Ll;      // length of the last chunk (1..L)
-    int stride;  // shared-memory stride of a chunk (L + 1 rounded up to odd)
+    int K0;      // F, gln, glnl are below 2^-64 of their first entry from position K0 on
     int levels;  // cyclic-reduction levels over the S separators
-    double alpha, delta;
-    // device arrays (one allocation): inv_den[L], cpos[L], gL[L], gR[L], gLl[L], gRl[L],
-    // k1[levels*S], k2[levels*S], invb[S]
-    const double* inv_den;
-    const double* cpos;
-    const double* gL;
-    const double* gR;
-    const double* gLl;
-    const double* gRl;
-    const double* k1;
-    const double* k2;
-    const double* invb;
+    int stride;  // x-lines: shared-memory stride of a chunk (L + 1 rounded up to odd)
+    double alpha, delta, wc;
+    // device arrays (one allocation)
+    const double* e;        // [L] alpha / den_q (den_q the zero-end chunk's Thomas pivots)
+    const double* inv_den;  // [L] 1 / den_q
+    const double* sc;       // [L + 1] wc / den_q; wc at index L (a separator's output scale)
+    const double* F;        // [L] forward elimination of alpha e_0: F_0 = alpha, F_q = F_{q-1} e_{q-1}
+    const double* gln;      // [L] first row of the inverse of a length-L chunk matrix
+    const double* glnl;     // [L] the same for the last chunk (length Ll)
+    const double* k1;       // [levels * 32] cyclic-reduction multipliers of the lower neighbour
+    const double* k2;       // [levels * 32] ... of the upper neighbour
+    const double* invb;     // [32] 1 / reduced diagonal
+};
+// Per-call scalars of a half sweep: bnd = off / cross (the Dirichlet ends' coefficient in the
+// scaled right-hand side), c1 = d (1 - w) / (w cross) (form B), omw = 1 - w, wc = w cross.
+struct LineCoefs {
+    double bnd, c1, omw, wc;
 };
 size_t line_smem_bytes(const LineTables& t);
 cudaError_t prepare_line_kernels(size_t smem);
-int line_threads(const LineTables& t);
-// Relax every line of one zebra colour: lines first_line, first_line + 2, ... (count of
-// them). Line l's element k (0..N+1) is at psi + l * sx + k * sa; its neighbouring lines
-// at +-sx. form 0 = A (relax after), 1 = B (relaxation inside the system).
-cudaError_t launch_line_colour(double* psi, int64_t sa, int64_t sx, int first_line, int count,
-                               const LineTables& t, int form, double cross, double w,
-                               cudaStream_t s);
-// dst[c * dp + r] = src[r * sp + c] for r < rows, c < cols (coalesced tiled transpose).
-cudaError_t launch_transpose(const double* src, int64_t sp, double* dst, int64_t dp, int rows,
-                             int cols, cudaStream_t s);
+// x-lines: rows first_line, first_line + 2, ... (count of them), one CTA each.
+cudaError_t launch_line_x(double* psi, int64_t pitch, int first_line, int count,
+                          const LineTables& t, int form, const LineCoefs& k, cudaStream_t s);
+// y-lines: columns first_line, first_line + 2, ... (count of them); scratch holds
+// line_y_scratch_doubles(t, gp) doubles, gp >= count a multiple of 32.
+size_t line_y_scratch_doubles(const LineTables& t, int64_t gp);
+cudaError_t launch_line_y(double* psi, int64_t pitch, int first_line, int count,
+                          const LineTables& t, int form, const LineCoefs& k, double* scratch,
+                          int64_t gp, cudaStream_t s);
 
 }  // namespace lap

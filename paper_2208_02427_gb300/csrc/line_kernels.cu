@@ -1,21 +1,37 @@
-// line_kernels.cu -- zebra line relaxation (SLOR / ADI half-sweeps, Eqs. 8-10).
+// line_kernels.cu -- zebra line relaxation (SLOR / ADI half sweeps, Eqs. 8-10).
 //
-// Every line of one colour is an independent tridiagonal system with constant
-// coefficients, -alpha x_{k-1} + delta x_k - alpha x_{k+1} = r_k (k = 1..N, Dirichlet
-// ends moved into r_1 and r_N). One CTA solves one line:
-//   1. the right-hand side is built from the two neighbouring lines (coalesced along the
-//      line for x-lines) into shared memory, laid out chunk by chunk;
-//   2. thread p runs the Thomas algorithm over its chunk of L unknowns with zero ends:
-//      y'_o = fma(alpha, y'_{o-1}, r_o) * inv_den_o, y_o = fma(cpos_o, y_{o+1}, y'_o);
-//   3. the P-1 separator unknowns between chunks satisfy a tridiagonal system whose
-//      coefficients come from the chunk influence vectors gL, gR; it is solved exactly by
-//      parallel cyclic reduction (one thread per separator, ceil(log2(P-1)) levels);
-//   4. every chunk adds x_left gL + x_right gR (the exact superposition) and the line is
-//      relaxed (form A: psi + w (x - psi), Eq. 9) or stored (form B, Eq. 10) and written.
-// Only the right-hand side depends on the data, so inv_den, cpos, gL, gR and the
-// cyclic-reduction multipliers are computed once on the host per (N, alpha, delta).
-// Per unknown this costs 3 FP64 operations in the chunk solve and 2 in the fix-up, plus
-// 1-3 for the right-hand side and 0-2 for the relaxation.
+// Every line of one zebra colour is an independent tridiagonal system with constant
+// coefficients, -alpha x_{k-1} + delta x_k - alpha x_{k+1} = b_k (k = 1..N). The kernels solve
+// it scaled: with nb_k the sum of the two neighbouring lines' values, the right-hand side is
+//   form A (Eqs. 8-9):  b~_k = nb_k                       and  x = cross x~,
+//   form B (Eq. 10):    b~_k = fma(c1, psi_k, nb_k)       and  x = w cross x~,
+// c1 = d (1 - w) / (w cross), the Dirichlet ends adding (off / cross) psi_end to b~_1 and b~_N
+// (off, cross: the along-line and across-line coefficients, 1 and beta^2 for x-lines). The line
+// is cut into P <= 32 chunks of L unknowns (the last holds Ll), each but the last followed by
+// one separator unknown. Per chunk, with den_q the Thomas pivots of the zero-end chunk matrix
+// and e_q = alpha / den_q:
+//   forward    G_q = fma(e_{q-1}, G_{q-1}, b~_q)             (G_q = den_q y'_q, unnormalised)
+//   separators  the chunks' zero-end solutions end in y_last = G_{L-1} / den_{L-1} and start in
+//              y_first = sum_q (T^-1)_{0q} b~_q; with them the separators satisfy a small
+//              tridiagonal system, solved exactly by parallel cyclic reduction over one warp;
+//   back       Z_q = fma(e_{q+1}, Z_{q+1}, G_q + xl F_q),  Z_{L-1} = G_{L-1} + xl F_{L-1} + alpha xr
+//              (Z_q = den_q x~_q; xl, xr the separators around the chunk; F_q the forward
+//              elimination of alpha at the chunk's left end),
+//   output     form A: psi = fma(sc_q, Z_q, (1 - w) psi),  form B: psi = sc_q Z_q,
+//              sc_q = w cross / den_q (w cross for a separator).
+// (T^-1)_{0q} and F_q decay geometrically away from the chunk's left end; from the position K0
+// on, where both are below 2^-64 of their first value, their terms are left out. Per unknown
+// this is 5 FP64 operations (1 add + 0-1 fma for b~, 1 forward, 1 back, 1-2 for the output)
+// plus 2 within K0 of a chunk's start. All tables depend on the line length and coefficients
+// only and are computed once on the host.
+//
+// x-lines (rows, contiguous): one CTA per line; b~ is built into shared memory with coalesced
+// loads, one warp runs the chunk recurrences (lane = chunk) and the separator solve (lane =
+// separator, register shuffles), and the CTA writes the line back coalesced.
+// y-lines (columns, strided by the pitch): lane = line (32 adjacent lines of a colour, so every
+// row access is a contiguous 512-byte run), one thread per (line, chunk); three launches per
+// colour -- forward (G to a scratch array laid out [position][line]), separators (a warp per
+// line), back -- so that no transposed copy of the field is needed.
 #include "lap_device.cuh"
 #include "lap_internal.cuh"
 
@@ -23,134 +39,278 @@ namespace lap {
 
 namespace {
 
-template <int FORM, bool UNIT_CROSS>
-__global__ void __launch_bounds__(256)
-    line_colour_kernel(double* __restrict__ psi, int64_t sa, int64_t sx, int first_line,
-                       const LineTables t, double cross, double w, double dmw, double wcross)
+constexpr unsigned FULL = 0xffffffffu;
+constexpr int LX_THREADS = 128;  // x-lines: threads of the CTA that builds and writes a line
+constexpr int LY_WARPS = 2;      // y-lines: chunk warps per CTA of the forward and back kernels
+constexpr int LS_WARPS = 4;      // y-lines: lines (warps) per CTA of the separator kernel
+
+// Parallel cyclic reduction of the separators of one line, lane p holding separator p < S:
+// returns x~ of separator p (0 for lanes p >= S).
+__device__ __forceinline__ double separator_solve(const LineTables& t, int p, int S, double rho)
+{
+    double r = p < S ? rho : 0.0;
+    for (int lev = 0, s = 1; lev < t.levels; ++lev, s <<= 1) {
+        const double up = __shfl_up_sync(FULL, r, s);
+        const double dn = __shfl_down_sync(FULL, r, s);
+        double v = r;
+        if (p < S && p >= s) v = __fma_rn(t.k1[lev * 32 + p], up, v);
+        if (p + s < S) v = __fma_rn(t.k2[lev * 32 + p], dn, v);
+        r = v;
+    }
+    return p < S ? r * t.invb[p] : 0.0;
+}
+
+// ---- x-lines --------------------------------------------------------------------------
+template <int FORM>
+__global__ void __launch_bounds__(LX_THREADS)
+    line_x_kernel(double* __restrict__ psi, int64_t pitch, int first_line, const LineTables t,
+                  double bnd, double c1, double omw)
 {
     const FmaOps o = load_fma_ops();
-    extern __shared__ double sm[];
-    const int N = t.N, L = t.L, P = t.P, S = P - 1, Ls = t.stride;
-    double* lane = sm;              // chunk p occupies lane[p*Ls .. p*Ls + L]; slot L = separator
-    double* rho = sm + (size_t)P * Ls;  // 2*S: cyclic-reduction double buffer
-    double* base = psi + (int64_t)(first_line + 2 * (int)blockIdx.x) * sx;
-    const double alpha = in_reg(o, t.alpha);
-    cross = in_reg(o, cross);
-    w = in_reg(o, w);
-    dmw = in_reg(o, dmw);
-    wcross = in_reg(o, wcross);
+    extern __shared__ double sm[];  // chunk p at sm[p * Ls], its separator at sm[p * Ls + L]
+    const int N = t.N, L = t.L, P = t.P, Ls = t.stride, K0 = t.K0;
+    double* row = psi + (int64_t)(first_line + 2 * (int)blockIdx.x) * pitch;
+    const double* __restrict__ up = row - pitch;
+    const double* __restrict__ dn = row + pitch;
+    c1 = in_reg(o, c1);
+    omw = in_reg(o, omw);
 
-    // 1. right-hand side; the Dirichlet ends' terms are added after the loop by the threads
-    //    that wrote those entries (the same fma, applied last, as written per point: a test
-    //    per point would let the compiler issue both fmas for every point)
-    for (int k = 1 + threadIdx.x; k <= N; k += blockDim.x) {
-        const int64_t at = (int64_t)k * sa;
-        const double nb = fadd(o, base[at - sx], base[at + sx]);
-        double r;
-        if (FORM == 0)
-            r = UNIT_CROSS ? nb : fmul(o, cross, nb);
-        else
-            r = __fma_rn(dmw, base[at], fmul(o, wcross, nb));
+    // 1. b~ in chunk layout
+#pragma unroll 4
+    for (int k = 1 + threadIdx.x; k <= N; k += LX_THREADS) {
+        const double nb = fadd(o, up[k], dn[k]);
+        const double b = FORM == 1 ? __fma_rn(c1, row[k], nb) : nb;
         const int g = k - 1, p = g / (L + 1);
-        lane[p * Ls + (g - p * (L + 1))] = r;
+        sm[p * Ls + (g - p * (L + 1))] = b;
     }
-    if (threadIdx.x == 0) lane[0] = __fma_rn(alpha, base[0], lane[0]);  // k = 1: chunk 0, slot 0
-    if (threadIdx.x == (N - 1) % blockDim.x) {  // k = N, written by this thread
+    // the Dirichlet ends, added by the threads that wrote those entries
+    if (threadIdx.x == 0) sm[0] = __fma_rn(bnd, row[0], sm[0]);
+    if (threadIdx.x == (N - 1) % LX_THREADS) {
         const int g = N - 1, p = g / (L + 1);
-        double* e = lane + p * Ls + (g - p * (L + 1));
-        *e = __fma_rn(alpha, base[(int64_t)(N + 1) * sa], *e);
+        double* e = sm + p * Ls + (g - p * (L + 1));
+        *e = __fma_rn(bnd, row[N + 1], *e);
     }
     __syncthreads();
 
-    // 2. Thomas inside each chunk, zero ends
-    const int p = threadIdx.x;
-    if (p < P) {
+    // 2. one warp: chunk recurrences (lane = chunk) and the separators (lane = separator)
+    if (threadIdx.x < 32) {
+        const int p = threadIdx.x, S = P - 1;
+        const bool act = p < P;
         const int len = p == P - 1 ? t.Ll : L;
-        double* y = lane + p * Ls;
-        double prev = 0.0;
-        for (int q = 0; q < len; ++q) {
-            prev = fmul(o, __fma_rn(alpha, prev, y[q]), t.inv_den[q]);
-            y[q] = prev;
+        double* y = sm + p * Ls;
+        const double* __restrict__ gl = p == P - 1 ? t.glnl : t.gln;
+        const double alpha = in_reg(o, t.alpha);
+        double G = 0.0, D = 0.0;
+        if (act) {
+            const int kb = min(len, K0);
+            G = y[0];
+            D = fmul(o, gl[0], G);
+            int q = 1;
+            for (; q < kb; ++q) {
+                const double b = y[q];
+                D = __fma_rn(gl[q], b, D);
+                G = __fma_rn(t.e[q - 1], G, b);
+                y[q] = G;
+            }
+#pragma unroll 4
+            for (; q < len; ++q) {
+                G = __fma_rn(t.e[q - 1], G, y[q]);
+                y[q] = G;
+            }
         }
-        for (int q = len - 2; q >= 0; --q) {
-            prev = __fma_rn(t.cpos[q], prev, y[q]);
-            y[q] = prev;
+        const double ylast = act ? fmul(o, t.inv_den[len - 1], G) : 0.0;
+        const double yfirst_next = __shfl_down_sync(FULL, D, 1);
+        double rho = 0.0;
+        if (p < S) rho = __fma_rn(alpha, fadd(o, ylast, yfirst_next), y[L]);
+        const double xs = separator_solve(t, p, S, rho);
+        const double xl_ = __shfl_up_sync(FULL, xs, 1);
+        if (act) {
+            const double xl = p > 0 ? xl_ : 0.0;
+            const double xr = p < S ? xs : 0.0;
+            int q = len - 1;
+            double Gq = y[q];
+            if (q < K0) Gq = __fma_rn(xl, t.F[q], Gq);
+            double Z = __fma_rn(alpha, xr, Gq);
+            y[q] = Z;
+            --q;
+#pragma unroll 4
+            for (; q >= K0; --q) {
+                Z = __fma_rn(t.e[q + 1], Z, y[q]);
+                y[q] = Z;
+            }
+            for (; q >= 0; --q) {
+                Z = __fma_rn(t.e[q + 1], Z, __fma_rn(xl, t.F[q], y[q]));
+                y[q] = Z;
+            }
+            if (p < S) y[L] = xs;
         }
     }
     __syncthreads();
 
-    // 3. separators: rho_p = r_sep + alpha (y_last(chunk p) + y_first(chunk p+1))
+    // 3. output, coalesced
+#pragma unroll 4
+    for (int k = 1 + threadIdx.x; k <= N; k += LX_THREADS) {
+        const int g = k - 1, p = g / (L + 1), q = g - p * (L + 1);
+        const double v = sm[p * Ls + q];
+        if (FORM == 0)
+            row[k] = __fma_rn(t.sc[q], v, fmul(o, omw, row[k]));
+        else
+            row[k] = fmul(o, t.sc[q], v);
+    }
+}
+
+// ---- y-lines --------------------------------------------------------------------------
+// Thread (line l = first + 2 * (32 * blockIdx.x + lane), chunk c = LY_WARPS * blockIdx.y +
+// warp); position k of line l is row k of column l. G[(k - 1) * gp + lane index].
+template <int FORM>
+__global__ void __launch_bounds__(32 * LY_WARPS)
+    line_y_forward_kernel(const double* __restrict__ psi, int64_t pitch, int first_line, int count,
+                          const LineTables t, double bnd, double c1, double* __restrict__ G,
+                          int64_t gp, double* __restrict__ ylast, double* __restrict__ yfirst)
+{
+    const FmaOps o = load_fma_ops();
+    const int li = blockIdx.x * 32 + (threadIdx.x & 31);
+    const int c = blockIdx.y * LY_WARPS + (threadIdx.x >> 5);
+    if (li >= count || c >= t.P) return;
+    const int L = t.L, len = c == t.P - 1 ? t.Ll : L, K0 = t.K0;
+    const int k0 = 1 + c * (L + 1);
+    const double* __restrict__ col = psi + first_line + 2 * li;
+    double* __restrict__ g = G + li;
+    const double* __restrict__ gl = c == t.P - 1 ? t.glnl : t.gln;
+    c1 = in_reg(o, c1);
+
+    auto rhs = [&](int k) {
+        const double* at = col + (int64_t)k * pitch;
+        const double nb = fadd(o, at[-1], at[1]);
+        return FORM == 1 ? __fma_rn(c1, at[0], nb) : nb;
+    };
+    double b = rhs(k0);
+    if (c == 0) b = __fma_rn(bnd, col[0], b);
+    double G_ = b;
+    double D = fmul(o, gl[0], b);
+    g[(int64_t)(k0 - 1) * gp] = G_;
+    const int kb = min(len, K0);
+    int q = 1;
+    for (; q < kb; ++q) {
+        b = rhs(k0 + q);
+        D = __fma_rn(gl[q], b, D);
+        G_ = __fma_rn(t.e[q - 1], G_, b);
+        g[(int64_t)(k0 + q - 1) * gp] = G_;
+    }
+    // the bulk: right-hand sides of 8 positions loaded before they are used
+    for (; q + 8 <= len; q += 8) {
+        double bv[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) bv[u] = rhs(k0 + q + u);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            G_ = __fma_rn(t.e[q + u - 1], G_, bv[u]);
+            g[(int64_t)(k0 + q + u - 1) * gp] = G_;
+        }
+    }
+    for (; q < len; ++q) {
+        G_ = __fma_rn(t.e[q - 1], G_, rhs(k0 + q));
+        g[(int64_t)(k0 + q - 1) * gp] = G_;
+    }
+    if (c == t.P - 1) {  // the far Dirichlet end enters b~_N with coefficient 1
+        const double extra = fmul(o, bnd, col[(int64_t)(t.N + 1) * pitch]);
+        G_ = fadd(o, G_, extra);
+        g[(int64_t)(t.N - 1) * gp] = G_;
+        if (len - 1 < K0) D = __fma_rn(gl[len - 1], extra, D);
+    }
+    ylast[(int64_t)c * gp + li] = fmul(o, t.inv_den[len - 1], G_);
+    yfirst[(int64_t)c * gp + li] = D;
+}
+
+// One warp per line: lane p = separator p; writes the separators' solution xs and their
+// output values.
+template <int FORM>
+__global__ void __launch_bounds__(32 * LS_WARPS)
+    line_y_separator_kernel(double* __restrict__ psi, int64_t pitch, int first_line, int count,
+                            const LineTables t, double c1, double omw, double wc,
+                            const double* __restrict__ ylast, const double* __restrict__ yfirst,
+                            double* __restrict__ xsep, int64_t gp)
+{
+    const FmaOps o = load_fma_ops();
+    const int li = blockIdx.x * LS_WARPS + (threadIdx.x >> 5);
+    if (li >= count) return;  // warp-uniform
+    const int p = threadIdx.x & 31, S = t.P - 1;
+    double* col = psi + first_line + 2 * li;
+    double* at = col + (int64_t)((p + 1) * (t.L + 1)) * pitch;
+    double rho = 0.0, old = 0.0;
     if (p < S) {
-        const double* yl = lane + p * Ls;
-        rho[p] = __fma_rn(alpha, fadd(o, yl[L - 1], yl[Ls]), yl[L]);
+        const double nb = fadd(o, at[-1], at[1]);
+        old = at[0];
+        const double b = FORM == 1 ? __fma_rn(c1, old, nb) : nb;
+        const double yl = ylast[(int64_t)p * gp + li], yf = yfirst[(int64_t)(p + 1) * gp + li];
+        rho = __fma_rn(t.alpha, fadd(o, yl, yf), b);
     }
-    __syncthreads();
-    double* cur = rho;
-    double* nxt = rho + S;
-    for (int lev = 0, s = 1; lev < t.levels; ++lev, s <<= 1) {
-        if (p < S) {
-            double v = cur[p];
-            if (p >= s) v = __fma_rn(t.k1[lev * S + p], cur[p - s], v);
-            if (p + s < S) v = __fma_rn(t.k2[lev * S + p], cur[p + s], v);
-            nxt[p] = v;
-        }
-        __syncthreads();
-        double* tmp = cur;
-        cur = nxt;
-        nxt = tmp;
+    const double xs = separator_solve(t, p, S, rho);
+    if (p < S) {
+        xsep[(int64_t)p * gp + li] = xs;
+        at[0] = FORM == 0 ? __fma_rn(wc, xs, fmul(o, omw, old)) : fmul(o, wc, xs);
     }
-    if (p < S) cur[p] = fmul(o, cur[p], t.invb[p]);
-    __syncthreads();
+}
 
-    // 4. superpose the separator values onto each chunk
-    if (p < P) {
-        const bool last = p == P - 1;
-        const int len = last ? t.Ll : L;
-        const double* gl = last ? t.gLl : t.gL;
-        const double* gr = last ? t.gRl : t.gR;
-        double* y = lane + p * Ls;
-        if (p >= 1) {
-            const double xl = cur[p - 1];
-            for (int q = 0; q < len; ++q) y[q] = __fma_rn(xl, gl[q], y[q]);
+template <int FORM>
+__global__ void __launch_bounds__(32 * LY_WARPS)
+    line_y_back_kernel(double* __restrict__ psi, int64_t pitch, int first_line, int count,
+                       const LineTables t, double omw, const double* __restrict__ G, int64_t gp,
+                       const double* __restrict__ xsep)
+{
+    const FmaOps o = load_fma_ops();
+    const int li = blockIdx.x * 32 + (threadIdx.x & 31);
+    const int c = blockIdx.y * LY_WARPS + (threadIdx.x >> 5);
+    if (li >= count || c >= t.P) return;
+    const int L = t.L, len = c == t.P - 1 ? t.Ll : L, K0 = t.K0, S = t.P - 1;
+    const int k0 = 1 + c * (L + 1);
+    double* __restrict__ col = psi + first_line + 2 * li;
+    const double* __restrict__ g = G + li;
+    const double xl = c > 0 ? xsep[(int64_t)(c - 1) * gp + li] : 0.0;
+    const double xr = c < S ? xsep[(int64_t)c * gp + li] : 0.0;
+    omw = in_reg(o, omw);
+
+    auto out = [&](int q, double Z) {
+        double* at = col + (int64_t)(k0 + q) * pitch;
+        *at = FORM == 0 ? __fma_rn(t.sc[q], Z, fmul(o, omw, *at)) : fmul(o, t.sc[q], Z);
+    };
+    int q = len - 1;
+    double Gq = g[(int64_t)(k0 + q - 1) * gp];
+    if (q < K0) Gq = __fma_rn(xl, t.F[q], Gq);
+    double Z = __fma_rn(t.alpha, xr, Gq);
+    out(q, Z);
+    --q;
+    // the bulk: G and the old values of 8 positions loaded before they are used
+    for (; q - 7 >= K0; q -= 8) {
+        double gv[8], ov[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            gv[u] = g[(int64_t)(k0 + q - u - 1) * gp];
+            ov[u] = FORM == 0 ? col[(int64_t)(k0 + q - u) * pitch] : 0.0;
         }
-        if (p < S) {
-            const double xr = cur[p];
-            for (int q = 0; q < len; ++q) y[q] = __fma_rn(xr, gr[q], y[q]);
-            y[L] = xr;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            Z = __fma_rn(t.e[q - u + 1], Z, gv[u]);
+            double* at = col + (int64_t)(k0 + q - u) * pitch;
+            *at = FORM == 0 ? __fma_rn(t.sc[q - u], Z, fmul(o, omw, ov[u])) : fmul(o, t.sc[q - u], Z);
         }
     }
-    __syncthreads();
-
-    // 5. relax and write back
-    for (int k = 1 + threadIdx.x; k <= N; k += blockDim.x) {
-        const int g = k - 1, c = g / (L + 1);
-        const double x = lane[c * Ls + (g - c * (L + 1))];
-        double* dst = base + (int64_t)k * sa;
-        if (FORM == 0) {
-            const double old = *dst;
-            *dst = __fma_rn(w, fadd(o, x, -old), old);
-        } else {
-            *dst = x;
-        }
+    for (; q >= K0; --q) {
+        Z = __fma_rn(t.e[q + 1], Z, g[(int64_t)(k0 + q - 1) * gp]);
+        out(q, Z);
+    }
+    for (; q >= 0; --q) {
+        Z = __fma_rn(t.e[q + 1], Z, __fma_rn(xl, t.F[q], g[(int64_t)(k0 + q - 1) * gp]));
+        out(q, Z);
     }
 }
 
 }  // namespace
 
-size_t line_smem_bytes(const LineTables& t)
-{
-    return sizeof(double) * ((size_t)t.P * t.stride + 2 * (size_t)(t.P > 1 ? t.P - 1 : 0));
-}
+size_t line_smem_bytes(const LineTables& t) { return sizeof(double) * (size_t)t.P * t.stride; }
 
-int line_threads(const LineTables& t)
-{
-    int th = ((t.P + 31) / 32) * 32;
-    return th < 64 ? 64 : th;
-}
-
-// Raise the dynamic shared-memory limit of every line-kernel instantiation to `smem`
-// on the current device (done outside stream capture; launches below only repeat it when a
-// larger line comes).
+// Raise the dynamic shared-memory limit of the x-line kernels to `smem` on the current device
+// (done outside stream capture; later launches only repeat it when a longer line comes).
 static std::atomic<size_t> g_line_smem_set[ATTR_DEVICES];
 
 cudaError_t prepare_line_kernels(size_t smem)
@@ -158,77 +318,71 @@ cudaError_t prepare_line_kernels(size_t smem)
     const int dev = attr_slot();
     if (smem <= 48 * 1024 || (dev >= 0 && smem <= g_line_smem_set[dev].load()))
         return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(line_colour_kernel<0, true>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(line_x_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(line_colour_kernel<0, false>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(line_colour_kernel<1, false>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = cudaFuncSetAttribute(line_x_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
     if (e == cudaSuccess) attr_record(g_line_smem_set, dev, smem);
     return e;
 }
 
-namespace {
-
-// dst[c][r] = src[r][c] for r < rows, c < cols: 32x32 tiles through shared memory (one
-// column of padding), reads and writes coalesced along rows.
-constexpr int TT = 32, TR = 8;
-__global__ void __launch_bounds__(TT* TR)
-    transpose_kernel(const double* __restrict__ src, int64_t sp, double* __restrict__ dst,
-                     int64_t dp, int rows, int cols)
+cudaError_t launch_line_x(double* psi, int64_t pitch, int first_line, int count,
+                          const LineTables& t, int form, const LineCoefs& k, cudaStream_t s)
 {
-    __shared__ double tile[TT][TT + 1];
-    const int c0 = blockIdx.x * TT, r0 = blockIdx.y * TT;
-    for (int k = threadIdx.y; k < TT; k += TR) {
-        const int r = r0 + k, c = c0 + threadIdx.x;
-        if (r < rows && c < cols) tile[k][threadIdx.x] = src[(int64_t)r * sp + c];
-    }
-    __syncthreads();
-    for (int k = threadIdx.y; k < TT; k += TR) {
-        const int c = c0 + k, r = r0 + threadIdx.x;
-        if (r < rows && c < cols) dst[(int64_t)c * dp + r] = tile[threadIdx.x][k];
-    }
-}
-
-}  // namespace
-
-cudaError_t launch_transpose(const double* src, int64_t sp, double* dst, int64_t dp, int rows,
-                             int cols, cudaStream_t s)
-{
-    const dim3 grid((cols + TT - 1) / TT, (rows + TT - 1) / TT), block(TT, TR);
-    transpose_kernel<<<grid, block, 0, s>>>(src, sp, dst, dp, rows, cols);
+    if (count <= 0) return cudaSuccess;
+    const size_t smem = line_smem_bytes(t);
+    cudaError_t err = prepare_line_kernels(smem);
+    if (err != cudaSuccess) return err;
+    if (form == 0)
+        line_x_kernel<0><<<count, LX_THREADS, smem, s>>>(psi, pitch, first_line, t, k.bnd, k.c1, k.omw);
+    else
+        line_x_kernel<1><<<count, LX_THREADS, smem, s>>>(psi, pitch, first_line, t, k.bnd, k.c1, k.omw);
     note_launch();
     return cudaGetLastError();
 }
 
-cudaError_t launch_line_colour(double* psi, int64_t sa, int64_t sx, int first_line, int count,
-                               const LineTables& t, int form, double cross, double w,
-                               cudaStream_t s)
+size_t line_y_scratch_doubles(const LineTables& t, int64_t gp)
+{
+    return (size_t)gp * ((size_t)t.N + 3 * (size_t)t.P);
+}
+
+cudaError_t launch_line_y(double* psi, int64_t pitch, int first_line, int count,
+                          const LineTables& t, int form, const LineCoefs& k, double* scratch,
+                          int64_t gp, cudaStream_t s)
 {
     if (count <= 0) return cudaSuccess;
-    const size_t smem = line_smem_bytes(t);
-    const int threads = line_threads(t);
-    const double d = t.delta;
-    const double dmw = d * (1.0 - w), wcross = w * cross;
-    const bool unit = cross == 1.0;
-    cudaError_t err = cudaSuccess;
-#define LAP_LINE(F, U)                                                                          \
-    do {                                                                                        \
-        auto kern = line_colour_kernel<F, U>;                                                   \
-        err = prepare_line_kernels(smem);                                                       \
-        if (err == cudaSuccess)                                                                 \
-            kern<<<count, threads, smem, s>>>(psi, sa, sx, first_line, t, cross, w, dmw, wcross); \
-    } while (0)
+    double* G = scratch;
+    double* yl = G + (size_t)gp * t.N;
+    double* yf = yl + (size_t)gp * t.P;
+    double* xs = yf + (size_t)gp * t.P;
+    const dim3 grid((count + 31) / 32, (t.P + LY_WARPS - 1) / LY_WARPS);
+    const dim3 sgrid((count + LS_WARPS - 1) / LS_WARPS);
     if (form == 0) {
-        if (unit) LAP_LINE(0, true); else LAP_LINE(0, false);
+        line_y_forward_kernel<0><<<grid, 32 * LY_WARPS, 0, s>>>(psi, pitch, first_line, count, t, k.bnd,
+                                                               k.c1, G, gp, yl, yf);
+        note_launch();
+        if (t.P > 1) {
+            line_y_separator_kernel<0><<<sgrid, 32 * LS_WARPS, 0, s>>>(psi, pitch, first_line, count, t,
+                                                                       k.c1, k.omw, k.wc, yl, yf, xs, gp);
+            note_launch();
+        }
+        line_y_back_kernel<0><<<grid, 32 * LY_WARPS, 0, s>>>(psi, pitch, first_line, count, t, k.omw, G,
+                                                            gp, xs);
+        note_launch();
     } else {
-        LAP_LINE(1, false);
+        line_y_forward_kernel<1><<<grid, 32 * LY_WARPS, 0, s>>>(psi, pitch, first_line, count, t, k.bnd,
+                                                               k.c1, G, gp, yl, yf);
+        note_launch();
+        if (t.P > 1) {
+            line_y_separator_kernel<1><<<sgrid, 32 * LS_WARPS, 0, s>>>(psi, pitch, first_line, count, t,
+                                                                       k.c1, k.omw, k.wc, yl, yf, xs, gp);
+            note_launch();
+        }
+        line_y_back_kernel<1><<<grid, 32 * LY_WARPS, 0, s>>>(psi, pitch, first_line, count, t, k.omw, G,
+                                                            gp, xs);
+        note_launch();
     }
-#undef LAP_LINE
-    note_launch();
-    if (err != cudaSuccess) return err;
     return cudaGetLastError();
 }
 

@@ -159,7 +159,8 @@ def test_coarsest_solve(lap, b, shape, beta):
     assert relerr(host(t), ora.coarse_direct(u, beta, q)) <= 1e-13
 
 
-LINE_SHAPES = [(3, 3), (25, 17), (300, 41), (41, 300), (1003, 7), (7, 1003), (4097, 5)]
+LINE_SHAPES = [(3, 3), (25, 17), (300, 41), (41, 300), (1003, 7), (7, 1003), (4097, 5), (5, 4097),
+               (1025, 385), (36, 20), (20, 36)]
 
 
 @pytest.mark.parametrize("shape", LINE_SHAPES)
@@ -175,6 +176,37 @@ def test_line_sweep(lap, b, shape, direction, form, w):
     want = ora.line_sweep(psi, w, direction, beta, ora.FORM_A if form == "A" else ora.FORM_B,
                           ora.LINES_ZEBRA)
     assert relerr(host(t), want) <= 1e-13
+
+
+@pytest.mark.parametrize("shape", [(130, 97), (97, 130), (33, 2049)])
+@pytest.mark.parametrize("direction", [0, 1])
+@pytest.mark.parametrize("form,w", [("A", 1.95), ("B", 1.95), ("B", 1.6)])
+@pytest.mark.parametrize("beta", [0.3, 3.0])
+def test_line_sweep_extreme_coefficients(lap, b, shape, direction, form, w, beta):
+    """Relaxation near 2 (form B: the line matrix close to singular, so its chunk influence
+    vectors barely decay) and strongly anisotropic grids (beta^2 = 0.09 and 9 along and across
+    the lines)."""
+    m, n = shape
+    psi = rand_field(m, n, 31)
+    t = b.to_field(psi)
+    lap.line_sweep(t, w, form, direction, beta, 1.0)
+    want = ora.line_sweep(psi, w, direction, beta, ora.FORM_A if form == "A" else ora.FORM_B,
+                          ora.LINES_ZEBRA)
+    assert relerr(host(t), want) <= REL
+
+
+def test_line_sweeps_reuse_scratch_across_shapes(lap, b):
+    """y-line sweeps of different shapes in a row (the handle's scratch grows, and is reused
+    by a smaller shape) give the same values as on a fresh handle."""
+    for shape in ((65, 1025), (1025, 65), (33, 33), (65, 1025)):
+        psi = rand_field(*shape, 32)
+        t = b.to_field(psi)
+        lap.line_sweep(t, 1.3, "A", 1, 1.0, 1.0)
+        fresh = b.Laplace()
+        u = b.to_field(psi)
+        fresh.line_sweep(u, 1.3, "A", 1, 1.0, 1.0)
+        fresh.close()
+        assert np.array_equal(host(t), host(u)), shape
 
 
 # ---- whole solves -------------------------------------------------------------------
