@@ -289,7 +289,11 @@ const LineTables& line_tables(lap_handle h, int N, double alpha, double delta, d
 }
 
 // Row pitch (in lines) of the y-line scratch: the lines of the larger zebra colour, rounded up.
-int64_t line_y_pitch(const Field& f) { return round_up((int64_t)(f.m - 2 + 1) / 2, 32); }
+int64_t line_scratch_pitch(const Field& f, int direction)
+{
+    const int nlines = direction == 0 ? f.n - 2 : f.m - 2;
+    return round_up((int64_t)(nlines + 1) / 2, 32);
+}
 
 // The y-line scratch for tables t (grown on demand, outside graph capture: growing drops the
 // handle's graphs, which hold the old buffer).
@@ -326,7 +330,7 @@ const LineTables& line_setup(lap_handle h, const Field& f, const Coef& c, double
         ck(prepare_line_kernels(line_smem_bytes(t)), "line kernel attributes");
         *scratch = nullptr;
     } else {
-        *scratch = line_scratch(h, t, line_y_pitch(f));
+        *scratch = line_scratch(h, t, line_scratch_pitch(f, direction));
     }
     return t;
 }
@@ -340,12 +344,13 @@ void line_half_sweep(lap_handle h, const Field& f, const Coef& c, double w, int 
     double* scratch = nullptr;
     const LineTables& t = line_setup(h, f, c, w, form, direction, &k, &scratch);
     const int nlines = direction == 0 ? f.n - 2 : f.m - 2;
+    const int64_t gp = line_scratch_pitch(f, direction);
     for (int first = 1; first <= 2; ++first) {
         const int count = first == 1 ? (nlines + 1) / 2 : nlines / 2;
         if (direction == 0)
             ck(launch_line_x(f.p, f.pitch, first, count, t, form, k, s), "x-line kernel");
         else
-            ck(launch_line_y(f.p, f.pitch, first, count, t, form, k, scratch, line_y_pitch(f), s),
+            ck(launch_line_scratch(f.p, f.pitch, 1, first, count, t, form, k, scratch, gp, s),
                "y-line kernels");
     }
 }

@@ -303,11 +303,13 @@ cudaError_t prepare_line_kernels(size_t smem);
 // x-lines: rows first_line, first_line + 2, ... (count of them), one CTA each.
 cudaError_t launch_line_x(double* psi, int64_t pitch, int first_line, int count,
                           const LineTables& t, int form, const LineCoefs& k, cudaStream_t s);
-// y-lines: columns first_line, first_line + 2, ... (count of them); scratch holds
-// line_y_scratch_doubles(t, gp) doubles, gp >= count a multiple of 32.
+// Lines first_line, first_line + 2, ... (count of them) through a scratch array, one thread
+// per (line, chunk): element k of line l at psi + l * sx + k * sa (y-lines: sa = pitch,
+// sx = 1; x-lines: sa = 1, sx = pitch). scratch holds line_y_scratch_doubles(t, gp)
+// doubles, gp >= count a multiple of 32.
 size_t line_y_scratch_doubles(const LineTables& t, int64_t gp);
-cudaError_t launch_line_y(double* psi, int64_t pitch, int first_line, int count,
-                          const LineTables& t, int form, const LineCoefs& k, double* scratch,
-                          int64_t gp, cudaStream_t s);
+cudaError_t launch_line_scratch(double* psi, int64_t sa, int64_t sx, int first_line, int count,
+                                const LineTables& t, int form, const LineCoefs& k, double* scratch,
+                                int64_t gp, cudaStream_t s);
 
 }  // namespace lap

@@ -27,11 +27,16 @@
 //
 // x-lines (rows, contiguous): one CTA per line; b~ is built into shared memory with coalesced
 // loads, one warp runs the chunk recurrences (lane = chunk) and the separator solve (lane =
-// separator, register shuffles), and the CTA writes the line back coalesced.
+// separator, register shuffles), and the CTA writes the line back coalesced. On GB300 each of
+// an SM's four schedulers has its own FP64 unit (0.5 fma per clock; measured), and one warp's
+// dependent fma chain alone keeps it busy, so the six line CTAs that fit an SM's shared memory
+// are enough recurrence warps; the CTA's other warps shorten the load and store phases.
 // y-lines (columns, strided by the pitch): lane = line (32 adjacent lines of a colour, so every
 // row access is a contiguous 512-byte run), one thread per (line, chunk); three launches per
 // colour -- forward (G to a scratch array laid out [position][line]), separators (a warp per
-// line), back -- so that no transposed copy of the field is needed.
+// line), back -- so that no transposed copy of the field is needed. (The same kernels serve
+// x-lines with the strides swapped, but their lanes then read 32 rows apart and ran 20-70%
+// slower than the shared-memory kernel.)
 #include "lap_device.cuh"
 #include "lap_internal.cuh"
 
@@ -40,7 +45,13 @@ namespace lap {
 namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
-constexpr int LX_THREADS = 128;  // x-lines: threads of the CTA that builds and writes a line
+// x-lines: threads of the CTA that builds and writes a line (measured at 4097^2: 128, 160,
+// 224, 256, 288, 320 threads gave 288, 285, 269, 266, 262, 255 us per form-A half sweep, the
+// form-B ones 293, 282, 258, 265, 242, 272 us), the unrolling of its load and store loops,
+// and the positions per batch of the chunk recurrences
+constexpr int LX_THREADS = 256;
+constexpr int LX_UNROLL = 8;
+constexpr int XB = 8;
 constexpr int LY_WARPS = 2;      // y-lines: chunk warps per CTA of the forward and back kernels
 constexpr int LS_WARPS = 4;      // y-lines: lines (warps) per CTA of the separator kernel
 
@@ -76,7 +87,7 @@ __global__ void __launch_bounds__(LX_THREADS)
     omw = in_reg(o, omw);
 
     // 1. b~ in chunk layout
-#pragma unroll 4
+#pragma unroll LX_UNROLL
     for (int k = 1 + threadIdx.x; k <= N; k += LX_THREADS) {
         const double nb = fadd(o, up[k], dn[k]);
         const double b = FORM == 1 ? __fma_rn(c1, row[k], nb) : nb;
@@ -112,7 +123,20 @@ __global__ void __launch_bounds__(LX_THREADS)
                 G = __fma_rn(t.e[q - 1], G, b);
                 y[q] = G;
             }
-#pragma unroll 4
+            // the bulk in batches: operands of XB positions loaded before the chain uses them
+            for (; q + XB <= len; q += XB) {
+                double bv[XB], ev[XB];
+#pragma unroll
+                for (int u = 0; u < XB; ++u) {
+                    bv[u] = y[q + u];
+                    ev[u] = t.e[q + u - 1];
+                }
+#pragma unroll
+                for (int u = 0; u < XB; ++u) {
+                    G = __fma_rn(ev[u], G, bv[u]);
+                    y[q + u] = G;
+                }
+            }
             for (; q < len; ++q) {
                 G = __fma_rn(t.e[q - 1], G, y[q]);
                 y[q] = G;
@@ -133,7 +157,19 @@ __global__ void __launch_bounds__(LX_THREADS)
             double Z = __fma_rn(alpha, xr, Gq);
             y[q] = Z;
             --q;
-#pragma unroll 4
+            for (; q - XB + 1 >= K0; q -= XB) {
+                double gv[XB], ev[XB];
+#pragma unroll
+                for (int u = 0; u < XB; ++u) {
+                    gv[u] = y[q - u];
+                    ev[u] = t.e[q - u + 1];
+                }
+#pragma unroll
+                for (int u = 0; u < XB; ++u) {
+                    Z = __fma_rn(ev[u], Z, gv[u]);
+                    y[q - u] = Z;
+                }
+            }
             for (; q >= K0; --q) {
                 Z = __fma_rn(t.e[q + 1], Z, y[q]);
                 y[q] = Z;
@@ -148,7 +184,7 @@ __global__ void __launch_bounds__(LX_THREADS)
     __syncthreads();
 
     // 3. output, coalesced
-#pragma unroll 4
+#pragma unroll LX_UNROLL
     for (int k = 1 + threadIdx.x; k <= N; k += LX_THREADS) {
         const int g = k - 1, p = g / (L + 1), q = g - p * (L + 1);
         const double v = sm[p * Ls + q];
@@ -159,14 +195,20 @@ __global__ void __launch_bounds__(LX_THREADS)
     }
 }
 
-// ---- y-lines --------------------------------------------------------------------------
+// ---- lines through a scratch array: lane = line --------------------------------------
 // Thread (line l = first + 2 * (32 * blockIdx.x + lane), chunk c = LY_WARPS * blockIdx.y +
-// warp); position k of line l is row k of column l. G[(k - 1) * gp + lane index].
+// warp); element k of line l at psi + l * sx + k * sa, its neighbouring lines at +-sx
+// (y-lines: sa = pitch, sx = 1, so a warp's 32 lines read one contiguous run of a row;
+// x-lines: sa = 1, sx = pitch). G[(k - 1) * gp + lane index], coalesced either way. The
+// loops are software-pipelined: the loads of the next PIPE positions are issued before the
+// current ones are used.
+constexpr int PIPE = 8;  // 16 was slower (registers), and L2 evict-last hints on G gained nothing
+
 template <int FORM>
 __global__ void __launch_bounds__(32 * LY_WARPS)
-    line_y_forward_kernel(const double* __restrict__ psi, int64_t pitch, int first_line, int count,
-                          const LineTables t, double bnd, double c1, double* __restrict__ G,
-                          int64_t gp, double* __restrict__ ylast, double* __restrict__ yfirst)
+    line_forward_kernel(const double* __restrict__ psi, int64_t sa, int64_t sx, int first_line,
+                        int count, const LineTables t, double bnd, double c1, double* __restrict__ G,
+                        int64_t gp, double* __restrict__ ylast, double* __restrict__ yfirst)
 {
     const FmaOps o = load_fma_ops();
     const int li = blockIdx.x * 32 + (threadIdx.x & 31);
@@ -174,48 +216,76 @@ __global__ void __launch_bounds__(32 * LY_WARPS)
     if (li >= count || c >= t.P) return;
     const int L = t.L, len = c == t.P - 1 ? t.Ll : L, K0 = t.K0;
     const int k0 = 1 + c * (L + 1);
-    const double* __restrict__ col = psi + first_line + 2 * li;
-    double* __restrict__ g = G + li;
+    const double* __restrict__ line = psi + (int64_t)(first_line + 2 * li) * sx;
+    double* __restrict__ g = G + li + (int64_t)(k0 - 1) * gp;
     const double* __restrict__ gl = c == t.P - 1 ? t.glnl : t.gln;
     c1 = in_reg(o, c1);
 
-    auto rhs = [&](int k) {
-        const double* at = col + (int64_t)k * pitch;
-        const double nb = fadd(o, at[-1], at[1]);
-        return FORM == 1 ? __fma_rn(c1, at[0], nb) : nb;
+    // right-hand side of chunk position q (loads only; the adds come with the recurrence)
+    double ra[PIPE], rb[PIPE], rc[PIPE];
+    auto load = [&](int q0, double* a, double* b_, double* cc) {
+#pragma unroll
+        for (int u = 0; u < PIPE; ++u)
+            if (q0 + u < len) {
+                const double* at = line + (int64_t)(k0 + q0 + u) * sa;
+                a[u] = at[-sx];
+                b_[u] = at[sx];
+                if (FORM == 1) cc[u] = at[0];
+            }
     };
-    double b = rhs(k0);
-    if (c == 0) b = __fma_rn(bnd, col[0], b);
-    double G_ = b;
-    double D = fmul(o, gl[0], b);
-    g[(int64_t)(k0 - 1) * gp] = G_;
-    const int kb = min(len, K0);
-    int q = 1;
-    for (; q < kb; ++q) {
-        b = rhs(k0 + q);
-        D = __fma_rn(gl[q], b, D);
-        G_ = __fma_rn(t.e[q - 1], G_, b);
-        g[(int64_t)(k0 + q - 1) * gp] = G_;
+    // position 0 (peeled: a per-step test inside the batches would issue both sides' FP64
+    // operations on every step)
+    double b0;
+    {
+        const double* at = line + (int64_t)k0 * sa;
+        b0 = fadd(o, at[-sx], at[sx]);
+        if (FORM == 1) b0 = __fma_rn(c1, at[0], b0);
+        if (c == 0) b0 = __fma_rn(bnd, line[0], b0);  // the near Dirichlet end
     }
-    // the bulk: right-hand sides of 8 positions loaded before they are used
-    for (; q + 8 <= len; q += 8) {
-        double bv[8];
+    double G_ = b0;
+    double D = fmul(o, gl[0], b0);
+    g[0] = G_;
+    // positions 1.., PIPE at a time; batches that reach into the boundary layer also carry the
+    // y_first sum, the others only the recurrence
+    auto step = [&](int q, double a_, double b_, double c_) {
+        const double nbv = fadd(o, a_, b_);
+        const double b = FORM == 1 ? __fma_rn(c1, c_, nbv) : nbv;
+        G_ = __fma_rn(t.e[q - 1], G_, b);
+        g[(int64_t)q * gp] = G_;
+        return b;
+    };
+    load(1, ra, rb, rc);
+    for (int q0 = 1; q0 < len; q0 += PIPE) {
+        double na[PIPE], nb_[PIPE], nc[PIPE];
+        if (q0 + PIPE < len) load(q0 + PIPE, na, nb_, nc);
+        if (q0 < K0) {
 #pragma unroll
-        for (int u = 0; u < 8; ++u) bv[u] = rhs(k0 + q + u);
+            for (int u = 0; u < PIPE; ++u) {
+                const int q = q0 + u;
+                if (q < len) {
+                    const double b = step(q, ra[u], rb[u], rc[u]);
+                    if (q < K0) D = __fma_rn(gl[q], b, D);
+                }
+            }
+        } else if (q0 + PIPE <= len) {
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            G_ = __fma_rn(t.e[q + u - 1], G_, bv[u]);
-            g[(int64_t)(k0 + q + u - 1) * gp] = G_;
+            for (int u = 0; u < PIPE; ++u) step(q0 + u, ra[u], rb[u], rc[u]);
+        } else {
+#pragma unroll
+            for (int u = 0; u < PIPE; ++u)
+                if (q0 + u < len) step(q0 + u, ra[u], rb[u], rc[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < PIPE; ++u) {
+            ra[u] = na[u];
+            rb[u] = nb_[u];
+            if (FORM == 1) rc[u] = nc[u];
         }
     }
-    for (; q < len; ++q) {
-        G_ = __fma_rn(t.e[q - 1], G_, rhs(k0 + q));
-        g[(int64_t)(k0 + q - 1) * gp] = G_;
-    }
     if (c == t.P - 1) {  // the far Dirichlet end enters b~_N with coefficient 1
-        const double extra = fmul(o, bnd, col[(int64_t)(t.N + 1) * pitch]);
+        const double extra = fmul(o, bnd, line[(int64_t)(t.N + 1) * sa]);
         G_ = fadd(o, G_, extra);
-        g[(int64_t)(t.N - 1) * gp] = G_;
+        g[(int64_t)(len - 1) * gp] = G_;
         if (len - 1 < K0) D = __fma_rn(gl[len - 1], extra, D);
     }
     ylast[(int64_t)c * gp + li] = fmul(o, t.inv_den[len - 1], G_);
@@ -226,20 +296,20 @@ __global__ void __launch_bounds__(32 * LY_WARPS)
 // output values.
 template <int FORM>
 __global__ void __launch_bounds__(32 * LS_WARPS)
-    line_y_separator_kernel(double* __restrict__ psi, int64_t pitch, int first_line, int count,
-                            const LineTables t, double c1, double omw, double wc,
-                            const double* __restrict__ ylast, const double* __restrict__ yfirst,
-                            double* __restrict__ xsep, int64_t gp)
+    line_separator_kernel(double* __restrict__ psi, int64_t sa, int64_t sx, int first_line, int count,
+                          const LineTables t, double c1, double omw, double wc,
+                          const double* __restrict__ ylast, const double* __restrict__ yfirst,
+                          double* __restrict__ xsep, int64_t gp)
 {
     const FmaOps o = load_fma_ops();
     const int li = blockIdx.x * LS_WARPS + (threadIdx.x >> 5);
     if (li >= count) return;  // warp-uniform
     const int p = threadIdx.x & 31, S = t.P - 1;
-    double* col = psi + first_line + 2 * li;
-    double* at = col + (int64_t)((p + 1) * (t.L + 1)) * pitch;
+    double* line = psi + (int64_t)(first_line + 2 * li) * sx;
+    double* at = line + (int64_t)((p + 1) * (t.L + 1)) * sa;
     double rho = 0.0, old = 0.0;
     if (p < S) {
-        const double nb = fadd(o, at[-1], at[1]);
+        const double nb = fadd(o, at[-sx], at[sx]);
         old = at[0];
         const double b = FORM == 1 ? __fma_rn(c1, old, nb) : nb;
         const double yl = ylast[(int64_t)p * gp + li], yf = yfirst[(int64_t)(p + 1) * gp + li];
@@ -254,9 +324,9 @@ __global__ void __launch_bounds__(32 * LS_WARPS)
 
 template <int FORM>
 __global__ void __launch_bounds__(32 * LY_WARPS)
-    line_y_back_kernel(double* __restrict__ psi, int64_t pitch, int first_line, int count,
-                       const LineTables t, double omw, const double* __restrict__ G, int64_t gp,
-                       const double* __restrict__ xsep)
+    line_back_kernel(double* __restrict__ psi, int64_t sa, int64_t sx, int first_line, int count,
+                     const LineTables t, double omw, const double* __restrict__ G, int64_t gp,
+                     const double* __restrict__ xsep)
 {
     const FmaOps o = load_fma_ops();
     const int li = blockIdx.x * 32 + (threadIdx.x & 31);
@@ -264,44 +334,64 @@ __global__ void __launch_bounds__(32 * LY_WARPS)
     if (li >= count || c >= t.P) return;
     const int L = t.L, len = c == t.P - 1 ? t.Ll : L, K0 = t.K0, S = t.P - 1;
     const int k0 = 1 + c * (L + 1);
-    double* __restrict__ col = psi + first_line + 2 * li;
-    const double* __restrict__ g = G + li;
+    double* __restrict__ line = psi + (int64_t)(first_line + 2 * li) * sx + (int64_t)k0 * sa;
+    const double* __restrict__ g = G + li + (int64_t)(k0 - 1) * gp;
     const double xl = c > 0 ? xsep[(int64_t)(c - 1) * gp + li] : 0.0;
     const double xr = c < S ? xsep[(int64_t)c * gp + li] : 0.0;
     omw = in_reg(o, omw);
+    const double alpha = in_reg(o, t.alpha);
 
-    auto out = [&](int q, double Z) {
-        double* at = col + (int64_t)(k0 + q) * pitch;
-        *at = FORM == 0 ? __fma_rn(t.sc[q], Z, fmul(o, omw, *at)) : fmul(o, t.sc[q], Z);
+    // positions run backwards: batch j holds q = top - u, u = 0..PIPE-1
+    double gv[PIPE], ov[PIPE];
+    auto load = [&](int top, double* gg, double* oo) {
+#pragma unroll
+        for (int u = 0; u < PIPE; ++u)
+            if (top - u >= 0) {
+                gg[u] = g[(int64_t)(top - u) * gp];
+                if (FORM == 0) oo[u] = line[(int64_t)(top - u) * sa];
+            }
     };
-    int q = len - 1;
-    double Gq = g[(int64_t)(k0 + q - 1) * gp];
-    if (q < K0) Gq = __fma_rn(xl, t.F[q], Gq);
-    double Z = __fma_rn(t.alpha, xr, Gq);
-    out(q, Z);
-    --q;
-    // the bulk: G and the old values of 8 positions loaded before they are used
-    for (; q - 7 >= K0; q -= 8) {
-        double gv[8], ov[8];
+    // position len - 1 (peeled), then len - 2 .. 0, PIPE at a time; batches wholly past the
+    // boundary layer skip its term
+    auto out = [&](int q, double Z, double old) {
+        double* at = line + (int64_t)q * sa;
+        *at = FORM == 0 ? __fma_rn(t.sc[q], Z, fmul(o, omw, old)) : fmul(o, t.sc[q], Z);
+    };
+    double Z;
+    {
+        const int q = len - 1;
+        double Gq = g[(int64_t)q * gp];
+        if (q < K0) Gq = __fma_rn(xl, t.F[q], Gq);
+        Z = __fma_rn(alpha, xr, Gq);
+        out(q, Z, FORM == 0 ? line[(int64_t)q * sa] : 0.0);
+    }
+    load(len - 2, gv, ov);
+    for (int top = len - 2; top >= 0; top -= PIPE) {
+        double ng[PIPE], no[PIPE];
+        if (top - PIPE >= 0) load(top - PIPE, ng, no);
+        if (top - PIPE + 1 >= K0) {
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            gv[u] = g[(int64_t)(k0 + q - u - 1) * gp];
-            ov[u] = FORM == 0 ? col[(int64_t)(k0 + q - u) * pitch] : 0.0;
+            for (int u = 0; u < PIPE; ++u) {
+                Z = __fma_rn(t.e[top - u + 1], Z, gv[u]);
+                out(top - u, Z, ov[u]);
+            }
+        } else {
+#pragma unroll
+            for (int u = 0; u < PIPE; ++u) {
+                const int q = top - u;
+                if (q >= 0) {
+                    double Gq = gv[u];
+                    if (q < K0) Gq = __fma_rn(xl, t.F[q], Gq);
+                    Z = __fma_rn(t.e[q + 1], Z, Gq);
+                    out(q, Z, ov[u]);
+                }
+            }
         }
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            Z = __fma_rn(t.e[q - u + 1], Z, gv[u]);
-            double* at = col + (int64_t)(k0 + q - u) * pitch;
-            *at = FORM == 0 ? __fma_rn(t.sc[q - u], Z, fmul(o, omw, ov[u])) : fmul(o, t.sc[q - u], Z);
+        for (int u = 0; u < PIPE; ++u) {
+            gv[u] = ng[u];
+            if (FORM == 0) ov[u] = no[u];
         }
-    }
-    for (; q >= K0; --q) {
-        Z = __fma_rn(t.e[q + 1], Z, g[(int64_t)(k0 + q - 1) * gp]);
-        out(q, Z);
-    }
-    for (; q >= 0; --q) {
-        Z = __fma_rn(t.e[q + 1], Z, __fma_rn(xl, t.F[q], g[(int64_t)(k0 + q - 1) * gp]));
-        out(q, Z);
     }
 }
 
@@ -347,9 +437,9 @@ size_t line_y_scratch_doubles(const LineTables& t, int64_t gp)
     return (size_t)gp * ((size_t)t.N + 3 * (size_t)t.P);
 }
 
-cudaError_t launch_line_y(double* psi, int64_t pitch, int first_line, int count,
-                          const LineTables& t, int form, const LineCoefs& k, double* scratch,
-                          int64_t gp, cudaStream_t s)
+cudaError_t launch_line_scratch(double* psi, int64_t sa, int64_t sx, int first_line, int count,
+                                const LineTables& t, int form, const LineCoefs& k, double* scratch,
+                                int64_t gp, cudaStream_t s)
 {
     if (count <= 0) return cudaSuccess;
     double* G = scratch;
@@ -358,31 +448,23 @@ cudaError_t launch_line_y(double* psi, int64_t pitch, int first_line, int count,
     double* xs = yf + (size_t)gp * t.P;
     const dim3 grid((count + 31) / 32, (t.P + LY_WARPS - 1) / LY_WARPS);
     const dim3 sgrid((count + LS_WARPS - 1) / LS_WARPS);
-    if (form == 0) {
-        line_y_forward_kernel<0><<<grid, 32 * LY_WARPS, 0, s>>>(psi, pitch, first_line, count, t, k.bnd,
-                                                               k.c1, G, gp, yl, yf);
-        note_launch();
-        if (t.P > 1) {
-            line_y_separator_kernel<0><<<sgrid, 32 * LS_WARPS, 0, s>>>(psi, pitch, first_line, count, t,
-                                                                       k.c1, k.omw, k.wc, yl, yf, xs, gp);
-            note_launch();
-        }
-        line_y_back_kernel<0><<<grid, 32 * LY_WARPS, 0, s>>>(psi, pitch, first_line, count, t, k.omw, G,
-                                                            gp, xs);
-        note_launch();
-    } else {
-        line_y_forward_kernel<1><<<grid, 32 * LY_WARPS, 0, s>>>(psi, pitch, first_line, count, t, k.bnd,
-                                                               k.c1, G, gp, yl, yf);
-        note_launch();
-        if (t.P > 1) {
-            line_y_separator_kernel<1><<<sgrid, 32 * LS_WARPS, 0, s>>>(psi, pitch, first_line, count, t,
-                                                                       k.c1, k.omw, k.wc, yl, yf, xs, gp);
-            note_launch();
-        }
-        line_y_back_kernel<1><<<grid, 32 * LY_WARPS, 0, s>>>(psi, pitch, first_line, count, t, k.omw, G,
-                                                            gp, xs);
-        note_launch();
-    }
+#define LAP_LINES(F)                                                                                 \
+    do {                                                                                             \
+        line_forward_kernel<F><<<grid, 32 * LY_WARPS, 0, s>>>(psi, sa, sx, first_line, count, t,      \
+                                                              k.bnd, k.c1, G, gp, yl, yf);           \
+        note_launch();                                                                               \
+        if (t.P > 1) {                                                                               \
+            line_separator_kernel<F><<<sgrid, 32 * LS_WARPS, 0, s>>>(psi, sa, sx, first_line, count,  \
+                                                                     t, k.c1, k.omw, k.wc, yl, yf,   \
+                                                                     xs, gp);                        \
+            note_launch();                                                                           \
+        }                                                                                            \
+        line_back_kernel<F><<<grid, 32 * LY_WARPS, 0, s>>>(psi, sa, sx, first_line, count, t, k.omw, \
+                                                           G, gp, xs);                               \
+        note_launch();                                                                               \
+    } while (0)
+    if (form == 0) LAP_LINES(0); else LAP_LINES(1);
+#undef LAP_LINES
     return cudaGetLastError();
 }
 
