@@ -72,40 +72,15 @@ __device__ __forceinline__ double separator_solve(const LineTables& t, int p, in
 }
 
 // ---- x-lines --------------------------------------------------------------------------
-template <int FORM>
-__global__ void __launch_bounds__(LX_THREADS)
-    line_x_kernel(double* __restrict__ psi, int64_t pitch, int first_line, const LineTables t,
-                  double bnd, double c1, double omw)
+// The recurrences of one line held in shared memory in chunk layout (chunk p at sm[p * Ls],
+// its separator at sm[p * Ls + L]), run by one warp, lane p = chunk p: b~ in, the output
+// values' Z (chunk positions) and x~ (separators) out.
+__device__ __forceinline__ void line_recurrences(const FmaOps& o, const LineTables& t,
+                                                 double* sm, int p)
 {
-    const FmaOps o = load_fma_ops();
-    extern __shared__ double sm[];  // chunk p at sm[p * Ls], its separator at sm[p * Ls + L]
-    const int N = t.N, L = t.L, P = t.P, Ls = t.stride, K0 = t.K0;
-    double* row = psi + (int64_t)(first_line + 2 * (int)blockIdx.x) * pitch;
-    const double* __restrict__ up = row - pitch;
-    const double* __restrict__ dn = row + pitch;
-    c1 = in_reg(o, c1);
-    omw = in_reg(o, omw);
-
-    // 1. b~ in chunk layout
-#pragma unroll LX_UNROLL
-    for (int k = 1 + threadIdx.x; k <= N; k += LX_THREADS) {
-        const double nb = fadd(o, up[k], dn[k]);
-        const double b = FORM == 1 ? __fma_rn(c1, row[k], nb) : nb;
-        const int g = k - 1, p = g / (L + 1);
-        sm[p * Ls + (g - p * (L + 1))] = b;
-    }
-    // the Dirichlet ends, added by the threads that wrote those entries
-    if (threadIdx.x == 0) sm[0] = __fma_rn(bnd, row[0], sm[0]);
-    if (threadIdx.x == (N - 1) % LX_THREADS) {
-        const int g = N - 1, p = g / (L + 1);
-        double* e = sm + p * Ls + (g - p * (L + 1));
-        *e = __fma_rn(bnd, row[N + 1], *e);
-    }
-    __syncthreads();
-
-    // 2. one warp: chunk recurrences (lane = chunk) and the separators (lane = separator)
-    if (threadIdx.x < 32) {
-        const int p = threadIdx.x, S = P - 1;
+    const int L = t.L, P = t.P, Ls = t.stride, K0 = t.K0;
+    {
+        const int S = P - 1;
         const bool act = p < P;
         const int len = p == P - 1 ? t.Ll : L;
         double* y = sm + p * Ls;
@@ -181,11 +156,42 @@ __global__ void __launch_bounds__(LX_THREADS)
             if (p < S) y[L] = xs;
         }
     }
-    __syncthreads();
+}
 
-    // 3. output, coalesced
+// Phase 1 of an x-line: b~ of the row into shared memory in chunk layout, by threads tid =
+// 0..nthr-1 (coalesced); each thread also adds the Dirichlet end terms of the entries it wrote.
+template <int FORM>
+__device__ __forceinline__ void line_x_load(const FmaOps& o, const LineTables& t, double* sm,
+                                            const double* row, int64_t pitch, double bnd, double c1,
+                                            int tid, int nthr)
+{
+    const int N = t.N, L = t.L, Ls = t.stride;
+    const double* __restrict__ up = row - pitch;
+    const double* __restrict__ dn = row + pitch;
 #pragma unroll LX_UNROLL
-    for (int k = 1 + threadIdx.x; k <= N; k += LX_THREADS) {
+    for (int k = 1 + tid; k <= N; k += nthr) {
+        const double nb = fadd(o, up[k], dn[k]);
+        const double b = FORM == 1 ? __fma_rn(c1, row[k], nb) : nb;
+        const int g = k - 1, p = g / (L + 1);
+        sm[p * Ls + (g - p * (L + 1))] = b;
+    }
+    if (tid == 0) sm[0] = __fma_rn(bnd, row[0], sm[0]);
+    if (tid == (N - 1) % nthr) {
+        const int g = N - 1, p = g / (L + 1);
+        double* e = sm + p * Ls + (g - p * (L + 1));
+        *e = __fma_rn(bnd, row[N + 1], *e);
+    }
+}
+
+// Phase 3 of an x-line: the output values written to the row (coalesced), by the same
+// thread-to-element mapping as line_x_load.
+template <int FORM>
+__device__ __forceinline__ void line_x_store(const FmaOps& o, const LineTables& t, const double* sm,
+                                             double* row, double omw, int tid, int nthr)
+{
+    const int N = t.N, L = t.L, Ls = t.stride;
+#pragma unroll LX_UNROLL
+    for (int k = 1 + tid; k <= N; k += nthr) {
         const int g = k - 1, p = g / (L + 1), q = g - p * (L + 1);
         const double v = sm[p * Ls + q];
         if (FORM == 0)
@@ -193,6 +199,27 @@ __global__ void __launch_bounds__(LX_THREADS)
         else
             row[k] = fmul(o, t.sc[q], v);
     }
+}
+
+// One CTA per line, the three phases separated by CTA barriers. (A persistent variant with two
+// line buffers per CTA, warp 0 running the recurrences of one line while the other warps wrote
+// back and loaded the neighbouring lines, measured no faster: the recurrences' dependent fma
+// chain shares its scheduler's FP64 unit with the other warps' independent FP64 operations.)
+template <int FORM>
+__global__ void __launch_bounds__(LX_THREADS)
+    line_x_kernel(double* __restrict__ psi, int64_t pitch, int first_line, const LineTables t,
+                  double bnd, double c1, double omw)
+{
+    const FmaOps o = load_fma_ops();
+    extern __shared__ double sm[];
+    double* row = psi + (int64_t)(first_line + 2 * (int)blockIdx.x) * pitch;
+    c1 = in_reg(o, c1);
+    omw = in_reg(o, omw);
+    line_x_load<FORM>(o, t, sm, row, pitch, bnd, c1, threadIdx.x, LX_THREADS);
+    __syncthreads();
+    if (threadIdx.x < 32) line_recurrences(o, t, sm, threadIdx.x);
+    __syncthreads();
+    line_x_store<FORM>(o, t, sm, row, omw, threadIdx.x, LX_THREADS);
 }
 
 // ---- lines through a scratch array: lane = line --------------------------------------
