@@ -157,7 +157,10 @@ int lap_solve(lap_handle h, const lap_grid* g, double* psi_dev, const lap_params
  * problem gets exactly the arithmetic of its own lap_solve (per problem the iterates are
  * the same), stops on its own (convergence is decided on the device) and reports in
  * results[k] (host). p->check_every sets how often (in cycles) the host polls for the
- * number of problems still running. Synchronises `stream` before returning. */
+ * number of problems still running. Synchronises `stream` before returning.
+ * The plan of a call (level descriptors, work lists, the captured cycle graphs) stays in the
+ * handle: a following call with the same grids, field addresses and multigrid parameters
+ * reuses it, unless another call of the handle has used its scratch memory in between. */
 int lap_solve_batched(lap_handle h, int count, const lap_grid* grids, double* const* psi_devs,
                       const lap_params* p, lap_result* results, void* stream);
 

@@ -166,6 +166,24 @@ def params(method="sor", w=1.0, tol=1e-10, norm="l2_rel", max_iter=100000, check
                   1 if unfused else 0)
 
 
+class Batch:
+    """The C-ABI descriptors of a list of fields for lap_solve_batched (grid array and pointer
+    array), marshalled once so that repeated solves of the same batch pay for it once. The
+    fields stay referenced; their sizes and storage must not change while the Batch is used.
+    dx, dy: scalars or one value per field."""
+
+    def __init__(self, fields, dx=1.0, dy=1.0):
+        self.fields = list(fields)
+        n = self.count = len(self.fields)
+        if n == 0:
+            raise ValueError("empty batch")
+        dxs = dx if hasattr(dx, "__len__") else [dx] * n
+        dys = dy if hasattr(dy, "__len__") else [dy] * n
+        self.grids = (Grid * n)(*[_grid(f, a, c) for f, a, c in zip(self.fields, dxs, dys)])
+        self.ptrs = (c_void_p * n)(*[f.data_ptr() for f in self.fields])
+        self.device = self.fields[0].device
+
+
 class Laplace:
     """A handle of the library on one CUDA device (scratch memory, cached tables)."""
 
@@ -227,16 +245,12 @@ class Laplace:
 
     def solve_batched(self, fields, dx=1.0, dy=1.0, stream=None, **kw) -> list:
         """Solve many fields (different sizes allowed) with the V-cycle in batched launches.
-        dx, dy: scalars or one value per field. Returns one result dict per field."""
-        n = len(fields)
-        dxs = dx if hasattr(dx, "__len__") else [dx] * n
-        dys = dy if hasattr(dy, "__len__") else [dy] * n
-        grids = (Grid * n)(*[_grid(f, a, c) for f, a, c in zip(fields, dxs, dys)])
-        ptrs = (c_void_p * n)(*[f.data_ptr() for f in fields])
-        res = (Result * n)()
-        dev = fields[0].device
-        _check(self._lib.lap_solve_batched(self._h, n, grids, ptrs, C.byref(params(**kw)), res,
-                                           _stream(stream, dev)))
+        fields: a list of fields (dx, dy: scalars or one value per field) or a Batch (its own
+        spacings). Returns one result dict per field."""
+        batch = fields if isinstance(fields, Batch) else Batch(fields, dx, dy)
+        res = (Result * batch.count)()
+        _check(self._lib.lap_solve_batched(self._h, batch.count, batch.grids, batch.ptrs,
+                                           C.byref(params(**kw)), res, _stream(stream, batch.device)))
         return [{"status": STATUS.get(r.status, r.status), "iters": r.iters, "r0": r.r0,
                  "r_final": r.r_final, "last_check": r.last_check} for r in res]
 

@@ -373,7 +373,7 @@ __global__ void __launch_bounds__(TAIL_THREADS)
 // descaling by 2^2e is exact, so it is done once on the block's sum (the same value as
 // descaling every thread's sum first). A thread takes two walk positions per step, both
 // points' stencils loaded before either is used; the sums keep the walk order.
-template <bool MIXED, bool UNIT>
+template <bool MIXED, bool UNIT, bool SCALED>
 __device__ __forceinline__ double sumsq_item(const BatchItem& it, const BatchLevel<double>& L,
                                              const BatchLevel<float>* __restrict__ lv32,
                                              float sc)
@@ -395,7 +395,7 @@ __device__ __forceinline__ double sumsq_item(const BatchItem& it, const BatchLev
         const double r = __fma_rn(nd, x.c, A.template nsum<UNIT>(x.w, x.e, x.s, x.n, b2));
         if (MIXED) {
             const float rf = to_float_rn(r);
-            if (sc > 0.0f) {
+            if (SCALED) {
                 const float rs = __fmul_rn(rf, sc);
                 acc32 = __fmaf_rn(rs, rs, acc32);
             } else {
@@ -423,7 +423,7 @@ __device__ __forceinline__ double sumsq_item(const BatchItem& it, const BatchLev
         point(x0, i0, j0);
         point(x1, i1, j1);
     }
-    if (MIXED && sc > 0.0f) acc = (double)acc32;
+    if (MIXED && SCALED) acc = (double)acc32;
     return acc;
 }
 
@@ -446,9 +446,15 @@ __global__ void __launch_bounds__(BT, 5)
         }
     }
     double acc = 0.0;
+    // the FP32 or the FP64 sum of squares, chosen per block (as a per-point choice the
+    // compiler would issue the FP64 fma for every point)
     on_flag(L.unit_beta != 0, [&](auto U) {
-        acc = mixed ? sumsq_item<true, decltype(U)::value>(it, L, lv32, sc)
-                    : sumsq_item<false, decltype(U)::value>(it, L, lv32, 0.0f);
+        if (!mixed)
+            acc = sumsq_item<false, decltype(U)::value, false>(it, L, lv32, 0.0f);
+        else
+            on_flag(sc > 0.0f, [&](auto SC) {
+                acc = sumsq_item<true, decltype(U)::value, decltype(SC)::value>(it, L, lv32, sc);
+            });
     });
     __shared__ double red[BT / 32];
     acc = warp_sum(acc);

@@ -80,6 +80,7 @@ void drop_graphs(lap_handle h)
 // is in flight between calls (lap_solve synchronises), so regrowing is safe.
 double* arena(lap_handle h, size_t bytes)
 {
+    ++h->arena_epoch;  // whatever was kept in the arena is overwritten from here on
     bytes = (size_t)round_up((int64_t)std::max<size_t>(bytes, 256), 1 << 20);
     if (bytes > h->arena_bytes) {
         drop_graphs(h);
@@ -1314,6 +1315,7 @@ void lap_destroy(lap_handle h)
     if (!h) return;
     cudaSetDevice(h->device);
     cudaDeviceSynchronize();
+    h->batch_cache.reset();
     for (auto& kv : h->lines) dev_free(h, kv.second.dev, kv.second.bytes);
     for (auto& kv : h->coarse) dev_free(h, kv.second.dev, kv.second.bytes);
     drop_graphs(h);

@@ -120,6 +120,200 @@ struct BatchPlan {
     int levels = 0;
 };
 
+// What a call's plan depends on: the grids (sizes, spacings, pitches), the fields' addresses
+// and the parameters that shape the lists and the captured cycle.
+struct BatchKey {
+    std::vector<lap_grid> grids;
+    std::vector<const double*> psi;
+    int32_t method, norm, nu1, nu2, coarsest_min, max_levels, inner_cycles, tail_size, unfused;
+    double smoother_w, tol;
+    bool operator==(const BatchKey& o) const
+    {
+        if (grids.size() != o.grids.size() || psi != o.psi) return false;
+        for (size_t k = 0; k < grids.size(); ++k) {
+            const lap_grid &a = grids[k], &b = o.grids[k];
+            if (a.m != b.m || a.n != b.n || a.dx != b.dx || a.dy != b.dy || a.pitch != b.pitch)
+                return false;
+        }
+        return method == o.method && norm == o.norm && nu1 == o.nu1 && nu2 == o.nu2 &&
+               coarsest_min == o.coarsest_min && max_levels == o.max_levels &&
+               inner_cycles == o.inner_cycles && tail_size == o.tail_size && unfused == o.unfused &&
+               smoother_w == o.smoother_w && tol == o.tol;
+    }
+};
+
+// A plan with its device tables in the handle's arena and the cycle graphs captured so far
+// (one per tail-size candidate). Valid while nothing else has carved the arena (epoch).
+struct BatchCache : BatchCacheBase {
+    BatchKey key;
+    BatchPlan P;
+    uint64_t epoch = 0;
+    size_t level_bytes = 0;
+    BatchLevel<double>* lv64 = nullptr;
+    BatchLevel<float>* lv32 = nullptr;
+    BatchItem* items = nullptr;
+    TailJob* jobs = nullptr;
+    TileItem* tiles = nullptr;
+    int *first = nullptr, *active = nullptr, *status = nullptr, *remaining = nullptr;
+    long long* iters = nullptr;
+    double *r0 = nullptr, *rnow = nullptr, *partials = nullptr;
+    bool fused = false;
+    std::vector<std::pair<cudaGraphExec_t, int64_t>> exec;  // graph, kernels it launches
+    ~BatchCache() override
+    {
+        for (auto& e : exec)
+            if (e.first) cudaGraphExecDestroy(e.first);
+    }
+};
+
+BatchKey make_key(int count, const lap_grid* grids, double* const* psi_devs, const lap_params* p)
+{
+    BatchKey k;
+    k.grids.assign(grids, grids + count);
+    k.psi.assign(psi_devs, psi_devs + count);
+    k.method = p->method;
+    k.norm = p->norm;
+    k.nu1 = p->nu1;
+    k.nu2 = p->nu2;
+    k.coarsest_min = p->coarsest_min;
+    k.max_levels = p->max_levels;
+    k.inner_cycles = p->inner_cycles;
+    k.tail_size = p->tail_size;
+    k.unfused = p->unfused;
+    k.smoother_w = p->smoother_w;
+    k.tol = p->tol;
+    return k;
+}
+
+// The level descriptors, the work lists of every tail-size candidate, the arena carved for
+// them and the tables uploaded (stream-ordered on s, synchronised before returning).
+std::unique_ptr<BatchCache> build_plan(lap_handle h, int count, const lap_grid* grids,
+                                       double* const* psi_devs, const lap_params* p, TailTuner& tuner,
+                                       cudaStream_t s)
+{
+    auto C = std::make_unique<BatchCache>();
+    BatchPlan& P = C->P;
+    const bool mixed = p->method == LAP_MG_MIXED;
+    P.nlev.resize(count);
+    P.base.resize(count);
+    // ---- level descriptors (buffers are carved below) ----
+    for (int q = 0; q < count; ++q) {
+        const lap_grid* g = &grids[q];
+        const int L = mg_level_count(g->m, g->n, p->coarsest_min, p->max_levels);
+        P.nlev[q] = L;
+        P.base[q] = (int)P.lv64.size();
+        P.levels = std::max(P.levels, L);
+        const Coef c = make_coef(g->dx, g->dy);
+        int m = g->m, n = g->n;
+        for (int l = 0; l < L; ++l) {
+            BatchLevel<double> d{};
+            d.m = m;
+            d.n = n;
+            d.pitch = l == 0 ? g->pitch : round_up(m, 32);
+            d.problem = q;
+            d.unit_beta = c.unit_beta;
+            d.inv_d_shift = c.inv_d_shift;
+            d.b2 = c.b2;
+            d.d = c.d;
+            d.inv_d = c.inv_d;
+            BatchLevel<float> f{};
+            f.m = m;
+            f.n = n;
+            f.pitch = round_up(m, 32);
+            f.problem = q;
+            f.unit_beta = c.unit_beta;
+            f.inv_d_shift = 0;
+            f.b2 = c.b2;
+            f.d = c.d;
+            f.inv_d = c.inv_d;
+            if (l == L - 1) {
+                if ((int64_t)(m - 2) * (n - 2) > COARSE_MAX_UNKNOWNS)
+                    fail(LAP_EUNSUPPORTED, "coarsest level with more than 1024 unknowns");
+                d.ainv_t = f.ainv_t = coarse_inverse(h, m, n, c.b2, c.d);
+                P.max_coarse_unknowns = std::max(P.max_coarse_unknowns, (m - 2) * (n - 2));
+            }
+            P.lv64.push_back(d);
+            P.lv32.push_back(f);
+            m = (m - 1) / 2 + 1;
+            n = (n - 1) / 2 + 1;
+        }
+    }
+    // ---- work lists: one set per tail-size candidate ----
+    std::vector<int> all_problems(count);
+    for (int q = 0; q < count; ++q) all_problems[q] = q;
+    C->fused = mixed && !p->unfused && fused32_supported(p->nu1, p->nu2);
+    for (int cand : tuner.cand) {
+        LevelLists L;
+        build_lists(L, P.items, P.jobs, all_problems, P.base, P.nlev, P.lv64, cand,
+                    C->fused ? &P.tiles : nullptr, p->nu1, p->nu2);
+        P.max_coarse_unknowns = std::max(P.max_coarse_unknowns, L.max_coarse);
+        P.cands.push_back(L);
+    }
+    const int n0 = (int)P.items.size();
+    for (int q = 0; q < count; ++q) {
+        P.first_item.push_back((int)P.items.size() - n0);
+        add_items(P.items, P.base[q], grids[q].m, grids[q].n);
+    }
+    P.first_item.push_back((int)P.items.size() - n0);
+    P.norm = {n0, (int)P.items.size() - n0};
+    // ---- memory: level buffers, descriptors, lists, state ----
+    auto carve_all = [&](auto& cv) {
+        for (int q = 0; q < count; ++q)
+            for (int l = 0; l < P.nlev[q]; ++l) {
+                const int k = P.base[q] + l;
+                BatchLevel<double>& d = P.lv64[k];
+                BatchLevel<float>& f = P.lv32[k];
+                const bool last = l == P.nlev[q] - 1;
+                if (!mixed) {
+                    if (l == 0) {
+                        d.u = psi_devs[q];
+                        d.q = nullptr;
+                    } else {
+                        d.u = cv.template take<double>((size_t)d.n * d.pitch);
+                        d.q = cv.template take<double>((size_t)d.n * d.pitch);
+                    }
+                    d.r = last ? nullptr : cv.template take<double>((size_t)d.n * d.pitch);
+                } else {
+                    if (l == 0) d.u = psi_devs[q];
+                    f.u = cv.template take<float>((size_t)f.n * f.pitch);
+                    f.q = cv.template take<float>((size_t)f.n * f.pitch);
+                    f.r = last ? nullptr : cv.template take<float>((size_t)f.n * f.pitch);
+                }
+            }
+        C->lv64 = cv.template take<BatchLevel<double>>(P.lv64.size());
+        C->lv32 = cv.template take<BatchLevel<float>>(P.lv32.size());
+        C->items = cv.template take<BatchItem>(P.items.size());
+        C->jobs = cv.template take<TailJob>(std::max<size_t>(1, P.jobs.size()));
+        C->tiles = cv.template take<TileItem>(std::max<size_t>(1, P.tiles.size()));
+        C->first = cv.template take<int>(P.first_item.size());
+        C->active = cv.template take<int>(count);
+        C->status = cv.template take<int>(count);
+        C->remaining = cv.template take<int>(1);
+        C->iters = cv.template take<long long>(count);
+        C->r0 = cv.template take<double>(count);
+        C->rnow = cv.template take<double>(count);
+        C->partials = cv.template take<double>(std::max(1, P.norm.second));
+    };
+    Sizer sz;
+    carve_all(sz);
+    Carver cv(arena(h, sz.off));
+    carve_all(cv);
+    C->epoch = h->arena_epoch;
+    C->level_bytes = (size_t)((char*)C->lv64 - (char*)h->arena);
+    // pageable sources: each copy is staged before it returns
+    ck(cudaMemcpyAsync(C->lv64, P.lv64.data(), P.lv64.size() * sizeof(P.lv64[0]), cudaMemcpyHostToDevice, s), "upload levels");
+    ck(cudaMemcpyAsync(C->lv32, P.lv32.data(), P.lv32.size() * sizeof(P.lv32[0]), cudaMemcpyHostToDevice, s), "upload levels");
+    ck(cudaMemcpyAsync(C->items, P.items.data(), P.items.size() * sizeof(BatchItem), cudaMemcpyHostToDevice, s), "upload items");
+    if (!P.jobs.empty())
+        ck(cudaMemcpyAsync(C->jobs, P.jobs.data(), P.jobs.size() * sizeof(TailJob), cudaMemcpyHostToDevice, s), "upload jobs");
+    if (!P.tiles.empty())
+        ck(cudaMemcpyAsync(C->tiles, P.tiles.data(), P.tiles.size() * sizeof(TileItem), cudaMemcpyHostToDevice, s), "upload tiles");
+    ck(cudaMemcpyAsync(C->first, P.first_item.data(), P.first_item.size() * sizeof(int), cudaMemcpyHostToDevice, s), "upload items");
+    C->exec.assign(P.cands.size(), {nullptr, 0});
+    C->key = make_key(count, grids, psi_devs, p);
+    return C;
+}
+
 }  // namespace
 
 extern "C" int lap_solve_batched(lap_handle h, int count, const lap_grid* grids,
@@ -134,220 +328,116 @@ extern "C" int lap_solve_batched(lap_handle h, int count, const lap_grid* grids,
             fail(LAP_EINVAL, "batched solves take LAP_MG or LAP_MG_MIXED");
         if (p->norm == LAP_NORM_MAXDELTA) fail(LAP_EINVAL, "batched solves stop on an L2 norm");
         set_device(h);
+        for (int q = 0; q < count; ++q) {
+            check_grid(&grids[q]);
+            check_device_ptr(h, psi_devs[q], "psi");
+        }
         const bool mixed = p->method == LAP_MG_MIXED;
         cudaStream_t s = (cudaStream_t)stream;
-        BatchPlan P;
-        P.nlev.resize(count);
-        P.base.resize(count);
-        // ---- level descriptors (buffers are carved below) ----
+        std::vector<int> shape;
         for (int q = 0; q < count; ++q) {
-            const lap_grid* g = &grids[q];
-            check_grid(g);
-            check_device_ptr(h, psi_devs[q], "psi");
-            const int L = mg_level_count(g->m, g->n, p->coarsest_min, p->max_levels);
-            P.nlev[q] = L;
-            P.base[q] = (int)P.lv64.size();
-            P.levels = std::max(P.levels, L);
-            const Coef c = make_coef(g->dx, g->dy);
-            int m = g->m, n = g->n;
-            for (int l = 0; l < L; ++l) {
-                BatchLevel<double> d{};
-                d.m = m;
-                d.n = n;
-                d.pitch = l == 0 ? g->pitch : round_up(m, 32);
-                d.problem = q;
-                d.unit_beta = c.unit_beta;
-                d.inv_d_shift = c.inv_d_shift;
-                d.b2 = c.b2;
-                d.d = c.d;
-                d.inv_d = c.inv_d;
-                BatchLevel<float> f{};
-                f.m = m;
-                f.n = n;
-                f.pitch = round_up(m, 32);
-                f.problem = q;
-                f.unit_beta = c.unit_beta;
-                f.inv_d_shift = 0;
-                f.b2 = c.b2;
-                f.d = c.d;
-                f.inv_d = c.inv_d;
-                if (l == L - 1) {
-                    if ((int64_t)(m - 2) * (n - 2) > COARSE_MAX_UNKNOWNS)
-                        fail(LAP_EUNSUPPORTED, "coarsest level with more than 1024 unknowns");
-                    d.ainv_t = f.ainv_t = coarse_inverse(h, m, n, c.b2, c.d);
-                    P.max_coarse_unknowns = std::max(P.max_coarse_unknowns, (m - 2) * (n - 2));
-                }
-                P.lv64.push_back(d);
-                P.lv32.push_back(f);
-                m = (m - 1) / 2 + 1;
-                n = (n - 1) / 2 + 1;
-            }
-        }
-        // ---- work lists: one set per tail-size candidate ----
-        std::vector<int> all_problems(count), shape;
-        for (int q = 0; q < count; ++q) {
-            all_problems[q] = q;
             shape.push_back(grids[q].m);
             shape.push_back(grids[q].n);
         }
         TailTuner& tuner = h->tail_tuners[tuner_key('B', p, shape)];
         if (tuner.cand.empty()) tuner.init(tail_candidates(true, mixed, p->tail_size));
-        const bool fused = mixed && !p->unfused && fused32_supported(p->nu1, p->nu2);
-        if (fused) ck(prepare_fused32(), "tile kernel attributes");
-        for (int cand : tuner.cand) {
-            LevelLists L;
-            build_lists(L, P.items, P.jobs, all_problems, P.base, P.nlev, P.lv64, cand,
-                        fused ? &P.tiles : nullptr, p->nu1, p->nu2);
-            P.max_coarse_unknowns = std::max(P.max_coarse_unknowns, L.max_coarse);
-            P.cands.push_back(L);
+        // the plan of the previous call, if it was this batch and nothing has carved the arena
+        // since; else a new one
+        BatchCache* C = static_cast<BatchCache*>(h->batch_cache.get());
+        if (!C || C->epoch != h->arena_epoch || !(C->key == make_key(count, grids, psi_devs, p))) {
+            h->batch_cache.reset();  // releases the old plan's graphs
+            if (mixed && !p->unfused && fused32_supported(p->nu1, p->nu2))
+                ck(prepare_fused32(), "tile kernel attributes");
+            h->batch_cache = build_plan(h, count, grids, psi_devs, p, tuner, s);
+            C = static_cast<BatchCache*>(h->batch_cache.get());
         }
-        const int n0 = (int)P.items.size();
-        for (int q = 0; q < count; ++q) {
-            P.first_item.push_back((int)P.items.size() - n0);
-            add_items(P.items, P.base[q], grids[q].m, grids[q].n);
-        }
-        P.first_item.push_back((int)P.items.size() - n0);
-        P.norm = {n0, (int)P.items.size() - n0};
-        // ---- memory: level buffers, descriptors, lists, state ----
-        auto carve_all = [&](auto& cv) {
-            for (int q = 0; q < count; ++q)
-                for (int l = 0; l < P.nlev[q]; ++l) {
-                    const int k = P.base[q] + l;
-                    BatchLevel<double>& d = P.lv64[k];
-                    BatchLevel<float>& f = P.lv32[k];
-                    const bool last = l == P.nlev[q] - 1;
-                    if (!mixed) {
-                        if (l == 0) {
-                            d.u = psi_devs[q];
-                            d.q = nullptr;
-                        } else {
-                            d.u = cv.template take<double>((size_t)d.n * d.pitch);
-                            d.q = cv.template take<double>((size_t)d.n * d.pitch);
-                        }
-                        d.r = last ? nullptr : cv.template take<double>((size_t)d.n * d.pitch);
-                    } else {
-                        if (l == 0) d.u = psi_devs[q];
-                        f.u = cv.template take<float>((size_t)f.n * f.pitch);
-                        f.q = cv.template take<float>((size_t)f.n * f.pitch);
-                        f.r = last ? nullptr : cv.template take<float>((size_t)f.n * f.pitch);
-                    }
-                }
-            auto* lv64 = cv.template take<BatchLevel<double>>(P.lv64.size());
-            auto* lv32 = cv.template take<BatchLevel<float>>(P.lv32.size());
-            auto* items = cv.template take<BatchItem>(P.items.size());
-            auto* jobs = cv.template take<TailJob>(std::max<size_t>(1, P.jobs.size()));
-            auto* tiles = cv.template take<TileItem>(std::max<size_t>(1, P.tiles.size()));
-            auto* first = cv.template take<int>(P.first_item.size());
-            auto* active = cv.template take<int>(count);
-            auto* status = cv.template take<int>(count);
-            auto* remaining = cv.template take<int>(1);
-            auto* iters = cv.template take<long long>(count);
-            auto* r0 = cv.template take<double>(count);
-            auto* rnow = cv.template take<double>(count);
-            auto* partials = cv.template take<double>(std::max(1, P.norm.second));
-            return std::make_tuple(lv64, lv32, items, jobs, tiles, first, active, status, remaining,
-                                   iters, r0, rnow, partials);
-        };
-        Sizer sz;
-        carve_all(sz);
-        Carver cv(arena(h, sz.off));
-        // plain variables (lambdas below capture them; capturing structured bindings is C++20)
-        BatchLevel<double>* lv64;
-        BatchLevel<float>* lv32;
-        BatchItem* items;
-        TailJob* jobs;
-        TileItem* tiles;
-        int *first, *active, *status, *remaining;
-        long long* iters;
-        double *r0, *rnow, *partials;
-        std::tie(lv64, lv32, items, jobs, tiles, first, active, status, remaining, iters, r0, rnow,
-                 partials) = carve_all(cv);
-        // zero every level buffer (rings of corrections stay zero), then upload tables
-        const size_t level_bytes = (size_t)((char*)lv64 - (char*)h->arena);
-        if (level_bytes) ck(cudaMemsetAsync(h->arena, 0, level_bytes, s), "zero levels");
-        std::vector<int> ones(count, 1);
-        const int cnt = count;
-        ck(cudaMemcpyAsync(lv64, P.lv64.data(), P.lv64.size() * sizeof(P.lv64[0]), cudaMemcpyHostToDevice, s), "upload levels");
-        ck(cudaMemcpyAsync(lv32, P.lv32.data(), P.lv32.size() * sizeof(P.lv32[0]), cudaMemcpyHostToDevice, s), "upload levels");
-        ck(cudaMemcpyAsync(items, P.items.data(), P.items.size() * sizeof(BatchItem), cudaMemcpyHostToDevice, s), "upload items");
-        if (!P.jobs.empty())
-            ck(cudaMemcpyAsync(jobs, P.jobs.data(), P.jobs.size() * sizeof(TailJob), cudaMemcpyHostToDevice, s), "upload jobs");
-        if (!P.tiles.empty())
-            ck(cudaMemcpyAsync(tiles, P.tiles.data(), P.tiles.size() * sizeof(TileItem), cudaMemcpyHostToDevice, s), "upload tiles");
-        ck(cudaMemcpyAsync(first, P.first_item.data(), P.first_item.size() * sizeof(int), cudaMemcpyHostToDevice, s), "upload items");
-        ck(cudaMemcpyAsync(active, ones.data(), count * sizeof(int), cudaMemcpyHostToDevice, s), "upload flags");
-        ck(cudaMemcpyAsync(status, ones.data(), count * sizeof(int), cudaMemcpyHostToDevice, s), "upload flags");
-        ck(cudaMemcpyAsync(remaining, &cnt, sizeof(int), cudaMemcpyHostToDevice, s), "upload count");
-        ck(cudaMemsetAsync(iters, 0, count * sizeof(long long), s), "zero iterations");
-        ck(cudaStreamSynchronize(s), "stream sync");  // host vectors above go out of scope
-        auto list = [&](std::pair<int, int> r) { return BatchList{items + r.first, r.second}; };
-        const BatchList norm_list = list(P.norm);
-        const bool rel = p->norm == LAP_NORM_L2_REL;
-        // ---- one cycle (V-cycle(s) and stopping test) with tail-size candidate c ----
-        auto cycle = [&](int c, cudaStream_t st) {
-            const LevelLists& L = P.cands[c];
-            if (mixed) {
-                for (int k = 0; k < p->inner_cycles; ++k) {
-                    if (L.fused)
-                        enqueue_vcycle32_fused(list, L, lv32, active, jobs, tiles, *p, p->smoother_w,
-                                               k == 0, st, k == p->inner_cycles - 1 ? lv64 : nullptr);
-                    else
-                        enqueue_vcycle(list, L, lv32, active, jobs, *p, p->smoother_w, st);
-                }
-                // fused: the level-0 ascents did psi += e except where a tail holds level 0
-                ck(launch_b_update(L.fused ? list(L.upd0) : norm_list, lv64, active, lv32, st),
-                   "batched update");
-                ck(launch_b_sumsq(norm_list, lv64, active, partials, lv32, st, r0), "batched residual");
-            } else {
-                enqueue_vcycle(list, L, lv64, active, jobs, *p, p->smoother_w, st);
-                ck(launch_b_sumsq(norm_list, lv64, active, partials, nullptr, st), "batched residual");
-            }
-            ck(launch_b_converge(partials, first, count, active, r0, rnow, iters, status, remaining,
-                                 1, rel, p->tol, st), "batched convergence");
-        };
-        // initial residuals (and, for the mixed solver, the first FP32 right-hand sides)
-        ck(launch_b_sumsq(norm_list, lv64, active, partials, mixed ? lv32 : nullptr, s), "batched residual");
-        ck(launch_b_converge(partials, first, count, active, r0, rnow, iters, status, remaining, 0,
-                             rel, p->tol, s), "batched convergence");
-        // one cycle per candidate as a graph, captured on the handle's stream when first
-        // used and replayed on the caller's
-        std::vector<std::pair<cudaGraphExec_t, int64_t>> exec(P.cands.size(), {nullptr, 0});
-        auto release = [&] {
-            for (auto& e : exec)
-                if (e.first) cudaGraphExecDestroy(e.first);
-        };
-        auto launch_cycle = [&](int c) {
-            if (!h->use_graphs) {
-                cycle(c, s);
-                return;
-            }
-            if (!exec[c].first) {
-                if (!h->capture)
-                    ck(cudaStreamCreateWithFlags(&h->capture, cudaStreamNonBlocking), "capture stream");
-                const int64_t before = launches_now();
-                ck(cudaStreamBeginCapture(h->capture, cudaStreamCaptureModeThreadLocal), "begin capture");
-                cudaGraph_t g = nullptr;
-                try {
-                    cycle(c, h->capture);
-                } catch (...) {
-                    cudaStreamEndCapture(h->capture, &g);
-                    if (g) cudaGraphDestroy(g);
-                    cudaGetLastError();
-                    throw;
-                }
-                ck(cudaStreamEndCapture(h->capture, &g), "end capture");
-                exec[c].second = launches_now() - before;
-                add_launches(-exec[c].second);
-                const cudaError_t e = cudaGraphInstantiate(&exec[c].first, g, 0);
-                cudaGraphDestroy(g);
-                ck(e, "instantiate graph");
-            }
-            ck(cudaGraphLaunch(exec[c].first, s), "launch graph");
-            add_launches(exec[c].second);
-        };
-        int64_t done = 0;
-        int left = count;
         try {
+            const BatchPlan& P = C->P;
+            // per call: every level buffer zeroed (rings of corrections stay zero), every
+            // problem active, no cycles done
+            if (C->level_bytes) ck(cudaMemsetAsync(h->arena, 0, C->level_bytes, s), "zero levels");
+            std::vector<int> ones(count, 1);
+            const int cnt = count;
+            ck(cudaMemcpyAsync(C->active, ones.data(), count * sizeof(int), cudaMemcpyHostToDevice, s), "upload flags");
+            ck(cudaMemcpyAsync(C->status, ones.data(), count * sizeof(int), cudaMemcpyHostToDevice, s), "upload flags");
+            ck(cudaMemcpyAsync(C->remaining, &cnt, sizeof(int), cudaMemcpyHostToDevice, s), "upload count");
+            ck(cudaMemsetAsync(C->iters, 0, count * sizeof(long long), s), "zero iterations");
+            BatchLevel<double>* lv64 = C->lv64;
+            BatchLevel<float>* lv32 = C->lv32;
+            BatchItem* items = C->items;
+            TailJob* jobs = C->jobs;
+            TileItem* tiles = C->tiles;
+            int* first = C->first;
+            int* active = C->active;
+            int* status = C->status;
+            int* remaining = C->remaining;
+            long long* iters = C->iters;
+            double* r0 = C->r0;
+            double* rnow = C->rnow;
+            double* partials = C->partials;
+            auto list = [&](std::pair<int, int> r) { return BatchList{items + r.first, r.second}; };
+            const BatchList norm_list = list(P.norm);
+            const bool rel = p->norm == LAP_NORM_L2_REL;
+            // ---- one cycle (V-cycle(s) and stopping test) with tail-size candidate c ----
+            auto cycle = [&](int c, cudaStream_t st) {
+                const LevelLists& L = P.cands[c];
+                if (mixed) {
+                    for (int k = 0; k < p->inner_cycles; ++k) {
+                        if (L.fused)
+                            enqueue_vcycle32_fused(list, L, lv32, active, jobs, tiles, *p, p->smoother_w,
+                                                   k == 0, st, k == p->inner_cycles - 1 ? lv64 : nullptr);
+                        else
+                            enqueue_vcycle(list, L, lv32, active, jobs, *p, p->smoother_w, st);
+                    }
+                    // fused: the level-0 ascents did psi += e except where a tail holds level 0
+                    ck(launch_b_update(L.fused ? list(L.upd0) : norm_list, lv64, active, lv32, st),
+                       "batched update");
+                    ck(launch_b_sumsq(norm_list, lv64, active, partials, lv32, st, r0), "batched residual");
+                } else {
+                    enqueue_vcycle(list, L, lv64, active, jobs, *p, p->smoother_w, st);
+                    ck(launch_b_sumsq(norm_list, lv64, active, partials, nullptr, st), "batched residual");
+                }
+                ck(launch_b_converge(partials, first, count, active, r0, rnow, iters, status, remaining,
+                                     1, rel, p->tol, st), "batched convergence");
+            };
+            // initial residuals (and, for the mixed solver, the first FP32 right-hand sides)
+            ck(launch_b_sumsq(norm_list, lv64, active, partials, mixed ? lv32 : nullptr, s), "batched residual");
+            ck(launch_b_converge(partials, first, count, active, r0, rnow, iters, status, remaining, 0,
+                                 rel, p->tol, s), "batched convergence");
+            // one cycle per candidate as a graph, captured on the handle's stream when first
+            // used (kept with the plan for later calls) and replayed on the caller's
+            auto& exec = C->exec;
+            auto launch_cycle = [&](int c) {
+                if (!h->use_graphs) {
+                    cycle(c, s);
+                    return;
+                }
+                if (!exec[c].first) {
+                    if (!h->capture)
+                        ck(cudaStreamCreateWithFlags(&h->capture, cudaStreamNonBlocking), "capture stream");
+                    const int64_t before = launches_now();
+                    ck(cudaStreamBeginCapture(h->capture, cudaStreamCaptureModeThreadLocal), "begin capture");
+                    cudaGraph_t g = nullptr;
+                    try {
+                        cycle(c, h->capture);
+                    } catch (...) {
+                        cudaStreamEndCapture(h->capture, &g);
+                        if (g) cudaGraphDestroy(g);
+                        cudaGetLastError();
+                        throw;
+                    }
+                    ck(cudaStreamEndCapture(h->capture, &g), "end capture");
+                    exec[c].second = launches_now() - before;
+                    add_launches(-exec[c].second);
+                    const cudaError_t e = cudaGraphInstantiate(&exec[c].first, g, 0);
+                    cudaGraphDestroy(g);
+                    ck(e, "instantiate graph");
+                }
+                ck(cudaGraphLaunch(exec[c].first, s), "launch graph");
+                add_launches(exec[c].second);
+            };
+            int64_t done = 0;
+            int left = count;
             while (done < p->max_iter) {
                 ck(cudaMemcpyAsync(h->pinned, remaining, sizeof(int), cudaMemcpyDeviceToHost, s), "copy count");
                 ck(cudaStreamSynchronize(s), "stream sync");
@@ -382,26 +472,25 @@ extern "C" int lap_solve_batched(lap_handle h, int count, const lap_grid* grids,
                 }
                 done += steps;
             }
+            // ---- results ----
+            std::vector<long long> it(count);
+            std::vector<int> st(count);
+            std::vector<double> a(count), z(count);
+            ck(cudaMemcpyAsync(it.data(), iters, count * sizeof(long long), cudaMemcpyDeviceToHost, s), "copy results");
+            ck(cudaMemcpyAsync(st.data(), status, count * sizeof(int), cudaMemcpyDeviceToHost, s), "copy results");
+            ck(cudaMemcpyAsync(a.data(), r0, count * sizeof(double), cudaMemcpyDeviceToHost, s), "copy results");
+            ck(cudaMemcpyAsync(z.data(), rnow, count * sizeof(double), cudaMemcpyDeviceToHost, s), "copy results");
+            ck(cudaStreamSynchronize(s), "stream sync");
+            for (int q = 0; q < count; ++q) {
+                results[q].status = st[q];
+                results[q].iters = it[q];
+                results[q].r0 = a[q];
+                results[q].r_final = z[q];
+                results[q].last_check = rel ? (a[q] > 0 ? z[q] / a[q] : 0.0) : z[q];
+            }
         } catch (...) {
-            release();
+            h->batch_cache.reset();  // a failed call leaves no plan behind
             throw;
-        }
-        release();
-        // ---- results ----
-        std::vector<long long> it(count);
-        std::vector<int> st(count);
-        std::vector<double> a(count), z(count);
-        ck(cudaMemcpyAsync(it.data(), iters, count * sizeof(long long), cudaMemcpyDeviceToHost, s), "copy results");
-        ck(cudaMemcpyAsync(st.data(), status, count * sizeof(int), cudaMemcpyDeviceToHost, s), "copy results");
-        ck(cudaMemcpyAsync(a.data(), r0, count * sizeof(double), cudaMemcpyDeviceToHost, s), "copy results");
-        ck(cudaMemcpyAsync(z.data(), rnow, count * sizeof(double), cudaMemcpyDeviceToHost, s), "copy results");
-        ck(cudaStreamSynchronize(s), "stream sync");
-        for (int q = 0; q < count; ++q) {
-            results[q].status = st[q];
-            results[q].iters = it[q];
-            results[q].r0 = a[q];
-            results[q].r_final = z[q];
-            results[q].last_check = rel ? (a[q] > 0 ? z[q] / a[q] : 0.0) : z[q];
         }
     });
 }

@@ -12,6 +12,7 @@
 #include <cstring>
 #include <deque>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <stdexcept>
 #include <string>
@@ -97,6 +98,12 @@ int guarded(F&& body)
 
 inline int64_t round_up(int64_t v, int64_t a) { return (v + a - 1) / a * a; }
 
+// A batched solve's plan kept in the handle for the next call on the same batch (defined in
+// lap_batched.cu; destroyed with the handle or when another batch or call takes the arena).
+struct BatchCacheBase {
+    virtual ~BatchCacheBase() = default;
+};
+
 // Host-side copy of a line-solver table set plus its device allocation.
 struct LineEntry {
     LineTables t;
@@ -117,6 +124,8 @@ struct lap_handle_s {
     size_t held = 0;      // bytes of device memory held (arena + tables)
     double* arena = nullptr;
     size_t arena_bytes = 0;
+    uint64_t arena_epoch = 0;  // counts the calls that carved the arena (arena())
+    std::unique_ptr<lap::BatchCacheBase> batch_cache;  // the last batched solve's plan
     double* pinned = nullptr;  // 8 doubles of pinned host memory for results
     std::map<std::tuple<int, double, double, double>, lap::LineEntry> lines;
     std::map<std::tuple<int, int, double>, lap::CoarseEntry> coarse;

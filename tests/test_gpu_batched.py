@@ -78,3 +78,35 @@ def test_batched_rejects_bad_requests(b):
     with pytest.raises(b.LapError):
         lap.solve_batched([f], method="mg", norm="maxdelta")
     lap.close()
+
+
+@pytest.mark.parametrize("method", ["mg", "mg_mixed"])
+def test_repeated_batched_solves_reuse_the_plan(b, method):
+    """The handle keeps a batch's plan and cycle graphs for the next call on the same batch:
+    repeated calls, calls after a single-grid solve (which takes the scratch memory), after a
+    different tolerance and after another batch all give the first call's results bit for bit."""
+    lap = b.Laplace()
+    shapes = [(65, 33), (129, 129), (33, 65), (257, 65), (9, 9)]
+    inputs = [wl.random_ring(m, n, seed=500 + k) for k, (m, n) in enumerate(shapes)]
+    fields = [b.to_field(x) for x in inputs]
+    batch = b.Batch(fields, 1.0, 1.0)
+
+    def run(**kw):
+        for f, x in zip(fields, inputs):
+            f.copy_(torch.from_numpy(x))
+        res = lap.solve_batched(batch, method=method, max_iter=40, **kw)
+        return [host(f) for f in fields], [(r["status"], r["iters"], r["r_final"]) for r in res]
+
+    first = run(tol=1e-10)
+    others = [run(tol=1e-10), run(tol=1e-10)]
+    lap.solve(b.to_field(wl.random_ring(65, 65, seed=3)), method="mg", max_iter=2)
+    others.append(run(tol=1e-10))
+    run(tol=1e-6)
+    others.append(run(tol=1e-10))
+    lap.solve_batched([b.to_field(wl.random_ring(33, 33, seed=4))], method=method, max_iter=3)
+    others.append(run(tol=1e-10))
+    for fields_k, res_k in others:
+        assert res_k == first[1]
+        for a, c in zip(fields_k, first[0]):
+            assert np.array_equal(a, c)
+    lap.close()
