@@ -484,7 +484,7 @@ def main():
         for name, method in (("fp64", "mg"), ("mixed", "mg_mixed")):
             kw = dict(mg_kw, method=method)
             times, res = [], None
-            for rep in range(3 + reps):  # warm-ups: graphs, tail and item-size choice
+            for rep in range(8 + reps):  # warm-ups: plan, graphs, the configuration's choice
                 for f, g in zip(work_, pristine):
                     f.copy_(g)
                 torch.cuda.synchronize(dev)
@@ -493,7 +493,7 @@ def main():
                 res = lap.solve_batched(batch_, stream=stream, **kw)
                 e1.record(stream)
                 stream.synchronize()
-                if rep >= 3:
+                if rep >= 8:
                     times.append(e0.elapsed_time(e1))
             if not all(r["status"] == "converged" for r in res):
                 raise RuntimeError(f"batch {name}: not all problems converged")
@@ -558,26 +558,40 @@ def main():
         points = sum((m - 2) * (n - 2) for m, n in shapes)
         out = {"problems": count, "interior_points": points,
                "shapes": "m, n in {33, 65, 129, 257, 513}, aspect <= 4, ring U[0,1], interior 0"}
-        kw = dict(mg_kw)
-        for name, method in (("fp64", "mg"), ("mixed", "mg_mixed")):
+
+        def time_batch(method, warm, reps, **extra):
+            # warm-ups: the plan, the candidates' graphs and the choice by timing (each call's
+            # cycles with every problem running time one candidate configuration)
             times, res = [], None
-            for rep in range(6):  # three warm-ups: graphs, tail and item-size choice
+            for rep in range(warm + reps):
                 for f, g in zip(work, pristine):
                     f.copy_(g)
                 torch.cuda.synchronize(dev)
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 e0.record(stream)
-                res = lap.solve_batched(batch, stream=stream, **dict(kw, method=method))
+                res = lap.solve_batched(batch, stream=stream, **dict(mg_kw, method=method, **extra))
                 e1.record(stream)
                 stream.synchronize()
-                if rep >= 3:
+                if rep >= warm:
                     times.append(e0.elapsed_time(e1))
             if not all(r["status"] == "converged" for r in res):
-                raise RuntimeError(f"batched {name}: not all problems converged")
-            ms = statistics.median(times)
+                raise RuntimeError(f"batched {method}: not all problems converged")
+            return statistics.median(times), res
+
+        for name, method in (("fp64", "mg"), ("mixed", "mg_mixed")):
+            ms, res = time_batch(method, 8, 3)
             out[name] = {"ms": ms, "solves_per_s": count / (ms / 1e3),
-                         "max_cycles": max(r["iters"] for r in res)}
+                         "max_cycles": max(r["iters"] for r in res),
+                         "configuration": lap.last_batch_config()}
+        # the FP32 tilings one by one (tail and item size still chosen by timing): what the
+        # choice between them is worth
+        out["mixed_by_tiling"] = {}
+        for tiling, label in ((1, "tiles_512x128x64"), (2, "tiles_1024x128x64"),
+                              (3, "tiles_512x128x32"), (-1, "one_kernel_per_pass")):
+            ms, _ = time_batch("mg_mixed", 6, 3, tiling=tiling)
+            out["mixed_by_tiling"][label] = {"ms": ms, "configuration": lap.last_batch_config()}
         # one problem at a time through lap_solve, on a sample
+        kw = dict(mg_kw)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         for f, g in zip(work[:sample], pristine[:sample]):
             f.copy_(g)

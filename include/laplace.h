@@ -38,7 +38,7 @@
 extern "C" {
 #endif
 
-#define LAP_ABI_VERSION 1
+#define LAP_ABI_VERSION 2
 
 enum {
     LAP_OK = 0,
@@ -113,6 +113,13 @@ typedef struct {
                              restriction) and ascent (interpolation, smoothing) run as one
                              shared-memory tile kernel each; non-zero = one kernel per pass
                              (the same values bit for bit; the reference for the tiles) */
+    int32_t tiling;       /* batched LAP_MG_MIXED with unfused == 0: how the FP32 levels run.
+                             0 = chosen by timing (see lap_solve_batched), -1 = one kernel per
+                             pass, 1..3 = tiles of one variant (1: 512 threads over 128 x 64
+                             regions, 2: 1024 threads over 128 x 64, 3: 512 threads over
+                             128 x 32). Every choice gives the same values bit for bit */
+    int32_t item_points;  /* batched solves: interior points per work item of the per-pass
+                             kernels (>= 32), 0 = chosen by timing. No effect on the values */
 } lap_params;
 
 typedef struct {
@@ -158,11 +165,24 @@ int lap_solve(lap_handle h, const lap_grid* g, double* psi_dev, const lap_params
  * the same), stops on its own (convergence is decided on the device) and reports in
  * results[k] (host). p->check_every sets how often (in cycles) the host polls for the
  * number of problems still running. Synchronises `stream` before returning.
+ * The launch configuration -- the small-level tail size (p->tail_size), the FP32 levels'
+ * temporal blocking and tile shape (p->tiling) and the per-pass kernels' work-item size
+ * (p->item_points) -- is chosen by timing where a parameter leaves it open (0): the first
+ * cycles of a batch shape each run a different candidate, one knob at a time, the fastest
+ * is kept in the handle for that shape. No choice changes a value.
  * The plan of a call (level descriptors, work lists, the captured cycle graphs) stays in the
  * handle: a following call with the same grids, field addresses and multigrid parameters
  * reuses it, unless another call of the handle has used its scratch memory in between. */
 int lap_solve_batched(lap_handle h, int count, const lap_grid* grids, double* const* psi_devs,
                       const lap_params* p, lap_result* results, void* stream);
+
+/* The launch configuration of the last cycle of the last lap_solve_batched call on h (no
+ * counterpart in the paper; for reports): *tail_size (-1 = no tail), *tiling (-1 = one kernel
+ * per pass, 1..3 = tile variant; see lap_params), *item_points, and *tuned = 1 if the choice
+ * by timing had finished for that batch shape (0 while candidates were still being timed).
+ * Any pointer may be NULL. All zero before the first batched solve. */
+int lap_last_batch_config(lap_handle h, int32_t* tail_size, int32_t* tiling, int32_t* item_points,
+                          int32_t* tuned);
 
 /* ---- serving: continuous batching over a stream of solve requests ----
  * A server owns a device pool of hbm_budget_bytes for the grid hierarchies of the requests it

@@ -30,12 +30,15 @@ namespace {
 
 constexpr int FT_THREADS = 512;
 constexpr int FT_W = 128;               // region columns (even): 64 column pairs
-constexpr int FT_H = 64;                // region rows: 4 per warp
+constexpr int FT_H = 64;                // region rows (single-grid tiles; batched: a variant)
 constexpr int FT_HS = FT_W / 2 + 16;    // half-row stride, 16 mod 32
 constexpr int FT_RS = 2 * FT_HS;        // row stride
-constexpr int FT_ARR = FT_RS * FT_H;    // floats per shared array
 constexpr int FT_CS = FT_W / 2 + 4;     // row stride of the staged coarse points
-constexpr int FT_CARR = FT_CS * (FT_H / 2 + 2);
+// floats per shared array, and of the staged coarse points, for regions of H rows
+__host__ __device__ constexpr int ft_arr(int H) { return FT_RS * H; }
+__host__ __device__ constexpr int ft_carr(int H) { return FT_CS * (H / 2 + 2); }
+constexpr int FT_ARR = ft_arr(FT_H);
+constexpr int FT_CARR = ft_carr(FT_H);
 
 // The region of a tile: global (gx0 + lx, gy0 + ly) for local 0 <= lx < w, 0 <= ly < h.
 // gx0 is even: local column lx = 2p + half sits at half `half`, index p, of its row, and
@@ -85,12 +88,13 @@ __device__ __forceinline__ void sts2_masked(float* p, float2 v, bool lo, bool hi
 // The region's u and q (0 outside the array; u = 0 when zero_u): each lane moves column
 // pairs (gx, gx + 1), gx even, with 8-byte loads, all 16 of a thread in flight together,
 // and splits them into the two halves of the row. Level pitches are even.
-template <int NT>
+template <int NT, int H>
 __device__ __forceinline__ void load_region(float* su, float* sq, const float* u, const float* q,
                                             int64_t pitch, int m, int n, const Region& R,
                                             bool zero_u)
 {
-    constexpr int NW = NT / 32, RPW = FT_H / NW;  // region rows per warp
+    constexpr int NW = NT / 32, RPW = H / NW;  // region rows per warp
+    static_assert(RPW >= 1 && RPW * NW == H, "region rows must be a multiple of the warps");
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     float2 vu[2 * RPW], vq[2 * RPW];
 #pragma unroll
@@ -268,7 +272,7 @@ __device__ __forceinline__ Region region_of(int x0, int y0, int tx, int ty, int 
 // Descent on one tile of level F: nu1 smoothing sweeps, the smoothed u of the owned points
 // to F.r (the second buffer of the level), the residual, and qc = 0.25 ((4 r + 2 edges) +
 // corners) with the correction zeroed at the coarse points whose centre the tile owns.
-template <int NT>
+template <int NT, int H>
 __device__ __forceinline__ void down_tile(const BatchLevel<float>& F, const BatchLevel<float>& C,
                                           int x0, int y0, int tx, int ty, int nu1, bool zero_u,
                                           const Coef32& k, float* su, float* sq)
@@ -276,7 +280,7 @@ __device__ __forceinline__ void down_tile(const BatchLevel<float>& F, const Batc
     constexpr int NW = NT / 32;
     const int m = F.m, n = F.n;
     const Region R = region_of(x0, y0, tx, ty, 2 + 2 * nu1);
-    load_region<NT>(su, sq, F.u, F.q, F.pitch, m, n, R, zero_u);
+    load_region<NT, H>(su, sq, F.u, F.q, F.pitch, m, n, R, zero_u);
     __syncthreads();
     smooth_region<NT>(su, sq, R, m, n, nu1, k);
     const int x1 = min(x0 + tx, m - 1), y1 = min(y0 + ty, n - 1);
@@ -336,7 +340,7 @@ __device__ __forceinline__ void down_tile(const BatchLevel<float>& F, const Batc
 // in shared memory (sc): a column pair p of the region lies over coarse column gx0 / 2 + p.
 // With psi (the FP64 field of the mixed solver's level 0), the last ascent adds its result
 // to psi in FP64 (psi += e, the update of the defect correction) instead of storing e.
-template <int NT>
+template <int NT, int H>
 __device__ __forceinline__ void up_tile(const BatchLevel<float>& F, const BatchLevel<float>& C,
                                         int x0, int y0, int tx, int ty, int nu2, const Coef32& k,
                                         float* su, float* sq, float* sc, double* psi,
@@ -371,7 +375,7 @@ __device__ __forceinline__ void up_tile(const BatchLevel<float>& F, const BatchL
             else *d = 0.f;
         }
     }
-    load_region<NT>(su, sq, F.r, F.q, F.pitch, m, n, R, false);
+    load_region<NT, H>(su, sq, F.r, F.q, F.pitch, m, n, R, false);
     cp_async_wait_all();
     __syncthreads();
     // u += P e: even rows take coarse row J = gy / 2, odd rows the mean of rows J and J + 1;
@@ -454,8 +458,8 @@ __global__ void __launch_bounds__(NT, 1024 / NT)
 {
     extern __shared__ float4 smem4[];
     float* smem = reinterpret_cast<float*>(smem4);
-    down_tile<NT>(F, C, 1 + blockIdx.x * tx, 1 + blockIdx.y * ty, tx, ty, nu1, zero_u != 0,
-                  coef32(F, gs != 0, w, omw), smem, smem + FT_ARR);
+    down_tile<NT, FT_H>(F, C, 1 + blockIdx.x * tx, 1 + blockIdx.y * ty, tx, ty, nu1, zero_u != 0,
+                        coef32(F, gs != 0, w, omw), smem, smem + FT_ARR);
 }
 
 template <int NT>
@@ -465,12 +469,13 @@ __global__ void __launch_bounds__(NT, 1024 / NT)
 {
     extern __shared__ float4 smem4[];
     float* smem = reinterpret_cast<float*>(smem4);
-    up_tile<NT>(F, C, 1 + blockIdx.x * tx, 1 + blockIdx.y * ty, tx, ty, nu2,
-                coef32(F, gs != 0, w, omw), smem, smem + FT_ARR, smem + 2 * FT_ARR, psi, psi_pitch);
+    up_tile<NT, FT_H>(F, C, 1 + blockIdx.x * tx, 1 + blockIdx.y * ty, tx, ty, nu2,
+                      coef32(F, gs != 0, w, omw), smem, smem + FT_ARR, smem + 2 * FT_ARR, psi, psi_pitch);
 }
 
-// ---- many grids: one tile item per CTA ----
-__global__ void __launch_bounds__(FT_THREADS, 2)
+// ---- many grids: one tile item per CTA, NT threads, regions of H rows ----
+template <int NT, int H>
+__global__ void __launch_bounds__(NT, 1024 / NT)
     b_down32_kernel(const TileItem* __restrict__ items, const BatchLevel<float>* __restrict__ lv,
                     const int* __restrict__ active, int nu1, int zero_u, int gs, float w, float omw)
 {
@@ -479,11 +484,12 @@ __global__ void __launch_bounds__(FT_THREADS, 2)
     const TileItem it = items[blockIdx.x];
     const BatchLevel<float> F = lv[it.level];
     if (active && !active[F.problem]) return;
-    down_tile<FT_THREADS>(F, lv[it.level + 1], it.x0, it.y0, it.tx, it.ty, nu1, zero_u != 0,
-                          coef32(F, gs != 0, w, omw), smem, smem + FT_ARR);
+    down_tile<NT, H>(F, lv[it.level + 1], it.x0, it.y0, it.tx, it.ty, nu1, zero_u != 0,
+                     coef32(F, gs != 0, w, omw), smem, smem + ft_arr(H));
 }
 
-__global__ void __launch_bounds__(FT_THREADS, 2)
+template <int NT, int H>
+__global__ void __launch_bounds__(NT, 1024 / NT)
     b_up32_kernel(const TileItem* __restrict__ items, const BatchLevel<float>* __restrict__ lv,
                   const int* __restrict__ active, int nu2, int gs, float w, float omw,
                   const BatchLevel<double>* __restrict__ lv64)
@@ -495,11 +501,12 @@ __global__ void __launch_bounds__(FT_THREADS, 2)
     if (active && !active[F.problem]) return;
     double* psi = lv64 ? lv64[it.level].u : nullptr;
     const int64_t pp = lv64 ? lv64[it.level].pitch : 0;
-    up_tile<FT_THREADS>(F, lv[it.level + 1], it.x0, it.y0, it.tx, it.ty, nu2,
-                        coef32(F, gs != 0, w, omw), smem, smem + FT_ARR, smem + 2 * FT_ARR, psi, pp);
+    up_tile<NT, H>(F, lv[it.level + 1], it.x0, it.y0, it.tx, it.ty, nu2, coef32(F, gs != 0, w, omw),
+                   smem, smem + ft_arr(H), smem + 2 * ft_arr(H), psi, pp);
 }
 
-constexpr size_t FT_SMEM = (2 * FT_ARR + FT_CARR) * sizeof(float);
+constexpr size_t ft_smem(int H) { return (2 * (size_t)ft_arr(H) + ft_carr(H)) * sizeof(float); }
+constexpr size_t FT_SMEM = ft_smem(FT_H);
 constexpr int FT_FEW_TILES = 152;  // below one tile per SM: 1024-thread tiles
 
 }  // namespace
@@ -509,23 +516,47 @@ constexpr int FT_FEW_TILES = 152;  // below one tile per SM: 1024-thread tiles
 static int halo_down(int nu1) { return 2 + 2 * nu1; }
 static int halo_up(int nu2) { return 2 * nu2; }
 
-bool fused32_supported(int nu1, int nu2)
+// Region rows of a batched tile variant: 1 = 512 threads over 128 x 64 regions (two CTAs per
+// SM), 2 = 1024 threads over 128 x 64 (one CTA per SM, half the rows per warp: a shorter
+// critical path per tile), 3 = 512 threads over 128 x 32 (smaller tiles, more of them).
+static int variant_rows(int variant) { return variant == 3 ? 32 : FT_H; }
+static int variant_threads(int variant) { return variant == 2 ? 1024 : 512; }
+
+static bool tiles_fit(int H, int nu1, int nu2)
 {
     const int h = std::max(halo_down(nu1), halo_up(nu2));
-    return FT_W - 2 * h - 2 >= 16 && FT_H - 2 * h >= 8;
+    return FT_W - 2 * h - 2 >= 16 && H - 2 * h >= 8;
 }
 
-// Balanced tiles no larger than the region allows: the interior (m-2) x (n-2) split into
-// ntx x nty tiles of tx x ty owned points.
-void fused32_tile(int m, int n, int nu1, int nu2, int* tx, int* ty, int* ntx, int* nty)
+bool fused32_supported(int nu1, int nu2) { return tiles_fit(FT_H, nu1, nu2); }
+
+bool fused32_variant_supported(int variant, int nu1, int nu2)
+{
+    return variant >= 1 && variant <= FUSED32_VARIANTS && tiles_fit(variant_rows(variant), nu1, nu2);
+}
+
+// Balanced tiles no larger than a region of H rows allows: the interior (m-2) x (n-2) split
+// into ntx x nty tiles of tx x ty owned points.
+static void tile_split(int H, int m, int n, int nu1, int nu2, int* tx, int* ty, int* ntx, int* nty)
 {
     const int h = std::max(halo_down(nu1), halo_up(nu2));
-    const int mx = FT_W - 2 * h - 2, my = FT_H - 2 * h;
-    const int W = std::max(1, m - 2), H = std::max(1, n - 2);
+    const int mx = FT_W - 2 * h - 2, my = H - 2 * h;
+    const int W = std::max(1, m - 2), Hh = std::max(1, n - 2);
     *ntx = (W + mx - 1) / mx;
-    *nty = (H + my - 1) / my;
+    *nty = (Hh + my - 1) / my;
     *tx = (W + *ntx - 1) / *ntx;
-    *ty = (H + *nty - 1) / *nty;
+    *ty = (Hh + *nty - 1) / *nty;
+}
+
+void fused32_tile(int m, int n, int nu1, int nu2, int* tx, int* ty, int* ntx, int* nty)
+{
+    tile_split(FT_H, m, n, nu1, nu2, tx, ty, ntx, nty);
+}
+
+void fused32_tile_variant(int variant, int m, int n, int nu1, int nu2, int* tx, int* ty, int* ntx,
+                          int* nty)
+{
+    tile_split(variant_rows(variant), m, n, nu1, nu2, tx, ty, ntx, nty);
 }
 
 // Nonzero once the tile kernels' shared-memory limit is raised on that device.
@@ -540,8 +571,12 @@ cudaError_t prepare_fused32()
     if (e == cudaSuccess) e = cudaFuncSetAttribute(up32_kernel<512>, a, (int)FT_SMEM);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(down32_kernel<1024>, a, (int)FT_SMEM);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(up32_kernel<1024>, a, (int)FT_SMEM);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(b_down32_kernel, a, (int)FT_SMEM);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(b_up32_kernel, a, (int)FT_SMEM);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(b_down32_kernel<512, 64>, a, (int)ft_smem(64));
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(b_up32_kernel<512, 64>, a, (int)ft_smem(64));
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(b_down32_kernel<1024, 64>, a, (int)ft_smem(64));
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(b_up32_kernel<1024, 64>, a, (int)ft_smem(64));
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(b_down32_kernel<512, 32>, a, (int)ft_smem(32));
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(b_up32_kernel<512, 32>, a, (int)ft_smem(32));
     if (e == cudaSuccess) attr_record(g_fused32_ready, dev, 1);
     return e;
 }
@@ -579,22 +614,35 @@ cudaError_t launch_up32(const BatchLevel<float>& F, const BatchLevel<float>& C, 
 }
 
 cudaError_t launch_b_down32(const TileItem* items, int count, const BatchLevel<float>* lv,
-                            const int* active, int nu1, bool zero_u, bool gs, double w, cudaStream_t s)
+                            const int* active, int nu1, bool zero_u, bool gs, double w, cudaStream_t s,
+                            int variant)
 {
     if (count == 0) return cudaSuccess;
-    b_down32_kernel<<<count, FT_THREADS, FT_SMEM, s>>>(items, lv, active, nu1, zero_u ? 1 : 0,
-                                                       gs ? 1 : 0, (float)w, (float)(1.0 - w));
+    const int z = zero_u ? 1 : 0, g = gs ? 1 : 0;
+    const float wf = (float)w, omw = (float)(1.0 - w);
+    if (variant == 2)
+        b_down32_kernel<1024, 64><<<count, 1024, ft_smem(64), s>>>(items, lv, active, nu1, z, g, wf, omw);
+    else if (variant == 3)
+        b_down32_kernel<512, 32><<<count, 512, ft_smem(32), s>>>(items, lv, active, nu1, z, g, wf, omw);
+    else
+        b_down32_kernel<512, 64><<<count, 512, ft_smem(64), s>>>(items, lv, active, nu1, z, g, wf, omw);
     note_launch();
     return cudaGetLastError();
 }
 
 cudaError_t launch_b_up32(const TileItem* items, int count, const BatchLevel<float>* lv,
                           const int* active, int nu2, bool gs, double w, cudaStream_t s,
-                          const BatchLevel<double>* lv64)
+                          const BatchLevel<double>* lv64, int variant)
 {
     if (count == 0) return cudaSuccess;
-    b_up32_kernel<<<count, FT_THREADS, FT_SMEM, s>>>(items, lv, active, nu2, gs ? 1 : 0, (float)w,
-                                                     (float)(1.0 - w), lv64);
+    const int g = gs ? 1 : 0;
+    const float wf = (float)w, omw = (float)(1.0 - w);
+    if (variant == 2)
+        b_up32_kernel<1024, 64><<<count, 1024, ft_smem(64), s>>>(items, lv, active, nu2, g, wf, omw, lv64);
+    else if (variant == 3)
+        b_up32_kernel<512, 32><<<count, 512, ft_smem(32), s>>>(items, lv, active, nu2, g, wf, omw, lv64);
+    else
+        b_up32_kernel<512, 64><<<count, 512, ft_smem(64), s>>>(items, lv, active, nu2, g, wf, omw, lv64);
     note_launch();
     return cudaGetLastError();
 }

@@ -147,6 +147,10 @@ void check_params(const lap_params* p)
             fail(LAP_EINVAL, "smoother_w must lie in (0, 2)");
         if (p->tail_size < -1 || p->tail_size == 1 || p->tail_size == 2)
             fail(LAP_EINVAL, "tail_size must be -1, 0 or >= 3");
+        if (p->tiling < -1 || p->tiling > FUSED32_VARIANTS)
+            fail(LAP_EINVAL, "tiling must be -1, 0 or a tile variant 1..3");
+        if (p->item_points != 0 && p->item_points < 32)
+            fail(LAP_EINVAL, "item_points must be 0 or >= 32");
     }
     if ((p->method == LAP_ADI || p->method == LAP_SLOR) && p->line_form != LAP_FORM_A &&
         p->line_form != LAP_FORM_B)
@@ -441,10 +445,11 @@ std::string tuner_key(char kind, const lap_params* p, const std::vector<int>& sh
         hsh ^= (uint32_t)v;
         hsh *= 1099511628211ull;
     }
-    char buf[192];
-    std::snprintf(buf, sizeof buf, "%c %d %d %d %d %d %.17g %d %d %d %zu %llx", kind, p->method,
+    char buf[224];
+    std::snprintf(buf, sizeof buf, "%c %d %d %d %d %d %.17g %d %d %d %d %d %zu %llx", kind, p->method,
                   p->nu1, p->nu2, p->coarsest_min, p->max_levels, p->smoother_w, p->inner_cycles,
-                  p->tail_size, p->unfused, shape.size(), (unsigned long long)hsh);
+                  p->tail_size, p->unfused, p->tiling, p->item_points, shape.size(),
+                  (unsigned long long)hsh);
     return buf;
 }
 

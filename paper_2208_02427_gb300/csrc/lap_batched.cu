@@ -5,9 +5,9 @@
 
 namespace lap {
 
-void add_items(std::vector<BatchItem>& items, int level_index, int m, int n)
+void add_items(std::vector<BatchItem>& items, int level_index, int m, int n, int points)
 {
-    const int per = std::max(1, BATCH_ITEM_POINTS / std::max(1, m - 2));
+    const int per = std::max(1, points / std::max(1, m - 2));
     for (int r = 1; r <= n - 2; r += per) items.push_back(BatchItem{level_index, r, std::min(per, n - 1 - r)});
 }
 
@@ -27,9 +27,11 @@ int tail_start(const BatchLevel<double>* lv, int nlev, int tail_size)
 void build_lists(LevelLists& L, std::vector<BatchItem>& items, std::vector<TailJob>& jobs,
                  const std::vector<int>& who, const std::vector<int>& base,
                  const std::vector<int>& nlev, const std::vector<BatchLevel<double>>& lv,
-                 int tail_size, std::vector<TileItem>* tiles, int nu1, int nu2)
+                 int tail_size, std::vector<TileItem>* tiles, int nu1, int nu2, int tile_variant,
+                 int item_points)
 {
     L.fused = tiles != nullptr;
+    L.tile_variant = tile_variant;
     L.tiles.assign(0, {0, 0});
     L.levels = 0;
     for (int q : who) L.levels = std::max(L.levels, nlev[q]);
@@ -45,7 +47,7 @@ void build_lists(LevelLists& L, std::vector<BatchItem>& items, std::vector<TailJ
         for (size_t k = 0; k < who.size(); ++k) {
             const int q = who[k];
             if (nlev[q] - 1 > l && l < t[k])
-                add_items(items, base[q] + l, lv[base[q] + l].m, lv[base[q] + l].n);
+                add_items(items, base[q] + l, lv[base[q] + l].m, lv[base[q] + l].n, item_points);
         }
         L.fine[l] = {f0, (int)items.size() - f0};
         if (tiles) {
@@ -55,7 +57,7 @@ void build_lists(LevelLists& L, std::vector<BatchItem>& items, std::vector<TailJ
                 if (!(nlev[q] - 1 > l && l < t[k])) continue;
                 const BatchLevel<double>& d = lv[base[q] + l];
                 int tx, ty, ntx, nty;
-                fused32_tile(d.m, d.n, nu1, nu2, &tx, &ty, &ntx, &nty);
+                fused32_tile_variant(tile_variant, d.m, d.n, nu1, nu2, &tx, &ty, &ntx, &nty);
                 for (int by = 0; by < nty; ++by)
                     for (int bx = 0; bx < ntx; ++bx)
                         tiles->push_back(TileItem{base[q] + l, 1 + bx * tx, 1 + by * ty, tx, ty});
@@ -66,7 +68,7 @@ void build_lists(LevelLists& L, std::vector<BatchItem>& items, std::vector<TailJ
         for (size_t k = 0; k < who.size(); ++k) {
             const int q = who[k];
             if (nlev[q] > l && l <= t[k])
-                add_items(items, base[q] + l, lv[base[q] + l].m, lv[base[q] + l].n);
+                add_items(items, base[q] + l, lv[base[q] + l].m, lv[base[q] + l].n, item_points);
         }
         L.all[l] = {a0, (int)items.size() - a0};
         const int c0 = (int)items.size();
@@ -110,14 +112,23 @@ struct BatchPlan {
     std::vector<BatchLevel<double>> lv64;
     std::vector<BatchLevel<float>> lv32;
     std::vector<int> nlev, base;       // levels and first level index per problem
-    std::vector<BatchItem> items;      // all work lists, back to back
-    std::vector<TailJob> jobs;         // tail jobs of every candidate, back to back
-    std::vector<TileItem> tiles;       // FP32 tile items of every candidate (fused cycle)
-    std::vector<LevelLists> cands;     // the V-cycle's lists for each tail-size candidate
-    std::pair<int, int> norm;          // level-0 items of every problem, problem by problem
+    std::vector<BatchItem> norm_items; // level-0 items of every problem, problem by problem
     std::vector<int> first_item;       // per problem: its first item in the norm list (+ end)
     int max_coarse_unknowns = 0;
     int levels = 0;
+};
+
+// The work lists of one tuner candidate (a BatchConfig), on the device in one allocation, and
+// the cycle graph captured with them.
+struct CandPlan {
+    LevelLists L;
+    BatchItem* items = nullptr;
+    TailJob* jobs = nullptr;
+    TileItem* tiles = nullptr;
+    void* dev = nullptr;
+    size_t bytes = 0;
+    cudaGraphExec_t exec = nullptr;
+    int64_t kernels = 0;  // kernels one replay of exec launches
 };
 
 // What a call's plan depends on: the grids (sizes, spacings, pitches), the fields' addresses
@@ -125,7 +136,8 @@ struct BatchPlan {
 struct BatchKey {
     std::vector<lap_grid> grids;
     std::vector<const double*> psi;
-    int32_t method, norm, nu1, nu2, coarsest_min, max_levels, inner_cycles, tail_size, unfused;
+    int32_t method, norm, nu1, nu2, coarsest_min, max_levels, inner_cycles, tail_size, unfused,
+        tiling, item_points;
     double smoother_w, tol;
     bool operator==(const BatchKey& o) const
     {
@@ -138,31 +150,32 @@ struct BatchKey {
         return method == o.method && norm == o.norm && nu1 == o.nu1 && nu2 == o.nu2 &&
                coarsest_min == o.coarsest_min && max_levels == o.max_levels &&
                inner_cycles == o.inner_cycles && tail_size == o.tail_size && unfused == o.unfused &&
-               smoother_w == o.smoother_w && tol == o.tol;
+               tiling == o.tiling && item_points == o.item_points && smoother_w == o.smoother_w &&
+               tol == o.tol;
     }
 };
 
-// A plan with its device tables in the handle's arena and the cycle graphs captured so far
-// (one per tail-size candidate). Valid while nothing else has carved the arena (epoch).
+// A plan with its level buffers and tables in the handle's arena, and the candidates' lists
+// and graphs built so far. Valid while nothing else has carved the arena (epoch).
 struct BatchCache : BatchCacheBase {
+    lap_handle h = nullptr;
     BatchKey key;
     BatchPlan P;
     uint64_t epoch = 0;
     size_t level_bytes = 0;
     BatchLevel<double>* lv64 = nullptr;
     BatchLevel<float>* lv32 = nullptr;
-    BatchItem* items = nullptr;
-    TailJob* jobs = nullptr;
-    TileItem* tiles = nullptr;
+    BatchItem* norm_items = nullptr;
     int *first = nullptr, *active = nullptr, *status = nullptr, *remaining = nullptr;
     long long* iters = nullptr;
     double *r0 = nullptr, *rnow = nullptr, *partials = nullptr;
-    bool fused = false;
-    std::vector<std::pair<cudaGraphExec_t, int64_t>> exec;  // graph, kernels it launches
+    std::vector<CandPlan> cands;  // indexed like the tuner's candidates
     ~BatchCache() override
     {
-        for (auto& e : exec)
-            if (e.first) cudaGraphExecDestroy(e.first);
+        for (CandPlan& c : cands) {
+            if (c.exec) cudaGraphExecDestroy(c.exec);
+            dev_free(h, c.dev, c.bytes);
+        }
     }
 };
 
@@ -180,23 +193,45 @@ BatchKey make_key(int count, const lap_grid* grids, double* const* psi_devs, con
     k.inner_cycles = p->inner_cycles;
     k.tail_size = p->tail_size;
     k.unfused = p->unfused;
+    k.tiling = p->tiling;
+    k.item_points = p->item_points;
     k.smoother_w = p->smoother_w;
     k.tol = p->tol;
     return k;
 }
 
-// The level descriptors, the work lists of every tail-size candidate, the arena carved for
-// them and the tables uploaded (stream-ordered on s, synchronised before returning).
+// The configurations a batched solve of these parameters tries (first = the default of each
+// knob): tail sizes, FP32 tilings (mixed solver, tiles allowed: the tile variants and one
+// kernel per pass), work-item sizes.
+void tuner_values(const lap_params* p, std::vector<int>* tails, std::vector<int>* tilings,
+                  std::vector<int>* items)
+{
+    const bool mixed = p->method == LAP_MG_MIXED;
+    *tails = tail_candidates(true, mixed, p->tail_size);
+    tilings->clear();
+    if (mixed && !p->unfused && fused32_supported(p->nu1, p->nu2) && p->tiling >= 0) {
+        for (int v = 1; v <= FUSED32_VARIANTS; ++v)
+            if ((p->tiling == 0 || p->tiling == v) && fused32_variant_supported(v, p->nu1, p->nu2))
+                tilings->push_back(v);
+        if (p->tiling == 0) tilings->push_back(0);
+    }
+    if (tilings->empty()) tilings->push_back(0);  // one kernel per pass
+    if (p->item_points > 0) *items = {p->item_points};
+    else *items = {BATCH_ITEM_POINTS, 2048, 32768};
+}
+
+// The level descriptors, the norm list, the arena carved for them (level buffers first) and
+// the tables uploaded (stream-ordered on s; pageable sources are staged before each copy
+// returns).
 std::unique_ptr<BatchCache> build_plan(lap_handle h, int count, const lap_grid* grids,
-                                       double* const* psi_devs, const lap_params* p, TailTuner& tuner,
-                                       cudaStream_t s)
+                                       double* const* psi_devs, const lap_params* p, cudaStream_t s)
 {
     auto C = std::make_unique<BatchCache>();
+    C->h = h;
     BatchPlan& P = C->P;
     const bool mixed = p->method == LAP_MG_MIXED;
     P.nlev.resize(count);
     P.base.resize(count);
-    // ---- level descriptors (buffers are carved below) ----
     for (int q = 0; q < count; ++q) {
         const lap_grid* g = &grids[q];
         const int L = mg_level_count(g->m, g->n, p->coarsest_min, p->max_levels);
@@ -238,25 +273,11 @@ std::unique_ptr<BatchCache> build_plan(lap_handle h, int count, const lap_grid* 
             n = (n - 1) / 2 + 1;
         }
     }
-    // ---- work lists: one set per tail-size candidate ----
-    std::vector<int> all_problems(count);
-    for (int q = 0; q < count; ++q) all_problems[q] = q;
-    C->fused = mixed && !p->unfused && fused32_supported(p->nu1, p->nu2);
-    for (int cand : tuner.cand) {
-        LevelLists L;
-        build_lists(L, P.items, P.jobs, all_problems, P.base, P.nlev, P.lv64, cand,
-                    C->fused ? &P.tiles : nullptr, p->nu1, p->nu2);
-        P.max_coarse_unknowns = std::max(P.max_coarse_unknowns, L.max_coarse);
-        P.cands.push_back(L);
-    }
-    const int n0 = (int)P.items.size();
     for (int q = 0; q < count; ++q) {
-        P.first_item.push_back((int)P.items.size() - n0);
-        add_items(P.items, P.base[q], grids[q].m, grids[q].n);
+        P.first_item.push_back((int)P.norm_items.size());
+        add_items(P.norm_items, P.base[q], grids[q].m, grids[q].n);
     }
-    P.first_item.push_back((int)P.items.size() - n0);
-    P.norm = {n0, (int)P.items.size() - n0};
-    // ---- memory: level buffers, descriptors, lists, state ----
+    P.first_item.push_back((int)P.norm_items.size());
     auto carve_all = [&](auto& cv) {
         for (int q = 0; q < count; ++q)
             for (int l = 0; l < P.nlev[q]; ++l) {
@@ -282,9 +303,7 @@ std::unique_ptr<BatchCache> build_plan(lap_handle h, int count, const lap_grid* 
             }
         C->lv64 = cv.template take<BatchLevel<double>>(P.lv64.size());
         C->lv32 = cv.template take<BatchLevel<float>>(P.lv32.size());
-        C->items = cv.template take<BatchItem>(P.items.size());
-        C->jobs = cv.template take<TailJob>(std::max<size_t>(1, P.jobs.size()));
-        C->tiles = cv.template take<TileItem>(std::max<size_t>(1, P.tiles.size()));
+        C->norm_items = cv.template take<BatchItem>(P.norm_items.size());
         C->first = cv.template take<int>(P.first_item.size());
         C->active = cv.template take<int>(count);
         C->status = cv.template take<int>(count);
@@ -292,7 +311,7 @@ std::unique_ptr<BatchCache> build_plan(lap_handle h, int count, const lap_grid* 
         C->iters = cv.template take<long long>(count);
         C->r0 = cv.template take<double>(count);
         C->rnow = cv.template take<double>(count);
-        C->partials = cv.template take<double>(std::max(1, P.norm.second));
+        C->partials = cv.template take<double>(std::max<size_t>(1, P.norm_items.size()));
     };
     Sizer sz;
     carve_all(sz);
@@ -300,18 +319,48 @@ std::unique_ptr<BatchCache> build_plan(lap_handle h, int count, const lap_grid* 
     carve_all(cv);
     C->epoch = h->arena_epoch;
     C->level_bytes = (size_t)((char*)C->lv64 - (char*)h->arena);
-    // pageable sources: each copy is staged before it returns
     ck(cudaMemcpyAsync(C->lv64, P.lv64.data(), P.lv64.size() * sizeof(P.lv64[0]), cudaMemcpyHostToDevice, s), "upload levels");
     ck(cudaMemcpyAsync(C->lv32, P.lv32.data(), P.lv32.size() * sizeof(P.lv32[0]), cudaMemcpyHostToDevice, s), "upload levels");
-    ck(cudaMemcpyAsync(C->items, P.items.data(), P.items.size() * sizeof(BatchItem), cudaMemcpyHostToDevice, s), "upload items");
-    if (!P.jobs.empty())
-        ck(cudaMemcpyAsync(C->jobs, P.jobs.data(), P.jobs.size() * sizeof(TailJob), cudaMemcpyHostToDevice, s), "upload jobs");
-    if (!P.tiles.empty())
-        ck(cudaMemcpyAsync(C->tiles, P.tiles.data(), P.tiles.size() * sizeof(TileItem), cudaMemcpyHostToDevice, s), "upload tiles");
+    ck(cudaMemcpyAsync(C->norm_items, P.norm_items.data(), P.norm_items.size() * sizeof(BatchItem), cudaMemcpyHostToDevice, s), "upload items");
     ck(cudaMemcpyAsync(C->first, P.first_item.data(), P.first_item.size() * sizeof(int), cudaMemcpyHostToDevice, s), "upload items");
-    C->exec.assign(P.cands.size(), {nullptr, 0});
     C->key = make_key(count, grids, psi_devs, p);
     return C;
+}
+
+// The lists of candidate c (configuration cfg), built and uploaded on first use; called
+// outside graph capture (it allocates and copies synchronously).
+CandPlan& ensure_candidate(BatchCache& C, int c, const BatchConfig& cfg, const lap_params* p,
+                           int count)
+{
+    if ((int)C.cands.size() <= c) C.cands.resize(c + 1);
+    CandPlan& K = C.cands[c];
+    if (K.dev) return K;
+    const BatchPlan& P = C.P;
+    std::vector<int> all_problems(count);
+    for (int q = 0; q < count; ++q) all_problems[q] = q;
+    std::vector<BatchItem> items;
+    std::vector<TailJob> jobs;
+    std::vector<TileItem> tiles;
+    build_lists(K.L, items, jobs, all_problems, P.base, P.nlev, P.lv64, cfg.tail,
+                cfg.tiles > 0 ? &tiles : nullptr, p->nu1, p->nu2, std::max(1, cfg.tiles), cfg.item);
+    // one allocation: items, jobs, tiles (each 256-byte aligned)
+    Sizer sz;
+    sz.take<BatchItem>(std::max<size_t>(1, items.size()));
+    sz.take<TailJob>(std::max<size_t>(1, jobs.size()));
+    sz.take<TileItem>(std::max<size_t>(1, tiles.size()));
+    K.bytes = sz.off;
+    K.dev = dev_alloc(C.h, K.bytes);
+    Carver cv(K.dev);
+    K.items = cv.take<BatchItem>(std::max<size_t>(1, items.size()));
+    K.jobs = cv.take<TailJob>(std::max<size_t>(1, jobs.size()));
+    K.tiles = cv.take<TileItem>(std::max<size_t>(1, tiles.size()));
+    if (!items.empty())
+        ck(cudaMemcpy(K.items, items.data(), items.size() * sizeof(BatchItem), cudaMemcpyHostToDevice), "upload items");
+    if (!jobs.empty())
+        ck(cudaMemcpy(K.jobs, jobs.data(), jobs.size() * sizeof(TailJob), cudaMemcpyHostToDevice), "upload jobs");
+    if (!tiles.empty())
+        ck(cudaMemcpy(K.tiles, tiles.data(), tiles.size() * sizeof(TileItem), cudaMemcpyHostToDevice), "upload tiles");
+    return K;
 }
 
 }  // namespace
@@ -339,16 +388,20 @@ extern "C" int lap_solve_batched(lap_handle h, int count, const lap_grid* grids,
             shape.push_back(grids[q].m);
             shape.push_back(grids[q].n);
         }
-        TailTuner& tuner = h->tail_tuners[tuner_key('B', p, shape)];
-        if (tuner.cand.empty()) tuner.init(tail_candidates(true, mixed, p->tail_size));
+        BatchTuner& tuner = h->batch_tuners[tuner_key('B', p, shape)];
+        if (tuner.cand.empty()) {
+            std::vector<int> tails, tilings, items;
+            tuner_values(p, &tails, &tilings, &items);
+            tuner.init(tails, tilings, items);
+        }
+        if (mixed && !p->unfused && fused32_supported(p->nu1, p->nu2))
+            ck(prepare_fused32(), "tile kernel attributes");
         // the plan of the previous call, if it was this batch and nothing has carved the arena
         // since; else a new one
         BatchCache* C = static_cast<BatchCache*>(h->batch_cache.get());
         if (!C || C->epoch != h->arena_epoch || !(C->key == make_key(count, grids, psi_devs, p))) {
-            h->batch_cache.reset();  // releases the old plan's graphs
-            if (mixed && !p->unfused && fused32_supported(p->nu1, p->nu2))
-                ck(prepare_fused32(), "tile kernel attributes");
-            h->batch_cache = build_plan(h, count, grids, psi_devs, p, tuner, s);
+            h->batch_cache.reset();  // releases the old plan's lists and graphs
+            h->batch_cache = build_plan(h, count, grids, psi_devs, p, s);
             C = static_cast<BatchCache*>(h->batch_cache.get());
         }
         try {
@@ -364,9 +417,6 @@ extern "C" int lap_solve_batched(lap_handle h, int count, const lap_grid* grids,
             ck(cudaMemsetAsync(C->iters, 0, count * sizeof(long long), s), "zero iterations");
             BatchLevel<double>* lv64 = C->lv64;
             BatchLevel<float>* lv32 = C->lv32;
-            BatchItem* items = C->items;
-            TailJob* jobs = C->jobs;
-            TileItem* tiles = C->tiles;
             int* first = C->first;
             int* active = C->active;
             int* status = C->status;
@@ -375,26 +425,26 @@ extern "C" int lap_solve_batched(lap_handle h, int count, const lap_grid* grids,
             double* r0 = C->r0;
             double* rnow = C->rnow;
             double* partials = C->partials;
-            auto list = [&](std::pair<int, int> r) { return BatchList{items + r.first, r.second}; };
-            const BatchList norm_list = list(P.norm);
+            const BatchList norm_list{C->norm_items, (int)P.norm_items.size()};
             const bool rel = p->norm == LAP_NORM_L2_REL;
-            // ---- one cycle (V-cycle(s) and stopping test) with tail-size candidate c ----
-            auto cycle = [&](int c, cudaStream_t st) {
-                const LevelLists& L = P.cands[c];
+            // ---- one cycle (V-cycle(s) and stopping test) with candidate c's lists ----
+            auto cycle = [&](const CandPlan& K, cudaStream_t st) {
+                const LevelLists& L = K.L;
+                auto list = [&](std::pair<int, int> r) { return BatchList{K.items + r.first, r.second}; };
                 if (mixed) {
                     for (int k = 0; k < p->inner_cycles; ++k) {
                         if (L.fused)
-                            enqueue_vcycle32_fused(list, L, lv32, active, jobs, tiles, *p, p->smoother_w,
+                            enqueue_vcycle32_fused(list, L, lv32, active, K.jobs, K.tiles, *p, p->smoother_w,
                                                    k == 0, st, k == p->inner_cycles - 1 ? lv64 : nullptr);
                         else
-                            enqueue_vcycle(list, L, lv32, active, jobs, *p, p->smoother_w, st);
+                            enqueue_vcycle(list, L, lv32, active, K.jobs, *p, p->smoother_w, st);
                     }
                     // fused: the level-0 ascents did psi += e except where a tail holds level 0
                     ck(launch_b_update(L.fused ? list(L.upd0) : norm_list, lv64, active, lv32, st),
                        "batched update");
                     ck(launch_b_sumsq(norm_list, lv64, active, partials, lv32, st, r0), "batched residual");
                 } else {
-                    enqueue_vcycle(list, L, lv64, active, jobs, *p, p->smoother_w, st);
+                    enqueue_vcycle(list, L, lv64, active, K.jobs, *p, p->smoother_w, st);
                     ck(launch_b_sumsq(norm_list, lv64, active, partials, nullptr, st), "batched residual");
                 }
                 ck(launch_b_converge(partials, first, count, active, r0, rnow, iters, status, remaining,
@@ -404,22 +454,24 @@ extern "C" int lap_solve_batched(lap_handle h, int count, const lap_grid* grids,
             ck(launch_b_sumsq(norm_list, lv64, active, partials, mixed ? lv32 : nullptr, s), "batched residual");
             ck(launch_b_converge(partials, first, count, active, r0, rnow, iters, status, remaining, 0,
                                  rel, p->tol, s), "batched convergence");
-            // one cycle per candidate as a graph, captured on the handle's stream when first
+            // one cycle of candidate c as a graph, captured on the handle's stream when first
             // used (kept with the plan for later calls) and replayed on the caller's
-            auto& exec = C->exec;
             auto launch_cycle = [&](int c) {
+                CandPlan& K = ensure_candidate(*C, c, tuner.cand[c], p, count);
+                h->last_batch = tuner.cand[c];
+                h->last_batch_tuned = tuner.done;
                 if (!h->use_graphs) {
-                    cycle(c, s);
+                    cycle(K, s);
                     return;
                 }
-                if (!exec[c].first) {
+                if (!K.exec) {
                     if (!h->capture)
                         ck(cudaStreamCreateWithFlags(&h->capture, cudaStreamNonBlocking), "capture stream");
                     const int64_t before = launches_now();
                     ck(cudaStreamBeginCapture(h->capture, cudaStreamCaptureModeThreadLocal), "begin capture");
                     cudaGraph_t g = nullptr;
                     try {
-                        cycle(c, h->capture);
+                        cycle(K, h->capture);
                     } catch (...) {
                         cudaStreamEndCapture(h->capture, &g);
                         if (g) cudaGraphDestroy(g);
@@ -427,14 +479,14 @@ extern "C" int lap_solve_batched(lap_handle h, int count, const lap_grid* grids,
                         throw;
                     }
                     ck(cudaStreamEndCapture(h->capture, &g), "end capture");
-                    exec[c].second = launches_now() - before;
-                    add_launches(-exec[c].second);
-                    const cudaError_t e = cudaGraphInstantiate(&exec[c].first, g, 0);
+                    K.kernels = launches_now() - before;
+                    add_launches(-K.kernels);
+                    const cudaError_t e = cudaGraphInstantiate(&K.exec, g, 0);
                     cudaGraphDestroy(g);
                     ck(e, "instantiate graph");
                 }
-                ck(cudaGraphLaunch(exec[c].first, s), "launch graph");
-                add_launches(exec[c].second);
+                ck(cudaGraphLaunch(K.exec, s), "launch graph");
+                add_launches(K.kernels);
             };
             int64_t done = 0;
             int left = count;
@@ -452,13 +504,14 @@ extern "C" int lap_solve_batched(lap_handle h, int count, const lap_grid* grids,
                     }
                     if (left < count) {
                         // problems already converged make the cycle cheaper: its time is not
-                        // comparable, so the best tail so far runs untimed
+                        // comparable, so the best configuration so far runs untimed
                         launch_cycle(tuner.best);
                         continue;
                     }
-                    // not tuned yet: time this cycle (the graph of c is captured before e0)
-                    if (h->use_graphs && !exec[c].first) {
-                        launch_cycle(c);  // first use captures and runs it once
+                    // not tuned yet: time this cycle (candidate c's graph captured before e0)
+                    const bool fresh = c >= (int)C->cands.size() || !C->cands[c].dev || !C->cands[c].exec;
+                    if (h->use_graphs && fresh) {
+                        launch_cycle(c);  // first use builds, captures and runs it once
                         ck(cudaStreamSynchronize(s), "stream sync");
                         continue;
                     }
@@ -492,5 +545,17 @@ extern "C" int lap_solve_batched(lap_handle h, int count, const lap_grid* grids,
             h->batch_cache.reset();  // a failed call leaves no plan behind
             throw;
         }
+    });
+}
+
+extern "C" int lap_last_batch_config(lap_handle h, int32_t* tail_size, int32_t* tiling,
+                                     int32_t* item_points, int32_t* tuned)
+{
+    return guarded([&] {
+        if (!h) fail(LAP_EINVAL, "handle is NULL");
+        if (tail_size) *tail_size = h->last_batch.tail;
+        if (tiling) *tiling = h->last_batch.tiles == 0 ? -1 : h->last_batch.tiles;
+        if (item_points) *item_points = h->last_batch.item;
+        if (tuned) *tuned = h->last_batch_tuned ? 1 : 0;
     });
 }

@@ -64,6 +64,91 @@ struct TailTuner {
     }
 };
 
+// One launch configuration of a batched V-cycle; none of its choices changes a computed value.
+struct BatchConfig {
+    int tail;   // small-level tail size (-1: none; see TailTuner)
+    int tiles;  // FP32 levels of the mixed solver: 0 = one kernel per pass (temporal depth 1),
+                // 1..FUSED32_VARIANTS = a level's whole descent / ascent per tile load (depth nu)
+                // with that tile variant (CTA size and region rows)
+    int item;   // interior points per work item of the per-pass kernels
+    bool operator==(const BatchConfig& o) const { return tail == o.tail && tiles == o.tiles && item == o.item; }
+};
+
+// Chooses a batched solve's configuration by timing real cycles, one knob at a time (a
+// coordinate search): stage 0 the small-level tail (the level-to-CTA mapping), stage 1 the
+// FP32 levels' temporal blocking and tile shape (mixed solver), stage 2 the work-item size of
+// the per-pass kernels (when some run). A stage's candidates are the best configuration so far
+// with that one knob changed; each is timed on one cycle in which every problem still runs
+// (the graph of a candidate is captured on an earlier cycle), and the fastest is kept. The
+// cycles being timed are real cycles of the solve, and all candidates give the same iterates.
+struct BatchTuner {
+    std::vector<BatchConfig> cand;
+    std::vector<double> ms;  // time per cycle, +inf = not timed yet
+    int best = 0;
+    int stage = 0;
+    int stage_begin = 0;
+    bool done = false;
+    std::vector<int> tails, tilings, items;  // the values each stage tries
+    void init(std::vector<int> tail_values, std::vector<int> tiling_values, std::vector<int> item_values)
+    {
+        tails = std::move(tail_values);
+        tilings = std::move(tiling_values);
+        items = std::move(item_values);
+        cand.clear();
+        ms.clear();
+        best = stage = stage_begin = 0;
+        done = false;
+        for (int t : tails) add(BatchConfig{t, tilings.front(), items.front()});
+        if (cand.size() <= 1) advance();
+    }
+    void add(BatchConfig c)
+    {
+        for (const BatchConfig& k : cand)
+            if (k == c) return;
+        cand.push_back(c);
+        ms.push_back(HUGE_VAL);
+    }
+    int next() const
+    {
+        if (done) return best;
+        for (size_t i = stage_begin; i < cand.size(); ++i)
+            if (ms[i] == HUGE_VAL) return (int)i;
+        return best;
+    }
+    void record(int i, double v)
+    {
+        if (done || i < 0 || i >= (int)cand.size() || !(v > 0.0)) return;
+        ms[i] = std::min(ms[i], v);
+        if (ms[best] == HUGE_VAL || ms[i] < ms[best]) best = i;
+        for (size_t k = stage_begin; k < cand.size(); ++k)
+            if (ms[k] == HUGE_VAL) return;
+        advance();
+    }
+    // The next stage with more than the current best to try, or done.
+    void advance()
+    {
+        while (stage < 2) {
+            ++stage;
+            stage_begin = (int)cand.size();
+            const BatchConfig b = cand[best];
+            const std::vector<int>& values = stage == 1 ? tilings : items;
+            for (int v : values) {
+                BatchConfig c = b;
+                if (stage == 1) c.tiles = v;
+                else c.item = v;
+                if (c == b) continue;
+                if (stage == 2 && b.tiles != 0 && c.item != b.item) {
+                    // with tiles the per-pass kernels only serve the tail's neighbours: skip
+                    continue;
+                }
+                add(c);
+            }
+            if ((int)cand.size() > stage_begin) return;
+        }
+        done = true;
+    }
+};
+
 extern thread_local std::string t_last_error;
 
 struct Error {
@@ -136,6 +221,9 @@ struct lap_handle_s {
     std::map<std::string, std::pair<cudaGraphExec_t, int64_t>> graphs;  // exec, kernels
     // Small-level tail sizes chosen by timing, per shape (see TailTuner)
     std::map<std::string, lap::TailTuner> tail_tuners;
+    std::map<std::string, lap::BatchTuner> batch_tuners;  // batched solves' configurations
+    lap::BatchConfig last_batch{0, 0, 0};  // the configuration the last batched cycle ran
+    bool last_batch_tuned = false;         // whether its tuner had finished
     cudaEvent_t ev[2] = {nullptr, nullptr};
     // y-line scratch of line relaxation: forward-elimination values and chunk ends (grown on
     // demand)
@@ -204,7 +292,8 @@ cudaEvent_t tuner_event(lap_handle h, int k);
 // 33..513, V(2,2) to 1e-10): FP64 145 / 140 / 140 / 145 ms at 2048 / 8192 / 16384 / 32768
 // points, the mixed solver 74 / 71 / 69 / 68 ms; 8192 for both.
 constexpr int BATCH_ITEM_POINTS = 8192;
-void add_items(std::vector<BatchItem>& items, int level_index, int m, int n);
+void add_items(std::vector<BatchItem>& items, int level_index, int m, int n,
+               int points = BATCH_ITEM_POINTS);
 
 // Per-level work lists of one V-cycle over a set of problems: [first, count) into the items
 // (fine, all, coarse) or into the tail jobs (tail).
@@ -213,6 +302,7 @@ struct LevelLists {
     std::vector<std::pair<int, int>> tiles;  // FP32 tile items of the fine lists (fused cycle)
     std::pair<int, int> upd0{0, 0};  // fused: level-0 items of the problems without level-0 tiles
     bool fused = false;
+    int tile_variant = 1;  // the fused FP32 levels' tile variant
     int levels = 0;
     int max_coarse = 0;
 };
@@ -227,7 +317,8 @@ int tail_start(const BatchLevel<double>* lv, int nlev, int tail_size);
 void build_lists(LevelLists& L, std::vector<BatchItem>& items, std::vector<TailJob>& jobs,
                  const std::vector<int>& who, const std::vector<int>& base,
                  const std::vector<int>& nlev, const std::vector<BatchLevel<double>>& lv,
-                 int tail_size, std::vector<TileItem>* tiles = nullptr, int nu1 = 0, int nu2 = 0);
+                 int tail_size, std::vector<TileItem>* tiles = nullptr, int nu1 = 0, int nu2 = 0,
+                 int tile_variant = 1, int item_points = BATCH_ITEM_POINTS);
 
 // One V-cycle over every active problem of L: descend (coarsest solves and tails start when
 // the descent reaches a problem's coarsest or tail level), then ascend; each problem sees
@@ -274,12 +365,12 @@ void enqueue_vcycle32_fused(ListFn list, const LevelLists& L, const BatchLevel<f
            "batched tail");
         if (l == L.levels - 1) break;
         ck(launch_b_down32(tiles + L.tiles[l].first, L.tiles[l].second, lv, active, p.nu1,
-                           l > 0 || first, gs, smoother_w, st),
+                           l > 0 || first, gs, smoother_w, st, L.tile_variant),
            "batched descent");
     }
     for (int l = L.levels - 2; l >= 0; --l)
         ck(launch_b_up32(tiles + L.tiles[l].first, L.tiles[l].second, lv, active, p.nu2, gs,
-                         smoother_w, st, l == 0 ? fold64 : nullptr),
+                         smoother_w, st, l == 0 ? fold64 : nullptr, L.tile_variant),
            "batched ascent");
 }
 

@@ -247,6 +247,12 @@ struct TileItem {
 // Whether nu1, nu2 sweeps fit the tile halos; tiles of a level: ntx x nty of tx x ty.
 bool fused32_supported(int nu1, int nu2);
 void fused32_tile(int m, int n, int nu1, int nu2, int* tx, int* ty, int* ntx, int* nty);
+// Batched tile variants (CTA size and region rows, see fused32_kernels.cu): 1..FUSED32_VARIANTS;
+// every variant computes the same values. 1 is the single-grid tiles' shape.
+constexpr int FUSED32_VARIANTS = 3;
+bool fused32_variant_supported(int variant, int nu1, int nu2);
+void fused32_tile_variant(int variant, int m, int n, int nu1, int nu2, int* tx, int* ty, int* ntx,
+                          int* nty);
 cudaError_t prepare_fused32();  // shared-memory limit of the tile kernels (outside capture)
 // Descent of level F: nu1 sweeps on u (F.u, or zeros), smoothed u -> F.r, C.q := restricted
 // residual, C.u := 0. Ascent: F.u := smoothed (F.r + P C.u) after nu2 sweeps.
@@ -259,11 +265,12 @@ cudaError_t launch_up32(const BatchLevel<float>& F, const BatchLevel<float>& C, 
                         int64_t psi_pitch = 0);
 // The same over tile items of many problems (the coarse level of item level l is l + 1).
 cudaError_t launch_b_down32(const TileItem* items, int count, const BatchLevel<float>* lv,
-                            const int* active, int nu1, bool zero_u, bool gs, double w, cudaStream_t s);
+                            const int* active, int nu1, bool zero_u, bool gs, double w, cudaStream_t s,
+                            int variant = 1);
 // lv64 (nullable): items' FP64 fields (same level indices) take psi += result instead.
 cudaError_t launch_b_up32(const TileItem* items, int count, const BatchLevel<float>* lv,
                           const int* active, int nu2, bool gs, double w, cudaStream_t s,
-                          const BatchLevel<double>* lv64 = nullptr);
+                          const BatchLevel<double>* lv64 = nullptr, int variant = 1);
 
 // ---- line relaxation (line_kernels.cu) --------------------------------------------
 // Constant-coefficient tridiagonal systems -alpha x_{k-1} + delta x_k - alpha x_{k+1} = b_k,
