@@ -58,6 +58,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--latency-solves", type=int, default=30, help="extra MG solves for p50/p99")
+    ap.add_argument("--serving-requests", type=int, default=10000,
+                    help="requests served across the load levels of the serving workload")
     return ap.parse_args()
 
 
@@ -611,8 +613,7 @@ def main():
     batched = batched_workload()
 
     # ---- serving: Poisson arrivals, continuous batching under a 40 GB budget ---------------
-    def serving_workload(seconds_per_load=3.0, burst=200):
-        import numpy as np
+    def serving_workload(total_requests=args.serving_requests, burst=400):
         rng = np.random.default_rng(wl.SEED_BASE + 4)
 
         def draw(count):
@@ -625,48 +626,63 @@ def main():
                 out.append((m, n, tol, method, int(rng.integers(1 << 30))))
             return out
 
+        def pct(v, q):
+            v = sorted(v)
+            return 1e3 * v[min(len(v) - 1, int(q * len(v)))] if v else None
+
         def run(reqs, rate):
             srv = b.Server(lap, hbm_budget=40 << 30, max_running=512, sor_sweeps=50)
             fields = [b.to_field(wl.random_ring(m, n, seed), dev) for m, n, _, _, seed in reqs]
             arrivals = np.cumsum(rng.exponential(1.0 / rate, size=len(reqs))) if rate else np.zeros(len(reqs))
             torch.cuda.synchronize(dev)
             t0 = time.perf_counter()
-            ids, lat, nxt = {}, [], 0
-            while len(lat) < len(reqs):
+            ids, lat, nxt, steps = {}, {"mg_mixed": [], "sor": []}, 0, 0
+            finished = 0
+            while finished < len(reqs):
                 now = time.perf_counter() - t0
                 while nxt < len(reqs) and arrivals[nxt] <= now:
                     m, n, tol, method, _ = reqs[nxt]
                     w = wl.w_opt_sor(m, n) if method == "sor" else 1.0
-                    ids[srv.submit(fields[nxt], 1.0, 1.0, method=method, w=w, tol=tol,
-                                   max_iter=10 ** 6)] = arrivals[nxt]
+                    rid = srv.submit(fields[nxt], 1.0, 1.0, method=method, w=w, tol=tol, max_iter=10 ** 6)
+                    ids[rid] = (arrivals[nxt], method)
                     nxt += 1
                 if not ids:
                     time.sleep(max(0.0, min(arrivals[nxt] - now, 0.01)))
                     continue
                 srv.step(stream)
+                steps += 1
                 done = time.perf_counter() - t0
-                for rid in list(ids):
-                    res = srv.poll(rid)
-                    if res is not None:
-                        if res["status"] != "converged":
-                            raise RuntimeError(f"served request did not converge: {res}")
-                        lat.append(done - ids.pop(rid))
+                # the step's completion list: the requests its convergence tests retired
+                for rid, res in srv.drain():
+                    if res["status"] != "converged":
+                        raise RuntimeError(f"served request did not converge: {res}")
+                    arrived, method = ids.pop(rid)
+                    lat[method].append(done - arrived)
+                    finished += 1
             total = time.perf_counter() - t0
             srv.close()
-            lat.sort()
+            del fields
+            both = lat["mg_mixed"] + lat["sor"]
             return {"requests": len(reqs), "seconds": total, "solves_per_s": len(reqs) / total,
-                    "p50_ms": 1e3 * lat[len(lat) // 2],
-                    "p99_ms": 1e3 * lat[min(len(lat) - 1, int(0.99 * len(lat)))]}
+                    "steps": steps, "p50_ms": pct(both, 0.5), "p99_ms": pct(both, 0.99),
+                    "by_class": {k: {"requests": len(v), "p50_ms": pct(v, 0.5), "p99_ms": pct(v, 0.99)}
+                                 for k, v in lat.items()}}
 
         sat = run(draw(burst), 0.0)
+        loads = (0.1, 0.3, 0.5, 0.7, 0.9, 1.2)
+        # equal arrival windows per load level, sized so that the levels together serve about
+        # total_requests requests
+        window = total_requests / (sat["solves_per_s"] * sum(loads))
         out = {"workload": "m, n log-uniform in [33, 2049] snapped to 2^k+1; tol log-uniform in "
                            "[1e-10, 1e-6]; 50% mixed-precision V(2,2) / 50% RB-SOR(w_opt, 50 sweeps "
-                           "per step); ring U[0,1]; 40 GB budget; host-side latency arrival -> result",
-               "saturation": sat, "loads": {}}
-        for load in (0.1, 0.3, 0.5, 0.7, 0.9, 1.2):
+                           "per step); ring U[0,1]; 40 GB budget; host-side latency arrival -> the "
+                           "step whose completion list holds the request",
+               "saturation": sat, "arrival_window_s": window, "loads": {}}
+        for load in loads:
             rate = load * sat["solves_per_s"]
-            count = max(20, int(rate * seconds_per_load))
+            count = max(20, int(rate * window))
             out["loads"][f"{load:.1f}"] = run(draw(count), rate)
+        out["requests_total"] = sat["requests"] + sum(v["requests"] for v in out["loads"].values())
         return out
 
     serving = serving_workload()

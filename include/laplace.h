@@ -211,6 +211,12 @@ int lap_server_step(lap_server s, void* stream, int* running, int* queued);
 /* 1 and *out filled if request id has finished (the request is then forgotten), 0 if not,
  * LAP_EINVAL for an unknown id. */
 int lap_server_poll(lap_server s, int64_t id, lap_result* out);
+/* The requests that have finished, oldest step first (within a step by id): up to capacity of
+ * them are written to ids[] and results[] (host arrays) and forgotten; *count receives how
+ * many. Each step reads the device-written list of the requests its convergence tests retired
+ * (one copy per step), so draining costs no per-request query. Requests already taken by
+ * lap_server_poll are skipped. */
+int lap_server_drain(lap_server s, int64_t* ids, lap_result* results, int capacity, int* count);
 
 /* ||r||_2 over interior nodes of the scaled residual of Eqs. 11-12,
  * r = fma(-d, psi, fma(beta^2, N + S, E + W) [+ q]), written to *out (host).

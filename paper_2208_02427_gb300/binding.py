@@ -98,6 +98,7 @@ def load():
                                             C.POINTER(c_int64)]),
             "lap_server_step": (C.c_int, [c_void_p, c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
             "lap_server_poll": (C.c_int, [c_void_p, c_int64, R]),
+            "lap_server_drain": (C.c_int, [c_void_p, C.POINTER(c_int64), R, C.c_int, C.POINTER(C.c_int)]),
             "lap_strerror": (C.c_char_p, [C.c_int]),
             "lap_last_error": (C.c_char_p, []),
             "lap_kernel_launches": (c_int64, []),
@@ -374,6 +375,22 @@ class Server:
         self._fields.pop(rid, None)
         return {"status": STATUS.get(res.status, res.status), "iters": res.iters, "r0": res.r0,
                 "r_final": res.r_final, "last_check": res.last_check}
+
+    def drain(self, capacity: int = 4096) -> list:
+        """(id, result dict) of the requests finished so far, oldest first (see lap_server_drain)."""
+        out = []
+        ids = (c_int64 * capacity)()
+        res = (Result * capacity)()
+        n = C.c_int(0)
+        while True:
+            _check(self._lib.lap_server_drain(self._h, ids, res, capacity, C.byref(n)))
+            for k in range(n.value):
+                r = res[k]
+                self._fields.pop(ids[k], None)
+                out.append((ids[k], {"status": STATUS.get(r.status, r.status), "iters": r.iters,
+                                     "r0": r.r0, "r_final": r.r_final, "last_check": r.last_check}))
+            if n.value < capacity:
+                return out
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:

@@ -488,13 +488,16 @@ __global__ void __launch_bounds__(BT)
 
 // Per problem: the norm from its items' partials (fixed order), then the stopping test.
 // first_item[p] .. first_item[p+1] are problem p's items in the norm list. mode 0 records
-// r0; mode 1 tests ||r|| <= tol r0 (rel) or <= tol (abs) and retires converged problems.
+// r0; mode 1 tests ||r|| <= tol r0 (rel) or <= tol (abs) and retires converged problems, and
+// (maxit) problems that have run their cycles. Retiring problems go to the completion list.
 __global__ void b_converge_kernel(const double* __restrict__ partials,
                                   const int* __restrict__ first_item, int count,
                                   int* __restrict__ active, double* __restrict__ r0,
                                   double* __restrict__ rnow, long long* __restrict__ iters,
                                   int* __restrict__ status, int* __restrict__ remaining, int mode,
-                                  int rel, double tol, const double* __restrict__ tolv)
+                                  int rel, double tol, const double* __restrict__ tolv,
+                                  const long long* __restrict__ maxit, Completion* __restrict__ done,
+                                  int* __restrict__ ndone)
 {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= count || !active[p]) return;
@@ -518,10 +521,15 @@ __global__ void b_converge_kernel(const double* __restrict__ partials,
         iters[p] += 1;  // cycles done while active (replayed graphs need no host counter)
         if (!isfinite(nr)) status[p] = 2;
         else if (rel ? nr <= tol * r0[p] : nr <= tol) status[p] = 0;
+        else if (maxit && iters[p] >= maxit[p]) status[p] = 1;
         else return;
     }
     active[p] = 0;
     atomicSub(remaining, 1);
+    if (done) {
+        const int k = atomicAdd(ndone, 1);
+        done[k] = Completion{p, status[p], iters[p], r0[p], nr};
+    }
 }
 
 }  // namespace
@@ -622,11 +630,12 @@ cudaError_t launch_b_update(const BatchList& l, const BatchLevel<double>* lv, co
 cudaError_t launch_b_converge(const double* partials, const int* first_item, int count, int* active,
                               double* r0, double* rnow, long long* iters, int* status,
                               int* remaining, int mode, bool rel, double tol, cudaStream_t s,
-                              const double* tolv)
+                              const double* tolv, const long long* maxit, Completion* done,
+                              int* ndone)
 {
     b_converge_kernel<<<(count + 127) / 128, 128, 0, s>>>(partials, first_item, count, active, r0,
                                                           rnow, iters, status, remaining, mode,
-                                                          rel ? 1 : 0, tol, tolv);
+                                                          rel ? 1 : 0, tol, tolv, maxit, done, ndone);
     note_launch();
     return cudaGetLastError();
 }

@@ -232,12 +232,23 @@ cudaError_t launch_b_sumsq(const BatchList& l, const BatchLevel<double>* lv, con
                            const double* r0 = nullptr);
 cudaError_t launch_b_update(const BatchList& l, const BatchLevel<double>* lv, const int* active,
                             const BatchLevel<float>* lv32, cudaStream_t s);
+// A problem that left the batch in a convergence test: its index, lap_status, cycles run and
+// norms (the serving loop's completion list).
+struct Completion {
+    int problem;
+    int status;
+    long long iters;
+    double r0, rnow;
+};
 // mode 0: record r0 (retire problems already converged); mode 1: count a cycle and test.
-// Problems with no items in the list are left alone; tolv (nullable) gives one tol each.
+// Problems with no items in the list are left alone; tolv (nullable) gives one tol each;
+// maxit (nullable): a problem that has run its maxit[p] cycles without converging retires
+// with LAP_MAXITER; done (nullable): every retiring problem is appended to done[*ndone++].
 cudaError_t launch_b_converge(const double* partials, const int* first_item, int count, int* active,
                               double* r0, double* rnow, long long* iters, int* status,
                               int* remaining, int mode, bool rel, double tol, cudaStream_t s,
-                              const double* tolv = nullptr);
+                              const double* tolv = nullptr, const long long* maxit = nullptr,
+                              Completion* done = nullptr, int* ndone = nullptr);
 
 // ---- the FP32 cycle's levels in two tile passes (fused32_kernels.cu) --------------
 // One tile of owned points [x0, x0 + tx) x [y0, y0 + ty) of level `level` of lv.

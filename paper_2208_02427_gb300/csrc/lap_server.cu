@@ -41,6 +41,7 @@ struct lap_server_s {
     lap_params mg{};  // nu1, nu2, coarsest_min, max_levels, smoother_w, inner_cycles
     char* stage = nullptr;
     size_t stage_bytes = 0;
+    std::deque<int64_t> completed;  // finished requests, in the order their steps ended
 };
 
 namespace {
@@ -224,6 +225,27 @@ extern "C" int lap_server_poll(lap_server S, int64_t id, lap_result* out)
     return 1;
 }
 
+extern "C" int lap_server_drain(lap_server S, int64_t* ids, lap_result* results, int capacity,
+                                int* count)
+{
+    return guarded([&] {
+        if (!S || !count || capacity < 0 || (capacity > 0 && (!ids || !results)))
+            fail(LAP_EINVAL, "NULL server, arrays or count, or negative capacity");
+        int n = 0;
+        while (n < capacity && !S->completed.empty()) {
+            const int64_t id = S->completed.front();
+            S->completed.pop_front();
+            auto it = S->reqs.find(id);
+            if (it == S->reqs.end()) continue;  // already taken by lap_server_poll
+            ids[n] = id;
+            results[n] = it->second.res;
+            S->reqs.erase(it);
+            ++n;
+        }
+        *count = n;
+    });
+}
+
 extern "C" int lap_server_step(lap_server S, void* stream, int* running, int* queued)
 {
     return guarded([&] {
@@ -305,12 +327,15 @@ extern "C" int lap_server_step(lap_server S, void* stream, int* running, int* qu
         P.norm = level0([](const SrvRequest&) { return true; }, &P.first_norm);
         // ---- stage: descriptors, items, per-request state ----
         std::vector<int> act(R, 1), stat(R, 1);
-        std::vector<long long> it(R);
+        std::vector<long long> it(R), cap(R);
         std::vector<double> r0(R), tolv(R);
         for (int q = 0; q < R; ++q) {
             it[q] = run[q]->steps;
             r0[q] = run[q]->r0;
             tolv[q] = run[q]->tol;
+            // iterations a request may run: V-cycles, or batches of sor_sweeps sweeps
+            cap[q] = run[q]->method == LAP_SOR_RB ? (run[q]->max_iter + S->sor_sweeps - 1) / S->sor_sweeps
+                                                  : run[q]->max_iter;
         }
         auto carve_stage = [&](auto& cv) {
             auto* lv64 = cv.template take<BatchLevel<double>>(P.lv64.size());
@@ -324,13 +349,16 @@ extern "C" int lap_server_step(lap_server S, void* stream, int* running, int* qu
             auto* status = cv.template take<int>(R);
             auto* remaining = cv.template take<int>(1);
             auto* iters = cv.template take<long long>(R);
+            auto* maxit = cv.template take<long long>(R);
             auto* dr0 = cv.template take<double>(R);
             auto* rnow = cv.template take<double>(R);
             auto* dtol = cv.template take<double>(R);
             auto* pinit = cv.template take<double>(std::max(1, P.init.second));
             auto* pnorm = cv.template take<double>(std::max(1, P.norm.second));
+            auto* done = cv.template take<Completion>(R);
+            auto* ndone = cv.template take<int>(1);
             return std::make_tuple(lv64, lv32, items, jobs, tiles, fi, fn, active, status, remaining,
-                                   iters, dr0, rnow, dtol, pinit, pnorm);
+                                   iters, maxit, dr0, rnow, dtol, pinit, pnorm, done, ndone);
         };
         Sizer sz;
         carve_stage(sz);
@@ -349,11 +377,12 @@ extern "C" int lap_server_step(lap_server S, void* stream, int* running, int* qu
         BatchItem* items;
         TailJob* jobs;
         TileItem* tiles;
-        int *fi, *fn, *active, *status, *remaining;
-        long long* iters;
+        int *fi, *fn, *active, *status, *remaining, *ndone;
+        long long *iters, *maxit;
         double *dr0, *rnow, *dtol, *pinit, *pnorm;
-        std::tie(lv64, lv32, items, jobs, tiles, fi, fn, active, status, remaining, iters, dr0, rnow,
-                 dtol, pinit, pnorm) = carve_stage(cv);
+        Completion* done;
+        std::tie(lv64, lv32, items, jobs, tiles, fi, fn, active, status, remaining, iters, maxit, dr0,
+                 rnow, dtol, pinit, pnorm, done, ndone) = carve_stage(cv);
         auto up = [&](void* dst, const void* src, size_t bytes) {
             if (bytes) ck(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st), "upload plan");
         };
@@ -369,13 +398,15 @@ extern "C" int lap_server_step(lap_server S, void* stream, int* running, int* qu
         up(status, stat.data(), R * sizeof(int));
         up(remaining, &R, sizeof(int));
         up(iters, it.data(), R * sizeof(long long));
+        up(maxit, cap.data(), R * sizeof(long long));
         up(dr0, r0.data(), R * sizeof(double));
         up(dtol, tolv.data(), R * sizeof(double));
+        ck(cudaMemsetAsync(ndone, 0, sizeof(int), st), "zero completions");
         auto list = [&](std::pair<int, int> r) { return BatchList{items + r.first, r.second}; };
         // ---- one iteration of every running request ----
         ck(launch_b_sumsq(list(P.init), lv64, active, pinit, lv32, st), "server residual");
         ck(launch_b_converge(pinit, fi, R, active, dr0, rnow, iters, status, remaining, 0, true, 0.0,
-                             st, dtol), "server convergence");
+                             st, dtol, maxit, done, ndone), "server convergence");
         enqueue_vcycle(list, P.mg64, lv64, active, jobs, S->mg, S->mg.smoother_w, st);
         for (int k = 0; k < S->mg.inner_cycles && P.mg32.levels; ++k) {
             if (P.mg32.fused)
@@ -392,37 +423,44 @@ extern "C" int lap_server_step(lap_server S, void* stream, int* running, int* qu
                 ck(launch_b_rb(list(P.sor), lv64, active, colour, false, 1.0, st, true), "server sweep");
         ck(launch_b_sumsq(list(P.norm), lv64, active, pnorm, lv32, st, dr0), "server residual");
         ck(launch_b_converge(pnorm, fn, R, active, dr0, rnow, iters, status, remaining, 1, true, 0.0,
-                             st, dtol), "server convergence");
-        auto down = [&](void* dst, const void* src, size_t bytes) {
-            ck(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, st), "download state");
-        };
-        std::vector<double> rn(R);
-        down(stat.data(), status, R * sizeof(int));
-        down(it.data(), iters, R * sizeof(long long));
-        down(r0.data(), dr0, R * sizeof(double));
-        down(rn.data(), rnow, R * sizeof(double));
+                             st, dtol, maxit, done, ndone), "server convergence");
+        // ---- the step's completion list (written by the convergence tests), read once ----
+        std::vector<Completion> fin(R);
+        int nfin = 0;
+        ck(cudaMemcpyAsync(&nfin, ndone, sizeof(int), cudaMemcpyDeviceToHost, st), "download completions");
+        ck(cudaMemcpyAsync(fin.data(), done, R * sizeof(Completion), cudaMemcpyDeviceToHost, st),
+           "download completions");
+        ck(cudaMemcpyAsync(r0.data(), dr0, R * sizeof(double), cudaMemcpyDeviceToHost, st), "download norms");
         ck(cudaStreamSynchronize(st), "stream sync");
-        // ---- retire finished requests ----
+        // ---- retire finished requests; the others ran exactly one iteration ----
+        std::vector<char> finished(R, 0);
+        std::sort(fin.begin(), fin.begin() + nfin,
+                  [&](const Completion& a, const Completion& b) { return run[a.problem]->id < run[b.problem]->id; });
+        for (int k = 0; k < nfin; ++k) {
+            const Completion& c = fin[k];
+            SrvRequest& r = *run[c.problem];
+            finished[c.problem] = 1;
+            r.steps = c.iters;
+            r.r0 = c.r0;
+            r.rnow = c.rnow;
+            r.res.status = c.status;
+            r.res.iters = r.method == LAP_SOR_RB ? c.iters * S->sor_sweeps : c.iters;
+            r.res.r0 = c.r0;
+            r.res.r_final = c.rnow;
+            r.res.last_check = c.r0 > 0 ? c.rnow / c.r0 : 0.0;
+            r.state = 2;
+            r.fresh = false;
+            if (r.bytes) pool_free(S, r.off, r.bytes);
+            S->completed.push_back(r.id);
+        }
         int still = 0;
         for (int q = 0; q < R; ++q) {
+            if (finished[q]) continue;
             SrvRequest& r = *run[q];
             r.fresh = false;
-            r.steps = it[q];
+            r.steps += 1;
             r.r0 = r0[q];
-            r.rnow = rn[q];
-            const int64_t done = r.method == LAP_SOR_RB ? r.steps * S->sor_sweeps : r.steps;
-            const bool capped = stat[q] == 1 && done >= r.max_iter;
-            if (stat[q] == 1 && !capped) {
-                ++still;
-                continue;
-            }
-            r.res.status = stat[q] == 1 ? LAP_MAXITER : stat[q];
-            r.res.iters = done;
-            r.res.r0 = r.r0;
-            r.res.r_final = r.rnow;
-            r.res.last_check = r.r0 > 0 ? r.rnow / r.r0 : 0.0;
-            r.state = 2;
-            if (r.bytes) pool_free(S, r.off, r.bytes);
+            ++still;
         }
         if (running) *running = still;
     });

@@ -122,3 +122,42 @@ def test_admission_respects_the_budget(b):
     assert e.value.code == -2
     tiny.close()
     lap.close()
+
+
+def test_completion_list_gives_the_same_results_as_polling(b):
+    """drain() reads the requests each step's convergence tests retired (a device-written
+    list, one copy per step): every request comes out exactly once, in step order, with the
+    result it has alone -- converged requests and ones stopped by their iteration cap."""
+    lap = b.Laplace()
+    srv = b.Server(lap, hbm_budget=64 << 20, max_running=5, sor_sweeps=K)
+    reqs = requests()
+    fields, ids = {}, {}
+    order, results = [], {}
+    pending = list(range(len(reqs)))
+    capped = {3: 4, 2: 2 * K}  # max_iter: V-cycles (a mixed request), or sweeps (an SOR one)
+    for step in range(20000):
+        for _ in range(2):
+            if pending:
+                k = pending.pop(0)
+                fields[k] = b.to_field(reqs[k]["psi"])
+                ids[srv.submit(fields[k], method=reqs[k]["method"], w=reqs[k]["w"],
+                               tol=reqs[k]["tol"], max_iter=capped.get(k, 200000))] = k
+        srv.step()
+        for rid, res in srv.drain(capacity=3):  # a small capacity: several calls per drain
+            assert rid in ids
+            order.append(rid)
+            results[ids[rid]] = res
+        if not pending and len(results) == len(reqs):
+            break
+    assert sorted(results) == list(range(len(reqs)))
+    assert len(order) == len(set(order))
+    for k, r in enumerate(reqs):
+        t = b.to_field(r["psi"])
+        g = lap.solve(t, method=r["method"], w=r["w"], tol=r["tol"], max_iter=capped.get(k, 200000),
+                      check_every=K if r["method"] == "sor" else 1)
+        assert results[k]["status"] == g["status"], (k, results[k], g)
+        assert results[k]["iters"] == g["iters"], (k, results[k], g)
+        assert np.array_equal(host(fields[k]), host(t)), k
+    assert srv.drain() == []
+    srv.close()
+    lap.close()
