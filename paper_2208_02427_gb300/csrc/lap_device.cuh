@@ -52,13 +52,52 @@ static __device__ __noinline__ double fmul_rare(double x, double y, double nzero
 {
     return __fma_rn(x, y, nzero);
 }
-static __device__ __noinline__ float to_float_rare(double x) { return __double2float_rn(x); }
-static __device__ __noinline__ double to_double_rare(float x) { return (double)x; }
+// The rare inputs of the FP32 <-> FP64 conversions below, in integer arithmetic from the
+// IEEE-754 formats (no FP64-pipe instruction: a conversion instruction on a path the
+// compiler evaluates for every point would cost one FP64 issue per point; measured).
+// x: |x| below FP32's normal range (including FP64 subnormals), or an FP32 overflow, or
+// infinite or NaN: the nearest FP32 value, ties to even (subnormal, zero or infinite); NaN
+// stays NaN (quiet).
+static __device__ __noinline__ float to_float_rare(double x)
+{
+    const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
+    const unsigned int sign = (unsigned int)(b >> 32) & 0x80000000u;
+    const int ex = (int)((b >> 52) & 0x7ff);
+    const unsigned long long frac = b & 0xfffffffffffffull;
+    if (ex == 0x7ff) return __uint_as_float(sign | 0x7f800000u | (frac ? 0x00400000u | (unsigned int)(frac >> 29) : 0u));
+    if (ex - 1023 + 127 >= 1) return __uint_as_float(sign | 0x7f800000u);  // overflow: infinity
+    if (ex == 0) return __uint_as_float(sign);  // FP64 subnormal or zero: far below 2^-150
+    // |x| = m 2^(ex - 1075) with a 53-bit m; in units of 2^-149 (the FP32 subnormal step)
+    // that is m / 2^sh, sh = 926 - ex >= 54 - 28 (ex <= 896 here)
+    const unsigned long long m = frac | (1ull << 52);
+    const int sh = 926 - ex;
+    if (sh >= 64) return __uint_as_float(sign);  // below half the smallest subnormal
+    unsigned int q = (unsigned int)(m >> sh);
+    const unsigned long long rem = m & ((1ull << sh) - 1), half = 1ull << (sh - 1);
+    if (rem > half || (rem == half && (q & 1u))) ++q;  // may carry to the smallest normal
+    return __uint_as_float(sign | q);
+}
+// f: an FP32 subnormal, infinity or NaN: (double)f exactly (NaN stays NaN, quiet).
+static __device__ __noinline__ double to_double_rare(float f)
+{
+    const unsigned int u = __float_as_uint(f);
+    const unsigned int sign = u & 0x80000000u, e = (u >> 23) & 0xffu, frac = u & 0x7fffffu;
+    if (e == 0xffu) {
+        const unsigned int fr = frac ? (frac | 0x00400000u) : 0u;
+        return __hiloint2double((int)(sign | 0x7ff00000u | (fr >> 3)), (int)(fr << 29));
+    }
+    if (frac == 0) return __hiloint2double((int)sign, 0);
+    // frac 2^-149 with the leading bit at position k: 2^(k - 149) (1 + the bits below k)
+    const int k = 31 - __clz(frac);
+    const unsigned long long mant = ((unsigned long long)frac << (52 - k)) & 0xfffffffffffffull;
+    const unsigned long long bits = ((unsigned long long)sign << 32) |
+                                    ((unsigned long long)(k + 874) << 52) | mant;
+    return __longlong_as_double((long long)bits);
+}
 
 // (double)f, exact, on the integer pipe when f is a normal FP32 number or +-0: the 8-bit
 // exponent is rebiased (127 -> 1023) and the 23-bit fraction becomes the top of the 52-bit
-// one. FP32 subnormals, infinities and NaN take the conversion instruction, which on GB300
-// issues on the FP64 pipe.
+// one. FP32 subnormals, infinities and NaN take to_double_rare (integer arithmetic too).
 __device__ __forceinline__ double to_double_exact(float f)
 {
     const unsigned int u = __float_as_uint(f);
@@ -108,21 +147,25 @@ __device__ __forceinline__ double neighbour_sum(const FmaOps& o, double w_, doub
 // x rounded to the nearest FP32 value (ties to even), bit-identical to __double2float_rn,
 // on the integer pipe when the result is a normal FP32 number or overflows: the 52-bit
 // fraction keeps its top 23 bits and rounds on the 29 below (a carry out of the fraction
-// raises the exponent, up to infinity); +-0 maps to +-0. FP32-subnormal results, infinities
-// and NaN take the conversion instruction. On GB300 that instruction competes with the FP64
-// arithmetic of the residual kernels for the FP64 pipe.
+// raises the exponent, up to infinity); +-0 maps to +-0. FP32-subnormal results, overflows
+// past the exponent range, infinities and NaN take to_float_rare (integer arithmetic too).
+// On GB300 the conversion instruction would compete with the FP64 arithmetic of the
+// residual kernels for the FP64 pipe.
 __device__ __forceinline__ float to_float_rn(double x)
 {
-    const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
-    const int e = (int)((b >> 52) & 0x7ff) - 1023 + 127;
+    // on the two 32-bit halves of x (formulated on one 64-bit integer, the compiler issued an
+    // FP64-pipe instruction per call; measured)
+    const unsigned int hi = (unsigned int)__double2hiint(x), lo = (unsigned int)__double2loint(x);
+    const int e = (int)((hi >> 20) & 0x7ffu) - 1023 + 127;
     if (e < 1 || e > 254) {
-        if ((b << 1) == 0) return __uint_as_float((unsigned int)(b >> 32));
+        if (((hi << 1) | lo) == 0) return __uint_as_float(hi);  // +-0
         return to_float_rare(x);
     }
-    unsigned int out = ((unsigned int)e << 23) | ((unsigned int)(b >> 29) & 0x7fffffu);
-    const unsigned int rem = (unsigned int)b & 0x1fffffffu;
+    // the top 23 of the 52 fraction bits: 20 from hi, 3 from lo; round on lo's low 29 bits
+    unsigned int out = ((unsigned int)e << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
+    const unsigned int rem = lo & 0x1fffffffu;
     if (rem > 0x10000000u || (rem == 0x10000000u && (out & 1u))) ++out;
-    out |= (unsigned int)(b >> 32) & 0x80000000u;
+    out |= hi & 0x80000000u;
     return __uint_as_float(out);
 }
 
