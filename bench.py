@@ -690,17 +690,23 @@ def main():
     # ---- end to end through the public API with host buffers -----------------------------
     pinned = torch.from_numpy(psi_host.copy()).pin_memory()
     out_host = torch.empty_like(pinned).pin_memory()
+    # one untimed pass: the library's device copy of the field and its graphs are made here
+    for kw in (sor_kw, mg_kw):
+        out_host.copy_(pinned)
+        lap.solve_host(out_host, H, H, stream=stream, **kw)
     torch.cuda.synchronize(dev)
     e2e_steps = max(1, args.steps)
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         for kw in (sor_kw, mg_kw):
             out_host.copy_(pinned)
-            lap.solve_host(out_host, H, H, work=work, stream=stream, **kw)
+            lap.solve_host(out_host, H, H, stream=stream, **kw)
     e2e_s = replicas.reduce_scalar(time.perf_counter() - t0, "max")
     field_bytes = M * N * 8
     e2e = {"value": replicas.reduce_scalar(2.0 * e2e_steps, "sum") / e2e_s, "unit": "solves/s",
-           "h2d_bytes_per_step": 2 * field_bytes, "d2h_bytes_per_step": 2 * field_bytes}
+           "h2d_bytes_per_step": 2 * field_bytes, "d2h_bytes_per_step": 2 * field_bytes,
+           "api": "lap_solve_host: pinned host field in, the library's copies and solve, "
+                  "host field out; host wall clock, the host-side reset of the input included"}
 
     cpu = None
     if rank == 0:

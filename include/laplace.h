@@ -158,6 +158,18 @@ int lap_workspace_bytes(const lap_grid* g, const lap_params* p, size_t* bytes);
 int lap_solve(lap_handle h, const lap_grid* g, double* psi_dev, const lap_params* p,
               lap_result* out, void* stream);
 
+/* lap_solve on a field in host memory, end to end: psi_host (n rows of host_pitch >= m
+ * doubles, row-major, i contiguous; ring and initial interior) is copied to a device field
+ * that the handle owns (row pitch g->pitch doubles; allocated against the budget on first
+ * use, grown when a larger grid comes, freed by lap_destroy), solved exactly as lap_solve
+ * solves it (same kernels, same iterates), and the last iterate is copied back into
+ * psi_host. The copies are enqueued on `stream`; pinned host memory lets them run at the
+ * link's rate, pageable memory works but stages through the driver. Synchronises `stream`
+ * before returning. LAP_EINVAL if psi_host is NULL, not 8-byte aligned or device memory,
+ * or host_pitch < m; on an error the content of psi_host is unspecified. */
+int lap_solve_host(lap_handle h, const lap_grid* g, double* psi_host, int64_t host_pitch,
+                   const lap_params* p, lap_result* out, void* stream);
+
 /* Solve `count` independent problems (grids[k], psi_devs[k], each its own size and
  * spacing) with the V-cycle: p->method LAP_MG or LAP_MG_MIXED, norm L2_REL or L2_ABS.
  * Every phase of a cycle is one launch over all problems that take part in it; each

@@ -82,6 +82,7 @@ def load():
             "lap_destroy": (None, [c_void_p]),
             "lap_workspace_bytes": (C.c_int, [G, P, C.POINTER(C.c_size_t)]),
             "lap_solve": (C.c_int, [c_void_p, G, c_void_p, P, R, c_void_p]),
+            "lap_solve_host": (C.c_int, [c_void_p, G, c_void_p, C.c_int64, P, R, c_void_p]),
             "lap_residual": (C.c_int, [c_void_p, G, c_void_p, c_void_p, C.POINTER(c_double), c_void_p]),
             "lap_smooth": (C.c_int, [G, c_void_p, c_void_p, c_double, C.c_int, c_void_p]),
             "lap_jacobi_sweep": (C.c_int, [G, c_void_p, c_void_p, c_void_p]),
@@ -266,18 +267,23 @@ class Laplace:
         return {"tail_size": v[0].value, "tiling": v[1].value, "item_points": v[2].value,
                 "tuned": bool(v[3].value)}
 
-    def solve_host(self, psi_host: torch.Tensor, dx=1.0, dy=1.0, work=None, stream=None, **kw):
-        """End-to-end solve of a host array: copy in, solve on the device, copy back
-        (into psi_host, in place). `work` is an optional device field to reuse."""
-        if work is None:
-            work = field(psi_host.shape[1], psi_host.shape[0], self.device)
-        s = stream if stream is not None else torch.cuda.current_stream(self.device)
-        with torch.cuda.stream(s):
-            work.copy_(psi_host, non_blocking=True)
-            info = self.solve(work, dx, dy, stream=s, **kw)
-            psi_host.copy_(work, non_blocking=True)
-        s.synchronize()
-        return info
+    def solve_host(self, psi_host: torch.Tensor, dx=1.0, dy=1.0, stream=None, align: int = 32,
+                   **kw):
+        """End-to-end solve of a host array through lap_solve_host: the library copies it to
+        a device field of its own (row pitch rounded up to `align`), solves and copies the
+        result back into psi_host, in place. Pinned host memory lets the copies overlap."""
+        t = psi_host
+        if (not isinstance(t, torch.Tensor) or t.is_cuda or t.dtype != torch.float64 or t.dim() != 2
+                or t.stride(1) != 1 or t.stride(0) < t.shape[1]):
+            raise TypeError("psi_host is a 2-D float64 host tensor with unit column stride")
+        m, n = t.shape[1], t.shape[0]
+        g = Grid(m, n, float(dx), float(dy), (m + align - 1) // align * align)
+        res = Result()
+        _check(self._lib.lap_solve_host(self._h, C.byref(g), _ptr(t), t.stride(0),
+                                        C.byref(params(**kw)), C.byref(res),
+                                        _stream(stream, self.device)))
+        return {"status": STATUS.get(res.status, res.status), "iters": res.iters, "r0": res.r0,
+                "r_final": res.r_final, "last_check": res.last_check}
 
     def residual(self, psi, dx=1.0, dy=1.0, q=None, stream=None) -> float:
         if q is not None:

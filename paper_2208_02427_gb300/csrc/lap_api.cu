@@ -334,6 +334,20 @@ const LineTables& line_setup(lap_handle h, const Field& f, const Coef& c, double
     if (x) {
         ck(prepare_line_kernels(line_smem_bytes(t)), "line kernel attributes");
         *scratch = nullptr;
+        const size_t bytes = std::max<size_t>(line_x_sync_words(f.n - 2) * sizeof(unsigned), 1 << 20);
+        if (bytes > h->lsync_bytes) {
+            // keep a timeout that the old block recorded
+            unsigned err = 0;
+            if (h->lsync) ck(cudaMemcpy(&err, h->lsync, sizeof err, cudaMemcpyDeviceToHost), "read line flags");
+            drop_graphs(h);
+            dev_free(h, h->lsync, h->lsync_bytes);
+            h->lsync = nullptr;
+            h->lsync_bytes = 0;
+            h->lsync = (unsigned*)dev_alloc(h, bytes);
+            h->lsync_bytes = bytes;
+            ck(cudaMemset(h->lsync, 0, sizeof(unsigned)), "clear line error");
+            if (err) ck(cudaMemcpy(h->lsync, &err, sizeof err, cudaMemcpyHostToDevice), "keep line error");
+        }
     } else {
         *scratch = line_scratch(h, t, line_scratch_pitch(f, direction));
     }
@@ -348,15 +362,34 @@ void line_half_sweep(lap_handle h, const Field& f, const Coef& c, double w, int 
     LineCoefs k;
     double* scratch = nullptr;
     const LineTables& t = line_setup(h, f, c, w, form, direction, &k, &scratch);
-    const int nlines = direction == 0 ? f.n - 2 : f.m - 2;
+    if (direction == 0) {  // both colours in one launch
+        ck(launch_line_x(f.p, f.pitch, f.n - 2, t, form, k, h->lsync, s), "x-line kernel");
+        return;
+    }
+    const int nlines = f.m - 2;
     const int64_t gp = line_scratch_pitch(f, direction);
     for (int first = 1; first <= 2; ++first) {
         const int count = first == 1 ? (nlines + 1) / 2 : nlines / 2;
-        if (direction == 0)
-            ck(launch_line_x(f.p, f.pitch, first, count, t, form, k, s), "x-line kernel");
-        else
-            ck(launch_line_scratch(f.p, f.pitch, 1, first, count, t, form, k, scratch, gp, s),
-               "y-line kernels");
+        ck(launch_line_scratch(f.p, f.pitch, 1, first, count, t, form, k, scratch, gp, s),
+           "y-line kernels");
+    }
+}
+
+// A wait of an x-line sweep that timed out (recorded on the device; the sweep went on, with
+// results that cannot be trusted) becomes an error of the next synchronising call on the
+// handle: the word is read once the stream is idle, and cleared.
+void check_line_waits(lap_handle h, cudaStream_t s)
+{
+    if (!h->lsync) return;
+    ck(cudaMemcpyAsync(h->pinned, h->lsync, sizeof(unsigned), cudaMemcpyDeviceToHost, s), "read line flags");
+    ck(cudaStreamSynchronize(s), "stream sync");
+    unsigned word = 0;
+    std::memcpy(&word, h->pinned, sizeof word);
+    if (word) {
+        ck(cudaMemsetAsync(h->lsync, 0, sizeof(unsigned), s), "clear line error");
+        ck(cudaStreamSynchronize(s), "stream sync");
+        fail(LAP_ECUDA, "an x-line sweep gave up waiting for a neighbouring line (its results are "
+                        "invalid)");
     }
 }
 
@@ -1328,6 +1361,8 @@ void lap_destroy(lap_handle h)
     for (cudaEvent_t e : h->ev)
         if (e) cudaEventDestroy(e);
     dev_free(h, h->lscratch, h->lscratch_bytes);
+    dev_free(h, h->hfield, h->hfield_bytes);
+    dev_free(h, h->lsync, h->lsync_bytes);
     dev_free(h, h->arena, h->arena_bytes);
     if (h->pinned) cudaFreeHost(h->pinned);
     delete h;
@@ -1343,6 +1378,40 @@ int lap_workspace_bytes(const lap_grid* g, const lap_params* p, size_t* bytes)
     });
 }
 
+namespace {
+
+// lap_solve after the handle, result and pointer checks
+void solve_device(lap_handle h, const lap_grid* g, double* psi_dev, const lap_params* p,
+                  lap_result* out, cudaStream_t stream)
+{
+    Solver sv{h, stream, Field{psi_dev, g->m, g->n, g->pitch}, make_coef(g->dx, g->dy), p, {}};
+    if (p->method == LAP_MG || p->method == LAP_MG_MIXED || p->method == LAP_MG_FP32) {
+        const int L = mg_level_count(g->m, g->n, p->coarsest_min, p->max_levels);
+        int m = g->m, n = g->n;
+        for (int l = 1; l < L; ++l) {
+            m = (m - 1) / 2 + 1;
+            n = (n - 1) / 2 + 1;
+        }
+        if ((int64_t)(m - 2) * (n - 2) > COARSE_MAX_UNKNOWNS)
+            fail(LAP_EUNSUPPORTED, "coarsest multigrid level has more than 1024 unknowns; "
+                                   "use sizes with (m-1), (n-1) divisible by more powers of two");
+    }
+    if ((p->method == LAP_GS_LEX || p->method == LAP_SOR_LEX) &&
+        (int64_t)g->m * g->n > lex_max_points())
+        fail(LAP_EUNSUPPORTED, "lexicographic methods hold the grid in one SM's shared memory: "
+                               "at most 28672 points");
+    if ((p->method == LAP_ADI || p->method == LAP_SLOR) &&
+        (g->m - 2 > LINE_MAX_N || g->n - 2 > LINE_MAX_N))
+        fail(LAP_EUNSUPPORTED, "ADI lines longer than 16383 unknowns");
+    const size_t need = work_bytes(g, p);
+    Carver cv(arena(h, need));
+    carve(cv, sv.w, g, p);
+    sv.run(out);
+    check_line_waits(h, stream);
+}
+
+}  // namespace
+
 int lap_solve(lap_handle h, const lap_grid* g, double* psi_dev, const lap_params* p,
               lap_result* out, void* stream)
 {
@@ -1353,29 +1422,48 @@ int lap_solve(lap_handle h, const lap_grid* g, double* psi_dev, const lap_params
         check_params(p);
         set_device(h);
         check_device_ptr(h, psi_dev, "psi");
-        Solver sv{h, (cudaStream_t)stream, Field{psi_dev, g->m, g->n, g->pitch}, make_coef(g->dx, g->dy), p, {}};
-        if (p->method == LAP_MG || p->method == LAP_MG_MIXED || p->method == LAP_MG_FP32) {
-            const int L = mg_level_count(g->m, g->n, p->coarsest_min, p->max_levels);
-            int m = g->m, n = g->n;
-            for (int l = 1; l < L; ++l) {
-                m = (m - 1) / 2 + 1;
-                n = (n - 1) / 2 + 1;
-            }
-            if ((int64_t)(m - 2) * (n - 2) > COARSE_MAX_UNKNOWNS)
-                fail(LAP_EUNSUPPORTED, "coarsest multigrid level has more than 1024 unknowns; "
-                                       "use sizes with (m-1), (n-1) divisible by more powers of two");
+        solve_device(h, g, psi_dev, p, out, (cudaStream_t)stream);
+    });
+}
+
+int lap_solve_host(lap_handle h, const lap_grid* g, double* psi_host, int64_t host_pitch,
+                   const lap_params* p, lap_result* out, void* stream)
+{
+    return guarded([&] {
+        if (!h) fail(LAP_EINVAL, "handle is NULL");
+        if (!out) fail(LAP_EINVAL, "result is NULL");
+        check_grid(g);
+        check_params(p);
+        if (!psi_host) fail(LAP_EINVAL, "psi_host is NULL");
+        if (((uintptr_t)psi_host) % 8) fail(LAP_EINVAL, "psi_host is not 8-byte aligned");
+        if (host_pitch < g->m) fail(LAP_EINVAL, "host_pitch must be >= m");
+        set_device(h);
+        cudaPointerAttributes a;
+        if (cudaPointerGetAttributes(&a, psi_host) != cudaSuccess) {
+            cudaGetLastError();
+            a.type = cudaMemoryTypeUnregistered;
         }
-        if ((p->method == LAP_GS_LEX || p->method == LAP_SOR_LEX) &&
-            (int64_t)g->m * g->n > lex_max_points())
-            fail(LAP_EUNSUPPORTED, "lexicographic methods hold the grid in one SM's shared memory: "
-                                   "at most 28672 points");
-        if ((p->method == LAP_ADI || p->method == LAP_SLOR) &&
-            (g->m - 2 > LINE_MAX_N || g->n - 2 > LINE_MAX_N))
-            fail(LAP_EUNSUPPORTED, "ADI lines longer than 16383 unknowns");
-        const size_t need = work_bytes(g, p);
-        Carver cv(arena(h, need));
-        carve(cv, sv.w, g, p);
-        sv.run(out);
+        if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged)
+            fail(LAP_EINVAL, "psi_host is device memory (use lap_solve)");
+        const size_t bytes = (size_t)g->n * (size_t)g->pitch * sizeof(double);
+        if (bytes > h->hfield_bytes) {
+            // the handle's graphs may hold the old field's address
+            drop_graphs(h);
+            dev_free(h, h->hfield, h->hfield_bytes);
+            h->hfield = nullptr;
+            h->hfield_bytes = 0;
+            h->hfield = (double*)dev_alloc(h, bytes);
+            h->hfield_bytes = bytes;
+        }
+        cudaStream_t s = (cudaStream_t)stream;
+        ck(cudaMemcpy2DAsync(h->hfield, (size_t)g->pitch * 8, psi_host, (size_t)host_pitch * 8,
+                             (size_t)g->m * 8, (size_t)g->n, cudaMemcpyHostToDevice, s),
+           "copy the field to the device");
+        solve_device(h, g, h->hfield, p, out, s);
+        ck(cudaMemcpy2DAsync(psi_host, (size_t)host_pitch * 8, h->hfield, (size_t)g->pitch * 8,
+                             (size_t)g->m * 8, (size_t)g->n, cudaMemcpyDeviceToHost, s),
+           "copy the field to the host");
+        ck(cudaStreamSynchronize(s), "stream sync");
     });
 }
 
@@ -1400,6 +1488,7 @@ int lap_residual(lap_handle h, const lap_grid* g, const double* psi_dev, const d
         ck(cudaMemcpyAsync(h->pinned, nrm + 1, 8, cudaMemcpyDeviceToHost, s), "copy norm");
         ck(cudaStreamSynchronize(s), "stream sync");
         *out = h->pinned[0];
+        check_line_waits(h, s);
     });
 }
 

@@ -229,6 +229,13 @@ struct lap_handle_s {
     // demand)
     double* lscratch = nullptr;
     size_t lscratch_bytes = 0;
+    // x-line sweeps: error word, item counter and row flags; one block of at least 1 MiB,
+    // allocated on first use and grown only for more than 262,140 lines
+    unsigned* lsync = nullptr;
+    size_t lsync_bytes = 0;
+    // device copy of the field of lap_solve_host (grown on demand)
+    double* hfield = nullptr;
+    size_t hfield_bytes = 0;
 };
 
 namespace lap {

@@ -318,9 +318,13 @@ struct LineCoefs {
 };
 size_t line_smem_bytes(const LineTables& t);
 cudaError_t prepare_line_kernels(size_t smem);
-// x-lines: rows first_line, first_line + 2, ... (count of them), one CTA each.
-cudaError_t launch_line_x(double* psi, int64_t pitch, int first_line, int count,
-                          const LineTables& t, int form, const LineCoefs& k, cudaStream_t s);
+// x-lines: a whole zebra half sweep of the nlines interior rows (both colours) in one launch.
+// sync: line_x_sync_words(nlines) words of device memory; word 0 is an error word that the
+// kernel sets if a wait for a neighbouring row timed out (never cleared by the launch), the
+// others are zeroed by the launch.
+size_t line_x_sync_words(int nlines);
+cudaError_t launch_line_x(double* psi, int64_t pitch, int nlines, const LineTables& t, int form,
+                          const LineCoefs& k, unsigned* sync, cudaStream_t s);
 // Lines first_line, first_line + 2, ... (count of them) through a scratch array, one thread
 // per (line, chunk): element k of line l at psi + l * sx + k * sa (y-lines: sa = pitch,
 // sx = 1; x-lines: sa = 1, sx = pitch). scratch holds line_y_scratch_doubles(t, gp)

@@ -25,9 +25,11 @@
 // plus 2 within K0 of a chunk's start. All tables depend on the line length and coefficients
 // only and are computed once on the host.
 //
-// x-lines (rows, contiguous): one CTA per line; b~ is built into shared memory with coalesced
-// loads, one warp runs the chunk recurrences (lane = chunk) and the separator solve (lane =
-// separator, register shuffles), and the CTA writes the line back coalesced. On GB300 each of
+// x-lines (rows, contiguous): a CTA works on one line at a time; b~ is built into shared memory
+// with coalesced loads, one warp runs the chunk recurrences (lane = chunk) and the separator
+// solve (lane = separator, register shuffles), and the CTA writes the line back coalesced. The
+// CTAs stay resident and take the lines of both zebra colours in order from a counter, so a
+// half sweep is one launch (line_x_kernel). On GB300 each of
 // an SM's four schedulers has its own FP64 unit (0.5 fma per clock; measured), and one warp's
 // dependent fma chain alone keeps it busy, so the six line CTAs that fit an SM's shared memory
 // are enough recurrence warps; the CTA's other warps shorten the load and store phases.
@@ -160,26 +162,28 @@ __device__ __forceinline__ void line_recurrences(const FmaOps& o, const LineTabl
 
 // Phase 1 of an x-line: b~ of the row into shared memory in chunk layout, by threads tid =
 // 0..nthr-1 (coalesced); each thread also adds the Dirichlet end terms of the entries it wrote.
+// Loads go to L2 (ld.global.cg): rows of the first colour are written by other CTAs of the same
+// launch, and L1 is not coherent between SMs.
 template <int FORM>
 __device__ __forceinline__ void line_x_load(const FmaOps& o, const LineTables& t, double* sm,
                                             const double* row, int64_t pitch, double bnd, double c1,
                                             int tid, int nthr)
 {
     const int N = t.N, L = t.L, Ls = t.stride;
-    const double* __restrict__ up = row - pitch;
-    const double* __restrict__ dn = row + pitch;
+    const double* up = row - pitch;
+    const double* dn = row + pitch;
 #pragma unroll LX_UNROLL
     for (int k = 1 + tid; k <= N; k += nthr) {
-        const double nb = fadd(o, up[k], dn[k]);
-        const double b = FORM == 1 ? __fma_rn(c1, row[k], nb) : nb;
+        const double nb = fadd(o, __ldcg(up + k), __ldcg(dn + k));
+        const double b = FORM == 1 ? __fma_rn(c1, __ldcg(row + k), nb) : nb;
         const int g = k - 1, p = g / (L + 1);
         sm[p * Ls + (g - p * (L + 1))] = b;
     }
-    if (tid == 0) sm[0] = __fma_rn(bnd, row[0], sm[0]);
+    if (tid == 0) sm[0] = __fma_rn(bnd, __ldcg(row), sm[0]);
     if (tid == (N - 1) % nthr) {
         const int g = N - 1, p = g / (L + 1);
         double* e = sm + p * Ls + (g - p * (L + 1));
-        *e = __fma_rn(bnd, row[N + 1], *e);
+        *e = __fma_rn(bnd, __ldcg(row + N + 1), *e);
     }
 }
 
@@ -195,31 +199,83 @@ __device__ __forceinline__ void line_x_store(const FmaOps& o, const LineTables& 
         const int g = k - 1, p = g / (L + 1), q = g - p * (L + 1);
         const double v = sm[p * Ls + q];
         if (FORM == 0)
-            row[k] = __fma_rn(t.sc[q], v, fmul(o, omw, row[k]));
+            row[k] = __fma_rn(t.sc[q], v, fmul(o, omw, __ldcg(row + k)));
         else
             row[k] = fmul(o, t.sc[q], v);
     }
 }
 
-// One CTA per line, the three phases separated by CTA barriers. (A persistent variant with two
-// line buffers per CTA, warp 0 running the recurrences of one line while the other warps wrote
-// back and loaded the neighbouring lines, measured no faster: the recurrences' dependent fma
-// chain shares its scheduler's FP64 unit with the other warps' independent FP64 operations.)
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release(unsigned* p, unsigned v)
+{
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Wait until *flag != 0, at most LX_SPIN_LIMIT polls (seconds); after that the error word is
+// set and the caller goes on: the host reports the error, nothing hangs.
+constexpr unsigned LX_SPIN_LIMIT = 1u << 24;
+__device__ __forceinline__ void wait_flag(const unsigned* flag, unsigned* err)
+{
+    for (unsigned it = 0; it < LX_SPIN_LIMIT; ++it) {
+        if (ld_acquire(flag) != 0u) return;
+        __nanosleep(128);
+    }
+    atomicExch(err, 1u);
+}
+
+// A whole x-line half sweep (both zebra colours) in one launch of resident CTAs. Work item
+// i < nodd is row 1 + 2i (first colour), item nodd + i is row 2 + 2i (second colour); a CTA
+// claims items from a counter in that order and runs the three phases on each, separated by
+// CTA barriers. A second-colour row needs its two first-colour neighbours finished: they were
+// claimed a colour earlier by CTAs that are running, so the wait ends (almost always at once).
+// A first-colour row is published by a release store of its flag after the CTA's barrier.
+// Against one launch per colour this removes the second launch's wait for the first's last
+// CTAs (2048 lines on 912 CTA slots at 4097^2 left a third of the last wave idle) and lets
+// CTAs at different phases overlap. sync: [0] error word (kept until the host reads it),
+// [1] item counter, [2 + r] flag of row r; [1 ..] zeroed before each launch.
 template <int FORM>
 __global__ void __launch_bounds__(LX_THREADS)
-    line_x_kernel(double* __restrict__ psi, int64_t pitch, int first_line, const LineTables t,
-                  double bnd, double c1, double omw)
+    line_x_kernel(double* __restrict__ psi, int64_t pitch, int nlines, const LineTables t,
+                  double bnd, double c1, double omw, unsigned* __restrict__ sync)
 {
     const FmaOps o = load_fma_ops();
     extern __shared__ double sm[];
-    double* row = psi + (int64_t)(first_line + 2 * (int)blockIdx.x) * pitch;
+    __shared__ int s_item;
+    const int nodd = (nlines + 1) / 2;
     c1 = in_reg(o, c1);
     omw = in_reg(o, omw);
-    line_x_load<FORM>(o, t, sm, row, pitch, bnd, c1, threadIdx.x, LX_THREADS);
-    __syncthreads();
-    if (threadIdx.x < 32) line_recurrences(o, t, sm, threadIdx.x);
-    __syncthreads();
-    line_x_store<FORM>(o, t, sm, row, omw, threadIdx.x, LX_THREADS);
+    unsigned* const done = sync + 2;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const int item = (int)atomicAdd(sync + 1, 1u);
+            if (item >= nodd && item < nlines) {
+                const int r = 2 + 2 * (item - nodd);
+                wait_flag(done + r - 1, sync);
+                if (r + 1 <= nlines) wait_flag(done + r + 1, sync);
+            }
+            s_item = item;
+        }
+        __syncthreads();
+        const int item = s_item;
+        if (item >= nlines) return;
+        const int r = item < nodd ? 1 + 2 * item : 2 + 2 * (item - nodd);
+        double* row = psi + (int64_t)r * pitch;
+        line_x_load<FORM>(o, t, sm, row, pitch, bnd, c1, threadIdx.x, LX_THREADS);
+        __syncthreads();
+        if (threadIdx.x < 32) line_recurrences(o, t, sm, threadIdx.x);
+        __syncthreads();
+        line_x_store<FORM>(o, t, sm, row, omw, threadIdx.x, LX_THREADS);
+        __syncthreads();
+        if (threadIdx.x == 0 && item < nodd) {
+            __threadfence();
+            st_release(done + r, 1u);
+        }
+    }
 }
 
 // ---- lines through a scratch array: lane = line --------------------------------------
@@ -444,17 +500,26 @@ cudaError_t prepare_line_kernels(size_t smem)
     return e;
 }
 
-cudaError_t launch_line_x(double* psi, int64_t pitch, int first_line, int count,
-                          const LineTables& t, int form, const LineCoefs& k, cudaStream_t s)
+size_t line_x_sync_words(int nlines) { return (size_t)nlines + 4; }
+
+cudaError_t launch_line_x(double* psi, int64_t pitch, int nlines, const LineTables& t, int form,
+                          const LineCoefs& k, unsigned* sync, cudaStream_t s)
 {
-    if (count <= 0) return cudaSuccess;
+    if (nlines <= 0) return cudaSuccess;
     const size_t smem = line_smem_bytes(t);
-    cudaError_t err = prepare_line_kernels(smem);
-    if (err != cudaSuccess) return err;
+    cudaError_t e = prepare_line_kernels(smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &per_sm, form == 0 ? line_x_kernel<0> : line_x_kernel<1>, LX_THREADS, smem);
+    if (e != cudaSuccess) return e;
+    const int grid = std::min(nlines, std::max(1, per_sm) * device_sms());
+    e = cudaMemsetAsync(sync + 1, 0, (line_x_sync_words(nlines) - 1) * sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
     if (form == 0)
-        line_x_kernel<0><<<count, LX_THREADS, smem, s>>>(psi, pitch, first_line, t, k.bnd, k.c1, k.omw);
+        line_x_kernel<0><<<grid, LX_THREADS, smem, s>>>(psi, pitch, nlines, t, k.bnd, k.c1, k.omw, sync);
     else
-        line_x_kernel<1><<<count, LX_THREADS, smem, s>>>(psi, pitch, first_line, t, k.bnd, k.c1, k.omw);
+        line_x_kernel<1><<<grid, LX_THREADS, smem, s>>>(psi, pitch, nlines, t, k.bnd, k.c1, k.omw, sync);
     note_launch();
     return cudaGetLastError();
 }

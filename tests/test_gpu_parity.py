@@ -408,12 +408,37 @@ def test_solves_are_deterministic_and_count_launches(lap, b, big):
 
 
 def test_host_buffer_solve_equals_device_solve(lap, b):
-    psi = wl.sine_edges(257, 129, seed=3)
-    pinned = torch.from_numpy(psi.copy()).pin_memory()
-    g1 = lap.solve_host(pinned, method="mg", tol=1e-10)
-    t = b.to_field(psi)
-    g2 = lap.solve(t, method="mg", tol=1e-10)
-    assert g1["iters"] == g2["iters"] and np.array_equal(pinned.numpy(), host(t))
+    """lap_solve_host (host field in, the library's copies, host field out) gives lap_solve's
+    iterates bit for bit: pinned and pageable memory, a host row stride wider than the grid,
+    the library's device field grown for a larger grid and reused for a smaller one."""
+    for shape, kw in (((257, 129), dict(method="mg", tol=1e-10)),
+                      ((513, 257), dict(method="sor", w=1.9, max_iter=40, check_every=10)),
+                      ((65, 33), dict(method="adi", w=1.3, max_iter=3)),
+                      ((129, 65), dict(method="mg_mixed", tol=1e-10))):
+        psi = wl.sine_edges(*shape, seed=3 + shape[0])
+        t = b.to_field(psi)
+        want = lap.solve(t, **kw)
+        for pin in (True, False):
+            wide = torch.zeros((shape[1], shape[0] + 7), dtype=torch.float64)
+            if pin:
+                wide = wide.pin_memory()
+            hv = wide[:, :shape[0]]
+            hv.copy_(torch.from_numpy(psi))
+            got = lap.solve_host(hv, **kw)
+            assert (got["iters"], got["status"], got["r_final"]) == \
+                (want["iters"], want["status"], want["r_final"]), (shape, pin)
+            assert np.array_equal(hv.numpy(), host(t)), (shape, pin)
+            assert np.all(wide[:, shape[0]:].numpy() == 0.0)  # the padding is not written
+    with pytest.raises(TypeError):
+        lap.solve_host(b.field(33, 33), method="mg")
+    # a device pointer given as the host field is refused by the library itself
+    d = b.field(33, 33)
+    g = b.Grid(33, 33, 1.0, 1.0, d.stride(0))
+    r = b.Result()
+    rc = lap._lib.lap_solve_host(lap._h, b.C.byref(g), b.c_void_p(d.data_ptr()), d.stride(0),
+                                 b.C.byref(b.params(method="mg")), b.C.byref(r),
+                                 b.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert b.ERRORS.get(rc) == "EINVAL"
 
 
 @pytest.mark.parametrize("kw", [
