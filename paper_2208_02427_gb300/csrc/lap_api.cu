@@ -894,6 +894,8 @@ struct Solver {
     {
         if (p->norm != LAP_NORM_MAXDELTA) return false;
         if (p->method == LAP_GS_LEX || p->method == LAP_SOR_LEX) return true;
+        if (p->method == LAP_ADI || p->method == LAP_SLOR)
+            return (int64_t)f.m * f.n <= 4096 && solve_lines_cta_smem(f.m, f.n) <= 200 * 1024;
         return (p->method == LAP_JACOBI || p->method == LAP_GS_RB || p->method == LAP_SOR_RB) &&
                (int64_t)f.m * f.n <= 4096;
     }
@@ -1216,9 +1218,15 @@ struct Solver {
             st.last_check = NAN;
             st.last_nr = r0;
             ck(cudaMemcpyAsync(w.loop, &st, sizeof st, cudaMemcpyHostToDevice, s), "upload loop state");
-            const int kind = p->method == LAP_JACOBI ? 0 : (p->method == LAP_GS_RB || p->method == LAP_SOR_RB ? 1 : 2);
-            const bool gs = p->method == LAP_GS_RB || p->method == LAP_GS_LEX;
-            ck(launch_solve_cta(f, c, kind, gs, w.wslot, w.loop, s), "one-CTA solve kernel");
+            if (p->method == LAP_ADI || p->method == LAP_SLOR) {
+                ck(launch_solve_lines_cta(f, c, p->method == LAP_ADI, p->line_form == LAP_FORM_B,
+                                          w.wslot, w.loop, s),
+                   "one-CTA line solve kernel");
+            } else {
+                const int kind = p->method == LAP_JACOBI ? 0 : (p->method == LAP_GS_RB || p->method == LAP_SOR_RB ? 1 : 2);
+                const bool gs = p->method == LAP_GS_RB || p->method == LAP_GS_LEX;
+                ck(launch_solve_cta(f, c, kind, gs, w.wslot, w.loop, s), "one-CTA solve kernel");
+            }
             ck(cudaMemcpyAsync(h->pinned, w.loop, sizeof st, cudaMemcpyDeviceToHost, s), "copy loop state");
             ck(cudaStreamSynchronize(s), "stream sync");
             std::memcpy(&st, h->pinned, sizeof st);

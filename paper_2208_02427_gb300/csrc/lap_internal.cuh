@@ -164,6 +164,11 @@ cudaError_t launch_lex_sweeps(const Field& f, const Coef& c, bool gs, double w, 
 // after every st->steps iterations, up to st->max_iter): kind 0 Jacobi (2 m n doubles of
 // shared memory), 1 red-black, 2 lexicographic (m n doubles); gs or SOR with {w, 1 - w}
 // from wslot. Reads st->k, steps, max_iter, tol, last_check; writes k, status, last_check.
+// Zebra SLOR (adi = false) or ADI in one CTA with the field in shared memory, periods until
+// the stopping rule (MAXDELTA) holds; LoopState as for launch_solve_cta.
+size_t solve_lines_cta_smem(int m, int n);
+cudaError_t launch_solve_lines_cta(const Field& f, const Coef& c, bool adi, int form,
+                                   const double* wslot, LoopState* st, cudaStream_t s);
 cudaError_t launch_solve_cta(const Field& f, const Coef& c, int kind, bool gs, const double* wslot,
                              LoopState* st, cudaStream_t s);
 

@@ -478,6 +478,150 @@ __global__ void __launch_bounds__(32 * LY_WARPS)
     }
 }
 
+// ---- a whole line-relaxation solve in one CTA (small grids, the paper's stopping rule) ----
+// On grids of a few thousand points (the paper's 25 x 17 chamber) every launch costs more than
+// the work it does. This kernel keeps the field in shared memory and runs whole check periods
+// of zebra SLOR (x-lines) or ADI (x-lines then y-lines), forms A and B, until the largest
+// change of an iteration, max |psi^{k+1} - psi^k| (Eq. 16), is <= tol; a thread solves one
+// line at a time by the Thomas algorithm. The pivots of the constant-coefficient line matrix
+// depend on its length and coefficients only: 1/den_i and alpha/den_i are tabulated once per
+// solve, so a step of the elimination is an fma and a multiply (an FP64 division costs about
+// ten dependent FP64 operations on this GPU).
+constexpr int LC_THREADS = 256;
+
+// Tables of one direction: inv[i] = 1 / den_i, cc[i] = coupling / den_i, den_0 = d,
+// den_i = d - coupling^2 / den_{i-1}.
+__device__ __forceinline__ void cta_line_tables(int len, double d, double coupling, double* inv,
+                                                double* cc)
+{
+    double den = d;
+    for (int i = 0; i < len; ++i) {
+        if (i) den = d - coupling * (coupling / den);
+        inv[i] = 1.0 / den;
+        cc[i] = coupling / den;
+    }
+}
+
+template <int FORM>
+__device__ __forceinline__ void cta_relax_line(const FmaOps& o, double* u, int m, int dir, int line,
+                                               int len, double cross, double c1, double w,
+                                               double coupling, const double* inv, const double* cc,
+                                               double* dp)
+{
+    // element k (0..len+1) of the line, and of its two neighbouring lines
+    auto at = [&](int l, int k) -> double& { return dir == 0 ? u[l * m + k] : u[k * m + l]; };
+    double prev = 0.0;
+    for (int k = 1; k <= len; ++k) {
+        const double nb = fadd(o, at(line - 1, k), at(line + 1, k));
+        // form A: cross (P + Q); form B: d (1 - w) psi + w cross (P + Q), here as
+        // (w cross) (c1 psi + P + Q) with c1 = d (1 - w) / (w cross); `cross` is w cross there
+        double r = FORM == 0 ? fmul(o, cross, nb) : fmul(o, cross, __fma_rn(c1, at(line, k), nb));
+        if (k == 1) r = __fma_rn(coupling, at(line, 0), r);
+        if (k == len) r = __fma_rn(coupling, at(line, len + 1), r);
+        prev = fmul(o, __fma_rn(coupling, prev, r), inv[k - 1]);
+        dp[k - 1] = prev;
+    }
+    // back substitution, then the relaxed output (form A: psi + w (x - psi); form B: x)
+    double x = 0.0;
+    for (int i = len - 1; i >= 0; --i) {
+        x = i == len - 1 ? dp[i] : __fma_rn(cc[i], x, dp[i]);
+        double& p = at(line, i + 1);
+        p = FORM == 0 ? __fma_rn(w, fadd(o, x, -p), p) : x;
+    }
+}
+
+// One zebra half sweep in direction dir: odd lines, then even lines, each line by one thread.
+template <int FORM>
+__device__ __forceinline__ void cta_half_sweep(const FmaOps& o, double* u, int m, int n, int dir,
+                                               double b2, double c1, double w, const double* inv,
+                                               const double* cc, double* work, int wlen)
+{
+    const int lines = dir == 0 ? n - 2 : m - 2, len = dir == 0 ? m - 2 : n - 2;
+    const double off = dir == 0 ? 1.0 : b2, cross = dir == 0 ? b2 : 1.0;
+    const double coupling = FORM == 0 ? off : w * off;
+    const double rcross = FORM == 0 ? cross : w * cross;
+    for (int first = 1; first <= 2; ++first) {
+        for (int l = first + 2 * (int)threadIdx.x; l <= lines; l += 2 * LC_THREADS)
+            cta_relax_line<FORM>(o, u, m, dir, l, len, rcross, c1, w, coupling, inv, cc,
+                                 work + (size_t)threadIdx.x * wlen);
+        __syncthreads();
+    }
+}
+
+template <bool ADI, int FORM>
+__global__ void __launch_bounds__(LC_THREADS)
+    solve_lines_cta_kernel(double* __restrict__ psi, int m, int n, int64_t pitch, double b2, double d,
+                           const double* __restrict__ wslot, LoopState* __restrict__ st)
+{
+    extern __shared__ double lsm[];
+    const FmaOps o = load_fma_ops();
+    const int wlen = max(m, n);
+    double* u = lsm;                  // the field, dense m x n
+    double* prev = u + m * n;         // the field before the period's last iteration
+    double* tabs = prev + m * n;      // x-line tables (inv, cc), then y-line tables
+    double* work = tabs + 4 * wlen;   // forward values: wlen doubles per thread that has a line
+    const double w = wslot[0];
+    // form B's right-hand side factor d (1 - w) / (w cross), per direction
+    const double c1x = FORM == 1 ? d * (1.0 - w) / (w * b2) : 0.0;
+    const double c1y = FORM == 1 ? d * (1.0 - w) / w : 0.0;
+    const int tid = threadIdx.x;
+    for (int k = tid; k < m * n; k += LC_THREADS) u[k] = psi[(int64_t)(k / m) * pitch + k % m];
+    if (tid == 0) cta_line_tables(m - 2, d, FORM == 0 ? 1.0 : w, tabs, tabs + wlen);
+    if (tid == 32 && ADI) cta_line_tables(n - 2, d, FORM == 0 ? b2 : w * b2, tabs + 2 * wlen, tabs + 3 * wlen);
+    __shared__ unsigned long long red[LC_THREADS / 32];
+    __shared__ int go;
+    long long k = st->k;
+    const long long every = st->steps, max_iter = st->max_iter;
+    const double tol = st->tol;
+    double val = st->last_check;
+    int status = 1;  // LAP_MAXITER
+    __syncthreads();
+    while (k < max_iter) {
+        const long long left = every - k % every, rest = max_iter - k;
+        const long long nst = left < rest ? left : rest;
+        for (long long s = 0; s < nst; ++s) {
+            if (s == nst - 1) {
+                for (int q = tid; q < m * n; q += LC_THREADS) prev[q] = u[q];
+                __syncthreads();
+            }
+            cta_half_sweep<FORM>(o, u, m, n, 0, b2, c1x, w, tabs, tabs + wlen, work, wlen);
+            if (ADI)
+                cta_half_sweep<FORM>(o, u, m, n, 1, b2, c1y, w, tabs + 2 * wlen, tabs + 3 * wlen,
+                                     work, wlen);
+        }
+        k += nst;
+        unsigned long long dl = 0;
+        for (int q = tid; q < m * n; q += LC_THREADS) {
+            const unsigned long long v = abs_bits(__dadd_rn(u[q], -prev[q]));
+            dl = v > dl ? v : dl;
+        }
+        dl = warp_max_u64(dl);
+        if ((tid & 31) == 0) red[tid >> 5] = dl;
+        __syncthreads();
+        if (tid < 32) {
+            unsigned long long v = tid < LC_THREADS / 32 ? red[tid] : 0ull;
+            v = warp_max_u64(v);
+            if (tid == 0) {
+                val = __longlong_as_double((long long)v);
+                status = !isfinite(val) ? 2 : (val <= tol ? 0 : 1);
+                go = status == 1;
+            }
+        }
+        __syncthreads();
+        if (!go) break;
+    }
+    const int mi = m - 2;
+    for (int q = tid; q < mi * (n - 2); q += LC_THREADS) {
+        const int i = 1 + q % mi, j = 1 + q / mi;
+        psi[(int64_t)j * pitch + i] = u[j * m + i];
+    }
+    if (tid == 0) {
+        st->k = k;
+        st->status = status;
+        st->last_check = val;
+    }
+}
+
 }  // namespace
 
 size_t line_smem_bytes(const LineTables& t) { return sizeof(double) * (size_t)t.P * t.stride; }
@@ -557,6 +701,38 @@ cudaError_t launch_line_scratch(double* psi, int64_t sa, int64_t sx, int first_l
     } while (0)
     if (form == 0) LAP_LINES(0); else LAP_LINES(1);
 #undef LAP_LINES
+    return cudaGetLastError();
+}
+
+// the field, its copy, the two directions' tables, and forward values for as many lines as a
+// colour has (at most one per thread)
+size_t solve_lines_cta_smem(int m, int n)
+{
+    const int per_colour = std::min(LC_THREADS, std::max((n - 1) / 2, (m - 1) / 2));
+    return sizeof(double) * ((size_t)2 * m * n + (size_t)(4 + per_colour) * std::max(m, n));
+}
+
+static std::atomic<size_t> g_lines_cta_smem_set[ATTR_DEVICES];
+
+cudaError_t launch_solve_lines_cta(const Field& f, const Coef& c, bool adi, int form,
+                                   const double* wslot, LoopState* st, cudaStream_t s)
+{
+    const size_t smem = solve_lines_cta_smem(f.m, f.n);
+    const int dev = attr_slot();
+    cudaError_t e = cudaSuccess;
+    if (smem > 48 * 1024 && !(dev >= 0 && smem <= g_lines_cta_smem_set[dev].load())) {
+        const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(solve_lines_cta_kernel<false, 0>, a, (int)smem);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(solve_lines_cta_kernel<false, 1>, a, (int)smem);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(solve_lines_cta_kernel<true, 0>, a, (int)smem);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(solve_lines_cta_kernel<true, 1>, a, (int)smem);
+        if (e == cudaSuccess) attr_record(g_lines_cta_smem_set, dev, smem);
+        if (e != cudaSuccess) return e;
+    }
+    auto kern = adi ? (form == 0 ? solve_lines_cta_kernel<true, 0> : solve_lines_cta_kernel<true, 1>)
+                    : (form == 0 ? solve_lines_cta_kernel<false, 0> : solve_lines_cta_kernel<false, 1>);
+    kern<<<1, LC_THREADS, smem, s>>>(f.p, f.m, f.n, f.pitch, c.b2, c.d, wslot, st);
+    note_launch();
     return cudaGetLastError();
 }
 

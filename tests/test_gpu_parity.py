@@ -487,10 +487,12 @@ def test_slor_fixed_iterations(lap, b, shape, form, w):
 
 @pytest.mark.parametrize("form,w", [("A", 1.65), ("B", 1.25)])
 def test_slor_chamber_matches_oracle(lap, b, form, w):
+    """The paper's stopping rule on the chamber (the one-CTA line solver): the oracle's
+    stopping iteration, its iterate to rounding."""
     got, g, want, o = both(lap, b, wl.chamber(), 0.25, 0.25, method="slor", line_form=form, w=w,
                            norm="maxdelta", tol=1e-9)
-    assert g["status"] == o["status"] == "converged" and abs(g["iters"] - o["iters"]) <= 1
-    assert relerr(got, want) <= 1e-10
+    assert g["status"] == o["status"] == "converged" and g["iters"] == o["iters"]
+    assert relerr(got, want) <= REL
 
 
 @pytest.mark.parametrize("shape", [(3, 3), (25, 17), (67, 45), (130, 97), (33, 257)])
@@ -526,6 +528,34 @@ def test_lexicographic_refuses_grids_beyond_one_sm(lap, b):
 
 
 # ---- the whole solve in one CTA (small grids, the stopping rule of Eq. 16) -------------
+
+@pytest.mark.parametrize("method", ["slor", "adi"])
+@pytest.mark.parametrize("form,w", [("A", 1.3), ("B", 1.25), ("A", 1.0)])
+@pytest.mark.parametrize("every,max_iter,tol", [(1, 400, 1e-9), (3, 10, 0.0), (4, 23, 0.0),
+                                                (5, 1000, 1e-8)])
+@pytest.mark.parametrize("shape,beta", [((25, 17), 1.0), ((33, 65), 0.8), ((3, 3), 1.0),
+                                        ((4, 61), 1.3)])
+def test_one_cta_line_solve_matches_oracle(lap, b, method, form, w, every, max_iter, tol, shape, beta):
+    """SLOR and ADI on grids of at most 4096 points with the stopping rule of Eq. 16 run the
+    whole solve in one kernel: the oracle's iterates to rounding (tabulated pivots instead of
+    the serial solver's divisions), its stopping iteration, for any period length and cap."""
+    m, n = shape
+    psi = rand_field(m, n, 41 + m)
+    t = b.to_field(psi)
+    torch.cuda.synchronize()
+    before = b.kernel_launches()
+    g = lap.solve(t, beta, 1.0, method=method, w=w, line_form=form, norm="maxdelta", tol=tol,
+                  check_every=every, max_iter=max_iter)
+    # one kernel for the whole solve, beside the initial and final residual norms
+    assert b.kernel_launches() - before <= 5
+    want, o = ora.solve(psi, dx=beta, dy=1.0, tol=tol, norm=ora.NORM_MAXDELTA, max_iter=max_iter,
+                        check_every=every, history=True, **ora_kw(method, w=w, line_form=form))
+    assert g["status"] == o["status"]
+    assert g["iters"] == o["iters"]
+    assert relerr(host(t), want) <= REL
+    if g["iters"]:
+        assert abs(g["last_check"] - o["hist"][-1]) <= 1e-10 * o["hist"][-1] + 1e-15
+
 
 @pytest.mark.parametrize("method,w", [("jacobi", 1.0), ("gs", 1.0), ("sor", 1.6), ("gs_lex", 1.0),
                                       ("sor_lex", 1.6)])
