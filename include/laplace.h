@@ -269,8 +269,12 @@ int lap_coarse_solve(lap_handle h, const lap_grid* g, double* u_dev, const doubl
 
 /* One zebra half-sweep of line relaxation (Eqs. 8-10): direction 0 solves every x-line
  * (row j; odd j first, then even j), direction 1 every y-line (column i; odd i first).
- * A line system is solved exactly (partitioned Thomas with a cyclic-reduction solve of
- * the interface unknowns); form A relaxes afterwards, form B inside the system. */
+ * A line system is solved exactly (chunked recurrences with a cyclic-reduction solve of
+ * the chunk separators); form A relaxes afterwards, form B inside the system. Only
+ * enqueues. The x-line kernel's rows of the second colour wait on flags set by the first
+ * colour's rows (bounded waits); a wait that gives up, which nothing but a stalled device
+ * can cause, makes the next synchronising call on the handle (lap_solve, lap_residual)
+ * return LAP_ECUDA. */
 int lap_line_sweep(lap_handle h, const lap_grid* g, double* psi_dev, double w, int form,
                    int direction, void* stream);
 
