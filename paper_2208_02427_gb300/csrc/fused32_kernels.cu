@@ -20,6 +20,7 @@
 // east/west neighbours are contiguous in the other half (no bank conflicts); the half
 // stride is 16 mod 32 words so that the two halves of a row fall into different banks.
 #include <algorithm>
+#include <type_traits>
 
 #include "lap_device.cuh"
 #include "lap_internal.cuh"
@@ -62,11 +63,22 @@ __device__ __forceinline__ Coef32 coef32(const BatchLevel<float>& L, bool gs, fl
 
 // (E+W) + b2 (N+S) for two points at once: per component the FP32 neighbour sum of the
 // per-pass kernels (packed FP32 operations round each component like the scalar ones).
+template <bool UNIT>
 __device__ __forceinline__ float2 nsum2(float2 w_, float2 e_, float2 s_, float2 n_, const Coef32& k)
 {
     const float2 ew = __fadd2_rn(w_, e_);
     const float2 ns = __fadd2_rn(s_, n_);
-    return k.unit ? __fadd2_rn(ns, ew) : __ffma2_rn(k.b2, ns, ew);
+    return UNIT ? __fadd2_rn(ns, ew) : __ffma2_rn(k.b2, ns, ew);
+}
+
+// beta == 1 and Gauss-Seidel (w = 1) are the same for every point of a tile: the tile's code
+// is compiled for each combination and chosen once per block (as run-time choices they cost
+// a test and a branch in every group of points).
+template <class F>
+__device__ __forceinline__ void on_flag32(bool a, F&& f)
+{
+    if (a) f(std::true_type{});
+    else f(std::false_type{});
 }
 
 // Asynchronous 4-byte copy global -> shared; completes at cp_async_wait_all.
@@ -153,7 +165,7 @@ __device__ __forceinline__ void sts4_masked(float* p, float4 v, int c0, int lo, 
 // s = (E+W) + b2 (N+S) + q for the four points c0 .. c0 + 3 of half HALF of region row ly,
 // as two float2 (points c0, c0 + 1 and c0 + 2, c0 + 3). Their west/east neighbours are in the
 // other half of the row at c - 1 + HALF and c + HALF.
-template <int HALF>
+template <int HALF, bool UNIT>
 __device__ __forceinline__ void stencil4(const float* su, const float* sq, int ly, int c0,
                                          const Coef32& k, float2& sA, float2& sB)
 {
@@ -175,21 +187,21 @@ __device__ __forceinline__ void stencil4(const float* su, const float* sq, int l
         eB = make_float2(o.w, orr);
     }
     const float4 S = lds4(su + a - FT_RS), N = lds4(su + a + FT_RS), Q = lds4(sq + a);
-    sA = __fadd2_rn(nsum2(wA, eA, make_float2(S.x, S.y), make_float2(N.x, N.y), k), make_float2(Q.x, Q.y));
-    sB = __fadd2_rn(nsum2(wB, eB, make_float2(S.z, S.w), make_float2(N.z, N.w), k), make_float2(Q.z, Q.w));
+    sA = __fadd2_rn(nsum2<UNIT>(wA, eA, make_float2(S.x, S.y), make_float2(N.x, N.y), k), make_float2(Q.x, Q.y));
+    sB = __fadd2_rn(nsum2<UNIT>(wB, eB, make_float2(S.z, S.w), make_float2(N.z, N.w), k), make_float2(Q.z, Q.w));
 }
 
 // Eq. 6 (gs) or Eq. 7 on the four points c0 .. c0 + 3 of half HALF of row ly, those in
 // [c_lo, c_hi] stored.
-template <int HALF>
+template <int HALF, bool UNIT, bool GS>
 __device__ __forceinline__ void relax4(float* su, const float* sq, int ly, int c0, int c_lo, int c_hi,
                                        const Coef32& k)
 {
     float2 sA, sB;
-    stencil4<HALF>(su, sq, ly, c0, k, sA, sB);
+    stencil4<HALF, UNIT>(su, sq, ly, c0, k, sA, sB);
     float* at = su + ly * FT_RS + HALF * FT_HS + c0;
     float2 gA = __fmul2_rn(sA, k.inv_d), gB = __fmul2_rn(sB, k.inv_d);
-    if (!k.gs) {
+    if (!GS) {
         const float4 old = lds4(at);
         gA = __ffma2_rn(k.w, gA, __fmul2_rn(k.omw, make_float2(old.x, old.y)));
         gB = __ffma2_rn(k.w, gB, __fmul2_rn(k.omw, make_float2(old.z, old.w)));
@@ -201,7 +213,7 @@ __device__ __forceinline__ void relax4(float* su, const float* sq, int ly, int c
 // but its outer ring: points (gx + gy) % 2 == colour, i.e. half (colour + gy) & 1 of row
 // gy. A warp takes two rows of the same parity (ly, ly + 2: the same half), a half warp one
 // row, a lane four consecutive points of its half row.
-template <int NT>
+template <int NT, bool UNIT, bool GS>
 __device__ __forceinline__ void colour_pass(float* su, const float* sq, const Region& R, int m, int n,
                                             int colour, const Coef32& k)
 {
@@ -220,20 +232,20 @@ __device__ __forceinline__ void colour_pass(float* su, const float* sq, const Re
         const int half = (colour + R.gy0 + r) & 1;  // the same for r and r + 2
         if (ly > ly_hi) continue;
         if (half == 0) {
-            if (c0 + 3 >= cl0 && c0 <= ch0) relax4<0>(su, sq, ly, c0, cl0, ch0, k);
+            if (c0 + 3 >= cl0 && c0 <= ch0) relax4<0, UNIT, GS>(su, sq, ly, c0, cl0, ch0, k);
         } else {
-            if (c0 + 3 >= cl1 && c0 <= ch1) relax4<1>(su, sq, ly, c0, cl1, ch1, k);
+            if (c0 + 3 >= cl1 && c0 <= ch1) relax4<1, UNIT, GS>(su, sq, ly, c0, cl1, ch1, k);
         }
     }
 }
 
-template <int NT>
+template <int NT, bool UNIT, bool GS>
 __device__ __forceinline__ void smooth_region(float* su, const float* sq, const Region& R, int m,
                                               int n, int sweeps, const Coef32& k)
 {
     for (int s = 0; s < sweeps; ++s)
         for (int colour = 0; colour < 2; ++colour) {
-            colour_pass<NT>(su, sq, R, m, n, colour, k);
+            colour_pass<NT, UNIT, GS>(su, sq, R, m, n, colour, k);
             __syncthreads();
         }
 }
@@ -272,7 +284,7 @@ __device__ __forceinline__ Region region_of(int x0, int y0, int tx, int ty, int 
 // Descent on one tile of level F: nu1 smoothing sweeps, the smoothed u of the owned points
 // to F.r (the second buffer of the level), the residual, and qc = 0.25 ((4 r + 2 edges) +
 // corners) with the correction zeroed at the coarse points whose centre the tile owns.
-template <int NT, int H>
+template <int NT, int H, bool UNIT, bool GS>
 __device__ __forceinline__ void down_tile(const BatchLevel<float>& F, const BatchLevel<float>& C,
                                           int x0, int y0, int tx, int ty, int nu1, bool zero_u,
                                           const Coef32& k, float* su, float* sq)
@@ -282,7 +294,7 @@ __device__ __forceinline__ void down_tile(const BatchLevel<float>& F, const Batc
     const Region R = region_of(x0, y0, tx, ty, 2 + 2 * nu1);
     load_region<NT, H>(su, sq, F.u, F.q, F.pitch, m, n, R, zero_u);
     __syncthreads();
-    smooth_region<NT>(su, sq, R, m, n, nu1, k);
+    smooth_region<NT, UNIT, GS>(su, sq, R, m, n, nu1, k);
     const int x1 = min(x0 + tx, m - 1), y1 = min(y0 + ty, n - 1);
     store_owned<NT>(F.r, F.pitch, su, R, x0, x1, y0, y1);
     // residual r = (E+W) + b2 (N+S) + q - d u on the owned points and a ring of one, written
@@ -302,8 +314,8 @@ __device__ __forceinline__ void down_tile(const BatchLevel<float>& F, const Batc
         const int clo = half ? cl1 : cl0, chi = half ? ch1 : ch0;
         if (ly > ly_hi || c0 + 3 < clo || c0 > chi) continue;
         float2 sA, sB;
-        if (half == 0) stencil4<0>(su, sq, ly, c0, k, sA, sB);
-        else stencil4<1>(su, sq, ly, c0, k, sA, sB);
+        if (half == 0) stencil4<0, UNIT>(su, sq, ly, c0, k, sA, sB);
+        else stencil4<1, UNIT>(su, sq, ly, c0, k, sA, sB);
         const int a = ly * FT_RS + half * FT_HS + c0;
         const float4 u4 = lds4(su + a);
         const float2 rA = __ffma2_rn(nd, make_float2(u4.x, u4.y), sA);
@@ -340,7 +352,7 @@ __device__ __forceinline__ void down_tile(const BatchLevel<float>& F, const Batc
 // in shared memory (sc): a column pair p of the region lies over coarse column gx0 / 2 + p.
 // With psi (the FP64 field of the mixed solver's level 0), the last ascent adds its result
 // to psi in FP64 (psi += e, the update of the defect correction) instead of storing e.
-template <int NT, int H>
+template <int NT, int H, bool UNIT, bool GS>
 __device__ __forceinline__ void up_tile(const BatchLevel<float>& F, const BatchLevel<float>& C,
                                         int x0, int y0, int tx, int ty, int nu2, const Coef32& k,
                                         float* su, float* sq, float* sc, double* psi,
@@ -402,7 +414,7 @@ __device__ __forceinline__ void up_tile(const BatchLevel<float>& F, const BatchL
         }
     }
     __syncthreads();
-    smooth_region<NT>(su, sq, R, m, n, nu2, k);
+    smooth_region<NT, UNIT, GS>(su, sq, R, m, n, nu2, k);
     const int x1 = min(x0 + tx, m - 1), y1 = min(y0 + ty, n - 1);
     if (!psi) {
         store_owned<NT>(F.u, F.pitch, su, R, x0, x1, y0, y1);
@@ -458,8 +470,13 @@ __global__ void __launch_bounds__(NT, 1024 / NT)
 {
     extern __shared__ float4 smem4[];
     float* smem = reinterpret_cast<float*>(smem4);
-    down_tile<NT, FT_H>(F, C, 1 + blockIdx.x * tx, 1 + blockIdx.y * ty, tx, ty, nu1, zero_u != 0,
-                        coef32(F, gs != 0, w, omw), smem, smem + FT_ARR);
+    const Coef32 k = coef32(F, gs != 0, w, omw);
+    on_flag32(k.unit, [&](auto U) {
+        on_flag32(k.gs, [&](auto G) {
+            down_tile<NT, FT_H, U.value, G.value>(F, C, 1 + blockIdx.x * tx, 1 + blockIdx.y * ty, tx,
+                                                  ty, nu1, zero_u != 0, k, smem, smem + FT_ARR);
+        });
+    });
 }
 
 template <int NT>
@@ -469,8 +486,14 @@ __global__ void __launch_bounds__(NT, 1024 / NT)
 {
     extern __shared__ float4 smem4[];
     float* smem = reinterpret_cast<float*>(smem4);
-    up_tile<NT, FT_H>(F, C, 1 + blockIdx.x * tx, 1 + blockIdx.y * ty, tx, ty, nu2,
-                      coef32(F, gs != 0, w, omw), smem, smem + FT_ARR, smem + 2 * FT_ARR, psi, psi_pitch);
+    const Coef32 k = coef32(F, gs != 0, w, omw);
+    on_flag32(k.unit, [&](auto U) {
+        on_flag32(k.gs, [&](auto G) {
+            up_tile<NT, FT_H, U.value, G.value>(F, C, 1 + blockIdx.x * tx, 1 + blockIdx.y * ty, tx, ty,
+                                                nu2, k, smem, smem + FT_ARR, smem + 2 * FT_ARR, psi,
+                                                psi_pitch);
+        });
+    });
 }
 
 // ---- many grids: one tile item per CTA, NT threads, regions of H rows ----
@@ -484,8 +507,13 @@ __global__ void __launch_bounds__(NT, 1024 / NT)
     const TileItem it = items[blockIdx.x];
     const BatchLevel<float> F = lv[it.level];
     if (active && !active[F.problem]) return;
-    down_tile<NT, H>(F, lv[it.level + 1], it.x0, it.y0, it.tx, it.ty, nu1, zero_u != 0,
-                     coef32(F, gs != 0, w, omw), smem, smem + ft_arr(H));
+    const Coef32 k = coef32(F, gs != 0, w, omw);
+    on_flag32(k.unit, [&](auto U) {
+        on_flag32(k.gs, [&](auto G) {
+            down_tile<NT, H, U.value, G.value>(F, lv[it.level + 1], it.x0, it.y0, it.tx, it.ty, nu1,
+                                               zero_u != 0, k, smem, smem + ft_arr(H));
+        });
+    });
 }
 
 template <int NT, int H>
@@ -501,8 +529,13 @@ __global__ void __launch_bounds__(NT, 1024 / NT)
     if (active && !active[F.problem]) return;
     double* psi = lv64 ? lv64[it.level].u : nullptr;
     const int64_t pp = lv64 ? lv64[it.level].pitch : 0;
-    up_tile<NT, H>(F, lv[it.level + 1], it.x0, it.y0, it.tx, it.ty, nu2, coef32(F, gs != 0, w, omw),
-                   smem, smem + ft_arr(H), smem + 2 * ft_arr(H), psi, pp);
+    const Coef32 k = coef32(F, gs != 0, w, omw);
+    on_flag32(k.unit, [&](auto U) {
+        on_flag32(k.gs, [&](auto G) {
+            up_tile<NT, H, U.value, G.value>(F, lv[it.level + 1], it.x0, it.y0, it.tx, it.ty, nu2, k,
+                                             smem, smem + ft_arr(H), smem + 2 * ft_arr(H), psi, pp);
+        });
+    });
 }
 
 constexpr size_t ft_smem(int H) { return (2 * (size_t)ft_arr(H) + ft_carr(H)) * sizeof(float); }
