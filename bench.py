@@ -592,6 +592,14 @@ def main():
                               (3, "tiles_512x128x32"), (-1, "one_kernel_per_pass")):
             ms, _ = time_batch("mg_mixed", 6, 3, tiling=tiling)
             out["mixed_by_tiling"][label] = {"ms": ms, "configuration": lap.last_batch_config()}
+        # one CTA per work item against persistent launches (resident CTAs looping over the
+        # items), the other knobs still chosen by timing
+        out["by_launch"] = {}
+        for name, method in (("fp64", "mg"), ("mixed", "mg_mixed")):
+            for persistent, label in ((-1, "one_cta_per_item"), (1, "persistent")):
+                ms, _ = time_batch(method, 6, 3, persistent=persistent)
+                out["by_launch"][f"{name}_{label}"] = {"ms": ms,
+                                                       "configuration": lap.last_batch_config()}
         # one problem at a time through lap_solve, on a sample
         kw = dict(mg_kw)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

@@ -38,7 +38,7 @@
 extern "C" {
 #endif
 
-#define LAP_ABI_VERSION 2
+#define LAP_ABI_VERSION 3
 
 enum {
     LAP_OK = 0,
@@ -120,6 +120,10 @@ typedef struct {
                              128 x 32). Every choice gives the same values bit for bit */
     int32_t item_points;  /* batched solves: interior points per work item of the per-pass
                              kernels (>= 32), 0 = chosen by timing. No effect on the values */
+    int32_t persistent;   /* batched solves: how a phase's work items map to CTAs. -1 = one
+                             CTA per item, 1 = persistent: as many CTAs as fit the device at
+                             once, each looping over items k, k + grid, ...; 0 = chosen by
+                             timing. No effect on the values */
 } lap_params;
 
 typedef struct {
@@ -178,8 +182,9 @@ int lap_solve_host(lap_handle h, const lap_grid* g, double* psi_host, int64_t ho
  * results[k] (host). p->check_every sets how often (in cycles) the host polls for the
  * number of problems still running. Synchronises `stream` before returning.
  * The launch configuration -- the small-level tail size (p->tail_size), the FP32 levels'
- * temporal blocking and tile shape (p->tiling) and the per-pass kernels' work-item size
- * (p->item_points) -- is chosen by timing where a parameter leaves it open (0): the first
+ * temporal blocking and tile shape (p->tiling), the per-pass kernels' work-item size
+ * (p->item_points) and persistent or one-CTA-per-item launches (p->persistent) -- is chosen
+ * by timing where a parameter leaves it open (0): the first
  * cycles of a batch shape each run a different candidate, one knob at a time, the fastest
  * is kept in the handle for that shape. No choice changes a value.
  * The plan of a call (level descriptors, work lists, the captured cycle graphs) stays in the
@@ -190,11 +195,12 @@ int lap_solve_batched(lap_handle h, int count, const lap_grid* grids, double* co
 
 /* The launch configuration of the last cycle of the last lap_solve_batched call on h (no
  * counterpart in the paper; for reports): *tail_size (-1 = no tail), *tiling (-1 = one kernel
- * per pass, 1..3 = tile variant; see lap_params), *item_points, and *tuned = 1 if the choice
- * by timing had finished for that batch shape (0 while candidates were still being timed).
- * Any pointer may be NULL. All zero before the first batched solve. */
+ * per pass, 1..3 = tile variant; see lap_params), *item_points, *persistent (1 = persistent
+ * launches, -1 = one CTA per item), and *tuned = 1 if the choice by timing had finished for
+ * that batch shape (0 while candidates were still being timed). Any pointer may be NULL. All
+ * zero before the first batched solve. */
 int lap_last_batch_config(lap_handle h, int32_t* tail_size, int32_t* tiling, int32_t* item_points,
-                          int32_t* tuned);
+                          int32_t* persistent, int32_t* tuned);
 
 /* ---- serving: continuous batching over a stream of solve requests ----
  * A server owns a device pool of hbm_budget_bytes for the grid hierarchies of the requests it

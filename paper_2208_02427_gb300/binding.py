@@ -45,7 +45,7 @@ class Params(C.Structure):
                 ("nu2", c_int32), ("coarsest_min", c_int32), ("max_levels", c_int32),
                 ("smoother_w", c_double), ("line_form", c_int32), ("inner_cycles", c_int32),
                 ("tail_size", c_int32), ("unfused", c_int32), ("tiling", c_int32),
-                ("item_points", c_int32)]
+                ("item_points", c_int32), ("persistent", c_int32)]
 
 
 class Result(C.Structure):
@@ -106,7 +106,8 @@ def load():
             "lap_check_rounding": (C.c_int, [c_void_p, c_int64, C.c_uint64, C.POINTER(c_int64)]),
             "lap_fp64_rate": (C.c_int, [c_void_p, C.POINTER(c_double)]),
             "lap_last_batch_config": (C.c_int, [c_void_p, C.POINTER(c_int32), C.POINTER(c_int32),
-                                                C.POINTER(c_int32), C.POINTER(c_int32)]),
+                                                C.POINTER(c_int32), C.POINTER(c_int32),
+                                                C.POINTER(c_int32)]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -164,11 +165,12 @@ def _stream(stream, device):
 
 def params(method="sor", w=1.0, tol=1e-10, norm="l2_rel", max_iter=100000, check_every=1,
            nu1=2, nu2=2, coarsest_min=5, max_levels=0, smoother_w=1.0, line_form="A",
-           inner_cycles=1, tail_size=0, unfused=False, tiling=0, item_points=0) -> Params:
+           inner_cycles=1, tail_size=0, unfused=False, tiling=0, item_points=0,
+           persistent=0) -> Params:
     return Params(METHODS[method], float(w), float(tol), NORMS[norm], int(max_iter),
                   int(check_every), int(nu1), int(nu2), int(coarsest_min), int(max_levels),
                   float(smoother_w), FORMS[line_form], int(inner_cycles), int(tail_size),
-                  1 if unfused else 0, int(tiling), int(item_points))
+                  1 if unfused else 0, int(tiling), int(item_points), int(persistent))
 
 
 class Batch:
@@ -262,10 +264,10 @@ class Laplace:
     def last_batch_config(self) -> dict:
         """The launch configuration the last batched cycle ran, and whether the choice by timing
         had finished (see lap_last_batch_config)."""
-        v = [c_int32(0) for _ in range(4)]
+        v = [c_int32(0) for _ in range(5)]
         _check(self._lib.lap_last_batch_config(self._h, *[C.byref(x) for x in v]))
         return {"tail_size": v[0].value, "tiling": v[1].value, "item_points": v[2].value,
-                "tuned": bool(v[3].value)}
+                "persistent": v[3].value, "tuned": bool(v[4].value)}
 
     def solve_host(self, psi_host: torch.Tensor, dx=1.0, dy=1.0, stream=None, align: int = 32,
                    **kw):

@@ -182,76 +182,89 @@ __device__ __forceinline__ void prolong_pair(const Arith<T>& A, const BatchLevel
 // One smoother colour pass (Eq. 6 when gs, Eq. 7 otherwise) over the rows of each item.
 template <class T>
 __global__ void __launch_bounds__(BT)
-    b_rb_kernel(const BatchItem* __restrict__ items, const BatchLevel<T>* __restrict__ lv,
-                const int* __restrict__ active, int colour, int gs, T w, T omw, int per_level_w)
+    b_rb_kernel(const BatchItem* __restrict__ items, int count, unsigned* claim, const BatchLevel<T>* __restrict__ lv,
+                const int* __restrict__ active, int colour, int gs, T w_arg, T omw_arg, int per_level_w)
 {
-    const BatchItem it = items[blockIdx.x];
-    const BatchLevel<T> L = lv[it.level];
-    if (!active[L.problem]) return;
     const Arith<T> A = arith<T>();
-    if (per_level_w) {
-        w = (T)L.w;
-        omw = (T)L.omw;
+    const ItemClaim ic{claim, count};
+    for (int b = ic.take(-1); b < count; b = ic.take(b)) {
+        const BatchItem it = items[b];
+        const BatchLevel<T> L = lv[it.level];
+        if (!active[L.problem]) continue;
+        const T w = per_level_w ? (T)L.w : w_arg, omw = per_level_w ? (T)L.omw : omw_arg;
+        const int half_w = (L.m - 2 + 1) / 2;
+        on_rb_flags(L, gs != 0, [&](auto U, auto P, auto Q, auto G) {
+            for (Walk k(half_w); k.r < it.rows; k.next()) {
+                const int j = it.row0 + k.r;
+                const int i = 1 + ((1 + j + colour) & 1) + 2 * k.c;
+                if (i <= L.m - 2)
+                    rb_point<T, decltype(U)::value, decltype(P)::value, decltype(Q)::value,
+                             decltype(G)::value>(A, L, i, j, w, omw);
+            }
+        });
     }
-    const int half_w = (L.m - 2 + 1) / 2;
-    on_rb_flags(L, gs != 0, [&](auto U, auto P, auto Q, auto G) {
-        for (Walk k(half_w); k.r < it.rows; k.next()) {
-            const int j = it.row0 + k.r;
-            const int i = 1 + ((1 + j + colour) & 1) + 2 * k.c;
-            if (i <= L.m - 2)
-                rb_point<T, decltype(U)::value, decltype(P)::value, decltype(Q)::value,
-                         decltype(G)::value>(A, L, i, j, w, omw);
-        }
-    });
+    ic.finish();
 }
 
 template <class T>
 __global__ void __launch_bounds__(BT)
-    b_defect_kernel(const BatchItem* __restrict__ items, const BatchLevel<T>* __restrict__ lv,
-                    const int* __restrict__ active)
+    b_defect_kernel(const BatchItem* __restrict__ items, int count, unsigned* claim,
+                    const BatchLevel<T>* __restrict__ lv, const int* __restrict__ active)
 {
-    const BatchItem it = items[blockIdx.x];
-    const BatchLevel<T> L = lv[it.level];
-    if (!active[L.problem]) return;
     const Arith<T> A = arith<T>();
-    const int wdt = L.m - 2;
-    on_flag(L.unit_beta != 0, [&](auto U) {
-        on_flag(L.q != nullptr, [&](auto Q) {
-            for (Walk k(wdt); k.r < it.rows; k.next())
-                defect_point<T, decltype(U)::value, decltype(Q)::value>(A, L, 1 + k.c, it.row0 + k.r);
+    const ItemClaim ic{claim, count};
+    for (int b = ic.take(-1); b < count; b = ic.take(b)) {
+        const BatchItem it = items[b];
+        const BatchLevel<T> L = lv[it.level];
+        if (!active[L.problem]) continue;
+        const int wdt = L.m - 2;
+        on_flag(L.unit_beta != 0, [&](auto U) {
+            on_flag(L.q != nullptr, [&](auto Q) {
+                for (Walk k(wdt); k.r < it.rows; k.next())
+                    defect_point<T, decltype(U)::value, decltype(Q)::value>(A, L, 1 + k.c, it.row0 + k.r);
+            });
         });
-    });
+    }
+    ic.finish();
 }
 
 // Items of the coarse level: qc from the fine residual (the level before it in lv), and the
 // coarse correction zeroed.
 template <class T>
 __global__ void __launch_bounds__(BT)
-    b_restrict_kernel(const BatchItem* __restrict__ items, const BatchLevel<T>* __restrict__ lv,
-                      const int* __restrict__ active)
+    b_restrict_kernel(const BatchItem* __restrict__ items, int count, unsigned* claim,
+                      const BatchLevel<T>* __restrict__ lv, const int* __restrict__ active)
 {
-    const BatchItem it = items[blockIdx.x];
-    const BatchLevel<T> C = lv[it.level];
-    if (!active[C.problem]) return;
-    const BatchLevel<T> F = lv[it.level - 1];
     const Arith<T> A = arith<T>();
-    const int wdt = C.m - 2;
-    for (Walk k(wdt); k.r < it.rows; k.next()) restrict_point(A, C, F, 1 + k.c, it.row0 + k.r);
+    const ItemClaim ic{claim, count};
+    for (int b = ic.take(-1); b < count; b = ic.take(b)) {
+        const BatchItem it = items[b];
+        const BatchLevel<T> C = lv[it.level];
+        if (!active[C.problem]) continue;
+        const BatchLevel<T> F = lv[it.level - 1];
+        const int wdt = C.m - 2;
+        for (Walk k(wdt); k.r < it.rows; k.next()) restrict_point(A, C, F, 1 + k.c, it.row0 + k.r);
+    }
+    ic.finish();
 }
 
 // Items of the fine level: u += bilinear interpolation of the next level's correction.
 template <class T>
 __global__ void __launch_bounds__(BT)
-    b_prolong_kernel(const BatchItem* __restrict__ items, const BatchLevel<T>* __restrict__ lv,
-                     const int* __restrict__ active)
+    b_prolong_kernel(const BatchItem* __restrict__ items, int count, unsigned* claim,
+                     const BatchLevel<T>* __restrict__ lv, const int* __restrict__ active)
 {
-    const BatchItem it = items[blockIdx.x];
-    const BatchLevel<T> F = lv[it.level];
-    if (!active[F.problem]) return;
-    const BatchLevel<T> C = lv[it.level + 1];
     const Arith<T> A = arith<T>();
-    const int pairs = (F.m - 1) / 2;  // coarse columns 0 .. mc-2
-    for (Walk k(pairs); k.r < it.rows; k.next()) prolong_pair(A, F, C, k.c, it.row0 + k.r);
+    const ItemClaim ic{claim, count};
+    for (int b = ic.take(-1); b < count; b = ic.take(b)) {
+        const BatchItem it = items[b];
+        const BatchLevel<T> F = lv[it.level];
+        if (!active[F.problem]) continue;
+        const BatchLevel<T> C = lv[it.level + 1];
+        const int pairs = (F.m - 1) / 2;  // coarse columns 0 .. mc-2
+        for (Walk k(pairs); k.r < it.rows; k.next()) prolong_pair(A, F, C, k.c, it.row0 + k.r);
+    }
+    ic.finish();
 }
 
 // u = A^-1 b at the coarsest level L, b = q + ring terms assembled in FP64; all threads of the
@@ -282,14 +295,19 @@ __device__ __forceinline__ void coarse_cta(const BatchLevel<T>& L, double* b)
 // One item per problem at its coarsest level: u = A^-1 b in FP64.
 template <class T>
 __global__ void __launch_bounds__(1024)
-    b_coarse_kernel(const BatchItem* __restrict__ items, const BatchLevel<T>* __restrict__ lv,
-                    const int* __restrict__ active)
+    b_coarse_kernel(const BatchItem* __restrict__ items, int count, unsigned* claim,
+                    const BatchLevel<T>* __restrict__ lv, const int* __restrict__ active)
 {
     extern __shared__ double b[];
-    const BatchItem it = items[blockIdx.x];
-    const BatchLevel<T> L = lv[it.level];
-    if (!active[L.problem]) return;
-    coarse_cta(L, b);
+    const ItemClaim ic{claim, count};
+    for (int k = ic.take(-1); k < count; k = ic.take(k)) {
+        const BatchItem it = items[k];
+        const BatchLevel<T> L = lv[it.level];
+        if (!active[L.problem]) continue;
+        coarse_cta(L, b);
+        __syncthreads();  // b is reused by the next item
+    }
+    ic.finish();
 }
 
 // ---- the small-level tail: the rest of a V-cycle in one CTA ----
@@ -322,20 +340,12 @@ __device__ __forceinline__ void smooth_cta(const Arith<T>& A, const BatchLevel<T
     });
 }
 
+// The V-cycle of one tail job by the whole CTA (levels jb.first .. jb.last).
 template <class T>
-__global__ void __launch_bounds__(TAIL_THREADS)
-    b_tail_kernel(const TailJob* __restrict__ jobs, const BatchLevel<T>* __restrict__ lv,
-                  const int* __restrict__ active, int nu1, int nu2, int gs, T w, T omw,
-                  int per_level_w)
+__device__ __forceinline__ void tail_job(const TailJob& jb, const BatchLevel<T>* __restrict__ lv,
+                                         int nu1, int nu2, bool gs, T w, T omw, double* b)
 {
-    extern __shared__ double b[];
-    const TailJob jb = jobs[blockIdx.x];
-    if (active && !active[lv[jb.first].problem]) return;
     const Arith<T> A = arith<T>();
-    if (per_level_w) {
-        w = (T)lv[jb.first].w;
-        omw = (T)lv[jb.first].omw;
-    }
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int l = jb.first; l < jb.last; ++l) {
         const BatchLevel<T> F = lv[l];
@@ -364,6 +374,25 @@ __global__ void __launch_bounds__(TAIL_THREADS)
         __syncthreads();
         smooth_cta(A, F, nu2, gs != 0, w, omw);
     }
+}
+
+template <class T>
+__global__ void __launch_bounds__(TAIL_THREADS)
+    b_tail_kernel(const TailJob* __restrict__ jobs, int count, unsigned* claim, const BatchLevel<T>* __restrict__ lv,
+                  const int* __restrict__ active, int nu1, int nu2, int gs, T w_arg, T omw_arg,
+                  int per_level_w)
+{
+    extern __shared__ double b[];
+    const ItemClaim ic{claim, count};
+    for (int k = ic.take(-1); k < count; k = ic.take(k)) {
+        const TailJob jb = jobs[k];
+        if (active && !active[lv[jb.first].problem]) continue;
+        const T w = per_level_w ? (T)lv[jb.first].w : w_arg;
+        const T omw = per_level_w ? (T)lv[jb.first].omw : omw_arg;
+        tail_job(jb, lv, nu1, nu2, gs != 0, w, omw, b);
+        __syncthreads();  // shared memory and the job's levels are reused by the next job
+    }
+    ic.finish();
 }
 
 // FP64 residual of each item's rows: per-item sum of squares (fixed order) and, for the
@@ -427,12 +456,14 @@ __device__ __forceinline__ double sumsq_item(const BatchItem& it, const BatchLev
     return acc;
 }
 
-__global__ void __launch_bounds__(BT, 5)
-    b_sumsq_kernel(const BatchItem* __restrict__ items, const BatchLevel<double>* __restrict__ lv,
-                   const int* __restrict__ active, double* __restrict__ partials,
-                   const BatchLevel<float>* __restrict__ lv32, const double* __restrict__ r0)
+// Item ib's partial sum of squares (see b_sumsq_kernel) by the whole CTA into partials[ib].
+__device__ __forceinline__ void sumsq_block(const BatchItem* __restrict__ items, int ib,
+                                            const BatchLevel<double>* __restrict__ lv,
+                                            const int* __restrict__ active, double* __restrict__ partials,
+                                            const BatchLevel<float>* __restrict__ lv32,
+                                            const double* __restrict__ r0)
 {
-    const BatchItem it = items[blockIdx.x];
+    const BatchItem it = items[ib];
     const BatchLevel<double> L = lv[it.level];
     if (!active[L.problem]) return;
     // problems solved by the FP32 inner cycle have an FP32 level 0
@@ -456,7 +487,7 @@ __global__ void __launch_bounds__(BT, 5)
                 acc = sumsq_item<true, decltype(U)::value, decltype(SC)::value>(it, L, lv32, sc);
             });
     });
-    __shared__ double red[BT / 32];
+    __shared__ double red[BT / 32];  // a persistent CTA's next claim waits for the reads below
     acc = warp_sum(acc);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
     __syncthreads();
@@ -464,26 +495,50 @@ __global__ void __launch_bounds__(BT, 5)
         double v = threadIdx.x < BT / 32 ? red[threadIdx.x] : 0.0;
         v = warp_sum(v);
         if (threadIdx.x == 0)
-            partials[blockIdx.x] = sc > 0.0f ? v / ((double)sc * (double)sc) : v;  // exact
+            partials[ib] = sc > 0.0f ? v / ((double)sc * (double)sc) : v;  // exact
     }
+}
+
+// CLAIM: a persistent launch (compiled apart: the one-item form keeps its registers free of
+// the loop's state)
+template <bool CLAIM>
+__global__ void __launch_bounds__(BT, 5)
+    b_sumsq_kernel(const BatchItem* __restrict__ items, int count, unsigned* claim,
+                   const BatchLevel<double>* __restrict__ lv, const int* __restrict__ active,
+                   double* __restrict__ partials, const BatchLevel<float>* __restrict__ lv32,
+                   const double* __restrict__ r0)
+{
+    if (!CLAIM) {
+        sumsq_block(items, blockIdx.x, lv, active, partials, lv32, r0);
+        return;
+    }
+    const ItemClaim ic{claim, count};
+    for (int b = ic.take(-1); b < count; b = ic.take(b))
+        sumsq_block(items, b, lv, active, partials, lv32, r0);
+    ic.finish();
 }
 
 // psi += e32 (FP64 update of the mixed solver).
 __global__ void __launch_bounds__(BT)
-    b_update_kernel(const BatchItem* __restrict__ items, const BatchLevel<double>* __restrict__ lv,
-                    const int* __restrict__ active, const BatchLevel<float>* __restrict__ lv32)
+    b_update_kernel(const BatchItem* __restrict__ items, int count, unsigned* claim,
+                    const BatchLevel<double>* __restrict__ lv, const int* __restrict__ active,
+                    const BatchLevel<float>* __restrict__ lv32)
 {
-    const BatchItem it = items[blockIdx.x];
-    const BatchLevel<double> L = lv[it.level];
-    if (!active[L.problem]) return;
     const FmaOps o = load_fma_ops();
-    const BatchLevel<float> E = lv32[it.level];
-    const int wdt = L.m - 2;
-    for (Walk k(wdt); k.r < it.rows; k.next()) {
-        const int j = it.row0 + k.r, i = 1 + k.c;
-        double* c = L.u + (int64_t)j * L.pitch + i;
-        *c = fadd(o, *c, to_double_exact(E.u[(int64_t)j * E.pitch + i]));
+    const ItemClaim ic{claim, count};
+    for (int b = ic.take(-1); b < count; b = ic.take(b)) {
+        const BatchItem it = items[b];
+        const BatchLevel<double> L = lv[it.level];
+        if (!active[L.problem]) continue;
+        const BatchLevel<float> E = lv32[it.level];
+        const int wdt = L.m - 2;
+        for (Walk k(wdt); k.r < it.rows; k.next()) {
+            const int j = it.row0 + k.r, i = 1 + k.c;
+            double* c = L.u + (int64_t)j * L.pitch + i;
+            *c = fadd(o, *c, to_double_exact(E.u[(int64_t)j * E.pitch + i]));
+        }
     }
+    ic.finish();
 }
 
 // Per problem: the norm from its items' partials (fixed order), then the stopping test.
@@ -539,8 +594,9 @@ cudaError_t launch_b_rb(const BatchList& l, const BatchLevel<T>* lv, const int* 
                         bool gs, double w, cudaStream_t s, bool per_level_w)
 {
     if (l.count == 0) return cudaSuccess;
-    b_rb_kernel<T><<<l.count, BT, 0, s>>>(l.items, lv, active, colour, gs ? 1 : 0, (T)w, (T)(1.0 - w),
-                                          per_level_w ? 1 : 0);
+    const int grid = batch_grid((const void*)b_rb_kernel<T>, BT, 0, l.count, l.claim != nullptr);
+    b_rb_kernel<T><<<grid, BT, 0, s>>>(l.items, l.count, l.claim, lv, active, colour, gs ? 1 : 0, (T)w,
+                                       (T)(1.0 - w), per_level_w ? 1 : 0);
     note_launch();
     return cudaGetLastError();
 }
@@ -549,7 +605,8 @@ cudaError_t launch_b_defect(const BatchList& l, const BatchLevel<T>* lv, const i
                             cudaStream_t s)
 {
     if (l.count == 0) return cudaSuccess;
-    b_defect_kernel<T><<<l.count, BT, 0, s>>>(l.items, lv, active);
+    const int grid = batch_grid((const void*)b_defect_kernel<T>, BT, 0, l.count, l.claim != nullptr);
+    b_defect_kernel<T><<<grid, BT, 0, s>>>(l.items, l.count, l.claim, lv, active);
     note_launch();
     return cudaGetLastError();
 }
@@ -558,7 +615,8 @@ cudaError_t launch_b_restrict(const BatchList& l, const BatchLevel<T>* lv, const
                               cudaStream_t s)
 {
     if (l.count == 0) return cudaSuccess;
-    b_restrict_kernel<T><<<l.count, BT, 0, s>>>(l.items, lv, active);
+    const int grid = batch_grid((const void*)b_restrict_kernel<T>, BT, 0, l.count, l.claim != nullptr);
+    b_restrict_kernel<T><<<grid, BT, 0, s>>>(l.items, l.count, l.claim, lv, active);
     note_launch();
     return cudaGetLastError();
 }
@@ -567,7 +625,8 @@ cudaError_t launch_b_prolong(const BatchList& l, const BatchLevel<T>* lv, const 
                              cudaStream_t s)
 {
     if (l.count == 0) return cudaSuccess;
-    b_prolong_kernel<T><<<l.count, BT, 0, s>>>(l.items, lv, active);
+    const int grid = batch_grid((const void*)b_prolong_kernel<T>, BT, 0, l.count, l.claim != nullptr);
+    b_prolong_kernel<T><<<grid, BT, 0, s>>>(l.items, l.count, l.claim, lv, active);
     note_launch();
     return cudaGetLastError();
 }
@@ -578,7 +637,9 @@ cudaError_t launch_b_coarse(const BatchList& l, const BatchLevel<T>* lv, const i
     if (l.count == 0) return cudaSuccess;
     int threads = ((max_unknowns + 31) / 32) * 32;
     threads = threads < 32 ? 32 : (threads > 1024 ? 1024 : threads);
-    b_coarse_kernel<T><<<l.count, threads, sizeof(double) * max_unknowns, s>>>(l.items, lv, active);
+    const size_t smem = sizeof(double) * max_unknowns;
+    const int grid = batch_grid((const void*)b_coarse_kernel<T>, threads, smem, l.count, l.claim != nullptr);
+    b_coarse_kernel<T><<<grid, threads, smem, s>>>(l.items, l.count, l.claim, lv, active);
     note_launch();
     return cudaGetLastError();
 }
@@ -597,23 +658,31 @@ template cudaError_t launch_b_coarse<float>(const BatchList&, const BatchLevel<f
 template <class T>
 cudaError_t launch_b_tail(const TailJob* jobs, int count, const BatchLevel<T>* lv, const int* active,
                           int nu1, int nu2, bool gs, double w, int max_unknowns, cudaStream_t s,
-                          bool per_level_w)
+                          bool per_level_w, unsigned* claim)
 {
     if (count == 0) return cudaSuccess;
-    b_tail_kernel<T><<<count, TAIL_THREADS, sizeof(double) * (max_unknowns > 0 ? max_unknowns : 1), s>>>(
-        jobs, lv, active, nu1, nu2, gs ? 1 : 0, (T)w, (T)(1.0 - w), per_level_w ? 1 : 0);
+    const size_t smem = sizeof(double) * (max_unknowns > 0 ? max_unknowns : 1);
+    const int grid = batch_grid((const void*)b_tail_kernel<T>, TAIL_THREADS, smem, count, claim != nullptr);
+    b_tail_kernel<T><<<grid, TAIL_THREADS, smem, s>>>(jobs, count, claim, lv, active, nu1, nu2, gs ? 1 : 0,
+                                                      (T)w, (T)(1.0 - w), per_level_w ? 1 : 0);
     note_launch();
     return cudaGetLastError();
 }
-template cudaError_t launch_b_tail<double>(const TailJob*, int, const BatchLevel<double>*, const int*, int, int, bool, double, int, cudaStream_t, bool);
-template cudaError_t launch_b_tail<float>(const TailJob*, int, const BatchLevel<float>*, const int*, int, int, bool, double, int, cudaStream_t, bool);
+template cudaError_t launch_b_tail<double>(const TailJob*, int, const BatchLevel<double>*, const int*, int, int, bool, double, int, cudaStream_t, bool, unsigned*);
+template cudaError_t launch_b_tail<float>(const TailJob*, int, const BatchLevel<float>*, const int*, int, int, bool, double, int, cudaStream_t, bool, unsigned*);
 
 cudaError_t launch_b_sumsq(const BatchList& l, const BatchLevel<double>* lv, const int* active,
                            double* partials, const BatchLevel<float>* lv32, cudaStream_t s,
                            const double* r0)
 {
     if (l.count == 0) return cudaSuccess;
-    b_sumsq_kernel<<<l.count, BT, 0, s>>>(l.items, lv, active, partials, lv32, r0);
+    if (l.claim) {
+        const int grid = batch_grid((const void*)b_sumsq_kernel<true>, BT, 0, l.count, true);
+        b_sumsq_kernel<true><<<grid, BT, 0, s>>>(l.items, l.count, l.claim, lv, active, partials, lv32, r0);
+    } else {
+        b_sumsq_kernel<false><<<l.count, BT, 0, s>>>(l.items, l.count, nullptr, lv, active, partials, lv32,
+                                                     r0);
+    }
     note_launch();
     return cudaGetLastError();
 }
@@ -622,7 +691,8 @@ cudaError_t launch_b_update(const BatchList& l, const BatchLevel<double>* lv, co
                             const BatchLevel<float>* lv32, cudaStream_t s)
 {
     if (l.count == 0) return cudaSuccess;
-    b_update_kernel<<<l.count, BT, 0, s>>>(l.items, lv, active, lv32);
+    const int grid = batch_grid((const void*)b_update_kernel, BT, 0, l.count, l.claim != nullptr);
+    b_update_kernel<<<grid, BT, 0, s>>>(l.items, l.count, l.claim, lv, active, lv32);
     note_launch();
     return cudaGetLastError();
 }

@@ -499,43 +499,56 @@ __global__ void __launch_bounds__(NT, 1024 / NT)
 // ---- many grids: one tile item per CTA, NT threads, regions of H rows ----
 template <int NT, int H>
 __global__ void __launch_bounds__(NT, 1024 / NT)
-    b_down32_kernel(const TileItem* __restrict__ items, const BatchLevel<float>* __restrict__ lv,
+    b_down32_kernel(const TileItem* __restrict__ items, int count, unsigned* claim,
+                    const BatchLevel<float>* __restrict__ lv,
                     const int* __restrict__ active, int nu1, int zero_u, int gs, float w, float omw)
 {
     extern __shared__ float4 smem4[];
     float* smem = reinterpret_cast<float*>(smem4);
-    const TileItem it = items[blockIdx.x];
-    const BatchLevel<float> F = lv[it.level];
-    if (active && !active[F.problem]) return;
-    const Coef32 k = coef32(F, gs != 0, w, omw);
-    on_flag32(k.unit, [&](auto U) {
-        on_flag32(k.gs, [&](auto G) {
-            down_tile<NT, H, U.value, G.value>(F, lv[it.level + 1], it.x0, it.y0, it.tx, it.ty, nu1,
-                                               zero_u != 0, k, smem, smem + ft_arr(H));
+    const ItemClaim ic{claim, count};
+    for (int b = ic.take(-1); b < count; b = ic.take(b)) {
+        const TileItem it = items[b];
+        const BatchLevel<float> F = lv[it.level];
+        if (active && !active[F.problem]) continue;
+        const Coef32 k = coef32(F, gs != 0, w, omw);
+        on_flag32(k.unit, [&](auto U) {
+            on_flag32(k.gs, [&](auto G) {
+                down_tile<NT, H, U.value, G.value>(F, lv[it.level + 1], it.x0, it.y0, it.tx, it.ty,
+                                                   nu1, zero_u != 0, k, smem, smem + ft_arr(H));
+            });
         });
-    });
+        __syncthreads();  // the next tile reloads the shared arrays
+    }
+    ic.finish();
 }
 
 template <int NT, int H>
 __global__ void __launch_bounds__(NT, 1024 / NT)
-    b_up32_kernel(const TileItem* __restrict__ items, const BatchLevel<float>* __restrict__ lv,
+    b_up32_kernel(const TileItem* __restrict__ items, int count, unsigned* claim,
+                  const BatchLevel<float>* __restrict__ lv,
                   const int* __restrict__ active, int nu2, int gs, float w, float omw,
                   const BatchLevel<double>* __restrict__ lv64)
 {
     extern __shared__ float4 smem4[];
     float* smem = reinterpret_cast<float*>(smem4);
-    const TileItem it = items[blockIdx.x];
-    const BatchLevel<float> F = lv[it.level];
-    if (active && !active[F.problem]) return;
-    double* psi = lv64 ? lv64[it.level].u : nullptr;
-    const int64_t pp = lv64 ? lv64[it.level].pitch : 0;
-    const Coef32 k = coef32(F, gs != 0, w, omw);
-    on_flag32(k.unit, [&](auto U) {
-        on_flag32(k.gs, [&](auto G) {
-            up_tile<NT, H, U.value, G.value>(F, lv[it.level + 1], it.x0, it.y0, it.tx, it.ty, nu2, k,
-                                             smem, smem + ft_arr(H), smem + 2 * ft_arr(H), psi, pp);
+    const ItemClaim ic{claim, count};
+    for (int b = ic.take(-1); b < count; b = ic.take(b)) {
+        const TileItem it = items[b];
+        const BatchLevel<float> F = lv[it.level];
+        if (active && !active[F.problem]) continue;
+        double* psi = lv64 ? lv64[it.level].u : nullptr;
+        const int64_t pp = lv64 ? lv64[it.level].pitch : 0;
+        const Coef32 k = coef32(F, gs != 0, w, omw);
+        on_flag32(k.unit, [&](auto U) {
+            on_flag32(k.gs, [&](auto G) {
+                up_tile<NT, H, U.value, G.value>(F, lv[it.level + 1], it.x0, it.y0, it.tx, it.ty, nu2,
+                                                 k, smem, smem + ft_arr(H), smem + 2 * ft_arr(H), psi,
+                                                 pp);
+            });
         });
-    });
+        __syncthreads();  // the next tile reloads the shared arrays
+    }
+    ic.finish();
 }
 
 constexpr size_t ft_smem(int H) { return (2 * (size_t)ft_arr(H) + ft_carr(H)) * sizeof(float); }
@@ -646,36 +659,52 @@ cudaError_t launch_up32(const BatchLevel<float>& F, const BatchLevel<float>& C, 
     return cudaGetLastError();
 }
 
+// The launch of a batched tile kernel over `count` items (nt threads, smem bytes; see BatchList).
+template <class... Params, class... Args>
+static void tile_launch(void (*kernel)(const TileItem*, int, unsigned*, Params...), int nt,
+                        size_t smem, const TileItem* items, int count, unsigned* claim,
+                        cudaStream_t s, Args... args)
+{
+    const int grid = batch_grid((const void*)kernel, nt, smem, count, claim != nullptr);
+    kernel<<<grid, nt, smem, s>>>(items, count, claim, args...);
+}
+
 cudaError_t launch_b_down32(const TileItem* items, int count, const BatchLevel<float>* lv,
                             const int* active, int nu1, bool zero_u, bool gs, double w, cudaStream_t s,
-                            int variant)
+                            int variant, unsigned* claim)
 {
     if (count == 0) return cudaSuccess;
     const int z = zero_u ? 1 : 0, g = gs ? 1 : 0;
     const float wf = (float)w, omw = (float)(1.0 - w);
     if (variant == 2)
-        b_down32_kernel<1024, 64><<<count, 1024, ft_smem(64), s>>>(items, lv, active, nu1, z, g, wf, omw);
+        tile_launch(b_down32_kernel<1024, 64>, 1024, ft_smem(64), items, count, claim, s,
+                    lv, active, nu1, z, g, wf, omw);
     else if (variant == 3)
-        b_down32_kernel<512, 32><<<count, 512, ft_smem(32), s>>>(items, lv, active, nu1, z, g, wf, omw);
+        tile_launch(b_down32_kernel<512, 32>, 512, ft_smem(32), items, count, claim, s,
+                    lv, active, nu1, z, g, wf, omw);
     else
-        b_down32_kernel<512, 64><<<count, 512, ft_smem(64), s>>>(items, lv, active, nu1, z, g, wf, omw);
+        tile_launch(b_down32_kernel<512, 64>, 512, ft_smem(64), items, count, claim, s,
+                    lv, active, nu1, z, g, wf, omw);
     note_launch();
     return cudaGetLastError();
 }
 
 cudaError_t launch_b_up32(const TileItem* items, int count, const BatchLevel<float>* lv,
                           const int* active, int nu2, bool gs, double w, cudaStream_t s,
-                          const BatchLevel<double>* lv64, int variant)
+                          const BatchLevel<double>* lv64, int variant, unsigned* claim)
 {
     if (count == 0) return cudaSuccess;
     const int g = gs ? 1 : 0;
     const float wf = (float)w, omw = (float)(1.0 - w);
     if (variant == 2)
-        b_up32_kernel<1024, 64><<<count, 1024, ft_smem(64), s>>>(items, lv, active, nu2, g, wf, omw, lv64);
+        tile_launch(b_up32_kernel<1024, 64>, 1024, ft_smem(64), items, count, claim, s,
+                    lv, active, nu2, g, wf, omw, lv64);
     else if (variant == 3)
-        b_up32_kernel<512, 32><<<count, 512, ft_smem(32), s>>>(items, lv, active, nu2, g, wf, omw, lv64);
+        tile_launch(b_up32_kernel<512, 32>, 512, ft_smem(32), items, count, claim, s,
+                    lv, active, nu2, g, wf, omw, lv64);
     else
-        b_up32_kernel<512, 64><<<count, 512, ft_smem(64), s>>>(items, lv, active, nu2, g, wf, omw, lv64);
+        tile_launch(b_up32_kernel<512, 64>, 512, ft_smem(64), items, count, claim, s,
+                    lv, active, nu2, g, wf, omw, lv64);
     note_launch();
     return cudaGetLastError();
 }

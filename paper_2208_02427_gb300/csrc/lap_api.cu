@@ -31,6 +31,29 @@ int device_sms()
     return sms;
 }
 
+int resident_blocks(const void* kernel, int threads, size_t smem)
+{
+    static std::mutex mu;
+    static std::map<std::tuple<const void*, int, int, size_t>, int> known;
+    const int d = attr_slot();
+    const auto key = std::make_tuple(kernel, d, threads, smem);
+    {
+        std::lock_guard<std::mutex> g(mu);
+        const auto it = known.find(key);
+        if (it != known.end()) return it->second;
+    }
+    int per = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, threads, smem) != cudaSuccess ||
+        per < 1) {
+        cudaGetLastError();
+        per = 1;
+    }
+    const int v = per * device_sms();
+    std::lock_guard<std::mutex> g(mu);
+    known[key] = v;
+    return v;
+}
+
 Coef make_coef(double dx, double dy)
 {
     Coef c;
@@ -151,6 +174,8 @@ void check_params(const lap_params* p)
             fail(LAP_EINVAL, "tiling must be -1, 0 or a tile variant 1..3");
         if (p->item_points != 0 && p->item_points < 32)
             fail(LAP_EINVAL, "item_points must be 0 or >= 32");
+        if (p->persistent < -1 || p->persistent > 1)
+            fail(LAP_EINVAL, "persistent must be -1, 0 or 1");
     }
     if ((p->method == LAP_ADI || p->method == LAP_SLOR) && p->line_form != LAP_FORM_A &&
         p->line_form != LAP_FORM_B)
@@ -478,11 +503,11 @@ std::string tuner_key(char kind, const lap_params* p, const std::vector<int>& sh
         hsh ^= (uint32_t)v;
         hsh *= 1099511628211ull;
     }
-    char buf[224];
-    std::snprintf(buf, sizeof buf, "%c %d %d %d %d %d %.17g %d %d %d %d %d %zu %llx", kind, p->method,
-                  p->nu1, p->nu2, p->coarsest_min, p->max_levels, p->smoother_w, p->inner_cycles,
-                  p->tail_size, p->unfused, p->tiling, p->item_points, shape.size(),
-                  (unsigned long long)hsh);
+    char buf[240];
+    std::snprintf(buf, sizeof buf, "%c %d %d %d %d %d %.17g %d %d %d %d %d %d %zu %llx", kind,
+                  p->method, p->nu1, p->nu2, p->coarsest_min, p->max_levels, p->smoother_w,
+                  p->inner_cycles, p->tail_size, p->unfused, p->tiling, p->item_points,
+                  p->persistent, shape.size(), (unsigned long long)hsh);
     return buf;
 }
 

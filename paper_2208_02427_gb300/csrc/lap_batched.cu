@@ -137,7 +137,7 @@ struct BatchKey {
     std::vector<lap_grid> grids;
     std::vector<const double*> psi;
     int32_t method, norm, nu1, nu2, coarsest_min, max_levels, inner_cycles, tail_size, unfused,
-        tiling, item_points;
+        tiling, item_points, persistent;
     double smoother_w, tol;
     bool operator==(const BatchKey& o) const
     {
@@ -150,8 +150,8 @@ struct BatchKey {
         return method == o.method && norm == o.norm && nu1 == o.nu1 && nu2 == o.nu2 &&
                coarsest_min == o.coarsest_min && max_levels == o.max_levels &&
                inner_cycles == o.inner_cycles && tail_size == o.tail_size && unfused == o.unfused &&
-               tiling == o.tiling && item_points == o.item_points && smoother_w == o.smoother_w &&
-               tol == o.tol;
+               tiling == o.tiling && item_points == o.item_points && persistent == o.persistent &&
+               smoother_w == o.smoother_w && tol == o.tol;
     }
 };
 
@@ -169,6 +169,7 @@ struct BatchCache : BatchCacheBase {
     int *first = nullptr, *active = nullptr, *status = nullptr, *remaining = nullptr;
     long long* iters = nullptr;
     double *r0 = nullptr, *rnow = nullptr, *partials = nullptr;
+    unsigned* claim = nullptr;  // item counter of the persistent launches (two words, zero between launches)
     std::vector<CandPlan> cands;  // indexed like the tuner's candidates
     ~BatchCache() override
     {
@@ -195,6 +196,7 @@ BatchKey make_key(int count, const lap_grid* grids, double* const* psi_devs, con
     k.unfused = p->unfused;
     k.tiling = p->tiling;
     k.item_points = p->item_points;
+    k.persistent = p->persistent;
     k.smoother_w = p->smoother_w;
     k.tol = p->tol;
     return k;
@@ -202,9 +204,9 @@ BatchKey make_key(int count, const lap_grid* grids, double* const* psi_devs, con
 
 // The configurations a batched solve of these parameters tries (first = the default of each
 // knob): tail sizes, FP32 tilings (mixed solver, tiles allowed: the tile variants and one
-// kernel per pass), work-item sizes.
+// kernel per pass), work-item sizes, one CTA per item or persistent launches.
 void tuner_values(const lap_params* p, std::vector<int>* tails, std::vector<int>* tilings,
-                  std::vector<int>* items)
+                  std::vector<int>* items, std::vector<int>* persists)
 {
     const bool mixed = p->method == LAP_MG_MIXED;
     *tails = tail_candidates(true, mixed, p->tail_size);
@@ -218,6 +220,8 @@ void tuner_values(const lap_params* p, std::vector<int>* tails, std::vector<int>
     if (tilings->empty()) tilings->push_back(0);  // one kernel per pass
     if (p->item_points > 0) *items = {p->item_points};
     else *items = {BATCH_ITEM_POINTS, 2048, 32768};
+    if (p->persistent != 0) *persists = {p->persistent > 0 ? 1 : 0};
+    else *persists = {0, 1};
 }
 
 // The level descriptors, the norm list, the arena carved for them (level buffers first) and
@@ -312,6 +316,7 @@ std::unique_ptr<BatchCache> build_plan(lap_handle h, int count, const lap_grid* 
         C->r0 = cv.template take<double>(count);
         C->rnow = cv.template take<double>(count);
         C->partials = cv.template take<double>(std::max<size_t>(1, P.norm_items.size()));
+        C->claim = cv.template take<unsigned>(2);
     };
     Sizer sz;
     carve_all(sz);
@@ -323,6 +328,7 @@ std::unique_ptr<BatchCache> build_plan(lap_handle h, int count, const lap_grid* 
     ck(cudaMemcpyAsync(C->lv32, P.lv32.data(), P.lv32.size() * sizeof(P.lv32[0]), cudaMemcpyHostToDevice, s), "upload levels");
     ck(cudaMemcpyAsync(C->norm_items, P.norm_items.data(), P.norm_items.size() * sizeof(BatchItem), cudaMemcpyHostToDevice, s), "upload items");
     ck(cudaMemcpyAsync(C->first, P.first_item.data(), P.first_item.size() * sizeof(int), cudaMemcpyHostToDevice, s), "upload items");
+    ck(cudaMemsetAsync(C->claim, 0, 2 * sizeof(unsigned), s), "zero claim counter");
     C->key = make_key(count, grids, psi_devs, p);
     return C;
 }
@@ -343,6 +349,7 @@ CandPlan& ensure_candidate(BatchCache& C, int c, const BatchConfig& cfg, const l
     std::vector<TileItem> tiles;
     build_lists(K.L, items, jobs, all_problems, P.base, P.nlev, P.lv64, cfg.tail,
                 cfg.tiles > 0 ? &tiles : nullptr, p->nu1, p->nu2, std::max(1, cfg.tiles), cfg.item);
+    K.L.claim = cfg.persist != 0 ? C.claim : nullptr;
     // one allocation: items, jobs, tiles (each 256-byte aligned)
     Sizer sz;
     sz.take<BatchItem>(std::max<size_t>(1, items.size()));
@@ -390,9 +397,9 @@ extern "C" int lap_solve_batched(lap_handle h, int count, const lap_grid* grids,
         }
         BatchTuner& tuner = h->batch_tuners[tuner_key('B', p, shape)];
         if (tuner.cand.empty()) {
-            std::vector<int> tails, tilings, items;
-            tuner_values(p, &tails, &tilings, &items);
-            tuner.init(tails, tilings, items);
+            std::vector<int> tails, tilings, items, persists;
+            tuner_values(p, &tails, &tilings, &items, &persists);
+            tuner.init(tails, tilings, items, persists);
         }
         if (mixed && !p->unfused && fused32_supported(p->nu1, p->nu2))
             ck(prepare_fused32(), "tile kernel attributes");
@@ -430,7 +437,10 @@ extern "C" int lap_solve_batched(lap_handle h, int count, const lap_grid* grids,
             // ---- one cycle (V-cycle(s) and stopping test) with candidate c's lists ----
             auto cycle = [&](const CandPlan& K, cudaStream_t st) {
                 const LevelLists& L = K.L;
-                auto list = [&](std::pair<int, int> r) { return BatchList{K.items + r.first, r.second}; };
+                auto list = [&](std::pair<int, int> r) {
+                    return BatchList{K.items + r.first, r.second, L.claim};
+                };
+                const BatchList norms{norm_list.items, norm_list.count, L.claim};
                 if (mixed) {
                     for (int k = 0; k < p->inner_cycles; ++k) {
                         if (L.fused)
@@ -440,12 +450,12 @@ extern "C" int lap_solve_batched(lap_handle h, int count, const lap_grid* grids,
                             enqueue_vcycle(list, L, lv32, active, K.jobs, *p, p->smoother_w, st);
                     }
                     // fused: the level-0 ascents did psi += e except where a tail holds level 0
-                    ck(launch_b_update(L.fused ? list(L.upd0) : norm_list, lv64, active, lv32, st),
+                    ck(launch_b_update(L.fused ? list(L.upd0) : norms, lv64, active, lv32, st),
                        "batched update");
-                    ck(launch_b_sumsq(norm_list, lv64, active, partials, lv32, st, r0), "batched residual");
+                    ck(launch_b_sumsq(norms, lv64, active, partials, lv32, st, r0), "batched residual");
                 } else {
                     enqueue_vcycle(list, L, lv64, active, K.jobs, *p, p->smoother_w, st);
-                    ck(launch_b_sumsq(norm_list, lv64, active, partials, nullptr, st), "batched residual");
+                    ck(launch_b_sumsq(norms, lv64, active, partials, nullptr, st), "batched residual");
                 }
                 ck(launch_b_converge(partials, first, count, active, r0, rnow, iters, status, remaining,
                                      1, rel, p->tol, st), "batched convergence");
@@ -549,13 +559,14 @@ extern "C" int lap_solve_batched(lap_handle h, int count, const lap_grid* grids,
 }
 
 extern "C" int lap_last_batch_config(lap_handle h, int32_t* tail_size, int32_t* tiling,
-                                     int32_t* item_points, int32_t* tuned)
+                                     int32_t* item_points, int32_t* persistent, int32_t* tuned)
 {
     return guarded([&] {
         if (!h) fail(LAP_EINVAL, "handle is NULL");
         if (tail_size) *tail_size = h->last_batch.tail;
         if (tiling) *tiling = h->last_batch.tiles == 0 ? -1 : h->last_batch.tiles;
         if (item_points) *item_points = h->last_batch.item;
+        if (persistent) *persistent = h->last_batch.item == 0 ? 0 : (h->last_batch.persist ? 1 : -1);
         if (tuned) *tuned = h->last_batch_tuned ? 1 : 0;
     });
 }

@@ -239,4 +239,33 @@ __device__ __forceinline__ unsigned long long abs_bits(double x)
     return static_cast<unsigned long long>(__double_as_longlong(x)) & 0x7fffffffffffffffull;
 }
 
+// The work items a CTA of a batched launch takes. Without a claim counter: item blockIdx.x
+// alone (one CTA per item). With one (a persistent launch of as many CTAs as fit the device):
+// each CTA takes the next unclaimed item from claim[0] until none is left, so CTAs that drew
+// cheap items (small, or of converged problems) take more. claim[1] counts the CTAs that have
+// finished; the last one resets both words for the next launch on the stream, which starts
+// after this one ends. No CTA waits for another.
+struct ItemClaim {
+    unsigned* claim;
+    int count;
+    __device__ __forceinline__ int take(int prev) const
+    {
+        if (!claim) return prev < 0 ? (int)blockIdx.x : count;
+        __shared__ int s_item;
+        __syncthreads();  // every thread has read the previous item
+        if (threadIdx.x == 0) s_item = (int)atomicAdd(claim, 1u);
+        __syncthreads();
+        return s_item;
+    }
+    __device__ __forceinline__ void finish() const
+    {
+        if (!claim || threadIdx.x != 0) return;
+        __threadfence();
+        if (atomicAdd(claim + 1, 1u) == gridDim.x - 1) {
+            claim[0] = 0u;
+            claim[1] = 0u;
+        }
+    }
+};
+
 }  // namespace lap

@@ -71,13 +71,18 @@ struct BatchConfig {
                 // 1..FUSED32_VARIANTS = a level's whole descent / ascent per tile load (depth nu)
                 // with that tile variant (CTA size and region rows)
     int item;   // interior points per work item of the per-pass kernels
-    bool operator==(const BatchConfig& o) const { return tail == o.tail && tiles == o.tiles && item == o.item; }
+    int persist;  // 1: every phase a persistent launch (resident CTAs claim its items), 0: one CTA per item
+    bool operator==(const BatchConfig& o) const
+    {
+        return tail == o.tail && tiles == o.tiles && item == o.item && persist == o.persist;
+    }
 };
 
 // Chooses a batched solve's configuration by timing real cycles, one knob at a time (a
 // coordinate search): stage 0 the small-level tail (the level-to-CTA mapping), stage 1 the
 // FP32 levels' temporal blocking and tile shape (mixed solver), stage 2 the work-item size of
-// the per-pass kernels (when some run). A stage's candidates are the best configuration so far
+// the per-pass kernels (when some run), stage 3 one CTA per work item or persistent launches
+// (resident CTAs claiming items from a counter). A stage's candidates are the best configuration so far
 // with that one knob changed; each is timed on one cycle in which every problem still runs
 // (the graph of a candidate is captured on an earlier cycle), and the fastest is kept. The
 // cycles being timed are real cycles of the solve, and all candidates give the same iterates.
@@ -88,17 +93,19 @@ struct BatchTuner {
     int stage = 0;
     int stage_begin = 0;
     bool done = false;
-    std::vector<int> tails, tilings, items;  // the values each stage tries
-    void init(std::vector<int> tail_values, std::vector<int> tiling_values, std::vector<int> item_values)
+    std::vector<int> tails, tilings, items, persists;  // the values each stage tries
+    void init(std::vector<int> tail_values, std::vector<int> tiling_values, std::vector<int> item_values,
+              std::vector<int> persist_values)
     {
         tails = std::move(tail_values);
         tilings = std::move(tiling_values);
         items = std::move(item_values);
+        persists = std::move(persist_values);
         cand.clear();
         ms.clear();
         best = stage = stage_begin = 0;
         done = false;
-        for (int t : tails) add(BatchConfig{t, tilings.front(), items.front()});
+        for (int t : tails) add(BatchConfig{t, tilings.front(), items.front(), persists.front()});
         if (cand.size() <= 1) advance();
     }
     void add(BatchConfig c)
@@ -127,15 +134,16 @@ struct BatchTuner {
     // The next stage with more than the current best to try, or done.
     void advance()
     {
-        while (stage < 2) {
+        while (stage < 3) {
             ++stage;
             stage_begin = (int)cand.size();
             const BatchConfig b = cand[best];
-            const std::vector<int>& values = stage == 1 ? tilings : items;
+            const std::vector<int>& values = stage == 1 ? tilings : stage == 2 ? items : persists;
             for (int v : values) {
                 BatchConfig c = b;
                 if (stage == 1) c.tiles = v;
-                else c.item = v;
+                else if (stage == 2) c.item = v;
+                else c.persist = v;
                 if (c == b) continue;
                 if (stage == 2 && b.tiles != 0 && c.item != b.item) {
                     // with tiles the per-pass kernels only serve the tail's neighbours: skip
@@ -222,7 +230,7 @@ struct lap_handle_s {
     // Small-level tail sizes chosen by timing, per shape (see TailTuner)
     std::map<std::string, lap::TailTuner> tail_tuners;
     std::map<std::string, lap::BatchTuner> batch_tuners;  // batched solves' configurations
-    lap::BatchConfig last_batch{0, 0, 0};  // the configuration the last batched cycle ran
+    lap::BatchConfig last_batch{0, 0, 0, 0};  // the configuration the last batched cycle ran
     bool last_batch_tuned = false;         // whether its tuner had finished
     cudaEvent_t ev[2] = {nullptr, nullptr};
     // y-line scratch of line relaxation: forward-elimination values and chunk ends (grown on
@@ -310,6 +318,7 @@ struct LevelLists {
     std::pair<int, int> upd0{0, 0};  // fused: level-0 items of the problems without level-0 tiles
     bool fused = false;
     int tile_variant = 1;  // the fused FP32 levels' tile variant
+    unsigned* claim = nullptr;  // non-null: every launch persistent, claiming items here (BatchList)
     int levels = 0;
     int max_coarse = 0;
 };
@@ -338,7 +347,7 @@ void enqueue_vcycle(ListFn list, const LevelLists& L, const BatchLevel<T>* lv, c
     for (int l = 0; l < L.levels; ++l) {
         ck(launch_b_coarse(list(L.coarse[l]), lv, active, L.max_coarse, st), "batched coarse");
         ck(launch_b_tail(jobs + L.tail[l].first, L.tail[l].second, lv, active, p.nu1, p.nu2, gs,
-                         smoother_w, L.max_coarse, st),
+                         smoother_w, L.max_coarse, st, false, L.claim),
            "batched tail");
         if (l == L.levels - 1) break;
         for (int k = 0; k < p.nu1; ++k)
@@ -368,16 +377,16 @@ void enqueue_vcycle32_fused(ListFn list, const LevelLists& L, const BatchLevel<f
     for (int l = 0; l < L.levels; ++l) {
         ck(launch_b_coarse(list(L.coarse[l]), lv, active, L.max_coarse, st), "batched coarse");
         ck(launch_b_tail(jobs + L.tail[l].first, L.tail[l].second, lv, active, p.nu1, p.nu2, gs,
-                         smoother_w, L.max_coarse, st),
+                         smoother_w, L.max_coarse, st, false, L.claim),
            "batched tail");
         if (l == L.levels - 1) break;
         ck(launch_b_down32(tiles + L.tiles[l].first, L.tiles[l].second, lv, active, p.nu1,
-                           l > 0 || first, gs, smoother_w, st, L.tile_variant),
+                           l > 0 || first, gs, smoother_w, st, L.tile_variant, L.claim),
            "batched descent");
     }
     for (int l = L.levels - 2; l >= 0; --l)
         ck(launch_b_up32(tiles + L.tiles[l].first, L.tiles[l].second, lv, active, p.nu2, gs,
-                         smoother_w, st, l == 0 ? fold64 : nullptr, L.tile_variant),
+                         smoother_w, st, l == 0 ? fold64 : nullptr, L.tile_variant, L.claim),
            "batched ascent");
 }
 

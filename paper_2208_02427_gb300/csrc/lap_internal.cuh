@@ -193,10 +193,25 @@ struct BatchItem {
     int row0;   // first interior row
     int rows;   // rows in this item
 };
+// A work list of one launch. claim (nullable): two words of device memory, zero between
+// launches; with it the launch is persistent -- as many CTAs as fit the device at once, each
+// taking the next unclaimed item until none is left (ItemClaim) -- and without it one CTA per
+// item. Either way every item gets the same arithmetic.
 struct BatchList {
     const BatchItem* items;
     int count;
+    unsigned* claim = nullptr;
 };
+// CTAs of `kernel` (threads per CTA, dynamic shared memory) resident on the current device at
+// once: multiprocessors x CTAs per multiprocessor, looked up once per kernel and device.
+int resident_blocks(const void* kernel, int threads, size_t smem);
+// The grid of a launch over `count` items: count, or when persistent at most resident_blocks.
+inline int batch_grid(const void* kernel, int threads, size_t smem, int count, bool persist)
+{
+    if (!persist) return count;
+    const int r = resident_blocks(kernel, threads, smem);
+    return r < count ? r : count;
+}
 // The small-level tail of one problem's V-cycle: levels first .. last (its coarsest) of lv.
 struct TailJob {
     int first, last;
@@ -225,10 +240,11 @@ cudaError_t launch_b_coarse(const BatchList& l, const BatchLevel<T>* lv, const i
 // One CTA per job runs the V-cycle from level `first` down to the coarsest and back (nu1/nu2
 // smoothing sweeps, gs or SOR with w, or each level's own w); active may be null (all run).
 // max_unknowns: the largest coarsest level among the jobs.
+// claim (nullable): a persistent launch over the jobs (see BatchList).
 template <class T>
 cudaError_t launch_b_tail(const TailJob* jobs, int count, const BatchLevel<T>* lv, const int* active,
                           int nu1, int nu2, bool gs, double w, int max_unknowns, cudaStream_t s,
-                          bool per_level_w = false);
+                          bool per_level_w = false, unsigned* claim = nullptr);
 // per-item FP64 sum of squares of the residual; with lv32 also r32 := residual, e32 := 0;
 // with r0 (per problem) the mixed problems sum their squares in FP32 after an exact
 // power-of-two scaling from r0 (the partials are stored descaled)
@@ -280,13 +296,15 @@ cudaError_t launch_up32(const BatchLevel<float>& F, const BatchLevel<float>& C, 
                         bool gs, double w, cudaStream_t s, double* psi = nullptr,
                         int64_t psi_pitch = 0);
 // The same over tile items of many problems (the coarse level of item level l is l + 1).
+// claim (nullable): a persistent launch over the tiles (see BatchList).
 cudaError_t launch_b_down32(const TileItem* items, int count, const BatchLevel<float>* lv,
                             const int* active, int nu1, bool zero_u, bool gs, double w, cudaStream_t s,
-                            int variant = 1);
+                            int variant = 1, unsigned* claim = nullptr);
 // lv64 (nullable): items' FP64 fields (same level indices) take psi += result instead.
 cudaError_t launch_b_up32(const TileItem* items, int count, const BatchLevel<float>* lv,
                           const int* active, int nu2, bool gs, double w, cudaStream_t s,
-                          const BatchLevel<double>* lv64 = nullptr, int variant = 1);
+                          const BatchLevel<double>* lv64 = nullptr, int variant = 1,
+                          unsigned* claim = nullptr);
 
 // ---- line relaxation (line_kernels.cu) --------------------------------------------
 // Constant-coefficient tridiagonal systems -alpha x_{k-1} + delta x_k - alpha x_{k+1} = b_k,

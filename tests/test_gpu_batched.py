@@ -115,8 +115,9 @@ def test_repeated_batched_solves_reuse_the_plan(b, method):
 @pytest.mark.parametrize("method", ["mg", "mg_mixed"])
 def test_batched_launch_configurations_are_bitwise_equal(b, method):
     """The batched solver's tuner chooses the tail size, the FP32 levels' tiling (tile variant
-    or one kernel per pass) and the work-item size by timing; every choice must give the same
-    iterates, cycle counts and norms bit for bit (ragged tiles, beta != 1, tiny grids)."""
+    or one kernel per pass), the work-item size and persistent or one-CTA-per-item launches by
+    timing; every choice must give the same iterates, cycle counts and norms bit for bit
+    (ragged tiles, beta != 1, tiny grids)."""
     shapes = [(33, 129), (257, 65), (129, 129), (513, 257), (65, 33), (9, 17), (3, 3), (1025, 257)]
     inputs = [wl.random_ring(m, n, seed=700 + k) for k, (m, n) in enumerate(shapes)]
     dxs = [1.0 if k % 3 else 0.8 for k in range(len(shapes))]
@@ -127,12 +128,15 @@ def test_batched_launch_configurations_are_bitwise_equal(b, method):
         res = lap.solve_batched(fields, dxs, 1.0, method=method, tol=0.0, max_iter=3, **kw)
         return [host(f) for f in fields], [(r["iters"], r["r_final"]) for r in res]
 
-    ref = run(tail_size=-1, tiling=-1, item_points=8192)
+    ref = run(tail_size=-1, tiling=-1, item_points=8192, persistent=-1)
     configs = [dict(item_points=64), dict(item_points=2048), dict(item_points=32768),
-               dict(tail_size=65), dict(tail_size=257, item_points=2048), dict()]
+               dict(tail_size=65), dict(tail_size=257, item_points=2048), dict(),
+               dict(persistent=1, tail_size=-1, tiling=-1), dict(persistent=1, item_points=64),
+               dict(persistent=1, tail_size=33)]
     if method == "mg_mixed":
         configs += [dict(tiling=1), dict(tiling=2), dict(tiling=3), dict(tiling=2, tail_size=33),
-                    dict(tiling=3, tail_size=129)]
+                    dict(tiling=3, tail_size=129), dict(tiling=1, persistent=1),
+                    dict(tiling=2, persistent=1, tail_size=65), dict(tiling=3, persistent=1)]
     for kw in configs:
         got = run(**kw)
         assert got[1] == ref[1], kw
@@ -147,4 +151,6 @@ def test_batched_launch_configurations_are_bitwise_equal(b, method):
         run(tiling=4)
     with pytest.raises(b.LapError):
         run(item_points=16)
+    with pytest.raises(b.LapError):
+        run(persistent=2)
     lap.close()
