@@ -27,6 +27,7 @@ FORM_A, FORM_B = 0, 1
 JACOBI, GS, SOR, SLOR, ADI, MG = range(6)
 NORM_L2_REL, NORM_L2_ABS, NORM_MAXDELTA = 0, 1, 2
 COARSE_DIRECT, COARSE_GS = 0, 1
+SUM_PAPER, SUM_DIAGONAL = 0, 1
 STATUS = {0: "converged", 1: "max_iter", 2: "diverged"}
 
 
@@ -53,6 +54,7 @@ class _Params(C.Structure):
         ("w", C.c_double), ("norm", C.c_int), ("tol", C.c_double), ("max_iter", C.c_long),
         ("check_every", C.c_int), ("nu1", C.c_int), ("nu2", C.c_int),
         ("coarsest_min", C.c_int), ("max_levels", C.c_int), ("coarse", C.c_int),
+        ("sum_order", C.c_int),
     ]
 
 
@@ -71,6 +73,8 @@ def lib():
             "ora_jacobi_sweep": (None, [i, i, d, dp, dp]),
             "ora_gs_sweep": (None, [i, i, d, i, dp, dp]),
             "ora_sor_sweep": (None, [i, i, d, d, i, dp, dp]),
+            "ora_gs_sweep_ordered": (i, [i, i, d, i, i, dp, dp]),
+            "ora_sor_sweep_ordered": (i, [i, i, d, d, i, i, dp, dp]),
             "ora_thomas": (None, [i, dp, dp, dp, dp, dp, dp, dp]),
             "ora_line_sweep": (None, [i, i, d, d, i, i, i, dp]),
             "ora_adi_iteration": (None, [i, i, d, d, i, i, dp]),
@@ -149,17 +153,23 @@ def jacobi_sweep(psi, beta=1.0):
     return out
 
 
-def gs_sweep(psi, beta=1.0, ordering=RB, q=None):
+def gs_sweep(psi, beta=1.0, ordering=RB, q=None, sum_order=SUM_PAPER):
     psi = _field(psi).copy()
     n, m = psi.shape
-    lib().ora_gs_sweep(m, n, beta, ordering, _ptr(psi), _ptr(None if q is None else _field(q)))
+    rc = lib().ora_gs_sweep_ordered(m, n, beta, ordering, sum_order, _ptr(psi),
+                                    _ptr(None if q is None else _field(q)))
+    if rc:
+        raise ValueError("the diagonal summation order needs beta = 1")
     return psi
 
 
-def sor_sweep(psi, w, beta=1.0, ordering=RB, q=None):
+def sor_sweep(psi, w, beta=1.0, ordering=RB, q=None, sum_order=SUM_PAPER):
     psi = _field(psi).copy()
     n, m = psi.shape
-    lib().ora_sor_sweep(m, n, beta, w, ordering, _ptr(psi), _ptr(None if q is None else _field(q)))
+    rc = lib().ora_sor_sweep_ordered(m, n, beta, w, ordering, sum_order, _ptr(psi),
+                                     _ptr(None if q is None else _field(q)))
+    if rc:
+        raise ValueError("the diagonal summation order needs beta = 1")
     return psi
 
 
@@ -218,12 +228,12 @@ def mg_levels(m, n, coarsest_min=5, max_levels=0):
 
 def solve(psi, method, dx=1.0, dy=1.0, w=1.0, tol=1e-10, norm=NORM_L2_REL, max_iter=100000,
           check_every=1, ordering=RB, line_order=LINES_ZEBRA, form=FORM_A, nu1=2, nu2=2,
-          coarsest_min=5, max_levels=0, coarse=COARSE_DIRECT, history=False):
+          coarsest_min=5, max_levels=0, coarse=COARSE_DIRECT, history=False, sum_order=SUM_PAPER):
     """Run ``ora_solve``; returns (psi, info) with info = dict(status, iters, r0, r_final[, hist])."""
     psi = _field(psi).copy()
     n, m = psi.shape
     p = _Params(method, ordering, line_order, form, w, norm, tol, max_iter, check_every, nu1,
-                nu2, coarsest_min, max_levels, coarse)
+                nu2, coarsest_min, max_levels, coarse, sum_order)
     iters, r0, rf = C.c_long(0), C.c_double(0), C.c_double(0)
     hist = np.zeros(max(1, max_iter // check_every + 1)) if history else None
     rc = lib().ora_solve(m, n, dx, dy, _ptr(psi), C.byref(p), C.byref(iters), C.byref(r0),

@@ -49,6 +49,22 @@ static double neighbour_sum(const double* p, int m, int i, int j, double b2)
     return fma(b2, ns, ew);
 }
 
+/* The same sum for beta = 1 with the four terms paired the other way, west with south and
+ * east with north: (psi_{i-1,j} + psi_{i,j-1}) + (psi_{i+1,j} + psi_{i,j+1}). Eq. 5 fixes no
+ * order of its additions; this one differs from neighbour_sum only in rounding. */
+static double neighbour_sum_diagonal(const double* p, int m, int i, int j)
+{
+    double ws = AT(p, m, i - 1, j) + AT(p, m, i, j - 1);
+    double en = AT(p, m, i + 1, j) + AT(p, m, i, j + 1);
+    return ws + en;
+}
+
+static double neighbour_sum_ordered(const double* p, int m, int i, int j, double b2, int order)
+{
+    return order == ORA_SUM_DIAGONAL ? neighbour_sum_diagonal(p, m, i, j)
+                                     : neighbour_sum(p, m, i, j, b2);
+}
+
 /* ------------------------------------------------------------------------- */
 /* Residual, Eqs. 11-12. R = L(psi) is scaled by dx^2 so that it reads
  * r = (E + W) + beta^2 (N + S) - d psi, plus the source term q of a coarse level
@@ -101,38 +117,54 @@ static int visits(int ordering, int colour, int i, int j)
     return ordering == ORA_RB ? ((i + j) & 1) == colour : 1;
 }
 
-/* Gauss-Seidel, Eq. 6 (source q on coarse levels). */
-void ora_gs_sweep(int m, int n, double beta, int ordering, double* psi, const double* q)
+/* Gauss-Seidel, Eq. 6 (source q on coarse levels), neighbour sum in order sum_order. */
+int ora_gs_sweep_ordered(int m, int n, double beta, int ordering, int sum_order, double* psi,
+                         const double* q)
 {
     double b2, d;
     coefficients(beta, &b2, &d);
+    if (sum_order == ORA_SUM_DIAGONAL && b2 != 1.0) return -1;
     double inv_d = 1.0 / d;
     for (int c = 0; c < colour_count(ordering); ++c)
         for (int j = 1; j < n - 1; ++j)
             for (int i = 1; i < m - 1; ++i) {
                 if (!visits(ordering, c, i, j)) continue;
-                double s = neighbour_sum(psi, m, i, j, b2);
+                double s = neighbour_sum_ordered(psi, m, i, j, b2, sum_order);
                 if (q) s = s + AT(q, m, i, j);
                 AT(psi, m, i, j) = s * inv_d;
             }
+    return 0;
+}
+
+void ora_gs_sweep(int m, int n, double beta, int ordering, double* psi, const double* q)
+{
+    ora_gs_sweep_ordered(m, n, beta, ordering, ORA_SUM_PAPER, psi, q);
 }
 
 /* SOR, Eq. 7: psi^{k+1} = (1 - w) psi^k + w * (Gauss-Seidel value of Eq. 6). */
-void ora_sor_sweep(int m, int n, double beta, double w, int ordering, double* psi,
-                   const double* q)
+int ora_sor_sweep_ordered(int m, int n, double beta, double w, int ordering, int sum_order,
+                          double* psi, const double* q)
 {
     double b2, d;
     coefficients(beta, &b2, &d);
+    if (sum_order == ORA_SUM_DIAGONAL && b2 != 1.0) return -1;
     double inv_d = 1.0 / d, one_minus_w = 1.0 - w;
     for (int c = 0; c < colour_count(ordering); ++c)
         for (int j = 1; j < n - 1; ++j)
             for (int i = 1; i < m - 1; ++i) {
                 if (!visits(ordering, c, i, j)) continue;
-                double s = neighbour_sum(psi, m, i, j, b2);
+                double s = neighbour_sum_ordered(psi, m, i, j, b2, sum_order);
                 if (q) s = s + AT(q, m, i, j);
                 double gs = s * inv_d;
                 AT(psi, m, i, j) = fma(w, gs, one_minus_w * AT(psi, m, i, j));
             }
+    return 0;
+}
+
+void ora_sor_sweep(int m, int n, double beta, double w, int ordering, double* psi,
+                   const double* q)
+{
+    ora_sor_sweep_ordered(m, n, beta, w, ordering, ORA_SUM_PAPER, psi, q);
 }
 
 /* ------------------------------------------------------------------------- */
@@ -408,6 +440,10 @@ int ora_solve(int m, int n, double dx, double dy, double* psi, const ora_params*
         p->max_iter < 0 || !(p->tol >= 0.0))
         return -1;
     if (p->method < ORA_JACOBI || p->method > ORA_MG) return -1;
+    if (p->sum_order != ORA_SUM_PAPER && p->sum_order != ORA_SUM_DIAGONAL) return -1;
+    if (p->sum_order == ORA_SUM_DIAGONAL &&
+        ((p->method != ORA_GS && p->method != ORA_SOR) || dx != dy))
+        return -1;
     double beta = dx / dy;
     size_t sz = (size_t)m * (size_t)n;
     double* prev = (double*)malloc(sizeof(double) * sz);
@@ -446,8 +482,10 @@ int ora_solve(int m, int n, double dx, double dy, double* psi, const ora_params*
             ora_jacobi_sweep(m, n, beta, psi, tmp);
             memcpy(psi, tmp, sizeof(double) * sz);
             break;
-        case ORA_GS: ora_gs_sweep(m, n, beta, p->ordering, psi, NULL); break;
-        case ORA_SOR: ora_sor_sweep(m, n, beta, p->w, p->ordering, psi, NULL); break;
+        case ORA_GS: ora_gs_sweep_ordered(m, n, beta, p->ordering, p->sum_order, psi, NULL); break;
+        case ORA_SOR:
+            ora_sor_sweep_ordered(m, n, beta, p->w, p->ordering, p->sum_order, psi, NULL);
+            break;
         case ORA_SLOR: ora_line_sweep(m, n, beta, p->w, p->form, 0, p->line_order, psi); break;
         case ORA_ADI: ora_adi_iteration(m, n, beta, p->w, p->form, p->line_order, psi); break;
         case ORA_MG:

@@ -39,6 +39,11 @@ enum { ORA_NORM_L2_REL = 0,   /* ||r(psi^k)||_2 <= tol * ||r(psi^0)||_2 */
        ORA_NORM_L2_ABS = 1,   /* ||r(psi^k)||_2 <= tol */
        ORA_NORM_MAXDELTA = 2 };/* max |psi^k - psi^(k-1)| <= tol, Eq. 16 */
 
+/* rounding order of the 4-term neighbour sum of Eqs. 5-7 (the paper writes the sum and fixes
+ * no order; both orders are the same sum) */
+enum { ORA_SUM_PAPER = 0,     /* (E + W) + beta^2 (N + S), as the equation is printed */
+       ORA_SUM_DIAGONAL = 1 };/* (W + S) + (E + N), beta = 1 only */
+
 /* coarsest-level solver for the V-cycle */
 enum { ORA_COARSE_DIRECT = 0,   /* Gaussian elimination with partial pivoting */
        ORA_COARSE_GS = 1 };     /* Gauss-Seidel until the update stops changing */
@@ -57,6 +62,7 @@ typedef struct {
     int coarsest_min;  /* MG: coarsen while both coarse sides stay >= this */
     int max_levels;    /* MG: 0 = as many as the sizes allow */
     int coarse;        /* ORA_COARSE_* */
+    int sum_order;     /* ORA_SUM_* for the GS and SOR methods (beta = 1 for DIAGONAL) */
 } ora_params;
 
 /* ---- building blocks (each cites the passage it follows) ---- */
@@ -71,6 +77,12 @@ void ora_jacobi_sweep(int m, int n, double beta, const double* in, double* out);
 void ora_gs_sweep(int m, int n, double beta, int ordering, double* psi, const double* q);
 /* One SOR sweep, Eq. 7 (with source q when non-NULL), in place. */
 void ora_sor_sweep(int m, int n, double beta, double w, int ordering, double* psi, const double* q);
+/* The same two sweeps with the neighbour sum in order sum_order (ORA_SUM_*; DIAGONAL needs
+ * beta = 1 and returns -1 otherwise, leaving psi unchanged). */
+int ora_gs_sweep_ordered(int m, int n, double beta, int ordering, int sum_order, double* psi,
+                         const double* q);
+int ora_sor_sweep_ordered(int m, int n, double beta, double w, int ordering, int sum_order,
+                          double* psi, const double* q);
 
 /* Thomas algorithm: a[i] x[i-1] + b[i] x[i] + c[i] x[i+1] = d[i], i = 0..N-1. */
 void ora_thomas(int N, const double* a, const double* b, const double* c, const double* d,

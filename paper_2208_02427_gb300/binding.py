@@ -24,6 +24,7 @@ METHODS = {"jacobi": 0, "gs": 1, "sor": 2, "adi": 3, "mg": 4, "mg_mixed": 5, "sl
            "gs_lex": 7, "sor_lex": 8}
 NORMS = {"l2_rel": 0, "l2_abs": 1, "maxdelta": 2}
 FORMS = {"A": 0, "B": 1}
+SUM_ORDERS = {"paper": 0, "diagonal": 1}
 STATUS = {0: "converged", 1: "max_iter", 2: "diverged"}
 ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "EUNSUPPORTED"}
 
@@ -45,7 +46,7 @@ class Params(C.Structure):
                 ("nu2", c_int32), ("coarsest_min", c_int32), ("max_levels", c_int32),
                 ("smoother_w", c_double), ("line_form", c_int32), ("inner_cycles", c_int32),
                 ("tail_size", c_int32), ("unfused", c_int32), ("tiling", c_int32),
-                ("item_points", c_int32), ("persistent", c_int32)]
+                ("item_points", c_int32), ("persistent", c_int32), ("sum_order", c_int32)]
 
 
 class Result(C.Structure):
@@ -166,11 +167,12 @@ def _stream(stream, device):
 def params(method="sor", w=1.0, tol=1e-10, norm="l2_rel", max_iter=100000, check_every=1,
            nu1=2, nu2=2, coarsest_min=5, max_levels=0, smoother_w=1.0, line_form="A",
            inner_cycles=1, tail_size=0, unfused=False, tiling=0, item_points=0,
-           persistent=0) -> Params:
+           persistent=0, sum_order="paper") -> Params:
     return Params(METHODS[method], float(w), float(tol), NORMS[norm], int(max_iter),
                   int(check_every), int(nu1), int(nu2), int(coarsest_min), int(max_levels),
                   float(smoother_w), FORMS[line_form], int(inner_cycles), int(tail_size),
-                  1 if unfused else 0, int(tiling), int(item_points), int(persistent))
+                  1 if unfused else 0, int(tiling), int(item_points), int(persistent),
+                  SUM_ORDERS[sum_order])
 
 
 class Batch:

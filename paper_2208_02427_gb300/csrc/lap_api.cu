@@ -148,6 +148,10 @@ void check_device_ptr(lap_handle h, const void* p, const char* what, bool allow_
 void check_params(const lap_params* p)
 {
     if (!p) fail(LAP_EINVAL, "params is NULL");
+    if (p->sum_order != LAP_SUM_PAPER && p->sum_order != LAP_SUM_DIAGONAL)
+        fail(LAP_EINVAL, "sum_order must be LAP_SUM_PAPER or LAP_SUM_DIAGONAL");
+    if (p->sum_order == LAP_SUM_DIAGONAL && p->method != LAP_GS_RB && p->method != LAP_SOR_RB)
+        fail(LAP_EINVAL, "sum_order LAP_SUM_DIAGONAL is for LAP_GS_RB and LAP_SOR_RB");
     if (p->method < LAP_JACOBI || p->method > LAP_MG_FP32) fail(LAP_EINVAL, "unknown method");
     if (p->norm < LAP_NORM_L2_REL || p->norm > LAP_NORM_MAXDELTA) fail(LAP_EINVAL, "unknown norm");
     if (!(p->tol >= 0.0)) fail(LAP_EINVAL, "tol must be >= 0");
@@ -700,9 +704,14 @@ struct Solver {
         }
         case LAP_GS_RB:
         case LAP_SOR_RB:
-            for (int colour = 0; colour < 2; ++colour)
-                ck(launch_rb_colour(f, nullptr, c, gs, gs ? 1.0 : p->w, colour, md, s, w.wslot),
-                   "rb kernel");
+            for (int colour = 0; colour < 2; ++colour) {
+                if (p->sum_order == LAP_SUM_DIAGONAL)
+                    ck(launch_rb_diag(f, nullptr, gs, gs ? 1.0 : p->w, colour, md, s, w.wslot),
+                       "rb kernel (diagonal pairs)");
+                else
+                    ck(launch_rb_colour(f, nullptr, c, gs, gs ? 1.0 : p->w, colour, md, s, w.wslot),
+                       "rb kernel");
+            }
             break;
         case LAP_ADI:
             line_half_sweep(h, f, c, p->w, p->line_form, 0, s);
@@ -918,6 +927,7 @@ struct Solver {
     bool solve_cta_ok() const
     {
         if (p->norm != LAP_NORM_MAXDELTA) return false;
+        if (p->sum_order == LAP_SUM_DIAGONAL) return false;  // the one-CTA sweeps sum in paper order
         if (p->method == LAP_GS_LEX || p->method == LAP_SOR_LEX) return true;
         if (p->method == LAP_ADI || p->method == LAP_SLOR)
             return (int64_t)f.m * f.n <= 4096 && solve_lines_cta_smem(f.m, f.n) <= 200 * 1024;
@@ -981,7 +991,8 @@ struct Solver {
         const int64_t ints[] = {p->method, f.m, f.n, f.pitch, steps, maxdelta, fused_maxd,
                                 p->nu1, p->nu2, p->coarsest_min, p->max_levels, p->line_form,
                                 (int64_t)w.levels.size(), p->inner_cycles,
-                                (int64_t)w.levels32.size(), tail_first, fused32, norm_sc > 0.0};
+                                (int64_t)w.levels32.size(), tail_first, fused32, norm_sc > 0.0,
+                                p->sum_order};
         const double dbl[] = {c.b2, c.d, c.inv_d, p->w, p->smoother_w};
         const void* ptrs[] = {f.p, jac_cur, jac_other, w.aux, w.maxd, h->arena, h->lscratch};
         put(ints, sizeof ints);
@@ -1418,6 +1429,8 @@ void solve_device(lap_handle h, const lap_grid* g, double* psi_dev, const lap_pa
                   lap_result* out, cudaStream_t stream)
 {
     Solver sv{h, stream, Field{psi_dev, g->m, g->n, g->pitch}, make_coef(g->dx, g->dy), p, {}};
+    if (p->sum_order == LAP_SUM_DIAGONAL && !sv.c.unit_beta)
+        fail(LAP_EUNSUPPORTED, "sum_order LAP_SUM_DIAGONAL needs dx == dy (beta = 1)");
     if (p->method == LAP_MG || p->method == LAP_MG_MIXED || p->method == LAP_MG_FP32) {
         const int L = mg_level_count(g->m, g->n, p->coarsest_min, p->max_levels);
         int m = g->m, n = g->n;

@@ -61,6 +61,10 @@ void note_launch();
 cudaError_t launch_rb_colour(const Field& f, const double* q, const Coef& c, bool gs, double w,
                              int colour, unsigned long long* maxd, cudaStream_t s,
                              const double* wslot = nullptr);
+// The same colour pass with the neighbour sum paired along diagonals, (W + S) + (E + N), for
+// beta = 1 only (rb_diag_kernel): 4 FP64 operations per SOR update instead of 5.
+cudaError_t launch_rb_diag(const Field& f, const double* q, bool gs, double w, int colour,
+                           unsigned long long* maxd, cudaStream_t s, const double* wslot = nullptr);
 // One Jacobi sweep (Eq. 5) from in to out (same pitch; ring not touched).
 cudaError_t launch_jacobi(const Field& in, double* out, const Coef& c, unsigned long long* maxd,
                           cudaStream_t s);

@@ -66,6 +66,116 @@ __global__ void __launch_bounds__(RB_BX* RB_BY)
     if (MAXD) flush_maxd(dl, maxd);
 }
 
+// One colour of a red-black sweep with the neighbour sum paired along diagonals (beta = 1):
+// s = (W + S) + (E + N). A diagonal i - j = const holds points of one colour, and the pair
+// E + N of point (i, j) is the pair W + S of point (i + 1, j + 1): the same two values, and
+// a + b == b + a in IEEE arithmetic. A thread walks RD_K points down one diagonal and carries
+// the pair, so the neighbour sum costs two FP64 adds instead of three: 4 FP64 operations per SOR
+// update, 2 per Gauss-Seidel update (the multiply by 1/4 on the integer pipe). Every point gets
+// the value of the same expression whatever the launch shape (the pair is computed afresh as
+// W + S at the start of a walk). The rounding differs from the paper-order sum
+// (E + W) + (N + S) in the last bits.
+// Strip s of rows j0 = 1 + s RD_K .. j0 + RD_K - 1: walk x of the strip starts on row j0 at
+// column lo + 2x, lo the first column >= 2 - RD_K of the colour, and visits (lo + 2x + k,
+// j0 + k). Thread g of the launch takes walk g % starts of strip g / starts (no CTA is left
+// nearly empty at the end of a strip). Walks of 6 points in 128-thread CTAs: measured per
+// colour pass inside the solve's graphs at 4097^2, (walk, CTA) = (4, 128) 63.2 us, (6, 128)
+// 62.9, (8, 128) 64.7, (8, 256) 68.3, (16, 128) 66.0 with the loads one point ahead and
+// 73.4 for walks of 32 (a longer walk adds registers, a shorter one pair adds), against 71.0 us
+// for the paper-order kernel.
+constexpr int RD_BX = 128, RD_K = 6;
+
+template <bool HAS_Q, bool GS, bool MAXD>
+__global__ void __launch_bounds__(RD_BX)
+    rb_diag_kernel(double* __restrict__ psi, const double* __restrict__ q, int m, int n,
+                   int64_t pitch, int colour, int starts, double w, double one_minus_w,
+                   unsigned long long* __restrict__ maxd, const double* __restrict__ wslot)
+{
+    const FmaOps o = load_fma_ops();
+    if (!GS && wslot) {
+        w = wslot[0];
+        one_minus_w = wslot[1];
+    } else if (!GS) {
+        w = in_reg(o, w);
+        one_minus_w = in_reg(o, one_minus_w);
+    }
+    const int g = blockIdx.x * RD_BX + threadIdx.x;
+    const int strip = g / starts;
+    const int j0 = 1 + strip * RD_K;
+    const int lo0 = 2 - RD_K;
+    const int lo = lo0 + ((lo0 + j0 + colour) & 1);
+    const int is = lo + 2 * (g - strip * starts);
+    // the walk's points inside the interior: k0 .. k1
+    const int k0 = max(0, 1 - is);
+    const int k1 = min(RD_K - 1, min(m - 2 - is, n - 2 - j0));
+    unsigned long long dl = 0;
+    if (k0 == 0 && k1 == RD_K - 1) {
+        // a whole walk inside the interior: every operand of its RD_K points loaded before any
+        // point is written (none of them is written by this pass but the walk's own centres,
+        // each read before its own store), so the loads are in flight together
+        const int64_t step = pitch + 1;
+        const int64_t a0 = (int64_t)j0 * pitch + is;
+        double E[RD_K], N[RD_K], C[RD_K], Q[RD_K];
+        const double pSW0 = fadd(o, psi[a0 - 1], psi[a0 - pitch]);
+#pragma unroll
+        for (int k = 0; k < RD_K; ++k) {
+            const int64_t a = a0 + k * step;
+            E[k] = psi[a + 1];
+            N[k] = psi[a + pitch];
+            C[k] = psi[a];
+            Q[k] = HAS_Q ? q[a] : 0.0;
+        }
+        double pSW = pSW0;
+#pragma unroll
+        for (int k = 0; k < RD_K; ++k) {
+            const double pNE = fadd(o, E[k], N[k]);
+            double s = fadd(o, pSW, pNE);
+            if (HAS_Q) s = fadd(o, s, Q[k]);
+            const double g = times_inv_d<true>(o, s, 0.25, 2);
+            const double nv = GS ? g : __fma_rn(w, g, fmul(o, one_minus_w, C[k]));
+            psi[a0 + k * step] = nv;
+            if (MAXD) {
+                const unsigned long long v = abs_bits(fadd(o, nv, -C[k]));
+                dl = v > dl ? v : dl;
+            }
+            pSW = pNE;
+        }
+    } else if (k0 <= k1) {
+        const int64_t step = pitch + 1;
+        int64_t at = (int64_t)(j0 + k0) * pitch + (is + k0);
+        double pSW = fadd(o, psi[at - 1], psi[at - pitch]);
+        double E = psi[at + 1], N = psi[at + pitch], C = psi[at], Q = HAS_Q ? q[at] : 0.0;
+        for (int k = k0; k <= k1; ++k) {
+            // the next point's operands first: none of them is the point this step writes
+            double En = 0.0, Nn = 0.0, Cn = 0.0, Qn = 0.0;
+            if (k < k1) {
+                const int64_t nx = at + step;
+                En = psi[nx + 1];
+                Nn = psi[nx + pitch];
+                Cn = psi[nx];
+                if (HAS_Q) Qn = q[nx];
+            }
+            const double pNE = fadd(o, E, N);
+            double s = fadd(o, pSW, pNE);
+            if (HAS_Q) s = fadd(o, s, Q);
+            const double g = times_inv_d<true>(o, s, 0.25, 2);
+            const double nv = GS ? g : __fma_rn(w, g, fmul(o, one_minus_w, C));
+            psi[at] = nv;
+            if (MAXD) {
+                const unsigned long long v = abs_bits(fadd(o, nv, -C));
+                dl = v > dl ? v : dl;
+            }
+            pSW = pNE;
+            at += step;
+            E = En;
+            N = Nn;
+            C = Cn;
+            Q = Qn;
+        }
+    }
+    if (MAXD) flush_maxd(dl, maxd);
+}
+
 template <bool UNIT_BETA, bool POW2, bool MAXD>
 __global__ void __launch_bounds__(JA_BX* JA_BY)
     jacobi_kernel(const double* __restrict__ in, double* __restrict__ out, int m, int n,
@@ -235,6 +345,20 @@ cudaError_t launch_rb_colour(const Field& f, const double* q, const Coef& c, boo
             rb_colour_kernel<UB, P2, HQ, GS, MD><<<grid, block, 0, s>>>(
                 f.p, q, f.m, f.n, f.pitch, colour, c.b2, c.inv_d, c.inv_d_shift, w, omw, maxd,
                 wslot))))));
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rb_diag(const Field& f, const double* q, bool gs, double w, int colour,
+                           unsigned long long* maxd, cudaStream_t s, const double* wslot)
+{
+    const int starts = (f.m - 2 - (2 - RD_K)) / 2 + 1;  // walks per strip (the widest)
+    const int64_t walks = (int64_t)starts * ((f.n - 2 + RD_K - 1) / RD_K);
+    const int grid = (int)((walks + RD_BX - 1) / RD_BX);
+    const double omw = 1.0 - w;
+    LAP_DISPATCH_BOOL(q != nullptr, HQ, LAP_DISPATCH_BOOL(gs, GS, LAP_DISPATCH_BOOL(maxd != nullptr, MD,
+        rb_diag_kernel<HQ, GS, MD><<<grid, RD_BX, 0, s>>>(f.p, q, f.m, f.n, f.pitch, colour, starts,
+                                                           w, omw, maxd, wslot))));
     note_launch();
     return cudaGetLastError();
 }

@@ -2,7 +2,8 @@
 
     python -m paper_2208_02427_gb300.sweeps --method sor --m 4097 --n 4097 --iters 20
 
-Methods: jacobi, gs, sor (one red-black sweep = 2 launches), residual, adi-x, adi-y
+Methods: jacobi, gs, sor (one red-black sweep = 2 launches), sor_diag (one sweep with the
+neighbour sums paired along diagonals, inside a one-sweep solve), residual, adi-x, adi-y
 (zebra half sweeps), restrict, prolong, mg (one V(2,2) cycle), mg_mixed (one FP32
 V(2,2) cycle inside one FP64 defect-correction step), batched / batched_mixed (one cycle
 of --count uneven grids, 33..513 per side, through lap_solve_batched), step (one step of
@@ -33,6 +34,12 @@ def main():
                     help="V-cycle small-level tail size (0 = timed choice, -1 = none)")
     ap.add_argument("--unfused", action="store_true",
                     help="FP32 cycle: one kernel per pass instead of the tile kernels")
+    ap.add_argument("--tiling", type=int, default=0,
+                    help="batched mixed: FP32 tile variant 1..3, -1 = one kernel per pass, 0 = timed")
+    ap.add_argument("--item-points", type=int, default=0,
+                    help="batched: points per work item (0 = timed)")
+    ap.add_argument("--persistent", type=int, default=0,
+                    help="batched: 1 = persistent launches, -1 = one CTA per item, 0 = timed")
     ap.add_argument("--no-graphs", action="store_true",
                     help="direct launches (kernels inside conditional graphs cannot be profiled "
                          "one by one)")
@@ -52,6 +59,8 @@ def main():
         "jacobi": lambda: b.jacobi_sweep(u, other, h, h),
         "gs": lambda: b.smooth(u, w=1.0, nsweeps=1, dx=h, dy=h),
         "sor": lambda: b.smooth(u, w=w, nsweeps=1, dx=h, dy=h),
+        "sor_diag": lambda: lap.solve(u, h, h, method="sor", w=w, tol=0.0, max_iter=1,
+                                      sum_order="diagonal"),
         "residual": lambda: lap.residual(u, h, h),
         "adi-x": lambda: lap.line_sweep(u, 1.3, "A", 0, h, h),
         "adi-y": lambda: lap.line_sweep(u, 1.3, "A", 1, h, h),
@@ -80,7 +89,9 @@ def main():
         meth = "mg_mixed" if a.method == "batched_mixed" else "mg"
         ops[a.method] = lambda: lap.solve_batched(fields, 1.0, 1.0, method=meth, tol=0.0,
                                                   max_iter=1, tail_size=a.tail,
-                                                  unfused=a.unfused)
+                                                  unfused=a.unfused, tiling=a.tiling,
+                                                  item_points=a.item_points,
+                                                  persistent=a.persistent)
     fn = ops[a.method]
     for _ in range(a.warmup):
         fn()

@@ -578,3 +578,74 @@ def test_one_cta_solve_matches_oracle(lap, b, method, w, every, max_iter, tol, s
     assert np.array_equal(host(t), want)
     if g["iters"]:
         assert g["last_check"] == o["hist"][-1]
+
+
+# ---- the diagonal summation order: (W + S) + (E + N), beta = 1 ----------------------
+
+DIAG_SHAPES = [(3, 3), (4, 5), (25, 17), (67, 45), (130, 97), (257, 33), (40, 300), (600, 21)]
+
+
+@pytest.mark.parametrize("shape", DIAG_SHAPES)
+@pytest.mark.parametrize("method,w", [("gs", 1.0), ("sor", 1.0), ("sor", 1.8)])
+@pytest.mark.parametrize("norm", ["l2_rel", "maxdelta"])
+def test_diagonal_order_fixed_iterations_bitwise(lap, b, shape, method, w, norm):
+    """The diagonal-pair kernel (threads walking 16-point diagonal runs) against the oracle's
+    sweeps in the same summation order: the same bits for every launch shape and tail."""
+    m, n = shape
+    psi = rand_field(m, n, 31 + m)
+    t = b.to_field(psi)
+    g = lap.solve(t, 1.0, 1.0, method=method, w=w, tol=0.0, max_iter=7, check_every=3, norm=norm,
+                  sum_order="diagonal")
+    want, o = ora.solve(psi, tol=0.0, max_iter=7, check_every=3, norm=NORMS[norm],
+                        sum_order=ora.SUM_DIAGONAL, **ora_kw(method, w=w))
+    # (a 3 x 3 grid is solved exactly by one Gauss-Seidel sweep: both stop at the first test)
+    assert g["status"] == o["status"]
+    assert g["iters"] == o["iters"] == (3 if shape == (3, 3) and w == 1.0 else 7)
+    assert np.array_equal(host(t), want)
+
+
+@pytest.mark.parametrize("method,w", [("gs", 1.0), ("sor", 1.75), ("sor", 1.9)])
+@pytest.mark.parametrize("norm,tol", [("l2_rel", 1e-10), ("maxdelta", 1e-9)])
+def test_diagonal_order_chamber_solves_match_oracle(lap, b, method, w, norm, tol):
+    psi = wl.chamber()
+    t = b.to_field(psi)
+    g = lap.solve(t, 0.25, 0.25, method=method, w=w, norm=norm, tol=tol, sum_order="diagonal")
+    want, o = ora.solve(psi, dx=0.25, dy=0.25, tol=tol, norm=NORMS[norm],
+                        sum_order=ora.SUM_DIAGONAL, **ora_kw(method, w=w))
+    assert g["status"] == o["status"] == "converged"
+    assert g["iters"] == o["iters"]
+    assert np.array_equal(host(t), want)
+
+
+def test_diagonal_order_full_size_sweeps_bitwise(lap, b, big):
+    w = wl.w_opt_sor(4097, 4097)
+    t = b.to_field(big)
+    lap.solve(t, 1 / 4096, 1 / 4096, method="sor", w=w, tol=0.0, max_iter=3, check_every=3,
+              sum_order="diagonal")
+    want, _ = ora.solve(big, dx=1 / 4096, dy=1 / 4096, tol=0.0, max_iter=3, check_every=3,
+                        sum_order=ora.SUM_DIAGONAL, **ora_kw("sor", w=w))
+    assert np.array_equal(host(t), want)
+
+
+def test_diagonal_order_stays_within_rounding_of_the_paper_order(lap, b):
+    """Many sweeps in either order: the iterates part only by accumulated rounding."""
+    m, n = 513, 385
+    psi = wl.sine_edges(m, n, seed=wl.SEED_BASE + 5)
+    w = wl.w_opt_sor(m, n)
+    a, c = b.to_field(psi), b.to_field(psi)
+    ga = lap.solve(a, 1.0, 1.0, method="sor", w=w, tol=1e-10, check_every=25, sum_order="diagonal")
+    gc = lap.solve(c, 1.0, 1.0, method="sor", w=w, tol=1e-10, check_every=25)
+    assert ga["status"] == gc["status"] == "converged"
+    assert ga["iters"] == gc["iters"]
+    assert 0.0 < relerr(host(a), host(c)) <= REL
+
+
+def test_diagonal_order_refuses_other_methods_and_beta(lap, b):
+    good = b.to_field(rand_field(33, 33, 3))
+    with pytest.raises(b.LapError) as e:
+        lap.solve(good, 1.0, 0.5, method="sor", w=1.5, max_iter=2, sum_order="diagonal")
+    assert "EUNSUPPORTED" in str(e.value)
+    for method in ("jacobi", "mg", "adi", "mg_mixed"):
+        with pytest.raises(b.LapError) as e:
+            lap.solve(good, 1.0, 1.0, method=method, max_iter=2, sum_order="diagonal")
+        assert "EINVAL" in str(e.value)

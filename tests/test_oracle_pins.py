@@ -413,3 +413,81 @@ def test_threaded_timing_sweeps_equal_the_oracle(shape, beta, threads):
         want = ora.sor_sweep(want, 1.7, beta, ora.RB)
     got = ora.mt_sor_rb_sweeps(psi, 1.7, 5, beta, threads)
     assert np.array_equal(got, want)
+
+
+# ---- the diagonal summation order (W + S) + (E + N), beta = 1 ---------------------
+
+def integer_field(m, n, seed):
+    """Values that are small integers: every partial sum of four of them is exact, so any
+    order of the neighbour sum gives the same bits, and a wrong neighbour gives another value."""
+    rng = np.random.default_rng(seed)
+    return rng.integers(-1000, 1001, size=(n, m)).astype(np.float64)
+
+
+@pytest.mark.parametrize("shape", [(3, 3), (7, 5), (16, 9), (33, 20)])
+@pytest.mark.parametrize("w", [1.0, 0.75, 1.5])
+def test_diagonal_order_equals_paper_order_on_exact_sums(shape, w):
+    m, n = shape
+    psi = integer_field(m, n, 40 + m)
+    q = integer_field(m, n, 41 + m)
+    for qq in (None, q):
+        if w == 1.0:
+            a = ora.gs_sweep(psi, 1.0, ora.RB, qq, sum_order=ora.SUM_DIAGONAL)
+            ref = ora.gs_sweep(psi, 1.0, ora.RB, qq)
+        else:
+            a = ora.sor_sweep(psi, w, 1.0, ora.RB, qq, sum_order=ora.SUM_DIAGONAL)
+            ref = ora.sor_sweep(psi, w, 1.0, ora.RB, qq)
+        assert np.array_equal(a, ref)
+        # and both are Eq. 6 / 7 written out for the red-black order (exact sums)
+        want = psi.copy()
+        for colour in (0, 1):
+            for j in range(1, n - 1):
+                for i in range(1, m - 1):
+                    if (i + j) % 2 != colour:
+                        continue
+                    s = want[j, i - 1] + want[j, i + 1] + want[j - 1, i] + want[j + 1, i]
+                    if qq is not None:
+                        s += qq[j, i]
+                    want[j, i] = (1 - w) * want[j, i] + w * 0.25 * s if w != 1.0 else 0.25 * s
+        assert np.allclose(a, want, rtol=0, atol=1e-9 * np.max(np.abs(want)))
+
+
+def test_diagonal_order_differs_from_paper_order_only_in_rounding():
+    m, n = 40, 31
+    psi = wl.random_interior(wl.random_ring(m, n, seed=3), seed=4)
+    a = ora.sor_sweep(psi, 1.7, 1.0, ora.RB, sum_order=ora.SUM_DIAGONAL)
+    ref = ora.sor_sweep(psi, 1.7, 1.0, ora.RB)
+    diff = np.max(np.abs(a - ref))
+    assert 0.0 < diff <= 8 * np.finfo(float).eps * np.max(np.abs(ref))
+
+
+def test_diagonal_order_converges_to_dense_solution_and_keeps_harmonics():
+    for m, n in [(9, 9), (7, 5)]:
+        psi = wl.random_ring(m, n, seed=200 + m)
+        ref = exact.dense_solve(psi, 1.0)
+        for method, w in ((ora.GS, 1.0), (ora.SOR, 1.4)):
+            sol, info = ora.solve(psi, method=method, ordering=ora.RB, w=w, tol=1e-14,
+                                  max_iter=20000, sum_order=ora.SUM_DIAGONAL)
+            assert info["status"] == "converged"
+            assert np.max(np.abs(sol - ref)) <= 1e-11
+    # x^2 - y^2 on unit spacing is discrete-harmonic with exact sums: a fixed point
+    m, n = 12, 9
+    x, y = np.meshgrid(np.arange(m, dtype=float), np.arange(n, dtype=float))
+    h = x ** 2 - y ** 2
+    start = h.copy()
+    start[1:-1, 1:-1] = 0.0
+    sol, info = ora.solve(start, method=ora.SOR, ordering=ora.RB, w=1.5, tol=1e-15,
+                          max_iter=20000, sum_order=ora.SUM_DIAGONAL)
+    assert np.max(np.abs(sol - h)) <= 1e-9
+    again = ora.sor_sweep(h, 1.5, 1.0, ora.RB, sum_order=ora.SUM_DIAGONAL)
+    assert np.array_equal(again, h)
+
+
+def test_diagonal_order_needs_unit_beta_and_a_point_method():
+    psi = wl.random_ring(9, 9, seed=5)
+    with pytest.raises(ValueError):
+        ora.sor_sweep(psi, 1.5, 0.8, ora.RB, sum_order=ora.SUM_DIAGONAL)
+    with pytest.raises(ValueError):
+        ora.solve(psi, method=ora.MG, sum_order=ora.SUM_DIAGONAL)
+    with pytest.raises(ValueError):
+        ora.solve(psi, method=ora.SOR, w=1.5, dx=0.5, dy=1.0, sum_order=ora.SUM_DIAGONAL)
