@@ -188,6 +188,40 @@ def oracle_sample(psi, sor_sweeps: int, sor_total: int, threads: int = 0):
             "seconds_per_solve_pair": solve_s, "mg_cycles": info["iters"]}, sol
 
 
+def _oracle_batched_problem(job):
+    """One problem of the batched workload solved by the oracle's V(2,2) multigrid to 1e-10
+    (run in a spawned worker process); returns its wall time and cycle count."""
+    m, n, seed = job
+    import oracle as ora
+    from paper_2208_02427_gb300 import workloads as wl
+    psi = wl.random_ring(m, n, seed=seed)
+    t0 = time.perf_counter()
+    _, info = ora.solve(psi, method=ora.MG, ordering=ora.RB, dx=1.0, dy=1.0, tol=TOL, max_iter=100)
+    return time.perf_counter() - t0, info["iters"]
+
+
+def oracle_batched_sample(count=4096, every=16):
+    """The batched workload's oracle baseline: every `every`-th problem of the 4096 solved by
+    the oracle, one problem per worker process over all host cores (spawned: the parent holds
+    a CUDA context). solves/s = problems / wall time of the pool."""
+    import multiprocessing as mp
+
+    from paper_2208_02427_gb300 import workloads as wl
+    shapes = wl.batch_shapes(count, seed=wl.SEED_BASE + 2)
+    jobs = [(m, n, wl.SEED_BASE + 2 + 10 * k) for k, (m, n) in enumerate(shapes)][::every]
+    cores = os.cpu_count() or 1
+    with mp.get_context("spawn").Pool(cores) as pool:
+        pool.map(_oracle_batched_problem, jobs[:cores])  # workers import and build once
+        t0 = time.perf_counter()
+        res = pool.map(_oracle_batched_problem, jobs)
+        wall = time.perf_counter() - t0
+    return {"value": len(jobs) / wall, "unit": "solves/s", "cores": cores, "kind": "oracle",
+            "sample": f"{len(jobs)} of the {count} problems (every {every}th), V(2,2) to 1e-10, "
+                      f"one problem per process over {cores} host processes; "
+                      f"{sum(t for t, _ in res):.2f} s of single-core oracle time in {wall:.2f} s",
+            "max_cycles": max(c for _, c in res)}
+
+
 # Sweeps of this input to 1e-10 (RB-SOR tested every 100 sweeps; in either summation order the
 # oracle's RB-SOR iterates are bitwise identical to the GPU's in that order, and both orders stop
 # at the same test, so the oracle needs the same count).
@@ -768,6 +802,7 @@ def main():
                 bo[name].append(rel(kept["batch_256x1025"][name][k], ref))
         mixed["batch_256x1025"]["oracle"] = {name: max(v) for name, v in bo.items()}
         mixed["batch_256x1025"]["oracle"]["sample"] = f"problems {list(ORACLE_BATCH_SAMPLE)}"
+        batched["cpu_baseline"] = oracle_batched_sample()
         for key in ("grid_4097", "grid_8193", "batch_256x1025"):
             o = mixed[key]["oracle"]
             o["mixed_within_1e-10"] = o["mixed"] <= 1e-10

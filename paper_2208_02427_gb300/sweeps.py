@@ -71,13 +71,15 @@ def main():
                                       tail_size=a.tail, unfused=a.unfused),
     }
     if a.method == "step":
-        # one step of the benchmark: RB-SOR at w_opt (tested every 100 sweeps) and the V(2,2)
-        # multigrid, each to ||r|| <= 1e-10 ||r0|| from the same initial field
+        # one step of the benchmark: RB-SOR at w_opt (tested every 100 sweeps, neighbour sums
+        # paired along diagonals) and the V(2,2) multigrid, each to ||r|| <= 1e-10 ||r0|| from the
+        # same initial field
         init = u.clone()
 
         def step():
             u.copy_(init)
-            lap.solve(u, h, h, method="sor", w=w, tol=1e-10, check_every=100, max_iter=200000)
+            lap.solve(u, h, h, method="sor", w=w, tol=1e-10, check_every=100, max_iter=200000,
+                      sum_order="diagonal")
             u.copy_(init)
             lap.solve(u, h, h, method="mg", tol=1e-10, nu1=2, nu2=2, coarsest_min=5, max_iter=100)
 
