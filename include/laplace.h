@@ -194,8 +194,11 @@ int lap_solve_host(lap_handle h, const lap_grid* g, double* psi_host, int64_t ho
  * Every phase of a cycle is one launch over all problems that take part in it; each
  * problem gets exactly the arithmetic of its own lap_solve (per problem the iterates are
  * the same), stops on its own (convergence is decided on the device) and reports in
- * results[k] (host). p->check_every sets how often (in cycles) the host polls for the
- * number of problems still running. Synchronises `stream` before returning.
+ * results[k] (host). While the launch configuration is still being chosen (below), the
+ * host polls the number of problems still running every p->check_every cycles; once it is
+ * chosen (and graphs are on), the remaining cycles run on the device as one conditional CUDA
+ * graph that stops itself when no problem is left or p->max_iter cycles are done, and the host
+ * waits once. Synchronises `stream` before returning.
  * The launch configuration -- the small-level tail size (p->tail_size), the FP32 levels'
  * temporal blocking and tile shape (p->tiling), the per-pass kernels' work-item size
  * (p->item_points) and persistent or one-CTA-per-item launches (p->persistent) -- is chosen

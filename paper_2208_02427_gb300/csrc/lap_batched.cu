@@ -129,6 +129,9 @@ struct CandPlan {
     size_t bytes = 0;
     cudaGraphExec_t exec = nullptr;
     int64_t kernels = 0;  // kernels one replay of exec launches
+    // the device-resident loop: cycle after cycle as the body of a conditional (while) node
+    cudaGraphExec_t loop_exec = nullptr;
+    int64_t loop_kernels = 0;  // kernels one iteration of the loop launches
 };
 
 // What a call's plan depends on: the grids (sizes, spacings, pitches), the fields' addresses
@@ -170,11 +173,13 @@ struct BatchCache : BatchCacheBase {
     long long* iters = nullptr;
     double *r0 = nullptr, *rnow = nullptr, *partials = nullptr;
     unsigned* claim = nullptr;  // item counter of the persistent launches (two words, zero between launches)
+    long long* loop = nullptr;  // device-resident loop: cycles done, cycle cap
     std::vector<CandPlan> cands;  // indexed like the tuner's candidates
     ~BatchCache() override
     {
         for (CandPlan& c : cands) {
             if (c.exec) cudaGraphExecDestroy(c.exec);
+            if (c.loop_exec) cudaGraphExecDestroy(c.loop_exec);
             dev_free(h, c.dev, c.bytes);
         }
     }
@@ -317,6 +322,7 @@ std::unique_ptr<BatchCache> build_plan(lap_handle h, int count, const lap_grid* 
         C->rnow = cv.template take<double>(count);
         C->partials = cv.template take<double>(std::max<size_t>(1, P.norm_items.size()));
         C->claim = cv.template take<unsigned>(2);
+        C->loop = cv.template take<long long>(2);
     };
     Sizer sz;
     carve_all(sz);
@@ -498,6 +504,66 @@ extern "C" int lap_solve_batched(lap_handle h, int count, const lap_grid* grids,
                 ck(cudaGraphLaunch(K.exec, s), "launch graph");
                 add_launches(K.kernels);
             };
+            // once the configuration is chosen: the remaining cycles on the device, each followed
+            // by the loop test, as one conditional graph replayed on the caller's stream until no
+            // problem is left or max_iter cycles are done; the host waits once
+            auto device_loop = [&](int c, int64_t done) {
+                CandPlan& K = ensure_candidate(*C, c, tuner.cand[c], p, count);
+                h->last_batch = tuner.cand[c];
+                h->last_batch_tuned = true;
+                if (!K.loop_exec) {
+                    if (!h->capture)
+                        ck(cudaStreamCreateWithFlags(&h->capture, cudaStreamNonBlocking), "capture stream");
+                    cudaGraph_t g = nullptr;
+                    ck(cudaGraphCreate(&g, 0), "create graph");
+                    try {
+                        cudaGraphConditionalHandle hnd;
+                        ck(cudaGraphConditionalHandleCreate(&hnd, g, 1, cudaGraphCondAssignDefault),
+                           "conditional handle");
+                        alignas(cudaGraphNodeParams) unsigned char raw[sizeof(cudaGraphNodeParams)] = {};
+                        cudaGraphNodeParams* np = reinterpret_cast<cudaGraphNodeParams*>(raw);
+                        np->type = cudaGraphNodeTypeConditional;
+                        np->conditional.handle = hnd;
+                        np->conditional.type = cudaGraphCondTypeWhile;
+                        np->conditional.size = 1;
+                        cudaGraphNode_t node;
+                        ck(cudaGraphAddNode(&node, g, nullptr, nullptr, 0, np), "conditional node");
+                        cudaGraph_t body = np->conditional.phGraph_out[0];
+                        const int64_t before = launches_now();
+                        ck(cudaStreamBeginCaptureToGraph(h->capture, body, nullptr, nullptr, 0,
+                                                         cudaStreamCaptureModeThreadLocal),
+                           "begin capture");
+                        try {
+                            cycle(K, h->capture);
+                            ck(launch_batch_loop_decide(C->loop, remaining, hnd, h->capture),
+                               "batched loop test");
+                        } catch (...) {
+                            cudaGraph_t junk = nullptr;
+                            cudaStreamEndCapture(h->capture, &junk);
+                            cudaGetLastError();
+                            throw;
+                        }
+                        cudaGraph_t body_out = nullptr;
+                        ck(cudaStreamEndCapture(h->capture, &body_out), "end capture");
+                        K.loop_kernels = launches_now() - before;
+                        add_launches(-K.loop_kernels);
+                        ck(cudaGraphInstantiate(&K.loop_exec, g, 0), "instantiate graph");
+                    } catch (...) {
+                        cudaGraphDestroy(g);
+                        throw;
+                    }
+                    cudaGraphDestroy(g);
+                }
+                long long st[2] = {(long long)done, (long long)p->max_iter};
+                std::memcpy(h->pinned, st, sizeof st);
+                ck(cudaMemcpyAsync(C->loop, h->pinned, sizeof st, cudaMemcpyHostToDevice, s), "upload loop state");
+                ck(cudaGraphLaunch(K.loop_exec, s), "launch graph");
+                ck(cudaMemcpyAsync(h->pinned, C->loop, sizeof st, cudaMemcpyDeviceToHost, s), "copy loop state");
+                ck(cudaStreamSynchronize(s), "stream sync");
+                std::memcpy(st, h->pinned, sizeof st);
+                add_launches(K.loop_kernels * (st[0] - (long long)done));
+                return (int64_t)st[0];
+            };
             int64_t done = 0;
             int left = count;
             while (done < p->max_iter) {
@@ -505,6 +571,10 @@ extern "C" int lap_solve_batched(lap_handle h, int count, const lap_grid* grids,
                 ck(cudaStreamSynchronize(s), "stream sync");
                 std::memcpy(&left, h->pinned, sizeof(int));
                 if (left == 0) break;
+                if (tuner.done && h->use_graphs) {
+                    done = device_loop(tuner.best, done);
+                    continue;
+                }
                 const int64_t steps = std::min<int64_t>(p->check_every, p->max_iter - done);
                 for (int64_t k = 0; k < steps; ++k) {
                     const int c = tuner.next();

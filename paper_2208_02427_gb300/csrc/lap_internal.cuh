@@ -114,6 +114,10 @@ struct LoopState {
 // cudaGraphSetConditional(h, keep going).
 cudaError_t launch_loop_decide(LoopState* st, const double* nrm, const unsigned long long* maxd,
                                const float* scale, cudaGraphConditionalHandle h, cudaStream_t s);
+// Batched solves: st[0] += 1 (cycles done), then the loop's condition := some problem still
+// running (*remaining > 0) and st[0] < st[1] (the cycle cap).
+cudaError_t launch_batch_loop_decide(long long* st, const int* remaining, cudaGraphConditionalHandle h,
+                                     cudaStream_t s);
 // maxd := max |a - b| over interior nodes (bit pattern), a and b share f's shape/pitch.
 cudaError_t launch_maxdelta(const Field& a, const double* b, unsigned long long* maxd,
                             cudaStream_t s);

@@ -42,6 +42,19 @@ __global__ void loop_decide_kernel(LoopState* st, const double* __restrict__ nrm
     cudaGraphSetConditional(h, status == 1 && st->k + st->steps <= st->max_iter ? 1u : 0u);
 }
 
+// The loop test of a device-resident batched solve, run after each cycle inside the body of
+// a conditional CUDA graph: st[0] counts the cycles, st[1] is the cap; the loop goes on while
+// some problem is still running (the convergence kernel counts them down) and the cap is not
+// reached.
+__global__ void batch_loop_decide_kernel(long long* st, const int* __restrict__ remaining,
+                                         cudaGraphConditionalHandle h)
+{
+    if (threadIdx.x != 0) return;
+    const long long k = st[0] + 1;
+    st[0] = k;
+    cudaGraphSetConditional(h, *remaining > 0 && k < st[1] ? 1u : 0u);
+}
+
 }  // namespace
 
 namespace {
@@ -134,6 +147,14 @@ cudaError_t launch_check_rounding(long long count, unsigned long long seed, unsi
                                   cudaStream_t s)
 {
     check_rounding_kernel<<<152 * 8, 256, 0, s>>>(count, seed, bad);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_loop_decide(long long* st, const int* remaining, cudaGraphConditionalHandle h,
+                                     cudaStream_t s)
+{
+    batch_loop_decide_kernel<<<1, 32, 0, s>>>(st, remaining, h);
     note_launch();
     return cudaGetLastError();
 }

@@ -154,3 +154,29 @@ def test_batched_launch_configurations_are_bitwise_equal(b, method):
     with pytest.raises(b.LapError):
         run(persistent=2)
     lap.close()
+
+
+@pytest.mark.parametrize("method", ["mg", "mg_mixed"])
+def test_batched_device_loop_equals_host_polled_cycles(b, method):
+    """With the configuration fixed, a batched solve runs its cycles as one conditional graph
+    that stops itself (no problem left, or the cycle cap); with graphs off the host polls the
+    count after every cycle. Both give the same iterates, statuses, cycle counts and norms."""
+    shapes = [(33, 65), (129, 129), (257, 65), (65, 33), (9, 9), (3, 3)]
+    inputs = [wl.random_ring(m, n, seed=900 + k) for k, (m, n) in enumerate(shapes)]
+    lap = b.Laplace()
+    fixed = dict(tail_size=-1, tiling=-1 if method == "mg" else 1, item_points=8192, persistent=-1)
+
+    def run(graphs, **kw):
+        lap.set_graphs(graphs)
+        fields = [b.to_field(x) for x in inputs]
+        res = lap.solve_batched(fields, 1.0, 1.0, method=method, **fixed, **kw)
+        return [host(f) for f in fields], [(r["status"], r["iters"], r["r_final"]) for r in res]
+
+    for kw in (dict(tol=1e-10, max_iter=100), dict(tol=0.0, max_iter=4), dict(tol=1e-10, max_iter=3),
+               dict(tol=1e-10, max_iter=100, check_every=5)):
+        on, off = run(True, **kw), run(False, **kw)
+        assert on[1] == off[1], kw
+        assert all(np.array_equal(x, y) for x, y in zip(on[0], off[0])), kw
+        if kw["tol"] == 0.0 or kw["max_iter"] == 3:
+            assert all(it == kw["max_iter"] for _, it, _ in on[1] if it > 0), on[1]
+    lap.close()
