@@ -177,6 +177,8 @@ def test_batched_device_loop_equals_host_polled_cycles(b, method):
         on, off = run(True, **kw), run(False, **kw)
         assert on[1] == off[1], kw
         assert all(np.array_equal(x, y) for x, y in zip(on[0], off[0])), kw
-        if kw["tol"] == 0.0 or kw["max_iter"] == 3:
-            assert all(it == kw["max_iter"] for _, it, _ in on[1] if it > 0), on[1]
+        # the cycle cap holds, and binds where the tolerance is not reached first
+        assert max(it for _, it, _ in on[1]) == min(kw["max_iter"], max(it for _, it, _ in off[1]))
+        if kw["max_iter"] <= 4:
+            assert max(it for _, it, _ in on[1]) == kw["max_iter"]
     lap.close()
