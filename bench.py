@@ -222,6 +222,48 @@ def oracle_batched_sample(count=4096, every=16):
             "max_cycles": max(c for _, c in res)}
 
 
+def oracle_serving_estimate(work, gpu_solves_per_s):
+    """The serving workload's oracle baseline, extrapolated: for each request size of the
+    saturation run, one oracle RB-SOR sweep and one V(2,2) cycle (with its residual norm) are
+    timed once on one host core; a request costs its unit times the iterations the GPU ran for it
+    (the oracle's red-black and multigrid iterates follow the same counts), plus one residual norm
+    per 50 SOR sweeps (the server's test period). Mixed-precision requests are charged as the
+    oracle's FP64 multigrid."""
+    import numpy as np
+
+    import oracle as ora
+    from paper_2208_02427_gb300 import workloads as wl
+    units = {}
+    for m, n in sorted({(m, n) for m, n, _, _ in work}):
+        psi = wl.random_interior(wl.random_ring(m, n, seed=7), seed=8)
+        t0 = time.perf_counter()
+        reps = max(1, int(2e6 // (m * n)))
+        for _ in range(reps):
+            ora.sor_sweep(psi, 1.9, 1.0, ora.RB)
+        sweep = (time.perf_counter() - t0) / reps
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            ora.defect_norm(psi, 1.0)
+        norm = (time.perf_counter() - t0) / reps
+        t0 = time.perf_counter()
+        ora.solve(psi, method=ora.MG, ordering=ora.RB, tol=0.0, max_iter=1)
+        cycle = time.perf_counter() - t0
+        units[(m, n)] = (sweep + norm / 50.0, cycle + norm)
+    seconds = sum(units[(m, n)][0 if method == "sor" else 1] * max(1, it)
+                  for m, n, method, it in work)
+    cores = os.cpu_count() or 1
+    value = len(work) / seconds if seconds > 0 else None
+    return {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle",
+            "sample": f"extrapolated: the {len(work)} requests of the saturation run, each charged "
+                      f"its size's oracle RB-SOR sweep (+ a norm per 50 sweeps) or V(2,2) cycle "
+                      f"(+ norm), timed once per size on one host core, times the GPU's iteration "
+                      f"count; {len(units)} sizes, {seconds:.1f} s of oracle time",
+            "all_cores_ideal": {"value": value * cores if value else None, "cores": cores,
+                                "how": "the single-core estimate with requests spread evenly over "
+                                       "all host cores (not run)"},
+            "gpu_over_oracle_single_core": gpu_solves_per_s / value if value else None}
+
+
 # Sweeps of this input to 1e-10 (RB-SOR tested every 100 sweeps; in either summation order the
 # oracle's RB-SOR iterates are bitwise identical to the GPU's in that order, and both orders stop
 # at the same test, so the oracle needs the same count).
@@ -698,6 +740,7 @@ def main():
             torch.cuda.synchronize(dev)
             t0 = time.perf_counter()
             ids, lat, nxt, steps = {}, {"mg_mixed": [], "sor": []}, 0, 0
+            work_done = []  # (m, n, method, iterations) per finished request
             finished = 0
             while finished < len(reqs):
                 now = time.perf_counter() - t0
@@ -705,7 +748,7 @@ def main():
                     m, n, tol, method, _ = reqs[nxt]
                     w = wl.w_opt_sor(m, n) if method == "sor" else 1.0
                     rid = srv.submit(fields[nxt], 1.0, 1.0, method=method, w=w, tol=tol, max_iter=10 ** 6)
-                    ids[rid] = (arrivals[nxt], method)
+                    ids[rid] = (arrivals[nxt], method, m, n)
                     nxt += 1
                 if not ids:
                     time.sleep(max(0.0, min(arrivals[nxt] - now, 0.01)))
@@ -717,8 +760,9 @@ def main():
                 for rid, res in srv.drain():
                     if res["status"] != "converged":
                         raise RuntimeError(f"served request did not converge: {res}")
-                    arrived, method = ids.pop(rid)
+                    arrived, method, m, n = ids.pop(rid)
                     lat[method].append(done - arrived)
+                    work_done.append((m, n, method, res["iters"]))
                     finished += 1
             total = time.perf_counter() - t0
             srv.close()
@@ -727,9 +771,11 @@ def main():
             return {"requests": len(reqs), "seconds": total, "solves_per_s": len(reqs) / total,
                     "steps": steps, "p50_ms": pct(both, 0.5), "p99_ms": pct(both, 0.99),
                     "by_class": {k: {"requests": len(v), "p50_ms": pct(v, 0.5), "p99_ms": pct(v, 0.99)}
-                                 for k, v in lat.items()}}
+                                 for k, v in lat.items()},
+                    "_work": work_done}
 
         sat = run(draw(burst), 0.0)
+        serving_work.extend(sat["_work"])
         loads = (0.1, 0.3, 0.5, 0.7, 0.9, 1.2)
         # equal arrival windows per load level, sized so that the levels together serve about
         # total_requests requests
@@ -743,9 +789,12 @@ def main():
             rate = load * sat["solves_per_s"]
             count = max(20, int(rate * window))
             out["loads"][f"{load:.1f}"] = run(draw(count), rate)
+        for v in [out["saturation"], *out["loads"].values()]:
+            v.pop("_work", None)
         out["requests_total"] = sat["requests"] + sum(v["requests"] for v in out["loads"].values())
         return out
 
+    serving_work = []  # the saturation run's requests: (m, n, method, iterations)
     serving = serving_workload()
 
     # ---- end to end through the public API with host buffers -----------------------------
@@ -803,6 +852,7 @@ def main():
         mixed["batch_256x1025"]["oracle"] = {name: max(v) for name, v in bo.items()}
         mixed["batch_256x1025"]["oracle"]["sample"] = f"problems {list(ORACLE_BATCH_SAMPLE)}"
         batched["cpu_baseline"] = oracle_batched_sample()
+        serving["cpu_baseline"] = oracle_serving_estimate(serving_work, serving["saturation"]["solves_per_s"])
         for key in ("grid_4097", "grid_8193", "batch_256x1025"):
             o = mixed[key]["oracle"]
             o["mixed_within_1e-10"] = o["mixed"] <= 1e-10
