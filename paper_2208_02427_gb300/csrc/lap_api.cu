@@ -203,9 +203,10 @@ std::vector<double> host_thomas(int len, double alpha, double delta, const std::
     return x;
 }
 
-const LineTables& line_tables(lap_handle h, int N, double alpha, double delta, double wc)
+const LineTables& line_tables(lap_handle h, int N, double alpha, double delta, double wc,
+                              int max_chunks)
 {
-    auto key = std::make_tuple(N, alpha, delta, wc);
+    auto key = std::make_tuple(N, alpha, delta, wc, max_chunks);
     auto it = h->lines.find(key);
     if (it != h->lines.end()) return it->second.t;
     if (N > LINE_MAX_N) fail(LAP_EUNSUPPORTED, "line longer than 16383 unknowns");
@@ -214,20 +215,21 @@ const LineTables& line_tables(lap_handle h, int N, double alpha, double delta, d
     t.alpha = alpha;
     t.delta = delta;
     t.wc = wc;
-    // P <= 32 chunks of L unknowns, each but the last followed by one separator unknown; the
-    // last chunk holds the remaining 1..L unknowns (the line never ends on a separator)
+    t.maxp = max_chunks;
+    // P <= max_chunks chunks of L unknowns, each but the last followed by one separator unknown;
+    // the last chunk holds the remaining 1..L unknowns (the line never ends on a separator)
     if (N <= LINE_MIN_CHUNK) {
         t.L = t.Ll = N;
         t.P = 1;
     } else {
-        t.L = std::max(LINE_MIN_CHUNK, (N - (LINE_MAX_CHUNKS - 1) + LINE_MAX_CHUNKS - 1) / LINE_MAX_CHUNKS);
+        t.L = std::max(LINE_MIN_CHUNK, (N - (max_chunks - 1) + max_chunks - 1) / max_chunks);
         for (;; ++t.L) {
             t.P = (N + 1 + t.L) / (t.L + 1);  // ceil((N + 1) / (L + 1))
             t.Ll = N - (t.P - 1) * (t.L + 1);
             if (t.Ll >= 1) break;
         }
     }
-    if (t.Ll > t.L || t.P > LINE_MAX_CHUNKS) fail(LAP_ECUDA, "internal: bad line partition");
+    if (t.Ll > t.L || t.P > max_chunks) fail(LAP_ECUDA, "internal: bad line partition");
     t.stride = (t.L + 1) | 1;
     const int L = t.L, S = t.P - 1;
     t.levels = 0;
@@ -278,8 +280,9 @@ const LineTables& line_tables(lap_handle h, int N, double alpha, double delta, d
         b[p] = delta - alpha * gR[L - 1] - alpha * (right_last ? gLl[0] : gL[0]);
         c[p] = p + 1 <= S - 1 ? -alpha * gR[0] : 0.0;
     }
-    // parallel cyclic reduction, one lane per separator: tables indexed [level * 32 + lane]
-    std::vector<double> k1((size_t)std::max(1, t.levels) * 32, 0.0), k2(k1.size(), 0.0), invb(32, 0.0);
+    // parallel cyclic reduction, one lane per separator: tables indexed [level * maxp + lane]
+    const size_t mp = (size_t)max_chunks;
+    std::vector<double> k1((size_t)std::max(1, t.levels) * mp, 0.0), k2(k1.size(), 0.0), invb(mp, 0.0);
     for (int lev = 0, s = 1; lev < t.levels; ++lev, s <<= 1) {
         std::vector<double> na(S), nb(S), nc(S);
         for (int p = 0; p < S; ++p) {
@@ -288,8 +291,8 @@ const LineTables& line_tables(lap_handle h, int N, double alpha, double delta, d
             na[p] = p - s >= 0 ? al * a[p - s] : 0.0;
             nc[p] = p + s < S ? ga * c[p + s] : 0.0;
             nb[p] = b[p] + (p - s >= 0 ? al * c[p - s] : 0.0) + (p + s < S ? ga * a[p + s] : 0.0);
-            k1[(size_t)lev * 32 + p] = al;
-            k2[(size_t)lev * 32 + p] = ga;
+            k1[(size_t)lev * mp + p] = al;
+            k2[(size_t)lev * mp + p] = ga;
         }
         a.swap(na);
         b.swap(nb);
@@ -359,7 +362,11 @@ const LineTables& line_setup(lap_handle h, const Field& f, const Coef& c, double
     k->bnd = off / cross;
     k->c1 = form == LAP_FORM_B ? c.d * (1.0 - w) / k->wc : 0.0;
     k->omw = 1.0 - w;
-    const LineTables& t = line_tables(h, N, alpha, c.d, k->wc);
+    // x-lines long enough for 64 chunks of at least 48 unknowns take the two-warp cut (at 4097^2:
+    // 255 -> 242 us per half sweep); shorter chunks would spend most of their length in the
+    // boundary layer (about 34 positions at beta = 1), so shorter lines keep 32 chunks
+    const bool cut64 = x && N >= LINE_MAX_CHUNKS_X * 48;
+    const LineTables& t = line_tables(h, N, alpha, c.d, k->wc, cut64 ? LINE_MAX_CHUNKS_X : LINE_MAX_CHUNKS);
     if (x) {
         ck(prepare_line_kernels(line_smem_bytes(t)), "line kernel attributes");
         *scratch = nullptr;

@@ -220,7 +220,7 @@ struct lap_handle_s {
     uint64_t arena_epoch = 0;  // counts the calls that carved the arena (arena())
     std::unique_ptr<lap::BatchCacheBase> batch_cache;  // the last batched solve's plan
     double* pinned = nullptr;  // 8 doubles of pinned host memory for results
-    std::map<std::tuple<int, double, double, double>, lap::LineEntry> lines;
+    std::map<std::tuple<int, double, double, double, int>, lap::LineEntry> lines;
     std::map<std::tuple<int, int, double>, lap::CoarseEntry> coarse;
     // CUDA graphs of whole check periods (the iterations between two stopping tests),
     // keyed by every pointer and parameter baked into them; replayed on the caller's stream
@@ -286,7 +286,8 @@ void check_params(const lap_params* p);
 
 // line relaxation: cached tables of a line length and coefficients; the tables, coefficients
 // and scratch of a half sweep (allocating only on a shape's first use); one zebra half sweep
-const LineTables& line_tables(lap_handle h, int N, double alpha, double delta, double wc);
+const LineTables& line_tables(lap_handle h, int N, double alpha, double delta, double wc,
+                              int max_chunks = LINE_MAX_CHUNKS);
 const LineTables& line_setup(lap_handle h, const Field& f, const Coef& c, double w, int form,
                              int direction, LineCoefs* k, double** scratch);
 void line_half_sweep(lap_handle h, const Field& f, const Coef& c, double w, int form,

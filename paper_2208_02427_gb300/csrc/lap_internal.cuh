@@ -321,11 +321,13 @@ cudaError_t launch_b_up32(const TileItem* items, int count, const BatchLevel<flo
 // cyclic-reduction solve of the separators, and a scaled back substitution (line_kernels.cu).
 // Everything but the right-hand side depends only on (N, alpha, delta, w cross) and is
 // precomputed on the host.
-constexpr int LINE_MAX_CHUNKS = 32;
+constexpr int LINE_MAX_CHUNKS = 32;    // y-lines (one warp per line's separators)
+constexpr int LINE_MAX_CHUNKS_X = 64;  // x-lines (two warps run a line's chunks)
 struct LineTables {
     int N;       // unknowns per line
     int L;       // chunk length (full chunks)
-    int P;       // chunks (<= 32); separators S = P - 1
+    int P;       // chunks (<= maxp); separators S = P - 1
+    int maxp;    // chunk cap of this partition (32 or 64): the row stride of k1 and k2
     int Ll;      // length of the last chunk (1..L)
     int K0;      // F, gln, glnl are below 2^-64 of their first entry from position K0 on
     int levels;  // cyclic-reduction levels over the S separators
@@ -338,9 +340,9 @@ struct LineTables {
     const double* F;        // [L] forward elimination of alpha e_0: F_0 = alpha, F_q = F_{q-1} e_{q-1}
     const double* gln;      // [L] first row of the inverse of a length-L chunk matrix
     const double* glnl;     // [L] the same for the last chunk (length Ll)
-    const double* k1;       // [levels * 32] cyclic-reduction multipliers of the lower neighbour
-    const double* k2;       // [levels * 32] ... of the upper neighbour
-    const double* invb;     // [32] 1 / reduced diagonal
+    const double* k1;       // [levels * maxp] cyclic-reduction multipliers of the lower neighbour
+    const double* k2;       // [levels * maxp] ... of the upper neighbour
+    const double* invb;     // [maxp] 1 / reduced diagonal
 };
 // Per-call scalars of a half sweep: bnd = off / cross (the Dirichlet ends' coefficient in the
 // scaled right-hand side), c1 = d (1 - w) / (w cross) (form B), omw = 1 - w, wc = w cross.

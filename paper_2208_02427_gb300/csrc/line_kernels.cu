@@ -66,19 +66,45 @@ __device__ __forceinline__ double separator_solve(const LineTables& t, int p, in
         const double up = __shfl_up_sync(FULL, r, s);
         const double dn = __shfl_down_sync(FULL, r, s);
         double v = r;
-        if (p < S && p >= s) v = __fma_rn(t.k1[lev * 32 + p], up, v);
-        if (p + s < S) v = __fma_rn(t.k2[lev * 32 + p], dn, v);
+        if (p < S && p >= s) v = __fma_rn(t.k1[lev * t.maxp + p], up, v);
+        if (p + s < S) v = __fma_rn(t.k2[lev * t.maxp + p], dn, v);
         r = v;
     }
     return p < S ? r * t.invb[p] : 0.0;
 }
 
 // ---- x-lines --------------------------------------------------------------------------
+// x-lines are cut into up to LINE_MAX_CHUNKS_X = 64 chunks, run by the CTA's first two warps
+// (thread p = chunk p): the recurrences, the serial part of a line, take half the steps of a
+// 32-chunk cut on two schedulers, for about a tenth more FP64 operations (the chunks' boundary
+// layers cover a larger share of the shorter chunks). Values passed between neighbouring
+// chunks go through ex[] in shared memory, ordered by a 64-thread barrier.
+__device__ __forceinline__ void bar_chunks() { asm volatile("bar.sync 1, 64;" ::: "memory"); }
+
+// separator_solve across the two warps: level by level, each separator's value through ex[].
+__device__ __forceinline__ double separator_solve_x(const LineTables& t, int p, int S, double rho,
+                                                   double* ex)
+{
+    double r = p < S ? rho : 0.0;
+    for (int lev = 0, s = 1; lev < t.levels; ++lev, s <<= 1) {
+        ex[p] = r;
+        bar_chunks();
+        const double up = p >= s ? ex[p - s] : 0.0;
+        const double dn = p + s < LINE_MAX_CHUNKS_X ? ex[p + s] : 0.0;
+        bar_chunks();
+        double v = r;
+        if (p < S && p >= s) v = __fma_rn(t.k1[lev * t.maxp + p], up, v);
+        if (p + s < S) v = __fma_rn(t.k2[lev * t.maxp + p], dn, v);
+        r = v;
+    }
+    return p < S ? r * t.invb[p] : 0.0;
+}
+
 // The recurrences of one line held in shared memory in chunk layout (chunk p at sm[p * Ls],
-// its separator at sm[p * Ls + L]), run by one warp, lane p = chunk p: b~ in, the output
-// values' Z (chunk positions) and x~ (separators) out.
+// its separator at sm[p * Ls + L]), thread p = chunk p (p < 64): b~ in, the output values' Z
+// (chunk positions) and x~ (separators) out. ex: 64 doubles of shared memory.
 __device__ __forceinline__ void line_recurrences(const FmaOps& o, const LineTables& t,
-                                                 double* sm, int p)
+                                                 double* sm, int p, double* ex)
 {
     const int L = t.L, P = t.P, Ls = t.stride, K0 = t.K0;
     {
@@ -120,11 +146,16 @@ __device__ __forceinline__ void line_recurrences(const FmaOps& o, const LineTabl
             }
         }
         const double ylast = act ? fmul(o, t.inv_den[len - 1], G) : 0.0;
-        const double yfirst_next = __shfl_down_sync(FULL, D, 1);
+        ex[p] = D;
+        bar_chunks();
+        const double yfirst_next = p + 1 < LINE_MAX_CHUNKS_X ? ex[p + 1] : 0.0;
+        bar_chunks();
         double rho = 0.0;
         if (p < S) rho = __fma_rn(alpha, fadd(o, ylast, yfirst_next), y[L]);
-        const double xs = separator_solve(t, p, S, rho);
-        const double xl_ = __shfl_up_sync(FULL, xs, 1);
+        const double xs = separator_solve_x(t, p, S, rho, ex);
+        ex[p] = xs;
+        bar_chunks();
+        const double xl_ = p > 0 ? ex[p - 1] : 0.0;
         if (act) {
             const double xl = p > 0 ? xl_ : 0.0;
             const double xr = p < S ? xs : 0.0;
@@ -239,13 +270,14 @@ __device__ __forceinline__ void wait_flag(const unsigned* flag, unsigned* err)
 // CTAs at different phases overlap. sync: [0] error word (kept until the host reads it),
 // [1] item counter, [2 + r] flag of row r; [1 ..] zeroed before each launch.
 template <int FORM>
-__global__ void __launch_bounds__(LX_THREADS)
+__global__ void __launch_bounds__(LX_THREADS, 6)
     line_x_kernel(double* __restrict__ psi, int64_t pitch, int nlines, const LineTables t,
                   double bnd, double c1, double omw, unsigned* __restrict__ sync)
 {
     const FmaOps o = load_fma_ops();
     extern __shared__ double sm[];
     __shared__ int s_item;
+    __shared__ double ex[LINE_MAX_CHUNKS_X];
     const int nodd = (nlines + 1) / 2;
     c1 = in_reg(o, c1);
     omw = in_reg(o, omw);
@@ -267,7 +299,7 @@ __global__ void __launch_bounds__(LX_THREADS)
         double* row = psi + (int64_t)r * pitch;
         line_x_load<FORM>(o, t, sm, row, pitch, bnd, c1, threadIdx.x, LX_THREADS);
         __syncthreads();
-        if (threadIdx.x < 32) line_recurrences(o, t, sm, threadIdx.x);
+        if (threadIdx.x < LINE_MAX_CHUNKS_X) line_recurrences(o, t, sm, threadIdx.x, ex);
         __syncthreads();
         line_x_store<FORM>(o, t, sm, row, omw, threadIdx.x, LX_THREADS);
         __syncthreads();

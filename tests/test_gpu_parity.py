@@ -159,8 +159,10 @@ def test_coarsest_solve(lap, b, shape, beta):
     assert relerr(host(t), ora.coarse_direct(u, beta, q)) <= 1e-13
 
 
+# x-lines of 3072 unknowns or more are cut into up to 64 chunks (two warps), shorter ones into
+# up to 32: (3073, 5) and (3075, 5) sit on either side, (4097, 5) is the full 64-chunk cut
 LINE_SHAPES = [(3, 3), (25, 17), (300, 41), (41, 300), (1003, 7), (7, 1003), (4097, 5), (5, 4097),
-               (1025, 385), (36, 20), (20, 36)]
+               (1025, 385), (36, 20), (20, 36), (3073, 5), (3075, 5), (5, 3075)]
 
 
 @pytest.mark.parametrize("shape", LINE_SHAPES)
@@ -178,7 +180,7 @@ def test_line_sweep(lap, b, shape, direction, form, w):
     assert relerr(host(t), want) <= 1e-13
 
 
-@pytest.mark.parametrize("shape", [(130, 97), (97, 130), (33, 2049)])
+@pytest.mark.parametrize("shape", [(130, 97), (97, 130), (33, 2049), (3200, 9)])
 @pytest.mark.parametrize("direction", [0, 1])
 @pytest.mark.parametrize("form,w", [("A", 1.95), ("B", 1.95), ("B", 1.6)])
 @pytest.mark.parametrize("beta", [0.3, 3.0])
