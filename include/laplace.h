@@ -25,8 +25,10 @@
  * Arithmetic: FP64 throughout. Jacobi, Gauss-Seidel, SOR, the multigrid smoother,
  * residual, restriction and interpolation evaluate exactly the expressions written in
  * each entry's comment, with every multiply-add fused where the comment says fma and
- * nowhere else, so their results do not depend on the launch configuration. Line
- * solves, the coarsest-grid solve and norms are reassociated for parallelism.
+ * nowhere else, so their results do not depend on the launch configuration. lap_solve's
+ * Gauss-Seidel and SOR can instead sum the neighbours as (W + S) + (E + N) (lap_params
+ * sum_order, beta = 1), again one fixed expression. Line solves, the coarsest-grid solve
+ * and norms are reassociated for parallelism.
  */
 #ifndef LAPLACE_H
 #define LAPLACE_H
