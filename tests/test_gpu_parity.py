@@ -651,3 +651,38 @@ def test_diagonal_order_refuses_other_methods_and_beta(lap, b):
         with pytest.raises(b.LapError) as e:
             lap.solve(good, 1.0, 1.0, method=method, max_iter=2, sum_order="diagonal")
         assert "EINVAL" in str(e.value)
+
+
+# ---- size limits ---------------------------------------------------------------------
+
+@pytest.mark.parametrize("direction", [0, 1])
+@pytest.mark.parametrize("form", ["A", "B"])
+def test_longest_lines(lap, b, direction, form):
+    """Lines of 16383 unknowns, the longest the line solver takes (x-lines: 64 chunks of 255 in
+    131 KB of shared memory per CTA; y-lines: 32 chunks of 511), against the oracle; one more
+    unknown is refused with EUNSUPPORTED."""
+    shape = (16385, 5) if direction == 0 else (5, 16385)
+    psi = rand_field(*shape, 41)
+    t = b.to_field(psi)
+    lap.line_sweep(t, 1.3, form, direction, 1.0, 1.0)
+    want = ora.line_sweep(psi, 1.3, direction, 1.0, ora.FORM_A if form == "A" else ora.FORM_B,
+                          ora.LINES_ZEBRA)
+    assert relerr(host(t), want) <= 1e-13
+    big = b.to_field(rand_field(*((16386, 5) if direction == 0 else (5, 16386)), 42))
+    with pytest.raises(b.LapError) as e:
+        lap.line_sweep(big, 1.3, form, direction, 1.0, 1.0)
+    assert "EUNSUPPORTED" in str(e.value)
+
+
+def test_largest_coarsest_solve(lap, b):
+    """The exact coarsest-level solve at its limit of 1024 interior unknowns (34 x 34 field),
+    against the oracle's Gaussian elimination; 35 x 34 (1056 unknowns) is refused."""
+    u = wl.random_ring(34, 34, 13)
+    q = wl.random_interior(np.zeros((34, 34)), 14)
+    t = b.to_field(u)
+    lap.coarse_solve(t, 1.0, 1.0, b.to_field(q))
+    assert relerr(host(t), ora.coarse_direct(u, 1.0, q)) <= 1e-12
+    with pytest.raises(b.LapError) as e:
+        lap.coarse_solve(b.to_field(wl.random_ring(35, 34, 15)), 1.0, 1.0,
+                         b.to_field(np.zeros((34, 35))))
+    assert "EUNSUPPORTED" in str(e.value)
