@@ -2,7 +2,9 @@
 //
 // Every phase of a cycle (a smoother colour pass, the residual, the restriction, the
 // interpolation, the coarsest solve, the residual norm) is one launch over a work list of
-// (level, block of rows) items gathered from all problems that take part in that phase.
+// (level, block of rows) items gathered from all problems that take part in that phase:
+// one CTA per item, or a persistent launch whose resident CTAs claim the items from a counter
+// (ItemClaim); the tuner picks one.
 // Per problem the arithmetic is exactly the single-grid kernels' (same expressions, same
 // roundings), so a batched solve reproduces each problem's single-grid iterates. A
 // problem that has converged is skipped by every later launch (its `active` flag); the
