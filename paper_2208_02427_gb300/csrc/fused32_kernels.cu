@@ -17,8 +17,11 @@
 //
 // Shared-memory layout: a region row keeps its even columns in one half and its odd
 // columns in the other, so the points of one colour in a row are contiguous and their
-// east/west neighbours are contiguous in the other half (no bank conflicts); the half
-// stride is 16 mod 32 words so that the two halves of a row fall into different banks.
+// east/west neighbours are contiguous in the other half (no bank conflicts within a
+// half-row access). The half stride is the 64 points plus 4 words (16-byte aligned rows):
+// a descent tile's two arrays then take 68 KB, so three descent CTAs share an SM's shared
+// memory (measured: the batched mixed solve of 4096 uneven grids 46.5 -> 44.5 ms against a
+// half stride of 80 with two CTAs per SM).
 #include <algorithm>
 #include <type_traits>
 
@@ -32,7 +35,7 @@ namespace {
 constexpr int FT_THREADS = 512;
 constexpr int FT_W = 128;               // region columns (even): 64 column pairs
 constexpr int FT_H = 64;                // region rows (single-grid tiles; batched: a variant)
-constexpr int FT_HS = FT_W / 2 + 16;    // half-row stride, 16 mod 32
+constexpr int FT_HS = FT_W / 2 + 4;     // half-row stride (16-byte aligned)
 constexpr int FT_RS = 2 * FT_HS;        // row stride
 constexpr int FT_CS = FT_W / 2 + 4;     // row stride of the staged coarse points
 // floats per shared array, and of the staged coarse points, for regions of H rows
@@ -461,10 +464,12 @@ __device__ __forceinline__ void up_tile(const BatchLevel<float>& F, const BatchL
 }
 
 // ---- one grid: tile (blockIdx.x, blockIdx.y) of owned points 1 + (bx tx, by ty) ----
-// NT threads: 512 (two CTAs per SM) for levels with many tiles, 1024 (one CTA per SM, half
-// the rows per warp: a shorter critical path) for levels with fewer tiles than SMs.
+// NT threads: 512 for levels with many tiles (three descent or two ascent CTAs per SM: the
+// descent's two arrays fit three times in shared memory, at 40 registers; the ascent also
+// stages the coarse points), 1024 (one CTA per SM, half the rows per warp: a shorter critical
+// path) for levels with fewer tiles than SMs.
 template <int NT>
-__global__ void __launch_bounds__(NT, 1024 / NT)
+__global__ void __launch_bounds__(NT, NT == 512 ? 3 : 1)
     down32_kernel(BatchLevel<float> F, BatchLevel<float> C, int tx, int ty, int nu1, int zero_u,
                   int gs, float w, float omw)
 {
@@ -498,7 +503,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT)
 
 // ---- many grids: one tile item per CTA, NT threads, regions of H rows ----
 template <int NT, int H>
-__global__ void __launch_bounds__(NT, 1024 / NT)
+__global__ void __launch_bounds__(NT, NT == 512 ? 3 : 1)
     b_down32_kernel(const TileItem* __restrict__ items, int count, unsigned* claim,
                     const BatchLevel<float>* __restrict__ lv,
                     const int* __restrict__ active, int nu1, int zero_u, int gs, float w, float omw)
@@ -553,6 +558,8 @@ __global__ void __launch_bounds__(NT, 1024 / NT)
 
 constexpr size_t ft_smem(int H) { return (2 * (size_t)ft_arr(H) + ft_carr(H)) * sizeof(float); }
 constexpr size_t FT_SMEM = ft_smem(FT_H);
+constexpr size_t ft_smem_down(int H) { return 2 * (size_t)ft_arr(H) * sizeof(float); }
+constexpr size_t FT_SMEM_DOWN = ft_smem_down(FT_H);
 constexpr int FT_FEW_TILES = 152;  // below one tile per SM: 1024-thread tiles
 
 }  // namespace
@@ -613,15 +620,15 @@ cudaError_t prepare_fused32()
     const int dev = attr_slot();
     if (dev >= 0 && g_fused32_ready[dev].load() != 0) return cudaSuccess;
     const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
-    cudaError_t e = cudaFuncSetAttribute(down32_kernel<512>, a, (int)FT_SMEM);
+    cudaError_t e = cudaFuncSetAttribute(down32_kernel<512>, a, (int)FT_SMEM_DOWN);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(up32_kernel<512>, a, (int)FT_SMEM);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(down32_kernel<1024>, a, (int)FT_SMEM);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(down32_kernel<1024>, a, (int)FT_SMEM_DOWN);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(up32_kernel<1024>, a, (int)FT_SMEM);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(b_down32_kernel<512, 64>, a, (int)ft_smem(64));
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(b_down32_kernel<512, 64>, a, (int)ft_smem_down(64));
     if (e == cudaSuccess) e = cudaFuncSetAttribute(b_up32_kernel<512, 64>, a, (int)ft_smem(64));
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(b_down32_kernel<1024, 64>, a, (int)ft_smem(64));
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(b_down32_kernel<1024, 64>, a, (int)ft_smem_down(64));
     if (e == cudaSuccess) e = cudaFuncSetAttribute(b_up32_kernel<1024, 64>, a, (int)ft_smem(64));
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(b_down32_kernel<512, 32>, a, (int)ft_smem(32));
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(b_down32_kernel<512, 32>, a, (int)ft_smem_down(32));
     if (e == cudaSuccess) e = cudaFuncSetAttribute(b_up32_kernel<512, 32>, a, (int)ft_smem(32));
     if (e == cudaSuccess) attr_record(g_fused32_ready, dev, 1);
     return e;
@@ -634,10 +641,10 @@ cudaError_t launch_down32(const BatchLevel<float>& F, const BatchLevel<float>& C
     fused32_tile(F.m, F.n, nu1, nu2, &tx, &ty, &ntx, &nty);
     const float wf = (float)w, omw = (float)(1.0 - w);
     if (ntx * nty < FT_FEW_TILES)
-        down32_kernel<1024><<<dim3(ntx, nty), 1024, FT_SMEM, s>>>(F, C, tx, ty, nu1, zero_u ? 1 : 0,
+        down32_kernel<1024><<<dim3(ntx, nty), 1024, FT_SMEM_DOWN, s>>>(F, C, tx, ty, nu1, zero_u ? 1 : 0,
                                                                   gs ? 1 : 0, wf, omw);
     else
-        down32_kernel<512><<<dim3(ntx, nty), 512, FT_SMEM, s>>>(F, C, tx, ty, nu1, zero_u ? 1 : 0,
+        down32_kernel<512><<<dim3(ntx, nty), 512, FT_SMEM_DOWN, s>>>(F, C, tx, ty, nu1, zero_u ? 1 : 0,
                                                                 gs ? 1 : 0, wf, omw);
     note_launch();
     return cudaGetLastError();
@@ -677,13 +684,13 @@ cudaError_t launch_b_down32(const TileItem* items, int count, const BatchLevel<f
     const int z = zero_u ? 1 : 0, g = gs ? 1 : 0;
     const float wf = (float)w, omw = (float)(1.0 - w);
     if (variant == 2)
-        tile_launch(b_down32_kernel<1024, 64>, 1024, ft_smem(64), items, count, claim, s,
+        tile_launch(b_down32_kernel<1024, 64>, 1024, ft_smem_down(64), items, count, claim, s,
                     lv, active, nu1, z, g, wf, omw);
     else if (variant == 3)
-        tile_launch(b_down32_kernel<512, 32>, 512, ft_smem(32), items, count, claim, s,
+        tile_launch(b_down32_kernel<512, 32>, 512, ft_smem_down(32), items, count, claim, s,
                     lv, active, nu1, z, g, wf, omw);
     else
-        tile_launch(b_down32_kernel<512, 64>, 512, ft_smem(64), items, count, claim, s,
+        tile_launch(b_down32_kernel<512, 64>, 512, ft_smem_down(64), items, count, claim, s,
                     lv, active, nu1, z, g, wf, omw);
     note_launch();
     return cudaGetLastError();
