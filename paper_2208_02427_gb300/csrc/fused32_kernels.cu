@@ -32,7 +32,6 @@ namespace lap {
 
 namespace {
 
-constexpr int FT_THREADS = 512;
 constexpr int FT_W = 128;               // region columns (even): 64 column pairs
 constexpr int FT_H = 64;                // region rows (single-grid tiles; batched: a variant)
 constexpr int FT_HS = FT_W / 2 + 4;     // half-row stride (16-byte aligned)
@@ -569,11 +568,11 @@ constexpr int FT_FEW_TILES = 152;  // below one tile per SM: 1024-thread tiles
 static int halo_down(int nu1) { return 2 + 2 * nu1; }
 static int halo_up(int nu2) { return 2 * nu2; }
 
-// Region rows of a batched tile variant: 1 = 512 threads over 128 x 64 regions (two CTAs per
-// SM), 2 = 1024 threads over 128 x 64 (one CTA per SM, half the rows per warp: a shorter
-// critical path per tile), 3 = 512 threads over 128 x 32 (smaller tiles, more of them).
+// Region rows of a batched tile variant: 1 = 512 threads over 128 x 64 regions (three descent
+// or two ascent CTAs per SM), 2 = 1024 threads over 128 x 64 (one CTA per SM, half the rows per
+// warp: a shorter critical path per tile), 3 = 512 threads over 128 x 32 (smaller tiles, more
+// of them).
 static int variant_rows(int variant) { return variant == 3 ? 32 : FT_H; }
-static int variant_threads(int variant) { return variant == 2 ? 1024 : 512; }
 
 static bool tiles_fit(int H, int nu1, int nu2)
 {
