@@ -41,7 +41,6 @@ constexpr int FT_CS = FT_W / 2 + 4;     // row stride of the staged coarse point
 __host__ __device__ constexpr int ft_arr(int H) { return FT_RS * H; }
 __host__ __device__ constexpr int ft_carr(int H) { return FT_CS * (H / 2 + 2); }
 constexpr int FT_ARR = ft_arr(FT_H);
-constexpr int FT_CARR = ft_carr(FT_H);
 
 // The region of a tile: global (gx0 + lx, gy0 + ly) for local 0 <= lx < w, 0 <= ly < h.
 // gx0 is even: local column lx = 2p + half sits at half `half`, index p, of its row, and
