@@ -491,3 +491,25 @@ def test_diagonal_order_needs_unit_beta_and_a_point_method():
         ora.solve(psi, method=ora.MG, sum_order=ora.SUM_DIAGONAL)
     with pytest.raises(ValueError):
         ora.solve(psi, method=ora.SOR, w=1.5, dx=0.5, dy=1.0, sum_order=ora.SUM_DIAGONAL)
+
+
+@pytest.mark.parametrize("w", [0.7, 1.0, 1.5, 1.9])
+@pytest.mark.parametrize("order", [ora.SUM_PAPER, ora.SUM_DIAGONAL])
+def test_sor_black_defect_is_one_minus_w_times_the_pass_defect(w, order):
+    """Eq. 7 in red-black order: a black point's neighbours are all red, so during the black
+    pass its defect is that of the field with the new reds and the old blacks, and after its
+    update the defect is (1 - w) times that. Both fields' defects come from the oracle's
+    residual, the sweep from its SOR; nothing here re-implements the update. A wrong blend
+    (sign, w or 1 - w swapped), a colour swept twice or in the wrong order breaks it."""
+    m, n = 23, 17
+    psi0 = wl.random_interior(wl.random_ring(m, n, seed=60), seed=61)
+    psi1 = ora.sor_sweep(psi0, w, 1.0, ora.RB, sum_order=order)
+    jj, ii = np.meshgrid(np.arange(n), np.arange(m), indexing="ij")
+    black = ((ii + jj) % 2 == 1)
+    black[0, :] = black[-1, :] = black[:, 0] = black[:, -1] = False
+    mid = np.where(black, psi0, psi1)  # new reds, old blacks (the ring is the same in both)
+    r_pass = ora.defect(mid, beta=1.0)[black]
+    r_after = ora.defect(psi1, beta=1.0)[black]
+    scale = np.max(np.abs(r_pass))
+    assert scale > 0
+    assert np.max(np.abs(r_after - (1.0 - w) * r_pass)) <= 1e-13 * scale
