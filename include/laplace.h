@@ -97,9 +97,17 @@ typedef enum {
                             instead of 3 (red-black sweeps are bound by the FP64 issue rate) */
 } lap_sum_order;
 
+/* The largest grid: m <= LAP_GRID_MAX_M (row indices and ring counts stay within 32-bit
+ * ints) and n <= LAP_GRID_MAX_N (the point kernels launch one CTA row per two field rows,
+ * at most 65535); larger grids give LAP_EUNSUPPORTED. Methods add their own limits: the
+ * coarsest multigrid level holds at most 1024 unknowns, ADI/SLOR lines at most 16383,
+ * lexicographic sweeps 28672 points, and LAP_SUM_DIAGONAL about 2.5e10 points. */
+#define LAP_GRID_MAX_M (1 << 28)
+#define LAP_GRID_MAX_N 131070
+
 /* The grid of Eq. 4: m points along x, n along y, spacings dx and dy (> 0). */
 typedef struct {
-    int32_t m, n;     /* >= 3 each */
+    int32_t m, n;     /* >= 3 each; at most LAP_GRID_MAX_M, LAP_GRID_MAX_N */
     double dx, dy;
     int64_t pitch;    /* row pitch of the field, in doubles, >= m */
 } lap_grid;

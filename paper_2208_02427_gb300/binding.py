@@ -25,6 +25,8 @@ METHODS = {"jacobi": 0, "gs": 1, "sor": 2, "adi": 3, "mg": 4, "mg_mixed": 5, "sl
 NORMS = {"l2_rel": 0, "l2_abs": 1, "maxdelta": 2}
 FORMS = {"A": 0, "B": 1}
 SUM_ORDERS = {"paper": 0, "diagonal": 1}
+GRID_MAX_M = 1 << 28  # LAP_GRID_MAX_M: the widest grid (points along x)
+GRID_MAX_N = 131070  # LAP_GRID_MAX_N: the tallest grid (points along y)
 STATUS = {0: "converged", 1: "max_iter", 2: "diverged"}
 ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "EUNSUPPORTED"}
 
@@ -239,9 +241,15 @@ class Laplace:
         _check(self._lib.lap_set_graphs(self._h, 1 if enabled else 0))
 
     def workspace_bytes(self, psi, dx=1.0, dy=1.0, **kw) -> int:
+        """Scratch bytes lap_solve needs for the field psi, or for a grid shape (m, n) (row
+        pitch m) before any field is allocated; LapError where the solve would refuse."""
+        if isinstance(psi, torch.Tensor):
+            g = _grid(psi, dx, dy)
+        else:
+            m, n = (int(v) for v in psi)
+            g = Grid(m, n, float(dx), float(dy), m)
         out = C.c_size_t(0)
-        _check(self._lib.lap_workspace_bytes(C.byref(_grid(psi, dx, dy)), C.byref(params(**kw)),
-                                             C.byref(out)))
+        _check(self._lib.lap_workspace_bytes(C.byref(g), C.byref(params(**kw)), C.byref(out)))
         return out.value
 
     def solve(self, psi: torch.Tensor, dx=1.0, dy=1.0, stream=None, **kw) -> dict:

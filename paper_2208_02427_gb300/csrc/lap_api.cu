@@ -123,6 +123,8 @@ void check_grid(const lap_grid* g)
     if (!(g->dx > 0.0) || !(g->dy > 0.0) || !std::isfinite(g->dx) || !std::isfinite(g->dy))
         fail(LAP_EINVAL, "dx and dy must be finite and > 0");
     if (g->pitch < g->m) fail(LAP_EINVAL, "pitch must be >= m");
+    if (g->m > LAP_GRID_MAX_M) fail(LAP_EUNSUPPORTED, "m above LAP_GRID_MAX_M (2^28)");
+    if (g->n > LAP_GRID_MAX_N) fail(LAP_EUNSUPPORTED, "n above LAP_GRID_MAX_N (131070)");
     if ((int64_t)g->n * g->pitch > ((int64_t)1 << 40)) fail(LAP_EUNSUPPORTED, "field too large");
 }
 
@@ -1419,25 +1421,20 @@ void lap_destroy(lap_handle h)
     delete h;
 }
 
-int lap_workspace_bytes(const lap_grid* g, const lap_params* p, size_t* bytes)
-{
-    return guarded([&] {
-        check_grid(g);
-        check_params(p);
-        if (!bytes) fail(LAP_EINVAL, "bytes is NULL");
-        *bytes = work_bytes(g, p);
-    });
-}
-
 namespace {
 
-// lap_solve after the handle, result and pointer checks
-void solve_device(lap_handle h, const lap_grid* g, double* psi_dev, const lap_params* p,
-                  lap_result* out, cudaStream_t stream)
+// What lap_solve cannot run on a valid grid with valid parameters (LAP_EUNSUPPORTED): the
+// same answer from the size query as from the solve.
+void check_supported(const lap_grid* g, const lap_params* p)
 {
-    Solver sv{h, stream, Field{psi_dev, g->m, g->n, g->pitch}, make_coef(g->dx, g->dy), p, {}};
-    if (p->sum_order == LAP_SUM_DIAGONAL && !sv.c.unit_beta)
-        fail(LAP_EUNSUPPORTED, "sum_order LAP_SUM_DIAGONAL needs dx == dy (beta = 1)");
+    if (p->sum_order == LAP_SUM_DIAGONAL) {
+        if (!make_coef(g->dx, g->dy).unit_beta)
+            fail(LAP_EUNSUPPORTED, "sum_order LAP_SUM_DIAGONAL needs dx == dy (beta = 1)");
+        if (rb_diag_walks(g->m, g->n) > RB_DIAG_MAX_WALKS)
+            fail(LAP_EUNSUPPORTED, "sum_order LAP_SUM_DIAGONAL numbers its diagonal walks with "
+                                   "32-bit ints: at most about 2.5e10 points (LAP_SUM_PAPER has "
+                                   "no such limit)");
+    }
     if (p->method == LAP_MG || p->method == LAP_MG_MIXED || p->method == LAP_MG_FP32) {
         const int L = mg_level_count(g->m, g->n, p->coarsest_min, p->max_levels);
         int m = g->m, n = g->n;
@@ -1456,6 +1453,29 @@ void solve_device(lap_handle h, const lap_grid* g, double* psi_dev, const lap_pa
     if ((p->method == LAP_ADI || p->method == LAP_SLOR) &&
         (g->m - 2 > LINE_MAX_N || g->n - 2 > LINE_MAX_N))
         fail(LAP_EUNSUPPORTED, "ADI lines longer than 16383 unknowns");
+}
+
+}  // namespace
+
+int lap_workspace_bytes(const lap_grid* g, const lap_params* p, size_t* bytes)
+{
+    return guarded([&] {
+        check_grid(g);
+        check_params(p);
+        if (!bytes) fail(LAP_EINVAL, "bytes is NULL");
+        check_supported(g, p);
+        *bytes = work_bytes(g, p);
+    });
+}
+
+namespace {
+
+// lap_solve after the handle, result and pointer checks
+void solve_device(lap_handle h, const lap_grid* g, double* psi_dev, const lap_params* p,
+                  lap_result* out, cudaStream_t stream)
+{
+    check_supported(g, p);
+    Solver sv{h, stream, Field{psi_dev, g->m, g->n, g->pitch}, make_coef(g->dx, g->dy), p, {}};
     const size_t need = work_bytes(g, p);
     Carver cv(arena(h, need));
     carve(cv, sv.w, g, p);
@@ -1487,6 +1507,7 @@ int lap_solve_host(lap_handle h, const lap_grid* g, double* psi_host, int64_t ho
         if (!out) fail(LAP_EINVAL, "result is NULL");
         check_grid(g);
         check_params(p);
+        check_supported(g, p);  // before the field is allocated and copied
         if (!psi_host) fail(LAP_EINVAL, "psi_host is NULL");
         if (((uintptr_t)psi_host) % 8) fail(LAP_EINVAL, "psi_host is not 8-byte aligned");
         if (host_pitch < g->m) fail(LAP_EINVAL, "host_pitch must be >= m");

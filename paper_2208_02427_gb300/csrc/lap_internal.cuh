@@ -62,7 +62,18 @@ cudaError_t launch_rb_colour(const Field& f, const double* q, const Coef& c, boo
                              int colour, unsigned long long* maxd, cudaStream_t s,
                              const double* wslot = nullptr);
 // The same colour pass with the neighbour sum paired along diagonals, (W + S) + (E + N), for
-// beta = 1 only (rb_diag_kernel): 4 FP64 operations per SOR update instead of 5.
+// beta = 1 only (rb_diag_kernel): 4 FP64 operations per SOR update instead of 5. A thread
+// walks RD_K points down a diagonal, RD_BX threads per CTA. The rows are cut into strips of
+// RD_K; the widest strip of an m-wide field has rb_diag_starts(m) walks, and the launch takes
+// rb_diag_walks(m, n) in all, numbered with 32-bit ints: at most RB_DIAG_MAX_WALKS (a field of
+// about 2.5e10 points). The launcher returns cudaErrorInvalidValue above that.
+constexpr int RD_BX = 128, RD_K = 6;
+constexpr int64_t RB_DIAG_MAX_WALKS = 2147483647 - RD_BX;
+inline int rb_diag_starts(int m) { return (m - 2 - (2 - RD_K)) / 2 + 1; }
+inline int64_t rb_diag_walks(int m, int n)
+{
+    return (int64_t)rb_diag_starts(m) * ((n - 2 + RD_K - 1) / RD_K);
+}
 cudaError_t launch_rb_diag(const Field& f, const double* q, bool gs, double w, int colour,
                            unsigned long long* maxd, cudaStream_t s, const double* wslot = nullptr);
 // One Jacobi sweep (Eq. 5) from in to out (same pitch; ring not touched).

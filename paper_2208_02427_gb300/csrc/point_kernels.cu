@@ -78,12 +78,13 @@ __global__ void __launch_bounds__(RB_BX* RB_BY)
 // Strip s of rows j0 = 1 + s RD_K .. j0 + RD_K - 1: walk x of the strip starts on row j0 at
 // column lo + 2x, lo the first column >= 2 - RD_K of the colour, and visits (lo + 2x + k,
 // j0 + k). Thread g of the launch takes walk g % starts of strip g / starts (no CTA is left
-// nearly empty at the end of a strip). Walks of 6 points in 128-thread CTAs: measured per
-// colour pass inside the solve's graphs at 4097^2, (walk, CTA) = (4, 128) 63.2 us, (6, 128)
-// 62.9, (8, 128) 64.7, (8, 256) 68.3, (16, 128) 66.0 with the loads one point ahead and
-// 73.4 for walks of 32 (a longer walk adds registers, a shorter one pair adds), against 71.0 us
-// for the paper-order kernel.
-constexpr int RD_BX = 128, RD_K = 6;
+// nearly empty at the end of a strip). Walks of RD_K = 6 points in CTAs of RD_BX = 128
+// threads: measured per colour pass inside the solve's graphs at 4097^2, (walk, CTA) =
+// (4, 128) 63.2 us, (6, 128) 62.9, (8, 128) 64.7, (8, 256) 68.3, (16, 128) 66.0 with the
+// loads one point ahead and 73.4 for walks of 32 (a longer walk adds registers, a shorter one
+// pair adds), against 71.0 us for the paper-order kernel. Within a walk, taking every pair sum
+// first or every (1 - w) C product first gave 63.1 and 62.9 us against 62.7 for the order
+// below (a pair, then its point).
 
 template <bool HAS_Q, bool GS, bool MAXD>
 __global__ void __launch_bounds__(RD_BX)
@@ -352,8 +353,9 @@ cudaError_t launch_rb_colour(const Field& f, const double* q, const Coef& c, boo
 cudaError_t launch_rb_diag(const Field& f, const double* q, bool gs, double w, int colour,
                            unsigned long long* maxd, cudaStream_t s, const double* wslot)
 {
-    const int starts = (f.m - 2 - (2 - RD_K)) / 2 + 1;  // walks per strip (the widest)
-    const int64_t walks = (int64_t)starts * ((f.n - 2 + RD_K - 1) / RD_K);
+    const int starts = rb_diag_starts(f.m);
+    const int64_t walks = rb_diag_walks(f.m, f.n);
+    if (walks > RB_DIAG_MAX_WALKS) return cudaErrorInvalidValue;  // the kernel's int numbering
     const int grid = (int)((walks + RD_BX - 1) / RD_BX);
     const double omw = 1.0 - w;
     LAP_DISPATCH_BOOL(q != nullptr, HQ, LAP_DISPATCH_BOOL(gs, GS, LAP_DISPATCH_BOOL(maxd != nullptr, MD,

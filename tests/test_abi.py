@@ -78,3 +78,20 @@ def test_struct_layouts_match_header(tmp_path):
         assert seen[(cname, "size")] == C.sizeof(py)
         for fname, _ in py._fields_:
             assert seen[(cname, fname)] == getattr(py, fname).offset, (cname, fname)
+
+
+def test_grid_limits_match_header(tmp_path):
+    """The binding's grid limits are the header's macros."""
+    import shutil
+    import subprocess
+    from paper_2208_02427_gb300 import binding
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if not cc:
+        pytest.skip("no C compiler")
+    prog = tmp_path / "limits.c"
+    prog.write_text('#include <stdio.h>\n#include "laplace.h"\nint main(void){'
+                    'printf("%ld %ld\\n", (long)LAP_GRID_MAX_M, (long)LAP_GRID_MAX_N); return 0;}\n')
+    exe = tmp_path / "limits"
+    subprocess.check_call([cc, "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)])
+    m, n = (int(v) for v in subprocess.check_output([str(exe)], text=True).split())
+    assert (m, n) == (binding.GRID_MAX_M, binding.GRID_MAX_N)
