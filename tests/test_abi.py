@@ -1,5 +1,6 @@
 """The C-ABI library builds, loads without a GPU and exports every entry point that
-include/laplace.h declares; host-only calls (defaults, error strings) work on the CPU."""
+include/laplace.h declares; host-only calls (defaults, error strings, size queries and their
+refusals) work on the CPU."""
 import ctypes as C
 import os
 import re
@@ -95,3 +96,36 @@ def test_grid_limits_match_header(tmp_path):
     subprocess.check_call([cc, "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)])
     m, n = (int(v) for v in subprocess.check_output([str(exe)], text=True).split())
     assert (m, n) == (binding.GRID_MAX_M, binding.GRID_MAX_N)
+
+
+def test_size_query_refuses_what_the_solve_refuses(lib):
+    """lap_workspace_bytes is host arithmetic: it gives lap_solve's refusals from the shape
+    alone, with nothing allocated. Refused (LAP_EUNSUPPORTED): one column more than
+    LAP_GRID_MAX_M, one row more than LAP_GRID_MAX_N, the diagonal summation order past its
+    32-bit walk numbering (2^28 x 97: 16 strips of 2^27 + 2 walks, 2^31 + 32 in all; 2^28 x 91
+    has 15 strips and is taken, and the printed order takes both), the diagonal order with
+    dx != dy, ADI lines past 16383 unknowns, lexicographic sweeps past 28672 points and a
+    coarsest multigrid level past 1024 unknowns."""
+    from paper_2208_02427_gb300 import binding as b
+    M, N = b.GRID_MAX_M, b.GRID_MAX_N
+
+    def query(shape, dx=1.0, dy=1.0, **kw):
+        g = b.Grid(shape[0], shape[1], dx, dy, shape[0])
+        out = C.c_size_t(0)
+        return lib.lap_workspace_bytes(C.byref(g), C.byref(b.params(**kw)), C.byref(out))
+
+    EUNSUPPORTED = -4
+    assert query((M, 5), method="jacobi") == 0
+    assert query((5, N), method="jacobi") == 0
+    assert query((M + 1, 5), method="jacobi") == EUNSUPPORTED
+    assert query((5, N + 1), method="jacobi") == EUNSUPPORTED
+    assert query((M, 91), method="sor", w=1.5, sum_order="diagonal") == 0
+    assert query((M, 97), method="sor", w=1.5, sum_order="diagonal") == EUNSUPPORTED
+    assert query((M, 97), method="sor", w=1.5) == 0
+    assert query((65, 65), 1.0, 0.5, method="sor", w=1.5, sum_order="diagonal") == EUNSUPPORTED
+    assert query((16385, 5), method="adi", w=1.3) == 0
+    assert query((16386, 5), method="adi", w=1.3) == EUNSUPPORTED
+    assert query((224, 128), method="sor_lex", w=1.5) == 0
+    assert query((225, 128), method="sor_lex", w=1.5) == EUNSUPPORTED
+    assert query((34, 34), method="mg", max_levels=1) == 0
+    assert query((35, 34), method="mg", max_levels=1) == EUNSUPPORTED

@@ -696,31 +696,6 @@ def test_tallest_grid(lap, b):
     assert "EUNSUPPORTED" in str(e.value)
 
 
-def test_size_limits_from_the_size_query(lap, b):
-    """lap_workspace_bytes refuses what lap_solve refuses, from the shape alone (nothing is
-    allocated): one column more than LAP_GRID_MAX_M, one row more than LAP_GRID_MAX_N, the
-    diagonal summation order past its 32-bit walk numbering (2^28 x 97: 16 strips of
-    2^27 + 2 walks, 2^31 + 32 in all; 2^28 x 91 has 15 strips and is taken, and the printed
-    order takes both), the diagonal order with dx != dy, and ADI lines past 16383 unknowns."""
-    M, N = b.GRID_MAX_M, b.GRID_MAX_N
-
-    def refused(shape, dx=1.0, dy=1.0, **kw):
-        with pytest.raises(b.LapError) as e:
-            lap.workspace_bytes(shape, dx, dy, **kw)
-        return "EUNSUPPORTED" in str(e.value)
-
-    assert lap.workspace_bytes((M, 5), method="jacobi") > 0
-    assert lap.workspace_bytes((5, N), method="jacobi") > 0
-    assert refused((M + 1, 5), method="jacobi")
-    assert refused((5, N + 1), method="jacobi")
-    assert lap.workspace_bytes((M, 91), method="sor", w=1.5, sum_order="diagonal") >= 0
-    assert refused((M, 97), method="sor", w=1.5, sum_order="diagonal")
-    assert lap.workspace_bytes((M, 97), method="sor", w=1.5) >= 0
-    assert refused((65, 65), 1.0, 0.5, method="sor", w=1.5, sum_order="diagonal")
-    assert lap.workspace_bytes((16385, 5), method="adi", w=1.3) >= 0
-    assert refused((16386, 5), method="adi", w=1.3)
-
-
 def test_largest_coarsest_solve(lap, b):
     """The exact coarsest-level solve at its limit of 1024 interior unknowns (34 x 34 field),
     against the oracle's Gaussian elimination; 35 x 34 (1056 unknowns) is refused."""
