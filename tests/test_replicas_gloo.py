@@ -28,7 +28,7 @@ def _worker(rank, size, port, out):
 
 def test_two_ranks_shard_and_reduce():
     port = _free_port()
-    with mp.Manager() as man:
+    with mp.get_context("spawn").Manager() as man:  # no fork of this multi-threaded process
         out = man.dict()
         mp.spawn(_worker, args=(2, port, out), nprocs=2, join=True)
         res = dict(out)
