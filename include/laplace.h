@@ -248,7 +248,9 @@ typedef struct lap_server_s* lap_server;
 int lap_server_create(lap_server* out, lap_handle h, size_t hbm_budget_bytes, const lap_params* p,
                       int max_running, int sor_sweeps);
 void lap_server_destroy(lap_server s);
-/* method: LAP_MG, LAP_MG_MIXED or LAP_SOR_RB; max_iter counts V-cycles, or sweeps for SOR.
+/* method: LAP_MG, LAP_MG_MIXED or LAP_SOR_RB; max_iter counts V-cycles, or sweeps for SOR
+ * (an SOR request's last step sweeps only up to max_iter, as lap_solve's last check period
+ * stops there; max_iter = 0 returns the initial residual, the field untouched).
  * LAP_ENOMEM if the request's hierarchy exceeds the whole pool. *id identifies it. */
 int lap_server_submit(lap_server s, const lap_grid* g, double* psi_dev, int method, double w,
                       double tol, int64_t max_iter, int64_t* id);

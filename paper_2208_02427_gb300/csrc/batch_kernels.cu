@@ -575,6 +575,8 @@ __global__ void b_converge_kernel(const double* __restrict__ partials,
             status[p] = 2;
         } else if ((rel && nr == 0.0) || (!rel && nr <= tol)) {
             status[p] = 0;
+        } else if (maxit && maxit[p] <= 0) {
+            status[p] = 1;  // no iteration allowed: retire with the initial norm
         } else {
             return;
         }

@@ -283,7 +283,8 @@ struct Completion {
 // mode 0: record r0 (retire problems already converged); mode 1: count a cycle and test.
 // Problems with no items in the list are left alone; tolv (nullable) gives one tol each;
 // maxit (nullable): a problem that has run its maxit[p] cycles without converging retires
-// with LAP_MAXITER; done (nullable): every retiring problem is appended to done[*ndone++].
+// with LAP_MAXITER (in mode 0 when maxit[p] is 0); done (nullable): every retiring problem is
+// appended to done[*ndone++].
 cudaError_t launch_b_converge(const double* partials, const int* first_item, int count, int* active,
                               double* r0, double* rnow, long long* iters, int* status,
                               int* remaining, int mode, bool rel, double tol, cudaStream_t s,

@@ -138,6 +138,7 @@ struct SrvPlan {
     LevelLists mg64, mg32;
     std::pair<int, int> sor, update, init, norm;
     std::vector<int> first_init, first_norm;
+    std::vector<int> sor_upto;  // items of `sor` (a prefix) swept in the step's k-th sweep
 };
 
 }  // namespace
@@ -321,7 +322,28 @@ extern "C" int lap_server_step(lap_server S, void* stream, int* running, int* qu
             if (first) first->push_back((int)P.items.size() - i0);
             return std::make_pair(i0, (int)P.items.size() - i0);
         };
-        P.sor = level0([](const SrvRequest& r) { return r.method == LAP_SOR_RB; }, nullptr);
+        // An SOR request sweeps min(sor_sweeps, sweeps left of its max_iter) times this step, so
+        // that its last check period is cut short at max_iter as lap_solve cuts it. Its items are
+        // laid out by that count, largest first: sweep k takes a prefix of the list.
+        {
+            auto sweeps_now = [&](int q) {
+                const SrvRequest& r = *run[q];
+                return (int)std::min<int64_t>(S->sor_sweeps, r.max_iter - (int64_t)r.steps * S->sor_sweeps);
+            };
+            std::vector<int> sor_q;
+            for (int q = 0; q < R; ++q)
+                if (run[q]->method == LAP_SOR_RB) sor_q.push_back(q);
+            std::stable_sort(sor_q.begin(), sor_q.end(),
+                             [&](int a, int c) { return sweeps_now(a) > sweeps_now(c); });
+            P.sor.first = (int)P.items.size();
+            P.sor_upto.assign(S->sor_sweeps, 0);
+            for (int q : sor_q) {
+                add_items(P.items, base[q], run[q]->g.m, run[q]->g.n);
+                const int upto = (int)P.items.size() - P.sor.first;
+                for (int k = 0; k < sweeps_now(q); ++k) P.sor_upto[k] = upto;
+            }
+            P.sor.second = (int)P.items.size() - P.sor.first;
+        }
         P.update = level0([](const SrvRequest& r) { return r.method == LAP_MG_MIXED; }, nullptr);
         P.init = level0([](const SrvRequest& r) { return r.fresh; }, &P.first_init);
         P.norm = level0([](const SrvRequest&) { return true; }, &P.first_norm);
@@ -418,9 +440,11 @@ extern "C" int lap_server_step(lap_server S, void* stream, int* running, int* qu
         // fused: the level-0 ascents did psi += e except where a tail holds level 0
         ck(launch_b_update(list(P.mg32.fused ? P.mg32.upd0 : P.update), lv64, active, lv32, st),
            "server update");
-        for (int k = 0; k < S->sor_sweeps && P.sor.second; ++k)
+        for (int k = 0; k < S->sor_sweeps && P.sor.second; ++k) {
+            const std::pair<int, int> swept{P.sor.first, P.sor_upto[k]};
             for (int colour = 0; colour < 2; ++colour)
-                ck(launch_b_rb(list(P.sor), lv64, active, colour, false, 1.0, st, true), "server sweep");
+                ck(launch_b_rb(list(swept), lv64, active, colour, false, 1.0, st, true), "server sweep");
+        }
         ck(launch_b_sumsq(list(P.norm), lv64, active, pnorm, lv32, st, dr0), "server residual");
         ck(launch_b_converge(pnorm, fn, R, active, dr0, rnow, iters, status, remaining, 1, true, 0.0,
                              st, dtol, maxit, done, ndone), "server convergence");
@@ -444,7 +468,9 @@ extern "C" int lap_server_step(lap_server S, void* stream, int* running, int* qu
             r.r0 = c.r0;
             r.rnow = c.rnow;
             r.res.status = c.status;
-            r.res.iters = r.method == LAP_SOR_RB ? c.iters * S->sor_sweeps : c.iters;
+            // SOR: sweeps, the last batch cut short at max_iter
+            r.res.iters = r.method == LAP_SOR_RB ? std::min<int64_t>(c.iters * S->sor_sweeps, r.max_iter)
+                                                 : c.iters;
             r.res.r0 = c.r0;
             r.res.r_final = c.rnow;
             r.res.last_check = c.r0 > 0 ? c.rnow / c.r0 : 0.0;

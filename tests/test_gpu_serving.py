@@ -161,3 +161,63 @@ def test_completion_list_gives_the_same_results_as_polling(b):
     assert srv.drain() == []
     srv.close()
     lap.close()
+
+
+def test_requests_at_the_edges_of_the_contract(b):
+    """Each request against the same request solved alone with lap_solve (status, iterations
+    and field, bit for bit): SOR caps that are not a multiple of the step's sweeps (the last
+    step cut short, as lap_solve cuts its last check period), a cap of no iterations for every
+    method (the initial residual, the field untouched), fields that already solve the problem
+    (converged at once), dx != dy, and a NaN on the ring (DIVERGED at once). A method the server
+    does not run and an unknown id are refused."""
+    lap = b.Laplace()
+    srv = b.Server(lap, hbm_budget=64 << 20, max_running=32, sor_sweeps=K)
+    base = wl.random_ring(65, 33, seed=11)
+    w = wl.w_opt_sor(65, 33)
+    nan = wl.random_ring(33, 33, seed=15)
+    nan[0, 5] = np.nan
+    cases = [dict(psi=base, method="sor", w=w, tol=1e-12, max_iter=it) for it in (30, 7, K + 1)]
+    for method in ("sor", "mg", "mg_mixed"):
+        ww = w if method == "sor" else 1.0
+        cases.append(dict(psi=base, method=method, w=ww, tol=1e-10, max_iter=0))
+        cases.append(dict(psi=np.zeros((33, 65)), method=method, w=ww, tol=1e-10, max_iter=100))
+        cases.append(dict(psi=nan, method=method, w=1.5 if method == "sor" else 1.0, tol=1e-10,
+                          max_iter=100))
+    cases += [dict(psi=wl.random_ring(65, 65, seed=12), method="mg", tol=1e-10, max_iter=50, dy=0.5),
+              dict(psi=wl.random_ring(65, 65, seed=13), method="mg_mixed", tol=1e-10, max_iter=50, dx=0.5),
+              dict(psi=wl.random_ring(65, 65, seed=14), method="sor", w=1.7, tol=1e-6, max_iter=2000,
+                   dy=0.8)]
+    fields, ids = [], []
+    for c in cases:
+        f = b.to_field(c["psi"])
+        fields.append(f)
+        ids.append(srv.submit(f, c.get("dx", 1.0), c.get("dy", 1.0), method=c["method"],
+                              w=c.get("w", 1.0), tol=c["tol"], max_iter=c["max_iter"]))
+    results = {}
+    for _ in range(5000):
+        srv.step()
+        results.update(dict(srv.drain()))
+        if len(results) == len(cases):
+            break
+    for k, (c, f, rid) in enumerate(zip(cases, fields, ids)):
+        t = b.to_field(c["psi"])
+        g = lap.solve(t, c.get("dx", 1.0), c.get("dy", 1.0), method=c["method"], w=c.get("w", 1.0),
+                      tol=c["tol"], max_iter=c["max_iter"],
+                      check_every=K if c["method"] == "sor" else 1)
+        got = results[rid]
+        assert (got["status"], got["iters"]) == (g["status"], g["iters"]), (k, c["method"], got, g)
+        assert np.array_equal(host(f), host(t), equal_nan=True), k
+    assert [results[i]["iters"] for i in ids[:3]] == [30, 7, K + 1]
+    assert all(results[i]["status"] == "max_iter" for i in ids[:3])
+    for j in range(3):
+        zero_cap, solved, diverged = (results[ids[3 + 3 * j + d]] for d in range(3))
+        assert (zero_cap["status"], zero_cap["iters"]) == ("max_iter", 0)
+        assert zero_cap["r_final"] == zero_cap["r0"] > 0
+        assert (solved["status"], solved["iters"]) == ("converged", 0)
+        assert (diverged["status"], diverged["iters"]) == ("diverged", 0)
+    with pytest.raises(b.LapError):
+        srv.submit(b.to_field(base), method="adi", w=1.3)
+    with pytest.raises(b.LapError):
+        srv.poll(10 ** 12)
+    srv.close()
+    lap.close()
