@@ -176,8 +176,9 @@ int lap_create(lap_handle* out, size_t hbm_budget_bytes, int device);
 void lap_destroy(lap_handle h);
 
 /* Scratch bytes lap_solve needs for this grid and method (admission against a budget).
- * Host arithmetic only: no allocation, no device access. Gives the refusals lap_solve would
- * give for the shape and parameters (LAP_EINVAL, LAP_EUNSUPPORTED: the size limits above). */
+ * Host arithmetic: no allocation and no launch (it reads the current device's multiprocessor
+ * count, 152 when there is no device). Gives the refusals lap_solve would give for the shape
+ * and parameters (LAP_EINVAL, LAP_EUNSUPPORTED: the size limits above). */
 int lap_workspace_bytes(const lap_grid* g, const lap_params* p, size_t* bytes);
 
 /* Iterate p->method on psi_dev until the stopping rule (p->norm, p->tol) holds or
