@@ -182,3 +182,34 @@ def test_batched_device_loop_equals_host_polled_cycles(b, method):
         if kw["max_iter"] <= 4:
             assert max(it for _, it, _ in on[1]) == kw["max_iter"]
     lap.close()
+
+
+@pytest.mark.parametrize("method", ["mg", "mg_mixed"])
+def test_batched_edge_problems_equal_their_own_solves(b, method):
+    """One batch holding a NaN on a problem's ring (DIVERGED at once, its field untouched), a
+    field that already solves its problem (converged at once), dx != dy and ordinary problems,
+    solved with a cap of 40 cycles and again with a cap of 0 (every problem stops at its initial
+    residual: MAXITER unless converged or diverged at once, fields untouched). Each result is
+    the problem's own lap_solve: status, cycles and field, bit for bit."""
+    lap = b.Laplace()
+    nan = wl.random_ring(33, 33, seed=41)
+    nan[0, 7] = np.nan
+    inputs = [wl.random_ring(65, 33, seed=40), nan, np.zeros((33, 65)),
+              wl.random_ring(65, 65, seed=42), wl.random_ring(33, 129, seed=43)]
+    dxs = [1.0, 1.0, 1.0, 0.5, 1.0]
+    for max_iter in (40, 0):
+        fields = [b.to_field(x) for x in inputs]
+        res = lap.solve_batched(fields, dxs, 1.0, method=method, tol=1e-10, max_iter=max_iter)
+        for k, (x, f, r) in enumerate(zip(inputs, fields, res)):
+            t = b.to_field(x)
+            g = lap.solve(t, dxs[k], 1.0, method=method, tol=1e-10, max_iter=max_iter)
+            assert (r["status"], r["iters"]) == (g["status"], g["iters"]), (max_iter, k, r, g)
+            assert np.array_equal(host(f), host(t), equal_nan=True), (max_iter, k)
+        assert [r["status"] for r in res[1:3]] == ["diverged", "converged"]
+        assert [r["iters"] for r in res[1:3]] == [0, 0]
+        if max_iter == 0:
+            assert all(r["iters"] == 0 for r in res)
+            assert res[0]["status"] == "max_iter" and res[0]["r_final"] == res[0]["r0"] > 0
+        else:
+            assert all(res[k]["status"] == "converged" for k in (0, 3, 4))
+    lap.close()
